@@ -1,0 +1,282 @@
+"""Pins of the CPU oracle against things other than itself (no GPU).
+
+Each test ties a part of the oracle to mathematics or to the paper: exactness of
+Newton-Cotes / Lagrange rules on polynomials, quadrature of the area, the
+closed-form volume potential of a disc, the Bessel-series solution of the
+penetrable disc (Section 3.3 Example 1), dense LU for GMRES, energy
+conservation (optical theorem) and reciprocity for the far field, an adaptive
+1-D integral for the polar rule, and the equivalent-source accuracy levels of
+the paper's acceleration tables.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy.integrate import quad
+from scipy.special import j0, y0
+
+import workloads as W
+from oracle import exact, farfield
+from oracle import geometry as geo
+from oracle import quadrature as qd
+from oracle.accel import Accelerator, Cells, mono_kernel, _lstsq_apply
+from oracle.geometry import Discretisation
+from oracle.gmres import gmres
+from oracle.operator import DirectOperator
+
+GOLDEN = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_tables.json")))
+
+QUAD = dict(collar_w=0.6, tau0=0.3, tau1=0.95, n_rho=48, N_tau=64)
+
+
+def disc_wl(level, n2c=0.0, kappa=2.0, **kw):
+    R = {1: dict(R_a=4, R_b=2, R_cart=3, p=7), 2: dict(R_a=8, R_b=4, R_cart=6)}[level]
+    args = dict(QUAD)
+    args.update(R)
+    args.update(kw)
+    return W.disc(level=level, kappa=kappa, n2c=n2c, **args)
+
+
+@pytest.fixture(scope="module")
+def K1_level1():
+    """Operator with m = 1 (n^2 = 0) at level 1; K is linear in m."""
+    dz = Discretisation(disc_wl(1))
+    return dz, DirectOperator(dz)
+
+
+@pytest.fixture(scope="module")
+def K1_level2():
+    dz = Discretisation(disc_wl(2))
+    return dz, DirectOperator(dz)
+
+
+# ---------------------------------------------------------------- building blocks
+@pytest.mark.parametrize("Q", [2, 3, 4, 5])
+def test_newton_cotes_is_exact_on_polynomials(Q):
+    w = geo.newton_cotes(Q)
+    x = np.arange(Q, dtype=float)
+    deg = Q - 1 if Q % 2 == 0 else Q      # odd Q gains one degree by symmetry
+    for k in range(deg + 1):
+        assert abs(np.dot(w, x ** k) - (Q - 1) ** (k + 1) / (k + 1)) < 1e-12 * (Q ** k)
+    # and is not exact one degree higher
+    k = deg + 1
+    assert abs(np.dot(w, x ** k) - (Q - 1) ** (k + 1) / (k + 1)) > 1e-6
+
+
+def test_composite_newton_cotes_integrates_polynomials():
+    w = geo.composite_nc(17, 5)
+    x = np.arange(17.0)
+    for k in range(6):
+        assert abs(np.dot(w, x ** k) - 16.0 ** (k + 1) / (k + 1)) < 1e-9 * 16.0 ** (k + 1)
+
+
+@pytest.mark.parametrize("j", [0, 1, 2, 3, 5, 7, 9, 15, 16])
+def test_split_newton_cotes_exact_piecewise(j):
+    """Eq. VolInt-Adj-Sing-MultiSplit integrates, on each side of t_2^x, any
+    polynomial of degree <= Q exactly (the integrand may kink at t_2^x)."""
+    nb, Q = 17, 5
+    tb = qd.split_newton_cotes(j, nb, Q)
+    b = np.array(sorted(tb))
+    w = np.array([tb[v] for v in b])
+    assert np.all(w > 0)
+    top = nb - 1
+    assert abs(w.sum() - top) < 1e-12
+    for k in range(1, Q + 1):                              # continuous at j, kink allowed
+        f = np.where(b <= j, (j - b) ** k, 0.0)           # polynomial left of j only
+        assert abs(np.dot(w, f) - j ** (k + 1) / (k + 1)) < 1e-9 * max(1.0, j ** (k + 1))
+        g = np.where(b >= j, (b - j) ** k, 0.0)
+        assert abs(np.dot(w, g) - (top - j) ** (k + 1) / (k + 1)) < 1e-9 * max(1.0, (top - j) ** (k + 1))
+
+
+def test_lagrange_reproduces_polynomials():
+    rng = np.random.default_rng(0)
+    x = rng.random(50) * 20 - 10
+    p = 9
+    start = qd.stencil_start(x, p)
+    L = qd.lagrange(x, start, p)
+    nodes = start[:, None] + np.arange(p + 1)
+    for k in range(p + 1):
+        assert np.max(np.abs(np.sum(L * nodes ** k, 1) - x ** k)) < 1e-9 * 10.0 ** k
+    assert np.allclose(L.sum(1), 1.0)
+
+
+def test_cutoff_and_partition_of_unity():
+    s = np.linspace(-2, 2, 4001)
+    c = qd.chi(s, 0.1)
+    assert np.all(c[np.abs(s) <= 0.1] == 1.0) and np.all(c[np.abs(s) >= 1.0] == 0.0)
+    assert np.all(np.diff(c[s >= 0]) <= 1e-15)
+    u = np.linspace(-0.5, 1.5, 2001)
+    S = geo.smooth_step(u)
+    assert np.allclose(S + geo.smooth_step(1.0 - u), 1.0)
+
+
+def test_polar_rule_against_adaptive_radial_integral():
+    """The polar template integrates G chi over the cut-off disc (a radial
+    integral that scipy.quad resolves adaptively)."""
+    kappa, h, R = 2.0, 0.05, 6.0
+    wl = disc_wl(1, n_rho=96)
+    da, db, wq = qd.polar_template(wl, R, R)
+    rr = np.hypot(da, db) * h
+    val = np.sum(wq * h * h * 0.25j * (j0(kappa * rr) + 1j * y0(kappa * rr)))
+    chi = lambda r: qd.chi(np.array([r / (R * h)]), wl.chi_s0)[0]
+    re = quad(lambda r: -2 * math.pi * r * 0.25 * y0(kappa * r) * chi(r), 0, R * h, limit=200)[0]
+    im = quad(lambda r: 2 * math.pi * r * 0.25 * j0(kappa * r) * chi(r), 0, R * h, limit=200)[0]
+    assert abs(val - (re + 1j * im)) / abs(re + 1j * im) < 1e-7
+
+
+def test_collar_chart_is_a_valid_parametrisation():
+    """Collar Jacobian equals (a - t w) 2 pi w / (n1 (n2 - 1)) on the disc, and
+    the inverse map recovers (s, t) of collar points."""
+    wl = disc_wl(1)
+    a = np.linspace(0, wl.n1, 37)
+    b = np.linspace(0, wl.n2 - 1, 37)
+    X, J = geo.collar_map(wl, a, b)
+    t = b / (wl.n2 - 1)
+    assert np.allclose(J, (1 - t * wl.collar_w) * 2 * math.pi * wl.collar_w / (wl.n1 * (wl.n2 - 1)))
+    s, d = geo.closest_point(wl, X)
+    assert np.allclose(d / wl.collar_w, t, atol=1e-12)
+    kite = W.kite(n1=256, n2=9, h=0.05, kappa=2.0, p=7, R_b=2, tau0=0.4, tau1=0.9, collar_w=0.07)
+    a = np.linspace(0, 255, 91)
+    Xk, Jk = geo.collar_map(kite, a, np.full(91, 4.0))
+    s, d = geo.closest_point(kite, Xk)
+    assert np.allclose(d, 0.5 * 0.07, atol=1e-12)
+    assert np.all(Jk > 0)
+
+
+@pytest.mark.parametrize("shape", ["disc", "kite"])
+def test_node_weights_integrate_the_area(shape):
+    if shape == "disc":
+        wl, area = disc_wl(2), math.pi
+        tol = 1e-4
+    else:
+        wl = W.kite(n1=512, n2=17, h=0.02, kappa=2.0, R_b=4, tau0=0.4, tau1=0.9, collar_w=0.07)
+        area, tol = 1.5 * math.pi, 2e-4
+    dz = Discretisation(wl)
+    assert abs(np.sum(dz.w * dz.omega) - area) < tol * area
+
+
+# ---------------------------------------------------------------- the operator
+def test_operator_is_identity_when_n2_is_one():
+    dz = Discretisation(disc_wl(1, n2c=1.0))
+    op = DirectOperator(dz)
+    assert np.max(np.abs(op.dense_K())) == 0.0
+
+
+def test_closed_form_volume_potential(K1_level1, K1_level2):
+    """K[1](x) = -1/kappa^2 + (i pi a/(2 kappa)) H_1(kappa a) J_0(kappa|x|) on the
+    unit disc; exercises every quadrature of the operator.  The error falls by
+    more than 2^2.5 when the grid is halved (these coarse levels are still
+    pre-asymptotic; the expected Newton-Cotes order is Q + 1 = 6)."""
+    errs = []
+    for dz, op in (K1_level1, K1_level2):
+        Ku = op.apply_K(np.ones(dz.N, complex))
+        ref = exact.disc_volume_potential_const(dz.wl.kappa, 1.0, dz.x)
+        errs.append(np.max(np.abs(Ku - ref)) / np.max(np.abs(ref)))
+    assert errs[0] < 1e-2 and errs[1] < 1e-3
+    assert errs[0] / errs[1] > 2 ** 2.5
+
+
+def test_disc_solution_against_bessel_series(K1_level1, K1_level2):
+    """Section 3.3 Example 1 style check: penetrable disc, n^2 = 2, kappa = 2."""
+    errs, its = [], []
+    for dz, op in (K1_level1, K1_level2):
+        A = np.eye(dz.N) - dz.wl.kappa ** 2 * op.dense_K()      # m = 1 - 2 = -1
+        ui = W.plane_wave(dz.wl.kappa, (1, 0), dz.x)
+        u, it, _ = gmres(lambda v: A @ v, ui, tol=1e-12, restart=200)
+        ud = np.linalg.solve(A, ui)
+        assert np.linalg.norm(u - ud) / np.linalg.norm(ud) < 1e-10
+        ue = exact.disc_total_field(dz.wl.kappa, 2.0, 1.0, dz.x)
+        errs.append(np.linalg.norm(u - ue) / np.linalg.norm(ue))
+        its.append(it)
+    assert errs[1] < 1e-3 and errs[0] / errs[1] > 8.0
+    g = GOLDEN["disc_Q5_kappa5_n_sqrt2"]["iterations"]
+    assert all(min(g) - 6 <= i <= max(g) + 6 for i in its)
+
+
+def test_gmres_restarts_reach_the_dense_solution(K1_level1):
+    dz, op = K1_level1
+    A = np.eye(dz.N) - 4.0 * op.dense_K()
+    b = W.random_density(dz.N)[0]
+    x, it, hist = gmres(lambda v: A @ v, b, tol=1e-11, restart=5, max_iter=500)
+    assert np.linalg.norm(A @ x - b) / np.linalg.norm(b) < 1e-10
+    assert np.linalg.norm(x - np.linalg.solve(A, b)) / np.linalg.norm(x) < 1e-8
+
+
+def test_series_reduces_to_plane_wave_for_n_equal_one():
+    x = np.random.default_rng(3).random((40, 2)) * 3 - 1.5
+    u = exact.disc_total_field(3.0, 1.0, 1.0, x, d=(0.6, 0.8))
+    assert np.allclose(u, W.plane_wave(3.0, (0.6, 0.8), x), atol=1e-12)
+
+
+def test_series_far_field_optical_theorem():
+    """Energy conservation for real n: int |A|^2 = -2 sqrt(2 pi / kappa) Re(e^{i pi/4} A(d))."""
+    kappa = 4.0
+    th = np.linspace(0, 2 * math.pi, 512, endpoint=False)
+    A = exact.disc_far_field(kappa, 2.0, 1.0, th)
+    lhs = np.sum(np.abs(A) ** 2) * 2 * math.pi / len(th)
+    rhs = -2 * math.sqrt(2 * math.pi / kappa) * np.real(np.exp(1j * math.pi / 4) * A[0])
+    assert abs(lhs - rhs) < 1e-10 * abs(lhs)
+
+
+def test_far_field_of_solution_and_reciprocity(K1_level2):
+    import copy
+    dz0, op = K1_level2
+    dz = copy.copy(dz0)                      # same nodes, true contrast n^2 = 2
+    dz.n2 = np.full(dz.N, 2.0)
+    k = dz.wl.kappa
+    A = np.eye(dz.N) - k ** 2 * op.dense_K()
+    th = np.linspace(0, 2 * math.pi, 16, endpoint=False)
+    u = np.linalg.solve(A, W.plane_wave(k, (1, 0), dz.x))
+    ff = farfield.far_field(dz, u, th)
+    ffe = exact.disc_far_field(k, 2.0, 1.0, th)
+    assert np.max(np.abs(ff - ffe)) / np.max(np.abs(ffe)) < 1e-3
+    # reciprocity A(xhat; d) = A(-d; -xhat) for two generic directions
+    d1, d2 = 0.3, 2.1
+    u1 = np.linalg.solve(A, W.plane_wave(k, (math.cos(d1), math.sin(d1)), dz.x))
+    u2 = np.linalg.solve(A, W.plane_wave(k, (-math.cos(d2), -math.sin(d2)), dz.x))
+    a12 = farfield.far_field(dz, u1, np.array([d2]))[0]
+    a21 = farfield.far_field(dz, u2, np.array([d1 + math.pi]))[0]
+    assert abs(a12 - a21) < 1e-3 * abs(a12)
+
+
+# ---------------------------------------------------------------- the accelerator
+def _accel_wl(Ne, kappa=2.0):
+    return disc_wl(2, n2c=2.0, kappa=kappa, R_a=4, R_b=4, R_cart=5,
+                   box_x0=-1.2, box_y0=-1.2, H=0.3, L=8, N_eq=Ne, n_fb=2 * Ne - 1)
+
+
+def test_equivalent_source_fit_accuracy():
+    """Exterior field of one cell's equivalent sources vs its true sources; the
+    error falls with the number of sources per face as in Table accel1/accel2."""
+    dz = Discretisation(_accel_wl(6))
+    errs = {}
+    for Ne in (6, 12):
+        acc = Accelerator(dz.__class__(_accel_wl(Ne)))
+        H = acc.H
+        rng = np.random.default_rng(5)
+        src = rng.random((30, 2)) * H
+        q = rng.standard_normal(30) + 1j * rng.standard_normal(30)
+        b = mono_kernel(acc.kappa, acc.coll[:, 0][:, None] - src[None, :, 0],
+                        acc.coll[:, 1][:, None] - src[None, :, 1]) @ q
+        sig = _lstsq_apply(acc.Asvd, b[:, None])[:, 0]
+        t = np.linspace(-2 * H, 3 * H, 101)
+        pts = np.concatenate([np.stack([t, np.full_like(t, -2 * H)], -1),
+                              np.stack([np.full_like(t, 3 * H), t], -1)])
+        true = mono_kernel(acc.kappa, pts[:, 0][:, None] - src[None, :, 0],
+                           pts[:, 1][:, None] - src[None, :, 1]) @ q
+        es = acc._es_field(pts[:, 0], pts[:, 1]) @ sig
+        errs[Ne] = np.max(np.abs(es - true)) / np.max(np.abs(true))
+    paper = GOLDEN["es_accuracy_fixed_kappa"]["eps2"]
+    assert errs[6] < 10 * paper[1]          # ~ the paper's 6 x 4 level or better
+    assert errs[12] < 1e-10
+
+
+def test_accelerated_far_part_matches_direct_sum():
+    dz = Discretisation(_accel_wl(12))
+    acc = Accelerator(dz)
+    u = W.random_density(dz.N)[0]
+    vf = acc.apply_far(u)
+    ref = acc.direct_far(u)
+    assert np.linalg.norm(vf - ref) / np.linalg.norm(ref) < 1e-10

@@ -1,0 +1,175 @@
+"""Seeded synthetic workloads for the Lippmann-Schwinger solver (2-D).
+
+This module only *describes* inputs: the scatterer family and its parameters,
+the refractive-index profile n^2(x), the incident plane wave, the wavenumber,
+the resolution / quadrature parameters of the Nystrom discretisation and the
+seeded random densities used for apply-throughput runs.  It holds none of the
+method's arithmetic (no charts, weights, quadratures, Green's functions or
+acceleration), so both the CPU oracle and the CUDA library consume it without
+sharing any of the method with each other.
+
+The shapes mirror the paper's experiments (disc, Section 3.3 Example 1 / the
+timing table; the kite stands in for the paper's "bean", whose parametrisation
+is not given).  All randomness comes from numpy's PCG64 seeded with 150905063.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+SEED = 150905063
+
+SHAPES = {"disc": 0, "kite": 1}
+N2_KINDS = {"const": 0, "gauss": 1, "sincos": 2}
+
+
+@dataclass
+class Workload:
+    """All parameters that define one discrete LS operator (2-D).
+
+    Geometry: boundary curve gamma(s), s in [0, 2pi).
+      disc : shape_params = (a, cx, cy)      gamma = c + a(cos s, sin s)
+      kite : shape_params = (scale, cx, cy)  gamma = c + scale(cos s + 0.65 cos 2s - 0.65, 1.5 sin s)
+    Collar (boundary) chart: X(a, b) = gamma(2 pi a / n1) - (b / (n2 - 1)) * collar_w * nu,
+      a in [0, n1) periodic, b in [0, n2 - 1]; b = 0 lies on the boundary.
+    Interior chart: Cartesian grid x = cart_x0 + i h, y = cart_y0 + j h,
+      0 <= i < cart_nx, 0 <= j < cart_ny; only points with omega_I > 0 are nodes.
+    Partition of unity: omega_B = S((t - tau0) / (tau1 - tau0)) on the collar,
+      omega_I = 1 - omega_B.
+    Quadrature: Q-point composite Newton-Cotes across the collar, Lagrange
+      interpolation of degree p, cut-off radii in grid-index units (R_a along
+      and R_b across the collar, R_cart on the Cartesian patch), rho(tau) = R tau^(M+1) with N_tau trapezoid points for the boundary
+      singular rule, polar rule with n_rho x n_theta points and rho = R s^q_polar.
+    Acceleration: square box [box_x0, box_x0 + L H] x [box_y0, box_y0 + L H],
+      L x L cells of side H, lattice spacing H / N_eq, Fourier-Bessel order n_fb,
+      n_coll collocation points on the 3H x 3H square around a cell.
+    """
+
+    name: str
+    shape: str
+    shape_params: tuple
+    kappa: float
+    n2_kind: str
+    n2_params: tuple
+    inc_dir: tuple = (1.0, 0.0)
+    collar_w: float = 0.4
+    n1: int = 64
+    n2: int = 9
+    tau0: float = 0.35
+    tau1: float = 0.8
+    h: float = 0.1
+    cart_x0: float = -1.0
+    cart_y0: float = -1.0
+    cart_nx: int = 21
+    cart_ny: int = 21
+    Q: int = 5
+    p: int = 9
+    R_a: float = 8.0
+    R_b: float = 4.0
+    R_cart: float = 6.0
+    M: int = 4
+    N_tau: int = 48
+    q_polar: int = 3
+    n_rho: int = 24
+    n_theta: int = 32
+    chi_s0: float = 0.1
+    # acceleration (ignored by the direct operator)
+    box_x0: float = -1.2
+    box_y0: float = -1.2
+    H: float = 0.3
+    L: int = 8
+    N_eq: int = 8
+    n_fb: int = 15
+    n_coll: int = 0  # 0 -> 4 * (4 (N_eq + 1))
+    dim: int = 2
+
+    def replace(self, **kw) -> "Workload":
+        return dataclasses.replace(self, **kw)
+
+    @property
+    def n_collar(self) -> int:
+        return self.n1 * self.n2
+
+
+def n2_eval(kind: str, params: tuple, x: np.ndarray) -> np.ndarray:
+    """Refractive index squared n^2 at points x (..., 2).  Input definition only."""
+    x = np.asarray(x, dtype=np.float64)
+    if kind == "const":
+        return np.full(x.shape[:-1], float(params[0]))
+    if kind == "gauss":  # n^2 = a + b exp(-|x - c|^2 / s)
+        a, b, s, cx, cy = params
+        r2 = (x[..., 0] - cx) ** 2 + (x[..., 1] - cy) ** 2
+        return a + b * np.exp(-r2 / s)
+    if kind == "sincos":  # n^2 = a + b sin(pi x1) cos(pi x2)
+        a, b = params[:2]
+        return a + b * np.sin(np.pi * x[..., 0]) * np.cos(np.pi * x[..., 1])
+    raise ValueError(kind)
+
+
+def plane_wave(kappa: float, d, x: np.ndarray) -> np.ndarray:
+    """Incident field exp(i kappa d . x) at points x (..., 2)."""
+    d = np.asarray(d, dtype=np.float64)
+    d = d / np.linalg.norm(d)
+    return np.exp(1j * kappa * (x[..., 0] * d[0] + x[..., 1] * d[1]))
+
+
+def random_density(n: int, nrhs: int = 1, seed: int = SEED) -> np.ndarray:
+    """u ~ CN(0, 1), shape (nrhs, n), complex128, seeded."""
+    rng = np.random.default_rng(seed)
+    re = rng.standard_normal((nrhs, n))
+    im = rng.standard_normal((nrhs, n))
+    return ((re + 1j * im) / math.sqrt(2.0)).astype(np.complex128)
+
+
+def random_rows(n: int, k: int, seed: int = SEED + 1) -> np.ndarray:
+    rng = np.random.default_rng(seed)
+    return np.sort(rng.choice(n, size=min(k, n), replace=False))
+
+
+# --------------------------------------------------------------------------
+# Named workloads.  Resolutions follow the paper's grid families
+# (boundary patch n1 x n2 plus an interior Cartesian patch).
+# --------------------------------------------------------------------------
+
+def _cart_grid_for(h: float, lo: float, hi: float, anchor: float = 0.0):
+    """Cartesian grid covering [lo, hi] with points anchor + i h."""
+    i0 = math.floor((lo - anchor) / h) - 1
+    i1 = math.ceil((hi - anchor) / h) + 1
+    return anchor + i0 * h, i1 - i0 + 1
+
+
+def disc(level: int = 1, kappa: float = 2.0, n2c: float = 2.0, a: float = 1.0,
+         Q: int = 5, accel: dict | None = None, **kw) -> Workload:
+    """Penetrable disc of radius a, constant n^2 inside, plane wave along x1.
+
+    level l: collar n1 = 32 * 2^l tangential, n2 = (Q-1) 2^l + 1 transverse,
+    Cartesian spacing matched to the collar's tangential spacing at radius a/2.
+    """
+    n1 = 32 * 2 ** level
+    n2 = (Q - 1) * 2 ** (level) + 1
+    w = kw.pop("collar_w", 0.45 * a)
+    h = kw.pop("h", 2 * math.pi * a / n1 * 1.0)
+    x0, nx = _cart_grid_for(h, -a, a)
+    wl = Workload(name=f"disc_l{level}", shape="disc", shape_params=(a, 0.0, 0.0),
+                  kappa=kappa, n2_kind="const", n2_params=(n2c,), collar_w=w,
+                  n1=n1, n2=n2, h=h, cart_x0=x0, cart_y0=x0, cart_nx=nx, cart_ny=nx,
+                  Q=Q, **kw)
+    if accel:
+        wl = wl.replace(**accel)
+    return wl
+
+
+def kite(n1: int, n2: int, h: float, kappa: float, scale: float = 1.0, collar_w: float = 0.07,
+         n2_kind: str = "gauss", n2_params: tuple | None = None, **kw) -> Workload:
+    if n2_params is None:
+        n2_params = (1.5, 0.5, 0.1 * scale * scale, 0.0, 0.0)
+    lo_x, hi_x = -1.5 * scale, 1.0 * scale
+    lo_y, hi_y = -1.5 * scale, 1.5 * scale
+    x0, nx = _cart_grid_for(h, lo_x, hi_x)
+    y0, ny = _cart_grid_for(h, lo_y, hi_y)
+    return Workload(name=f"kite_{n1}x{n2}", shape="kite", shape_params=(scale, 0.0, 0.0),
+                    kappa=kappa, n2_kind=n2_kind, n2_params=n2_params, collar_w=collar_w,
+                    n1=n1, n2=n2, h=h, cart_x0=x0, cart_y0=y0, cart_nx=nx, cart_ny=ny, **kw)
