@@ -1,0 +1,338 @@
+#!/usr/bin/env python
+"""Benchmark: LS matvecs/s and time to a 1e-10 solve, FP64 vs mixed, on one GB300.
+
+Workload (config 2): kite x = cos t + 0.65 cos 2t - 0.65, y = 1.5 sin t,
+n^2 = 1.5 + 0.5 exp(-|x|^2 / 0.1) inside, kappa = 20, ~274k Nystrom nodes,
+1024 x 1024 padded lattice FFT, synthetic seeded data.
+
+A step is one application of the whole hot path (equivalent-source projection,
+lattice FFT convolution, local expansion, near-field correction, assembly) to
+one right-hand side already resident in HBM.  ``value`` is FP64 matvecs/s over
+all ranks (replicas: one independent plan per GPU, no collectives).  ``e2e``
+times the same through the public API with the input copied from pinned host
+memory and the result read back every step.  The mixed (complex64) apply and
+the time to a 1e-10 solve with each path are reported beside it.
+
+``--impl reference`` times the CPU oracle (direct O(N^2) Nystrom sum, plain
+FP64 numpy) on a bounded sample of rows of the same operator.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "LS matvecs/s and time to 1e-10 solve at N, mixed vs FP64 path, 1 GB300"
+FALLBACK_HBM_GBS = 6800.0
+KERNELS_PER_APPLY = 11   # projection, lattice fill, 3 x (row + column FFT), product, local, near
+
+
+def hbm_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            d = json.load(open(p))
+            for k in ("hbm_gbs", "hbm_GBs", "hbm_copy_gbs"):
+                if k in d:
+                    return float(d[k]), "measured"
+        except Exception:
+            pass
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            self.proc.wait()
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 9:
+                    continue
+                try:
+                    sm.append(float(f[1]))
+                    smax.append(float(f[2]))
+                except ValueError:
+                    continue
+                for n, v in zip(names, f[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(n)
+        except Exception:
+            pass
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_info():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def cpu_oracle_rate(wl, n_rows: int, seed_rows=None):
+    """Oracle direct O(N^2) apply on a bounded sample of rows: returns
+    (matvecs/s extrapolated from rows/s, rows, seconds, N)."""
+    import numpy as np
+    import workloads as W
+    from oracle.geometry import Discretisation
+    from oracle.operator import DirectOperator
+    dz = Discretisation(wl)
+    op = DirectOperator(dz, dense_limit=0)
+    rows = W.random_rows(dz.N, n_rows)
+    u = W.random_density(dz.N)[0]
+    t0 = time.perf_counter()
+    op.apply(u, rows=rows)
+    dt = time.perf_counter() - t0
+    return (len(rows) / dt) / dz.N, len(rows), dt, dz.N
+
+
+def run_reference(args):
+    rank, world, _ = dist_info()
+    if rank != 0:
+        return 0
+    import workloads as W
+    wl = W.cfg2()
+    rows_per_step = args.ref_rows
+    import numpy as np
+    from oracle.geometry import Discretisation
+    from oracle.operator import DirectOperator
+    dz = Discretisation(wl)
+    op = DirectOperator(dz, dense_limit=0)
+    u = W.random_density(dz.N)[0]
+    rows_all = W.random_rows(dz.N, rows_per_step * (args.steps + args.warmup))
+    for s in range(args.warmup):
+        op.apply(u, rows=rows_all[s * rows_per_step:(s + 1) * rows_per_step])
+    t0 = time.perf_counter()
+    for s in range(args.warmup, args.warmup + args.steps):
+        op.apply(u, rows=rows_all[s * rows_per_step:(s + 1) * rows_per_step])
+    dt = time.perf_counter() - t0
+    rate = (args.steps * rows_per_step / dt) / dz.N
+    line = {
+        "impl": "reference", "metric": METRIC, "value": rate, "unit": "matvecs/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"cfg2 kite kappa=20 N={dz.N}", "N": dz.N,
+                   "sample": f"{rows_per_step} seeded rows x all N sources per step"},
+        "cpu_baseline": {"value": rate, "unit": "matvecs/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{rows_per_step} rows/step of the direct O(N^2) apply, extrapolated to N rows"},
+        "e2e": {"value": rate, "unit": "matvecs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-solve", action="store_true")
+    ap.add_argument("--cpu-rows", type=int, default=192)
+    ap.add_argument("--ref-rows", type=int, default=48)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+    import workloads as W
+    from paper_1509_05063_gb300 import LS_FP64, LS_MIXED, Plan
+
+    rank, world, local = dist_info()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    wl = W.cfg2()
+    plan = Plan(wl, W.n2_of(wl))
+    info = plan.info
+    N = plan.N
+    u = torch.from_numpy(W.random_density(N, seed=W.SEED + rank)[0]).to(dev)
+    u32 = u.to(torch.complex64)
+    out = torch.empty_like(u)
+    out32 = torch.empty_like(u32)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    def timed(fn, steps):
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            fn()
+        e1.record()
+        barrier()
+        ms = e0.elapsed_time(e1)
+        if world > 1:
+            t = torch.tensor([ms], device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms
+
+    f64 = lambda: plan.apply(u, out, prec=LS_FP64)
+    f32 = lambda: plan.apply(u32, out32, prec=LS_MIXED)
+    for _ in range(args.warmup):
+        f64()
+        f32()
+    with Clocks(local) as clk:
+        ms64 = timed(f64, args.steps)
+        ms32 = timed(f32, args.steps)
+    clocks = clk.summary()
+
+    # per-stage CUDA-event timing on the launch stream (roofline of the dominant kernel)
+    plan.set_stage_timing(True)
+    for _ in range(args.steps):
+        f64()
+    st64, c64 = plan.stage_times(LS_FP64)
+    for _ in range(args.steps):
+        f32()
+    st32, c32 = plan.stage_times(LS_MIXED)
+    plan.set_stage_timing(False)
+
+    # end to end through the public API: pinned host input in, result out, every step
+    h_u = torch.from_numpy(W.random_density(N, seed=W.SEED + 7 + rank)[0]).pin_memory()
+    h_out = torch.empty_like(h_u).pin_memory()
+    d_u = torch.empty_like(u)
+
+    def e2e_step():
+        d_u.copy_(h_u, non_blocking=True)
+        plan.apply(d_u, out, prec=LS_FP64)
+        h_out.copy_(out, non_blocking=True)
+
+    for _ in range(args.warmup):
+        e2e_step()
+    ms_e2e = timed(e2e_step, args.steps)
+
+    # time to tolerance
+    solve = None
+    if not args.no_solve:
+        xy, _ = plan.nodes()
+        ui = torch.from_numpy(W.plane_wave(wl.kappa, wl.inc_dir, xy)).to(dev)
+        plan.solve(ui, tol=1e-4, prec=LS_FP64, max_iter=5)      # allocate work space
+        barrier()
+        t0 = time.perf_counter()
+        s64, i64 = plan.solve(ui, tol=1e-10, prec=LS_FP64, max_iter=800, restart=100)
+        barrier()
+        t64 = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        s32, i32 = plan.solve(ui, tol=1e-10, prec=LS_MIXED, max_iter=800, restart=100)
+        barrier()
+        t32 = time.perf_counter() - t0
+        diff = float(torch.linalg.vector_norm(s32 - s64) / torch.linalg.vector_norm(s64))
+        solve = {"tol": 1e-10, "fp64_s": t64, "fp64_iterations": i64["iterations"],
+                 "fp64_residual": i64["residual"], "fp64_converged": i64["converged"],
+                 "mixed_s": t32, "mixed_inner_iterations": i32["iterations"],
+                 "mixed_refinements": i32["refinements"], "mixed_residual": i32["residual"],
+                 "mixed_converged": i32["converged"], "mixed_vs_fp64_solution_rel": diff}
+
+    # roofline of the dominant kernel (near field + local evaluation + assembly)
+    nnz = info["nnz_near"]
+    nfb2 = 2 * info["n_fb"] + 1
+    nocc = info["n_cells_occupied"]
+
+    def near_bytes(cb):   # algorithmic bytes of one k_near_eval launch, cb = bytes per complex
+        return nnz * (cb + 4) + (N + 1) * 8 + N * cb + N * nfb2 * cb + N * 4 + nocc * nfb2 * cb + N * cb
+
+    peak, peak_src = hbm_peak()
+    t_near64 = st64[4] / max(c64, 1) * 1e-3
+    t_near32 = st32[4] / max(c32, 1) * 1e-3
+    ach64 = near_bytes(16) / t_near64 / 1e9
+    ach32 = near_bytes(8) / t_near32 / 1e9
+    M = info["fft_M"]
+    apply_bytes64 = (2 * N * 16 + nnz * 20 + 6 * M * M * 16 + 2 * M * M * 16)
+    stage_names = ["es_project", "lattice_fill", "lattice_fft_conv", "local_coeffs", "near_eval"]
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, nrows, dt, n = cpu_oracle_rate(wl, args.cpu_rows)
+        cpu = {"value": rate, "unit": "matvecs/s", "cores": 1, "kind": "oracle",
+               "sample": f"{nrows} seeded rows of the direct O(N^2) FP64 apply ({dt:.1f} s), "
+                         f"extrapolated to all {n} rows"}
+
+    value = world * args.steps / (ms64 * 1e-3)
+    line = {
+        "metric": METRIC, "value": value, "unit": "matvecs/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms64 / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"cfg2 kite kappa=20 N={N} nnz_near={nnz} lattice {M}x{M}",
+                   "N": N, "nnz_near": nnz, "fft_M": M, "L": info["L"], "N_eq": info["N_eq"],
+                   "n_fb": info["n_fb"], "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2 (near-field weights %.1f GB)" % (nnz * 20 / 1e9),
+                   "plan_seconds": info["plan_seconds"], "device_bytes": info["device_bytes"]},
+        "e2e": {"value": world * args.steps / (ms_e2e * 1e-3), "unit": "matvecs/s",
+                "h2d_bytes_per_step": N * 16, "d2h_bytes_per_step": N * 16},
+        "roofline": {"bound": "hbm", "kernel": "k_near_eval<double2>", "achieved": ach64, "peak": peak,
+                     "unit": "GB/s", "frac": ach64 / peak, "traffic": None, "peak_source": peak_src,
+                     "bytes_per_launch": near_bytes(16), "launch_ms": t_near64 * 1e3},
+        "gpu_launches": KERNELS_PER_APPLY * args.steps,
+        "clocks": clocks,
+        "mixed": {"value": world * args.steps / (ms32 * 1e-3), "unit": "matvecs/s", "dtype": "f32",
+                  "ms_per_step": ms32 / args.steps,
+                  "roofline": {"kernel": "k_near_eval<float2>", "achieved": ach32, "peak": peak,
+                               "frac": ach32 / peak, "launch_ms": t_near32 * 1e3}},
+        "stages_ms": {"fp64": dict(zip(stage_names, [float(x) / max(c64, 1) for x in st64])),
+                      "mixed": dict(zip(stage_names, [float(x) / max(c32, 1) for x in st32]))},
+        "apply_hbm_frac_fp64": (apply_bytes64 / (ms64 / args.steps * 1e-3) / 1e9) / peak,
+        "time_to_tol": solve,
+    }
+    if cpu is not None:
+        line["cpu_baseline"] = cpu
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    plan.close()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

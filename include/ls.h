@@ -1,0 +1,210 @@
+/*
+ * ls.h -- C ABI of the GB300 Lippmann-Schwinger Nystrom library (2-D).
+ *
+ * The library applies and solves the discretised Lippmann-Schwinger operator
+ *
+ *     (A u)(x) = u(x) + kappa^2 int G_kappa(x, y) m(y) u(y) dy,   m = 1 - n^2,
+ *     G_kappa(x, y) = (i/4) H_0^(1)(kappa |x - y|)                  (2-D)
+ *
+ * (arXiv:1509.05063, Eq. Lippmann and Eq. G, Section 1) on a Nystrom grid made
+ * of one periodic boundary chart ("collar") and one Cartesian interior patch
+ * blended by a partition of unity (Section 2), with the localised singular
+ * quadratures of Section 3.1 and the equivalent-source / lattice-FFT
+ * acceleration of Section 3.2.  All compute runs in hand-written CUDA kernels
+ * for sm_103a; plan construction runs on the host (C++) and on the device.
+ *
+ * Conventions
+ *  - Complex vectors are interleaved (re, im): complex128 (double2) for
+ *    LS_FP64 entry points, complex64 (float2) where a call says so.
+ *  - Node order is the plan's order (nodes grouped by accelerator cell); see
+ *    ls_plan_nodes for coordinates and canonical ids.  Several right-hand
+ *    sides are stored one after another (column-major over RHS): rhs r of a
+ *    vector occupies elements [r N, (r+1) N).
+ *  - The caller owns every buffer it passes; the plan owns the device memory it
+ *    allocates (weights, matrices, spectra, work space) until ls_plan_destroy.
+ *  - Calls never exit or abort.  Every entry point returns an ls_status; the
+ *    message of the last failure of a plan is available from ls_last_error.
+ *  - Device entry points are asynchronous with respect to the host unless
+ *    stated; they run on the given CUDA stream (cudaStream_t passed as void*,
+ *    NULL = legacy default stream).  A plan is not re-entrant: calls on one
+ *    plan must not overlap (they share the plan's work space).
+ */
+#ifndef LS_GB300_H
+#define LS_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  LS_OK = 0,
+  LS_ERR_INVALID = 1,      /* bad argument or unsupported geometry/options     */
+  LS_ERR_NOMEM = 2,        /* host or device allocation failed                 */
+  LS_ERR_CUDA = 3,         /* a CUDA call or kernel launch failed              */
+  LS_ERR_NOCONV = 4,       /* GMRES / refinement did not reach the tolerance   */
+  LS_ERR_TIMEOUT = 5,      /* a bounded device wait gave up                    */
+  LS_ERR_UNSUPPORTED = 6   /* feature not built (e.g. dim = 3)                 */
+} ls_status;
+
+typedef enum { LS_FP64 = 0, LS_MIXED = 1 } ls_precision;
+
+typedef enum { LS_DISC = 0, LS_KITE = 1 } ls_shape;
+
+typedef struct ls_plan_s* ls_plan;
+
+/* Scatterer and Nystrom grid (Section 2).  The boundary curve is
+ *   disc : gamma(s) = (cx, cy) + a (cos s, sin s),              params = {a, cx, cy}
+ *   kite : gamma(s) = (cx, cy) + c (cos s + 0.65 cos 2s - 0.65, 1.5 sin s), params = {c, cx, cy}
+ * The collar chart is X(a, b) = gamma(2 pi a / n1) - (b / (n2 - 1)) collar_w nu(s),
+ * 0 <= a < n1 (periodic), 0 <= b <= n2 - 1, nu the outward normal; the interior
+ * chart is the Cartesian grid (cart_x0 + i h, cart_y0 + j h), 0 <= i < cart_nx,
+ * 0 <= j < cart_ny, of which the points with omega_I > 0 are nodes.  The
+ * partition of unity is omega_B = S((t - tau0) / (tau1 - tau0)) with S the
+ * C-infinity step 1 -> 0 and t = b / (n2 - 1) (the collar coordinate of a point),
+ * omega_I = 1 - omega_B. */
+typedef struct {
+  int dim;               /* must be 2                                           */
+  int shape;             /* ls_shape                                            */
+  double params[8];      /* shape parameters, see above                         */
+  double collar_w;       /* collar width along the inward normal                */
+  int n1, n2;            /* collar grid: tangential (periodic) x transverse      */
+  double tau0, tau1;     /* partition-of-unity transition, 0 < tau0 < tau1 < 1   */
+  double h;              /* Cartesian spacing                                   */
+  double cart_x0, cart_y0;
+  int cart_nx, cart_ny;
+} ls_geometry;
+
+/* Quadrature (Section 3.1) and accelerator (Section 3.2) parameters.  Radii
+ * are in grid-index units.  The accelerator uses L x L cells of side H whose
+ * lower-left corner is (box_x0, box_y0), N_eq lattice intervals per cell side,
+ * a Fourier-Bessel local expansion of order n_fb and n_coll collocation points
+ * (0 = 16 (N_eq + 1)).  eta must vanish outside the 3 x 3 cell block of every
+ * target (checked; LS_ERR_INVALID otherwise). */
+typedef struct {
+  int Q;                 /* Newton-Cotes points across the collar (2..5)        */
+  int p;                 /* Lagrange interpolation degree                       */
+  double R_a, R_b;       /* collar cut-off semi-axes (along / across)           */
+  double R_cart;         /* Cartesian cut-off radius                            */
+  int M;                 /* varrho(tau) = R_a tau^(M+1)                         */
+  int N_tau;             /* trapezoid points of the tau rule                    */
+  int q_polar;           /* polar rule radial map rho = s^q                     */
+  int n_rho, n_theta;    /* polar rule points                                   */
+  double chi_s0;         /* cut-off plateau: chi = 1 on [0, chi_s0]             */
+  double box_x0, box_y0, H;
+  int L, N_eq, n_fb, n_coll;
+  double rcond;          /* SVD truncation of the FP64 fits (0 = 1e-13)          */
+  double rcond_mixed;    /* SVD truncation of the complex64 fits (0 = 1e-7)     */
+  int n_threads;         /* host threads for plan construction (0 = all)        */
+} ls_options;
+
+/* n^2 at n points xy[2 i], xy[2 i + 1] -> n2[i]; called on the host during
+ * ls_plan_create only.  Returns 0 on success. */
+typedef int (*ls_n2_fn)(int64_t n, const double* xy, double* n2, void* ctx);
+
+typedef struct {
+  int64_t N;             /* Nystrom nodes                                       */
+  int64_t n_collar, n_cart;
+  int64_t nnz_near;      /* stored near-field weights                           */
+  int L, N_eq, n_es, n_loc, n_fb, fft_M;
+  int n_cells_occupied;
+  double plan_seconds;   /* host wall time of ls_plan_create                    */
+  int64_t device_bytes;  /* device memory held by the plan                      */
+} ls_plan_info_t;
+
+typedef struct {
+  int iterations;        /* total GMRES iterations (inner ones for LS_MIXED)     */
+  int refinements;       /* outer FP64 refinement steps (LS_MIXED)               */
+  double residual;       /* final ||b - A x|| / ||b|| (FP64 operator), max over RHS */
+  double seconds;        /* wall time of the call                               */
+} ls_solve_info;
+
+/* Build a plan: nodes, weights, near-field matrix (singular and regular
+ * adjacent quadrature), equivalent-source projections, local expansions and
+ * the kernel spectra; uploads them to the current CUDA device.  Host-blocking.
+ * Section 2 (charts, POU, nodes), Section 3.1 (singular rules), Section 3.2
+ * (acceleration).  Errors: LS_ERR_INVALID (bad geometry/options, eta support
+ * outside the 3 x 3 block, nodes outside the box), LS_ERR_NOMEM, LS_ERR_CUDA.
+ * On failure *out is NULL; the message is in ls_last_error(NULL). */
+ls_status ls_plan_create(const ls_geometry* geom, ls_n2_fn n2, void* ctx, double kappa,
+                         const ls_options* opt, ls_plan* out);
+
+ls_status ls_plan_info(ls_plan plan, ls_plan_info_t* info);
+
+/* Node coordinates (host array of 2 N doubles, x then y per node) and the
+ * canonical id of every node (host array of N int64, may be NULL): collar node
+ * (i, j) -> i n2 + j; Cartesian nodes follow in increasing (ix cart_ny + iy)
+ * order of the kept grid points. */
+ls_status ls_plan_nodes(ls_plan plan, double* xy_host, int64_t* canon_host);
+
+/* Au = A u for nrhs right-hand sides (Eq. Lippmann; Eq. VolInt-Adj-NonAdj).
+ * LS_FP64: u, Au complex128; LS_MIXED: u, Au complex64 (the accelerated apply
+ * in complex FP32 with FP32 near-field weights).  u and Au must not overlap.
+ * Device pointers, async on stream. */
+ls_status ls_apply(ls_plan plan, const void* u_dev, void* Au_dev, int nrhs,
+                   ls_precision prec, void* stream);
+
+/* Solve A u = uinc by GMRES (Section 2, matrix-free, complex arithmetic).
+ * uinc, u: complex128 device arrays (u: initial guess in, solution out).
+ * LS_FP64: restarted GMRES with the FP64 apply.  LS_MIXED: FP64 iterative
+ * refinement r = uinc - A_64 u whose correction equations are solved by GMRES
+ * with the complex64 apply (Arnoldi vectors in FP64).  Stops when
+ * ||uinc - A u|| / ||uinc|| <= tol for every RHS.  Synchronises the stream.
+ * Errors: LS_ERR_NOCONV if max_iter is reached (u holds the last iterate). */
+ls_status ls_solve(ls_plan plan, const void* uinc_dev, void* u_dev, int nrhs, double tol,
+                   int max_iter, int restart, ls_precision prec, ls_solve_info* info,
+                   void* stream);
+
+/* Far-field pattern A(x_hat_j) = e^{i pi/4} / sqrt(8 pi kappa) kappa^2
+ *   sum_l w_l omega_l (n^2_l - 1) u_l exp(-i kappa x_hat_j . y_l)
+ * for ndir unit directions (dirs_host: 2 ndir doubles) and nrhs complex128
+ * fields u_dev; A_dev receives ndir x nrhs complex128 (direction fastest).
+ * Not in the paper (it reports near fields); standard asymptotics of Eq. G. */
+ls_status ls_farfield(ls_plan plan, const void* u_dev, int nrhs, const double* dirs_host,
+                      int ndir, void* A_dev, void* stream);
+
+ls_status ls_plan_destroy(ls_plan plan);
+
+/* Per-stage device timing of ls_apply with CUDA events recorded on the call's
+ * stream (measurement aid; enabling it makes ls_apply wait for each apply).
+ * Stages: 0 equivalent-source projection, 1 lattice fill, 2 lattice FFT
+ * convolution (two forward transforms, spectral product, inverse), 3 local
+ * expansion coefficients, 4 near-field correction + evaluation + assembly.
+ * ls_set_stage_timing(enable) also resets the accumulators; ls_get_stage_times
+ * returns the summed milliseconds per stage (5 doubles) and the number of
+ * timed applies for the given precision. */
+ls_status ls_set_stage_timing(ls_plan plan, int enable);
+ls_status ls_get_stage_times(ls_plan plan, ls_precision prec, double* ms /* 5 */, int64_t* calls);
+
+/* ---- host-only inspection of plan construction (no device work) ----------
+ * Builds nodes, near-field matrix and accelerator matrices on the host exactly
+ * as ls_plan_create does, for validation and for callers that want the
+ * discretisation without a GPU.  Arrays are copied out into caller buffers
+ * sized from ls_host_plan_sizes: sizes[0] N, [1] nnz of the near field,
+ * [2] occupied cells, [3] n_es, [4] 2 n_fb + 1, [5] (N_eq + 1)^2, [6] FFT size M,
+ * [7] total length of the projections P.  Complex arrays are interleaved
+ * doubles.  Layouts: near field CSR (rowptr N + 1, col nnz, val nnz); P_c is
+ * n_es x n_c row-major at P_off[k] for occupied cell k (w m omega folded in);
+ * Bpinv (2 n_fb + 1) x n_loc; BT 9 x (2 n_fb + 1) x n_es with offset index
+ * (oi + 1) 3 + (oj + 1); Phi N x (2 n_fb + 1); Gtab, Dtab M x M kernel tables. */
+typedef struct ls_host_plan_s* ls_host_plan;
+ls_status ls_host_plan_create(const ls_geometry* geom, ls_n2_fn n2, void* ctx, double kappa,
+                              const ls_options* opt, ls_host_plan* out);
+ls_status ls_host_plan_sizes(ls_host_plan h, int64_t* sizes /* 8 */);
+ls_status ls_host_plan_nodes(ls_host_plan h, double* xy, int64_t* canon, double* wfac);
+ls_status ls_host_plan_near(ls_host_plan h, int64_t* rowptr, int32_t* col, double* val);
+ls_status ls_host_plan_accel(ls_host_plan h, int32_t* occ_cells, int64_t* P_off, double* P,
+                             double* Bpinv, double* BT, double* Phi, double* Gtab, double* Dtab);
+ls_status ls_host_plan_destroy(ls_host_plan h);
+
+const char* ls_status_string(ls_status s);
+
+/* Message of the last failure of this plan (or of the last failed
+ * ls_plan_create when plan is NULL).  Valid until the next call on the plan. */
+const char* ls_last_error(ls_plan plan);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LS_GB300_H */

@@ -1,0 +1,640 @@
+// C ABI of the library (include/ls.h): plan creation and upload, apply,
+// GMRES solve (FP64 and mixed complex64 + FP64 refinement) and far field.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <complex>
+#include <cstring>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "device/kernels.cuh"
+#include "host/host_plan.hpp"
+#include "ls.h"
+
+namespace {
+
+thread_local std::string g_create_error;
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+}  // namespace
+
+struct ls_plan_s {
+  lsh::Plan2D host;                 // kept for node queries (large arrays are released)
+  std::vector<DevBuf> bufs;
+  int64_t device_bytes = 0;
+  lsd::ApplyData<double2> d64;
+  lsd::ApplyData<float2> d32;
+  // plan-wide device arrays
+  double *x = nullptr, *y = nullptr, *ffw = nullptr;
+  // solve work space (lazily sized)
+  int ws_restart = -1;
+  double2 *V = nullptr, *w = nullptr, *r = nullptr, *e = nullptr, *cor = nullptr, *h = nullptr, *partial = nullptr;
+  double* dnorm = nullptr;
+  double* dpartial = nullptr;
+  float2 *c64a = nullptr, *c64b = nullptr;
+  double* dirs = nullptr;
+  int dirs_cap = 0;
+  ls_plan_info_t info{};
+  std::string err;
+  // optional per-stage event timing of ls_apply
+  bool timing = false;
+  cudaEvent_t ev[lsd::kStages + 1] = {};
+  double stage_ms[2][lsd::kStages] = {};
+  int64_t stage_calls[2] = {0, 0};
+
+  template <typename T>
+  T* alloc(size_t n, ls_status* st) {
+    void* p = nullptr;
+    if (n == 0) n = 1;
+    if (cudaMalloc(&p, n * sizeof(T)) != cudaSuccess) {
+      cudaGetLastError();
+      *st = LS_ERR_NOMEM;
+      err = "cudaMalloc of " + std::to_string(n * sizeof(T)) + " bytes failed";
+      return nullptr;
+    }
+    bufs.push_back({p, n * sizeof(T)});
+    device_bytes += int64_t(n * sizeof(T));
+    return static_cast<T*>(p);
+  }
+  template <typename T, typename S>
+  T* upload(const std::vector<S>& v, ls_status* st) {
+    static_assert(sizeof(T) == sizeof(S), "layout");
+    T* d = alloc<T>(v.size(), st);
+    if (!d) return nullptr;
+    if (!v.empty() && cudaMemcpy(d, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice) != cudaSuccess) {
+      *st = LS_ERR_CUDA;
+      err = "cudaMemcpy upload failed";
+      return nullptr;
+    }
+    return d;
+  }
+  void free_all() {
+    for (auto& b : bufs) cudaFree(b.p);
+    bufs.clear();
+  }
+};
+
+namespace {
+
+using cd = std::complex<double>;
+
+ls_status fail(ls_plan p, ls_status s, const std::string& m) {
+  if (p) p->err = m;
+  else g_create_error = m;
+  return s;
+}
+
+#define LS_CU(call)                                                                      \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess) return fail(plan, LS_ERR_CUDA, std::string(#call ": ") + cudaGetErrorString(e_)); \
+  } while (0)
+
+std::vector<std::complex<float>> to32(const std::vector<cd>& v) {
+  std::vector<std::complex<float>> o(v.size());
+  for (size_t i = 0; i < v.size(); ++i) o[i] = std::complex<float>(float(v[i].real()), float(v[i].imag()));
+  return o;
+}
+
+ls_status validate(const ls_geometry* g, const ls_options* o, double kappa) {
+  if (!g || !o) return LS_ERR_INVALID;
+  if (g->dim != 2) return LS_ERR_UNSUPPORTED;
+  if (g->shape != LS_DISC && g->shape != LS_KITE) return LS_ERR_INVALID;
+  if (g->n1 < 8 || g->n2 < 2 || g->collar_w <= 0 || g->h <= 0 || g->cart_nx < 1 || g->cart_ny < 1)
+    return LS_ERR_INVALID;
+  if (!(kappa > 0)) return LS_ERR_INVALID;
+  if (o->Q < 2 || o->Q > 5 || o->p < 1 || o->p > 15 || o->R_a <= 0 || o->R_b <= 0 || o->R_cart <= 0)
+    return LS_ERR_INVALID;
+  if (o->M < 0 || o->N_tau < 4 || o->q_polar < 1 || o->n_rho < 2 || o->n_theta < 4) return LS_ERR_INVALID;
+  if (o->L < 1 || o->N_eq < 2 || o->H <= 0 || o->n_fb < 0) return LS_ERR_INVALID;
+  if (!(o->chi_s0 >= 0 && o->chi_s0 < 1)) return LS_ERR_INVALID;
+  return LS_OK;
+}
+
+ls_status build_host(lsh::Plan2D& P, const ls_geometry* geom, ls_n2_fn n2, void* ctx, double kappa,
+                     const ls_options* opt, std::string* msg) {
+  P.geo.g = *geom;
+  P.opt = *opt;
+  P.kappa = kappa;
+  P.n_threads = opt->n_threads > 0 ? opt->n_threads : int(std::max(1u, std::thread::hardware_concurrency()));
+  try {
+    if (!lsh::build_nodes(P, n2, ctx) || !lsh::build_near(P) || !lsh::build_accel(P)) {
+      *msg = P.err;
+      return LS_ERR_INVALID;
+    }
+  } catch (const std::bad_alloc&) {
+    *msg = "host allocation failed during plan construction";
+    return LS_ERR_NOMEM;
+  }
+  return LS_OK;
+}
+
+}  // namespace
+
+struct ls_host_plan_s {
+  lsh::Plan2D P;
+};
+
+extern "C" {
+
+ls_status ls_host_plan_create(const ls_geometry* geom, ls_n2_fn n2, void* ctx, double kappa, const ls_options* opt,
+                              ls_host_plan* out) {
+  if (!out) return fail(nullptr, LS_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  const ls_status v = validate(geom, opt, kappa);
+  if (v != LS_OK) return fail(nullptr, v, "invalid geometry or options");
+  ls_host_plan h = new (std::nothrow) ls_host_plan_s;
+  if (!h) return fail(nullptr, LS_ERR_NOMEM, "host allocation failed");
+  std::string m;
+  const ls_status s = build_host(h->P, geom, n2, ctx, kappa, opt, &m);
+  if (s != LS_OK) {
+    delete h;
+    return fail(nullptr, s, m);
+  }
+  *out = h;
+  return LS_OK;
+}
+
+ls_status ls_host_plan_sizes(ls_host_plan h, int64_t* sizes) {
+  if (!h || !sizes) return LS_ERR_INVALID;
+  const lsh::Plan2D& P = h->P;
+  sizes[0] = P.nodes.N;
+  sizes[1] = P.rowptr.empty() ? 0 : P.rowptr.back();
+  sizes[2] = int64_t(P.occ_cells.size());
+  sizes[3] = P.n_es;
+  sizes[4] = P.nfb2;
+  sizes[5] = P.n_loc;
+  sizes[6] = P.M;
+  sizes[7] = int64_t(P.P64.size());
+  return LS_OK;
+}
+
+ls_status ls_host_plan_nodes(ls_host_plan h, double* xy, int64_t* canon, double* wfac) {
+  if (!h) return LS_ERR_INVALID;
+  const lsh::Nodes& nd = h->P.nodes;
+  for (int64_t i = 0; i < nd.N; ++i) {
+    if (xy) { xy[2 * i] = nd.x[i]; xy[2 * i + 1] = nd.y[i]; }
+    if (canon) canon[i] = nd.canon[i];
+    if (wfac) wfac[i] = nd.wfac[i];
+  }
+  return LS_OK;
+}
+
+ls_status ls_host_plan_near(ls_host_plan h, int64_t* rowptr, int32_t* col, double* val) {
+  if (!h || !rowptr || !col || !val) return LS_ERR_INVALID;
+  const lsh::Plan2D& P = h->P;
+  std::copy(P.rowptr.begin(), P.rowptr.end(), rowptr);
+  std::copy(P.col.begin(), P.col.end(), col);
+  std::memcpy(val, P.val.data(), P.val.size() * sizeof(cd));
+  return LS_OK;
+}
+
+ls_status ls_host_plan_accel(ls_host_plan h, int32_t* occ_cells, int64_t* P_off, double* Pm, double* Bpinv,
+                             double* BT, double* Phi, double* Gtab, double* Dtab) {
+  if (!h) return LS_ERR_INVALID;
+  const lsh::Plan2D& P = h->P;
+  if (occ_cells) std::copy(P.occ_cells.begin(), P.occ_cells.end(), occ_cells);
+  if (P_off) std::copy(P.P_off.begin(), P.P_off.end(), P_off);
+  if (Pm) std::memcpy(Pm, P.P64.data(), P.P64.size() * sizeof(cd));
+  if (Bpinv) std::memcpy(Bpinv, P.Bpinv.data(), P.Bpinv.size() * sizeof(cd));
+  if (BT) std::memcpy(BT, P.BT.data(), P.BT.size() * sizeof(cd));
+  if (Phi) std::memcpy(Phi, P.Phi.data(), P.Phi.size() * sizeof(cd));
+  if (Gtab) std::memcpy(Gtab, P.Gtab.data(), P.Gtab.size() * sizeof(cd));
+  if (Dtab) std::memcpy(Dtab, P.Dtab.data(), P.Dtab.size() * sizeof(cd));
+  return LS_OK;
+}
+
+ls_status ls_host_plan_destroy(ls_host_plan h) {
+  delete h;
+  return LS_OK;
+}
+
+const char* ls_status_string(ls_status s) {
+  switch (s) {
+    case LS_OK: return "ok";
+    case LS_ERR_INVALID: return "invalid argument";
+    case LS_ERR_NOMEM: return "out of memory";
+    case LS_ERR_CUDA: return "CUDA error";
+    case LS_ERR_NOCONV: return "no convergence";
+    case LS_ERR_TIMEOUT: return "device wait timed out";
+    case LS_ERR_UNSUPPORTED: return "unsupported";
+  }
+  return "unknown status";
+}
+
+const char* ls_last_error(ls_plan plan) { return plan ? plan->err.c_str() : g_create_error.c_str(); }
+
+ls_status ls_plan_create(const ls_geometry* geom, ls_n2_fn n2, void* ctx, double kappa, const ls_options* opt,
+                         ls_plan* out) {
+  if (!out) return fail(nullptr, LS_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  const ls_status v = validate(geom, opt, kappa);
+  if (v != LS_OK) return fail(nullptr, v, "invalid geometry or options");
+  const auto t0 = std::chrono::steady_clock::now();
+  ls_plan plan = new (std::nothrow) ls_plan_s;
+  if (!plan) return fail(nullptr, LS_ERR_NOMEM, "host allocation failed");
+  lsh::Plan2D& P = plan->host;
+  auto bail = [&](ls_status s, const std::string& m) {
+    g_create_error = m;
+    plan->free_all();
+    delete plan;
+    return s;
+  };
+  {
+    std::string m;
+    const ls_status hs = build_host(P, geom, n2, ctx, kappa, opt, &m);
+    if (hs != LS_OK) return bail(hs, m);
+  }
+  const lsh::Nodes& nd = P.nodes;
+  const int64_t N = nd.N;
+  const int nocc = int(P.occ_cells.size());
+  ls_status st = LS_OK;
+#define UP(T, v) plan->upload<T>(v, &st); if (st != LS_OK) return bail(st, plan->err)
+  // shared integer structure
+  std::vector<int64_t> occ_start(nocc + 1);
+  std::vector<int> occ_of_cell(size_t(P.opt.L) * P.opt.L, -1), occ_of_node(N);
+  for (int k = 0; k < nocc; ++k) {
+    occ_start[k] = nd.cell_start[P.occ_cells[k]];
+    occ_of_cell[P.occ_cells[k]] = k;
+  }
+  occ_start[nocc] = N;
+  for (int64_t q = 0; q < N; ++q) occ_of_node[q] = occ_of_cell[nd.cell[q]];
+  std::vector<int> col32(P.col.begin(), P.col.end());
+  const int64_t* d_occ_start = UP(int64_t, occ_start);
+  const int* d_occ_cells = UP(int, P.occ_cells);
+  const int* d_occ_of_cell = UP(int, occ_of_cell);
+  const int* d_occ_of_node = UP(int, occ_of_node);
+  const int64_t* d_P_off = UP(int64_t, P.P_off);
+  const int64_t* d_rowptr = UP(int64_t, P.rowptr);
+  const int* d_col = UP(int, col32);
+  plan->x = UP(double, nd.x);
+  plan->y = UP(double, nd.y);
+  plan->ffw = UP(double, P.ffw);
+  // twiddles and spectra
+  const int M = P.M;
+  int logM = 0;
+  while ((1 << logM) < M) ++logM;
+  std::vector<cd> tw(M);
+  for (int m = 0; m < M; ++m) tw[m] = std::polar(1.0, -2.0 * M_PI * double(m) / M);
+  std::vector<cd> G = P.Gtab, D = P.Dtab;
+  const double sc = 1.0 / (double(M) * double(M));
+  for (auto& z : G) z *= sc;
+  for (auto& z : D) z *= sc;
+  double2* d_tw64 = UP(double2, tw);
+  double2* d_G64 = UP(double2, G);
+  double2* d_D64 = UP(double2, D);
+  {
+    cudaError_t e = lsd::fft2d<double2>(d_G64, M, logM, d_tw64, false, 0);
+    if (e == cudaSuccess) e = lsd::fft2d<double2>(d_D64, M, logM, d_tw64, false, 0);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return bail(LS_ERR_CUDA, std::string("spectra: ") + cudaGetErrorString(e));
+  }
+  const int64_t MM = int64_t(M) * M;
+  float2* d_G32 = plan->alloc<float2>(MM, &st);
+  float2* d_D32 = plan->alloc<float2>(MM, &st);
+  if (st != LS_OK) return bail(st, plan->err);
+  if (lsd::to_c64(d_G64, d_G32, MM, 0) != cudaSuccess || lsd::to_c64(d_D64, d_D32, MM, 0) != cudaSuccess)
+    return bail(LS_ERR_CUDA, "spectra conversion failed");
+  // FP64 apply data
+  auto& a = plan->d64;
+  a.N = N; a.nocc = nocc; a.L = P.opt.L; a.Ne = P.Ne; a.n_es = P.n_es; a.n_loc = P.n_loc; a.nfb2 = P.nfb2;
+  a.M = M; a.n_lat = P.n_lat; a.logM = logM;
+  a.occ_start = d_occ_start; a.occ_cells = d_occ_cells; a.occ_of_cell = d_occ_of_cell;
+  a.occ_of_node = d_occ_of_node; a.P_off = d_P_off; a.rowptr = d_rowptr; a.col = d_col;
+  a.P = UP(double2, P.P64);
+  a.Bp = UP(double2, P.Bpinv);
+  a.BT = UP(double2, P.BT);
+  a.Phi = UP(double2, P.Phi);
+  a.val = UP(double2, P.val);
+  a.Ghat = d_G64; a.Dhat = d_D64; a.tw = d_tw64;
+  a.kappa2 = kappa * kappa;
+  a.sigma = plan->alloc<double2>(size_t(nocc) * P.n_es, &st);
+  a.Sm = plan->alloc<double2>(MM, &st);
+  a.Sd = plan->alloc<double2>(MM, &st);
+  a.gamma = plan->alloc<double2>(size_t(nocc) * P.nfb2, &st);
+  if (st != LS_OK) return bail(st, plan->err);
+  // complex64 apply data
+  auto& b = plan->d32;
+  b.N = a.N; b.nocc = a.nocc; b.L = a.L; b.Ne = a.Ne; b.n_es = a.n_es; b.n_loc = a.n_loc; b.nfb2 = a.nfb2;
+  b.M = a.M; b.n_lat = a.n_lat; b.logM = a.logM;
+  b.occ_start = a.occ_start; b.occ_cells = a.occ_cells; b.occ_of_cell = a.occ_of_cell;
+  b.occ_of_node = a.occ_of_node; b.P_off = a.P_off; b.rowptr = a.rowptr; b.col = a.col;
+  b.P = UP(float2, to32(P.P32));
+  b.Bp = UP(float2, to32(P.Bpinv));
+  b.BT = UP(float2, to32(P.BT));
+  b.Phi = UP(float2, to32(P.Phi));
+  b.val = UP(float2, to32(P.val));
+  b.Ghat = d_G32; b.Dhat = d_D32;
+  b.tw = UP(float2, to32(tw));
+  b.kappa2 = a.kappa2;
+  b.sigma = plan->alloc<float2>(size_t(nocc) * P.n_es, &st);
+  b.Sm = plan->alloc<float2>(MM, &st);
+  b.Sd = plan->alloc<float2>(MM, &st);
+  b.gamma = plan->alloc<float2>(size_t(nocc) * P.nfb2, &st);
+  if (st != LS_OK) return bail(st, plan->err);
+#undef UP
+  if (cudaDeviceSynchronize() != cudaSuccess) return bail(LS_ERR_CUDA, "upload failed");
+  // info, then release the large host arrays
+  ls_plan_info_t& inf = plan->info;
+  inf.N = N; inf.n_collar = nd.n_collar; inf.n_cart = nd.n_cart; inf.nnz_near = P.rowptr[N];
+  inf.L = P.opt.L; inf.N_eq = P.Ne; inf.n_es = P.n_es; inf.n_loc = P.n_loc; inf.n_fb = P.opt.n_fb;
+  inf.fft_M = M; inf.n_cells_occupied = nocc;
+  inf.plan_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  inf.device_bytes = plan->device_bytes;
+  std::vector<int32_t>().swap(P.col);
+  std::vector<cd>().swap(P.val);
+  std::vector<cd>().swap(P.P64);
+  std::vector<cd>().swap(P.P32);
+  std::vector<cd>().swap(P.Phi);
+  std::vector<cd>().swap(P.Gtab);
+  std::vector<cd>().swap(P.Dtab);
+  *out = plan;
+  return LS_OK;
+}
+
+ls_status ls_plan_info(ls_plan plan, ls_plan_info_t* info) {
+  if (!plan || !info) return LS_ERR_INVALID;
+  *info = plan->info;
+  return LS_OK;
+}
+
+ls_status ls_plan_nodes(ls_plan plan, double* xy, int64_t* canon) {
+  if (!plan) return LS_ERR_INVALID;
+  const lsh::Nodes& nd = plan->host.nodes;
+  if (xy)
+    for (int64_t i = 0; i < nd.N; ++i) { xy[2 * i] = nd.x[i]; xy[2 * i + 1] = nd.y[i]; }
+  if (canon) std::copy(nd.canon.begin(), nd.canon.end(), canon);
+  return LS_OK;
+}
+
+ls_status ls_apply(ls_plan plan, const void* u, void* Au, int nrhs, ls_precision prec, void* stream) {
+  if (!plan) return LS_ERR_INVALID;
+  if (!u || !Au || nrhs < 0) return fail(plan, LS_ERR_INVALID, "ls_apply: bad arguments");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int64_t N = plan->d64.N;
+  if (prec != LS_FP64 && prec != LS_MIXED) return fail(plan, LS_ERR_INVALID, "ls_apply: bad precision");
+  cudaEvent_t* ev = plan->timing ? plan->ev : nullptr;
+  for (int r = 0; r < nrhs; ++r) {
+    cudaError_t e;
+    if (prec == LS_FP64)
+      e = lsd::apply_one(plan->d64, static_cast<const double2*>(u) + r * N, static_cast<double2*>(Au) + r * N, st, ev);
+    else
+      e = lsd::apply_one(plan->d32, static_cast<const float2*>(u) + r * N, static_cast<float2*>(Au) + r * N, st, ev);
+    if (e != cudaSuccess) return fail(plan, LS_ERR_CUDA, std::string("ls_apply: ") + cudaGetErrorString(e));
+    if (ev) {
+      LS_CU(cudaEventSynchronize(ev[lsd::kStages]));
+      for (int k = 0; k < lsd::kStages; ++k) {
+        float ms = 0;
+        LS_CU(cudaEventElapsedTime(&ms, ev[k], ev[k + 1]));
+        plan->stage_ms[prec][k] += ms;
+      }
+      plan->stage_calls[prec]++;
+    }
+  }
+  return LS_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// One GMRES(m) solve of A x = b (FP64 Arnoldi).  op(v, Av) applies the
+// operator.  Stops when the true residual ||b - A x|| / ||b|| <= tol (checked
+// at restarts; inside a cycle the Givens estimate is used).
+template <typename Op>
+ls_status gmres_fp64(ls_plan plan, Op op, const double2* b, double2* x, double tol, int max_iter, int restart,
+                     cudaStream_t st, int* iters, double* relres) {
+  const int64_t N = plan->d64.N;
+  double2* V = plan->V;
+  double2* w = plan->w;
+  double2* r = plan->r;
+  auto dnorm = [&](const double2* v, double* out) -> cudaError_t {
+    cudaError_t e = lsd::norm2(v, N, plan->dpartial, plan->dnorm, st);
+    if (e != cudaSuccess) return e;
+    e = cudaMemcpyAsync(out, plan->dnorm, sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return e;
+    return cudaStreamSynchronize(st);
+  };
+  double bnorm = 0;
+  LS_CU(dnorm(b, &bnorm));
+  *iters = 0;
+  if (bnorm == 0.0) {
+    LS_CU(cudaMemsetAsync(x, 0, N * sizeof(double2), st));
+    *relres = 0;
+    return LS_OK;
+  }
+  const int m = restart;
+  std::vector<cd> H(size_t(m + 1) * m), cs(m), sn(m), g(m + 1), hcol(m + 2);
+  for (;;) {
+    LS_CU(op(x, w));
+    LS_CU(lsd::sub(b, w, r, N, st));
+    double beta = 0;
+    LS_CU(dnorm(r, &beta));
+    *relres = beta / bnorm;
+    if (*relres <= tol) return LS_OK;
+    if (*iters >= max_iter) return fail(plan, LS_ERR_NOCONV, "GMRES reached max_iter");
+    LS_CU(lsd::scale_into(r, plan->dnorm, V, N, st));
+    std::fill(H.begin(), H.end(), cd(0));
+    std::fill(g.begin(), g.end(), cd(0));
+    g[0] = beta;
+    int k_used = 0;
+    for (int k = 0; k < m; ++k) {
+      LS_CU(op(V + int64_t(k) * N, w));
+      // classical Gram-Schmidt, two passes
+      for (int pass = 0; pass < 2; ++pass) {
+        LS_CU(lsd::gram(V, k + 1, w, N, plan->partial, plan->h, st));
+        LS_CU(lsd::axpy_multi(V, k + 1, plan->h, w, N, st));
+        LS_CU(cudaMemcpyAsync(hcol.data(), plan->h, (k + 1) * sizeof(double2), cudaMemcpyDeviceToHost, st));
+        LS_CU(cudaStreamSynchronize(st));
+        for (int j = 0; j <= k; ++j) H[size_t(j) * m + k] += hcol[j];
+      }
+      double hk1 = 0;
+      LS_CU(dnorm(w, &hk1));
+      H[size_t(k + 1) * m + k] = hk1;
+      LS_CU(lsd::scale_into(w, plan->dnorm, V + int64_t(k + 1) * N, N, st));
+      for (int j = 0; j < k; ++j) {
+        const cd t = std::conj(cs[j]) * H[size_t(j) * m + k] + std::conj(sn[j]) * H[size_t(j + 1) * m + k];
+        H[size_t(j + 1) * m + k] = -sn[j] * H[size_t(j) * m + k] + cs[j] * H[size_t(j + 1) * m + k];
+        H[size_t(j) * m + k] = t;
+      }
+      const cd a = H[size_t(k) * m + k], bb = H[size_t(k + 1) * m + k];
+      const double den = std::sqrt(std::norm(a) + std::norm(bb));
+      cs[k] = den > 0 ? a / den : cd(1);
+      sn[k] = den > 0 ? bb / den : cd(0);
+      H[size_t(k) * m + k] = den;
+      H[size_t(k + 1) * m + k] = 0;
+      g[k + 1] = -sn[k] * g[k];
+      g[k] = std::conj(cs[k]) * g[k];
+      ++*iters;
+      k_used = k + 1;
+      if (std::abs(g[k + 1]) / bnorm <= tol || *iters >= max_iter || hk1 == 0.0) break;
+    }
+    // back substitution, x += V y
+    std::vector<cd> y(k_used);
+    for (int i = k_used - 1; i >= 0; --i) {
+      cd s = g[i];
+      for (int j = i + 1; j < k_used; ++j) s -= H[size_t(i) * m + j] * y[j];
+      y[i] = s / H[size_t(i) * m + i];
+    }
+    LS_CU(cudaMemcpyAsync(plan->h, y.data(), k_used * sizeof(double2), cudaMemcpyHostToDevice, st));
+    LS_CU(lsd::combine(V, k_used, plan->h, x, N, st));
+  }
+}
+
+ls_status ensure_workspace(ls_plan plan, int restart) {
+  if (plan->ws_restart >= restart) return LS_OK;
+  if (plan->ws_restart >= 0) return fail(plan, LS_ERR_INVALID, "restart larger than the first solve's is not supported");
+  const int64_t N = plan->d64.N;
+  ls_status st = LS_OK;
+  plan->V = plan->alloc<double2>(size_t(restart + 1) * N, &st);
+  plan->w = plan->alloc<double2>(N, &st);
+  plan->r = plan->alloc<double2>(N, &st);
+  plan->e = plan->alloc<double2>(N, &st);
+  plan->cor = plan->alloc<double2>(N, &st);
+  plan->h = plan->alloc<double2>(restart + 2, &st);
+  plan->partial = plan->alloc<double2>(size_t(lsd::gram_blocks(N)) * (restart + 2), &st);
+  plan->dnorm = plan->alloc<double>(1, &st);
+  plan->dpartial = plan->alloc<double>(lsd::gram_blocks(N), &st);
+  plan->c64a = plan->alloc<float2>(N, &st);
+  plan->c64b = plan->alloc<float2>(N, &st);
+  if (st != LS_OK) return st;
+  plan->ws_restart = restart;
+  return LS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+ls_status ls_solve(ls_plan plan, const void* uinc, void* u, int nrhs, double tol, int max_iter, int restart,
+                   ls_precision prec, ls_solve_info* info, void* stream) {
+  if (!plan) return LS_ERR_INVALID;
+  if (!uinc || !u || nrhs < 0 || !(tol > 0) || max_iter < 1 || restart < 1)
+    return fail(plan, LS_ERR_INVALID, "ls_solve: bad arguments");
+  if (prec != LS_FP64 && prec != LS_MIXED) return fail(plan, LS_ERR_INVALID, "ls_solve: bad precision");
+  const auto t0 = std::chrono::steady_clock::now();
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  ls_status s = ensure_workspace(plan, restart);
+  if (s != LS_OK) return s;
+  const int64_t N = plan->d64.N;
+  int total_it = 0, total_ref = 0;
+  double worst = 0;
+  auto op64 = [&](const double2* v, double2* Av) { return lsd::apply_one(plan->d64, v, Av, st); };
+  auto op32 = [&](const double2* v, double2* Av) {
+    cudaError_t e = lsd::to_c64(v, plan->c64a, N, st);
+    if (e == cudaSuccess) e = lsd::apply_one(plan->d32, plan->c64a, plan->c64b, st);
+    if (e == cudaSuccess) e = lsd::to_c128(plan->c64b, Av, N, st);
+    return e;
+  };
+  ls_status result = LS_OK;
+  for (int rh = 0; rh < nrhs; ++rh) {
+    const double2* b = static_cast<const double2*>(uinc) + int64_t(rh) * N;
+    double2* x = static_cast<double2*>(u) + int64_t(rh) * N;
+    if (prec == LS_FP64) {
+      int it = 0;
+      double rr = 0;
+      s = gmres_fp64(plan, op64, b, x, tol, max_iter, restart, st, &it, &rr);
+      total_it += it;
+      worst = std::max(worst, rr);
+      if (s != LS_OK) { result = s; if (s != LS_ERR_NOCONV) break; }
+    } else {
+      // FP64 iterative refinement around complex64 GMRES corrections:
+      // r = b - A_64 x (FP64), solve A_32 c = r to a loose tolerance, x += c.
+      double bnorm = 0, rnorm = 0;
+      double2* rres = plan->e;
+      double2* cor = plan->cor;
+      LS_CU(lsd::norm2(b, N, plan->dpartial, plan->dnorm, st));
+      LS_CU(cudaMemcpyAsync(&bnorm, plan->dnorm, sizeof(double), cudaMemcpyDeviceToHost, st));
+      LS_CU(cudaStreamSynchronize(st));
+      int inner_total = 0;
+      for (int ref = 0;; ++ref) {
+        LS_CU(lsd::apply_one(plan->d64, x, plan->w, st));
+        LS_CU(lsd::sub(b, plan->w, rres, N, st));
+        LS_CU(lsd::norm2(rres, N, plan->dpartial, plan->dnorm, st));
+        LS_CU(cudaMemcpyAsync(&rnorm, plan->dnorm, sizeof(double), cudaMemcpyDeviceToHost, st));
+        LS_CU(cudaStreamSynchronize(st));
+        const double rel = bnorm > 0 ? rnorm / bnorm : 0.0;
+        if (rel <= tol) { worst = std::max(worst, rel); break; }
+        if (inner_total >= max_iter || ref >= 50) {
+          worst = std::max(worst, rel);
+          result = fail(plan, LS_ERR_NOCONV, "refinement reached max_iter");
+          break;
+        }
+        total_ref++;
+        const double inner_tol = std::max(1e-5, 0.3 * tol / rel);
+        int it = 0;
+        double rr = 0;
+        LS_CU(cudaMemsetAsync(cor, 0, N * sizeof(double2), st));
+        s = gmres_fp64(plan, op32, rres, cor, inner_tol, std::max(1, max_iter - inner_total), restart, st, &it, &rr);
+        inner_total += it;
+        if (s != LS_OK && s != LS_ERR_NOCONV) return s;
+        LS_CU(lsd::add_inplace(x, cor, N, st));
+      }
+      total_it += inner_total;
+    }
+  }
+  if (info) {
+    info->iterations = total_it;
+    info->refinements = total_ref;
+    info->residual = worst;
+    info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  }
+  return result;
+}
+
+ls_status ls_farfield(ls_plan plan, const void* u, int nrhs, const double* dirs_host, int ndir, void* A,
+                      void* stream) {
+  if (!plan) return LS_ERR_INVALID;
+  if (!u || !dirs_host || !A || nrhs < 0 || ndir < 0) return fail(plan, LS_ERR_INVALID, "ls_farfield: bad arguments");
+  if (nrhs == 0 || ndir == 0) return LS_OK;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (ndir > plan->dirs_cap) {
+    ls_status s = LS_OK;
+    plan->dirs = plan->alloc<double>(size_t(2) * ndir, &s);
+    if (s != LS_OK) return s;
+    plan->dirs_cap = ndir;
+  }
+  LS_CU(cudaMemcpyAsync(plan->dirs, dirs_host, sizeof(double) * 2 * ndir, cudaMemcpyHostToDevice, st));
+  const double k = plan->host.kappa;
+  const std::complex<double> c = std::polar(1.0, M_PI / 4) / std::sqrt(8 * M_PI * k) * (k * k);
+  LS_CU(lsd::farfield(plan->d64.N, plan->x, plan->y, plan->ffw, static_cast<const double2*>(u), nrhs, plan->dirs,
+                      ndir, k, make_double2(c.real(), c.imag()), static_cast<double2*>(A), st));
+  LS_CU(cudaStreamSynchronize(st));
+  return LS_OK;
+}
+
+ls_status ls_set_stage_timing(ls_plan plan, int enable) {
+  if (!plan) return LS_ERR_INVALID;
+  if (enable && !plan->ev[0])
+    for (auto& e : plan->ev) LS_CU(cudaEventCreate(&e));
+  plan->timing = enable != 0;
+  for (auto& row : plan->stage_ms)
+    for (double& v : row) v = 0;
+  plan->stage_calls[0] = plan->stage_calls[1] = 0;
+  return LS_OK;
+}
+
+ls_status ls_get_stage_times(ls_plan plan, ls_precision prec, double* ms, int64_t* calls) {
+  if (!plan || !ms || (prec != LS_FP64 && prec != LS_MIXED)) return LS_ERR_INVALID;
+  for (int k = 0; k < lsd::kStages; ++k) ms[k] = plan->stage_ms[prec][k];
+  if (calls) *calls = plan->stage_calls[prec];
+  return LS_OK;
+}
+
+ls_status ls_plan_destroy(ls_plan plan) {
+  if (!plan) return LS_OK;
+  cudaDeviceSynchronize();
+  for (auto& e : plan->ev)
+    if (e) cudaEventDestroy(e);
+  plan->free_all();
+  delete plan;
+  return LS_OK;
+}
+
+}  // extern "C"

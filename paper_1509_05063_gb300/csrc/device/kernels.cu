@@ -1,0 +1,497 @@
+// sm_103a kernels of the LS apply (Section 3.2 accelerator + near field) and
+// of the GMRES solve.  One template per arithmetic precision: T = double2
+// (complex128 path) or float2 (complex64 inner path of mixed precision).
+//
+// Apply pipeline for one right-hand side (Eq. VolInt-Adj-NonAdj):
+//   k_es_project      sigma_c = P_c u_c            (equivalent-source fit)
+//   k_lattice_fill    sigma -> monopole / dipole lattice arrays (face points)
+//   fft2d x2, k_spectral, fft2d^-1   lattice convolution with G and dG/dz_1
+//   k_local_coeffs    gamma_c = B^+ V_c - sum_o (B^+ T_o) sigma_{c+o}
+//   k_near_eval       out_q = u_q + kappa^2 (sum_l W_ql u_l + Phi_q . gamma_c)
+#include <cstdio>
+
+#include "cplx.cuh"
+#include "kernels.cuh"
+
+namespace lsd {
+
+template <typename T> struct RealOf;
+template <> struct RealOf<double2> { using R = double; };
+template <> struct RealOf<float2> { using R = float; };
+
+// ------------------------------------------------------------ ES projection
+template <typename T>
+__global__ void __launch_bounds__(256) k_es_project(int nocc, const int64_t* __restrict__ occ_start,
+                                                    const int64_t* __restrict__ P_off,
+                                                    const T* __restrict__ P, const T* __restrict__ u,
+                                                    T* __restrict__ sigma, int n_es) {
+  const int k = blockIdx.x;
+  if (k >= nocc) return;
+  const int64_t s0 = occ_start[k];
+  const int nc = int(occ_start[k + 1] - s0);
+  const T* Pc = P + P_off[k];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int i = warp; i < n_es; i += nw) {
+    T acc = czero(T{});
+    for (int j = lane; j < nc; j += 32) acc = cfma(Pc[int64_t(i) * nc + j], u[s0 + j], acc);
+    acc = warp_sum(acc);
+    if (lane == 0) sigma[int64_t(k) * n_es + i] = acc;
+  }
+}
+
+// ------------------------------------------------------------ lattice sources
+// Face lattice point (a, b) with a = f Ne gathers the strengths of every cell
+// whose x-face passes through it (left face of cell f, right face of cell f-1;
+// the top point of a face is shared with the cell above).
+template <typename T>
+__global__ void __launch_bounds__(256) k_lattice_fill(int M, int n_lat, int Ne, int L,
+                                                      const int* __restrict__ occ_of_cell,
+                                                      const T* __restrict__ sigma, int n_es,
+                                                      T* __restrict__ Sm, T* __restrict__ Sd) {
+  const int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (idx >= int64_t(M) * M) return;
+  const int a = int(idx / M), b = int(idx % M);
+  T sm = czero(T{}), sd = czero(T{});
+  if (a < n_lat && b < n_lat && a % Ne == 0) {
+    const int fa = a / Ne;
+    for (int side = 0; side < 2; ++side) {
+      const int ci = fa - side;
+      if (ci < 0 || ci >= L) continue;
+      const int cjb = b / Ne, kb = b % Ne;
+      for (int t = 0; t < 2; ++t) {
+        if (t == 1 && kb != 0) break;
+        const int cj = cjb - t, k = kb + t * Ne;
+        if (cj < 0 || cj >= L) continue;
+        const int occ = occ_of_cell[cj * L + ci];
+        if (occ < 0) continue;
+        const T* s = sigma + int64_t(occ) * n_es;
+        sm = cadd(sm, s[side * (Ne + 1) + k]);
+        sd = cadd(sd, s[(2 + side) * (Ne + 1) + k]);
+      }
+    }
+  }
+  Sm[idx] = sm;
+  Sd[idx] = sd;
+}
+
+// ------------------------------------------------------------ Stockham FFT
+// In-place radix-4 (plus one radix-2 stage when log2 N is odd) Stockham
+// autosort transform of one length-N sequence held in shared memory, run by
+// G = N / 8 threads of the block (thread t): 2 radix-4 butterflies or 4
+// radix-2 butterflies per thread and stage.  Every stage reads all inputs to
+// registers, synchronises the block, then writes, so one buffer suffices.
+// tw[m] = exp(-2 pi i m / N); the inverse uses conjugate twiddles (no scaling).
+template <typename T>
+__device__ void fft_smem(T* x, int N, int logN, bool inv, const T* __restrict__ tw, int t) {
+  const int G = N / 8;
+  int Ns = 1;
+  if (logN & 1) {
+    T a[8];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int j = t + c * G;
+      a[2 * c] = x[j];
+      a[2 * c + 1] = x[j + N / 2];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int j = t + c * G;
+      x[2 * j] = cadd(a[2 * c], a[2 * c + 1]);
+      x[2 * j + 1] = csub(a[2 * c], a[2 * c + 1]);
+    }
+    __syncthreads();
+    Ns = 2;
+  }
+  for (; Ns < N; Ns *= 4) {
+    T v[2][4];
+    const int tstep = N / (4 * Ns);
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      const int j = t + c * G;
+      const int k = j & (Ns - 1);
+#pragma unroll
+      for (int r = 0; r < 4; ++r) v[c][r] = x[j + r * (N / 4)];
+      if (Ns > 1) {
+#pragma unroll
+        for (int r = 1; r < 4; ++r) {
+          T w = tw[r * k * tstep];
+          if (inv) w = cconj(w);
+          v[c][r] = cmul(v[c][r], w);
+        }
+      }
+      const T s02 = cadd(v[c][0], v[c][2]), d02 = csub(v[c][0], v[c][2]);
+      const T s13 = cadd(v[c][1], v[c][3]), d13 = csub(v[c][1], v[c][3]);
+      const T rot = inv ? cmul_i(d13) : cmul_mi(d13);   // (-i or +i) (v1 - v3)
+      v[c][0] = cadd(s02, s13);
+      v[c][2] = csub(s02, s13);
+      v[c][1] = cadd(d02, rot);
+      v[c][3] = csub(d02, rot);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      const int j = t + c * G;
+      const int k = j & (Ns - 1);
+      const int base = (j - k) * 4 + k;
+#pragma unroll
+      for (int r = 0; r < 4; ++r) x[base + r * Ns] = v[c][r];
+    }
+    __syncthreads();
+  }
+}
+
+constexpr int kFftCols = 4;       // columns per block of the column pass
+constexpr int kFftMaxM = 2048;    // column pass: 4 x M / 8 threads <= 1024
+
+// one row per block, M / 8 threads
+template <typename T>
+__global__ void __launch_bounds__(kFftMaxM / 8) k_fft_rows(T* __restrict__ X, int M, int logM,
+                                                           const T* __restrict__ tw, bool inv) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* s = reinterpret_cast<T*>(smem_raw);
+  T* row = X + int64_t(blockIdx.x) * M;
+  for (int i = threadIdx.x; i < M; i += blockDim.x) s[i] = row[i];
+  __syncthreads();
+  fft_smem<T>(s, M, logM, inv, tw, threadIdx.x);
+  for (int i = threadIdx.x; i < M; i += blockDim.x) row[i] = s[i];
+}
+
+// kFftCols adjacent columns per block, each held contiguously in shared memory;
+// M / 8 threads per column.
+template <typename T>
+__global__ void __launch_bounds__(kFftCols * kFftMaxM / 8) k_fft_cols(T* __restrict__ X, int M, int logM,
+                                                                      const T* __restrict__ tw, bool inv) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* s = reinterpret_cast<T*>(smem_raw);
+  const int c0 = blockIdx.x * kFftCols;
+  for (int e = threadIdx.x; e < kFftCols * M; e += blockDim.x) {
+    const int r = e / kFftCols, c = e % kFftCols;
+    s[c * M + r] = X[int64_t(r) * M + c0 + c];
+  }
+  __syncthreads();
+  const int G = M / 8;
+  const int c = threadIdx.x / G, t = threadIdx.x % G;
+  fft_smem<T>(s + c * M, M, logM, inv, tw, t);
+  for (int e = threadIdx.x; e < kFftCols * M; e += blockDim.x) {
+    const int r = e / kFftCols, cc = e % kFftCols;
+    X[int64_t(r) * M + c0 + cc] = s[cc * M + r];
+  }
+}
+
+template <typename T>
+cudaError_t fft2d(T* x, int M, int logM, const T* tw, bool inverse, cudaStream_t st) {
+  if (M < 256 || M > kFftMaxM || (M & (M - 1))) return cudaErrorInvalidValue;
+  const size_t srow = size_t(M) * sizeof(T), scol = size_t(M) * kFftCols * sizeof(T);
+  static bool attr_done = false;
+  if (!attr_done) {
+    cudaFuncSetAttribute(k_fft_rows<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kFftMaxM * sizeof(T)));
+    cudaFuncSetAttribute(k_fft_cols<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         int(kFftMaxM * kFftCols * sizeof(T)));
+    attr_done = true;
+  }
+  k_fft_rows<T><<<M, M / 8, srow, st>>>(x, M, logM, tw, inverse);
+  k_fft_cols<T><<<M / kFftCols, kFftCols * M / 8, scol, st>>>(x, M, logM, tw, inverse);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ spectral product
+template <typename T>
+__global__ void __launch_bounds__(256) k_spectral(int64_t n, T* __restrict__ Sm, const T* __restrict__ Sd,
+                                                  const T* __restrict__ Gh, const T* __restrict__ Dh) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i < n) Sm[i] = cfma(Sd[i], Dh[i], cmul(Sm[i], Gh[i]));
+}
+
+// ------------------------------------------------------------ local expansion
+template <typename T>
+__global__ void __launch_bounds__(256) k_local_coeffs(int nocc, const int* __restrict__ occ_cells,
+                                                      const int* __restrict__ occ_of_cell, int L, int Ne,
+                                                      int M, const T* __restrict__ V, const T* __restrict__ Bp,
+                                                      const T* __restrict__ BT, const T* __restrict__ sigma,
+                                                      int n_es, int nfb2, T* __restrict__ gamma) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int n_loc = (Ne + 1) * (Ne + 1);
+  T* Vc = reinterpret_cast<T*>(smem_raw);
+  T* sg = Vc + n_loc;
+  const int k = blockIdx.x;
+  const int c = occ_cells[k], ci = c % L, cj = c / L;
+  for (int p = threadIdx.x; p < n_loc; p += blockDim.x) {
+    const int a = p / (Ne + 1), b = p % (Ne + 1);
+    Vc[p] = V[int64_t(ci * Ne + a) * M + cj * Ne + b];
+  }
+  for (int e = threadIdx.x; e < 9 * n_es; e += blockDim.x) {
+    const int o = e / n_es, l = e % n_es;
+    const int ni = ci + o / 3 - 1, nj = cj + o % 3 - 1;
+    T v = czero(T{});
+    if (ni >= 0 && ni < L && nj >= 0 && nj < L) {
+      const int occ = occ_of_cell[nj * L + ni];
+      if (occ >= 0) v = sigma[int64_t(occ) * n_es + l];
+    }
+    sg[e] = v;
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int n = warp; n < nfb2; n += nw) {
+    T acc = czero(T{});
+    for (int p = lane; p < n_loc; p += 32) acc = cfma(Bp[int64_t(n) * n_loc + p], Vc[p], acc);
+    T sub = czero(T{});
+    for (int e = lane; e < 9 * n_es; e += 32) {
+      const int o = e / n_es, l = e % n_es;
+      sub = cfma(BT[(int64_t(o) * nfb2 + n) * n_es + l], sg[e], sub);
+    }
+    acc = warp_sum(csub(acc, sub));
+    if (lane == 0) gamma[int64_t(k) * nfb2 + n] = acc;
+  }
+}
+
+// ------------------------------------------------------------ near field + assembly
+template <typename T>
+__global__ void __launch_bounds__(256) k_near_eval(int64_t N, const int64_t* __restrict__ rowptr,
+                                                   const int* __restrict__ col, const T* __restrict__ val,
+                                                   const T* __restrict__ u, const T* __restrict__ Phi,
+                                                   const T* __restrict__ gamma, const int* __restrict__ occ_of_node,
+                                                   int nfb2, typename RealOf<T>::R kappa2, T* __restrict__ out) {
+  const int64_t q = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (q >= N) return;
+  T acc = czero(T{});
+  const int64_t r0 = rowptr[q], r1 = rowptr[q + 1];
+  for (int64_t k = r0 + lane; k < r1; k += 32) acc = cfma(val[k], u[col[k]], acc);
+  const T* ph = Phi + q * nfb2;
+  const T* g = gamma + int64_t(occ_of_node[q]) * nfb2;
+  for (int n = lane; n < nfb2; n += 32) acc = cfma(ph[n], g[n], acc);
+  acc = warp_sum(acc);
+  if (lane == 0) {
+    const T uq = u[q];
+    out[q] = mk(uq.x + kappa2 * acc.x, uq.y + kappa2 * acc.y);
+  }
+}
+
+template <typename T>
+cudaError_t apply_one(const ApplyData<T>& d, const T* u, T* out, cudaStream_t st, cudaEvent_t* ev) {
+  if (ev) cudaEventRecord(ev[0], st);
+  k_es_project<T><<<d.nocc, 256, 0, st>>>(d.nocc, d.occ_start, d.P_off, d.P, u, d.sigma, d.n_es);
+  if (ev) cudaEventRecord(ev[1], st);
+  const int64_t MM = int64_t(d.M) * d.M;
+  k_lattice_fill<T><<<unsigned((MM + 255) / 256), 256, 0, st>>>(d.M, d.n_lat, d.Ne, d.L, d.occ_of_cell,
+                                                                 d.sigma, d.n_es, d.Sm, d.Sd);
+  if (ev) cudaEventRecord(ev[2], st);
+  cudaError_t e = fft2d<T>(d.Sm, d.M, d.logM, d.tw, false, st);
+  if (e != cudaSuccess) return e;
+  e = fft2d<T>(d.Sd, d.M, d.logM, d.tw, false, st);
+  if (e != cudaSuccess) return e;
+  k_spectral<T><<<unsigned((MM + 255) / 256), 256, 0, st>>>(MM, d.Sm, d.Sd, d.Ghat, d.Dhat);
+  e = fft2d<T>(d.Sm, d.M, d.logM, d.tw, true, st);
+  if (e != cudaSuccess) return e;
+  if (ev) cudaEventRecord(ev[3], st);
+  const size_t sm_local = size_t(d.n_loc + 9 * d.n_es) * sizeof(T);
+  k_local_coeffs<T><<<d.nocc, 256, sm_local, st>>>(d.nocc, d.occ_cells, d.occ_of_cell, d.L, d.Ne, d.M, d.Sm,
+                                                   d.Bp, d.BT, d.sigma, d.n_es, d.nfb2, d.gamma);
+  if (ev) cudaEventRecord(ev[4], st);
+  k_near_eval<T><<<unsigned((d.N * 32 + 255) / 256), 256, 0, st>>>(
+      d.N, d.rowptr, d.col, d.val, u, d.Phi, d.gamma, d.occ_of_node, d.nfb2,
+      typename RealOf<T>::R(d.kappa2), out);
+  if (ev) cudaEventRecord(ev[5], st);
+  return cudaGetLastError();
+}
+
+template cudaError_t apply_one<double2>(const ApplyData<double2>&, const double2*, double2*, cudaStream_t,
+                                        cudaEvent_t*);
+template cudaError_t apply_one<float2>(const ApplyData<float2>&, const float2*, float2*, cudaStream_t,
+                                       cudaEvent_t*);
+template cudaError_t fft2d<double2>(double2*, int, int, const double2*, bool, cudaStream_t);
+template cudaError_t fft2d<float2>(float2*, int, int, const float2*, bool, cudaStream_t);
+
+// ------------------------------------------------------------ GMRES helpers
+constexpr int kRedThreads = 256;
+
+int gram_blocks(int64_t N) {
+  int64_t b = (N + kRedThreads * 4 - 1) / (kRedThreads * 4);
+  if (b > 304) b = 304;
+  if (b < 1) b = 1;
+  return int(b);
+}
+
+__device__ __forceinline__ double2 block_sum(double2 v, double2* red) {
+  v = warp_sum(v);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  double2 r = make_double2(0, 0);
+  if (threadIdx.x < 32) {
+    r = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : make_double2(0, 0);
+    r = warp_sum(r);
+  }
+  return r;
+}
+
+__global__ void __launch_bounds__(kRedThreads) k_gram_partial(const double2* __restrict__ V, int nv,
+                                                              const double2* __restrict__ w, int64_t N,
+                                                              double2* __restrict__ partial) {
+  __shared__ double2 red[32];
+  for (int j = 0; j < nv; ++j) {
+    const double2* vj = V + int64_t(j) * N;
+    double2 acc = make_double2(0, 0);
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < N; i += int64_t(gridDim.x) * blockDim.x)
+      acc = cfma(cconj(vj[i]), w[i], acc);
+    const double2 s = block_sum(acc, red);
+    if (threadIdx.x == 0) partial[int64_t(blockIdx.x) * nv + j] = s;
+  }
+}
+
+__global__ void k_gram_reduce(const double2* __restrict__ partial, int nblk, int nv, double2* __restrict__ h) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= nv) return;
+  double2 s = make_double2(0, 0);
+  for (int b = 0; b < nblk; ++b) s = cadd(s, partial[int64_t(b) * nv + j]);
+  h[j] = s;
+}
+
+cudaError_t gram(const double2* V, int nv, const double2* w, int64_t N, double2* partial, double2* h,
+                 cudaStream_t st) {
+  const int nb = gram_blocks(N);
+  k_gram_partial<<<nb, kRedThreads, 0, st>>>(V, nv, w, N, partial);
+  k_gram_reduce<<<(nv + 127) / 128, 128, 0, st>>>(partial, nb, nv, h);
+  return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(256) k_axpy_multi(const double2* __restrict__ V, int nv,
+                                                    const double2* __restrict__ h, double2* __restrict__ w,
+                                                    int64_t N) {
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < N; i += int64_t(gridDim.x) * blockDim.x) {
+    double2 acc = w[i];
+    for (int j = 0; j < nv; ++j) {
+      const double2 hj = h[j];
+      const double2 v = V[int64_t(j) * N + i];
+      acc = csub(acc, cmul(hj, v));
+    }
+    w[i] = acc;
+  }
+}
+
+static unsigned grid_for(int64_t N) {
+  int64_t b = (N + 255) / 256;
+  if (b > 152 * 16) b = 152 * 16;
+  return unsigned(b < 1 ? 1 : b);
+}
+
+cudaError_t axpy_multi(const double2* V, int nv, const double2* h, double2* w, int64_t N, cudaStream_t st) {
+  k_axpy_multi<<<grid_for(N), 256, 0, st>>>(V, nv, h, w, N);
+  return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(kRedThreads) k_norm_partial(const double2* __restrict__ w, int64_t N,
+                                                              double* __restrict__ partial) {
+  __shared__ double2 red[32];
+  double2 acc = make_double2(0, 0);
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < N; i += int64_t(gridDim.x) * blockDim.x)
+    acc.x = fma(w[i].x, w[i].x, fma(w[i].y, w[i].y, acc.x));
+  const double2 s = block_sum(acc, red);
+  if (threadIdx.x == 0) partial[blockIdx.x] = s.x;
+}
+
+__global__ void k_norm_reduce(const double* __restrict__ partial, int nb, double* __restrict__ out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double s = 0;
+    for (int b = 0; b < nb; ++b) s += partial[b];
+    out[0] = sqrt(s);
+  }
+}
+
+cudaError_t norm2(const double2* w, int64_t N, double* partial, double* out, cudaStream_t st) {
+  const int nb = gram_blocks(N);
+  k_norm_partial<<<nb, kRedThreads, 0, st>>>(w, N, partial);
+  k_norm_reduce<<<1, 32, 0, st>>>(partial, nb, out);
+  return cudaGetLastError();
+}
+
+__global__ void k_scale_into(const double2* __restrict__ w, const double* __restrict__ nrm, double2* __restrict__ v,
+                             int64_t N) {
+  const double s = nrm[0] > 0 ? 1.0 / nrm[0] : 0.0;
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < N; i += int64_t(gridDim.x) * blockDim.x)
+    v[i] = cscale(w[i], s);
+}
+
+cudaError_t scale_into(const double2* w, const double* nrm, double2* v, int64_t N, cudaStream_t st) {
+  k_scale_into<<<grid_for(N), 256, 0, st>>>(w, nrm, v, N);
+  return cudaGetLastError();
+}
+
+__global__ void k_combine(const double2* __restrict__ V, int k, const double2* __restrict__ y, double2* __restrict__ x,
+                          int64_t N) {
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < N; i += int64_t(gridDim.x) * blockDim.x) {
+    double2 acc = x[i];
+    for (int j = 0; j < k; ++j) acc = cfma(y[j], V[int64_t(j) * N + i], acc);
+    x[i] = acc;
+  }
+}
+
+cudaError_t combine(const double2* V, int k, const double2* y, double2* x, int64_t N, cudaStream_t st) {
+  k_combine<<<grid_for(N), 256, 0, st>>>(V, k, y, x, N);
+  return cudaGetLastError();
+}
+
+__global__ void k_sub(const double2* __restrict__ a, const double2* __restrict__ b, double2* __restrict__ o, int64_t N) {
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < N; i += int64_t(gridDim.x) * blockDim.x)
+    o[i] = csub(a[i], b[i]);
+}
+cudaError_t sub(const double2* a, const double2* b, double2* out, int64_t N, cudaStream_t st) {
+  k_sub<<<grid_for(N), 256, 0, st>>>(a, b, out, N);
+  return cudaGetLastError();
+}
+
+__global__ void k_to_c64(const double2* __restrict__ a, float2* __restrict__ b, int64_t N) {
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < N; i += int64_t(gridDim.x) * blockDim.x)
+    b[i] = make_float2(float(a[i].x), float(a[i].y));
+}
+cudaError_t to_c64(const double2* a, float2* b, int64_t N, cudaStream_t st) {
+  k_to_c64<<<grid_for(N), 256, 0, st>>>(a, b, N);
+  return cudaGetLastError();
+}
+__global__ void k_to_c128(const float2* __restrict__ a, double2* __restrict__ b, int64_t N) {
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < N; i += int64_t(gridDim.x) * blockDim.x)
+    b[i] = make_double2(double(a[i].x), double(a[i].y));
+}
+cudaError_t to_c128(const float2* a, double2* b, int64_t N, cudaStream_t st) {
+  k_to_c128<<<grid_for(N), 256, 0, st>>>(a, b, N);
+  return cudaGetLastError();
+}
+__global__ void k_add(double2* __restrict__ x, const double2* __restrict__ e, int64_t N) {
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < N; i += int64_t(gridDim.x) * blockDim.x)
+    x[i] = cadd(x[i], e[i]);
+}
+cudaError_t add_inplace(double2* x, const double2* e, int64_t N, cudaStream_t st) {
+  k_add<<<grid_for(N), 256, 0, st>>>(x, e, N);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ far field
+__global__ void __launch_bounds__(kRedThreads) k_farfield(int64_t N, const double* __restrict__ x,
+                                                          const double* __restrict__ y,
+                                                          const double* __restrict__ ffw,
+                                                          const double2* __restrict__ u,
+                                                          const double* __restrict__ dirs, int ndir, double kappa,
+                                                          double2 c, double2* __restrict__ A) {
+  __shared__ double2 red[32];
+  const int j = blockIdx.x, r = blockIdx.y;
+  const double dx = dirs[2 * j], dy = dirs[2 * j + 1];
+  const double2* ur = u + int64_t(r) * N;
+  double2 acc = make_double2(0, 0);
+  for (int64_t l = threadIdx.x; l < N; l += blockDim.x) {
+    double s, co;
+    sincos(-kappa * (dx * x[l] + dy * y[l]), &s, &co);
+    acc = cfma(cscale(make_double2(co, s), ffw[l]), ur[l], acc);
+  }
+  const double2 t = block_sum(acc, red);
+  if (threadIdx.x == 0) A[int64_t(r) * ndir + j] = cmul(c, t);
+}
+
+cudaError_t farfield(int64_t N, const double* x, const double* y, const double* ffw, const double2* u, int nrhs,
+                     const double* dirs, int ndir, double kappa, double2 c, double2* A, cudaStream_t st) {
+  k_farfield<<<dim3(ndir, nrhs), kRedThreads, 0, st>>>(N, x, y, ffw, u, dirs, ndir, kappa, c, A);
+  return cudaGetLastError();
+}
+
+}  // namespace lsd

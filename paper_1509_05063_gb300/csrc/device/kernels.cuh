@@ -1,0 +1,71 @@
+// Launchers of the sm_103a kernels of the LS apply / solve (device/kernels.cu).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace lsd {
+
+// Device-resident pieces of a plan for one arithmetic precision R.
+template <typename T>
+struct ApplyData {
+  int64_t N = 0;
+  int nocc = 0, L = 0, Ne = 0, n_es = 0, n_loc = 0, nfb2 = 0, M = 0, n_lat = 0, logM = 0;
+  const int64_t* occ_start = nullptr;   // nocc + 1: node range of each occupied cell
+  const int* occ_cells = nullptr;       // nocc: cell id
+  const int* occ_of_cell = nullptr;     // L*L: occupied index or -1
+  const int* occ_of_node = nullptr;     // N: occupied index of the node's cell
+  const int64_t* P_off = nullptr;       // nocc + 1
+  const T* P = nullptr;                 // projections
+  const T* Bp = nullptr;                // nfb2 x n_loc
+  const T* BT = nullptr;                // 9 x nfb2 x n_es
+  const T* Phi = nullptr;               // N x nfb2
+  const T* Ghat = nullptr;              // M x M spectra (scaled by 1/M^2)
+  const T* Dhat = nullptr;
+  const T* tw = nullptr;                // M twiddles exp(-2 pi i m / M)
+  const int64_t* rowptr = nullptr;      // near field CSR
+  const int* col = nullptr;
+  const T* val = nullptr;
+  double kappa2 = 0;
+  // work space
+  T* sigma = nullptr;                   // nocc x n_es
+  T* Sm = nullptr;                      // M x M
+  T* Sd = nullptr;                      // M x M
+  T* gamma = nullptr;                   // nocc x nfb2
+};
+
+// Stage boundaries of one apply, for event timing: projection, lattice fill,
+// forward FFTs + product + inverse FFT, local coefficients, near field + assembly.
+constexpr int kStages = 5;
+
+// out = A u for one right-hand side (u, out: N complex).  When ev is not null
+// it holds kStages + 1 events recorded at the stage boundaries.  Returns the
+// first launch error (cudaSuccess otherwise).
+template <typename T>
+cudaError_t apply_one(const ApplyData<T>& d, const T* u, T* out, cudaStream_t st, cudaEvent_t* ev = nullptr);
+
+// 2-D FFT of an M x M array in place (rows then columns), forward or inverse
+// (unscaled).
+template <typename T>
+cudaError_t fft2d(T* x, int M, int logM, const T* tw, bool inverse, cudaStream_t st);
+
+// GMRES helpers (complex128).  h[j] = <V_j, w> for j < nv (V: nv vectors of
+// length N, stride N); partial needs blocks * nv elements.
+cudaError_t gram(const double2* V, int nv, const double2* w, int64_t N, double2* partial,
+                 double2* h, cudaStream_t st);
+cudaError_t axpy_multi(const double2* V, int nv, const double2* h, double2* w, int64_t N,
+                       cudaStream_t st);
+cudaError_t norm2(const double2* w, int64_t N, double* partial, double* out, cudaStream_t st);
+cudaError_t scale_into(const double2* w, const double* nrm, double2* v, int64_t N, cudaStream_t st);
+cudaError_t combine(const double2* V, int k, const double2* y, double2* x, int64_t N, cudaStream_t st);
+cudaError_t sub(const double2* a, const double2* b, double2* out, int64_t N, cudaStream_t st);
+cudaError_t to_c64(const double2* a, float2* b, int64_t N, cudaStream_t st);
+cudaError_t to_c128(const float2* a, double2* b, int64_t N, cudaStream_t st);
+cudaError_t add_inplace(double2* x, const double2* e, int64_t N, cudaStream_t st);
+
+cudaError_t farfield(int64_t N, const double* x, const double* y, const double* ffw,
+                     const double2* u, int nrhs, const double* dirs, int ndir, double kappa,
+                     double2 c, double2* A, cudaStream_t st);
+
+int gram_blocks(int64_t N);
+
+}  // namespace lsd

@@ -1,0 +1,296 @@
+"""ctypes binding of libls_gb300.so (C ABI of include/ls.h).
+
+Argument marshalling only: geometry / option structs, the host n^2 callback,
+torch tensors passed as raw device pointers with torch's current CUDA stream.
+The library must have been built (``build_library()`` or ``__graft_entry__.build()``);
+loading fails loudly otherwise -- there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LS_FP64, LS_MIXED = 0, 1
+_SHAPES = {"disc": 0, "kite": 1}
+_STATUS = {0: "ok", 1: "invalid argument", 2: "out of memory", 3: "CUDA error", 4: "no convergence",
+           5: "device wait timed out", 6: "unsupported"}
+
+
+def lib_path() -> str:
+    return os.path.join(_PKG, "_lib", "libls_gb300.so")
+
+
+def build_library(verbose: bool = False) -> str:
+    from . import build as _b
+    return _b.build(verbose=verbose)
+
+
+class LSError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Geometry(C.Structure):
+    _fields_ = [("dim", C.c_int), ("shape", C.c_int), ("params", C.c_double * 8), ("collar_w", C.c_double),
+                ("n1", C.c_int), ("n2", C.c_int), ("tau0", C.c_double), ("tau1", C.c_double),
+                ("h", C.c_double), ("cart_x0", C.c_double), ("cart_y0", C.c_double),
+                ("cart_nx", C.c_int), ("cart_ny", C.c_int)]
+
+
+class Options(C.Structure):
+    _fields_ = [("Q", C.c_int), ("p", C.c_int), ("R_a", C.c_double), ("R_b", C.c_double),
+                ("R_cart", C.c_double), ("M", C.c_int), ("N_tau", C.c_int), ("q_polar", C.c_int),
+                ("n_rho", C.c_int), ("n_theta", C.c_int), ("chi_s0", C.c_double),
+                ("box_x0", C.c_double), ("box_y0", C.c_double), ("H", C.c_double),
+                ("L", C.c_int), ("N_eq", C.c_int), ("n_fb", C.c_int), ("n_coll", C.c_int),
+                ("rcond", C.c_double), ("rcond_mixed", C.c_double), ("n_threads", C.c_int)]
+
+
+class PlanInfo(C.Structure):
+    _fields_ = [("N", C.c_int64), ("n_collar", C.c_int64), ("n_cart", C.c_int64), ("nnz_near", C.c_int64),
+                ("L", C.c_int), ("N_eq", C.c_int), ("n_es", C.c_int), ("n_loc", C.c_int), ("n_fb", C.c_int),
+                ("fft_M", C.c_int), ("n_cells_occupied", C.c_int), ("plan_seconds", C.c_double),
+                ("device_bytes", C.c_int64)]
+
+
+class SolveInfo(C.Structure):
+    _fields_ = [("iterations", C.c_int), ("refinements", C.c_int), ("residual", C.c_double),
+                ("seconds", C.c_double)]
+
+
+N2FN = C.CFUNCTYPE(C.c_int, C.c_int64, C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_void_p)
+
+_lib = None
+_SIGS = {
+    "ls_plan_create": ([C.POINTER(Geometry), N2FN, C.c_void_p, C.c_double, C.POINTER(Options), C.POINTER(C.c_void_p)]),
+    "ls_plan_info": ([C.c_void_p, C.POINTER(PlanInfo)]),
+    "ls_plan_nodes": ([C.c_void_p, C.c_void_p, C.c_void_p]),
+    "ls_apply": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p]),
+    "ls_solve": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_double, C.c_int, C.c_int, C.c_int,
+                  C.POINTER(SolveInfo), C.c_void_p]),
+    "ls_farfield": ([C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
+    "ls_plan_destroy": ([C.c_void_p]),
+    "ls_status_string": ([C.c_int]),
+    "ls_last_error": ([C.c_void_p]),
+    "ls_host_plan_create": ([C.POINTER(Geometry), N2FN, C.c_void_p, C.c_double, C.POINTER(Options),
+                            C.POINTER(C.c_void_p)]),
+    "ls_host_plan_sizes": ([C.c_void_p, C.c_void_p]),
+    "ls_host_plan_nodes": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "ls_host_plan_near": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "ls_host_plan_accel": ([C.c_void_p] + [C.c_void_p] * 8),
+    "ls_host_plan_destroy": ([C.c_void_p]),
+    "ls_set_stage_timing": ([C.c_void_p, C.c_int]),
+    "ls_get_stage_times": ([C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
+}
+EXPORTED = tuple(_SIGS)
+
+
+def load_library(path: str | None = None):
+    """Load libls_gb300.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or lib_path()
+    if not os.path.exists(p):
+        raise LSError(6, f"{p} is missing: build it with paper_1509_05063_gb300.build_library()")
+    lib = C.CDLL(p)
+    for name, args in _SIGS.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = C.c_char_p if name in ("ls_status_string", "ls_last_error") else C.c_int
+    if path is None:
+        _lib = lib
+    return lib
+
+
+def _check(st: int, handle=None):
+    if st != 0:
+        msg = _lib.ls_last_error(handle).decode() if _lib is not None else ""
+        raise LSError(st, msg)
+
+
+def geometry_from(wl) -> Geometry:
+    g = Geometry()
+    g.dim = 2
+    g.shape = _SHAPES[wl.shape]
+    for i, v in enumerate(wl.shape_params):
+        g.params[i] = float(v)
+    g.collar_w, g.n1, g.n2, g.tau0, g.tau1 = wl.collar_w, wl.n1, wl.n2, wl.tau0, wl.tau1
+    g.h, g.cart_x0, g.cart_y0, g.cart_nx, g.cart_ny = wl.h, wl.cart_x0, wl.cart_y0, wl.cart_nx, wl.cart_ny
+    return g
+
+
+def options_from(wl, n_threads: int = 0, rcond: float = 0.0, rcond_mixed: float = 0.0) -> Options:
+    o = Options()
+    for f in ("Q", "p", "R_a", "R_b", "R_cart", "M", "N_tau", "q_polar", "n_rho", "n_theta", "chi_s0",
+              "box_x0", "box_y0", "H", "L", "N_eq", "n_fb", "n_coll"):
+        setattr(o, f, getattr(wl, f))
+    o.rcond, o.rcond_mixed, o.n_threads = rcond, rcond_mixed, n_threads
+    return o
+
+
+def _n2_callback(n2):
+    def cb(n, xy, out, ctx):
+        try:
+            pts = np.ctypeslib.as_array(xy, shape=(n, 2))
+            vals = np.asarray(n2(pts), dtype=np.float64).reshape(n)
+            np.ctypeslib.as_array(out, shape=(n,))[:] = vals
+            return 0
+        except Exception:  # the C side reports the failure
+            return 1
+    return N2FN(cb)
+
+
+def _stream(stream):
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return C.c_void_p(s.cuda_stream)
+
+
+class Plan:
+    """A device plan (ls_plan_create).  n2: callable mapping (n, 2) points to n^2 values."""
+
+    def __init__(self, wl, n2, n_threads: int = 0, rcond: float = 0.0, rcond_mixed: float = 0.0):
+        load_library()
+        self.wl = wl
+        self.kappa = float(wl.kappa)
+        self._cb = _n2_callback(n2)
+        h = C.c_void_p()
+        st = _lib.ls_plan_create(C.byref(geometry_from(wl)), self._cb, None, self.kappa,
+                                 C.byref(options_from(wl, n_threads, rcond, rcond_mixed)), C.byref(h))
+        if st != 0:
+            raise LSError(st, _lib.ls_last_error(None).decode())
+        self._h = h
+        info = PlanInfo()
+        _check(_lib.ls_plan_info(self._h, C.byref(info)), self._h)
+        self.info = {f: getattr(info, f) for f, _ in PlanInfo._fields_}
+        self.N = int(info.N)
+
+    def nodes(self):
+        xy = np.zeros((self.N, 2))
+        canon = np.zeros(self.N, np.int64)
+        _check(_lib.ls_plan_nodes(self._h, xy.ctypes.data, canon.ctypes.data), self._h)
+        return xy, canon
+
+    def apply(self, u, out=None, prec: int = LS_FP64, stream=None):
+        """A u for torch tensors on the GPU: complex128 (LS_FP64) or complex64
+        (LS_MIXED), shape (N,) or (nrhs, N)."""
+        import torch
+        want = torch.complex128 if prec == LS_FP64 else torch.complex64
+        if u.dtype != want or not u.is_cuda or not u.is_contiguous():
+            raise LSError(1, f"u must be a contiguous CUDA {want} tensor")
+        nrhs = 1 if u.dim() == 1 else u.shape[0]
+        if u.shape[-1] != self.N:
+            raise LSError(1, "length mismatch")
+        if out is None:
+            out = torch.empty_like(u)
+        _check(_lib.ls_apply(self._h, C.c_void_p(u.data_ptr()), C.c_void_p(out.data_ptr()), nrhs, prec,
+                             _stream(stream)), self._h)
+        return out
+
+    def solve(self, uinc, u0=None, tol: float = 1e-10, max_iter: int = 500, restart: int = 100,
+              prec: int = LS_FP64, stream=None):
+        import torch
+        if uinc.dtype != torch.complex128 or not uinc.is_cuda or not uinc.is_contiguous():
+            raise LSError(1, "uinc must be a contiguous CUDA complex128 tensor")
+        nrhs = 1 if uinc.dim() == 1 else uinc.shape[0]
+        u = torch.zeros_like(uinc) if u0 is None else u0.clone()
+        info = SolveInfo()
+        st = _lib.ls_solve(self._h, C.c_void_p(uinc.data_ptr()), C.c_void_p(u.data_ptr()), nrhs, tol, max_iter,
+                           restart, prec, C.byref(info), _stream(stream))
+        res = {f: getattr(info, f) for f, _ in SolveInfo._fields_}
+        if st not in (0, 4):
+            _check(st, self._h)
+        res["converged"] = st == 0
+        return u, res
+
+    def farfield(self, u, dirs, stream=None):
+        import torch
+        dirs = np.ascontiguousarray(dirs, dtype=np.float64).reshape(-1, 2)
+        nrhs = 1 if u.dim() == 1 else u.shape[0]
+        A = torch.empty((nrhs, len(dirs)), dtype=torch.complex128, device=u.device)
+        _check(_lib.ls_farfield(self._h, C.c_void_p(u.data_ptr()), nrhs, dirs.ctypes.data, len(dirs),
+                                C.c_void_p(A.data_ptr()), _stream(stream)), self._h)
+        return A
+
+    def set_stage_timing(self, enable: bool):
+        _check(_lib.ls_set_stage_timing(self._h, int(enable)), self._h)
+
+    def stage_times(self, prec: int = LS_FP64):
+        ms = np.zeros(5)
+        calls = np.zeros(1, np.int64)
+        _check(_lib.ls_get_stage_times(self._h, prec, ms.ctypes.data, calls.ctypes.data), self._h)
+        return ms, int(calls[0])
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.ls_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class HostPlan:
+    """Host-only plan construction (ls_host_plan_*): nodes, near-field CSR and
+    accelerator matrices as numpy arrays.  No GPU needed."""
+
+    def __init__(self, wl, n2, n_threads: int = 0, rcond: float = 0.0):
+        load_library()
+        self.wl = wl
+        cb = _n2_callback(n2)
+        h = C.c_void_p()
+        st = _lib.ls_host_plan_create(C.byref(geometry_from(wl)), cb, None, float(wl.kappa),
+                                      C.byref(options_from(wl, n_threads, rcond)), C.byref(h))
+        if st != 0:
+            raise LSError(st, _lib.ls_last_error(None).decode())
+        self._h = h
+        sz = np.zeros(8, np.int64)
+        _check(_lib.ls_host_plan_sizes(h, sz.ctypes.data))
+        self.N, self.nnz, self.nocc, self.n_es, self.nfb2, self.n_loc, self.M, self.P_len = map(int, sz)
+
+    def nodes(self):
+        xy = np.zeros((self.N, 2))
+        canon = np.zeros(self.N, np.int64)
+        wfac = np.zeros(self.N)
+        _check(_lib.ls_host_plan_nodes(self._h, xy.ctypes.data, canon.ctypes.data, wfac.ctypes.data))
+        return xy, canon, wfac
+
+    def near(self):
+        import scipy.sparse as sp
+        rowptr = np.zeros(self.N + 1, np.int64)
+        col = np.zeros(self.nnz, np.int32)
+        val = np.zeros(self.nnz, np.complex128)
+        _check(_lib.ls_host_plan_near(self._h, rowptr.ctypes.data, col.ctypes.data, val.ctypes.data))
+        return sp.csr_matrix((val, col, rowptr), shape=(self.N, self.N))
+
+    def accel(self):
+        occ = np.zeros(self.nocc, np.int32)
+        P_off = np.zeros(self.nocc + 1, np.int64)
+        P = np.zeros(self.P_len, np.complex128)
+        Bp = np.zeros((self.nfb2, self.n_loc), np.complex128)
+        BT = np.zeros((9, self.nfb2, self.n_es), np.complex128)
+        Phi = np.zeros((self.N, self.nfb2), np.complex128)
+        G = np.zeros((self.M, self.M), np.complex128)
+        D = np.zeros((self.M, self.M), np.complex128)
+        _check(_lib.ls_host_plan_accel(self._h, occ.ctypes.data, P_off.ctypes.data, P.ctypes.data, Bp.ctypes.data,
+                                       BT.ctypes.data, Phi.ctypes.data, G.ctypes.data, D.ctypes.data))
+        return dict(occ=occ, P_off=P_off, P=P, Bpinv=Bp, BT=BT, Phi=Phi, Gtab=G, Dtab=D)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.ls_host_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,137 @@
+"""CPU checks of the C-ABI library (no GPU): it loads, exports every symbol
+declared in include/ls.h, rejects bad input with status codes, and its
+independent host plan construction reproduces the oracle's discretisation
+(nodes, weights, near-field matrix, accelerator matrices)."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle.accel import Accelerator, Cells, near_matrix
+from oracle.geometry import Discretisation
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import paper_1509_05063_gb300 as pkg
+    if not os.path.exists(pkg.lib_path()):
+        pkg.build_library()
+    return pkg.load_library()
+
+
+def declared_symbols():
+    src = open(os.path.join(ROOT, "include", "ls.h")).read()
+    return sorted(set(re.findall(r"^\s*(?:ls_status|const char\*)\s+(ls_\w+)\s*\(", src, re.M)))
+
+
+def test_library_exports_every_declared_symbol(lib):
+    import paper_1509_05063_gb300.ls as b
+    names = declared_symbols()
+    assert len(names) >= 14
+    for n in names:
+        assert hasattr(lib, n), n
+        assert n in b.EXPORTED, n
+
+
+def test_invalid_arguments_return_status(lib):
+    import paper_1509_05063_gb300.ls as b
+    wl = W.cfg1()
+    g = b.geometry_from(wl)
+    o = b.options_from(wl)
+    h = C.c_void_p()
+    cb = b._n2_callback(W.n2_of(wl))
+    g.dim = 3
+    assert lib.ls_host_plan_create(C.byref(g), cb, None, wl.kappa, C.byref(o), C.byref(h)) == 6
+    g.dim = 2
+    assert lib.ls_host_plan_create(C.byref(g), cb, None, -1.0, C.byref(o), C.byref(h)) == 1
+    o.L = 2            # cells too large for the box -> nodes outside
+    assert lib.ls_host_plan_create(C.byref(g), cb, None, wl.kappa, C.byref(o), C.byref(h)) == 1
+    assert b"outside" in lib.ls_last_error(None)
+    o = b.options_from(wl)
+    o.H, o.L = 0.12, 20   # cells too small for the cut-off support -> eta leaves N(x)
+    o.box_x0 = o.box_y0 = -1.2
+    assert lib.ls_host_plan_create(C.byref(g), cb, None, wl.kappa, C.byref(o), C.byref(h)) == 1
+    assert b"3 x 3" in lib.ls_last_error(None)
+    bad = b.N2FN(lambda n, xy, out, ctx: 1)
+    o = b.options_from(wl)
+    assert lib.ls_host_plan_create(C.byref(g), bad, None, wl.kappa, C.byref(o), C.byref(h)) == 1
+    assert lib.ls_apply(None, None, None, 1, 0, None) == 1
+    assert lib.ls_plan_destroy(None) == 0
+    assert lib.ls_status_string(4) == b"no convergence"
+
+
+def _small_disc():
+    return W.disc(level=1, kappa=2.0, n2c=2.0, collar_w=0.6, tau0=0.3, tau1=0.95, R_a=4, R_b=2, R_cart=3,
+                  p=7, n_rho=48, N_tau=64, box_x0=-1.2, box_y0=-1.2, H=0.3, L=8, N_eq=8, n_fb=15)
+
+
+def _small_kite():
+    return W.kite(n1=512, n2=17, h=0.025, kappa=6.0, collar_w=0.07, tau0=0.4, tau1=0.9, R_a=6, R_b=5,
+                  R_cart=4, n_rho=32, N_tau=48).replace(box_x0=-1.65, box_y0=-1.6, H=0.2, L=17,
+                                                        N_eq=8, n_fb=15)
+
+
+@pytest.mark.parametrize("make", [_small_disc, _small_kite])
+def test_host_plan_matches_oracle_discretisation(lib, make):
+    from paper_1509_05063_gb300 import HostPlan
+    wl = make()
+    hp = HostPlan(wl, W.n2_of(wl))
+    xy, canon, wfac = hp.nodes()
+    dz = Discretisation(wl)
+    assert hp.N == dz.N
+    assert np.array_equal(np.sort(canon), np.arange(dz.N))
+    assert np.max(np.abs(xy - dz.x[canon])) < 1e-13
+    assert np.max(np.abs(wfac - dz.wfac[canon])) < 1e-15
+    cells = Cells(dz)
+    rows = np.arange(dz.N) if dz.N < 2000 else W.random_rows(dz.N, 300)
+    ref = near_matrix(dz, cells, rows=rows)[:, canon].toarray()
+    inv = np.argsort(canon)
+    got = hp.near()[inv[rows]].toarray()
+    assert np.max(np.abs(got - ref)) <= 1e-13 * np.max(np.abs(ref))
+
+
+def test_host_accelerator_matrices_reproduce_oracle_far_field(lib):
+    """Run the accelerator's steps in numpy with the library's matrices (P_c,
+    B^+, B^+ T_o, Phi, kernel tables) and compare with the oracle's far part."""
+    from paper_1509_05063_gb300 import HostPlan
+    wl = _small_disc()
+    hp = HostPlan(wl, W.n2_of(wl))
+    xy, canon, _ = hp.nodes()
+    dz = Discretisation(wl)
+    acc = Accelerator(dz)
+    u = W.random_density(dz.N)[0]
+    ref = acc.apply_far(u)[canon]
+    A = hp.accel()
+    up = u[canon]
+    L, Ne, n_es, M = wl.L, wl.N_eq, hp.n_es, hp.M
+    cell = (np.floor((xy[:, 0] - wl.box_x0) / wl.H).astype(int)
+            + L * np.floor((xy[:, 1] - wl.box_y0) / wl.H).astype(int))
+    sig = {}
+    for k, c in enumerate(A["occ"]):
+        mem = np.nonzero(cell == c)[0]
+        sig[c] = A["P"][A["P_off"][k]:A["P_off"][k + 1]].reshape(n_es, len(mem)) @ up[mem]
+    Sm = np.zeros((M, M), complex)
+    Sd = np.zeros((M, M), complex)
+    for c, s in sig.items():
+        ci, cj = c % L, c // L
+        for f in range(4):
+            for kk in range(Ne + 1):
+                (Sm if f < 2 else Sd)[(ci + f % 2) * Ne, cj * Ne + kk] += s[f * (Ne + 1) + kk]
+    V = np.fft.ifft2(np.fft.fft2(Sm) * np.fft.fft2(A["Gtab"]) + np.fft.fft2(Sd) * np.fft.fft2(A["Dtab"]))
+    got = np.zeros(hp.N, complex)
+    for c in sig:
+        ci, cj = c % L, c // L
+        g = A["Bpinv"] @ np.array([V[ci * Ne + a, cj * Ne + b] for a in range(Ne + 1) for b in range(Ne + 1)])
+        for oi in (-1, 0, 1):
+            for oj in (-1, 0, 1):
+                nb = (cj + oj) * L + (ci + oi)
+                if 0 <= ci + oi < L and 0 <= cj + oj < L and nb in sig:
+                    g = g - A["BT"][(oi + 1) * 3 + (oj + 1)] @ sig[nb]
+        mem = np.nonzero(cell == c)[0]
+        got[mem] = A["Phi"][mem] @ g
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 1e-11

@@ -173,3 +173,31 @@ def kite(n1: int, n2: int, h: float, kappa: float, scale: float = 1.0, collar_w:
     return Workload(name=f"kite_{n1}x{n2}", shape="kite", shape_params=(scale, 0.0, 0.0),
                     kappa=kappa, n2_kind=n2_kind, n2_params=n2_params, collar_w=collar_w,
                     n1=n1, n2=n2, h=h, cart_x0=x0, cart_y0=y0, cart_nx=nx, cart_ny=ny, **kw)
+
+
+def cfg1() -> Workload:
+    """Disc a = 1, n^2 = 2 inside, kappa = 2, plane wave along x1; ~4k nodes
+    (collar 128 tangential x 17 transverse, Cartesian h = 0.03); complex128;
+    checked against the Bessel series."""
+    h = 0.03
+    x0, nx = _cart_grid_for(h, -1.0, 1.0)
+    return Workload(name="cfg1_disc_kappa2", shape="disc", shape_params=(1.0, 0.0, 0.0), kappa=2.0,
+                    n2_kind="const", n2_params=(2.0,), collar_w=0.48, n1=128, n2=17, tau0=0.35, tau1=0.9,
+                    h=h, cart_x0=x0, cart_y0=x0, cart_nx=nx, cart_ny=nx, R_a=5, R_b=5, R_cart=6,
+                    box_x0=-1.2, box_y0=-1.2, H=0.3, L=8, N_eq=8, n_fb=15)
+
+
+def cfg2(h: float = 0.0045, n1: int = 3200, L: int = 56, H: float = 0.055, N_eq: int = 8) -> Workload:
+    """Kite x = cos t + 0.65 cos 2t - 0.65, y = 1.5 sin t; n^2 = 1.5 + 0.5 exp(-|x|^2/0.1)
+    inside, 1 outside; kappa = 20, ~260k nodes, 1024^2 padded lattice FFT, GMRES tol 1e-10."""
+    wl = kite(n1=n1, n2=17, h=h, kappa=20.0, collar_w=0.07, tau0=0.4, tau1=0.9,
+              R_a=10, R_b=6, R_cart=8)
+    A = L * H
+    cx, cy = -0.25, 0.0
+    return wl.replace(name="cfg2_kite_kappa20", box_x0=cx - A / 2, box_y0=cy - A / 2, H=H, L=L,
+                      N_eq=N_eq, n_fb=2 * N_eq - 1)
+
+
+def n2_of(wl: Workload):
+    """Callable x -> n^2(x) for the workload (input definition)."""
+    return lambda x: n2_eval(wl.n2_kind, wl.n2_params, x)
