@@ -33,6 +33,9 @@ sys.path.insert(0, ROOT)
 
 METRIC = "LS matvecs/s and time to 1e-10 solve at N, mixed vs FP64 path, 1 GB300"
 FALLBACK_HBM_GBS = 6800.0
+# FP64 (non-tensor) peak derived from the unit counts and clock: 152 SMs x 2070 MHz x
+# 4 FLOP/clock/SM (2 FP64 FMA per clock per SM, the nominal 1.25 TFLOP/s)
+FP64_PEAK_TFLOPS = 152 * 2.070e9 * 4 / 1e12
 KERNELS_PER_APPLY = 11   # projection, lattice fill, 3 x (row + column FFT), product, local, near
 
 
@@ -66,7 +69,7 @@ class Clocks:
         os.close(fd)
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
@@ -164,13 +167,15 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--cpu-rows", type=int, default=192)
     ap.add_argument("--ref-rows", type=int, default=48)
+    ap.add_argument("--scale", type=int, default=1,
+                    help="coarsen config 2 by this factor (h, cells) for profiling captures")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -189,7 +194,8 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
 
-    wl = W.cfg2()
+    sc = args.scale
+    wl = W.cfg2(h=0.0045 * sc, n1=3200 // sc, L=56 // sc)
     plan = Plan(wl, W.n2_of(wl))
     info = plan.info
     N = plan.N
@@ -283,6 +289,7 @@ def main():
         return nnz * (cb + 4) + (N + 1) * 8 + N * cb + N * nfb2 * cb + N * 4 + nocc * nfb2 * cb + N * cb
 
     peak, peak_src = hbm_peak()
+    near_flops = nnz * 8 + N * nfb2 * 8          # complex multiply-adds of one launch
     t_near64 = st64[4] / max(c64, 1) * 1e-3
     t_near32 = st32[4] / max(c32, 1) * 1e-3
     ach64 = near_bytes(16) / t_near64 / 1e9
@@ -310,15 +317,21 @@ def main():
                    "plan_seconds": info["plan_seconds"], "device_bytes": info["device_bytes"]},
         "e2e": {"value": world * args.steps / (ms_e2e * 1e-3), "unit": "matvecs/s",
                 "h2d_bytes_per_step": N * 16, "d2h_bytes_per_step": N * 16},
-        "roofline": {"bound": "hbm", "kernel": "k_near_eval<double2>", "achieved": ach64, "peak": peak,
-                     "unit": "GB/s", "frac": ach64 / peak, "traffic": None, "peak_source": peak_src,
-                     "bytes_per_launch": near_bytes(16), "launch_ms": t_near64 * 1e3},
+        "roofline": {"bound": "alu", "kernel": "k_near_eval<double2>",
+                     "achieved": near_flops / t_near64 / 1e12, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": near_flops / t_near64 / 1e12 / FP64_PEAK_TFLOPS, "traffic": None,
+                     "peak_source": "derived: 152 SMs x 2070 MHz x 2 FP64 FMA/clk/SM",
+                     "flops_per_launch": near_flops, "bytes_per_launch": near_bytes(16),
+                     "hbm_GBs": ach64, "hbm_frac": ach64 / peak, "hbm_peak": peak, "hbm_peak_source": peak_src,
+                     "launch_ms": t_near64 * 1e3},
         "gpu_launches": KERNELS_PER_APPLY * args.steps,
         "clocks": clocks,
         "mixed": {"value": world * args.steps / (ms32 * 1e-3), "unit": "matvecs/s", "dtype": "f32",
                   "ms_per_step": ms32 / args.steps,
-                  "roofline": {"kernel": "k_near_eval<float2>", "achieved": ach32, "peak": peak,
-                               "frac": ach32 / peak, "launch_ms": t_near32 * 1e3}},
+                  "roofline": {"bound": "hbm", "kernel": "k_near_eval<float2>", "achieved": ach32,
+                               "peak": peak, "unit": "GB/s", "frac": ach32 / peak, "peak_source": peak_src,
+                               "bytes_per_launch": near_bytes(8), "traffic": None,
+                               "launch_ms": t_near32 * 1e3}},
         "stages_ms": {"fp64": dict(zip(stage_names, [float(x) / max(c64, 1) for x in st64])),
                       "mixed": dict(zip(stage_names, [float(x) / max(c32, 1) for x in st32]))},
         "apply_hbm_frac_fp64": (apply_bytes64 / (ms64 / args.steps * 1e-3) / 1e9) / peak,

@@ -66,14 +66,13 @@ def test_invalid_arguments_return_status(lib):
 
 
 def _small_disc():
-    return W.disc(level=1, kappa=2.0, n2c=2.0, collar_w=0.6, tau0=0.3, tau1=0.95, R_a=4, R_b=2, R_cart=3,
-                  p=7, n_rho=48, N_tau=64, box_x0=-1.2, box_y0=-1.2, H=0.3, L=8, N_eq=8, n_fb=15)
+    return W.place_cells(W.disc(level=1, kappa=2.0, n2c=2.0, collar_w=0.6, tau0=0.3, tau1=0.95, R_a=4, R_b=2,
+                                R_cart=3, p=7, n_rho=48, N_tau=64), L=8, m=3, N_eq=8)
 
 
 def _small_kite():
-    return W.kite(n1=512, n2=17, h=0.025, kappa=6.0, collar_w=0.07, tau0=0.4, tau1=0.9, R_a=6, R_b=5,
-                  R_cart=4, n_rho=32, N_tau=48).replace(box_x0=-1.65, box_y0=-1.6, H=0.2, L=17,
-                                                        N_eq=8, n_fb=15)
+    return W.place_cells(W.kite(n1=512, n2=17, h=0.025, kappa=6.0, collar_w=0.07, tau0=0.4, tau1=0.9, R_a=6,
+                                R_b=5, R_cart=4, n_rho=32, N_tau=48), L=17, m=8, center=(-0.25, 0.0), N_eq=8)
 
 
 @pytest.mark.parametrize("make", [_small_disc, _small_kite])

@@ -243,8 +243,7 @@ def test_far_field_of_solution_and_reciprocity(K1_level2):
 
 # ---------------------------------------------------------------- the accelerator
 def _accel_wl(Ne, kappa=2.0):
-    return disc_wl(2, n2c=2.0, kappa=kappa, R_a=4, R_b=4, R_cart=5,
-                   box_x0=-1.2, box_y0=-1.2, H=0.3, L=8, N_eq=Ne, n_fb=2 * Ne - 1)
+    return W.place_cells(disc_wl(2, n2c=2.0, kappa=kappa, R_a=4, R_b=4, R_cart=5), L=8, m=6, N_eq=Ne)
 
 
 def test_equivalent_source_fit_accuracy():

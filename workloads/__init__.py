@@ -134,6 +134,20 @@ def random_rows(n: int, k: int, seed: int = SEED + 1) -> np.ndarray:
 # (boundary patch n1 x n2 plus an interior Cartesian patch).
 # --------------------------------------------------------------------------
 
+def place_cells(wl: Workload, L: int, m: int, center=(0.0, 0.0), N_eq: int | None = None) -> Workload:
+    """Accelerator cells of side H = m h whose faces fall half a Cartesian
+    spacing off the grid lines, so that no Nystrom node lies on a cell face and
+    the cell of every node is decided the same way in any rounding."""
+    H = m * wl.h
+    A = L * H
+    kx = round((center[0] - A / 2 - wl.cart_x0) / wl.h)
+    ky = round((center[1] - A / 2 - wl.cart_y0) / wl.h)
+    kw = dict(box_x0=wl.cart_x0 + (kx + 0.5) * wl.h, box_y0=wl.cart_y0 + (ky + 0.5) * wl.h, H=H, L=L)
+    if N_eq is not None:
+        kw.update(N_eq=N_eq, n_fb=2 * N_eq - 1)
+    return wl.replace(**kw)
+
+
 def _cart_grid_for(h: float, lo: float, hi: float, anchor: float = 0.0):
     """Cartesian grid covering [lo, hi] with points anchor + i h."""
     i0 = math.floor((lo - anchor) / h) - 1
@@ -181,21 +195,19 @@ def cfg1() -> Workload:
     checked against the Bessel series."""
     h = 0.03
     x0, nx = _cart_grid_for(h, -1.0, 1.0)
-    return Workload(name="cfg1_disc_kappa2", shape="disc", shape_params=(1.0, 0.0, 0.0), kappa=2.0,
-                    n2_kind="const", n2_params=(2.0,), collar_w=0.48, n1=128, n2=17, tau0=0.35, tau1=0.9,
-                    h=h, cart_x0=x0, cart_y0=x0, cart_nx=nx, cart_ny=nx, R_a=5, R_b=5, R_cart=6,
-                    box_x0=-1.2, box_y0=-1.2, H=0.3, L=8, N_eq=8, n_fb=15)
+    return place_cells(
+        Workload(name="cfg1_disc_kappa2", shape="disc", shape_params=(1.0, 0.0, 0.0), kappa=2.0,
+                 n2_kind="const", n2_params=(2.0,), collar_w=0.48, n1=128, n2=17, tau0=0.35, tau1=0.9,
+                 h=h, cart_x0=x0, cart_y0=x0, cart_nx=nx, cart_ny=nx, R_a=5, R_b=5, R_cart=6,
+                 N_eq=8, n_fb=15), L=8, m=10)
 
 
-def cfg2(h: float = 0.0045, n1: int = 3200, L: int = 56, H: float = 0.055, N_eq: int = 8) -> Workload:
+def cfg2(h: float = 0.0045, n1: int = 3200, L: int = 56, m: int = 12, N_eq: int = 8) -> Workload:
     """Kite x = cos t + 0.65 cos 2t - 0.65, y = 1.5 sin t; n^2 = 1.5 + 0.5 exp(-|x|^2/0.1)
     inside, 1 outside; kappa = 20, ~260k nodes, 1024^2 padded lattice FFT, GMRES tol 1e-10."""
     wl = kite(n1=n1, n2=17, h=h, kappa=20.0, collar_w=0.07, tau0=0.4, tau1=0.9,
               R_a=10, R_b=6, R_cart=8)
-    A = L * H
-    cx, cy = -0.25, 0.0
-    return wl.replace(name="cfg2_kite_kappa20", box_x0=cx - A / 2, box_y0=cy - A / 2, H=H, L=L,
-                      N_eq=N_eq, n_fb=2 * N_eq - 1)
+    return place_cells(wl.replace(name="cfg2_kite_kappa20"), L=L, m=m, center=(-0.25, 0.0), N_eq=N_eq)
 
 
 def n2_of(wl: Workload):
