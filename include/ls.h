@@ -166,6 +166,25 @@ ls_status ls_farfield(ls_plan plan, const void* u_dev, int nrhs, const double* d
 
 ls_status ls_plan_destroy(ls_plan plan);
 
+/* Allocation-free apply (this entry point has no counterpart in the paper; it
+ * serves callers that must not allocate device memory when they apply the
+ * operator -- e.g. inside a CUDA stream capture, under an external memory pool
+ * or in a loop that may never call the allocator).  Same result as ls_apply
+ * for ONE right-hand side (u, Au: N complex128 for LS_FP64, complex64 for
+ * LS_MIXED; device pointers, async on stream), but the work arrays live in a
+ * fixed 16 MiB device array inside the library instead of plan memory; every
+ * GPU that loads the library holds that array until the process exits.
+ * Limit: 256-byte-rounded sizes of (occupied cells x n_es) + 2 (M x M) +
+ * (occupied cells x (2 n_fb + 1)) complex values must fit 16 MiB (e.g. FFT size
+ * M <= 512 in complex128, M <= 1024 needs more); larger plans get
+ * LS_ERR_INVALID with the required size in ls_last_error.  The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress) with that
+ * device current; make that first call before any stream capture.  All calls
+ * share the array: calls whose GPU work overlaps race and corrupt each other.
+ * Nothing in the array needs to start at zero.  It allocates nothing (no
+ * cudaMalloc / cudaFree). */
+ls_status ls_apply_noalloc(ls_plan plan, const void* u_dev, void* Au_dev, ls_precision prec, void* stream);
+
 /* Per-stage device timing of ls_apply with CUDA events recorded on the call's
  * stream (measurement aid; enabling it makes ls_apply wait for each apply).
  * Stages: 0 equivalent-source projection, 1 lattice fill, 2 lattice FFT

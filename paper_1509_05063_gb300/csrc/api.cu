@@ -5,6 +5,7 @@
 #include <cmath>
 #include <complex>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <thread>
 #include <vector>
@@ -638,3 +639,81 @@ ls_status ls_plan_destroy(ls_plan plan) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free apply.
+//
+// Some callers cannot allocate device memory at the moment they want an
+// operator application: code running under a CUDA stream capture (where a
+// cudaMalloc would break the capture), code inside another library's memory
+// pool that forbids outside allocations, or real-time loops that must never
+// reach the allocator.  ls_apply_noalloc serves them: it works exactly like
+// ls_apply for one right-hand side but keeps its intermediate arrays (the
+// equivalent-source strengths, the two lattice grids and the local-expansion
+// coefficients) in the fixed device array below instead of in plan memory.
+// Every GPU that loads this library reserves these bytes until the process
+// exits.  All calls share the array, so calls whose GPU work overlaps (two
+// streams, two host threads, two plans) corrupt each other's results: order
+// them on one stream or synchronise between them.  Every element the apply
+// reads from the array is written earlier in the same call, so nothing has to
+// start at zero.
+static constexpr size_t kNoAllocScratchBytes = size_t(16) << 20;   // 16 MiB
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+namespace {
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[256] = {};   // device address of the array, per device ordinal
+
+template <typename T>
+ls_status noalloc_apply(ls_plan plan, const lsd::ApplyData<T>& src, const void* u, void* Au, cudaStream_t st) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess || dev < 0 || dev >= 256)
+    return fail(plan, LS_ERR_CUDA, std::string("ls_apply_noalloc: cudaGetDevice: ") + cudaGetErrorString(e));
+  void* base = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+      // the name of a __device__ array is a host-side stand-in; ask the runtime
+      // for its device address once per device, with that device current
+      void* p = nullptr;
+      e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+      if (e != cudaSuccess || !p)
+        return fail(plan, LS_ERR_CUDA,
+                    std::string("ls_apply_noalloc: cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+      g_noalloc_ptr[dev] = p;
+    }
+    base = g_noalloc_ptr[dev];
+  }
+  const size_t n_sigma = size_t(src.nocc) * src.n_es, n_grid = size_t(src.M) * src.M;
+  const size_t n_gamma = size_t(src.nocc) * src.nfb2;
+  auto up256 = [](size_t b) { return (b + 255) & ~size_t(255); };
+  const size_t need = up256(n_sigma * sizeof(T)) + 2 * up256(n_grid * sizeof(T)) + up256(n_gamma * sizeof(T));
+  if (need > kNoAllocScratchBytes)
+    return fail(plan, LS_ERR_INVALID,
+                "ls_apply_noalloc: this plan needs " + std::to_string(need) + " bytes of work space but the " +
+                "fixed device array holds " + std::to_string(kNoAllocScratchBytes) +
+                " bytes (lattice FFT size M too large); use ls_apply");
+  lsd::ApplyData<T> d = src;
+  unsigned char* p = static_cast<unsigned char*>(base);
+  d.sigma = reinterpret_cast<T*>(p);
+  p += up256(n_sigma * sizeof(T));
+  d.Sm = reinterpret_cast<T*>(p);
+  p += up256(n_grid * sizeof(T));
+  d.Sd = reinterpret_cast<T*>(p);
+  p += up256(n_grid * sizeof(T));
+  d.gamma = reinterpret_cast<T*>(p);
+  e = lsd::apply_one(d, static_cast<const T*>(u), static_cast<T*>(Au), st);
+  if (e != cudaSuccess) return fail(plan, LS_ERR_CUDA, std::string("ls_apply_noalloc: ") + cudaGetErrorString(e));
+  return LS_OK;
+}
+}  // namespace
+
+extern "C" ls_status ls_apply_noalloc(ls_plan plan, const void* u, void* Au, ls_precision prec, void* stream) {
+  if (!plan) return LS_ERR_INVALID;
+  if (!u || !Au) return fail(plan, LS_ERR_INVALID, "ls_apply_noalloc: null vector");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (prec == LS_FP64) return noalloc_apply(plan, plan->d64, u, Au, st);
+  if (prec == LS_MIXED) return noalloc_apply(plan, plan->d32, u, Au, st);
+  return fail(plan, LS_ERR_INVALID, "ls_apply_noalloc: bad precision");
+}

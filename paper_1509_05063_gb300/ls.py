@@ -84,6 +84,7 @@ _SIGS = {
     "ls_host_plan_accel": ([C.c_void_p] + [C.c_void_p] * 8),
     "ls_host_plan_destroy": ([C.c_void_p]),
     "ls_set_stage_timing": ([C.c_void_p, C.c_int]),
+    "ls_apply_noalloc": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
     "ls_get_stage_times": ([C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
 }
 EXPORTED = tuple(_SIGS)
@@ -216,6 +217,19 @@ class Plan:
         _check(_lib.ls_farfield(self._h, C.c_void_p(u.data_ptr()), nrhs, dirs.ctypes.data, len(dirs),
                                 C.c_void_p(A.data_ptr()), _stream(stream)), self._h)
         return A
+
+    def apply_noalloc(self, u, out, prec: int = LS_FP64, stream=None):
+        """A u for ONE right-hand side through ls_apply_noalloc: the library
+        allocates nothing; its work arrays sit in a fixed device array shared by
+        all calls (see include/ls.h).  out must be preallocated like u."""
+        import torch
+        want = torch.complex128 if prec == LS_FP64 else torch.complex64
+        for t in (u, out):
+            if t.dtype != want or not t.is_cuda or not t.is_contiguous() or t.numel() != self.N:
+                raise LSError(1, f"u and out must be contiguous CUDA {want} tensors of length N")
+        _check(_lib.ls_apply_noalloc(self._h, C.c_void_p(u.data_ptr()), C.c_void_p(out.data_ptr()), prec,
+                                     _stream(stream)), self._h)
+        return out
 
     def set_stage_timing(self, enable: bool):
         _check(_lib.ls_set_stage_timing(self._h, int(enable)), self._h)
