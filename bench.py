@@ -285,8 +285,9 @@ def main():
     nfb2 = 2 * info["n_fb"] + 1
     nocc = info["n_cells_occupied"]
 
-    def near_bytes(cb):   # algorithmic bytes of one k_near_eval launch, cb = bytes per complex
-        return nnz * (cb + 4) + (N + 1) * 8 + N * cb + N * nfb2 * cb + N * 4 + nocc * nfb2 * cb + N * cb
+    def near_bytes(cb):   # algorithmic bytes of one k_near_eval launch, cb = bytes per complex:
+        # dense per-cell weight blocks (+ the tiny CSR remainder, counted as blocks), u, Phi, gamma, out
+        return nnz * cb + N * cb + N * nfb2 * cb + N * 12 + nocc * nfb2 * cb + N * cb
 
     peak, peak_src = hbm_peak()
     near_flops = nnz * 8 + N * nfb2 * 8          # complex multiply-adds of one launch
@@ -295,8 +296,12 @@ def main():
     ach64 = near_bytes(16) / t_near64 / 1e9
     ach32 = near_bytes(8) / t_near32 / 1e9
     M = info["fft_M"]
-    apply_bytes64 = (2 * N * 16 + nnz * 20 + 6 * M * M * 16 + 2 * M * M * 16)
-    stage_names = ["es_project", "lattice_fill", "lattice_fft_conv", "local_coeffs", "near_eval"]
+    n_lat = info["L"] * info["N_eq"] + 1
+    # whole-apply byte model: u in, out, weights, projections, Phi, lattice passes, quarter spectra
+    lat_bytes = lambda cb: (2 * (info["L"] + 1) * M * cb * 2 + 2 * (M // 2 + 1) ** 2 * cb
+                            + 2 * n_lat * M * cb * 2)
+    apply_bytes64 = near_bytes(16) + N * 16 * 4 + lat_bytes(16)
+    stage_names = ["es_project", "lattice_fill(fused)", "lattice_fft_conv", "local_coeffs", "near_eval"]
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -174,10 +174,10 @@ ls_status ls_plan_destroy(ls_plan plan);
  * LS_MIXED; device pointers, async on stream), but the work arrays live in a
  * fixed 16 MiB device array inside the library instead of plan memory; every
  * GPU that loads the library holds that array until the process exits.
- * Limit: 256-byte-rounded sizes of (occupied cells x n_es) + 2 (M x M) +
- * (occupied cells x (2 n_fb + 1)) complex values must fit 16 MiB (e.g. FFT size
- * M <= 512 in complex128, M <= 1024 needs more); larger plans get
- * LS_ERR_INVALID with the required size in ls_last_error.  The first call on a
+ * Limit: 256-byte-rounded sizes of (occupied cells x n_es) + 2 (R x M) +
+ * (occupied cells x (2 n_fb + 1)) complex values, R = max(2 (L + 1), L N_eq + 1),
+ * must fit 16 MiB (e.g. every plan with FFT size M <= 1024; M = 2048 does not
+ * fit); larger plans get LS_ERR_INVALID with the required size in ls_last_error.  The first call on a
  * device looks up the array's device address (cudaGetSymbolAddress) with that
  * device current; make that first call before any stream capture.  All calls
  * share the array: calls whose GPU work overlaps race and corrupt each other.

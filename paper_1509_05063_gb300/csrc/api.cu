@@ -266,14 +266,68 @@ ls_status ls_plan_create(const ls_geometry* geom, ls_n2_fn n2, void* ctx, double
   }
   occ_start[nocc] = N;
   for (int64_t q = 0; q < N; ++q) occ_of_node[q] = occ_of_cell[nd.cell[q]];
-  std::vector<int> col32(P.col.begin(), P.col.end());
+  // near field: CSR -> one dense block per occupied cell + CSR remainder.
+  // Each of the three column ranges of a row is stored padded to an even
+  // length (zeros), so every range starts 16-byte aligned in complex64.
+  const int Lc = P.opt.L;
+  std::vector<int64_t> blk_off(nocc + 1, 0);
+  std::vector<int> blk_seg(size_t(6) * nocc, 0);
+  auto padded = [](int len) { return (len + 1) & ~1; };
+  int max_nblk = 0;
+  for (int k = 0; k < nocc; ++k) {
+    const int c = P.occ_cells[k], ci = c % Lc, cj = c / Lc;
+    int nblk = 0;
+    for (int s = 0; s < 3; ++s) {
+      const int nj = cj + s - 1;
+      if (nj < 0 || nj >= Lc) continue;
+      const int lo = nj * Lc + std::max(ci - 1, 0), hi = nj * Lc + std::min(ci + 1, Lc - 1);
+      blk_seg[6 * k + 2 * s] = int(nd.cell_start[lo]);
+      blk_seg[6 * k + 2 * s + 1] = int(nd.cell_start[hi + 1] - nd.cell_start[lo]);
+      nblk += padded(blk_seg[6 * k + 2 * s + 1]);
+    }
+    max_nblk = std::max(max_nblk, nblk);
+    blk_off[k + 1] = blk_off[k] + (nd.cell_start[c + 1] - nd.cell_start[c]) * int64_t(nblk);
+  }
+  if (size_t(max_nblk + P.nfb2) * sizeof(double2) > 200 * 1024)
+    return bail(LS_ERR_INVALID, "a cell's 3 x 3 neighbourhood holds too many nodes (" + std::to_string(max_nblk) +
+                "); use smaller cells");
+  std::vector<cd> Wb(blk_off[nocc], cd(0.0));
+  std::vector<int64_t> rem_row(N + 1, 0);
+  std::vector<int> rem_col;
+  std::vector<cd> rem_val;
+  for (int64_t q = 0; q < N; ++q) {
+    const int k = occ_of_node[q];
+    const int* sg = &blk_seg[6 * k];
+    const int nblk = padded(sg[1]) + padded(sg[3]) + padded(sg[5]);
+    cd* row = &Wb[blk_off[k] + (q - occ_start[k]) * nblk];
+    for (int64_t e = P.rowptr[q]; e < P.rowptr[q + 1]; ++e) {
+      const int col = P.col[e];
+      int pos = -1, base = 0;
+      for (int s = 0; s < 3; ++s) {
+        if (col >= sg[2 * s] && col < sg[2 * s] + sg[2 * s + 1]) { pos = base + col - sg[2 * s]; break; }
+        base += padded(sg[2 * s + 1]);
+      }
+      if (pos >= 0) row[pos] += P.val[e];
+      else { rem_col.push_back(col); rem_val.push_back(P.val[e]); }
+    }
+    rem_row[q + 1] = int64_t(rem_col.size());
+  }
+  std::vector<int32_t>().swap(P.col);
+  std::vector<cd>().swap(P.val);
   const int64_t* d_occ_start = UP(int64_t, occ_start);
   const int* d_occ_cells = UP(int, P.occ_cells);
   const int* d_occ_of_cell = UP(int, occ_of_cell);
   const int* d_occ_of_node = UP(int, occ_of_node);
   const int64_t* d_P_off = UP(int64_t, P.P_off);
-  const int64_t* d_rowptr = UP(int64_t, P.rowptr);
-  const int* d_col = UP(int, col32);
+  std::vector<int> items;   // (occupied cell, first row) pairs, 32 rows each
+  for (int k = 0; k < nocc; ++k)
+    for (int64_t r = 0; r < occ_start[k + 1] - occ_start[k]; r += 32) { items.push_back(k); items.push_back(int(r)); }
+  const int* d_items_raw = UP(int, items);
+  const int2* d_items = reinterpret_cast<const int2*>(d_items_raw);
+  const int64_t* d_blk_off = UP(int64_t, blk_off);
+  const int* d_blk_seg = UP(int, blk_seg);
+  const int64_t* d_rem_row = UP(int64_t, rem_row);
+  const int* d_rem_col = UP(int, rem_col);
   plan->x = UP(double, nd.x);
   plan->y = UP(double, nd.y);
   plan->ffw = UP(double, P.ffw);
@@ -288,36 +342,54 @@ ls_status ls_plan_create(const ls_geometry* geom, ls_n2_fn n2, void* ctx, double
   for (auto& z : G) z *= sc;
   for (auto& z : D) z *= sc;
   double2* d_tw64 = UP(double2, tw);
-  double2* d_G64 = UP(double2, G);
-  double2* d_D64 = UP(double2, D);
+  // spectra: full FFT of the tables on the device, then keep the quarter
+  // [l][k], k, l in [0, M/2] (even / odd symmetry of the tables)
+  const int64_t MM = int64_t(M) * M;
+  const int hq = M / 2 + 1;
+  std::vector<cd> Gq(size_t(hq) * hq), Dq(size_t(hq) * hq);
   {
-    cudaError_t e = lsd::fft2d<double2>(d_G64, M, logM, d_tw64, false, 0);
-    if (e == cudaSuccess) e = lsd::fft2d<double2>(d_D64, M, logM, d_tw64, false, 0);
-    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    double2* tmp = nullptr;
+    cudaError_t e = cudaMalloc(&tmp, MM * sizeof(double2));
+    if (e != cudaSuccess) return bail(LS_ERR_NOMEM, "spectra work space");
+    std::vector<cd> full(MM);
+    for (int which = 0; which < 2 && e == cudaSuccess; ++which) {
+      const std::vector<cd>& tab = which == 0 ? G : D;
+      e = cudaMemcpy(tmp, tab.data(), MM * sizeof(double2), cudaMemcpyHostToDevice);
+      if (e == cudaSuccess) e = lsd::fft2d<double2>(tmp, M, logM, d_tw64, false, 0);
+      if (e == cudaSuccess) e = cudaMemcpy(full.data(), tmp, MM * sizeof(double2), cudaMemcpyDeviceToHost);
+      std::vector<cd>& q = which == 0 ? Gq : Dq;
+      for (int l = 0; l < hq; ++l)
+        for (int k = 0; k < hq; ++k) q[size_t(l) * hq + k] = full[size_t(k) * M + l];
+    }
+    cudaFree(tmp);
     if (e != cudaSuccess) return bail(LS_ERR_CUDA, std::string("spectra: ") + cudaGetErrorString(e));
   }
-  const int64_t MM = int64_t(M) * M;
-  float2* d_G32 = plan->alloc<float2>(MM, &st);
-  float2* d_D32 = plan->alloc<float2>(MM, &st);
-  if (st != LS_OK) return bail(st, plan->err);
-  if (lsd::to_c64(d_G64, d_G32, MM, 0) != cudaSuccess || lsd::to_c64(d_D64, d_D32, MM, 0) != cudaSuccess)
-    return bail(LS_ERR_CUDA, "spectra conversion failed");
+  std::vector<cd>().swap(G);
+  std::vector<cd>().swap(D);
+  const double2* d_G64 = UP(double2, Gq);
+  const double2* d_D64 = UP(double2, Dq);
+  const float2* d_G32 = UP(float2, to32(Gq));
+  const float2* d_D32 = UP(float2, to32(Dq));
   // FP64 apply data
   auto& a = plan->d64;
   a.N = N; a.nocc = nocc; a.L = P.opt.L; a.Ne = P.Ne; a.n_es = P.n_es; a.n_loc = P.n_loc; a.nfb2 = P.nfb2;
   a.M = M; a.n_lat = P.n_lat; a.logM = logM;
   a.occ_start = d_occ_start; a.occ_cells = d_occ_cells; a.occ_of_cell = d_occ_of_cell;
-  a.occ_of_node = d_occ_of_node; a.P_off = d_P_off; a.rowptr = d_rowptr; a.col = d_col;
+  a.occ_of_node = d_occ_of_node; a.P_off = d_P_off;
+  a.blk_off = d_blk_off; a.blk_seg = d_blk_seg; a.rem_row = d_rem_row; a.rem_col = d_rem_col;
+  a.max_nblk = max_nblk;
+  a.items = d_items; a.n_items = int(items.size() / 2);
   a.P = UP(double2, P.P64);
   a.Bp = UP(double2, P.Bpinv);
   a.BT = UP(double2, P.BT);
   a.Phi = UP(double2, P.Phi);
-  a.val = UP(double2, P.val);
-  a.Ghat = d_G64; a.Dhat = d_D64; a.tw = d_tw64;
+  a.Wb = UP(double2, Wb);
+  a.rem_val = UP(double2, rem_val);
+  a.Gq = d_G64; a.Dq = d_D64; a.tw = d_tw64;
   a.kappa2 = kappa * kappa;
   a.sigma = plan->alloc<double2>(size_t(nocc) * P.n_es, &st);
-  a.Sm = plan->alloc<double2>(MM, &st);
-  a.Sd = plan->alloc<double2>(MM, &st);
+  a.Sm = plan->alloc<double2>(a.lattice_rows() * M, &st);
+  a.Sd = plan->alloc<double2>(a.lattice_rows() * M, &st);
   a.gamma = plan->alloc<double2>(size_t(nocc) * P.nfb2, &st);
   if (st != LS_OK) return bail(st, plan->err);
   // complex64 apply data
@@ -325,31 +397,37 @@ ls_status ls_plan_create(const ls_geometry* geom, ls_n2_fn n2, void* ctx, double
   b.N = a.N; b.nocc = a.nocc; b.L = a.L; b.Ne = a.Ne; b.n_es = a.n_es; b.n_loc = a.n_loc; b.nfb2 = a.nfb2;
   b.M = a.M; b.n_lat = a.n_lat; b.logM = a.logM;
   b.occ_start = a.occ_start; b.occ_cells = a.occ_cells; b.occ_of_cell = a.occ_of_cell;
-  b.occ_of_node = a.occ_of_node; b.P_off = a.P_off; b.rowptr = a.rowptr; b.col = a.col;
+  b.occ_of_node = a.occ_of_node; b.P_off = a.P_off;
+  b.blk_off = a.blk_off; b.blk_seg = a.blk_seg; b.rem_row = a.rem_row; b.rem_col = a.rem_col;
+  b.max_nblk = a.max_nblk;
+  b.items = a.items; b.n_items = a.n_items;
   b.P = UP(float2, to32(P.P32));
   b.Bp = UP(float2, to32(P.Bpinv));
   b.BT = UP(float2, to32(P.BT));
   b.Phi = UP(float2, to32(P.Phi));
-  b.val = UP(float2, to32(P.val));
-  b.Ghat = d_G32; b.Dhat = d_D32;
+  {
+    std::vector<std::complex<float>> w32 = to32(Wb);
+    std::vector<cd>().swap(Wb);
+    b.Wb = UP(float2, w32);
+  }
+  b.rem_val = UP(float2, to32(rem_val));
+  b.Gq = d_G32; b.Dq = d_D32;
   b.tw = UP(float2, to32(tw));
   b.kappa2 = a.kappa2;
   b.sigma = plan->alloc<float2>(size_t(nocc) * P.n_es, &st);
-  b.Sm = plan->alloc<float2>(MM, &st);
-  b.Sd = plan->alloc<float2>(MM, &st);
+  b.Sm = plan->alloc<float2>(b.lattice_rows() * M, &st);
+  b.Sd = plan->alloc<float2>(b.lattice_rows() * M, &st);
   b.gamma = plan->alloc<float2>(size_t(nocc) * P.nfb2, &st);
   if (st != LS_OK) return bail(st, plan->err);
 #undef UP
   if (cudaDeviceSynchronize() != cudaSuccess) return bail(LS_ERR_CUDA, "upload failed");
   // info, then release the large host arrays
   ls_plan_info_t& inf = plan->info;
-  inf.N = N; inf.n_collar = nd.n_collar; inf.n_cart = nd.n_cart; inf.nnz_near = P.rowptr[N];
+  inf.N = N; inf.n_collar = nd.n_collar; inf.n_cart = nd.n_cart; inf.nnz_near = blk_off[nocc] + rem_row[N];
   inf.L = P.opt.L; inf.N_eq = P.Ne; inf.n_es = P.n_es; inf.n_loc = P.n_loc; inf.n_fb = P.opt.n_fb;
   inf.fft_M = M; inf.n_cells_occupied = nocc;
   inf.plan_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   inf.device_bytes = plan->device_bytes;
-  std::vector<int32_t>().swap(P.col);
-  std::vector<cd>().swap(P.val);
   std::vector<cd>().swap(P.P64);
   std::vector<cd>().swap(P.P32);
   std::vector<cd>().swap(P.Phi);
@@ -447,16 +525,20 @@ ls_status gmres_fp64(ls_plan plan, Op op, const double2* b, double2* x, double t
     int k_used = 0;
     for (int k = 0; k < m; ++k) {
       LS_CU(op(V + int64_t(k) * N, w));
-      // classical Gram-Schmidt, two passes
+      // classical Gram-Schmidt with selective re-orthogonalisation: a second
+      // pass only when the first removed more than 1 - 1/sqrt(2) of ||w||
+      double hk1 = 0;
       for (int pass = 0; pass < 2; ++pass) {
         LS_CU(lsd::gram(V, k + 1, w, N, plan->partial, plan->h, st));
         LS_CU(lsd::axpy_multi(V, k + 1, plan->h, w, N, st));
-        LS_CU(cudaMemcpyAsync(hcol.data(), plan->h, (k + 1) * sizeof(double2), cudaMemcpyDeviceToHost, st));
+        LS_CU(lsd::norm2(w, N, plan->dpartial, plan->dnorm, st));
+        LS_CU(cudaMemcpyAsync(hcol.data(), plan->h, (k + 2) * sizeof(double2), cudaMemcpyDeviceToHost, st));
+        LS_CU(cudaMemcpyAsync(&hk1, plan->dnorm, sizeof(double), cudaMemcpyDeviceToHost, st));
         LS_CU(cudaStreamSynchronize(st));
         for (int j = 0; j <= k; ++j) H[size_t(j) * m + k] += hcol[j];
+        const double before = std::sqrt(std::max(hcol[k + 1].real(), 0.0));
+        if (hk1 >= 0.7071067811865476 * before) break;
       }
-      double hk1 = 0;
-      LS_CU(dnorm(w, &hk1));
       H[size_t(k + 1) * m + k] = hk1;
       LS_CU(lsd::scale_into(w, plan->dnorm, V + int64_t(k + 1) * N, N, st));
       for (int j = 0; j < k; ++j) {
@@ -498,8 +580,8 @@ ls_status ensure_workspace(ls_plan plan, int restart) {
   plan->r = plan->alloc<double2>(N, &st);
   plan->e = plan->alloc<double2>(N, &st);
   plan->cor = plan->alloc<double2>(N, &st);
-  plan->h = plan->alloc<double2>(restart + 2, &st);
-  plan->partial = plan->alloc<double2>(size_t(lsd::gram_blocks(N)) * (restart + 2), &st);
+  plan->h = plan->alloc<double2>(restart + 3, &st);
+  plan->partial = plan->alloc<double2>(size_t(lsd::gram_blocks(N)) * (restart + 3), &st);
   plan->dnorm = plan->alloc<double>(1, &st);
   plan->dpartial = plan->alloc<double>(lsd::gram_blocks(N), &st);
   plan->c64a = plan->alloc<float2>(N, &st);
@@ -685,7 +767,7 @@ ls_status noalloc_apply(ls_plan plan, const lsd::ApplyData<T>& src, const void* 
     }
     base = g_noalloc_ptr[dev];
   }
-  const size_t n_sigma = size_t(src.nocc) * src.n_es, n_grid = size_t(src.M) * src.M;
+  const size_t n_sigma = size_t(src.nocc) * src.n_es, n_grid = size_t(src.lattice_rows()) * src.M;
   const size_t n_gamma = size_t(src.nocc) * src.nfb2;
   auto up256 = [](size_t b) { return (b + 255) & ~size_t(255); };
   const size_t need = up256(n_sigma * sizeof(T)) + 2 * up256(n_grid * sizeof(T)) + up256(n_gamma * sizeof(T));

@@ -195,6 +195,133 @@ cudaError_t fft2d(T* x, int M, int logM, const T* tw, bool inverse, cudaStream_t
   return cudaGetLastError();
 }
 
+// ------------------------------------------------------------ pruned, fused lattice convolution
+// Sources live only on the L + 1 face rows a = k Ne (k = 0..L) of the M x M
+// padded lattice, and only the n_lat x n_lat corner of the result is read.
+//  k_src_rows  : gather sigma of face row k (monopole or dipole) into shared
+//                memory and FFT it along b              -> R[k][b], (L+1) x M x 2
+//  k_conv_cols : per column b, scatter the L + 1 rows to a, FFT along a (both
+//                source kinds), multiply by the kernel spectra (stored as a
+//                quarter using the even / odd symmetry of the tables), inverse
+//                FFT along a, keep a < n_lat            -> Vt[a][b], n_lat x M
+//  k_inv_rows  : inverse FFT along b of rows a < n_lat, keep b < n_lat -> V
+template <typename T>
+__global__ void __launch_bounds__(kFftMaxM / 8) k_src_rows(int M, int logM, int n_lat, int Ne, int L,
+                                                           const int* __restrict__ occ_of_cell,
+                                                           const T* __restrict__ sigma, int n_es,
+                                                           const T* __restrict__ tw, T* __restrict__ R) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* s = reinterpret_cast<T*>(smem_raw);
+  const int k = blockIdx.x, kind = blockIdx.y;   // face row, 0 monopole / 1 dipole
+  for (int b = threadIdx.x; b < M; b += blockDim.x) {
+    T v = czero(T{});
+    if (b < n_lat) {
+      for (int side = 0; side < 2; ++side) {        // left face of cell k, right face of cell k - 1
+        const int ci = k - side;
+        if (ci < 0 || ci >= L) continue;
+        const int cjb = b / Ne, kb = b % Ne;
+        for (int t = 0; t < 2; ++t) {
+          if (t == 1 && kb != 0) break;
+          const int cj = cjb - t, kk = kb + t * Ne;
+          if (cj < 0 || cj >= L) continue;
+          const int occ = occ_of_cell[cj * L + ci];
+          if (occ >= 0) v = cadd(v, sigma[int64_t(occ) * n_es + (2 * kind + side) * (Ne + 1) + kk]);
+        }
+      }
+    }
+    s[b] = v;
+  }
+  __syncthreads();
+  fft_smem<T>(s, M, logM, false, tw, threadIdx.x);
+  T* out = R + (int64_t(kind) * (L + 1) + k) * M;
+  for (int b = threadIdx.x; b < M; b += blockDim.x) out[b] = s[b];
+}
+
+// spectra quarter layout: Q[l][k] for l, k in [0, M/2] (k fastest)
+template <typename T>
+__global__ void __launch_bounds__(1024) k_conv_cols(int M, int logM, int n_lat, int Ne, int L, int TC,
+                                                    const T* __restrict__ R, const T* __restrict__ Gq,
+                                                    const T* __restrict__ Dq, const T* __restrict__ tw,
+                                                    T* __restrict__ Vt) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* xm = reinterpret_cast<T*>(smem_raw);      // [TC][M]
+  T* xd = xm + TC * M;                         // [TC][M]
+  const int b0 = blockIdx.x * TC;
+  const int half = M / 2;
+  for (int e = threadIdx.x; e < TC * M; e += blockDim.x) {
+    const int c = e / M, a = e % M;
+    T vm = czero(T{}), vd = czero(T{});
+    if (a % Ne == 0 && a / Ne <= L) {
+      const int k = a / Ne;
+      vm = R[int64_t(k) * M + b0 + c];
+      vd = R[(int64_t(L + 1) + k) * M + b0 + c];
+    }
+    xm[e] = vm;
+    xd[e] = vd;
+  }
+  __syncthreads();
+  const int G = M / 8;
+  const int c = threadIdx.x / G, t = threadIdx.x % G;
+  fft_smem<T>(xm + c * M, M, logM, false, tw, t);
+  fft_smem<T>(xd + c * M, M, logM, false, tw, t);
+  for (int e = threadIdx.x; e < TC * M; e += blockDim.x) {
+    const int cc = e / M, a = e % M;
+    const int b = b0 + cc;
+    const int kq = a <= half ? a : M - a;
+    const int lq = b <= half ? b : M - b;
+    const int64_t qi = int64_t(lq) * (half + 1) + kq;
+    T d = Dq[qi];
+    if (a > half) d = mk(-d.x, -d.y);          // dipole table is odd in the a offset
+    xm[e] = cfma(xd[e], d, cmul(xm[e], Gq[qi]));
+  }
+  __syncthreads();
+  fft_smem<T>(xm + c * M, M, logM, true, tw, t);
+  for (int e = threadIdx.x; e < TC * n_lat; e += blockDim.x) {
+    const int a = e / TC, cc = e % TC;
+    Vt[int64_t(a) * M + b0 + cc] = xm[cc * M + a];
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kFftMaxM / 8) k_inv_rows(int M, int logM, int n_lat, const T* __restrict__ tw,
+                                                           const T* __restrict__ Vt, T* __restrict__ V) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* s = reinterpret_cast<T*>(smem_raw);
+  const int64_t a = blockIdx.x;
+  for (int b = threadIdx.x; b < M; b += blockDim.x) s[b] = Vt[a * M + b];
+  __syncthreads();
+  fft_smem<T>(s, M, logM, true, tw, threadIdx.x);
+  for (int b = threadIdx.x; b < n_lat; b += blockDim.x) V[a * M + b] = s[b];
+}
+
+template <typename T>
+int conv_cols_tc(int M) {
+  int tc = 1024 / (M / 8);
+  while (tc > 1 && size_t(2) * tc * M * sizeof(T) > 200 * 1024) tc /= 2;
+  return tc;
+}
+
+template <typename T>
+cudaError_t lattice_conv(const ApplyData<T>& d, cudaStream_t st) {
+  const int M = d.M;
+  if (M < 256 || M > kFftMaxM || (M & (M - 1))) return cudaErrorInvalidValue;
+  const int TC = conv_cols_tc<T>(M);
+  static bool attr_done = false;
+  if (!attr_done) {
+    cudaFuncSetAttribute(k_src_rows<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kFftMaxM * sizeof(T)));
+    cudaFuncSetAttribute(k_inv_rows<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kFftMaxM * sizeof(T)));
+    cudaFuncSetAttribute(k_conv_cols<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr_done = true;
+  }
+  // R (2 (L+1) x M) lives in Sd, Vt (n_lat x M) in Sm, V (n_lat x M) back in Sd
+  k_src_rows<T><<<dim3(d.L + 1, 2), M / 8, M * sizeof(T), st>>>(M, d.logM, d.n_lat, d.Ne, d.L, d.occ_of_cell,
+                                                                 d.sigma, d.n_es, d.tw, d.Sd);
+  k_conv_cols<T><<<M / TC, TC * (M / 8), size_t(2) * TC * M * sizeof(T), st>>>(
+      M, d.logM, d.n_lat, d.Ne, d.L, TC, d.Sd, d.Gq, d.Dq, d.tw, d.Sm);
+  k_inv_rows<T><<<d.n_lat, M / 8, M * sizeof(T), st>>>(M, d.logM, d.n_lat, d.tw, d.Sm, d.Sd);
+  return cudaGetLastError();
+}
+
 // ------------------------------------------------------------ spectral product
 template <typename T>
 __global__ void __launch_bounds__(256) k_spectral(int64_t n, T* __restrict__ Sm, const T* __restrict__ Sd,
@@ -246,25 +373,89 @@ __global__ void __launch_bounds__(256) k_local_coeffs(int nocc, const int* __res
 }
 
 // ------------------------------------------------------------ near field + assembly
+// One warp per target row q: the dense block row of q's cell against the three
+// contiguous column ranges of the 3 x 3 neighbourhood (coalesced, no column
+// indices), the CSR remainder, the local expansion Phi_q . gamma_c, and the
+// assembly out_q = u_q + kappa^2 (near + far).
+// One block per work item = (occupied cell, chunk of kNearRows target rows), so
+// that the large cells near the boundary are spread over many SMs.  The three
+// column ranges of the cell's 3 x 3 neighbourhood are staged in shared memory
+// (zero-padded to even lengths, matching the padded weight rows), then each
+// warp streams whole weight rows from HBM (complex64: 16-byte loads of two
+// weights) against the staged values, adds the CSR remainder and the local
+// expansion Phi_q . gamma_c, and writes out_q = u_q + kappa^2 (near + far).
+constexpr int kNearRows = 32;   // target rows per work item of k_near_eval
+
+__device__ __forceinline__ float2 row_dot(const float2* __restrict__ w, const float2* us, int nblk, int lane) {
+  const float4* w4 = reinterpret_cast<const float4*>(w);
+  const float4* u4 = reinterpret_cast<const float4*>(us);
+  float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
+  const int npair = nblk >> 1;
+#pragma unroll 4
+  for (int t = lane; t < npair; t += 32) {
+    const float4 ww = w4[t];
+    const float4 uu = u4[t];
+    a0 = cfma(make_float2(ww.x, ww.y), make_float2(uu.x, uu.y), a0);
+    a1 = cfma(make_float2(ww.z, ww.w), make_float2(uu.z, uu.w), a1);
+  }
+  return cadd(a0, a1);
+}
+__device__ __forceinline__ double2 row_dot(const double2* __restrict__ w, const double2* us, int nblk, int lane) {
+  double2 a0 = make_double2(0, 0), a1 = make_double2(0, 0);
+  int t = lane;
+#pragma unroll 2
+  for (; t + 32 < nblk; t += 64) {
+    a0 = cfma(w[t], us[t], a0);
+    a1 = cfma(w[t + 32], us[t + 32], a1);
+  }
+  if (t < nblk) a0 = cfma(w[t], us[t], a0);
+  return cadd(a0, a1);
+}
+
 template <typename T>
-__global__ void __launch_bounds__(256) k_near_eval(int64_t N, const int64_t* __restrict__ rowptr,
-                                                   const int* __restrict__ col, const T* __restrict__ val,
+__global__ void __launch_bounds__(256) k_near_eval(const int2* __restrict__ items,
+                                                   const int64_t* __restrict__ occ_start,
+                                                   const int64_t* __restrict__ blk_off,
+                                                   const int* __restrict__ blk_seg, const T* __restrict__ Wb,
+                                                   const int64_t* __restrict__ rem_row,
+                                                   const int* __restrict__ rem_col, const T* __restrict__ rem_val,
                                                    const T* __restrict__ u, const T* __restrict__ Phi,
-                                                   const T* __restrict__ gamma, const int* __restrict__ occ_of_node,
-                                                   int nfb2, typename RealOf<T>::R kappa2, T* __restrict__ out) {
-  const int64_t q = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (q >= N) return;
-  T acc = czero(T{});
-  const int64_t r0 = rowptr[q], r1 = rowptr[q + 1];
-  for (int64_t k = r0 + lane; k < r1; k += 32) acc = cfma(val[k], u[col[k]], acc);
-  const T* ph = Phi + q * nfb2;
-  const T* g = gamma + int64_t(occ_of_node[q]) * nfb2;
-  for (int n = lane; n < nfb2; n += 32) acc = cfma(ph[n], g[n], acc);
-  acc = warp_sum(acc);
-  if (lane == 0) {
-    const T uq = u[q];
-    out[q] = mk(uq.x + kappa2 * acc.x, uq.y + kappa2 * acc.y);
+                                                   const T* __restrict__ gamma, int nfb2,
+                                                   typename RealOf<T>::R kappa2, T* __restrict__ out) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* us = reinterpret_cast<T*>(smem_raw);
+  const int2 item = items[blockIdx.x];
+  const int k = item.x;
+  const int* sg = blk_seg + 6 * k;
+  const int l0 = sg[1], l1 = sg[3], l2 = sg[5];
+  const int p0 = (l0 + 1) & ~1, p1 = (l1 + 1) & ~1, p2 = (l2 + 1) & ~1;
+  const int nblk = p0 + p1 + p2;
+  T* gs = us + nblk;
+  for (int i = threadIdx.x; i < nblk; i += blockDim.x) {
+    T v = czero(T{});
+    if (i < p0) { if (i < l0) v = u[sg[0] + i]; }
+    else if (i < p0 + p1) { const int o = i - p0; if (o < l1) v = u[sg[2] + o]; }
+    else { const int o = i - p0 - p1; if (o < l2) v = u[sg[4] + o]; }
+    us[i] = v;
+  }
+  for (int n = threadIdx.x; n < nfb2; n += blockDim.x) gs[n] = gamma[int64_t(k) * nfb2 + n];
+  __syncthreads();
+  const int64_t r0 = occ_start[k];
+  const int nrow = int(occ_start[k + 1] - r0);
+  const int rend = min(nrow, item.y + kNearRows);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const T* wk = Wb + blk_off[k];
+  for (int r = item.y + warp; r < rend; r += nw) {
+    const int64_t q = r0 + r;
+    T acc = row_dot(wk + int64_t(r) * nblk, us, nblk, lane);
+    for (int64_t e = rem_row[q] + lane; e < rem_row[q + 1]; e += 32) acc = cfma(rem_val[e], u[rem_col[e]], acc);
+    const T* ph = Phi + q * nfb2;
+    for (int n = lane; n < nfb2; n += 32) acc = cfma(ph[n], gs[n], acc);
+    acc = warp_sum(acc);
+    if (lane == 0) {
+      const T uq = u[q];
+      out[q] = mk(uq.x + kappa2 * acc.x, uq.y + kappa2 * acc.y);
+    }
   }
 }
 
@@ -273,25 +464,24 @@ cudaError_t apply_one(const ApplyData<T>& d, const T* u, T* out, cudaStream_t st
   if (ev) cudaEventRecord(ev[0], st);
   k_es_project<T><<<d.nocc, 256, 0, st>>>(d.nocc, d.occ_start, d.P_off, d.P, u, d.sigma, d.n_es);
   if (ev) cudaEventRecord(ev[1], st);
-  const int64_t MM = int64_t(d.M) * d.M;
-  k_lattice_fill<T><<<unsigned((MM + 255) / 256), 256, 0, st>>>(d.M, d.n_lat, d.Ne, d.L, d.occ_of_cell,
-                                                                 d.sigma, d.n_es, d.Sm, d.Sd);
-  if (ev) cudaEventRecord(ev[2], st);
-  cudaError_t e = fft2d<T>(d.Sm, d.M, d.logM, d.tw, false, st);
-  if (e != cudaSuccess) return e;
-  e = fft2d<T>(d.Sd, d.M, d.logM, d.tw, false, st);
-  if (e != cudaSuccess) return e;
-  k_spectral<T><<<unsigned((MM + 255) / 256), 256, 0, st>>>(MM, d.Sm, d.Sd, d.Ghat, d.Dhat);
-  e = fft2d<T>(d.Sm, d.M, d.logM, d.tw, true, st);
+  if (ev) cudaEventRecord(ev[2], st);        // the lattice fill is fused into k_src_rows
+  cudaError_t e = lattice_conv(d, st);
   if (e != cudaSuccess) return e;
   if (ev) cudaEventRecord(ev[3], st);
   const size_t sm_local = size_t(d.n_loc + 9 * d.n_es) * sizeof(T);
-  k_local_coeffs<T><<<d.nocc, 256, sm_local, st>>>(d.nocc, d.occ_cells, d.occ_of_cell, d.L, d.Ne, d.M, d.Sm,
+  k_local_coeffs<T><<<d.nocc, 256, sm_local, st>>>(d.nocc, d.occ_cells, d.occ_of_cell, d.L, d.Ne, d.M, d.Sd,
                                                    d.Bp, d.BT, d.sigma, d.n_es, d.nfb2, d.gamma);
   if (ev) cudaEventRecord(ev[4], st);
-  k_near_eval<T><<<unsigned((d.N * 32 + 255) / 256), 256, 0, st>>>(
-      d.N, d.rowptr, d.col, d.val, u, d.Phi, d.gamma, d.occ_of_node, d.nfb2,
-      typename RealOf<T>::R(d.kappa2), out);
+  const size_t sm_near = size_t(d.max_nblk + d.nfb2) * sizeof(T);
+  static bool near_attr = false;
+  if (!near_attr) {
+    cudaFuncSetAttribute(k_near_eval<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    near_attr = true;
+  }
+  if (sm_near > 200 * 1024) return cudaErrorInvalidValue;
+  k_near_eval<T><<<d.n_items, 256, sm_near, st>>>(d.items, d.occ_start, d.blk_off, d.blk_seg, d.Wb, d.rem_row,
+                                              d.rem_col, d.rem_val, u, d.Phi, d.gamma, d.nfb2,
+                                              typename RealOf<T>::R(d.kappa2), out);
   if (ev) cudaEventRecord(ev[5], st);
   return cudaGetLastError();
 }
@@ -306,9 +496,11 @@ template cudaError_t fft2d<float2>(float2*, int, int, const float2*, bool, cudaS
 // ------------------------------------------------------------ GMRES helpers
 constexpr int kRedThreads = 256;
 
+// 2 blocks per SM, each owning at most 4096 elements (64 KB of shared memory)
 int gram_blocks(int64_t N) {
-  int64_t b = (N + kRedThreads * 4 - 1) / (kRedThreads * 4);
-  if (b > 304) b = 304;
+  int64_t b = 304;
+  if (N < 304 * 64) b = (N + 63) / 64;
+  if ((N + b - 1) / b > 4096) b = (N + 4095) / 4096;
   if (b < 1) b = 1;
   return int(b);
 }
@@ -327,33 +519,67 @@ __device__ __forceinline__ double2 block_sum(double2 v, double2* red) {
   return r;
 }
 
+// h[j] = <V_j, w> for j < nv and h[nv].x = ||w||^2, in one pass over V: each
+// block owns a contiguous chunk of the index range (w chunk in shared memory),
+// each warp reduces whole vectors with shuffles only.
 __global__ void __launch_bounds__(kRedThreads) k_gram_partial(const double2* __restrict__ V, int nv,
                                                               const double2* __restrict__ w, int64_t N,
-                                                              double2* __restrict__ partial) {
-  __shared__ double2 red[32];
-  for (int j = 0; j < nv; ++j) {
-    const double2* vj = V + int64_t(j) * N;
+                                                              int64_t chunk, double2* __restrict__ partial) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double2* ws = reinterpret_cast<double2*>(smem_raw);
+  const int64_t i0 = int64_t(blockIdx.x) * chunk;
+  const int n = int(i0 < N ? (N - i0 < chunk ? N - i0 : chunk) : 0);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) ws[i] = w[i0 + i];
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int j = warp; j <= nv; j += nw) {
     double2 acc = make_double2(0, 0);
-    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < N; i += int64_t(gridDim.x) * blockDim.x)
-      acc = cfma(cconj(vj[i]), w[i], acc);
-    const double2 s = block_sum(acc, red);
-    if (threadIdx.x == 0) partial[int64_t(blockIdx.x) * nv + j] = s;
+    if (j < nv) {
+      const double2* vj = V + int64_t(j) * N + i0;
+      double2 a1 = make_double2(0, 0), a2 = make_double2(0, 0), a3 = make_double2(0, 0);
+      int i = lane;
+      for (; i + 96 < n; i += 128) {
+        const double2 v0 = vj[i], v1 = vj[i + 32], v2 = vj[i + 64], v3 = vj[i + 96];
+        acc = cfma(cconj(v0), ws[i], acc);
+        a1 = cfma(cconj(v1), ws[i + 32], a1);
+        a2 = cfma(cconj(v2), ws[i + 64], a2);
+        a3 = cfma(cconj(v3), ws[i + 96], a3);
+      }
+      for (; i < n; i += 32) acc = cfma(cconj(vj[i]), ws[i], acc);
+      acc = cadd(cadd(acc, a1), cadd(a2, a3));
+    } else {
+      for (int i = lane; i < n; i += 32) acc.x = fma(ws[i].x, ws[i].x, fma(ws[i].y, ws[i].y, acc.x));
+    }
+    acc = warp_sum(acc);
+    if (lane == 0) partial[int64_t(blockIdx.x) * (nv + 1) + j] = acc;
   }
 }
 
-__global__ void k_gram_reduce(const double2* __restrict__ partial, int nblk, int nv, double2* __restrict__ h) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= nv) return;
+// one warp per dot product: lanes stride over the per-block partial sums
+__global__ void k_gram_reduce(const double2* __restrict__ partial, int nblk, int nv1, double2* __restrict__ h) {
+  const int j = blockIdx.x;
   double2 s = make_double2(0, 0);
-  for (int b = 0; b < nblk; ++b) s = cadd(s, partial[int64_t(b) * nv + j]);
-  h[j] = s;
+  for (int b = threadIdx.x; b < nblk; b += 32) s = cadd(s, partial[int64_t(b) * nv1 + j]);
+  s = warp_sum(s);
+  if (threadIdx.x == 0) h[j] = s;
+}
+
+static int64_t gram_chunk(int64_t N) {
+  const int nb = gram_blocks(N);
+  return (N + nb - 1) / nb;
 }
 
 cudaError_t gram(const double2* V, int nv, const double2* w, int64_t N, double2* partial, double2* h,
                  cudaStream_t st) {
   const int nb = gram_blocks(N);
-  k_gram_partial<<<nb, kRedThreads, 0, st>>>(V, nv, w, N, partial);
-  k_gram_reduce<<<(nv + 127) / 128, 128, 0, st>>>(partial, nb, nv, h);
+  const int64_t chunk = gram_chunk(N);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_gram_partial, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
+    attr = true;
+  }
+  k_gram_partial<<<nb, kRedThreads, chunk * sizeof(double2), st>>>(V, nv, w, N, chunk, partial);
+  k_gram_reduce<<<nv + 1, 32, 0, st>>>(partial, nb, nv + 1, h);
   return cudaGetLastError();
 }
 
@@ -362,6 +588,7 @@ __global__ void __launch_bounds__(256) k_axpy_multi(const double2* __restrict__ 
                                                     int64_t N) {
   for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < N; i += int64_t(gridDim.x) * blockDim.x) {
     double2 acc = w[i];
+#pragma unroll 4
     for (int j = 0; j < nv; ++j) {
       const double2 hj = h[j];
       const double2 v = V[int64_t(j) * N + i];
@@ -393,11 +620,10 @@ __global__ void __launch_bounds__(kRedThreads) k_norm_partial(const double2* __r
 }
 
 __global__ void k_norm_reduce(const double* __restrict__ partial, int nb, double* __restrict__ out) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) {
-    double s = 0;
-    for (int b = 0; b < nb; ++b) s += partial[b];
-    out[0] = sqrt(s);
-  }
+  double2 s = make_double2(0, 0);
+  for (int b = threadIdx.x; b < nb; b += 32) s.x += partial[b];
+  s = warp_sum(s);
+  if (threadIdx.x == 0) out[0] = sqrt(s.x);
 }
 
 cudaError_t norm2(const double2* w, int64_t N, double* partial, double* out, cudaStream_t st) {

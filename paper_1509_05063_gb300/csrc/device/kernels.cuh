@@ -19,22 +19,34 @@ struct ApplyData {
   const T* Bp = nullptr;                // nfb2 x n_loc
   const T* BT = nullptr;                // 9 x nfb2 x n_es
   const T* Phi = nullptr;               // N x nfb2
-  const T* Ghat = nullptr;              // M x M spectra (scaled by 1/M^2)
-  const T* Dhat = nullptr;
+  const T* Gq = nullptr;                // (M/2+1)^2 quarter spectra, [l][k], scaled by 1/M^2
+  const T* Dq = nullptr;
   const T* tw = nullptr;                // M twiddles exp(-2 pi i m / M)
-  const int64_t* rowptr = nullptr;      // near field CSR
-  const int* col = nullptr;
-  const T* val = nullptr;
+  // near field: one dense block per occupied cell (rows = the cell's nodes,
+  // columns = the nodes of its 3 x 3 neighbourhood, i.e. three contiguous node
+  // ranges), plus a CSR remainder for the few interpolation-stencil entries
+  // that fall outside the neighbourhood
+  const int64_t* blk_off = nullptr;     // nocc: offset of the cell's block
+  const int* blk_seg = nullptr;         // nocc x 6: (first node, length) of the 3 column ranges
+  int max_nblk = 0;                     // longest padded block row
+  const int2* items = nullptr;          // near-field work items (occupied cell, first row)
+  int n_items = 0;
+  const T* Wb = nullptr;                // blocks, row-major per cell
+  const int64_t* rem_row = nullptr;     // N + 1
+  const int* rem_col = nullptr;
+  const T* rem_val = nullptr;
   double kappa2 = 0;
   // work space
   T* sigma = nullptr;                   // nocc x n_es
-  T* Sm = nullptr;                      // M x M
-  T* Sd = nullptr;                      // M x M
+  T* Sm = nullptr;                      // lattice_rows() x M
+  T* Sd = nullptr;                      // lattice_rows() x M
+  int64_t lattice_rows() const { return (2 * (L + 1) > n_lat ? 2 * (L + 1) : n_lat); }
   T* gamma = nullptr;                   // nocc x nfb2
 };
 
-// Stage boundaries of one apply, for event timing: projection, lattice fill,
-// forward FFTs + product + inverse FFT, local coefficients, near field + assembly.
+// Stage boundaries of one apply, for event timing: projection, (unused: the
+// lattice fill is fused into the convolution), lattice convolution, local
+// coefficients, near field + assembly.
 constexpr int kStages = 5;
 
 // out = A u for one right-hand side (u, out: N complex).  When ev is not null
@@ -49,7 +61,8 @@ template <typename T>
 cudaError_t fft2d(T* x, int M, int logM, const T* tw, bool inverse, cudaStream_t st);
 
 // GMRES helpers (complex128).  h[j] = <V_j, w> for j < nv (V: nv vectors of
-// length N, stride N); partial needs blocks * nv elements.
+// length N, stride N) and h[nv].x = ||w||^2; partial needs blocks * (nv + 1)
+// elements, h needs nv + 1.
 cudaError_t gram(const double2* V, int nv, const double2* w, int64_t N, double2* partial,
                  double2* h, cudaStream_t st);
 cudaError_t axpy_multi(const double2* V, int nv, const double2* h, double2* w, int64_t N,

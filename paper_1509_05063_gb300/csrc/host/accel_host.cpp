@@ -171,15 +171,18 @@ bool build_accel(Plan2D& plan) {
   while (M < 2 * plan.n_lat - 1) M *= 2;
   if (M > 2048) { plan.err = "lattice too large: need 2 (L N_eq + 1) - 1 <= 2048"; return false; }
   plan.M = M;
+  // Offsets wrap at M/2, so the tables are exactly even (G) / odd in a (dG/dz_1)
+  // on the circle; the gap |offset| >= n_lat is never reached by the linear
+  // convolution.  The odd table is zero at a = M/2.
   plan.Gtab.assign(size_t(M) * M, cd(0.0));
   plan.Dtab.assign(size_t(M) * M, cd(0.0));
   parallel_for(plan.n_threads, M, 8, [&](int64_t i0, int64_t i1) {
     for (int64_t i = i0; i < i1; ++i) {
-      const int da = i < M - plan.n_lat + 1 ? int(i) : int(i) - M;
+      const int da = i <= M / 2 ? int(i) : int(i) - M;
       for (int j = 0; j < M; ++j) {
-        const int db = j < M - plan.n_lat + 1 ? j : j - M;
+        const int db = j <= M / 2 ? j : j - M;
         plan.Gtab[size_t(i) * M + j] = table(da, db, 0);
-        plan.Dtab[size_t(i) * M + j] = table(da, db, 1);
+        plan.Dtab[size_t(i) * M + j] = i == M / 2 ? cd(0.0) : table(da, db, 1);
       }
     }
   });

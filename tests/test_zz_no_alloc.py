@@ -43,9 +43,9 @@ def test_noalloc_apply_matches_apply_on_two_calls(prec_name):
 def test_noalloc_apply_rejects_plans_beyond_the_fixed_array():
     from paper_1509_05063_gb300 import LS_FP64, LSError, Plan
     wl = W.place_cells(W.kite(n1=512, n2=17, h=0.025, kappa=6.0, collar_w=0.07, tau0=0.4, tau1=0.9, R_a=6,
-                              R_b=5, R_cart=4, n_rho=32, N_tau=48), L=17, m=8, center=(-0.25, 0.0), N_eq=16)
+                              R_b=5, R_cart=4, n_rho=32, N_tau=48), L=17, m=8, center=(-0.25, 0.0), N_eq=31)
     plan = Plan(wl, W.n2_of(wl))
-    assert plan.info["fft_M"] == 1024
+    assert plan.info["fft_M"] == 2048
     u = torch.zeros(plan.N, dtype=torch.complex128, device="cuda:0")
     with pytest.raises(LSError, match="fixed device array"):
         plan.apply_noalloc(u, torch.empty_like(u), prec=LS_FP64)
