@@ -112,6 +112,22 @@ def dist_info():
     return rank, world, local
 
 
+def replica_rate(local_ms: float, local_units: int, device="cpu"):
+    """Whole-job throughput of independent replicas: the units processed by all
+    ranks over the slowest rank's time.  Returns (units / s, max ms, total units).
+    Single process when torch.distributed is not initialised."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return local_units / (local_ms * 1e-3), local_ms, local_units
+    t = torch.tensor([float(local_ms)], dtype=torch.float64, device=device)
+    n = torch.tensor([float(local_units)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(n, op=dist.ReduceOp.SUM)
+    ms, units = float(t.item()), float(n.item())
+    return units / (ms * 1e-3), ms, units
+
+
 def cpu_oracle_rate(wl, n_rows: int, seed_rows=None):
     """Oracle direct O(N^2) apply on a bounded sample of rows: returns
     (matvecs/s extrapolated from rows/s, rows, seconds, N)."""
@@ -210,6 +226,7 @@ def main():
         torch.cuda.synchronize()
 
     def timed(fn, steps):
+        """max over ranks of the CUDA-event time of `steps` calls (ms)."""
         barrier()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
@@ -217,22 +234,30 @@ def main():
             fn()
         e1.record()
         barrier()
-        ms = e0.elapsed_time(e1)
-        if world > 1:
-            t = torch.tensor([ms], device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            ms = float(t.item())
-        return ms
+        return replica_rate(e0.elapsed_time(e1), steps, device=dev)[1]
 
     f64 = lambda: plan.apply(u, out, prec=LS_FP64)
     f32 = lambda: plan.apply(u32, out32, prec=LS_MIXED)
+    # batched right-hand sides: one pass over the near-field weights serves all of them
+    NB32, NB64 = 8, 4
+    ub32 = torch.from_numpy(W.random_density(N, nrhs=NB32, seed=W.SEED + 3 + rank)).to(dev, torch.complex64)
+    ob32 = torch.empty_like(ub32)
+    ub64 = torch.from_numpy(W.random_density(N, nrhs=NB64, seed=W.SEED + 5 + rank)).to(dev)
+    ob64 = torch.empty_like(ub64)
+    fb32 = lambda: plan.apply(ub32, ob32, prec=LS_MIXED)
+    fb64 = lambda: plan.apply(ub64, ob64, prec=LS_FP64)
     for _ in range(args.warmup):
         f64()
         f32()
+        fb32()
+        fb64()
     with Clocks(local) as clk:
         ms64 = timed(f64, args.steps)
         ms32 = timed(f32, args.steps)
+        msb32 = timed(fb32, max(args.steps // 4, 3))
+        msb64 = timed(fb64, max(args.steps // 4, 3))
     clocks = clk.summary()
+    nb_steps = max(args.steps // 4, 3)
 
     # per-stage CUDA-event timing on the launch stream (roofline of the dominant kernel)
     plan.set_stage_timing(True)
@@ -337,6 +362,9 @@ def main():
                                "peak": peak, "unit": "GB/s", "frac": ach32 / peak, "peak_source": peak_src,
                                "bytes_per_launch": near_bytes(8), "traffic": None,
                                "launch_ms": t_near32 * 1e3}},
+        "batched": {"unit": "RHS-matvecs/s",
+                    "mixed": {"nrhs": NB32, "value": world * nb_steps * NB32 / (msb32 * 1e-3), "dtype": "f32"},
+                    "fp64": {"nrhs": NB64, "value": world * nb_steps * NB64 / (msb64 * 1e-3), "dtype": "f64"}},
         "stages_ms": {"fp64": dict(zip(stage_names, [float(x) / max(c64, 1) for x in st64])),
                       "mixed": dict(zip(stage_names, [float(x) / max(c32, 1) for x in st32]))},
         "apply_hbm_frac_fp64": (apply_bytes64 / (ms64 / args.steps * 1e-3) / 1e9) / peak,

@@ -288,9 +288,6 @@ ls_status ls_plan_create(const ls_geometry* geom, ls_n2_fn n2, void* ctx, double
     max_nblk = std::max(max_nblk, nblk);
     blk_off[k + 1] = blk_off[k] + (nd.cell_start[c + 1] - nd.cell_start[c]) * int64_t(nblk);
   }
-  if (size_t(max_nblk + P.nfb2) * sizeof(double2) > 200 * 1024)
-    return bail(LS_ERR_INVALID, "a cell's 3 x 3 neighbourhood holds too many nodes (" + std::to_string(max_nblk) +
-                "); use smaller cells");
   std::vector<cd> Wb(blk_off[nocc], cd(0.0));
   std::vector<int64_t> rem_row(N + 1, 0);
   std::vector<int> rem_col;
@@ -319,9 +316,9 @@ ls_status ls_plan_create(const ls_geometry* geom, ls_n2_fn n2, void* ctx, double
   const int* d_occ_of_cell = UP(int, occ_of_cell);
   const int* d_occ_of_node = UP(int, occ_of_node);
   const int64_t* d_P_off = UP(int64_t, P.P_off);
-  std::vector<int> items;   // (occupied cell, first row) pairs, 32 rows each
+  std::vector<int> items;   // (occupied cell, first row) pairs, 16 rows each
   for (int k = 0; k < nocc; ++k)
-    for (int64_t r = 0; r < occ_start[k + 1] - occ_start[k]; r += 32) { items.push_back(k); items.push_back(int(r)); }
+    for (int64_t r = 0; r < occ_start[k + 1] - occ_start[k]; r += 16) { items.push_back(k); items.push_back(int(r)); }
   const int* d_items_raw = UP(int, items);
   const int2* d_items = reinterpret_cast<const int2*>(d_items_raw);
   const int64_t* d_blk_off = UP(int64_t, blk_off);
@@ -387,10 +384,10 @@ ls_status ls_plan_create(const ls_geometry* geom, ls_n2_fn n2, void* ctx, double
   a.rem_val = UP(double2, rem_val);
   a.Gq = d_G64; a.Dq = d_D64; a.tw = d_tw64;
   a.kappa2 = kappa * kappa;
-  a.sigma = plan->alloc<double2>(size_t(nocc) * P.n_es, &st);
-  a.Sm = plan->alloc<double2>(a.lattice_rows() * M, &st);
-  a.Sd = plan->alloc<double2>(a.lattice_rows() * M, &st);
-  a.gamma = plan->alloc<double2>(size_t(nocc) * P.nfb2, &st);
+  a.sigma = plan->alloc<double2>(size_t(lsd::kMaxRhs64) * nocc * P.n_es, &st);
+  a.Sm = plan->alloc<double2>(lsd::kMaxRhs64 * a.lattice_rows() * M, &st);
+  a.Sd = plan->alloc<double2>(lsd::kMaxRhs64 * a.lattice_rows() * M, &st);
+  a.gamma = plan->alloc<double2>(size_t(lsd::kMaxRhs64) * nocc * P.nfb2, &st);
   if (st != LS_OK) return bail(st, plan->err);
   // complex64 apply data
   auto& b = plan->d32;
@@ -414,10 +411,10 @@ ls_status ls_plan_create(const ls_geometry* geom, ls_n2_fn n2, void* ctx, double
   b.Gq = d_G32; b.Dq = d_D32;
   b.tw = UP(float2, to32(tw));
   b.kappa2 = a.kappa2;
-  b.sigma = plan->alloc<float2>(size_t(nocc) * P.n_es, &st);
-  b.Sm = plan->alloc<float2>(b.lattice_rows() * M, &st);
-  b.Sd = plan->alloc<float2>(b.lattice_rows() * M, &st);
-  b.gamma = plan->alloc<float2>(size_t(nocc) * P.nfb2, &st);
+  b.sigma = plan->alloc<float2>(size_t(lsd::kMaxRhs32) * nocc * P.n_es, &st);
+  b.Sm = plan->alloc<float2>(lsd::kMaxRhs32 * b.lattice_rows() * M, &st);
+  b.Sd = plan->alloc<float2>(lsd::kMaxRhs32 * b.lattice_rows() * M, &st);
+  b.gamma = plan->alloc<float2>(size_t(lsd::kMaxRhs32) * nocc * P.nfb2, &st);
   if (st != LS_OK) return bail(st, plan->err);
 #undef UP
   if (cudaDeviceSynchronize() != cudaSuccess) return bail(LS_ERR_CUDA, "upload failed");
@@ -459,12 +456,18 @@ ls_status ls_apply(ls_plan plan, const void* u, void* Au, int nrhs, ls_precision
   const int64_t N = plan->d64.N;
   if (prec != LS_FP64 && prec != LS_MIXED) return fail(plan, LS_ERR_INVALID, "ls_apply: bad precision");
   cudaEvent_t* ev = plan->timing ? plan->ev : nullptr;
-  for (int r = 0; r < nrhs; ++r) {
+  const int maxr = prec == LS_FP64 ? lsd::kMaxRhs64 : lsd::kMaxRhs32;
+  for (int r = 0; r < nrhs;) {
+    int nr = maxr;                       // largest power of two batch that fits
+    while (nr > nrhs - r) nr /= 2;
     cudaError_t e;
     if (prec == LS_FP64)
-      e = lsd::apply_one(plan->d64, static_cast<const double2*>(u) + r * N, static_cast<double2*>(Au) + r * N, st, ev);
+      e = lsd::apply_batch(plan->d64, static_cast<const double2*>(u) + r * N, static_cast<double2*>(Au) + r * N, nr,
+                           st, ev);
     else
-      e = lsd::apply_one(plan->d32, static_cast<const float2*>(u) + r * N, static_cast<float2*>(Au) + r * N, st, ev);
+      e = lsd::apply_batch(plan->d32, static_cast<const float2*>(u) + r * N, static_cast<float2*>(Au) + r * N, nr,
+                           st, ev);
+    r += nr;
     if (e != cudaSuccess) return fail(plan, LS_ERR_CUDA, std::string("ls_apply: ") + cudaGetErrorString(e));
     if (ev) {
       LS_CU(cudaEventSynchronize(ev[lsd::kStages]));

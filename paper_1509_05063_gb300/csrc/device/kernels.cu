@@ -20,10 +20,10 @@ template <> struct RealOf<double2> { using R = double; };
 template <> struct RealOf<float2> { using R = float; };
 
 // ------------------------------------------------------------ ES projection
-template <typename T>
+template <typename T, int R>
 __global__ void __launch_bounds__(256) k_es_project(int nocc, const int64_t* __restrict__ occ_start,
                                                     const int64_t* __restrict__ P_off,
-                                                    const T* __restrict__ P, const T* __restrict__ u,
+                                                    const T* __restrict__ P, const T* __restrict__ u, int64_t N,
                                                     T* __restrict__ sigma, int n_es) {
   const int k = blockIdx.x;
   if (k >= nocc) return;
@@ -32,10 +32,19 @@ __global__ void __launch_bounds__(256) k_es_project(int nocc, const int64_t* __r
   const T* Pc = P + P_off[k];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   for (int i = warp; i < n_es; i += nw) {
-    T acc = czero(T{});
-    for (int j = lane; j < nc; j += 32) acc = cfma(Pc[int64_t(i) * nc + j], u[s0 + j], acc);
-    acc = warp_sum(acc);
-    if (lane == 0) sigma[int64_t(k) * n_es + i] = acc;
+    T acc[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) acc[r] = czero(T{});
+    for (int j = lane; j < nc; j += 32) {
+      const T pij = Pc[int64_t(i) * nc + j];
+#pragma unroll
+      for (int r = 0; r < R; ++r) acc[r] = cfma(pij, u[r * N + s0 + j], acc[r]);
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const T v = warp_sum(acc[r]);
+      if (lane == 0) sigma[(int64_t(r) * nocc + k) * n_es + i] = v;
+    }
   }
 }
 
@@ -208,11 +217,14 @@ cudaError_t fft2d(T* x, int M, int logM, const T* tw, bool inverse, cudaStream_t
 template <typename T>
 __global__ void __launch_bounds__(kFftMaxM / 8) k_src_rows(int M, int logM, int n_lat, int Ne, int L,
                                                            const int* __restrict__ occ_of_cell,
-                                                           const T* __restrict__ sigma, int n_es,
-                                                           const T* __restrict__ tw, T* __restrict__ R) {
+                                                           const T* __restrict__ sigma_all, int n_es, int nocc,
+                                                           const T* __restrict__ tw, T* __restrict__ R_all,
+                                                           int64_t stride) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* s = reinterpret_cast<T*>(smem_raw);
   const int k = blockIdx.x, kind = blockIdx.y;   // face row, 0 monopole / 1 dipole
+  const T* sigma = sigma_all + int64_t(blockIdx.z) * nocc * n_es;
+  T* R = R_all + int64_t(blockIdx.z) * stride;
   for (int b = threadIdx.x; b < M; b += blockDim.x) {
     T v = czero(T{});
     if (b < n_lat) {
@@ -240,10 +252,12 @@ __global__ void __launch_bounds__(kFftMaxM / 8) k_src_rows(int M, int logM, int 
 // spectra quarter layout: Q[l][k] for l, k in [0, M/2] (k fastest)
 template <typename T>
 __global__ void __launch_bounds__(1024) k_conv_cols(int M, int logM, int n_lat, int Ne, int L, int TC,
-                                                    const T* __restrict__ R, const T* __restrict__ Gq,
+                                                    const T* __restrict__ R_all, const T* __restrict__ Gq,
                                                     const T* __restrict__ Dq, const T* __restrict__ tw,
-                                                    T* __restrict__ Vt) {
+                                                    T* __restrict__ Vt_all, int64_t stride) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  const T* R = R_all + int64_t(blockIdx.y) * stride;
+  T* Vt = Vt_all + int64_t(blockIdx.y) * stride;
   T* xm = reinterpret_cast<T*>(smem_raw);      // [TC][M]
   T* xd = xm + TC * M;                         // [TC][M]
   const int b0 = blockIdx.x * TC;
@@ -284,9 +298,12 @@ __global__ void __launch_bounds__(1024) k_conv_cols(int M, int logM, int n_lat, 
 
 template <typename T>
 __global__ void __launch_bounds__(kFftMaxM / 8) k_inv_rows(int M, int logM, int n_lat, const T* __restrict__ tw,
-                                                           const T* __restrict__ Vt, T* __restrict__ V) {
+                                                           const T* __restrict__ Vt_all, T* __restrict__ V_all,
+                                                           int64_t stride) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* s = reinterpret_cast<T*>(smem_raw);
+  const T* Vt = Vt_all + int64_t(blockIdx.y) * stride;
+  T* V = V_all + int64_t(blockIdx.y) * stride;
   const int64_t a = blockIdx.x;
   for (int b = threadIdx.x; b < M; b += blockDim.x) s[b] = Vt[a * M + b];
   __syncthreads();
@@ -302,7 +319,7 @@ int conv_cols_tc(int M) {
 }
 
 template <typename T>
-cudaError_t lattice_conv(const ApplyData<T>& d, cudaStream_t st) {
+cudaError_t lattice_conv(const ApplyData<T>& d, int nr, cudaStream_t st) {
   const int M = d.M;
   if (M < 256 || M > kFftMaxM || (M & (M - 1))) return cudaErrorInvalidValue;
   const int TC = conv_cols_tc<T>(M);
@@ -314,11 +331,12 @@ cudaError_t lattice_conv(const ApplyData<T>& d, cudaStream_t st) {
     attr_done = true;
   }
   // R (2 (L+1) x M) lives in Sd, Vt (n_lat x M) in Sm, V (n_lat x M) back in Sd
-  k_src_rows<T><<<dim3(d.L + 1, 2), M / 8, M * sizeof(T), st>>>(M, d.logM, d.n_lat, d.Ne, d.L, d.occ_of_cell,
-                                                                 d.sigma, d.n_es, d.tw, d.Sd);
-  k_conv_cols<T><<<M / TC, TC * (M / 8), size_t(2) * TC * M * sizeof(T), st>>>(
-      M, d.logM, d.n_lat, d.Ne, d.L, TC, d.Sd, d.Gq, d.Dq, d.tw, d.Sm);
-  k_inv_rows<T><<<d.n_lat, M / 8, M * sizeof(T), st>>>(M, d.logM, d.n_lat, d.tw, d.Sm, d.Sd);
+  const int64_t stride = d.lattice_rows() * M;
+  k_src_rows<T><<<dim3(d.L + 1, 2, nr), M / 8, M * sizeof(T), st>>>(M, d.logM, d.n_lat, d.Ne, d.L, d.occ_of_cell,
+                                                                     d.sigma, d.n_es, d.nocc, d.tw, d.Sd, stride);
+  k_conv_cols<T><<<dim3(M / TC, nr), TC * (M / 8), size_t(2) * TC * M * sizeof(T), st>>>(
+      M, d.logM, d.n_lat, d.Ne, d.L, TC, d.Sd, d.Gq, d.Dq, d.tw, d.Sm, stride);
+  k_inv_rows<T><<<dim3(d.n_lat, nr), M / 8, M * sizeof(T), st>>>(M, d.logM, d.n_lat, d.tw, d.Sm, d.Sd, stride);
   return cudaGetLastError();
 }
 
@@ -334,10 +352,13 @@ __global__ void __launch_bounds__(256) k_spectral(int64_t n, T* __restrict__ Sm,
 template <typename T>
 __global__ void __launch_bounds__(256) k_local_coeffs(int nocc, const int* __restrict__ occ_cells,
                                                       const int* __restrict__ occ_of_cell, int L, int Ne,
-                                                      int M, const T* __restrict__ V, const T* __restrict__ Bp,
-                                                      const T* __restrict__ BT, const T* __restrict__ sigma,
-                                                      int n_es, int nfb2, T* __restrict__ gamma) {
+                                                      int M, const T* __restrict__ V_all, const T* __restrict__ Bp,
+                                                      const T* __restrict__ BT, const T* __restrict__ sigma_all,
+                                                      int n_es, int nfb2, T* __restrict__ gamma_all, int64_t stride) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  const T* V = V_all + int64_t(blockIdx.y) * stride;
+  const T* sigma = sigma_all + int64_t(blockIdx.y) * nocc * n_es;
+  T* gamma = gamma_all + int64_t(blockIdx.y) * nocc * nfb2;
   const int n_loc = (Ne + 1) * (Ne + 1);
   T* Vc = reinterpret_cast<T*>(smem_raw);
   T* sg = Vc + n_loc;
@@ -377,119 +398,213 @@ __global__ void __launch_bounds__(256) k_local_coeffs(int nocc, const int* __res
 // contiguous column ranges of the 3 x 3 neighbourhood (coalesced, no column
 // indices), the CSR remainder, the local expansion Phi_q . gamma_c, and the
 // assembly out_q = u_q + kappa^2 (near + far).
-// One block per work item = (occupied cell, chunk of kNearRows target rows), so
-// that the large cells near the boundary are spread over many SMs.  The three
-// column ranges of the cell's 3 x 3 neighbourhood are staged in shared memory
-// (zero-padded to even lengths, matching the padded weight rows), then each
-// warp streams whole weight rows from HBM (complex64: 16-byte loads of two
-// weights) against the staged values, adds the CSR remainder and the local
-// expansion Phi_q . gamma_c, and writes out_q = u_q + kappa^2 (near + far).
-constexpr int kNearRows = 32;   // target rows per work item of k_near_eval
+// One block per work item = (occupied cell, chunk of 16 target rows), so that
+// the large cells near the boundary are spread over many SMs.  Each warp owns
+// 2 rows of the chunk and R right-hand sides at once: for every column of the
+// cell's 3 x 3 neighbourhood it loads the 2 weights from HBM and the R input
+// values from shared memory (staged chunk by chunk, one contiguous run per RHS,
+// zero in the padding), so one pass over the weights serves all R right-hand
+// sides.
+// The epilogue adds the CSR remainder and the local expansion Phi_q . gamma_c
+// and writes out_q = u_q + kappa^2 (near + far) for every RHS.
+constexpr int kNearRows = 16;      // rows per work item (8 warps x kNearRW rows)
+constexpr int kNearRW = 2;         // rows per warp
+constexpr int kNearSmem = 32768;   // bytes of staged input values per chunk
 
-__device__ __forceinline__ float2 row_dot(const float2* __restrict__ w, const float2* us, int nblk, int lane) {
-  const float4* w4 = reinterpret_cast<const float4*>(w);
-  const float4* u4 = reinterpret_cast<const float4*>(us);
-  float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
-  const int npair = nblk >> 1;
-#pragma unroll 4
-  for (int t = lane; t < npair; t += 32) {
-    const float4 ww = w4[t];
-    const float4 uu = u4[t];
-    a0 = cfma(make_float2(ww.x, ww.y), make_float2(uu.x, uu.y), a0);
-    a1 = cfma(make_float2(ww.z, ww.w), make_float2(uu.z, uu.w), a1);
-  }
-  return cadd(a0, a1);
-}
-__device__ __forceinline__ double2 row_dot(const double2* __restrict__ w, const double2* us, int nblk, int lane) {
-  double2 a0 = make_double2(0, 0), a1 = make_double2(0, 0);
-  int t = lane;
+// acc[i][r] += sum over the chunk's columns t of W[row_i][c0 + t] us[r][t]
+template <typename T, int R>
+__device__ __forceinline__ void near_chunk(const T* __restrict__ wk, const int* rows, int nblk, int c0, int cl,
+                                           const T* us, int CH, int lane, T (&acc)[kNearRW][R]) {
+  const T* w[kNearRW];
+#pragma unroll
+  for (int i = 0; i < kNearRW; ++i) w[i] = wk + int64_t(rows[i]) * nblk + c0;
 #pragma unroll 2
-  for (; t + 32 < nblk; t += 64) {
-    a0 = cfma(w[t], us[t], a0);
-    a1 = cfma(w[t + 32], us[t + 32], a1);
+  for (int t = lane; t < cl; t += 32) {
+    T a[kNearRW];
+#pragma unroll
+    for (int i = 0; i < kNearRW; ++i) a[i] = w[i][t];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const T x = us[r * CH + t];
+#pragma unroll
+      for (int i = 0; i < kNearRW; ++i) acc[i][r] = cfma(a[i], x, acc[i][r]);
+    }
   }
-  if (t < nblk) a0 = cfma(w[t], us[t], a0);
-  return cadd(a0, a1);
 }
 
-template <typename T>
+// complex64: two columns per lane and 16-byte loads (rows, chunk starts and
+// chunk lengths are even, so every pair is 16-byte aligned)
+template <int R>
+__device__ __forceinline__ void near_chunk_pairs(const float2* __restrict__ wk, const int* rows, int nblk, int c0,
+                                                 int cl, const float2* us, int CH, int lane,
+                                                 float2 (&acc)[kNearRW][R]) {
+  const float4* w[kNearRW];
+#pragma unroll
+  for (int i = 0; i < kNearRW; ++i) w[i] = reinterpret_cast<const float4*>(wk + int64_t(rows[i]) * nblk + c0);
+  const int np = cl >> 1;
+#pragma unroll 2
+  for (int t = lane; t < np; t += 32) {
+    float4 a[kNearRW];
+#pragma unroll
+    for (int i = 0; i < kNearRW; ++i) a[i] = w[i][t];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const float4 x = reinterpret_cast<const float4*>(us + r * CH)[t];
+      const float2 x0 = make_float2(x.x, x.y), x1 = make_float2(x.z, x.w);
+#pragma unroll
+      for (int i = 0; i < kNearRW; ++i)
+        acc[i][r] = cfma(make_float2(a[i].z, a[i].w), x1, cfma(make_float2(a[i].x, a[i].y), x0, acc[i][r]));
+    }
+  }
+}
+template <>
+__device__ __forceinline__ void near_chunk<float2, 1>(const float2* __restrict__ wk, const int* rows, int nblk,
+                                                      int c0, int cl, const float2* us, int CH, int lane,
+                                                      float2 (&acc)[kNearRW][1]) {
+  near_chunk_pairs<1>(wk, rows, nblk, c0, cl, us, CH, lane, acc);
+}
+template <>
+__device__ __forceinline__ void near_chunk<float2, 2>(const float2* __restrict__ wk, const int* rows, int nblk,
+                                                      int c0, int cl, const float2* us, int CH, int lane,
+                                                      float2 (&acc)[kNearRW][2]) {
+  near_chunk_pairs<2>(wk, rows, nblk, c0, cl, us, CH, lane, acc);
+}
+template <>
+__device__ __forceinline__ void near_chunk<float2, 4>(const float2* __restrict__ wk, const int* rows, int nblk,
+                                                      int c0, int cl, const float2* us, int CH, int lane,
+                                                      float2 (&acc)[kNearRW][4]) {
+  near_chunk_pairs<4>(wk, rows, nblk, c0, cl, us, CH, lane, acc);
+}
+template <>
+__device__ __forceinline__ void near_chunk<float2, 8>(const float2* __restrict__ wk, const int* rows, int nblk,
+                                                      int c0, int cl, const float2* us, int CH, int lane,
+                                                      float2 (&acc)[kNearRW][8]) {
+  near_chunk_pairs<8>(wk, rows, nblk, c0, cl, us, CH, lane, acc);
+}
+
+template <typename T, int R>
 __global__ void __launch_bounds__(256) k_near_eval(const int2* __restrict__ items,
                                                    const int64_t* __restrict__ occ_start,
                                                    const int64_t* __restrict__ blk_off,
                                                    const int* __restrict__ blk_seg, const T* __restrict__ Wb,
                                                    const int64_t* __restrict__ rem_row,
                                                    const int* __restrict__ rem_col, const T* __restrict__ rem_val,
-                                                   const T* __restrict__ u, const T* __restrict__ Phi,
-                                                   const T* __restrict__ gamma, int nfb2,
+                                                   const T* __restrict__ u, int64_t N, const T* __restrict__ Phi,
+                                                   const T* __restrict__ gamma, int nocc, int nfb2,
                                                    typename RealOf<T>::R kappa2, T* __restrict__ out) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* us = reinterpret_cast<T*>(smem_raw);
+  T* us = reinterpret_cast<T*>(smem_raw);               // [rhs][column]
+  constexpr int CH = kNearSmem / int(R * sizeof(T));    // columns per chunk (even)
   const int2 item = items[blockIdx.x];
   const int k = item.x;
   const int* sg = blk_seg + 6 * k;
   const int l0 = sg[1], l1 = sg[3], l2 = sg[5];
-  const int p0 = (l0 + 1) & ~1, p1 = (l1 + 1) & ~1, p2 = (l2 + 1) & ~1;
-  const int nblk = p0 + p1 + p2;
-  T* gs = us + nblk;
-  for (int i = threadIdx.x; i < nblk; i += blockDim.x) {
-    T v = czero(T{});
-    if (i < p0) { if (i < l0) v = u[sg[0] + i]; }
-    else if (i < p0 + p1) { const int o = i - p0; if (o < l1) v = u[sg[2] + o]; }
-    else { const int o = i - p0 - p1; if (o < l2) v = u[sg[4] + o]; }
-    us[i] = v;
-  }
-  for (int n = threadIdx.x; n < nfb2; n += blockDim.x) gs[n] = gamma[int64_t(k) * nfb2 + n];
-  __syncthreads();
+  const int p0 = (l0 + 1) & ~1, p1 = (l1 + 1) & ~1;
+  const int nblk = p0 + p1 + ((l2 + 1) & ~1);
   const int64_t r0 = occ_start[k];
   const int nrow = int(occ_start[k + 1] - r0);
-  const int rend = min(nrow, item.y + kNearRows);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const T* wk = Wb + blk_off[k];
-  for (int r = item.y + warp; r < rend; r += nw) {
-    const int64_t q = r0 + r;
-    T acc = row_dot(wk + int64_t(r) * nblk, us, nblk, lane);
-    for (int64_t e = rem_row[q] + lane; e < rem_row[q + 1]; e += 32) acc = cfma(rem_val[e], u[rem_col[e]], acc);
-    const T* ph = Phi + q * nfb2;
-    for (int n = lane; n < nfb2; n += 32) acc = cfma(ph[n], gs[n], acc);
-    acc = warp_sum(acc);
-    if (lane == 0) {
-      const T uq = u[q];
-      out[q] = mk(uq.x + kappa2 * acc.x, uq.y + kappa2 * acc.y);
+  int rows[kNearRW];
+  bool valid[kNearRW];
+#pragma unroll
+  for (int i = 0; i < kNearRW; ++i) {
+    const int r = item.y + warp + 8 * i;
+    valid[i] = r < nrow;
+    rows[i] = valid[i] ? r : item.y;
+  }
+  T acc[kNearRW][R];
+#pragma unroll
+  for (int i = 0; i < kNearRW; ++i)
+#pragma unroll
+    for (int r = 0; r < R; ++r) acc[i][r] = czero(T{});
+  for (int c0 = 0; c0 < nblk; c0 += CH) {
+    const int cl = min(CH, nblk - c0);
+    __syncthreads();
+    for (int e = threadIdx.x; e < cl * R; e += blockDim.x) {   // us[r * CH + col]: conflict-free reads
+      const int r = e / cl, col = c0 + e % cl;
+      T v = czero(T{});
+      if (col < p0) { if (col < l0) v = u[r * N + sg[0] + col]; }
+      else if (col < p0 + p1) { const int o = col - p0; if (o < l1) v = u[r * N + sg[2] + o]; }
+      else { const int o = col - p0 - p1; if (o < l2) v = u[r * N + sg[4] + o]; }
+      us[r * CH + (e % cl)] = v;
     }
+    __syncthreads();
+    near_chunk<T, R>(wk, rows, nblk, c0, cl, us, CH, lane, acc);
+  }
+#pragma unroll
+  for (int i = 0; i < kNearRW; ++i) {
+    if (!valid[i]) continue;                      // warp-uniform
+    const int64_t q = r0 + rows[i];
+    for (int64_t e = rem_row[q] + lane; e < rem_row[q + 1]; e += 32) {
+      const T w = rem_val[e];
+      const int c = rem_col[e];
+#pragma unroll
+      for (int r = 0; r < R; ++r) acc[i][r] = cfma(w, u[r * N + c], acc[i][r]);
+    }
+    const T* ph = Phi + q * nfb2;
+    for (int n = lane; n < nfb2; n += 32) {
+      const T p = ph[n];
+#pragma unroll
+      for (int r = 0; r < R; ++r) acc[i][r] = cfma(p, gamma[(int64_t(r) * nocc + k) * nfb2 + n], acc[i][r]);
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const T v = warp_sum(acc[i][r]);
+      if (lane == 0) {
+        const T uq = u[r * N + q];
+        out[r * N + q] = mk(uq.x + kappa2 * v.x, uq.y + kappa2 * v.y);
+      }
+    }
+  }
+}
+
+template <typename T, int R>
+cudaError_t apply_r(const ApplyData<T>& d, const T* u, T* out, cudaStream_t st, cudaEvent_t* ev) {
+  if (ev) cudaEventRecord(ev[0], st);
+  k_es_project<T, R><<<d.nocc, 256, 0, st>>>(d.nocc, d.occ_start, d.P_off, d.P, u, d.N, d.sigma, d.n_es);
+  if (ev) cudaEventRecord(ev[1], st);
+  if (ev) cudaEventRecord(ev[2], st);        // the lattice fill is fused into k_src_rows
+  cudaError_t e = lattice_conv(d, R, st);
+  if (e != cudaSuccess) return e;
+  if (ev) cudaEventRecord(ev[3], st);
+  const size_t sm_local = size_t(d.n_loc + 9 * d.n_es) * sizeof(T);
+  k_local_coeffs<T><<<dim3(d.nocc, R), 256, sm_local, st>>>(d.nocc, d.occ_cells, d.occ_of_cell, d.L, d.Ne, d.M,
+                                                            d.Sd, d.Bp, d.BT, d.sigma, d.n_es, d.nfb2, d.gamma,
+                                                            d.lattice_rows() * d.M);
+  if (ev) cudaEventRecord(ev[4], st);
+  k_near_eval<T, R><<<d.n_items, 256, kNearSmem, st>>>(d.items, d.occ_start, d.blk_off, d.blk_seg, d.Wb,
+                                                       d.rem_row, d.rem_col, d.rem_val, u, d.N, d.Phi, d.gamma,
+                                                       d.nocc, d.nfb2, typename RealOf<T>::R(d.kappa2), out);
+  if (ev) cudaEventRecord(ev[5], st);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t apply_batch(const ApplyData<T>& d, const T* u, T* out, int nr, cudaStream_t st, cudaEvent_t* ev) {
+  switch (nr) {
+    case 1: return apply_r<T, 1>(d, u, out, st, ev);
+    case 2: return apply_r<T, 2>(d, u, out, st, ev);
+    case 4: return apply_r<T, 4>(d, u, out, st, ev);
+    case 8: if (sizeof(T) == 8) return apply_r<T, 8>(d, u, out, st, ev);
+      return cudaErrorInvalidValue;
+    default: return cudaErrorInvalidValue;
   }
 }
 
 template <typename T>
 cudaError_t apply_one(const ApplyData<T>& d, const T* u, T* out, cudaStream_t st, cudaEvent_t* ev) {
-  if (ev) cudaEventRecord(ev[0], st);
-  k_es_project<T><<<d.nocc, 256, 0, st>>>(d.nocc, d.occ_start, d.P_off, d.P, u, d.sigma, d.n_es);
-  if (ev) cudaEventRecord(ev[1], st);
-  if (ev) cudaEventRecord(ev[2], st);        // the lattice fill is fused into k_src_rows
-  cudaError_t e = lattice_conv(d, st);
-  if (e != cudaSuccess) return e;
-  if (ev) cudaEventRecord(ev[3], st);
-  const size_t sm_local = size_t(d.n_loc + 9 * d.n_es) * sizeof(T);
-  k_local_coeffs<T><<<d.nocc, 256, sm_local, st>>>(d.nocc, d.occ_cells, d.occ_of_cell, d.L, d.Ne, d.M, d.Sd,
-                                                   d.Bp, d.BT, d.sigma, d.n_es, d.nfb2, d.gamma);
-  if (ev) cudaEventRecord(ev[4], st);
-  const size_t sm_near = size_t(d.max_nblk + d.nfb2) * sizeof(T);
-  static bool near_attr = false;
-  if (!near_attr) {
-    cudaFuncSetAttribute(k_near_eval<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    near_attr = true;
-  }
-  if (sm_near > 200 * 1024) return cudaErrorInvalidValue;
-  k_near_eval<T><<<d.n_items, 256, sm_near, st>>>(d.items, d.occ_start, d.blk_off, d.blk_seg, d.Wb, d.rem_row,
-                                              d.rem_col, d.rem_val, u, d.Phi, d.gamma, d.nfb2,
-                                              typename RealOf<T>::R(d.kappa2), out);
-  if (ev) cudaEventRecord(ev[5], st);
-  return cudaGetLastError();
+  return apply_batch(d, u, out, 1, st, ev);
 }
 
 template cudaError_t apply_one<double2>(const ApplyData<double2>&, const double2*, double2*, cudaStream_t,
                                         cudaEvent_t*);
 template cudaError_t apply_one<float2>(const ApplyData<float2>&, const float2*, float2*, cudaStream_t,
                                        cudaEvent_t*);
+template cudaError_t apply_batch<double2>(const ApplyData<double2>&, const double2*, double2*, int, cudaStream_t,
+                                          cudaEvent_t*);
+template cudaError_t apply_batch<float2>(const ApplyData<float2>&, const float2*, float2*, int, cudaStream_t,
+                                         cudaEvent_t*);
 template cudaError_t fft2d<double2>(double2*, int, int, const double2*, bool, cudaStream_t);
 template cudaError_t fft2d<float2>(float2*, int, int, const float2*, bool, cudaStream_t);
 

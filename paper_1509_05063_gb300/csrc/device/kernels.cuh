@@ -37,11 +37,11 @@ struct ApplyData {
   const T* rem_val = nullptr;
   double kappa2 = 0;
   // work space
-  T* sigma = nullptr;                   // nocc x n_es
-  T* Sm = nullptr;                      // lattice_rows() x M
-  T* Sd = nullptr;                      // lattice_rows() x M
+  T* sigma = nullptr;                   // max_rhs x nocc x n_es
+  T* Sm = nullptr;                      // max_rhs x lattice_rows() x M
+  T* Sd = nullptr;                      // max_rhs x lattice_rows() x M
   int64_t lattice_rows() const { return (2 * (L + 1) > n_lat ? 2 * (L + 1) : n_lat); }
-  T* gamma = nullptr;                   // nocc x nfb2
+  T* gamma = nullptr;                   // max_rhs x nocc x nfb2
 };
 
 // Stage boundaries of one apply, for event timing: projection, (unused: the
@@ -54,6 +54,15 @@ constexpr int kStages = 5;
 // first launch error (cudaSuccess otherwise).
 template <typename T>
 cudaError_t apply_one(const ApplyData<T>& d, const T* u, T* out, cudaStream_t st, cudaEvent_t* ev = nullptr);
+
+// out = A u for nr right-hand sides at once (nr in {1, 2, 4} for complex128,
+// {1, 2, 4, 8} for complex64; u, out: nr vectors of length N one after
+// another): one pass over the near-field weights serves all of them.  The work
+// arrays must hold max_rhs right-hand sides.
+template <typename T>
+cudaError_t apply_batch(const ApplyData<T>& d, const T* u, T* out, int nr, cudaStream_t st,
+                        cudaEvent_t* ev = nullptr);
+constexpr int kMaxRhs64 = 4, kMaxRhs32 = 8;
 
 // 2-D FFT of an M x M array in place (rows then columns), forward or inverse
 // (unscaled).

@@ -98,6 +98,18 @@ def test_multi_rhs_apply_equals_single(disc):
         assert np.array_equal(many[r], one)
 
 
+def test_batched_complex64_apply_equals_single(kite):
+    """Eight right-hand sides in one pass over the weights give exactly the
+    single-RHS results (same summation order per RHS)."""
+    from paper_1509_05063_gb300 import LS_MIXED
+    U = W.random_density(kite.dz.N, nrhs=8, seed=W.SEED + 11)
+    Ud = kite.dev(U, torch.complex64)
+    many = kite.plan.apply(Ud, prec=LS_MIXED).cpu().numpy()
+    for r in (0, 5, 7):
+        one = kite.plan.apply(kite.dev(U[r], torch.complex64), prec=LS_MIXED).cpu().numpy()
+        assert np.array_equal(many[r], one)
+
+
 @pytest.mark.parametrize("name", ["disc", "kite"])
 def test_mixed_apply_within_bound(name, request):
     c = request.getfixturevalue(name)
