@@ -299,11 +299,21 @@ def main():
         barrier()
         t32 = time.perf_counter() - t0
         diff = float(torch.linalg.vector_norm(s32 - s64) / torch.linalg.vector_norm(s64))
+        # block right-hand sides: 8 incident directions theta_j = 2 pi j / 8 in lock-step
+        th = [2 * math.pi * j / 8 for j in range(8)]
+        UI = torch.from_numpy(np.stack([W.plane_wave(wl.kappa, (math.cos(t), math.sin(t)), xy) for t in th])).to(dev)
+        barrier()
+        t0 = time.perf_counter()
+        sb32, ib32 = plan.solve(UI, tol=1e-10, prec=LS_MIXED, max_iter=800, restart=100)
+        barrier()
+        tb32 = time.perf_counter() - t0
         solve = {"tol": 1e-10, "fp64_s": t64, "fp64_iterations": i64["iterations"],
                  "fp64_residual": i64["residual"], "fp64_converged": i64["converged"],
                  "mixed_s": t32, "mixed_inner_iterations": i32["iterations"],
                  "mixed_refinements": i32["refinements"], "mixed_residual": i32["residual"],
-                 "mixed_converged": i32["converged"], "mixed_vs_fp64_solution_rel": diff}
+                 "mixed_converged": i32["converged"], "mixed_vs_fp64_solution_rel": diff,
+                 "mixed_8rhs_s": tb32, "mixed_8rhs_per_rhs_s": tb32 / 8, "mixed_8rhs_converged": ib32["converged"],
+                 "mixed_8rhs_residual": ib32["residual"], "mixed_8rhs_inner_iterations": ib32["iterations"]}
 
     # roofline of the dominant kernel (near field + local evaluation + assembly)
     nnz = info["nnz_near"]

@@ -34,7 +34,7 @@ struct ls_plan_s {
   // plan-wide device arrays
   double *x = nullptr, *y = nullptr, *ffw = nullptr;
   // solve work space (lazily sized)
-  int ws_restart = -1;
+  int ws_restart = -1, ws_rhs = 0;   // work space grows to the largest request
   double2 *V = nullptr, *w = nullptr, *r = nullptr, *e = nullptr, *cor = nullptr, *h = nullptr, *partial = nullptr;
   double* dnorm = nullptr;
   double* dpartial = nullptr;
@@ -489,108 +489,172 @@ namespace {
 // One GMRES(m) solve of A x = b (FP64 Arnoldi).  op(v, Av) applies the
 // operator.  Stops when the true residual ||b - A x|| / ||b|| <= tol (checked
 // at restarts; inside a cycle the Givens estimate is used).
+// Lock-step GMRES(m) for R right-hand sides (FP64 Arnoldi): every iteration
+// applies the operator to the R current basis vectors in ONE batched call
+// (they sit next to each other: slot-major basis V[j][r][N]), then runs the
+// Arnoldi step of each RHS with one host synchronisation for all of them.
+// Classical Gram-Schmidt with selective re-orthogonalisation (a second pass
+// only when the first removed more than 1 - 1/sqrt(2) of ||w||), Givens
+// rotations on the host, true residual checked at every restart.  op(in, out)
+// applies A to R contiguous vectors.  Stops when every RHS has
+// ||b - A x|| / ||b|| <= tol; iters[r] counts the iterations of RHS r.
 template <typename Op>
-ls_status gmres_fp64(ls_plan plan, Op op, const double2* b, double2* x, double tol, int max_iter, int restart,
-                     cudaStream_t st, int* iters, double* relres) {
+ls_status gmres_batch(ls_plan plan, Op op, int R, const double2* B, double2* X, double tol, int max_iter,
+                      int restart, cudaStream_t st, int* iters, double* relres) {
   const int64_t N = plan->d64.N;
+  const int64_t vs = int64_t(R) * N;                 // stride between basis slots
   double2* V = plan->V;
-  double2* w = plan->w;
-  double2* r = plan->r;
-  auto dnorm = [&](const double2* v, double* out) -> cudaError_t {
-    cudaError_t e = lsd::norm2(v, N, plan->dpartial, plan->dnorm, st);
-    if (e != cudaSuccess) return e;
-    e = cudaMemcpyAsync(out, plan->dnorm, sizeof(double), cudaMemcpyDeviceToHost, st);
+  double2* Wv = plan->w;                             // R vectors
+  double2* Rv = plan->r;                             // R vectors
+  const int m = restart;
+  const int nb = lsd::gram_blocks(N);
+  const int hstride = m + 3;
+  auto h_of = [&](int r) { return plan->h + size_t(r) * hstride; };
+  auto part_of = [&](int r) { return plan->partial + size_t(r) * nb * hstride; };
+  auto dn_of = [&](int r) { return plan->dnorm + r; };
+  auto dp_of = [&](int r) { return plan->dpartial + size_t(r) * nb; };
+  std::vector<double> nrm(R), bnorm(R);
+  auto norms = [&](const double2* base) -> cudaError_t {   // nrm[r] = ||base_r||
+    for (int r = 0; r < R; ++r) {
+      cudaError_t e = lsd::norm2(base + r * N, N, dp_of(r), dn_of(r), st);
+      if (e != cudaSuccess) return e;
+    }
+    cudaError_t e = cudaMemcpyAsync(nrm.data(), plan->dnorm, R * sizeof(double), cudaMemcpyDeviceToHost, st);
     if (e != cudaSuccess) return e;
     return cudaStreamSynchronize(st);
   };
-  double bnorm = 0;
-  LS_CU(dnorm(b, &bnorm));
-  *iters = 0;
-  if (bnorm == 0.0) {
-    LS_CU(cudaMemsetAsync(x, 0, N * sizeof(double2), st));
-    *relres = 0;
-    return LS_OK;
+  LS_CU(norms(B));
+  bnorm = nrm;
+  for (int r = 0; r < R; ++r) {
+    iters[r] = 0;
+    relres[r] = 0;
+    if (bnorm[r] == 0.0) LS_CU(cudaMemsetAsync(X + r * N, 0, N * sizeof(double2), st));
   }
-  const int m = restart;
-  std::vector<cd> H(size_t(m + 1) * m), cs(m), sn(m), g(m + 1), hcol(m + 2);
+  std::vector<std::vector<cd>> H(R, std::vector<cd>(size_t(m + 1) * m)), cs(R, std::vector<cd>(m)),
+      sn(R, std::vector<cd>(m)), g(R, std::vector<cd>(m + 1));
+  std::vector<cd> hcol(size_t(R) * hstride);
+  std::vector<int> k_used(R);
+  std::vector<char> done(R), active(R), again(R);
+  int total = 0;
   for (;;) {
-    LS_CU(op(x, w));
-    LS_CU(lsd::sub(b, w, r, N, st));
-    double beta = 0;
-    LS_CU(dnorm(r, &beta));
-    *relres = beta / bnorm;
-    if (*relres <= tol) return LS_OK;
-    if (*iters >= max_iter) return fail(plan, LS_ERR_NOCONV, "GMRES reached max_iter");
-    LS_CU(lsd::scale_into(r, plan->dnorm, V, N, st));
-    std::fill(H.begin(), H.end(), cd(0));
-    std::fill(g.begin(), g.end(), cd(0));
-    g[0] = beta;
-    int k_used = 0;
+    // true residuals
+    LS_CU(op(X, Wv));
+    LS_CU(lsd::sub(B, Wv, Rv, vs, st));
+    LS_CU(norms(Rv));
+    bool all_done = true;
+    for (int r = 0; r < R; ++r) {
+      relres[r] = bnorm[r] > 0 ? nrm[r] / bnorm[r] : 0.0;
+      done[r] = relres[r] <= tol;
+      all_done = all_done && done[r];
+    }
+    if (all_done) return LS_OK;
+    if (total >= max_iter) return fail(plan, LS_ERR_NOCONV, "GMRES reached max_iter");
+    for (int r = 0; r < R; ++r) {
+      double2* v0 = V + r * N;
+      if (done[r]) {
+        LS_CU(cudaMemsetAsync(v0, 0, N * sizeof(double2), st));
+      } else {
+        LS_CU(lsd::scale_into(Rv + r * N, dn_of(r), v0, N, st));
+        std::fill(H[r].begin(), H[r].end(), cd(0));
+        std::fill(g[r].begin(), g[r].end(), cd(0));
+        g[r][0] = nrm[r];
+      }
+      active[r] = !done[r];
+      k_used[r] = 0;
+    }
     for (int k = 0; k < m; ++k) {
-      LS_CU(op(V + int64_t(k) * N, w));
-      // classical Gram-Schmidt with selective re-orthogonalisation: a second
-      // pass only when the first removed more than 1 - 1/sqrt(2) of ||w||
-      double hk1 = 0;
+      LS_CU(op(V + k * vs, Wv));
+      std::vector<double> hk1(R, 0.0);
+      for (int r = 0; r < R; ++r) again[r] = active[r];
       for (int pass = 0; pass < 2; ++pass) {
-        LS_CU(lsd::gram(V, k + 1, w, N, plan->partial, plan->h, st));
-        LS_CU(lsd::axpy_multi(V, k + 1, plan->h, w, N, st));
-        LS_CU(lsd::norm2(w, N, plan->dpartial, plan->dnorm, st));
-        LS_CU(cudaMemcpyAsync(hcol.data(), plan->h, (k + 2) * sizeof(double2), cudaMemcpyDeviceToHost, st));
-        LS_CU(cudaMemcpyAsync(&hk1, plan->dnorm, sizeof(double), cudaMemcpyDeviceToHost, st));
+        bool any = false;
+        for (int r = 0; r < R; ++r) {
+          if (!again[r]) continue;
+          any = true;
+          LS_CU(lsd::gram(V + r * N, k + 1, vs, Wv + r * N, N, part_of(r), h_of(r), st));
+          LS_CU(lsd::axpy_multi(V + r * N, k + 1, vs, h_of(r), Wv + r * N, N, st));
+          LS_CU(lsd::norm2(Wv + r * N, N, dp_of(r), dn_of(r), st));
+        }
+        if (!any) break;
+        LS_CU(cudaMemcpyAsync(hcol.data(), plan->h, size_t(R) * hstride * sizeof(double2), cudaMemcpyDeviceToHost, st));
+        LS_CU(cudaMemcpyAsync(nrm.data(), plan->dnorm, R * sizeof(double), cudaMemcpyDeviceToHost, st));
         LS_CU(cudaStreamSynchronize(st));
-        for (int j = 0; j <= k; ++j) H[size_t(j) * m + k] += hcol[j];
-        const double before = std::sqrt(std::max(hcol[k + 1].real(), 0.0));
-        if (hk1 >= 0.7071067811865476 * before) break;
+        for (int r = 0; r < R; ++r) {
+          if (!again[r]) continue;
+          for (int j = 0; j <= k; ++j) H[r][size_t(j) * m + k] += hcol[size_t(r) * hstride + j];
+          const double before = std::sqrt(std::max(hcol[size_t(r) * hstride + k + 1].real(), 0.0));
+          hk1[r] = nrm[r];
+          again[r] = hk1[r] < 0.7071067811865476 * before;
+        }
       }
-      H[size_t(k + 1) * m + k] = hk1;
-      LS_CU(lsd::scale_into(w, plan->dnorm, V + int64_t(k + 1) * N, N, st));
-      for (int j = 0; j < k; ++j) {
-        const cd t = std::conj(cs[j]) * H[size_t(j) * m + k] + std::conj(sn[j]) * H[size_t(j + 1) * m + k];
-        H[size_t(j + 1) * m + k] = -sn[j] * H[size_t(j) * m + k] + cs[j] * H[size_t(j + 1) * m + k];
-        H[size_t(j) * m + k] = t;
+      bool any_active = false;
+      for (int r = 0; r < R; ++r) {
+        double2* vn = V + (k + 1) * vs + r * N;
+        if (!active[r]) {
+          LS_CU(cudaMemsetAsync(vn, 0, N * sizeof(double2), st));
+          continue;
+        }
+        std::vector<cd>& Hr = H[r];
+        Hr[size_t(k + 1) * m + k] = hk1[r];
+        LS_CU(lsd::scale_into(Wv + r * N, dn_of(r), vn, N, st));
+        for (int j = 0; j < k; ++j) {
+          const cd t = std::conj(cs[r][j]) * Hr[size_t(j) * m + k] + std::conj(sn[r][j]) * Hr[size_t(j + 1) * m + k];
+          Hr[size_t(j + 1) * m + k] = -sn[r][j] * Hr[size_t(j) * m + k] + cs[r][j] * Hr[size_t(j + 1) * m + k];
+          Hr[size_t(j) * m + k] = t;
+        }
+        const cd a = Hr[size_t(k) * m + k], bb = Hr[size_t(k + 1) * m + k];
+        const double den = std::sqrt(std::norm(a) + std::norm(bb));
+        cs[r][k] = den > 0 ? a / den : cd(1);
+        sn[r][k] = den > 0 ? bb / den : cd(0);
+        Hr[size_t(k) * m + k] = den;
+        Hr[size_t(k + 1) * m + k] = 0;
+        g[r][k + 1] = -sn[r][k] * g[r][k];
+        g[r][k] = std::conj(cs[r][k]) * g[r][k];
+        ++iters[r];
+        k_used[r] = k + 1;
+        if (std::abs(g[r][k + 1]) / bnorm[r] <= tol || hk1[r] == 0.0) active[r] = 0;
+        any_active = any_active || active[r];
       }
-      const cd a = H[size_t(k) * m + k], bb = H[size_t(k + 1) * m + k];
-      const double den = std::sqrt(std::norm(a) + std::norm(bb));
-      cs[k] = den > 0 ? a / den : cd(1);
-      sn[k] = den > 0 ? bb / den : cd(0);
-      H[size_t(k) * m + k] = den;
-      H[size_t(k + 1) * m + k] = 0;
-      g[k + 1] = -sn[k] * g[k];
-      g[k] = std::conj(cs[k]) * g[k];
-      ++*iters;
-      k_used = k + 1;
-      if (std::abs(g[k + 1]) / bnorm <= tol || *iters >= max_iter || hk1 == 0.0) break;
+      ++total;
+      if (!any_active || total >= max_iter) break;
     }
-    // back substitution, x += V y
-    std::vector<cd> y(k_used);
-    for (int i = k_used - 1; i >= 0; --i) {
-      cd s = g[i];
-      for (int j = i + 1; j < k_used; ++j) s -= H[size_t(i) * m + j] * y[j];
-      y[i] = s / H[size_t(i) * m + i];
+    // back substitution and x_r += V_r y_r
+    for (int r = 0; r < R; ++r) {
+      const int ku = k_used[r];
+      if (done[r] || ku == 0) continue;
+      std::vector<cd> y(ku);
+      for (int i = ku - 1; i >= 0; --i) {
+        cd sacc = g[r][i];
+        for (int j = i + 1; j < ku; ++j) sacc -= H[r][size_t(i) * m + j] * y[j];
+        y[i] = sacc / H[r][size_t(i) * m + i];
+      }
+      LS_CU(cudaMemcpyAsync(h_of(r), y.data(), ku * sizeof(double2), cudaMemcpyHostToDevice, st));
+      LS_CU(lsd::combine(V + r * N, ku, vs, h_of(r), X + r * N, N, st));
     }
-    LS_CU(cudaMemcpyAsync(plan->h, y.data(), k_used * sizeof(double2), cudaMemcpyHostToDevice, st));
-    LS_CU(lsd::combine(V, k_used, plan->h, x, N, st));
   }
 }
 
-ls_status ensure_workspace(ls_plan plan, int restart) {
-  if (plan->ws_restart >= restart) return LS_OK;
-  if (plan->ws_restart >= 0) return fail(plan, LS_ERR_INVALID, "restart larger than the first solve's is not supported");
+ls_status ensure_workspace(ls_plan plan, int restart, int R) {
+  if (plan->ws_restart >= restart && plan->ws_rhs >= R) return LS_OK;
   const int64_t N = plan->d64.N;
+  restart = std::max(restart, plan->ws_restart);
+  R = std::max(R, plan->ws_rhs);
   ls_status st = LS_OK;
-  plan->V = plan->alloc<double2>(size_t(restart + 1) * N, &st);
-  plan->w = plan->alloc<double2>(N, &st);
-  plan->r = plan->alloc<double2>(N, &st);
-  plan->e = plan->alloc<double2>(N, &st);
-  plan->cor = plan->alloc<double2>(N, &st);
-  plan->h = plan->alloc<double2>(restart + 3, &st);
-  plan->partial = plan->alloc<double2>(size_t(lsd::gram_blocks(N)) * (restart + 3), &st);
-  plan->dnorm = plan->alloc<double>(1, &st);
-  plan->dpartial = plan->alloc<double>(lsd::gram_blocks(N), &st);
-  plan->c64a = plan->alloc<float2>(N, &st);
-  plan->c64b = plan->alloc<float2>(N, &st);
+  const int nb = lsd::gram_blocks(N);
+  plan->V = plan->alloc<double2>(size_t(restart + 1) * R * N, &st);
+  plan->w = plan->alloc<double2>(size_t(R) * N, &st);
+  plan->r = plan->alloc<double2>(size_t(R) * N, &st);
+  plan->e = plan->alloc<double2>(size_t(R) * N, &st);
+  plan->cor = plan->alloc<double2>(size_t(R) * N, &st);
+  plan->h = plan->alloc<double2>(size_t(R) * (restart + 3), &st);
+  plan->partial = plan->alloc<double2>(size_t(R) * nb * (restart + 3), &st);
+  plan->dnorm = plan->alloc<double>(R, &st);
+  plan->dpartial = plan->alloc<double>(size_t(R) * nb, &st);
+  plan->c64a = plan->alloc<float2>(size_t(R) * N, &st);
+  plan->c64b = plan->alloc<float2>(size_t(R) * N, &st);
   if (st != LS_OK) return st;
   plan->ws_restart = restart;
+  plan->ws_rhs = R;
   return LS_OK;
 }
 
@@ -606,46 +670,75 @@ ls_status ls_solve(ls_plan plan, const void* uinc, void* u, int nrhs, double tol
   if (prec != LS_FP64 && prec != LS_MIXED) return fail(plan, LS_ERR_INVALID, "ls_solve: bad precision");
   const auto t0 = std::chrono::steady_clock::now();
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  ls_status s = ensure_workspace(plan, restart);
-  if (s != LS_OK) return s;
   const int64_t N = plan->d64.N;
+  // right-hand sides are solved in lock-step batches sharing one batched apply
+  const int maxb = prec == LS_FP64 ? lsd::kMaxRhs64 : lsd::kMaxRhs32;
+  const int Rb = std::max(1, std::min(nrhs, maxb));
+  ls_status s = ensure_workspace(plan, restart, Rb);
+  if (s != LS_OK) return s;
   int total_it = 0, total_ref = 0;
   double worst = 0;
-  auto op64 = [&](const double2* v, double2* Av) { return lsd::apply_one(plan->d64, v, Av, st); };
-  auto op32 = [&](const double2* v, double2* Av) {
-    cudaError_t e = lsd::to_c64(v, plan->c64a, N, st);
-    if (e == cudaSuccess) e = lsd::apply_one(plan->d32, plan->c64a, plan->c64b, st);
-    if (e == cudaSuccess) e = lsd::to_c128(plan->c64b, Av, N, st);
-    return e;
+  // FP64 apply of R contiguous vectors (chunks of at most kMaxRhs64)
+  auto op64 = [&](int R) {
+    return [&, R](const double2* v, double2* Av) -> cudaError_t {
+      for (int r = 0; r < R;) {
+        int nr = lsd::kMaxRhs64;
+        while (nr > R - r) nr /= 2;
+        cudaError_t e = lsd::apply_batch(plan->d64, v + r * N, Av + r * N, nr, st);
+        if (e != cudaSuccess) return e;
+        r += nr;
+      }
+      return cudaSuccess;
+    };
+  };
+  // complex64 apply of R contiguous complex128 vectors (cast in, batched apply, cast out)
+  auto op32 = [&](int R) {
+    return [&, R](const double2* v, double2* Av) -> cudaError_t {
+      cudaError_t e = lsd::to_c64(v, plan->c64a, int64_t(R) * N, st);
+      for (int r = 0; r < R && e == cudaSuccess;) {
+        int nr = lsd::kMaxRhs32;
+        while (nr > R - r) nr /= 2;
+        e = lsd::apply_batch(plan->d32, plan->c64a + r * N, plan->c64b + r * N, nr, st);
+        r += nr;
+      }
+      if (e == cudaSuccess) e = lsd::to_c128(plan->c64b, Av, int64_t(R) * N, st);
+      return e;
+    };
   };
   ls_status result = LS_OK;
-  for (int rh = 0; rh < nrhs; ++rh) {
-    const double2* b = static_cast<const double2*>(uinc) + int64_t(rh) * N;
-    double2* x = static_cast<double2*>(u) + int64_t(rh) * N;
+  std::vector<int> it(Rb);
+  std::vector<double> rr(Rb);
+  for (int r0 = 0; r0 < nrhs; r0 += Rb) {
+    const int R = std::min(Rb, nrhs - r0);
+    const double2* B = static_cast<const double2*>(uinc) + int64_t(r0) * N;
+    double2* X = static_cast<double2*>(u) + int64_t(r0) * N;
     if (prec == LS_FP64) {
-      int it = 0;
-      double rr = 0;
-      s = gmres_fp64(plan, op64, b, x, tol, max_iter, restart, st, &it, &rr);
-      total_it += it;
-      worst = std::max(worst, rr);
+      s = gmres_batch(plan, op64(R), R, B, X, tol, max_iter, restart, st, it.data(), rr.data());
+      for (int r = 0; r < R; ++r) { total_it += it[r]; worst = std::max(worst, rr[r]); }
       if (s != LS_OK) { result = s; if (s != LS_ERR_NOCONV) break; }
     } else {
       // FP64 iterative refinement around complex64 GMRES corrections:
       // r = b - A_64 x (FP64), solve A_32 c = r to a loose tolerance, x += c.
-      double bnorm = 0, rnorm = 0;
-      double2* rres = plan->e;
-      double2* cor = plan->cor;
-      LS_CU(lsd::norm2(b, N, plan->dpartial, plan->dnorm, st));
-      LS_CU(cudaMemcpyAsync(&bnorm, plan->dnorm, sizeof(double), cudaMemcpyDeviceToHost, st));
-      LS_CU(cudaStreamSynchronize(st));
+      double2* Res = plan->e;
+      double2* Cor = plan->cor;
+      std::vector<double> bn(R), rn(R);
+      auto norms = [&](const double2* base, std::vector<double>& out) -> cudaError_t {
+        for (int r = 0; r < R; ++r) {
+          cudaError_t e = lsd::norm2(base + r * N, N, plan->dpartial + size_t(r) * lsd::gram_blocks(N),
+                                     plan->dnorm + r, st);
+          if (e != cudaSuccess) return e;
+        }
+        cudaError_t e = cudaMemcpyAsync(out.data(), plan->dnorm, R * sizeof(double), cudaMemcpyDeviceToHost, st);
+        return e == cudaSuccess ? cudaStreamSynchronize(st) : e;
+      };
+      LS_CU(norms(B, bn));
       int inner_total = 0;
       for (int ref = 0;; ++ref) {
-        LS_CU(lsd::apply_one(plan->d64, x, plan->w, st));
-        LS_CU(lsd::sub(b, plan->w, rres, N, st));
-        LS_CU(lsd::norm2(rres, N, plan->dpartial, plan->dnorm, st));
-        LS_CU(cudaMemcpyAsync(&rnorm, plan->dnorm, sizeof(double), cudaMemcpyDeviceToHost, st));
-        LS_CU(cudaStreamSynchronize(st));
-        const double rel = bnorm > 0 ? rnorm / bnorm : 0.0;
+        LS_CU(op64(R)(X, plan->w));
+        LS_CU(lsd::sub(B, plan->w, Res, int64_t(R) * N, st));
+        LS_CU(norms(Res, rn));
+        double rel = 0;
+        for (int r = 0; r < R; ++r) rel = std::max(rel, bn[r] > 0 ? rn[r] / bn[r] : 0.0);
         if (rel <= tol) { worst = std::max(worst, rel); break; }
         if (inner_total >= max_iter || ref >= 50) {
           worst = std::max(worst, rel);
@@ -654,15 +747,15 @@ ls_status ls_solve(ls_plan plan, const void* uinc, void* u, int nrhs, double tol
         }
         total_ref++;
         const double inner_tol = std::max(1e-5, 0.3 * tol / rel);
-        int it = 0;
-        double rr = 0;
-        LS_CU(cudaMemsetAsync(cor, 0, N * sizeof(double2), st));
-        s = gmres_fp64(plan, op32, rres, cor, inner_tol, std::max(1, max_iter - inner_total), restart, st, &it, &rr);
-        inner_total += it;
+        LS_CU(cudaMemsetAsync(Cor, 0, size_t(R) * N * sizeof(double2), st));
+        s = gmres_batch(plan, op32(R), R, Res, Cor, inner_tol, std::max(1, max_iter - inner_total), restart, st,
+                        it.data(), rr.data());
+        int mx = 0;
+        for (int r = 0; r < R; ++r) { total_it += it[r]; mx = std::max(mx, it[r]); }
+        inner_total += mx;
         if (s != LS_OK && s != LS_ERR_NOCONV) return s;
-        LS_CU(lsd::add_inplace(x, cor, N, st));
+        LS_CU(lsd::add_inplace(X, Cor, int64_t(R) * N, st));
       }
-      total_it += inner_total;
     }
   }
   if (info) {

@@ -638,8 +638,9 @@ __device__ __forceinline__ double2 block_sum(double2 v, double2* red) {
 // block owns a contiguous chunk of the index range (w chunk in shared memory),
 // each warp reduces whole vectors with shuffles only.
 __global__ void __launch_bounds__(kRedThreads) k_gram_partial(const double2* __restrict__ V, int nv,
-                                                              const double2* __restrict__ w, int64_t N,
-                                                              int64_t chunk, double2* __restrict__ partial) {
+                                                              int64_t vstride, const double2* __restrict__ w,
+                                                              int64_t N, int64_t chunk,
+                                                              double2* __restrict__ partial) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double2* ws = reinterpret_cast<double2*>(smem_raw);
   const int64_t i0 = int64_t(blockIdx.x) * chunk;
@@ -650,7 +651,7 @@ __global__ void __launch_bounds__(kRedThreads) k_gram_partial(const double2* __r
   for (int j = warp; j <= nv; j += nw) {
     double2 acc = make_double2(0, 0);
     if (j < nv) {
-      const double2* vj = V + int64_t(j) * N + i0;
+      const double2* vj = V + int64_t(j) * vstride + i0;
       double2 a1 = make_double2(0, 0), a2 = make_double2(0, 0), a3 = make_double2(0, 0);
       int i = lane;
       for (; i + 96 < n; i += 128) {
@@ -684,8 +685,8 @@ static int64_t gram_chunk(int64_t N) {
   return (N + nb - 1) / nb;
 }
 
-cudaError_t gram(const double2* V, int nv, const double2* w, int64_t N, double2* partial, double2* h,
-                 cudaStream_t st) {
+cudaError_t gram(const double2* V, int nv, int64_t vstride, const double2* w, int64_t N, double2* partial,
+                 double2* h, cudaStream_t st) {
   const int nb = gram_blocks(N);
   const int64_t chunk = gram_chunk(N);
   static bool attr = false;
@@ -693,12 +694,12 @@ cudaError_t gram(const double2* V, int nv, const double2* w, int64_t N, double2*
     cudaFuncSetAttribute(k_gram_partial, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
     attr = true;
   }
-  k_gram_partial<<<nb, kRedThreads, chunk * sizeof(double2), st>>>(V, nv, w, N, chunk, partial);
+  k_gram_partial<<<nb, kRedThreads, chunk * sizeof(double2), st>>>(V, nv, vstride, w, N, chunk, partial);
   k_gram_reduce<<<nv + 1, 32, 0, st>>>(partial, nb, nv + 1, h);
   return cudaGetLastError();
 }
 
-__global__ void __launch_bounds__(256) k_axpy_multi(const double2* __restrict__ V, int nv,
+__global__ void __launch_bounds__(256) k_axpy_multi(const double2* __restrict__ V, int nv, int64_t vstride,
                                                     const double2* __restrict__ h, double2* __restrict__ w,
                                                     int64_t N) {
   for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < N; i += int64_t(gridDim.x) * blockDim.x) {
@@ -706,7 +707,7 @@ __global__ void __launch_bounds__(256) k_axpy_multi(const double2* __restrict__ 
 #pragma unroll 4
     for (int j = 0; j < nv; ++j) {
       const double2 hj = h[j];
-      const double2 v = V[int64_t(j) * N + i];
+      const double2 v = V[int64_t(j) * vstride + i];
       acc = csub(acc, cmul(hj, v));
     }
     w[i] = acc;
@@ -719,8 +720,9 @@ static unsigned grid_for(int64_t N) {
   return unsigned(b < 1 ? 1 : b);
 }
 
-cudaError_t axpy_multi(const double2* V, int nv, const double2* h, double2* w, int64_t N, cudaStream_t st) {
-  k_axpy_multi<<<grid_for(N), 256, 0, st>>>(V, nv, h, w, N);
+cudaError_t axpy_multi(const double2* V, int nv, int64_t vstride, const double2* h, double2* w, int64_t N,
+                       cudaStream_t st) {
+  k_axpy_multi<<<grid_for(N), 256, 0, st>>>(V, nv, vstride, h, w, N);
   return cudaGetLastError();
 }
 
@@ -760,17 +762,18 @@ cudaError_t scale_into(const double2* w, const double* nrm, double2* v, int64_t 
   return cudaGetLastError();
 }
 
-__global__ void k_combine(const double2* __restrict__ V, int k, const double2* __restrict__ y, double2* __restrict__ x,
-                          int64_t N) {
+__global__ void k_combine(const double2* __restrict__ V, int k, int64_t vstride, const double2* __restrict__ y,
+                          double2* __restrict__ x, int64_t N) {
   for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < N; i += int64_t(gridDim.x) * blockDim.x) {
     double2 acc = x[i];
-    for (int j = 0; j < k; ++j) acc = cfma(y[j], V[int64_t(j) * N + i], acc);
+    for (int j = 0; j < k; ++j) acc = cfma(y[j], V[int64_t(j) * vstride + i], acc);
     x[i] = acc;
   }
 }
 
-cudaError_t combine(const double2* V, int k, const double2* y, double2* x, int64_t N, cudaStream_t st) {
-  k_combine<<<grid_for(N), 256, 0, st>>>(V, k, y, x, N);
+cudaError_t combine(const double2* V, int k, int64_t vstride, const double2* y, double2* x, int64_t N,
+                    cudaStream_t st) {
+  k_combine<<<grid_for(N), 256, 0, st>>>(V, k, vstride, y, x, N);
   return cudaGetLastError();
 }
 

@@ -72,13 +72,15 @@ cudaError_t fft2d(T* x, int M, int logM, const T* tw, bool inverse, cudaStream_t
 // GMRES helpers (complex128).  h[j] = <V_j, w> for j < nv (V: nv vectors of
 // length N, stride N) and h[nv].x = ||w||^2; partial needs blocks * (nv + 1)
 // elements, h needs nv + 1.
-cudaError_t gram(const double2* V, int nv, const double2* w, int64_t N, double2* partial,
+// (basis vector j starts at V + j * vstride)
+cudaError_t gram(const double2* V, int nv, int64_t vstride, const double2* w, int64_t N, double2* partial,
                  double2* h, cudaStream_t st);
-cudaError_t axpy_multi(const double2* V, int nv, const double2* h, double2* w, int64_t N,
+cudaError_t axpy_multi(const double2* V, int nv, int64_t vstride, const double2* h, double2* w, int64_t N,
                        cudaStream_t st);
 cudaError_t norm2(const double2* w, int64_t N, double* partial, double* out, cudaStream_t st);
 cudaError_t scale_into(const double2* w, const double* nrm, double2* v, int64_t N, cudaStream_t st);
-cudaError_t combine(const double2* V, int k, const double2* y, double2* x, int64_t N, cudaStream_t st);
+cudaError_t combine(const double2* V, int k, int64_t vstride, const double2* y, double2* x, int64_t N,
+                    cudaStream_t st);
 cudaError_t sub(const double2* a, const double2* b, double2* out, int64_t N, cudaStream_t st);
 cudaError_t to_c64(const double2* a, float2* b, int64_t N, cudaStream_t st);
 cudaError_t to_c128(const float2* a, double2* b, int64_t N, cudaStream_t st);

@@ -147,6 +147,21 @@ def test_mixed_solve_reaches_fp64_tolerance(disc):
     assert rel(s32.cpu().numpy(), s64.cpu().numpy()) < 1e-8
 
 
+@pytest.mark.parametrize("prec_name", ["fp64", "mixed"])
+def test_lockstep_multi_rhs_solve_equals_single_solves(disc, prec_name):
+    """Three incident directions solved together (one batched apply per
+    iteration, Arnoldi per RHS) give the single-RHS solutions."""
+    from paper_1509_05063_gb300 import LS_FP64, LS_MIXED
+    prec = LS_FP64 if prec_name == "fp64" else LS_MIXED
+    dirs = [(1.0, 0.0), (0.6, 0.8), (-0.28, 0.96)]
+    U = np.stack([W.plane_wave(disc.wl.kappa, d, disc.dz.x) for d in dirs])
+    sol, info = disc.plan.solve(disc.dev(U), tol=1e-10, prec=prec)
+    assert info["converged"] and info["residual"] <= 1e-10
+    for r in range(3):
+        one, _ = disc.plan.solve(disc.dev(U[r]), tol=1e-10, prec=prec)
+        assert rel(sol[r].cpu().numpy(), one.cpu().numpy()) < 1e-12
+
+
 def test_far_field_matches_oracle(disc):
     from paper_1509_05063_gb300 import LS_FP64
     ui = W.plane_wave(disc.wl.kappa, (1, 0), disc.dz.x)
