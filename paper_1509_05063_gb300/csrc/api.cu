@@ -5,7 +5,10 @@
 #include <cmath>
 #include <complex>
 #include <cstring>
+#include <map>
 #include <mutex>
+#include <set>
+#include <tuple>
 #include <string>
 #include <thread>
 #include <vector>
@@ -43,6 +46,13 @@ struct ls_plan_s {
   int dirs_cap = 0;
   ls_plan_info_t info{};
   std::string err;
+  // CUDA graphs of the apply, one per (precision, batch, input, output); the
+  // first call with a key runs directly, the second captures and launches
+  using GraphKey = std::tuple<int, int, const void*, void*>;
+  std::map<GraphKey, cudaGraphExec_t> graphs;
+  std::set<GraphKey> graph_seen;
+  cudaStream_t cap_stream = nullptr;
+  bool graphs_off = false;
   // optional per-stage event timing of ls_apply
   bool timing = false;
   cudaEvent_t ev[lsd::kStages + 1] = {};
@@ -76,6 +86,10 @@ struct ls_plan_s {
     return d;
   }
   void free_all() {
+    for (auto& kv : graphs) cudaGraphExecDestroy(kv.second);
+    graphs.clear();
+    if (cap_stream) cudaStreamDestroy(cap_stream);
+    cap_stream = nullptr;
     for (auto& b : bufs) cudaFree(b.p);
     bufs.clear();
   }
@@ -96,6 +110,48 @@ ls_status fail(ls_plan p, ls_status s, const std::string& m) {
     cudaError_t e_ = (call);                                                             \
     if (e_ != cudaSuccess) return fail(plan, LS_ERR_CUDA, std::string(#call ": ") + cudaGetErrorString(e_)); \
   } while (0)
+
+// Apply through a cached CUDA graph of the whole kernel sequence (direct
+// launches when timing, on the first call of a key, or if capture fails).
+template <typename T>
+cudaError_t run_apply(ls_plan plan, int prec, const lsd::ApplyData<T>& d, const T* u, T* out, int nr,
+                      cudaStream_t st) {
+  if (plan->graphs_off || plan->timing) return lsd::apply_batch(d, u, out, nr, st);
+  const ls_plan_s::GraphKey key(prec, nr, static_cast<const void*>(u), static_cast<void*>(out));
+  auto it = plan->graphs.find(key);
+  if (it != plan->graphs.end()) return cudaGraphLaunch(it->second, st);
+  if (!plan->graph_seen.count(key)) {
+    if (plan->graph_seen.size() > 4096) plan->graph_seen.clear();
+    plan->graph_seen.insert(key);
+    return lsd::apply_batch(d, u, out, nr, st);
+  }
+  if (!plan->cap_stream && cudaStreamCreateWithFlags(&plan->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    plan->graphs_off = true;
+    return lsd::apply_batch(d, u, out, nr, st);
+  }
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t ex = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(plan->cap_stream, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    const cudaError_t e1 = lsd::apply_batch(d, u, out, nr, plan->cap_stream);
+    e = cudaStreamEndCapture(plan->cap_stream, &g);
+    if (e1 != cudaSuccess) e = e1;
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&ex, g, 0);
+  if (g) cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    plan->graphs_off = true;
+    return lsd::apply_batch(d, u, out, nr, st);
+  }
+  if (plan->graphs.size() >= 512) {
+    for (auto& kv : plan->graphs) cudaGraphExecDestroy(kv.second);
+    plan->graphs.clear();
+  }
+  plan->graphs[key] = ex;
+  return cudaGraphLaunch(ex, st);
+}
 
 std::vector<std::complex<float>> to32(const std::vector<cd>& v) {
   std::vector<std::complex<float>> o(v.size());
@@ -461,12 +517,20 @@ ls_status ls_apply(ls_plan plan, const void* u, void* Au, int nrhs, ls_precision
     int nr = maxr;                       // largest power of two batch that fits
     while (nr > nrhs - r) nr /= 2;
     cudaError_t e;
-    if (prec == LS_FP64)
-      e = lsd::apply_batch(plan->d64, static_cast<const double2*>(u) + r * N, static_cast<double2*>(Au) + r * N, nr,
-                           st, ev);
-    else
-      e = lsd::apply_batch(plan->d32, static_cast<const float2*>(u) + r * N, static_cast<float2*>(Au) + r * N, nr,
-                           st, ev);
+    if (ev) {
+      if (prec == LS_FP64)
+        e = lsd::apply_batch(plan->d64, static_cast<const double2*>(u) + r * N, static_cast<double2*>(Au) + r * N,
+                             nr, st, ev);
+      else
+        e = lsd::apply_batch(plan->d32, static_cast<const float2*>(u) + r * N, static_cast<float2*>(Au) + r * N, nr,
+                             st, ev);
+    } else if (prec == LS_FP64) {
+      e = run_apply(plan, prec, plan->d64, static_cast<const double2*>(u) + r * N, static_cast<double2*>(Au) + r * N,
+                    nr, st);
+    } else {
+      e = run_apply(plan, prec, plan->d32, static_cast<const float2*>(u) + r * N, static_cast<float2*>(Au) + r * N,
+                    nr, st);
+    }
     r += nr;
     if (e != cudaSuccess) return fail(plan, LS_ERR_CUDA, std::string("ls_apply: ") + cudaGetErrorString(e));
     if (ev) {
@@ -684,7 +748,7 @@ ls_status ls_solve(ls_plan plan, const void* uinc, void* u, int nrhs, double tol
       for (int r = 0; r < R;) {
         int nr = lsd::kMaxRhs64;
         while (nr > R - r) nr /= 2;
-        cudaError_t e = lsd::apply_batch(plan->d64, v + r * N, Av + r * N, nr, st);
+        cudaError_t e = run_apply(plan, LS_FP64, plan->d64, v + r * N, Av + r * N, nr, st);
         if (e != cudaSuccess) return e;
         r += nr;
       }
@@ -698,7 +762,7 @@ ls_status ls_solve(ls_plan plan, const void* uinc, void* u, int nrhs, double tol
       for (int r = 0; r < R && e == cudaSuccess;) {
         int nr = lsd::kMaxRhs32;
         while (nr > R - r) nr /= 2;
-        e = lsd::apply_batch(plan->d32, plan->c64a + r * N, plan->c64b + r * N, nr, st);
+        e = run_apply(plan, LS_MIXED, plan->d32, plan->c64a + r * N, plan->c64b + r * N, nr, st);
         r += nr;
       }
       if (e == cudaSuccess) e = lsd::to_c128(plan->c64b, Av, int64_t(R) * N, st);
