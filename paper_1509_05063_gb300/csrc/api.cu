@@ -39,9 +39,12 @@ struct ls_plan_s {
   // solve work space (lazily sized)
   int ws_restart = -1, ws_rhs = 0;   // work space grows to the largest request
   double2 *V = nullptr, *w = nullptr, *r = nullptr, *e = nullptr, *cor = nullptr, *h = nullptr, *partial = nullptr;
+  double2* apart = nullptr;     // kAxpyGroups x N partial sums of the Arnoldi update
   double* dnorm = nullptr;
   double* dpartial = nullptr;
   float2 *c64a = nullptr, *c64b = nullptr;
+  double2* pin_h = nullptr;     // pinned host copies of h and the norms (async D2H)
+  double* pin_n = nullptr;
   double* dirs = nullptr;
   int dirs_cap = 0;
   ls_plan_info_t info{};
@@ -86,6 +89,10 @@ struct ls_plan_s {
     return d;
   }
   void free_all() {
+    if (pin_h) cudaFreeHost(pin_h);
+    if (pin_n) cudaFreeHost(pin_n);
+    pin_h = nullptr;
+    pin_n = nullptr;
     for (auto& kv : graphs) cudaGraphExecDestroy(kv.second);
     graphs.clear();
     if (cap_stream) cudaStreamDestroy(cap_stream);
@@ -577,18 +584,19 @@ ls_status gmres_batch(ls_plan plan, Op op, int R, const double2* B, double2* X, 
   auto part_of = [&](int r) { return plan->partial + size_t(r) * nb * hstride; };
   auto dn_of = [&](int r) { return plan->dnorm + r; };
   auto dp_of = [&](int r) { return plan->dpartial + size_t(r) * nb; };
-  std::vector<double> nrm(R), bnorm(R);
+  double* nrm = plan->pin_n;                         // pinned: asynchronous copies
+  std::vector<double> bnorm(R);
   auto norms = [&](const double2* base) -> cudaError_t {   // nrm[r] = ||base_r||
     for (int r = 0; r < R; ++r) {
       cudaError_t e = lsd::norm2(base + r * N, N, dp_of(r), dn_of(r), st);
       if (e != cudaSuccess) return e;
     }
-    cudaError_t e = cudaMemcpyAsync(nrm.data(), plan->dnorm, R * sizeof(double), cudaMemcpyDeviceToHost, st);
+    cudaError_t e = cudaMemcpyAsync(nrm, plan->dnorm, R * sizeof(double), cudaMemcpyDeviceToHost, st);
     if (e != cudaSuccess) return e;
     return cudaStreamSynchronize(st);
   };
   LS_CU(norms(B));
-  bnorm = nrm;
+  bnorm.assign(nrm, nrm + R);
   for (int r = 0; r < R; ++r) {
     iters[r] = 0;
     relres[r] = 0;
@@ -596,7 +604,7 @@ ls_status gmres_batch(ls_plan plan, Op op, int R, const double2* B, double2* X, 
   }
   std::vector<std::vector<cd>> H(R, std::vector<cd>(size_t(m + 1) * m)), cs(R, std::vector<cd>(m)),
       sn(R, std::vector<cd>(m)), g(R, std::vector<cd>(m + 1));
-  std::vector<cd> hcol(size_t(R) * hstride);
+  cd* hcol = reinterpret_cast<cd*>(plan->pin_h);
   std::vector<int> k_used(R);
   std::vector<char> done(R), active(R), again(R);
   int total = 0;
@@ -636,12 +644,12 @@ ls_status gmres_batch(ls_plan plan, Op op, int R, const double2* B, double2* X, 
           if (!again[r]) continue;
           any = true;
           LS_CU(lsd::gram(V + r * N, k + 1, vs, Wv + r * N, N, part_of(r), h_of(r), st));
-          LS_CU(lsd::axpy_multi(V + r * N, k + 1, vs, h_of(r), Wv + r * N, N, st));
+          LS_CU(lsd::axpy_multi(V + r * N, k + 1, vs, h_of(r), Wv + r * N, plan->apart, N, st));
           LS_CU(lsd::norm2(Wv + r * N, N, dp_of(r), dn_of(r), st));
         }
         if (!any) break;
-        LS_CU(cudaMemcpyAsync(hcol.data(), plan->h, size_t(R) * hstride * sizeof(double2), cudaMemcpyDeviceToHost, st));
-        LS_CU(cudaMemcpyAsync(nrm.data(), plan->dnorm, R * sizeof(double), cudaMemcpyDeviceToHost, st));
+        LS_CU(cudaMemcpyAsync(hcol, plan->h, size_t(R) * hstride * sizeof(double2), cudaMemcpyDeviceToHost, st));
+        LS_CU(cudaMemcpyAsync(nrm, plan->dnorm, R * sizeof(double), cudaMemcpyDeviceToHost, st));
         LS_CU(cudaStreamSynchronize(st));
         for (int r = 0; r < R; ++r) {
           if (!again[r]) continue;
@@ -710,6 +718,7 @@ ls_status ensure_workspace(ls_plan plan, int restart, int R) {
   plan->r = plan->alloc<double2>(size_t(R) * N, &st);
   plan->e = plan->alloc<double2>(size_t(R) * N, &st);
   plan->cor = plan->alloc<double2>(size_t(R) * N, &st);
+  plan->apart = plan->alloc<double2>(size_t(lsd::kAxpyGroups) * N, &st);
   plan->h = plan->alloc<double2>(size_t(R) * (restart + 3), &st);
   plan->partial = plan->alloc<double2>(size_t(R) * nb * (restart + 3), &st);
   plan->dnorm = plan->alloc<double>(R, &st);
@@ -717,6 +726,15 @@ ls_status ensure_workspace(ls_plan plan, int restart, int R) {
   plan->c64a = plan->alloc<float2>(size_t(R) * N, &st);
   plan->c64b = plan->alloc<float2>(size_t(R) * N, &st);
   if (st != LS_OK) return st;
+  if (plan->pin_h) cudaFreeHost(plan->pin_h);
+  if (plan->pin_n) cudaFreeHost(plan->pin_n);
+  plan->pin_h = nullptr;
+  plan->pin_n = nullptr;
+  if (cudaMallocHost(&plan->pin_h, size_t(R) * (restart + 3) * sizeof(double2)) != cudaSuccess ||
+      cudaMallocHost(&plan->pin_n, size_t(R) * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(plan, LS_ERR_NOMEM, "pinned host staging");
+  }
   plan->ws_restart = restart;
   plan->ws_rhs = R;
   return LS_OK;

@@ -611,10 +611,10 @@ template cudaError_t fft2d<float2>(float2*, int, int, const float2*, bool, cudaS
 // ------------------------------------------------------------ GMRES helpers
 constexpr int kRedThreads = 256;
 
-// 2 blocks per SM, each owning at most 4096 elements (64 KB of shared memory)
+// chunks of about 1024 elements (16 KB of shared memory), at least 64 each
 int gram_blocks(int64_t N) {
-  int64_t b = 304;
-  if (N < 304 * 64) b = (N + 63) / 64;
+  int64_t b = (N + 1023) / 1024;
+  if (b > 4096) b = 4096;
   if ((N + b - 1) / b > 4096) b = (N + 4095) / 4096;
   if (b < 1) b = 1;
   return int(b);
@@ -648,7 +648,7 @@ __global__ void __launch_bounds__(kRedThreads) k_gram_partial(const double2* __r
   for (int i = threadIdx.x; i < n; i += blockDim.x) ws[i] = w[i0 + i];
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  for (int j = warp; j <= nv; j += nw) {
+  for (int j = blockIdx.y * nw + warp; j <= nv && j < (blockIdx.y + 1) * nw; j += nw) {
     double2 acc = make_double2(0, 0);
     if (j < nv) {
       const double2* vj = V + int64_t(j) * vstride + i0;
@@ -694,23 +694,42 @@ cudaError_t gram(const double2* V, int nv, int64_t vstride, const double2* w, in
     cudaFuncSetAttribute(k_gram_partial, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
     attr = true;
   }
-  k_gram_partial<<<nb, kRedThreads, chunk * sizeof(double2), st>>>(V, nv, vstride, w, N, chunk, partial);
+  // blockIdx.y selects 8 of the nv + 1 dot products: enough warps to hide the
+  // FP64 latency (the complex multiply-adds of this kernel run on GB300's
+  // narrow FP64 pipe)
+  const int ng = (nv + 1 + kRedThreads / 32 - 1) / (kRedThreads / 32);
+  k_gram_partial<<<dim3(nb, ng), kRedThreads, chunk * sizeof(double2), st>>>(V, nv, vstride, w, N, chunk, partial);
   k_gram_reduce<<<nv + 1, 32, 0, st>>>(partial, nb, nv + 1, h);
   return cudaGetLastError();
 }
 
+// w -= sum_j h_j V_j, the sum over j split into G groups (blockIdx.y) so that
+// G x N threads keep GB300's FP64 pipe and HBM busy; group sums go to
+// part[g][i] and k_axpy_finish adds them in a fixed order (deterministic).
 __global__ void __launch_bounds__(256) k_axpy_multi(const double2* __restrict__ V, int nv, int64_t vstride,
-                                                    const double2* __restrict__ h, double2* __restrict__ w,
+                                                    const double2* __restrict__ h, double2* __restrict__ part,
                                                     int64_t N) {
+  const int G = gridDim.y, g = blockIdx.y;
+  const int j0 = (nv * g) / G, j1 = (nv * (g + 1)) / G;
   for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < N; i += int64_t(gridDim.x) * blockDim.x) {
-    double2 acc = w[i];
-#pragma unroll 4
-    for (int j = 0; j < nv; ++j) {
-      const double2 hj = h[j];
-      const double2 v = V[int64_t(j) * vstride + i];
-      acc = csub(acc, cmul(hj, v));
+    double2 a0 = make_double2(0, 0), a1 = make_double2(0, 0);
+    int j = j0;
+    for (; j + 1 < j1; j += 2) {
+      const double2 v0 = V[int64_t(j) * vstride + i], v1 = V[int64_t(j + 1) * vstride + i];
+      a0 = cfma(h[j], v0, a0);
+      a1 = cfma(h[j + 1], v1, a1);
     }
-    w[i] = acc;
+    if (j < j1) a0 = cfma(h[j], V[int64_t(j) * vstride + i], a0);
+    part[int64_t(g) * N + i] = cadd(a0, a1);
+  }
+}
+
+__global__ void __launch_bounds__(256) k_axpy_finish(const double2* __restrict__ part, int G, double2* __restrict__ w,
+                                                     int64_t N) {
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < N; i += int64_t(gridDim.x) * blockDim.x) {
+    double2 s = part[i];
+    for (int g = 1; g < G; ++g) s = cadd(s, part[int64_t(g) * N + i]);
+    w[i] = csub(w[i], s);
   }
 }
 
@@ -720,9 +739,11 @@ static unsigned grid_for(int64_t N) {
   return unsigned(b < 1 ? 1 : b);
 }
 
-cudaError_t axpy_multi(const double2* V, int nv, int64_t vstride, const double2* h, double2* w, int64_t N,
-                       cudaStream_t st) {
-  k_axpy_multi<<<grid_for(N), 256, 0, st>>>(V, nv, vstride, h, w, N);
+cudaError_t axpy_multi(const double2* V, int nv, int64_t vstride, const double2* h, double2* w, double2* part,
+                       int64_t N, cudaStream_t st) {
+  const int G = nv >= 32 ? kAxpyGroups : (nv >= 8 ? 2 : 1);
+  k_axpy_multi<<<dim3(grid_for(N), G), 256, 0, st>>>(V, nv, vstride, h, part, N);
+  k_axpy_finish<<<grid_for(N), 256, 0, st>>>(part, G, w, N);
   return cudaGetLastError();
 }
 

@@ -75,8 +75,10 @@ cudaError_t fft2d(T* x, int M, int logM, const T* tw, bool inverse, cudaStream_t
 // (basis vector j starts at V + j * vstride)
 cudaError_t gram(const double2* V, int nv, int64_t vstride, const double2* w, int64_t N, double2* partial,
                  double2* h, cudaStream_t st);
-cudaError_t axpy_multi(const double2* V, int nv, int64_t vstride, const double2* h, double2* w, int64_t N,
-                       cudaStream_t st);
+// w -= sum_j h_j V_j; part needs kAxpyGroups x N elements of scratch
+constexpr int kAxpyGroups = 4;
+cudaError_t axpy_multi(const double2* V, int nv, int64_t vstride, const double2* h, double2* w, double2* part,
+                       int64_t N, cudaStream_t st);
 cudaError_t norm2(const double2* w, int64_t N, double* partial, double* out, cudaStream_t st);
 cudaError_t scale_into(const double2* w, const double* nrm, double2* v, int64_t N, cudaStream_t st);
 cudaError_t combine(const double2* V, int k, int64_t vstride, const double2* y, double2* x, int64_t N,
