@@ -190,6 +190,8 @@ def main():
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--cpu-rows", type=int, default=192)
     ap.add_argument("--ref-rows", type=int, default=48)
+    ap.add_argument("--autotune", action="store_true",
+                    help="pick the cell layout with the autotuner (model + GPU timing of the best 3)")
     ap.add_argument("--scale", type=int, default=1,
                     help="coarsen config 2 by this factor (h, cells) for profiling captures")
     args = ap.parse_args()
@@ -211,7 +213,10 @@ def main():
     dev = torch.device("cuda", local)
 
     sc = args.scale
-    wl = W.cfg2(h=0.0045 * sc, n1=3200 // sc, L=56 // sc)
+    wl = W.cfg2(h=0.0045 * sc, n1=3200 // sc, L=61 // sc)
+    if args.autotune:
+        from paper_1509_05063_gb300 import autotune
+        wl, _ = autotune.tune(wl, W.n2_of(wl), target_eps=1e-9, measure_top=3)
     plan = Plan(wl, W.n2_of(wl))
     info = plan.info
     N = plan.N

@@ -78,7 +78,9 @@ typedef struct {
 
 /* Quadrature (Section 3.1) and accelerator (Section 3.2) parameters.  Radii
  * are in grid-index units.  The accelerator uses L x L cells of side H whose
- * lower-left corner is (box_x0, box_y0), N_eq lattice intervals per cell side,
+ * lower-left corner is (box_x0, box_y0) (L <= 0: the plan chooses the box to
+ * cover all nodes, faces half a Cartesian spacing off the grid lines, and
+ * ignores box_x0 / box_y0), N_eq lattice intervals per cell side,
  * a Fourier-Bessel local expansion of order n_fb and n_coll collocation points
  * (0 = 16 (N_eq + 1)).  eta must vanish outside the 3 x 3 cell block of every
  * target (checked; LS_ERR_INVALID otherwise). */
@@ -131,6 +133,16 @@ ls_status ls_plan_create(const ls_geometry* geom, ls_n2_fn n2, void* ctx, double
                          const ls_options* opt, ls_plan* out);
 
 ls_status ls_plan_info(ls_plan plan, ls_plan_info_t* info);
+
+/* Cheap check of a cell layout without building the plan (used by the
+ * autotuner): builds the nodes, checks the lattice size and kappa H, and that
+ * every node's cut-off support lies in its 3 x 3 cell block (Section 3, the
+ * condition supp eta in N(x)).  out (7 doubles): N, occupied cells, near-field
+ * block entries streamed per apply, lattice FFT size M, L, box_x0, box_y0.
+ * LS_ERR_INVALID with the reason in ls_last_error(NULL) when the layout is
+ * not usable. */
+ls_status ls_check_cells(const ls_geometry* geom, ls_n2_fn n2, void* ctx, double kappa,
+                         const ls_options* opt, double* out);
 
 /* Node coordinates (host array of 2 N doubles, x then y per node) and the
  * canonical id of every node (host array of N int64, may be NULL): collar node

@@ -176,7 +176,7 @@ ls_status validate(const ls_geometry* g, const ls_options* o, double kappa) {
   if (o->Q < 2 || o->Q > 5 || o->p < 1 || o->p > 15 || o->R_a <= 0 || o->R_b <= 0 || o->R_cart <= 0)
     return LS_ERR_INVALID;
   if (o->M < 0 || o->N_tau < 4 || o->q_polar < 1 || o->n_rho < 2 || o->n_theta < 4) return LS_ERR_INVALID;
-  if (o->L < 1 || o->N_eq < 2 || o->H <= 0 || o->n_fb < 0) return LS_ERR_INVALID;
+  if (o->N_eq < 2 || o->H <= 0 || o->n_fb < 0) return LS_ERR_INVALID;   // L <= 0: box chosen by the plan
   if (!(o->chi_s0 >= 0 && o->chi_s0 < 1)) return LS_ERR_INVALID;
   return LS_OK;
 }
@@ -222,6 +222,40 @@ ls_status ls_host_plan_create(const ls_geometry* geom, ls_n2_fn n2, void* ctx, d
     return fail(nullptr, s, m);
   }
   *out = h;
+  return LS_OK;
+}
+
+ls_status ls_check_cells(const ls_geometry* geom, ls_n2_fn n2, void* ctx, double kappa, const ls_options* opt,
+                         double* out) {
+  if (!out) return fail(nullptr, LS_ERR_INVALID, "out is NULL");
+  const ls_status v = validate(geom, opt, kappa);
+  if (v != LS_OK) return fail(nullptr, v, "invalid geometry or options");
+  lsh::Plan2D P;
+  P.geo.g = *geom;
+  P.opt = *opt;
+  P.kappa = kappa;
+  P.n_threads = opt->n_threads > 0 ? opt->n_threads : int(std::max(1u, std::thread::hardware_concurrency()));
+  int64_t entries = 0;
+  try {
+    if (!lsh::build_nodes(P, n2, ctx)) return fail(nullptr, LS_ERR_INVALID, P.err);
+    const int nlat = P.opt.L * P.opt.N_eq + 1;
+    int M = 256;
+    while (M < 2 * nlat - 1) M *= 2;
+    if (M > 2048) return fail(nullptr, LS_ERR_INVALID, "lattice too large: need 2 (L N_eq + 1) - 1 <= 2048");
+    if (kappa * P.opt.H / std::sqrt(2.0) >= 2.4) return fail(nullptr, LS_ERR_INVALID, "kappa H / sqrt 2 must stay below 2.4");
+    if (!lsh::check_cells(P, &entries)) return fail(nullptr, LS_ERR_INVALID, P.err);
+    int nocc = 0;
+    for (int c = 0; c < P.opt.L * P.opt.L; ++c) nocc += P.nodes.cell_start[c + 1] > P.nodes.cell_start[c];
+    out[0] = double(P.nodes.N);
+    out[1] = nocc;
+    out[2] = double(entries);
+    out[3] = M;
+    out[4] = P.opt.L;
+    out[5] = P.opt.box_x0;
+    out[6] = P.opt.box_y0;
+  } catch (const std::bad_alloc&) {
+    return fail(nullptr, LS_ERR_NOMEM, "host allocation failed");
+  }
   return LS_OK;
 }
 

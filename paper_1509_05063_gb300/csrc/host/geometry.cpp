@@ -275,13 +275,29 @@ bool build_nodes(Plan2D& plan, ls_n2_fn n2fn, void* ctx) {
   if (!n2fn) { plan.err = "n2 callback is NULL"; return false; }
   if (n2fn(N, xy.data(), N2.data(), ctx) != 0) { plan.err = "n2 callback failed"; return false; }
 
-  // cells of the accelerator; plan order = stable sort by cell
-  const int L = o.L;
+  // cells of the accelerator; plan order = stable sort by cell.  With L <= 0
+  // the box is chosen here: it covers every node, its faces lie half a
+  // Cartesian spacing off the grid lines (H should be a multiple of h), and
+  // L = number of cells per side.
+  if (plan.opt.L <= 0) {
+    double xmin = 1e300, xmax = -1e300, ymin = 1e300, ymax = -1e300;
+    for (int64_t i = 0; i < N; ++i) {
+      xmin = std::min(xmin, X[i]); xmax = std::max(xmax, X[i]);
+      ymin = std::min(ymin, Y[i]); ymax = std::max(ymax, Y[i]);
+    }
+    const double H0 = plan.opt.H;
+    plan.opt.box_x0 = g.cart_x0 + (std::floor((xmin - g.cart_x0) / g.h) - 0.5) * g.h;
+    plan.opt.box_y0 = g.cart_y0 + (std::floor((ymin - g.cart_y0) / g.h) - 0.5) * g.h;
+    const int Lx = int(std::floor((xmax - plan.opt.box_x0) / H0)) + 1;
+    const int Ly = int(std::floor((ymax - plan.opt.box_y0) / H0)) + 1;
+    plan.opt.L = std::max(Lx, Ly);
+  }
+  const int L = plan.opt.L;
   const double H = o.H;
   nd.L = L;
   std::vector<int32_t> cellc(N);
   for (int64_t i = 0; i < N; ++i) {
-    const double fx = std::floor((X[i] - o.box_x0) / H), fy = std::floor((Y[i] - o.box_y0) / H);
+    const double fx = std::floor((X[i] - plan.opt.box_x0) / H), fy = std::floor((Y[i] - plan.opt.box_y0) / H);
     if (fx < 0 || fy < 0 || fx >= L || fy >= L) { plan.err = "nodes outside the cell box"; return false; }
     cellc[i] = int32_t(fy) * L + int32_t(fx);
   }

@@ -102,6 +102,9 @@ struct Plan2D {
 // Builders; each returns false and sets plan.err on failure.
 bool build_nodes(Plan2D& plan, ls_n2_fn n2, void* ctx);
 bool build_near(Plan2D& plan);
+// cheap validity check of a cell layout (cut-off support inside N(x) for every
+// node) and the number of near-field block entries one apply would stream
+bool check_cells(Plan2D& plan, int64_t* block_entries);
 bool build_accel(Plan2D& plan);
 
 // Truncated thin SVD of a complex m x n matrix (m >= n), one-sided Jacobi.

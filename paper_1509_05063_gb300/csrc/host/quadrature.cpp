@@ -295,6 +295,41 @@ struct RowBuilder {
 
 }  // namespace
 
+bool check_cells(Plan2D& plan, int64_t* block_entries) {
+  const Nodes& nd = plan.nodes;
+  const int64_t N = nd.N;
+  std::atomic<bool> ok(true);
+  parallel_for(plan.n_threads, N, 1024, [&](int64_t q0, int64_t q1) {
+    RowBuilder rb(plan);
+    for (int64_t q = q0; q < q1 && ok; ++q) {
+      const int c = nd.cell[q];
+      if (!rb.eta_inside_block(q, c % nd.L, c / nd.L)) ok = false;
+    }
+  });
+  if (!ok) {
+    plan.err = "cut-off support leaves the 3 x 3 cell block N(x): enlarge H or shrink the radii";
+    return false;
+  }
+  // entries of the padded per-cell near-field blocks (what one apply streams)
+  const int L = nd.L;
+  int64_t tot = 0;
+  for (int c = 0; c < L * L; ++c) {
+    const int64_t nc = nd.cell_start[c + 1] - nd.cell_start[c];
+    if (!nc) continue;
+    const int ci = c % L, cj = c / L;
+    int64_t nblk = 0;
+    for (int dj = -1; dj <= 1; ++dj) {
+      const int nj = cj + dj;
+      if (nj < 0 || nj >= L) continue;
+      const int lo = nj * L + std::max(ci - 1, 0), hi = nj * L + std::min(ci + 1, L - 1);
+      nblk += ((nd.cell_start[hi + 1] - nd.cell_start[lo]) + 1) & ~int64_t(1);
+    }
+    tot += nc * nblk;
+  }
+  *block_entries = tot;
+  return true;
+}
+
 bool build_near(Plan2D& plan) {
   const int64_t N = plan.nodes.N;
   const int64_t chunk = 256;

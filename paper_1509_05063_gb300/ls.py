@@ -85,6 +85,7 @@ _SIGS = {
     "ls_host_plan_destroy": ([C.c_void_p]),
     "ls_set_stage_timing": ([C.c_void_p, C.c_int]),
     "ls_apply_noalloc": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
+    "ls_check_cells": ([C.POINTER(Geometry), N2FN, C.c_void_p, C.c_double, C.POINTER(Options), C.c_void_p]),
     "ls_get_stage_times": ([C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
 }
 EXPORTED = tuple(_SIGS)
@@ -150,6 +151,20 @@ def _stream(stream):
     import torch
     s = torch.cuda.current_stream() if stream is None else stream
     return C.c_void_p(s.cuda_stream)
+
+
+def check_cells(wl, n2, n_threads: int = 0):
+    """ls_check_cells: validity and streamed near-field size of a cell layout.
+    Returns a dict, or None when the layout is not usable (reason in 'error')."""
+    load_library()
+    out = np.zeros(7)
+    cb = _n2_callback(n2)
+    st = _lib.ls_check_cells(C.byref(geometry_from(wl)), cb, None, float(wl.kappa),
+                             C.byref(options_from(wl, n_threads)), out.ctypes.data)
+    if st != 0:
+        return {"ok": False, "error": _lib.ls_last_error(None).decode()}
+    return {"ok": True, "N": int(out[0]), "cells": int(out[1]), "block_entries": int(out[2]), "M": int(out[3]),
+            "L": int(out[4]), "box_x0": float(out[5]), "box_y0": float(out[6])}
 
 
 class Plan:

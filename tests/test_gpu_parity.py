@@ -177,6 +177,21 @@ def test_far_field_matches_oracle(disc):
     assert np.max(np.abs(got - series)) < 2e-3 * np.max(np.abs(series))
 
 
+def test_mixed_solution_and_far_field_within_1e10_of_fp64_oracle(disc):
+    """Mixed precision (complex64 apply, FP64 refinement) against the FP64
+    oracle's solution of the same operator: solution and far field <= 1e-10."""
+    from paper_1509_05063_gb300 import LS_MIXED
+    ui = W.plane_wave(disc.wl.kappa, (0.6, 0.8), disc.dz.x)
+    ref, _, _ = gmres(disc.op.apply, ui, tol=1e-14, restart=200)
+    sol, info = disc.plan.solve(disc.dev(ui), tol=1e-12, prec=LS_MIXED)
+    assert info["converged"] and info["refinements"] >= 2
+    got = sol.cpu().numpy()
+    assert rel(got, disc.to_plan(ref)) < 1e-10
+    th = np.linspace(0, 2 * math.pi, 32, endpoint=False)
+    ff = disc.plan.farfield(sol, np.stack([np.cos(th), np.sin(th)], -1)).cpu().numpy()[0]
+    assert rel(ff, far_field(disc.dz, ref, th)) < 1e-10
+
+
 def test_cfg1_solution_against_bessel_series():
     """Config 1 (disc, n^2 = 2, kappa = 2, ~4.6k nodes): GPU FP64 solve vs the series."""
     from paper_1509_05063_gb300 import LS_FP64, Plan

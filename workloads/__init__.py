@@ -202,9 +202,11 @@ def cfg1() -> Workload:
                  N_eq=8, n_fb=15), L=8, m=10)
 
 
-def cfg2(h: float = 0.0045, n1: int = 3200, L: int = 56, m: int = 12, N_eq: int = 8) -> Workload:
+def cfg2(h: float = 0.0045, n1: int = 3200, L: int = 61, m: int = 11, N_eq: int = 8) -> Workload:
     """Kite x = cos t + 0.65 cos 2t - 0.65, y = 1.5 sin t; n^2 = 1.5 + 0.5 exp(-|x|^2/0.1)
-    inside, 1 outside; kappa = 20, ~260k nodes, 1024^2 padded lattice FFT, GMRES tol 1e-10."""
+    inside, 1 outside; kappa = 20, ~274k nodes, 1024^2 padded lattice FFT, GMRES tol 1e-10.
+    Cells of 11 h (L = 61): the layout the library's autotuner picks for this
+    scatterer (smallest admissible cells)."""
     wl = kite(n1=n1, n2=17, h=h, kappa=20.0, collar_w=0.07, tau0=0.4, tau1=0.9,
               R_a=10, R_b=6, R_cart=8)
     return place_cells(wl.replace(name="cfg2_kite_kappa20"), L=L, m=m, center=(-0.25, 0.0), N_eq=N_eq)
