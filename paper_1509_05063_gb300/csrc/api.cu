@@ -413,11 +413,16 @@ ls_status ls_plan_create(const ls_geometry* geom, ls_n2_fn n2, void* ctx, double
   const int* d_occ_of_cell = UP(int, occ_of_cell);
   const int* d_occ_of_node = UP(int, occ_of_node);
   const int64_t* d_P_off = UP(int64_t, P.P_off);
-  std::vector<int> items;   // (occupied cell, first row) pairs, 16 rows each
+  std::vector<int> items, items32;   // (occupied cell, first row) pairs, 16 / 32 rows each
   for (int k = 0; k < nocc; ++k)
-    for (int64_t r = 0; r < occ_start[k + 1] - occ_start[k]; r += 16) { items.push_back(k); items.push_back(int(r)); }
+    for (int64_t r = 0; r < occ_start[k + 1] - occ_start[k]; r += 16) {
+      items.push_back(k); items.push_back(int(r));
+      if (r % 32 == 0) { items32.push_back(k); items32.push_back(int(r)); }
+    }
   const int* d_items_raw = UP(int, items);
   const int2* d_items = reinterpret_cast<const int2*>(d_items_raw);
+  const int* d_items32_raw = UP(int, items32);
+  const int2* d_items32 = reinterpret_cast<const int2*>(d_items32_raw);
   const int64_t* d_blk_off = UP(int64_t, blk_off);
   const int* d_blk_seg = UP(int, blk_seg);
   const int64_t* d_rem_row = UP(int64_t, rem_row);
@@ -473,9 +478,19 @@ ls_status ls_plan_create(const ls_geometry* geom, ls_n2_fn n2, void* ctx, double
   a.blk_off = d_blk_off; a.blk_seg = d_blk_seg; a.rem_row = d_rem_row; a.rem_col = d_rem_col;
   a.max_nblk = max_nblk;
   a.items = d_items; a.n_items = int(items.size() / 2);
+  a.items32 = d_items32; a.n_items32 = int(items32.size() / 2);
   a.P = UP(double2, P.P64);
-  a.Bp = UP(double2, P.Bpinv);
-  a.BT = UP(double2, P.BT);
+  // local-expansion matrix [B^+ | -B^+ T_o ...]: one contraction with the cell's
+  // lattice values and its 3 x 3 neighbours' strengths gives gamma_c
+  const int n_lk = P.n_loc + 9 * P.n_es;
+  std::vector<cd> LA(size_t(P.nfb2) * n_lk);
+  for (int n = 0; n < P.nfb2; ++n) {
+    for (int p = 0; p < P.n_loc; ++p) LA[size_t(n) * n_lk + p] = P.Bpinv[size_t(n) * P.n_loc + p];
+    for (int o = 0; o < 9; ++o)
+      for (int l = 0; l < P.n_es; ++l)
+        LA[size_t(n) * n_lk + P.n_loc + o * P.n_es + l] = -P.BT[(size_t(o) * P.nfb2 + n) * P.n_es + l];
+  }
+  a.LA = UP(double2, LA);
   a.Phi = UP(double2, P.Phi);
   a.Wb = UP(double2, Wb);
   a.rem_val = UP(double2, rem_val);
@@ -495,9 +510,9 @@ ls_status ls_plan_create(const ls_geometry* geom, ls_n2_fn n2, void* ctx, double
   b.blk_off = a.blk_off; b.blk_seg = a.blk_seg; b.rem_row = a.rem_row; b.rem_col = a.rem_col;
   b.max_nblk = a.max_nblk;
   b.items = a.items; b.n_items = a.n_items;
+  b.items32 = a.items32; b.n_items32 = a.n_items32;
   b.P = UP(float2, to32(P.P32));
-  b.Bp = UP(float2, to32(P.Bpinv));
-  b.BT = UP(float2, to32(P.BT));
+  b.LA = UP(float2, to32(LA));
   b.Phi = UP(float2, to32(P.Phi));
   {
     std::vector<std::complex<float>> w32 = to32(Wb);

@@ -20,31 +20,33 @@ template <> struct RealOf<double2> { using R = double; };
 template <> struct RealOf<float2> { using R = float; };
 
 // ------------------------------------------------------------ ES projection
+// sigma_c = P_c u_c.  Block (cell, group of 8 rows of P_c), one warp per row:
+// lanes stride the cell's nodes (coalesced reads of P_c's row and of u_c),
+// then one warp reduction per RHS.
 template <typename T, int R>
 __global__ void __launch_bounds__(256) k_es_project(int nocc, const int64_t* __restrict__ occ_start,
                                                     const int64_t* __restrict__ P_off,
                                                     const T* __restrict__ P, const T* __restrict__ u, int64_t N,
                                                     T* __restrict__ sigma, int n_es) {
   const int k = blockIdx.x;
-  if (k >= nocc) return;
+  const int i = blockIdx.y * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (k >= nocc || i >= n_es) return;
   const int64_t s0 = occ_start[k];
   const int nc = int(occ_start[k + 1] - s0);
-  const T* Pc = P + P_off[k];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  for (int i = warp; i < n_es; i += nw) {
-    T acc[R];
+  const T* Pi = P + P_off[k] + int64_t(i) * nc;
+  T acc[R];
 #pragma unroll
-    for (int r = 0; r < R; ++r) acc[r] = czero(T{});
-    for (int j = lane; j < nc; j += 32) {
-      const T pij = Pc[int64_t(i) * nc + j];
+  for (int r = 0; r < R; ++r) acc[r] = czero(T{});
+#pragma unroll 4
+  for (int j = lane; j < nc; j += 32) {
+    const T pij = Pi[j];
 #pragma unroll
-      for (int r = 0; r < R; ++r) acc[r] = cfma(pij, u[r * N + s0 + j], acc[r]);
-    }
+    for (int r = 0; r < R; ++r) acc[r] = cfma(pij, u[r * N + s0 + j], acc[r]);
+  }
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
-      const T v = warp_sum(acc[r]);
-      if (lane == 0) sigma[(int64_t(r) * nocc + k) * n_es + i] = v;
-    }
+  for (int r = 0; r < R; ++r) {
+    const T v = warp_sum(acc[r]);
+    if (lane == 0) sigma[(int64_t(r) * nocc + k) * n_es + i] = v;
   }
 }
 
@@ -349,47 +351,61 @@ __global__ void __launch_bounds__(256) k_spectral(int64_t n, T* __restrict__ Sm,
 }
 
 // ------------------------------------------------------------ local expansion
-template <typename T>
+// gamma_c = B^+ V_c - sum_o (B^+ T_o) sigma_{c+o} as one contraction per cell
+//   gamma_c (nfb2 x R) = LA (nfb2 x K) X_c (K x R),  K = n_loc + 9 n_es,
+// where X_c stacks the cell's (Ne+1)^2 lattice values and the strengths of its
+// 3 x 3 neighbours (zero for empty or missing neighbours).  One block per
+// occupied cell and all R right-hand sides: X_c is gathered into shared memory
+// once ([r][k], conflict-free), then one warp per row n of LA: lanes stride k
+// (coalesced reads of the row, each serving all R), one warp reduction per
+// RHS.  Every (cell, RHS) is summed the same way whatever R.
+template <typename T, int R>
 __global__ void __launch_bounds__(256) k_local_coeffs(int nocc, const int* __restrict__ occ_cells,
-                                                      const int* __restrict__ occ_of_cell, int L, int Ne,
-                                                      int M, const T* __restrict__ V_all, const T* __restrict__ Bp,
-                                                      const T* __restrict__ BT, const T* __restrict__ sigma_all,
-                                                      int n_es, int nfb2, T* __restrict__ gamma_all, int64_t stride) {
+                                                      const int* __restrict__ occ_of_cell, int L, int Ne, int M,
+                                                      const T* __restrict__ V_all, const T* __restrict__ LA,
+                                                      const T* __restrict__ sigma_all, int n_es, int nfb2,
+                                                      T* __restrict__ gamma_all, int64_t stride) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const T* V = V_all + int64_t(blockIdx.y) * stride;
-  const T* sigma = sigma_all + int64_t(blockIdx.y) * nocc * n_es;
-  T* gamma = gamma_all + int64_t(blockIdx.y) * nocc * nfb2;
+  T* X = reinterpret_cast<T*>(smem_raw);           // [R][K]
   const int n_loc = (Ne + 1) * (Ne + 1);
-  T* Vc = reinterpret_cast<T*>(smem_raw);
-  T* sg = Vc + n_loc;
+  const int n_nb = 9 * n_es;
+  const int K = n_loc + n_nb;
   const int k = blockIdx.x;
   const int c = occ_cells[k], ci = c % L, cj = c / L;
-  for (int p = threadIdx.x; p < n_loc; p += blockDim.x) {
-    const int a = p / (Ne + 1), b = p % (Ne + 1);
-    Vc[p] = V[int64_t(ci * Ne + a) * M + cj * Ne + b];
+  for (int e = threadIdx.x; e < R * n_loc; e += blockDim.x) {
+    const int r = e / n_loc, p = e - r * n_loc;
+    const int a = p / (Ne + 1), b = p - a * (Ne + 1);
+    X[r * K + p] = V_all[int64_t(r) * stride + int64_t(ci * Ne + a) * M + cj * Ne + b];
   }
-  for (int e = threadIdx.x; e < 9 * n_es; e += blockDim.x) {
-    const int o = e / n_es, l = e % n_es;
+  for (int e = threadIdx.x; e < R * n_nb; e += blockDim.x) {
+    const int r = e / n_nb, q = e - r * n_nb;
+    const int o = q / n_es, l = q - o * n_es;
     const int ni = ci + o / 3 - 1, nj = cj + o % 3 - 1;
     T v = czero(T{});
     if (ni >= 0 && ni < L && nj >= 0 && nj < L) {
       const int occ = occ_of_cell[nj * L + ni];
-      if (occ >= 0) v = sigma[int64_t(occ) * n_es + l];
+      if (occ >= 0) v = sigma_all[(int64_t(r) * nocc + occ) * n_es + l];
     }
-    sg[e] = v;
+    X[r * K + n_loc + q] = v;
   }
   __syncthreads();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  for (int n = warp; n < nfb2; n += nw) {
-    T acc = czero(T{});
-    for (int p = lane; p < n_loc; p += 32) acc = cfma(Bp[int64_t(n) * n_loc + p], Vc[p], acc);
-    T sub = czero(T{});
-    for (int e = lane; e < 9 * n_es; e += 32) {
-      const int o = e / n_es, l = e % n_es;
-      sub = cfma(BT[(int64_t(o) * nfb2 + n) * n_es + l], sg[e], sub);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int n = warp; n < nfb2; n += 8) {
+    const T* la = LA + int64_t(n) * K;
+    T acc[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) acc[r] = czero(T{});
+#pragma unroll 4
+    for (int kk = lane; kk < K; kk += 32) {
+      const T w = la[kk];
+#pragma unroll
+      for (int r = 0; r < R; ++r) acc[r] = cfma(w, X[r * K + kk], acc[r]);
     }
-    acc = warp_sum(csub(acc, sub));
-    if (lane == 0) gamma[int64_t(k) * nfb2 + n] = acc;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const T v = warp_sum(acc[r]);
+      if (lane == 0) gamma_all[(int64_t(r) * nocc + k) * nfb2 + n] = v;
+    }
   }
 }
 
@@ -398,103 +414,80 @@ __global__ void __launch_bounds__(256) k_local_coeffs(int nocc, const int* __res
 // contiguous column ranges of the 3 x 3 neighbourhood (coalesced, no column
 // indices), the CSR remainder, the local expansion Phi_q . gamma_c, and the
 // assembly out_q = u_q + kappa^2 (near + far).
-// One block per work item = (occupied cell, chunk of 16 target rows), so that
-// the large cells near the boundary are spread over many SMs.  Each warp owns
-// 2 rows of the chunk and R right-hand sides at once: for every column of the
-// cell's 3 x 3 neighbourhood it loads the 2 weights from HBM and the R input
-// values from shared memory (staged chunk by chunk, one contiguous run per RHS,
-// zero in the padding), so one pass over the weights serves all R right-hand
-// sides.
-// The epilogue adds the CSR remainder and the local expansion Phi_q . gamma_c
-// and writes out_q = u_q + kappa^2 (near + far) for every RHS.
-constexpr int kNearRows = 16;      // rows per work item (8 warps x kNearRW rows)
-constexpr int kNearRW = 2;         // rows per warp
+// One block per work item = (occupied cell, chunk of 8 NRW target rows), so
+// that the large cells near the boundary are spread over many SMs.  Each warp
+// owns NRW rows of the chunk and R right-hand sides at once: for every column of
+// the cell's 3 x 3 neighbourhood it loads the NRW weights from HBM and the R
+// input values from shared memory (staged chunk by chunk, one contiguous run
+// per RHS, zero in the padding), so one pass over the weights serves all R
+// right-hand sides and every staged value serves NRW rows.
+// Every row is summed in the same order whatever R and NRW (lane l takes the
+// columns l, l + 32, ... (pairs for complex64) in chunks that start at multiples
+// of 64 columns, then one warp reduction), so a batched apply reproduces the
+// single-RHS results bit for bit.
 constexpr int kNearSmem = 32768;   // bytes of staged input values per chunk
 
-// acc[i][r] += sum over the chunk's columns t of W[row_i][c0 + t] us[r][t]
-template <typename T, int R>
+// acc[i][r] += sum over the chunk's columns t of W[row_i][c0 + t] us[r][t] for
+// the first NR rows of the warp
+template <typename T, int R, int NRW, int NR>
 __device__ __forceinline__ void near_chunk(const T* __restrict__ wk, const int* rows, int nblk, int c0, int cl,
-                                           const T* us, int CH, int lane, T (&acc)[kNearRW][R]) {
-  const T* w[kNearRW];
+                                           const T* us, int CH, int lane, T (&acc)[NRW][R]) {
+  const T* w[NR];
 #pragma unroll
-  for (int i = 0; i < kNearRW; ++i) w[i] = wk + int64_t(rows[i]) * nblk + c0;
+  for (int i = 0; i < NR; ++i) w[i] = wk + int64_t(rows[i]) * nblk + c0;
 #pragma unroll 2
   for (int t = lane; t < cl; t += 32) {
-    T a[kNearRW];
+    T a[NR];
 #pragma unroll
-    for (int i = 0; i < kNearRW; ++i) a[i] = w[i][t];
+    for (int i = 0; i < NR; ++i) a[i] = w[i][t];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       const T x = us[r * CH + t];
 #pragma unroll
-      for (int i = 0; i < kNearRW; ++i) acc[i][r] = cfma(a[i], x, acc[i][r]);
+      for (int i = 0; i < NR; ++i) acc[i][r] = cfma(a[i], x, acc[i][r]);
     }
   }
 }
 
 // complex64: two columns per lane and 16-byte loads (rows, chunk starts and
 // chunk lengths are even, so every pair is 16-byte aligned)
-template <int R>
+template <int R, int NRW>
 __device__ __forceinline__ void near_chunk_pairs(const float2* __restrict__ wk, const int* rows, int nblk, int c0,
                                                  int cl, const float2* us, int CH, int lane,
-                                                 float2 (&acc)[kNearRW][R]) {
-  const float4* w[kNearRW];
+                                                 float2 (&acc)[NRW][R]) {
+  const float4* w[NRW];
 #pragma unroll
-  for (int i = 0; i < kNearRW; ++i) w[i] = reinterpret_cast<const float4*>(wk + int64_t(rows[i]) * nblk + c0);
+  for (int i = 0; i < NRW; ++i) w[i] = reinterpret_cast<const float4*>(wk + int64_t(rows[i]) * nblk + c0);
   const int np = cl >> 1;
-#pragma unroll 2
+  constexpr int kUnroll = NRW * R >= 32 ? 1 : 2;     // the largest accumulator sets keep to 128 registers
+#pragma unroll kUnroll
   for (int t = lane; t < np; t += 32) {
-    float4 a[kNearRW];
+    float4 a[NRW];
 #pragma unroll
-    for (int i = 0; i < kNearRW; ++i) a[i] = w[i][t];
+    for (int i = 0; i < NRW; ++i) a[i] = w[i][t];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       const float4 x = reinterpret_cast<const float4*>(us + r * CH)[t];
       const float2 x0 = make_float2(x.x, x.y), x1 = make_float2(x.z, x.w);
 #pragma unroll
-      for (int i = 0; i < kNearRW; ++i)
+      for (int i = 0; i < NRW; ++i)
         acc[i][r] = cfma(make_float2(a[i].z, a[i].w), x1, cfma(make_float2(a[i].x, a[i].y), x0, acc[i][r]));
     }
   }
 }
-template <>
-__device__ __forceinline__ void near_chunk<float2, 1>(const float2* __restrict__ wk, const int* rows, int nblk,
-                                                      int c0, int cl, const float2* us, int CH, int lane,
-                                                      float2 (&acc)[kNearRW][1]) {
-  near_chunk_pairs<1>(wk, rows, nblk, c0, cl, us, CH, lane, acc);
-}
-template <>
-__device__ __forceinline__ void near_chunk<float2, 2>(const float2* __restrict__ wk, const int* rows, int nblk,
-                                                      int c0, int cl, const float2* us, int CH, int lane,
-                                                      float2 (&acc)[kNearRW][2]) {
-  near_chunk_pairs<2>(wk, rows, nblk, c0, cl, us, CH, lane, acc);
-}
-template <>
-__device__ __forceinline__ void near_chunk<float2, 4>(const float2* __restrict__ wk, const int* rows, int nblk,
-                                                      int c0, int cl, const float2* us, int CH, int lane,
-                                                      float2 (&acc)[kNearRW][4]) {
-  near_chunk_pairs<4>(wk, rows, nblk, c0, cl, us, CH, lane, acc);
-}
-template <>
-__device__ __forceinline__ void near_chunk<float2, 8>(const float2* __restrict__ wk, const int* rows, int nblk,
-                                                      int c0, int cl, const float2* us, int CH, int lane,
-                                                      float2 (&acc)[kNearRW][8]) {
-  near_chunk_pairs<8>(wk, rows, nblk, c0, cl, us, CH, lane, acc);
-}
 
-template <typename T, int R>
-__global__ void __launch_bounds__(256) k_near_eval(const int2* __restrict__ items,
-                                                   const int64_t* __restrict__ occ_start,
-                                                   const int64_t* __restrict__ blk_off,
-                                                   const int* __restrict__ blk_seg, const T* __restrict__ Wb,
-                                                   const int64_t* __restrict__ rem_row,
-                                                   const int* __restrict__ rem_col, const T* __restrict__ rem_val,
-                                                   const T* __restrict__ u, int64_t N, const T* __restrict__ Phi,
-                                                   const T* __restrict__ gamma, int nocc, int nfb2,
-                                                   typename RealOf<T>::R kappa2, T* __restrict__ out) {
+template <typename T, int R, int NRW>
+__device__ __forceinline__ void near_eval_body(const int2* __restrict__ items, const int64_t* __restrict__ occ_start,
+                                               const int64_t* __restrict__ blk_off, const int* __restrict__ blk_seg,
+                                               const T* __restrict__ Wb, const int64_t* __restrict__ rem_row,
+                                               const int* __restrict__ rem_col, const T* __restrict__ rem_val,
+                                               const T* __restrict__ u, int64_t N, const T* __restrict__ Phi,
+                                               const T* __restrict__ gamma, int nocc, int nfb2,
+                                               typename RealOf<T>::R kappa2, T* __restrict__ out) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* us = reinterpret_cast<T*>(smem_raw);               // [rhs][column]
-  constexpr int CH = kNearSmem / int(R * sizeof(T));    // columns per chunk (even)
+  constexpr int CH = kNearSmem / int(R * sizeof(T));    // columns per chunk (a multiple of 64)
+  static_assert(CH % 64 == 0, "chunks must start at multiples of 64 columns");
   const int2 item = items[blockIdx.x];
   const int k = item.x;
   const int* sg = blk_seg + 6 * k;
@@ -505,35 +498,59 @@ __global__ void __launch_bounds__(256) k_near_eval(const int2* __restrict__ item
   const int nrow = int(occ_start[k + 1] - r0);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const T* wk = Wb + blk_off[k];
-  int rows[kNearRW];
-  bool valid[kNearRW];
+  int rows[NRW];
+  bool valid[NRW];
 #pragma unroll
-  for (int i = 0; i < kNearRW; ++i) {
+  for (int i = 0; i < NRW; ++i) {
     const int r = item.y + warp + 8 * i;
     valid[i] = r < nrow;
     rows[i] = valid[i] ? r : item.y;
   }
-  T acc[kNearRW][R];
+  T acc[NRW][R];
 #pragma unroll
-  for (int i = 0; i < kNearRW; ++i)
+  for (int i = 0; i < NRW; ++i)
 #pragma unroll
     for (int r = 0; r < R; ++r) acc[i][r] = czero(T{});
   for (int c0 = 0; c0 < nblk; c0 += CH) {
     const int cl = min(CH, nblk - c0);
     __syncthreads();
-    for (int e = threadIdx.x; e < cl * R; e += blockDim.x) {   // us[r * CH + col]: conflict-free reads
-      const int r = e / cl, col = c0 + e % cl;
-      T v = czero(T{});
-      if (col < p0) { if (col < l0) v = u[r * N + sg[0] + col]; }
-      else if (col < p0 + p1) { const int o = col - p0; if (o < l1) v = u[r * N + sg[2] + o]; }
-      else { const int o = col - p0 - p1; if (o < l2) v = u[r * N + sg[4] + o]; }
-      us[r * CH + (e % cl)] = v;
+    if constexpr (R == 1) {
+      for (int col = threadIdx.x; col < cl; col += blockDim.x) {   // us[col]
+        const int cc = c0 + col;
+        T v = czero(T{});
+        if (cc < p0) { if (cc < l0) v = u[sg[0] + cc]; }
+        else if (cc < p0 + p1) { const int o = cc - p0; if (o < l1) v = u[sg[2] + o]; }
+        else { const int o = cc - p0 - p1; if (o < l2) v = u[sg[4] + o]; }
+        us[col] = v;
+      }
+    } else {
+      // us[r * CH + col]: one contiguous run per RHS (conflict-free reads)
+#pragma unroll 1
+      for (int r = 0; r < R; ++r) {
+        const T* ur = u + int64_t(r) * N;
+        for (int col = threadIdx.x; col < cl; col += blockDim.x) {
+          const int cc = c0 + col;
+          T v = czero(T{});
+          if (cc < p0) { if (cc < l0) v = ur[sg[0] + cc]; }
+          else if (cc < p0 + p1) { const int o = cc - p0; if (o < l1) v = ur[sg[2] + o]; }
+          else { const int o = cc - p0 - p1; if (o < l2) v = ur[sg[4] + o]; }
+          us[r * CH + col] = v;
+        }
+      }
     }
     __syncthreads();
-    near_chunk<T, R>(wk, rows, nblk, c0, cl, us, CH, lane, acc);
+    if constexpr (sizeof(T) == 16) {
+      // FP64 is bound by the FP64 pipe: a warp skips its rows past the end of the cell
+      static_assert(NRW == 2, "the FP64 variant takes two rows per warp");
+      if (valid[1]) near_chunk<T, R, NRW, 2>(wk, rows, nblk, c0, cl, us, CH, lane, acc);
+      else if (valid[0]) near_chunk<T, R, NRW, 1>(wk, rows, nblk, c0, cl, us, CH, lane, acc);
+    } else {
+      // complex64 is bound by HBM: a row past the end re-reads cached weights
+      near_chunk_pairs<R, NRW>(wk, rows, nblk, c0, cl, us, CH, lane, acc);
+    }
   }
 #pragma unroll
-  for (int i = 0; i < kNearRW; ++i) {
+  for (int i = 0; i < NRW; ++i) {
     if (!valid[i]) continue;                      // warp-uniform
     const int64_t q = r0 + rows[i];
     for (int64_t e = rem_row[q] + lane; e < rem_row[q + 1]; e += 32) {
@@ -559,23 +576,62 @@ __global__ void __launch_bounds__(256) k_near_eval(const int2* __restrict__ item
   }
 }
 
+#define LS_NEAR_ARGS                                                                                          \
+  const int2 *__restrict__ items, const int64_t *__restrict__ occ_start, const int64_t *__restrict__ blk_off,     \
+      const int *__restrict__ blk_seg, const T *__restrict__ Wb, const int64_t *__restrict__ rem_row,             \
+      const int *__restrict__ rem_col, const T *__restrict__ rem_val, const T *__restrict__ u, int64_t N,         \
+      const T *__restrict__ Phi, const T *__restrict__ gamma, int nocc, int nfb2,                                 \
+      typename RealOf<T>::R kappa2, T *__restrict__ out
+#define LS_NEAR_PASS items, occ_start, blk_off, blk_seg, Wb, rem_row, rem_col, rem_val, u, N, Phi, gamma, nocc, nfb2, \
+                     kappa2, out
+// two rows per warp, 16-row items: registers left to the compiler
+template <typename T, int R>
+__global__ void __launch_bounds__(256) k_near_eval(LS_NEAR_ARGS) {
+  near_eval_body<T, R, 2>(LS_NEAR_PASS);
+}
+// four rows per warp, 32-row items: two blocks per SM
+template <typename T, int R>
+__global__ void __launch_bounds__(256, 2) k_near_eval4(LS_NEAR_ARGS) {
+  near_eval_body<T, R, 4>(LS_NEAR_PASS);
+}
+#undef LS_NEAR_ARGS
+#undef LS_NEAR_PASS
+
+// rows per warp: 2, or 4 for multi-RHS complex64 (every staged value then
+// serves four rows; 32-row work items)
+template <typename T, int R>
+constexpr int near_rows_per_warp() { return sizeof(T) == 8 && R >= 2 ? 4 : 2; }
+
 template <typename T, int R>
 cudaError_t apply_r(const ApplyData<T>& d, const T* u, T* out, cudaStream_t st, cudaEvent_t* ev) {
   if (ev) cudaEventRecord(ev[0], st);
-  k_es_project<T, R><<<d.nocc, 256, 0, st>>>(d.nocc, d.occ_start, d.P_off, d.P, u, d.N, d.sigma, d.n_es);
+  k_es_project<T, R><<<dim3(d.nocc, (d.n_es + 7) / 8), 256, 0, st>>>(d.nocc, d.occ_start, d.P_off, d.P, u, d.N,
+                                                                     d.sigma, d.n_es);
   if (ev) cudaEventRecord(ev[1], st);
   if (ev) cudaEventRecord(ev[2], st);        // the lattice fill is fused into k_src_rows
   cudaError_t e = lattice_conv(d, R, st);
   if (e != cudaSuccess) return e;
   if (ev) cudaEventRecord(ev[3], st);
-  const size_t sm_local = size_t(d.n_loc + 9 * d.n_es) * sizeof(T);
-  k_local_coeffs<T><<<dim3(d.nocc, R), 256, sm_local, st>>>(d.nocc, d.occ_cells, d.occ_of_cell, d.L, d.Ne, d.M,
-                                                            d.Sd, d.Bp, d.BT, d.sigma, d.n_es, d.nfb2, d.gamma,
-                                                            d.lattice_rows() * d.M);
+  const size_t sm_local = size_t(R) * (d.n_loc + 9 * d.n_es) * sizeof(T);
+  static bool local_attr = false;     // X_c above 48 KB (large N_eq with many RHS)
+  if (!local_attr) {
+    cudaFuncSetAttribute(k_local_coeffs<T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+    local_attr = true;
+  }
+  if (sm_local > 160 * 1024) return cudaErrorInvalidValue;
+  k_local_coeffs<T, R><<<d.nocc, 256, sm_local, st>>>(d.nocc, d.occ_cells, d.occ_of_cell, d.L, d.Ne, d.M, d.Sd,
+                                                       d.LA, d.sigma, d.n_es, d.nfb2, d.gamma,
+                                                       d.lattice_rows() * d.M);
   if (ev) cudaEventRecord(ev[4], st);
-  k_near_eval<T, R><<<d.n_items, 256, kNearSmem, st>>>(d.items, d.occ_start, d.blk_off, d.blk_seg, d.Wb,
-                                                       d.rem_row, d.rem_col, d.rem_val, u, d.N, d.Phi, d.gamma,
-                                                       d.nocc, d.nfb2, typename RealOf<T>::R(d.kappa2), out);
+  if constexpr (near_rows_per_warp<T, R>() == 4)
+    k_near_eval4<T, R><<<d.n_items32, 256, kNearSmem, st>>>(d.items32, d.occ_start, d.blk_off, d.blk_seg, d.Wb,
+                                                            d.rem_row, d.rem_col, d.rem_val, u, d.N, d.Phi,
+                                                            d.gamma, d.nocc, d.nfb2,
+                                                            typename RealOf<T>::R(d.kappa2), out);
+  else
+    k_near_eval<T, R><<<d.n_items, 256, kNearSmem, st>>>(d.items, d.occ_start, d.blk_off, d.blk_seg, d.Wb,
+                                                         d.rem_row, d.rem_col, d.rem_val, u, d.N, d.Phi, d.gamma,
+                                                         d.nocc, d.nfb2, typename RealOf<T>::R(d.kappa2), out);
   if (ev) cudaEventRecord(ev[5], st);
   return cudaGetLastError();
 }
@@ -586,7 +642,8 @@ cudaError_t apply_batch(const ApplyData<T>& d, const T* u, T* out, int nr, cudaS
     case 1: return apply_r<T, 1>(d, u, out, st, ev);
     case 2: return apply_r<T, 2>(d, u, out, st, ev);
     case 4: return apply_r<T, 4>(d, u, out, st, ev);
-    case 8: if (sizeof(T) == 8) return apply_r<T, 8>(d, u, out, st, ev);
+    case 8:
+      if constexpr (sizeof(T) == 8) return apply_r<T, 8>(d, u, out, st, ev);
       return cudaErrorInvalidValue;
     default: return cudaErrorInvalidValue;
   }

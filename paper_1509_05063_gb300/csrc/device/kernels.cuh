@@ -16,8 +16,7 @@ struct ApplyData {
   const int* occ_of_node = nullptr;     // N: occupied index of the node's cell
   const int64_t* P_off = nullptr;       // nocc + 1
   const T* P = nullptr;                 // projections
-  const T* Bp = nullptr;                // nfb2 x n_loc
-  const T* BT = nullptr;                // 9 x nfb2 x n_es
+  const T* LA = nullptr;                // nfb2 x (n_loc + 9 n_es): [B^+ | -B^+ T_0 ... -B^+ T_8]
   const T* Phi = nullptr;               // N x nfb2
   const T* Gq = nullptr;                // (M/2+1)^2 quarter spectra, [l][k], scaled by 1/M^2
   const T* Dq = nullptr;
@@ -29,8 +28,10 @@ struct ApplyData {
   const int64_t* blk_off = nullptr;     // nocc: offset of the cell's block
   const int* blk_seg = nullptr;         // nocc x 6: (first node, length) of the 3 column ranges
   int max_nblk = 0;                     // longest padded block row
-  const int2* items = nullptr;          // near-field work items (occupied cell, first row)
+  const int2* items = nullptr;          // near-field work items (occupied cell, first row), 16 rows
   int n_items = 0;
+  const int2* items32 = nullptr;        // the same with 32 rows per item (multi-RHS complex64)
+  int n_items32 = 0;
   const T* Wb = nullptr;                // blocks, row-major per cell
   const int64_t* rem_row = nullptr;     // N + 1
   const int* rem_col = nullptr;
