@@ -178,6 +178,45 @@ ls_status ls_farfield(ls_plan plan, const void* u_dev, int nrhs, const double* d
 
 ls_status ls_plan_destroy(ls_plan plan);
 
+/* ---- multi-instance batches -------------------------------------------------
+ * Many scatterers of different shape, size and kappa, each with its own plan,
+ * applied and solved together: the paper solves one scatterer at a time with
+ * GMRES (Section 2) and the accelerated apply (Section 3); a batch runs that
+ * apply for every instance in one launch sequence and that GMRES for every
+ * instance in lock-step.
+ * A batch refers to its plans and does not own them: destroy the batch before
+ * them, and do not use its plans on another stream while a batch call runs
+ * (they share the plans' work arrays).  All plans must live on the current
+ * device.  Vectors of a batch are the instances' node vectors (ls_plan_nodes
+ * order) concatenated in plan order; instance i starts at element off[i]
+ * (ls_batch_offsets).  ls_batch_apply runs the projection, the local expansion
+ * and the near-field correction of all instances as ONE kernel each, walking an
+ * (instance, cell) work list, and the lattice convolution per instance;
+ * repeated calls with the same buffers replay a CUDA graph.
+ * Errors: LS_ERR_INVALID for null or empty arguments, LS_ERR_NOMEM / LS_ERR_CUDA
+ * from allocation or upload; the message is in ls_batch_last_error (or, for a
+ * failed ls_batch_create, ls_batch_last_error(NULL)). */
+typedef struct ls_batch_s* ls_batch;
+ls_status ls_batch_create(const ls_plan* plans, int n_plans, ls_batch* out);
+/* off_host receives n_plans + 1 int64 offsets; the last is the total length. */
+ls_status ls_batch_offsets(ls_batch b, int64_t* off_host);
+/* Au = A_i u_i for every instance (one right-hand side each).  LS_FP64:
+ * complex128, LS_MIXED: complex64; device pointers, async on stream; u and Au
+ * must not overlap. */
+ls_status ls_batch_apply(ls_batch b, const void* u_dev, void* Au_dev, ls_precision prec, void* stream);
+/* Solve A_i u_i = uinc_i for all instances as ls_solve does for one plan
+ * (FP64 GMRES, or FP64 refinement around complex64 GMRES), one batched apply
+ * per iteration.  uinc, u: complex128 concatenated vectors (u: initial guess
+ * in, solution out).  info: totals (iterations summed over instances, residual
+ * = the largest); per: n_plans entries (iterations and final residual of each
+ * instance) or NULL.  Synchronises the stream.  LS_ERR_NOCONV if max_iter is
+ * reached before every instance meets tol. */
+ls_status ls_batch_solve(ls_batch b, const void* uinc_dev, void* u_dev, double tol, int max_iter, int restart,
+                         ls_precision prec, ls_solve_info* info, ls_solve_info* per, void* stream);
+/* Synchronises the device, then frees the batch (not its plans); NULL is a no-op. */
+ls_status ls_batch_destroy(ls_batch b);
+const char* ls_batch_last_error(ls_batch b);
+
 /* Allocation-free apply (this entry point has no counterpart in the paper; it
  * serves callers that must not allocate device memory when they apply the
  * operator -- e.g. inside a CUDA stream capture, under an external memory pool

@@ -5,7 +5,10 @@
 #include <cmath>
 #include <complex>
 #include <cstring>
+#include <climits>
+#include <cstdint>
 #include <map>
+#include <new>
 #include <mutex>
 #include <set>
 #include <tuple>
@@ -28,39 +31,11 @@ struct DevBuf {
 
 }  // namespace
 
-struct ls_plan_s {
-  lsh::Plan2D host;                 // kept for node queries (large arrays are released)
+// Owner of device allocations and of the last error message (plans, batches).
+struct DevOwner {
   std::vector<DevBuf> bufs;
   int64_t device_bytes = 0;
-  lsd::ApplyData<double2> d64;
-  lsd::ApplyData<float2> d32;
-  // plan-wide device arrays
-  double *x = nullptr, *y = nullptr, *ffw = nullptr;
-  // solve work space (lazily sized)
-  int ws_restart = -1, ws_rhs = 0;   // work space grows to the largest request
-  double2 *V = nullptr, *w = nullptr, *r = nullptr, *e = nullptr, *cor = nullptr, *h = nullptr, *partial = nullptr;
-  double2* apart = nullptr;     // kAxpyGroups x N partial sums of the Arnoldi update
-  double* dnorm = nullptr;
-  double* dpartial = nullptr;
-  float2 *c64a = nullptr, *c64b = nullptr;
-  double2* pin_h = nullptr;     // pinned host copies of h and the norms (async D2H)
-  double* pin_n = nullptr;
-  double* dirs = nullptr;
-  int dirs_cap = 0;
-  ls_plan_info_t info{};
   std::string err;
-  // CUDA graphs of the apply, one per (precision, batch, input, output); the
-  // first call with a key runs directly, the second captures and launches
-  using GraphKey = std::tuple<int, int, const void*, void*>;
-  std::map<GraphKey, cudaGraphExec_t> graphs;
-  std::set<GraphKey> graph_seen;
-  cudaStream_t cap_stream = nullptr;
-  bool graphs_off = false;
-  // optional per-stage event timing of ls_apply
-  bool timing = false;
-  cudaEvent_t ev[lsd::kStages + 1] = {};
-  double stage_ms[2][lsd::kStages] = {};
-  int64_t stage_calls[2] = {0, 0};
 
   template <typename T>
   T* alloc(size_t n, ls_status* st) {
@@ -88,17 +63,108 @@ struct ls_plan_s {
     }
     return d;
   }
-  void free_all() {
+  void free_bufs() {
+    for (auto& b : bufs) cudaFree(b.p);
+    bufs.clear();
+  }
+};
+
+// Work space of lock-step GMRES and of the mixed refinement, for R right-hand
+// sides whose vectors occupy `total` elements together (grown on demand).
+struct Krylov {
+  int restart = -1, R = 0;
+  int64_t total = 0, max_len = 0;
+  double2 *V = nullptr, *w = nullptr, *r = nullptr, *e = nullptr, *cor = nullptr, *h = nullptr, *partial = nullptr;
+  double2* apart = nullptr;     // kAxpyGroups x max_len partial sums of the Arnoldi update
+  double* dnorm = nullptr;
+  double* dpartial = nullptr;
+  float2 *c64a = nullptr, *c64b = nullptr;
+  double2* pin_h = nullptr;     // pinned host copies of h and the norms (async D2H)
+  double* pin_n = nullptr;
+  void free_pinned() {
     if (pin_h) cudaFreeHost(pin_h);
     if (pin_n) cudaFreeHost(pin_n);
     pin_h = nullptr;
     pin_n = nullptr;
+  }
+};
+
+// CUDA graphs of a launch sequence keyed by (precision, batch, input, output):
+// the first call with a key launches directly, the second captures the
+// sequence on a private stream and launches the graph, later calls replay it.
+struct GraphCache {
+  using Key = std::tuple<int, int, const void*, void*>;
+  std::map<Key, cudaGraphExec_t> graphs;
+  std::set<Key> seen;
+  cudaStream_t cap_stream = nullptr;
+  bool off = false;
+
+  template <typename F>
+  cudaError_t run(const Key& key, F launch, cudaStream_t st) {
+    if (off) return launch(st);
+    auto it = graphs.find(key);
+    if (it != graphs.end()) return cudaGraphLaunch(it->second, st);
+    if (!seen.count(key)) {
+      if (seen.size() > 4096) seen.clear();
+      seen.insert(key);
+      return launch(st);
+    }
+    if (!cap_stream && cudaStreamCreateWithFlags(&cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      off = true;
+      return launch(st);
+    }
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ex = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(cap_stream, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      const cudaError_t e1 = launch(cap_stream);
+      e = cudaStreamEndCapture(cap_stream, &g);
+      if (e1 != cudaSuccess) e = e1;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&ex, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      off = true;
+      return launch(st);
+    }
+    if (graphs.size() >= 512) clear();
+    graphs[key] = ex;
+    return cudaGraphLaunch(ex, st);
+  }
+  void clear() {
     for (auto& kv : graphs) cudaGraphExecDestroy(kv.second);
     graphs.clear();
+  }
+  void release() {
+    clear();
     if (cap_stream) cudaStreamDestroy(cap_stream);
     cap_stream = nullptr;
-    for (auto& b : bufs) cudaFree(b.p);
-    bufs.clear();
+  }
+};
+
+struct ls_plan_s : DevOwner {
+  lsh::Plan2D host;                 // kept for node queries (large arrays are released)
+  lsd::ApplyData<double2> d64;
+  lsd::ApplyData<float2> d32;
+  // plan-wide device arrays
+  double *x = nullptr, *y = nullptr, *ffw = nullptr;
+  Krylov K;                         // solve work space (lazily sized)
+  double* dirs = nullptr;
+  int dirs_cap = 0;
+  ls_plan_info_t info{};
+  GraphCache graphs;                // CUDA graphs of the apply
+  // optional per-stage event timing of ls_apply
+  bool timing = false;
+  cudaEvent_t ev[lsd::kStages + 1] = {};
+  double stage_ms[2][lsd::kStages] = {};
+  int64_t stage_calls[2] = {0, 0};
+
+  void free_all() {
+    K.free_pinned();
+    graphs.release();
+    free_bufs();
   }
 };
 
@@ -106,7 +172,7 @@ namespace {
 
 using cd = std::complex<double>;
 
-ls_status fail(ls_plan p, ls_status s, const std::string& m) {
+ls_status fail(DevOwner* p, ls_status s, const std::string& m) {
   if (p) p->err = m;
   else g_create_error = m;
   return s;
@@ -123,41 +189,10 @@ ls_status fail(ls_plan p, ls_status s, const std::string& m) {
 template <typename T>
 cudaError_t run_apply(ls_plan plan, int prec, const lsd::ApplyData<T>& d, const T* u, T* out, int nr,
                       cudaStream_t st) {
-  if (plan->graphs_off || plan->timing) return lsd::apply_batch(d, u, out, nr, st);
-  const ls_plan_s::GraphKey key(prec, nr, static_cast<const void*>(u), static_cast<void*>(out));
-  auto it = plan->graphs.find(key);
-  if (it != plan->graphs.end()) return cudaGraphLaunch(it->second, st);
-  if (!plan->graph_seen.count(key)) {
-    if (plan->graph_seen.size() > 4096) plan->graph_seen.clear();
-    plan->graph_seen.insert(key);
-    return lsd::apply_batch(d, u, out, nr, st);
-  }
-  if (!plan->cap_stream && cudaStreamCreateWithFlags(&plan->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
-    cudaGetLastError();
-    plan->graphs_off = true;
-    return lsd::apply_batch(d, u, out, nr, st);
-  }
-  cudaGraph_t g = nullptr;
-  cudaGraphExec_t ex = nullptr;
-  cudaError_t e = cudaStreamBeginCapture(plan->cap_stream, cudaStreamCaptureModeThreadLocal);
-  if (e == cudaSuccess) {
-    const cudaError_t e1 = lsd::apply_batch(d, u, out, nr, plan->cap_stream);
-    e = cudaStreamEndCapture(plan->cap_stream, &g);
-    if (e1 != cudaSuccess) e = e1;
-  }
-  if (e == cudaSuccess) e = cudaGraphInstantiate(&ex, g, 0);
-  if (g) cudaGraphDestroy(g);
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    plan->graphs_off = true;
-    return lsd::apply_batch(d, u, out, nr, st);
-  }
-  if (plan->graphs.size() >= 512) {
-    for (auto& kv : plan->graphs) cudaGraphExecDestroy(kv.second);
-    plan->graphs.clear();
-  }
-  plan->graphs[key] = ex;
-  return cudaGraphLaunch(ex, st);
+  auto launch = [&](cudaStream_t s) { return lsd::apply_batch(d, u, out, nr, s); };
+  if (plan->timing) return launch(st);
+  return plan->graphs.run(GraphCache::Key(prec, nr, static_cast<const void*>(u), static_cast<void*>(out)), launch,
+                          st);
 }
 
 std::vector<std::complex<float>> to32(const std::vector<cd>& v) {
@@ -606,62 +641,119 @@ ls_status ls_apply(ls_plan plan, const void* u, void* Au, int nrhs, ls_precision
 
 namespace {
 
-// One GMRES(m) solve of A x = b (FP64 Arnoldi).  op(v, Av) applies the
-// operator.  Stops when the true residual ||b - A x|| / ||b|| <= tol (checked
-// at restarts; inside a cycle the Givens estimate is used).
-// Lock-step GMRES(m) for R right-hand sides (FP64 Arnoldi): every iteration
-// applies the operator to the R current basis vectors in ONE batched call
-// (they sit next to each other: slot-major basis V[j][r][N]), then runs the
-// Arnoldi step of each RHS with one host synchronisation for all of them.
-// Classical Gram-Schmidt with selective re-orthogonalisation (a second pass
-// only when the first removed more than 1 - 1/sqrt(2) of ||w||), Givens
-// rotations on the host, true residual checked at every restart.  op(in, out)
-// applies A to R contiguous vectors.  Stops when every RHS has
+// Where the R right-hand sides of a lock-step solve live: RHS r occupies
+// elements [off[r], off[r] + len[r]) of every vector, and one vector of all R
+// holds `total` elements (R contiguous vectors of one plan, or the
+// concatenated vectors of the instances of a batch).
+struct Layout {
+  int R = 0;
+  std::vector<int64_t> off, len;
+  int64_t total = 0;
+  int64_t max_len() const { return len.empty() ? 0 : *std::max_element(len.begin(), len.end()); }
+};
+
+Layout uniform_layout(int R, int64_t N) {
+  Layout L;
+  L.R = R;
+  for (int r = 0; r < R; ++r) { L.off.push_back(int64_t(r) * N); L.len.push_back(N); }
+  L.total = int64_t(R) * N;
+  return L;
+}
+
+ls_status ensure_krylov(DevOwner* plan, Krylov& K, int restart, const Layout& lay) {
+  const int R = lay.R;
+  const int64_t total = lay.total, max_len = lay.max_len();
+  if (K.restart >= restart && K.R >= R && K.total >= total && K.max_len >= max_len) return LS_OK;
+  restart = std::max(restart, K.restart);
+  const int Rw = std::max(R, K.R);
+  const int64_t Tw = std::max(total, K.total), Lw = std::max(max_len, K.max_len);
+  ls_status st = LS_OK;
+  const int nb = lsd::gram_blocks(Lw);
+  K.V = plan->alloc<double2>(size_t(restart + 1) * Tw, &st);
+  K.w = plan->alloc<double2>(size_t(Tw), &st);
+  K.r = plan->alloc<double2>(size_t(Tw), &st);
+  K.e = plan->alloc<double2>(size_t(Tw), &st);
+  K.cor = plan->alloc<double2>(size_t(Tw), &st);
+  K.apart = plan->alloc<double2>(size_t(lsd::kAxpyGroups) * Lw, &st);
+  K.h = plan->alloc<double2>(size_t(Rw) * (restart + 3), &st);
+  K.partial = plan->alloc<double2>(size_t(Rw) * nb * (restart + 3), &st);
+  K.dnorm = plan->alloc<double>(Rw, &st);
+  K.dpartial = plan->alloc<double>(size_t(Rw) * nb, &st);
+  K.c64a = plan->alloc<float2>(size_t(Tw), &st);
+  K.c64b = plan->alloc<float2>(size_t(Tw), &st);
+  if (st != LS_OK) return st;
+  K.free_pinned();
+  if (cudaMallocHost(&K.pin_h, size_t(Rw) * (restart + 3) * sizeof(double2)) != cudaSuccess ||
+      cudaMallocHost(&K.pin_n, size_t(Rw) * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(plan, LS_ERR_NOMEM, "pinned host staging");
+  }
+  K.restart = restart;
+  K.R = Rw;
+  K.total = Tw;
+  K.max_len = Lw;
+  return LS_OK;
+}
+
+// nrm[r] = ||base_r|| for every RHS of the layout (one host synchronisation)
+cudaError_t layout_norms(Krylov& K, const Layout& lay, const double2* base, cudaStream_t st) {
+  const int64_t nbmax = lsd::gram_blocks(K.max_len);
+  for (int r = 0; r < lay.R; ++r) {
+    cudaError_t e = lsd::norm2(base + lay.off[r], lay.len[r], K.dpartial + size_t(r) * nbmax, K.dnorm + r, st);
+    if (e != cudaSuccess) return e;
+  }
+  cudaError_t e = cudaMemcpyAsync(K.pin_n, K.dnorm, lay.R * sizeof(double), cudaMemcpyDeviceToHost, st);
+  if (e != cudaSuccess) return e;
+  return cudaStreamSynchronize(st);
+}
+
+// Lock-step GMRES(m) for the R right-hand sides of a layout (FP64 Arnoldi):
+// every iteration applies the operator to the R current basis vectors in ONE
+// call (op(in, out, need) on whole layout vectors: a batched apply of one
+// plan, or the apply of a multi-instance batch; need[r] = 0 marks RHS whose
+// product is not used, nullptr means all), then runs the Arnoldi step of each RHS
+// with one host synchronisation for all of them.  Classical Gram-Schmidt with
+// selective re-orthogonalisation (a second pass only when the first removed
+// more than 1 - 1/sqrt(2) of ||w||), Givens rotations on the host, true
+// residual checked at every restart.  Stops when every RHS has
 // ||b - A x|| / ||b|| <= tol; iters[r] counts the iterations of RHS r.
 template <typename Op>
-ls_status gmres_batch(ls_plan plan, Op op, int R, const double2* B, double2* X, double tol, int max_iter,
-                      int restart, cudaStream_t st, int* iters, double* relres) {
-  const int64_t N = plan->d64.N;
-  const int64_t vs = int64_t(R) * N;                 // stride between basis slots
-  double2* V = plan->V;
-  double2* Wv = plan->w;                             // R vectors
-  double2* Rv = plan->r;                             // R vectors
+ls_status gmres_lockstep(DevOwner* plan, Krylov& K, const Layout& lay, Op op, const double2* B, double2* X,
+                         double tol, int max_iter, int restart, cudaStream_t st, int* iters, double* relres) {
+  const int R = lay.R;
+  const int64_t vs = lay.total;                      // stride between basis slots
+  double2* V = K.V;
+  double2* Wv = K.w;
+  double2* Rv = K.r;
   const int m = restart;
-  const int nb = lsd::gram_blocks(N);
+  const int nbmax = lsd::gram_blocks(K.max_len);
   const int hstride = m + 3;
-  auto h_of = [&](int r) { return plan->h + size_t(r) * hstride; };
-  auto part_of = [&](int r) { return plan->partial + size_t(r) * nb * hstride; };
-  auto dn_of = [&](int r) { return plan->dnorm + r; };
-  auto dp_of = [&](int r) { return plan->dpartial + size_t(r) * nb; };
-  double* nrm = plan->pin_n;                         // pinned: asynchronous copies
+  auto h_of = [&](int r) { return K.h + size_t(r) * hstride; };
+  auto part_of = [&](int r) { return K.partial + size_t(r) * nbmax * hstride; };
+  auto dn_of = [&](int r) { return K.dnorm + r; };
+  auto dp_of = [&](int r) { return K.dpartial + size_t(r) * nbmax; };
+  auto O = [&](int r) { return lay.off[r]; };
+  auto Ln = [&](int r) { return lay.len[r]; };
+  double* nrm = K.pin_n;
   std::vector<double> bnorm(R);
-  auto norms = [&](const double2* base) -> cudaError_t {   // nrm[r] = ||base_r||
-    for (int r = 0; r < R; ++r) {
-      cudaError_t e = lsd::norm2(base + r * N, N, dp_of(r), dn_of(r), st);
-      if (e != cudaSuccess) return e;
-    }
-    cudaError_t e = cudaMemcpyAsync(nrm, plan->dnorm, R * sizeof(double), cudaMemcpyDeviceToHost, st);
-    if (e != cudaSuccess) return e;
-    return cudaStreamSynchronize(st);
-  };
-  LS_CU(norms(B));
+  LS_CU(layout_norms(K, lay, B, st));
   bnorm.assign(nrm, nrm + R);
   for (int r = 0; r < R; ++r) {
     iters[r] = 0;
     relres[r] = 0;
-    if (bnorm[r] == 0.0) LS_CU(cudaMemsetAsync(X + r * N, 0, N * sizeof(double2), st));
+    if (bnorm[r] == 0.0) LS_CU(cudaMemsetAsync(X + O(r), 0, Ln(r) * sizeof(double2), st));
   }
   std::vector<std::vector<cd>> H(R, std::vector<cd>(size_t(m + 1) * m)), cs(R, std::vector<cd>(m)),
       sn(R, std::vector<cd>(m)), g(R, std::vector<cd>(m + 1));
-  cd* hcol = reinterpret_cast<cd*>(plan->pin_h);
+  cd* hcol = reinterpret_cast<cd*>(K.pin_h);
   std::vector<int> k_used(R);
   std::vector<char> done(R), active(R), again(R);
   int total = 0;
   for (;;) {
     // true residuals
-    LS_CU(op(X, Wv));
+    LS_CU(op(X, Wv, nullptr));
     LS_CU(lsd::sub(B, Wv, Rv, vs, st));
-    LS_CU(norms(Rv));
+    LS_CU(layout_norms(K, lay, Rv, st));
     bool all_done = true;
     for (int r = 0; r < R; ++r) {
       relres[r] = bnorm[r] > 0 ? nrm[r] / bnorm[r] : 0.0;
@@ -671,11 +763,11 @@ ls_status gmres_batch(ls_plan plan, Op op, int R, const double2* B, double2* X, 
     if (all_done) return LS_OK;
     if (total >= max_iter) return fail(plan, LS_ERR_NOCONV, "GMRES reached max_iter");
     for (int r = 0; r < R; ++r) {
-      double2* v0 = V + r * N;
+      double2* v0 = V + O(r);
       if (done[r]) {
-        LS_CU(cudaMemsetAsync(v0, 0, N * sizeof(double2), st));
+        LS_CU(cudaMemsetAsync(v0, 0, Ln(r) * sizeof(double2), st));
       } else {
-        LS_CU(lsd::scale_into(Rv + r * N, dn_of(r), v0, N, st));
+        LS_CU(lsd::scale_into(Rv + O(r), dn_of(r), v0, Ln(r), st));
         std::fill(H[r].begin(), H[r].end(), cd(0));
         std::fill(g[r].begin(), g[r].end(), cd(0));
         g[r][0] = nrm[r];
@@ -684,7 +776,7 @@ ls_status gmres_batch(ls_plan plan, Op op, int R, const double2* B, double2* X, 
       k_used[r] = 0;
     }
     for (int k = 0; k < m; ++k) {
-      LS_CU(op(V + k * vs, Wv));
+      LS_CU(op(V + k * vs, Wv, active.data()));     // only the RHS still iterating need A v
       std::vector<double> hk1(R, 0.0);
       for (int r = 0; r < R; ++r) again[r] = active[r];
       for (int pass = 0; pass < 2; ++pass) {
@@ -692,13 +784,13 @@ ls_status gmres_batch(ls_plan plan, Op op, int R, const double2* B, double2* X, 
         for (int r = 0; r < R; ++r) {
           if (!again[r]) continue;
           any = true;
-          LS_CU(lsd::gram(V + r * N, k + 1, vs, Wv + r * N, N, part_of(r), h_of(r), st));
-          LS_CU(lsd::axpy_multi(V + r * N, k + 1, vs, h_of(r), Wv + r * N, plan->apart, N, st));
-          LS_CU(lsd::norm2(Wv + r * N, N, dp_of(r), dn_of(r), st));
+          LS_CU(lsd::gram(V + O(r), k + 1, vs, Wv + O(r), Ln(r), part_of(r), h_of(r), st));
+          LS_CU(lsd::axpy_multi(V + O(r), k + 1, vs, h_of(r), Wv + O(r), K.apart, Ln(r), st));
+          LS_CU(lsd::norm2(Wv + O(r), Ln(r), dp_of(r), dn_of(r), st));
         }
         if (!any) break;
-        LS_CU(cudaMemcpyAsync(hcol, plan->h, size_t(R) * hstride * sizeof(double2), cudaMemcpyDeviceToHost, st));
-        LS_CU(cudaMemcpyAsync(nrm, plan->dnorm, R * sizeof(double), cudaMemcpyDeviceToHost, st));
+        LS_CU(cudaMemcpyAsync(hcol, K.h, size_t(R) * hstride * sizeof(double2), cudaMemcpyDeviceToHost, st));
+        LS_CU(cudaMemcpyAsync(nrm, K.dnorm, R * sizeof(double), cudaMemcpyDeviceToHost, st));
         LS_CU(cudaStreamSynchronize(st));
         for (int r = 0; r < R; ++r) {
           if (!again[r]) continue;
@@ -710,14 +802,14 @@ ls_status gmres_batch(ls_plan plan, Op op, int R, const double2* B, double2* X, 
       }
       bool any_active = false;
       for (int r = 0; r < R; ++r) {
-        double2* vn = V + (k + 1) * vs + r * N;
+        double2* vn = V + (k + 1) * vs + O(r);
         if (!active[r]) {
-          LS_CU(cudaMemsetAsync(vn, 0, N * sizeof(double2), st));
+          LS_CU(cudaMemsetAsync(vn, 0, Ln(r) * sizeof(double2), st));
           continue;
         }
         std::vector<cd>& Hr = H[r];
         Hr[size_t(k + 1) * m + k] = hk1[r];
-        LS_CU(lsd::scale_into(Wv + r * N, dn_of(r), vn, N, st));
+        LS_CU(lsd::scale_into(Wv + O(r), dn_of(r), vn, Ln(r), st));
         for (int j = 0; j < k; ++j) {
           const cd t = std::conj(cs[r][j]) * Hr[size_t(j) * m + k] + std::conj(sn[r][j]) * Hr[size_t(j + 1) * m + k];
           Hr[size_t(j + 1) * m + k] = -sn[r][j] * Hr[size_t(j) * m + k] + cs[r][j] * Hr[size_t(j + 1) * m + k];
@@ -750,43 +842,77 @@ ls_status gmres_batch(ls_plan plan, Op op, int R, const double2* B, double2* X, 
         y[i] = sacc / H[r][size_t(i) * m + i];
       }
       LS_CU(cudaMemcpyAsync(h_of(r), y.data(), ku * sizeof(double2), cudaMemcpyHostToDevice, st));
-      LS_CU(lsd::combine(V + r * N, ku, vs, h_of(r), X + r * N, N, st));
+      LS_CU(lsd::combine(V + O(r), ku, vs, h_of(r), X + O(r), Ln(r), st));
     }
   }
 }
 
-ls_status ensure_workspace(ls_plan plan, int restart, int R) {
-  if (plan->ws_restart >= restart && plan->ws_rhs >= R) return LS_OK;
-  const int64_t N = plan->d64.N;
-  restart = std::max(restart, plan->ws_restart);
-  R = std::max(R, plan->ws_rhs);
-  ls_status st = LS_OK;
-  const int nb = lsd::gram_blocks(N);
-  plan->V = plan->alloc<double2>(size_t(restart + 1) * R * N, &st);
-  plan->w = plan->alloc<double2>(size_t(R) * N, &st);
-  plan->r = plan->alloc<double2>(size_t(R) * N, &st);
-  plan->e = plan->alloc<double2>(size_t(R) * N, &st);
-  plan->cor = plan->alloc<double2>(size_t(R) * N, &st);
-  plan->apart = plan->alloc<double2>(size_t(lsd::kAxpyGroups) * N, &st);
-  plan->h = plan->alloc<double2>(size_t(R) * (restart + 3), &st);
-  plan->partial = plan->alloc<double2>(size_t(R) * nb * (restart + 3), &st);
-  plan->dnorm = plan->alloc<double>(R, &st);
-  plan->dpartial = plan->alloc<double>(size_t(R) * nb, &st);
-  plan->c64a = plan->alloc<float2>(size_t(R) * N, &st);
-  plan->c64b = plan->alloc<float2>(size_t(R) * N, &st);
-  if (st != LS_OK) return st;
-  if (plan->pin_h) cudaFreeHost(plan->pin_h);
-  if (plan->pin_n) cudaFreeHost(plan->pin_n);
-  plan->pin_h = nullptr;
-  plan->pin_n = nullptr;
-  if (cudaMallocHost(&plan->pin_h, size_t(R) * (restart + 3) * sizeof(double2)) != cudaSuccess ||
-      cudaMallocHost(&plan->pin_n, size_t(R) * sizeof(double)) != cudaSuccess) {
-    cudaGetLastError();
-    return fail(plan, LS_ERR_NOMEM, "pinned host staging");
+struct SolveStats {
+  int iterations = 0, refinements = 0;
+  double worst = 0;
+  std::vector<int> it_per;          // per RHS: GMRES iterations (inner iterations for mixed)
+  std::vector<double> res_per;      // per RHS: final relative residual ||b - A_64 x|| / ||b||
+};
+
+// A x = B for the R right-hand sides of a layout.  FP64: lock-step GMRES on
+// op64.  Mixed: FP64 iterative refinement r = b - A_64 x (op64), lock-step
+// GMRES on op32 (complex64 apply) to a loose tolerance, x += correction, until
+// the FP64 residual of every RHS is <= tol.
+template <typename Op64, typename Op32>
+ls_status solve_lockstep(DevOwner* plan, Krylov& K, const Layout& lay, Op64 op64, Op32 op32, ls_precision prec,
+                         const double2* B, double2* X, double tol, int max_iter, int restart, cudaStream_t st,
+                         SolveStats& S) {
+  const int R = lay.R;
+  std::vector<int> it(R);
+  std::vector<double> rr(R);
+  S.it_per.assign(R, 0);
+  S.res_per.assign(R, 0.0);
+  if (prec == LS_FP64) {
+    const ls_status s = gmres_lockstep(plan, K, lay, op64, B, X, tol, max_iter, restart, st, it.data(), rr.data());
+    for (int r = 0; r < R; ++r) {
+      S.iterations += it[r];
+      S.it_per[r] = it[r];
+      S.res_per[r] = rr[r];
+      S.worst = std::max(S.worst, rr[r]);
+    }
+    return s;
   }
-  plan->ws_restart = restart;
-  plan->ws_rhs = R;
-  return LS_OK;
+  double2* Res = K.e;
+  double2* Cor = K.cor;
+  std::vector<double> bn(R), rn(R);
+  LS_CU(layout_norms(K, lay, B, st));
+  bn.assign(K.pin_n, K.pin_n + R);
+  int inner_total = 0;
+  for (int ref = 0;; ++ref) {
+    LS_CU(op64(X, K.w, nullptr));
+    LS_CU(lsd::sub(B, K.w, Res, lay.total, st));
+    LS_CU(layout_norms(K, lay, Res, st));
+    rn.assign(K.pin_n, K.pin_n + R);
+    double rel = 0;
+    for (int r = 0; r < R; ++r) {
+      S.res_per[r] = bn[r] > 0 ? rn[r] / bn[r] : 0.0;
+      rel = std::max(rel, S.res_per[r]);
+    }
+    // RHS already at tol get a zero correction equation (GMRES skips them)
+    if (rel > tol)
+      for (int r = 0; r < R; ++r)
+        if (S.res_per[r] <= tol) LS_CU(cudaMemsetAsync(Res + lay.off[r], 0, lay.len[r] * sizeof(double2), st));
+    if (rel <= tol) { S.worst = std::max(S.worst, rel); return LS_OK; }
+    if (inner_total >= max_iter || ref >= 50) {
+      S.worst = std::max(S.worst, rel);
+      return fail(plan, LS_ERR_NOCONV, "refinement reached max_iter");
+    }
+    S.refinements++;
+    const double inner_tol = std::max(1e-5, 0.3 * tol / rel);
+    LS_CU(cudaMemsetAsync(Cor, 0, size_t(lay.total) * sizeof(double2), st));
+    const ls_status s = gmres_lockstep(plan, K, lay, op32, Res, Cor, inner_tol, std::max(1, max_iter - inner_total),
+                                       restart, st, it.data(), rr.data());
+    int mx = 0;
+    for (int r = 0; r < R; ++r) { S.iterations += it[r]; S.it_per[r] += it[r]; mx = std::max(mx, it[r]); }
+    inner_total += mx;
+    if (s != LS_OK && s != LS_ERR_NOCONV) return s;
+    LS_CU(lsd::add_inplace(X, Cor, lay.total, st));
+  }
 }
 
 }  // namespace
@@ -805,13 +931,16 @@ ls_status ls_solve(ls_plan plan, const void* uinc, void* u, int nrhs, double tol
   // right-hand sides are solved in lock-step batches sharing one batched apply
   const int maxb = prec == LS_FP64 ? lsd::kMaxRhs64 : lsd::kMaxRhs32;
   const int Rb = std::max(1, std::min(nrhs, maxb));
-  ls_status s = ensure_workspace(plan, restart, Rb);
+  ls_status s = ensure_krylov(plan, plan->K, restart, uniform_layout(Rb, N));
   if (s != LS_OK) return s;
+  SolveStats S;
   int total_it = 0, total_ref = 0;
   double worst = 0;
-  // FP64 apply of R contiguous vectors (chunks of at most kMaxRhs64)
-  auto op64 = [&](int R) {
-    return [&, R](const double2* v, double2* Av) -> cudaError_t {
+  ls_status result = LS_OK;
+  for (int r0 = 0; r0 < nrhs; r0 += Rb) {
+    const int R = std::min(Rb, nrhs - r0);
+    // FP64 apply of R contiguous vectors (chunks of at most kMaxRhs64)
+    auto op64 = [&](const double2* v, double2* Av, const char*) -> cudaError_t {
       for (int r = 0; r < R;) {
         int nr = lsd::kMaxRhs64;
         while (nr > R - r) nr /= 2;
@@ -821,72 +950,28 @@ ls_status ls_solve(ls_plan plan, const void* uinc, void* u, int nrhs, double tol
       }
       return cudaSuccess;
     };
-  };
-  // complex64 apply of R contiguous complex128 vectors (cast in, batched apply, cast out)
-  auto op32 = [&](int R) {
-    return [&, R](const double2* v, double2* Av) -> cudaError_t {
-      cudaError_t e = lsd::to_c64(v, plan->c64a, int64_t(R) * N, st);
+    // complex64 apply of R contiguous complex128 vectors (cast in, batched apply, cast out)
+    auto op32 = [&](const double2* v, double2* Av, const char*) -> cudaError_t {
+      cudaError_t e = lsd::to_c64(v, plan->K.c64a, int64_t(R) * N, st);
       for (int r = 0; r < R && e == cudaSuccess;) {
         int nr = lsd::kMaxRhs32;
         while (nr > R - r) nr /= 2;
-        e = run_apply(plan, LS_MIXED, plan->d32, plan->c64a + r * N, plan->c64b + r * N, nr, st);
+        e = run_apply(plan, LS_MIXED, plan->d32, plan->K.c64a + r * N, plan->K.c64b + r * N, nr, st);
         r += nr;
       }
-      if (e == cudaSuccess) e = lsd::to_c128(plan->c64b, Av, int64_t(R) * N, st);
+      if (e == cudaSuccess) e = lsd::to_c128(plan->K.c64b, Av, int64_t(R) * N, st);
       return e;
     };
-  };
-  ls_status result = LS_OK;
-  std::vector<int> it(Rb);
-  std::vector<double> rr(Rb);
-  for (int r0 = 0; r0 < nrhs; r0 += Rb) {
-    const int R = std::min(Rb, nrhs - r0);
-    const double2* B = static_cast<const double2*>(uinc) + int64_t(r0) * N;
-    double2* X = static_cast<double2*>(u) + int64_t(r0) * N;
-    if (prec == LS_FP64) {
-      s = gmres_batch(plan, op64(R), R, B, X, tol, max_iter, restart, st, it.data(), rr.data());
-      for (int r = 0; r < R; ++r) { total_it += it[r]; worst = std::max(worst, rr[r]); }
-      if (s != LS_OK) { result = s; if (s != LS_ERR_NOCONV) break; }
-    } else {
-      // FP64 iterative refinement around complex64 GMRES corrections:
-      // r = b - A_64 x (FP64), solve A_32 c = r to a loose tolerance, x += c.
-      double2* Res = plan->e;
-      double2* Cor = plan->cor;
-      std::vector<double> bn(R), rn(R);
-      auto norms = [&](const double2* base, std::vector<double>& out) -> cudaError_t {
-        for (int r = 0; r < R; ++r) {
-          cudaError_t e = lsd::norm2(base + r * N, N, plan->dpartial + size_t(r) * lsd::gram_blocks(N),
-                                     plan->dnorm + r, st);
-          if (e != cudaSuccess) return e;
-        }
-        cudaError_t e = cudaMemcpyAsync(out.data(), plan->dnorm, R * sizeof(double), cudaMemcpyDeviceToHost, st);
-        return e == cudaSuccess ? cudaStreamSynchronize(st) : e;
-      };
-      LS_CU(norms(B, bn));
-      int inner_total = 0;
-      for (int ref = 0;; ++ref) {
-        LS_CU(op64(R)(X, plan->w));
-        LS_CU(lsd::sub(B, plan->w, Res, int64_t(R) * N, st));
-        LS_CU(norms(Res, rn));
-        double rel = 0;
-        for (int r = 0; r < R; ++r) rel = std::max(rel, bn[r] > 0 ? rn[r] / bn[r] : 0.0);
-        if (rel <= tol) { worst = std::max(worst, rel); break; }
-        if (inner_total >= max_iter || ref >= 50) {
-          worst = std::max(worst, rel);
-          result = fail(plan, LS_ERR_NOCONV, "refinement reached max_iter");
-          break;
-        }
-        total_ref++;
-        const double inner_tol = std::max(1e-5, 0.3 * tol / rel);
-        LS_CU(cudaMemsetAsync(Cor, 0, size_t(R) * N * sizeof(double2), st));
-        s = gmres_batch(plan, op32(R), R, Res, Cor, inner_tol, std::max(1, max_iter - inner_total), restart, st,
-                        it.data(), rr.data());
-        int mx = 0;
-        for (int r = 0; r < R; ++r) { total_it += it[r]; mx = std::max(mx, it[r]); }
-        inner_total += mx;
-        if (s != LS_OK && s != LS_ERR_NOCONV) return s;
-        LS_CU(lsd::add_inplace(X, Cor, int64_t(R) * N, st));
-      }
+    SolveStats Sb;
+    s = solve_lockstep(plan, plan->K, uniform_layout(R, N), op64, op32, prec,
+                       static_cast<const double2*>(uinc) + int64_t(r0) * N, static_cast<double2*>(u) + int64_t(r0) * N,
+                       tol, max_iter, restart, st, Sb);
+    total_it += Sb.iterations;
+    total_ref += Sb.refinements;
+    worst = std::max(worst, Sb.worst);
+    if (s != LS_OK) {
+      result = s;
+      if (s != LS_ERR_NOCONV) break;
     }
   }
   if (info) {
@@ -1026,3 +1111,252 @@ extern "C" ls_status ls_apply_noalloc(ls_plan plan, const void* u, void* Au, ls_
   if (prec == LS_MIXED) return noalloc_apply(plan, plan->d32, u, Au, st);
   return fail(plan, LS_ERR_INVALID, "ls_apply_noalloc: bad precision");
 }
+
+// ---------------------------------------------------------------- multi-instance batches
+// Work lists of a subset of a batch's instances (the instances still
+// iterating in a lock-step solve): device arrays owned by the set.
+struct ActiveSet {
+  std::vector<int> ids;
+  int2* cells = nullptr;
+  int n_cells = 0;
+  int4* items = nullptr;
+  int n_items = 0;
+  void release() {
+    if (cells) cudaFree(cells);
+    if (items) cudaFree(items);
+    cells = nullptr;
+    items = nullptr;
+  }
+};
+
+struct ls_batch_s : DevOwner {
+  std::vector<ls_plan> plans;
+  std::vector<int64_t> off;                          // n + 1 node offsets in the concatenated vectors
+  std::vector<lsd::InstData<double2>> h64;
+  std::vector<lsd::InstData<float2>> h32;
+  const lsd::InstData<double2>* d64 = nullptr;
+  const lsd::InstData<float2>* d32 = nullptr;
+  std::vector<std::vector<int>> cells_of, items_of;  // host work lists per instance (pairs / quadruples)
+  int max_nes = 0, max_K = 0;
+  std::map<std::vector<char>, int> set_of;           // instance subset -> index in sets
+  std::vector<ActiveSet> sets;
+  Krylov K;
+  GraphCache graphs;
+  void release_sets() {
+    for (auto& a : sets) a.release();
+    sets.clear();
+    set_of.clear();
+  }
+};
+
+namespace {
+
+// Index of the work lists of the instances with need[i] != 0 (all if need is
+// null), built and uploaded on first use.  A lock-step solve meets at most
+// n + 1 subsets (instances only drop out); the cache is bounded.
+int active_set(ls_batch b, const char* need, cudaError_t* err) {
+  const int n = int(b->plans.size());
+  std::vector<char> key(n, 1);
+  if (need)
+    for (int i = 0; i < n; ++i) key[i] = need[i] ? 1 : 0;
+  auto it = b->set_of.find(key);
+  if (it != b->set_of.end()) return it->second;
+  if (b->sets.size() >= 256) {                       // many distinct subsets: start over
+    cudaDeviceSynchronize();                         // no graph of the old lists may still run
+    b->graphs.clear();
+    b->release_sets();
+  }
+  ActiveSet a;
+  std::vector<int> cells, items;
+  for (int i = 0; i < n; ++i) {
+    if (!key[i]) continue;
+    a.ids.push_back(i);
+    cells.insert(cells.end(), b->cells_of[i].begin(), b->cells_of[i].end());
+    items.insert(items.end(), b->items_of[i].begin(), b->items_of[i].end());
+  }
+  a.n_cells = int(cells.size() / 2);
+  a.n_items = int(items.size() / 4);
+  *err = cudaSuccess;
+  if (!cells.empty()) {
+    *err = cudaMalloc(&a.cells, cells.size() * sizeof(int));
+    if (*err == cudaSuccess) *err = cudaMalloc(&a.items, items.size() * sizeof(int));
+    if (*err == cudaSuccess)
+      *err = cudaMemcpy(a.cells, cells.data(), cells.size() * sizeof(int), cudaMemcpyHostToDevice);
+    if (*err == cudaSuccess)
+      *err = cudaMemcpy(a.items, items.data(), items.size() * sizeof(int), cudaMemcpyHostToDevice);
+    if (*err != cudaSuccess) {
+      a.release();
+      return -1;
+    }
+  }
+  b->sets.push_back(std::move(a));
+  const int idx = int(b->sets.size()) - 1;
+  b->set_of[key] = idx;
+  return idx;
+}
+
+// need: per-instance flags (nullptr = every instance); the apply covers only
+// the instances with need != 0.
+template <typename T>
+cudaError_t batch_apply_t(ls_batch b, int prec, const lsd::InstData<T>* dI, const std::vector<lsd::InstData<T>>& hI,
+                          const T* u, T* out, cudaStream_t st, const char* need = nullptr) {
+  cudaError_t err = cudaSuccess;
+  const int si = active_set(b, need, &err);
+  if (si < 0) return err;
+  const ActiveSet& a = b->sets[si];
+  if (a.ids.empty()) return cudaSuccess;
+  auto launch = [&](cudaStream_t s) {
+    return lsd::apply_multi<T>(dI, hI.data(), a.ids.data(), int(a.ids.size()), a.cells, a.n_cells, a.items,
+                               a.n_items, b->max_nes, b->max_K, u, out, s);
+  };
+  return b->graphs.run(GraphCache::Key(prec, si, static_cast<const void*>(u), static_cast<void*>(out)), launch, st);
+}
+
+Layout batch_layout(ls_batch b) {
+  Layout L;
+  L.R = int(b->plans.size());
+  for (int i = 0; i < L.R; ++i) { L.off.push_back(b->off[i]); L.len.push_back(b->off[i + 1] - b->off[i]); }
+  L.total = b->off.back();
+  return L;
+}
+
+}  // namespace
+
+extern "C" {
+
+ls_status ls_batch_create(const ls_plan* plans, int n_plans, ls_batch* out) {
+  if (!out) return LS_ERR_INVALID;
+  *out = nullptr;
+  if (!plans || n_plans < 1) return fail(nullptr, LS_ERR_INVALID, "ls_batch_create: no plans");
+  for (int i = 0; i < n_plans; ++i)
+    if (!plans[i]) return fail(nullptr, LS_ERR_INVALID, "ls_batch_create: null plan");
+  auto* b = new (std::nothrow) ls_batch_s();
+  if (!b) return fail(nullptr, LS_ERR_NOMEM, "ls_batch_create: host allocation");
+  auto bail = [&](ls_status s) {
+    g_create_error = b->err;
+    b->release_sets();
+    b->free_bufs();
+    delete b;
+    return s;
+  };
+  b->plans.assign(plans, plans + n_plans);
+  b->off.push_back(0);
+  for (int i = 0; i < n_plans; ++i) {
+    const ls_plan p = plans[i];
+    b->h64.push_back({p->d64, b->off.back()});
+    b->h32.push_back({p->d32, b->off.back()});
+    b->off.push_back(b->off.back() + p->d64.N);
+    b->max_nes = std::max(b->max_nes, p->d64.n_es);
+    b->max_K = std::max(b->max_K, p->d64.n_loc + 9 * p->d64.n_es);
+    std::vector<int> cells, items;
+    for (int k = 0; k < p->d64.nocc; ++k) { cells.push_back(i); cells.push_back(k); }
+    std::vector<int> it(size_t(2) * p->d64.n_items);
+    if (cudaMemcpy(it.data(), p->d64.items, it.size() * sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) {
+      cudaGetLastError();
+      b->err = "ls_batch_create: reading a plan's work items failed";
+      return bail(LS_ERR_CUDA);
+    }
+    for (size_t e = 0; e < it.size(); e += 2) {
+      items.push_back(i); items.push_back(it[e]); items.push_back(it[e + 1]); items.push_back(0);
+    }
+    b->cells_of.push_back(std::move(cells));
+    b->items_of.push_back(std::move(items));
+  }
+  int64_t n_cells = 0, n_items = 0;
+  for (int i = 0; i < n_plans; ++i) {
+    n_cells += int64_t(b->cells_of[i].size() / 2);
+    n_items += int64_t(b->items_of[i].size() / 4);
+  }
+  if (n_cells > INT32_MAX || n_items > INT32_MAX) {
+    b->err = "ls_batch_create: work lists too long";
+    return bail(LS_ERR_INVALID);
+  }
+  ls_status st = LS_OK;
+  b->d64 = b->upload<lsd::InstData<double2>>(b->h64, &st);
+  if (st != LS_OK) return bail(st);
+  b->d32 = b->upload<lsd::InstData<float2>>(b->h32, &st);
+  if (st != LS_OK) return bail(st);
+  cudaError_t ce = cudaSuccess;
+  if (active_set(b, nullptr, &ce) < 0) {
+    cudaGetLastError();
+    b->err = std::string("ls_batch_create: work list upload: ") + cudaGetErrorString(ce);
+    return bail(LS_ERR_NOMEM);
+  }
+  *out = b;
+  return LS_OK;
+}
+
+ls_status ls_batch_offsets(ls_batch b, int64_t* off_host) {
+  if (!b || !off_host) return LS_ERR_INVALID;
+  std::copy(b->off.begin(), b->off.end(), off_host);
+  return LS_OK;
+}
+
+ls_status ls_batch_apply(ls_batch b, const void* u, void* Au, ls_precision prec, void* stream) {
+  if (!b) return LS_ERR_INVALID;
+  DevOwner* plan = b;
+  if (!u || !Au) return fail(b, LS_ERR_INVALID, "ls_batch_apply: bad arguments");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (prec == LS_FP64)
+    LS_CU(batch_apply_t(b, prec, b->d64, b->h64, static_cast<const double2*>(u), static_cast<double2*>(Au), st));
+  else if (prec == LS_MIXED)
+    LS_CU(batch_apply_t(b, prec, b->d32, b->h32, static_cast<const float2*>(u), static_cast<float2*>(Au), st));
+  else
+    return fail(b, LS_ERR_INVALID, "ls_batch_apply: bad precision");
+  return LS_OK;
+}
+
+ls_status ls_batch_solve(ls_batch b, const void* uinc, void* u, double tol, int max_iter, int restart,
+                         ls_precision prec, ls_solve_info* info, ls_solve_info* per, void* stream) {
+  if (!b) return LS_ERR_INVALID;
+  if (!uinc || !u || !(tol > 0) || max_iter < 1 || restart < 1)
+    return fail(b, LS_ERR_INVALID, "ls_batch_solve: bad arguments");
+  if (prec != LS_FP64 && prec != LS_MIXED) return fail(b, LS_ERR_INVALID, "ls_batch_solve: bad precision");
+  const auto t0 = std::chrono::steady_clock::now();
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const Layout lay = batch_layout(b);
+  ls_status s = ensure_krylov(b, b->K, restart, lay);
+  if (s != LS_OK) return s;
+  auto op64 = [&](const double2* v, double2* Av, const char* need) -> cudaError_t {
+    return batch_apply_t(b, LS_FP64, b->d64, b->h64, v, Av, st, need);
+  };
+  auto op32 = [&](const double2* v, double2* Av, const char* need) -> cudaError_t {
+    cudaError_t e = lsd::to_c64(v, b->K.c64a, lay.total, st);
+    if (e == cudaSuccess) e = batch_apply_t(b, LS_MIXED, b->d32, b->h32, b->K.c64a, b->K.c64b, st, need);
+    if (e == cudaSuccess) e = lsd::to_c128(b->K.c64b, Av, lay.total, st);
+    return e;
+  };
+  SolveStats S;
+  s = solve_lockstep(b, b->K, lay, op64, op32, prec, static_cast<const double2*>(uinc), static_cast<double2*>(u), tol,
+                     max_iter, restart, st, S);
+  const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  if (info) {
+    info->iterations = S.iterations;
+    info->refinements = S.refinements;
+    info->residual = S.worst;
+    info->seconds = secs;
+  }
+  if (per)
+    for (int i = 0; i < lay.R; ++i) {
+      per[i].iterations = S.it_per.empty() ? 0 : S.it_per[i];
+      per[i].refinements = S.refinements;
+      per[i].residual = S.res_per.empty() ? 0 : S.res_per[i];
+      per[i].seconds = secs;
+    }
+  return s;
+}
+
+ls_status ls_batch_destroy(ls_batch b) {
+  if (!b) return LS_OK;
+  cudaDeviceSynchronize();
+  b->K.free_pinned();
+  b->graphs.release();
+  b->release_sets();
+  b->free_bufs();
+  delete b;
+  return LS_OK;
+}
+
+const char* ls_batch_last_error(ls_batch b) { return b ? b->err.c_str() : g_create_error.c_str(); }
+
+}  // extern "C"

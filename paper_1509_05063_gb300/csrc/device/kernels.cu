@@ -24,12 +24,11 @@ template <> struct RealOf<float2> { using R = float; };
 // lanes stride the cell's nodes (coalesced reads of P_c's row and of u_c),
 // then one warp reduction per RHS.
 template <typename T, int R>
-__global__ void __launch_bounds__(256) k_es_project(int nocc, const int64_t* __restrict__ occ_start,
-                                                    const int64_t* __restrict__ P_off,
-                                                    const T* __restrict__ P, const T* __restrict__ u, int64_t N,
-                                                    T* __restrict__ sigma, int n_es) {
-  const int k = blockIdx.x;
-  const int i = blockIdx.y * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+__device__ __forceinline__ void es_project_body(int k, int i, int nocc, const int64_t* __restrict__ occ_start,
+                                                const int64_t* __restrict__ P_off, const T* __restrict__ P,
+                                                const T* __restrict__ u, int64_t N, T* __restrict__ sigma,
+                                                int n_es) {
+  const int lane = threadIdx.x & 31;
   if (k >= nocc || i >= n_es) return;
   const int64_t s0 = occ_start[k];
   const int nc = int(occ_start[k + 1] - s0);
@@ -48,6 +47,15 @@ __global__ void __launch_bounds__(256) k_es_project(int nocc, const int64_t* __r
     const T v = warp_sum(acc[r]);
     if (lane == 0) sigma[(int64_t(r) * nocc + k) * n_es + i] = v;
   }
+}
+
+template <typename T, int R>
+__global__ void __launch_bounds__(256) k_es_project(int nocc, const int64_t* __restrict__ occ_start,
+                                                    const int64_t* __restrict__ P_off,
+                                                    const T* __restrict__ P, const T* __restrict__ u, int64_t N,
+                                                    T* __restrict__ sigma, int n_es) {
+  es_project_body<T, R>(blockIdx.x, blockIdx.y * 8 + (threadIdx.x >> 5), nocc, occ_start, P_off, P, u, N, sigma,
+                        n_es);
 }
 
 // ------------------------------------------------------------ lattice sources
@@ -360,17 +368,16 @@ __global__ void __launch_bounds__(256) k_spectral(int64_t n, T* __restrict__ Sm,
 // (coalesced reads of the row, each serving all R), one warp reduction per
 // RHS.  Every (cell, RHS) is summed the same way whatever R.
 template <typename T, int R>
-__global__ void __launch_bounds__(256) k_local_coeffs(int nocc, const int* __restrict__ occ_cells,
-                                                      const int* __restrict__ occ_of_cell, int L, int Ne, int M,
-                                                      const T* __restrict__ V_all, const T* __restrict__ LA,
-                                                      const T* __restrict__ sigma_all, int n_es, int nfb2,
-                                                      T* __restrict__ gamma_all, int64_t stride) {
+__device__ __forceinline__ void local_coeffs_body(int k, int nocc, const int* __restrict__ occ_cells,
+                                                  const int* __restrict__ occ_of_cell, int L, int Ne, int M,
+                                                  const T* __restrict__ V_all, const T* __restrict__ LA,
+                                                  const T* __restrict__ sigma_all, int n_es, int nfb2,
+                                                  T* __restrict__ gamma_all, int64_t stride) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* X = reinterpret_cast<T*>(smem_raw);           // [R][K]
   const int n_loc = (Ne + 1) * (Ne + 1);
   const int n_nb = 9 * n_es;
   const int K = n_loc + n_nb;
-  const int k = blockIdx.x;
   const int c = occ_cells[k], ci = c % L, cj = c / L;
   for (int e = threadIdx.x; e < R * n_loc; e += blockDim.x) {
     const int r = e / n_loc, p = e - r * n_loc;
@@ -407,6 +414,16 @@ __global__ void __launch_bounds__(256) k_local_coeffs(int nocc, const int* __res
       if (lane == 0) gamma_all[(int64_t(r) * nocc + k) * nfb2 + n] = v;
     }
   }
+}
+
+template <typename T, int R>
+__global__ void __launch_bounds__(256) k_local_coeffs(int nocc, const int* __restrict__ occ_cells,
+                                                      const int* __restrict__ occ_of_cell, int L, int Ne, int M,
+                                                      const T* __restrict__ V_all, const T* __restrict__ LA,
+                                                      const T* __restrict__ sigma_all, int n_es, int nfb2,
+                                                      T* __restrict__ gamma_all, int64_t stride) {
+  local_coeffs_body<T, R>(blockIdx.x, nocc, occ_cells, occ_of_cell, L, Ne, M, V_all, LA, sigma_all, n_es, nfb2,
+                          gamma_all, stride);
 }
 
 // ------------------------------------------------------------ near field + assembly
@@ -477,7 +494,7 @@ __device__ __forceinline__ void near_chunk_pairs(const float2* __restrict__ wk, 
 }
 
 template <typename T, int R, int NRW>
-__device__ __forceinline__ void near_eval_body(const int2* __restrict__ items, const int64_t* __restrict__ occ_start,
+__device__ __forceinline__ void near_eval_body(const int2 item, const int64_t* __restrict__ occ_start,
                                                const int64_t* __restrict__ blk_off, const int* __restrict__ blk_seg,
                                                const T* __restrict__ Wb, const int64_t* __restrict__ rem_row,
                                                const int* __restrict__ rem_col, const T* __restrict__ rem_val,
@@ -488,7 +505,6 @@ __device__ __forceinline__ void near_eval_body(const int2* __restrict__ items, c
   T* us = reinterpret_cast<T*>(smem_raw);               // [rhs][column]
   constexpr int CH = kNearSmem / int(R * sizeof(T));    // columns per chunk (a multiple of 64)
   static_assert(CH % 64 == 0, "chunks must start at multiples of 64 columns");
-  const int2 item = items[blockIdx.x];
   const int k = item.x;
   const int* sg = blk_seg + 6 * k;
   const int l0 = sg[1], l1 = sg[3], l2 = sg[5];
@@ -582,7 +598,7 @@ __device__ __forceinline__ void near_eval_body(const int2* __restrict__ items, c
       const int *__restrict__ rem_col, const T *__restrict__ rem_val, const T *__restrict__ u, int64_t N,         \
       const T *__restrict__ Phi, const T *__restrict__ gamma, int nocc, int nfb2,                                 \
       typename RealOf<T>::R kappa2, T *__restrict__ out
-#define LS_NEAR_PASS items, occ_start, blk_off, blk_seg, Wb, rem_row, rem_col, rem_val, u, N, Phi, gamma, nocc, nfb2, \
+#define LS_NEAR_PASS items[blockIdx.x], occ_start, blk_off, blk_seg, Wb, rem_row, rem_col, rem_val, u, N, Phi, gamma, nocc, nfb2, \
                      kappa2, out
 // two rows per warp, 16-row items: registers left to the compiler
 template <typename T, int R>
@@ -635,6 +651,66 @@ cudaError_t apply_r(const ApplyData<T>& d, const T* u, T* out, cudaStream_t st, 
   if (ev) cudaEventRecord(ev[5], st);
   return cudaGetLastError();
 }
+
+// ------------------------------------------------------------ multi-instance batch
+template <typename T>
+__global__ void __launch_bounds__(256) k_es_project_multi(const int2* __restrict__ cells,
+                                                          const InstData<T>* __restrict__ I, const T* __restrict__ u) {
+  const int2 c = cells[blockIdx.x];
+  const ApplyData<T>& d = I[c.x].d;
+  es_project_body<T, 1>(c.y, blockIdx.y * 8 + (threadIdx.x >> 5), d.nocc, d.occ_start, d.P_off, d.P,
+                        u + I[c.x].off, d.N, d.sigma, d.n_es);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_local_coeffs_multi(const int2* __restrict__ cells,
+                                                            const InstData<T>* __restrict__ I) {
+  const int2 c = cells[blockIdx.x];
+  const ApplyData<T>& d = I[c.x].d;
+  local_coeffs_body<T, 1>(c.y, d.nocc, d.occ_cells, d.occ_of_cell, d.L, d.Ne, d.M, d.Sd, d.LA, d.sigma, d.n_es,
+                          d.nfb2, d.gamma, d.lattice_rows() * d.M);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_near_eval_multi(const int4* __restrict__ items,
+                                                         const InstData<T>* __restrict__ I, const T* __restrict__ u,
+                                                         T* __restrict__ out) {
+  const int4 it = items[blockIdx.x];
+  const ApplyData<T>& d = I[it.x].d;
+  const int64_t off = I[it.x].off;
+  near_eval_body<T, 1, 2>(make_int2(it.y, it.z), d.occ_start, d.blk_off, d.blk_seg, d.Wb, d.rem_row, d.rem_col,
+                          d.rem_val, u + off, d.N, d.Phi, d.gamma, d.nocc, d.nfb2,
+                          typename RealOf<T>::R(d.kappa2), out + off);
+}
+
+template <typename T>
+cudaError_t apply_multi(const InstData<T>* dev_inst, const InstData<T>* host_inst, const int* ids, int n_ids,
+                        const int2* cells, int n_cells, const int4* items, int n_items, int max_nes, int max_K,
+                        const T* u, T* out, cudaStream_t st) {
+  if (n_ids <= 0 || n_cells <= 0 || n_items <= 0) return cudaSuccess;
+  k_es_project_multi<T><<<dim3(n_cells, (max_nes + 7) / 8), 256, 0, st>>>(cells, dev_inst, u);
+  for (int j = 0; j < n_ids; ++j) {
+    cudaError_t e = lattice_conv(host_inst[ids[j]].d, 1, st);
+    if (e != cudaSuccess) return e;
+  }
+  const size_t sm_local = size_t(max_K) * sizeof(T);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_local_coeffs_multi<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+    attr = true;
+  }
+  if (sm_local > 160 * 1024) return cudaErrorInvalidValue;
+  k_local_coeffs_multi<T><<<n_cells, 256, sm_local, st>>>(cells, dev_inst);
+  k_near_eval_multi<T><<<n_items, 256, kNearSmem, st>>>(items, dev_inst, u, out);
+  return cudaGetLastError();
+}
+
+template cudaError_t apply_multi<double2>(const InstData<double2>*, const InstData<double2>*, const int*, int,
+                                          const int2*, int, const int4*, int, int, int, const double2*, double2*,
+                                          cudaStream_t);
+template cudaError_t apply_multi<float2>(const InstData<float2>*, const InstData<float2>*, const int*, int,
+                                         const int2*, int, const int4*, int, int, int, const float2*, float2*,
+                                         cudaStream_t);
 
 template <typename T>
 cudaError_t apply_batch(const ApplyData<T>& d, const T* u, T* out, int nr, cudaStream_t st, cudaEvent_t* ev) {

@@ -41,7 +41,7 @@ struct ApplyData {
   T* sigma = nullptr;                   // max_rhs x nocc x n_es
   T* Sm = nullptr;                      // max_rhs x lattice_rows() x M
   T* Sd = nullptr;                      // max_rhs x lattice_rows() x M
-  int64_t lattice_rows() const { return (2 * (L + 1) > n_lat ? 2 * (L + 1) : n_lat); }
+  __host__ __device__ int64_t lattice_rows() const { return (2 * (L + 1) > n_lat ? 2 * (L + 1) : n_lat); }
   T* gamma = nullptr;                   // max_rhs x nocc x nfb2
 };
 
@@ -64,6 +64,27 @@ template <typename T>
 cudaError_t apply_batch(const ApplyData<T>& d, const T* u, T* out, int nr, cudaStream_t st,
                         cudaEvent_t* ev = nullptr);
 constexpr int kMaxRhs64 = 4, kMaxRhs32 = 8;
+
+// One scatterer of a multi-instance batch: its apply data and the offset of
+// its nodes in the batch's concatenated vectors.
+template <typename T>
+struct InstData {
+  ApplyData<T> d;
+  int64_t off = 0;
+};
+
+// out = A_i u_i for the instances ids[0..n_ids) of a batch at once (one
+// right-hand side each; u, out: the concatenated vectors; the other instances'
+// parts of out are left untouched).  The projection, the local expansion and
+// the near field each run as ONE launch walking work lists over those
+// instances -- cells = (instance, occupied cell), items = (instance, occupied
+// cell, first of 16 rows, unused) -- and the lattice convolution runs per
+// instance (its size differs).  dev_inst is a device copy of host_inst; ids is
+// a host array; max_nes / max_K are the largest n_es and n_loc + 9 n_es.
+template <typename T>
+cudaError_t apply_multi(const InstData<T>* dev_inst, const InstData<T>* host_inst, const int* ids, int n_ids,
+                        const int2* cells, int n_cells, const int4* items, int n_items, int max_nes, int max_K,
+                        const T* u, T* out, cudaStream_t st);
 
 // 2-D FFT of an M x M array in place (rows then columns), forward or inverse
 // (unscaled).

@@ -87,6 +87,13 @@ _SIGS = {
     "ls_apply_noalloc": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
     "ls_check_cells": ([C.POINTER(Geometry), N2FN, C.c_void_p, C.c_double, C.POINTER(Options), C.c_void_p]),
     "ls_get_stage_times": ([C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
+    "ls_batch_create": ([C.c_void_p, C.c_int, C.POINTER(C.c_void_p)]),
+    "ls_batch_offsets": ([C.c_void_p, C.c_void_p]),
+    "ls_batch_apply": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
+    "ls_batch_solve": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_int, C.c_int, C.c_int,
+                        C.POINTER(SolveInfo), C.c_void_p, C.c_void_p]),
+    "ls_batch_destroy": ([C.c_void_p]),
+    "ls_batch_last_error": ([C.c_void_p]),
 }
 EXPORTED = tuple(_SIGS)
 
@@ -103,15 +110,17 @@ def load_library(path: str | None = None):
     for name, args in _SIGS.items():
         f = getattr(lib, name)
         f.argtypes = args
-        f.restype = C.c_char_p if name in ("ls_status_string", "ls_last_error") else C.c_int
+        f.restype = C.c_char_p if name in ("ls_status_string", "ls_last_error", "ls_batch_last_error") else C.c_int
     if path is None:
         _lib = lib
     return lib
 
 
-def _check(st: int, handle=None):
+def _check(st: int, handle=None, batch=False):
     if st != 0:
-        msg = _lib.ls_last_error(handle).decode() if _lib is not None else ""
+        msg = ""
+        if _lib is not None:
+            msg = (_lib.ls_batch_last_error if batch else _lib.ls_last_error)(handle).decode()
         raise LSError(st, msg)
 
 
@@ -316,6 +325,69 @@ class HostPlan:
     def close(self):
         if getattr(self, "_h", None):
             _lib.ls_host_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """A multi-instance batch (ls_batch_create) over existing Plans.  Vectors are
+    the instances' node vectors concatenated in plan order (offsets[i] ..
+    offsets[i + 1]); the plans must outlive the batch."""
+
+    def __init__(self, plans):
+        load_library()
+        self.plans = list(plans)
+        arr = (C.c_void_p * len(self.plans))(*[p._h.value for p in self.plans])
+        h = C.c_void_p()
+        st = _lib.ls_batch_create(arr, len(self.plans), C.byref(h))
+        if st != 0:
+            raise LSError(st, _lib.ls_batch_last_error(None).decode())
+        self._h = h
+        off = np.zeros(len(self.plans) + 1, np.int64)
+        _check(_lib.ls_batch_offsets(self._h, off.ctypes.data), self._h, batch=True)
+        self.offsets = off
+        self.N = int(off[-1])
+
+    def split(self, v):
+        """Views of the instances' parts of a concatenated vector."""
+        return [v[..., int(a):int(b)] for a, b in zip(self.offsets[:-1], self.offsets[1:])]
+
+    def apply(self, u, out=None, prec: int = LS_FP64, stream=None):
+        import torch
+        want = torch.complex128 if prec == LS_FP64 else torch.complex64
+        if u.dtype != want or not u.is_cuda or not u.is_contiguous() or u.numel() != self.N:
+            raise LSError(1, f"u must be a contiguous CUDA {want} tensor of length {self.N}")
+        if out is None:
+            out = torch.empty_like(u)
+        _check(_lib.ls_batch_apply(self._h, C.c_void_p(u.data_ptr()), C.c_void_p(out.data_ptr()), prec,
+                                   _stream(stream)), self._h, batch=True)
+        return out
+
+    def solve(self, uinc, u0=None, tol: float = 1e-10, max_iter: int = 500, restart: int = 100,
+              prec: int = LS_FP64, stream=None):
+        import torch
+        if uinc.dtype != torch.complex128 or not uinc.is_cuda or not uinc.is_contiguous() or uinc.numel() != self.N:
+            raise LSError(1, f"uinc must be a contiguous CUDA complex128 tensor of length {self.N}")
+        u = torch.zeros_like(uinc) if u0 is None else u0.clone()
+        info = SolveInfo()
+        per = (SolveInfo * len(self.plans))()
+        st = _lib.ls_batch_solve(self._h, C.c_void_p(uinc.data_ptr()), C.c_void_p(u.data_ptr()), tol, max_iter,
+                                 restart, prec, C.byref(info), per, _stream(stream))
+        res = {f: getattr(info, f) for f, _ in SolveInfo._fields_}
+        if st not in (0, 4):
+            _check(st, self._h, batch=True)
+        res["converged"] = st == 0
+        res["per_instance"] = [{f: getattr(p, f) for f, _ in SolveInfo._fields_} for p in per]
+        return u, res
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.ls_batch_destroy(self._h)
             self._h = None
 
     def __del__(self):

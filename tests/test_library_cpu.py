@@ -63,6 +63,12 @@ def test_invalid_arguments_return_status(lib):
     assert lib.ls_apply(None, None, None, 1, 0, None) == 1
     assert lib.ls_plan_destroy(None) == 0
     assert lib.ls_status_string(4) == b"no convergence"
+    hb = C.c_void_p()
+    assert lib.ls_batch_create(None, 0, C.byref(hb)) == 1
+    assert b"no plans" in lib.ls_batch_last_error(None)
+    assert lib.ls_batch_apply(None, None, None, 0, None) == 1
+    assert lib.ls_batch_solve(None, None, None, 1e-10, 10, 10, 0, None, None, None) == 1
+    assert lib.ls_batch_destroy(None) == 0
 
 
 def _small_disc():

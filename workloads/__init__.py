@@ -215,3 +215,53 @@ def cfg2(h: float = 0.0045, n1: int = 3200, L: int = 61, m: int = 11, N_eq: int 
 def n2_of(wl: Workload):
     """Callable x -> n^2(x) for the workload (input definition)."""
     return lambda x: n2_eval(wl.n2_kind, wl.n2_params, x)
+
+
+def scatterer(shape: str, scale: float, kappa: float, N_target: float, ppw_min: float = 24.0) -> Workload:
+    """A disc (radius `scale`, n^2 = 2) or kite (scaled by `scale`, n^2 = 1.5 +
+    0.5 exp(-|x/scale|^2 / 0.1)) with about N_target nodes: Cartesian spacing h
+    from the interior area, a 17-line collar of width 16 h (at most 0.07 scale
+    for the kite, below its smallest radius of curvature), tangential spacing
+    0.6 h, the cut-off radii of the kite workload in grid units; h is refined
+    to at least ppw_min points per wavelength.  The cell layout is left to the
+    library (L = 0, H = 11 h as a starting point)."""
+    if shape == "disc":
+        area, perim = math.pi * scale ** 2, 2 * math.pi * scale
+    else:
+        area, perim = 4.45 * scale ** 2, 8.5 * scale
+    # N ~ area / h^2 + 17 perim / (0.6 h): positive root of the quadratic in 1/h
+    b = 17 * perim / 0.6
+    inv_h = (-b + math.sqrt(b * b + 4 * area * N_target)) / (2 * area)
+    h = min(1.0 / inv_h, 2 * math.pi / (kappa * ppw_min))
+    n1 = max(64, int(round(perim / (0.6 * h) / 8)) * 8)
+    if shape == "disc":
+        x0, nx = _cart_grid_for(h, -scale, scale)
+        wl = Workload(name=f"disc_s{scale:.2f}_k{kappa:.1f}", shape="disc", shape_params=(scale, 0.0, 0.0),
+                      kappa=kappa, n2_kind="const", n2_params=(2.0,), collar_w=16 * h, n1=n1, n2=17,
+                      tau0=0.4, tau1=0.9, h=h, cart_x0=x0, cart_y0=x0, cart_nx=nx, cart_ny=nx,
+                      R_a=10, R_b=6, R_cart=8)
+        center = (0.0, 0.0)
+    else:
+        w = min(16 * h, 0.07 * scale)        # below the kite's radius of curvature (0.085 scale)
+        wl = kite(n1=n1, n2=17, h=h, kappa=kappa, scale=scale, collar_w=w, tau0=0.4, tau1=0.9,
+                  R_a=10, R_b=6, R_cart=8).replace(name=f"kite_s{scale:.2f}_k{kappa:.1f}")
+        center = (-0.25 * scale, 0.0)
+    wl = place_cells(wl, L=1, m=11, center=center, N_eq=8)
+    return wl.replace(L=0)
+
+
+def cfg3_instances(n: int = 48, seed: int = SEED + 3, N_lo: float = 2e4, N_hi: float = 1e6,
+                   scale_range=(0.5, 2.0), kappa_range=(5.0, 60.0)):
+    """The seed-drawn scatterers of the batched configuration: shape disc or
+    kite with probability 1/2, scale ~ U[scale_range], kappa ~ U[kappa_range],
+    N log-uniform in [N_lo, N_hi] (raised where 24 points per wavelength need
+    more), one plane wave along x1 each."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(n):
+        shape = "disc" if rng.random() < 0.5 else "kite"
+        scale = rng.uniform(*scale_range)
+        kappa = rng.uniform(*kappa_range)
+        N = math.exp(rng.uniform(math.log(N_lo), math.log(N_hi)))
+        out.append(scatterer(shape, scale, kappa, N))
+    return out
