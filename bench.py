@@ -185,6 +185,69 @@ def run_reference(args):
     return 0
 
 
+def run_batch(n_inst, dev, barrier, timed):
+    """Reduced config 3: n_inst seeded discs / kites (scale in [0.5, 1], kappa in
+    [5, 20], N log-uniform in [2e4, 1.2e5]) with autotuned layouts, as one
+    multi-instance batch: apply throughput (instance-matvecs/s) and the mixed
+    lock-step solve to 1e-10, against the instances' own applies and solves."""
+    import numpy as np
+    import torch
+    import workloads as W
+    from paper_1509_05063_gb300 import LS_FP64, LS_MIXED, Batch, Plan, autotune
+    insts = W.cfg3_instances(n_inst, N_lo=2e4, N_hi=1.2e5, scale_range=(0.5, 1.0), kappa_range=(5.0, 20.0))
+    t0 = time.perf_counter()
+    plans = []
+    for wl in insts:
+        tw, _ = autotune.tune(wl, W.n2_of(wl), target_eps=1e-9)
+        plans.append(Plan(tw, W.n2_of(tw)))
+    t_plan = time.perf_counter() - t0
+    b = Batch(plans)
+    out = {"instances": n_inst, "N_total": b.N, "N_each": [p.N for p in plans],
+           "kappa_each": [round(wl.kappa, 3) for wl in insts], "shape_each": [wl.shape for wl in insts],
+           "plan_s_total": t_plan}
+    steps = 20
+    for prec, dt, key in [(LS_FP64, torch.complex128, "fp64"), (LS_MIXED, torch.complex64, "mixed")]:
+        u = torch.from_numpy(W.random_density(b.N)[0]).to(dev, dt)
+        o = torch.empty_like(u)
+        for _ in range(3):
+            b.apply(u, o, prec=prec)
+        ms_b = timed(lambda: b.apply(u, o, prec=prec), steps)
+        pu = [x.contiguous() for x in b.split(u)]
+        po = [torch.empty_like(x) for x in pu]
+
+        def seq():
+            for p, x, y in zip(plans, pu, po):
+                p.apply(x, y, prec=prec)
+        for _ in range(3):
+            seq()
+        ms_s = timed(seq, steps)
+        out[key] = {"batch_apply_ms": ms_b / steps, "instance_matvecs_per_s": n_inst * steps / (ms_b * 1e-3),
+                    "separate_applies_ms": ms_s / steps}
+    parts = []
+    for wl, p in zip(insts, plans):
+        xy, _ = p.nodes()
+        parts.append(W.plane_wave(wl.kappa, wl.inc_dir, xy))
+    ui = torch.from_numpy(np.concatenate(parts)).to(dev)
+    b.solve(ui, tol=1e-3, prec=LS_MIXED, max_iter=3)
+    barrier()
+    t0 = time.perf_counter()
+    _, info = b.solve(ui, tol=1e-10, prec=LS_MIXED, max_iter=4000, restart=100)
+    barrier()
+    t_b = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    for p, x in zip(plans, b.split(ui)):
+        p.solve(x.contiguous(), tol=1e-10, prec=LS_MIXED, max_iter=4000, restart=100)
+    barrier()
+    t_s = time.perf_counter() - t0
+    out["solve_mixed"] = {"tol": 1e-10, "makespan_s": t_b, "separate_solves_s": t_s,
+                          "converged": info["converged"], "residual": info["residual"],
+                          "iterations_each": [r["iterations"] for r in info["per_instance"]]}
+    b.close()
+    for p in plans:
+        p.close()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -197,6 +260,10 @@ def main():
     ap.add_argument("--ref-rows", type=int, default=48)
     ap.add_argument("--autotune", action="store_true",
                     help="pick the cell layout with the autotuner (model + GPU timing of the best 3)")
+    ap.add_argument("--directions", type=int, default=8,
+                    help="incident directions of the lock-step mixed solve (theta_j = 2 pi j / D)")
+    ap.add_argument("--batch", type=int, default=0,
+                    help="also time a multi-instance batch of this many seeded scatterers (reduced config 3)")
     ap.add_argument("--scale", type=int, default=1,
                     help="coarsen config 2 by this factor (h, cells) for profiling captures")
     args = ap.parse_args()
@@ -311,8 +378,9 @@ def main():
         barrier()
         t32 = time.perf_counter() - t0
         diff = float(torch.linalg.vector_norm(s32 - s64) / torch.linalg.vector_norm(s64))
-        # block right-hand sides: 8 incident directions theta_j = 2 pi j / 8 in lock-step
-        th = [2 * math.pi * j / 8 for j in range(8)]
+        # block right-hand sides: D incident directions theta_j = 2 pi j / D in lock-step (batches of 8)
+        D = args.directions
+        th = [2 * math.pi * j / D for j in range(D)]
         UI = torch.from_numpy(np.stack([W.plane_wave(wl.kappa, (math.cos(t), math.sin(t)), xy) for t in th])).to(dev)
         barrier()
         t0 = time.perf_counter()
@@ -324,8 +392,11 @@ def main():
                  "mixed_s": t32, "mixed_inner_iterations": i32["iterations"],
                  "mixed_refinements": i32["refinements"], "mixed_residual": i32["residual"],
                  "mixed_converged": i32["converged"], "mixed_vs_fp64_solution_rel": diff,
-                 "mixed_8rhs_s": tb32, "mixed_8rhs_per_rhs_s": tb32 / 8, "mixed_8rhs_converged": ib32["converged"],
-                 "mixed_8rhs_residual": ib32["residual"], "mixed_8rhs_inner_iterations": ib32["iterations"]}
+                 "directions": D, "mixed_block_s": tb32, "mixed_block_per_rhs_s": tb32 / D,
+                 "mixed_block_converged": ib32["converged"], "mixed_block_residual": ib32["residual"],
+                 "mixed_block_inner_iterations": ib32["iterations"]}
+
+    batch = run_batch(args.batch, dev, barrier, timed) if args.batch > 0 else None
 
     # roofline of the dominant kernel (near field + local evaluation + assembly)
     nnz = info["nnz_near"]
@@ -393,6 +464,8 @@ def main():
         "apply_hbm_frac_fp64": (apply_bytes64 / (ms64 / args.steps * 1e-3) / 1e9) / peak,
         "time_to_tol": solve,
     }
+    if batch is not None:
+        line["batch"] = batch
     if cpu is not None:
         line["cpu_baseline"] = cpu
     if rank == 0:
