@@ -448,16 +448,20 @@ ls_status ls_plan_create(const ls_geometry* geom, ls_n2_fn n2, void* ctx, double
   const int* d_occ_of_cell = UP(int, occ_of_cell);
   const int* d_occ_of_node = UP(int, occ_of_node);
   const int64_t* d_P_off = UP(int64_t, P.P_off);
-  std::vector<int> items, items32;   // (occupied cell, first row) pairs, 16 / 32 rows each
+  std::vector<int> items, items32, items128;   // (occupied cell, first row) pairs, 16 / 32 / 128 rows each
   for (int k = 0; k < nocc; ++k)
     for (int64_t r = 0; r < occ_start[k + 1] - occ_start[k]; r += 16) {
       items.push_back(k); items.push_back(int(r));
       if (r % 32 == 0) { items32.push_back(k); items32.push_back(int(r)); }
+      if (r % 128 == 0) { items128.push_back(k); items128.push_back(int(r)); }
     }
   const int* d_items_raw = UP(int, items);
   const int2* d_items = reinterpret_cast<const int2*>(d_items_raw);
   const int* d_items32_raw = UP(int, items32);
   const int2* d_items32 = reinterpret_cast<const int2*>(d_items32_raw);
+  const int* d_items128_raw = UP(int, items128);
+  const int2* d_items128 = reinterpret_cast<const int2*>(d_items128_raw);
+  int* d_tc_err = UP(int, std::vector<int>(1, 0));
   const int64_t* d_blk_off = UP(int64_t, blk_off);
   const int* d_blk_seg = UP(int, blk_seg);
   const int64_t* d_rem_row = UP(int64_t, rem_row);
@@ -546,6 +550,8 @@ ls_status ls_plan_create(const ls_geometry* geom, ls_n2_fn n2, void* ctx, double
   b.max_nblk = a.max_nblk;
   b.items = a.items; b.n_items = a.n_items;
   b.items32 = a.items32; b.n_items32 = a.n_items32;
+  b.items128 = d_items128; b.n_items128 = int(items128.size() / 2);
+  b.tc_err = d_tc_err;
   b.P = UP(float2, to32(P.P32));
   b.LA = UP(float2, to32(LA));
   b.Phi = UP(float2, to32(P.Phi));

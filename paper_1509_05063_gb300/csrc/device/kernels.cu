@@ -639,7 +639,10 @@ cudaError_t apply_r(const ApplyData<T>& d, const T* u, T* out, cudaStream_t st, 
                                                        d.LA, d.sigma, d.n_es, d.nfb2, d.gamma,
                                                        d.lattice_rows() * d.M);
   if (ev) cudaEventRecord(ev[4], st);
-  if constexpr (near_rows_per_warp<T, R>() == 4)
+  if constexpr (sizeof(T) == 8 && R >= 8) {
+    const cudaError_t e2 = near_eval_tc<R>(d, u, out, st);
+    if (e2 != cudaSuccess) return e2;
+  } else if constexpr (near_rows_per_warp<T, R>() == 4)
     k_near_eval4<T, R><<<d.n_items32, 256, kNearSmem, st>>>(d.items32, d.occ_start, d.blk_off, d.blk_seg, d.Wb,
                                                             d.rem_row, d.rem_col, d.rem_val, u, d.N, d.Phi,
                                                             d.gamma, d.nocc, d.nfb2,
@@ -720,6 +723,9 @@ cudaError_t apply_batch(const ApplyData<T>& d, const T* u, T* out, int nr, cudaS
     case 4: return apply_r<T, 4>(d, u, out, st, ev);
     case 8:
       if constexpr (sizeof(T) == 8) return apply_r<T, 8>(d, u, out, st, ev);
+      return cudaErrorInvalidValue;
+    case 16:
+      if constexpr (sizeof(T) == 8) return apply_r<T, 16>(d, u, out, st, ev);
       return cudaErrorInvalidValue;
     default: return cudaErrorInvalidValue;
   }

@@ -32,6 +32,9 @@ struct ApplyData {
   int n_items = 0;
   const int2* items32 = nullptr;        // the same with 32 rows per item (multi-RHS complex64)
   int n_items32 = 0;
+  const int2* items128 = nullptr;       // 128-row items (tensor-core near field, 8 or 16 complex64 RHS)
+  int n_items128 = 0;
+  int* tc_err = nullptr;                // set by the tensor-core near field when a wait times out
   const T* Wb = nullptr;                // blocks, row-major per cell
   const int64_t* rem_row = nullptr;     // N + 1
   const int* rem_col = nullptr;
@@ -57,13 +60,19 @@ template <typename T>
 cudaError_t apply_one(const ApplyData<T>& d, const T* u, T* out, cudaStream_t st, cudaEvent_t* ev = nullptr);
 
 // out = A u for nr right-hand sides at once (nr in {1, 2, 4} for complex128,
-// {1, 2, 4, 8} for complex64; u, out: nr vectors of length N one after
+// {1, 2, 4, 8, 16} for complex64, 8 and 16 with the tensor-core near field; u, out: nr vectors of length N one after
 // another): one pass over the near-field weights serves all of them.  The work
 // arrays must hold max_rhs right-hand sides.
 template <typename T>
 cudaError_t apply_batch(const ApplyData<T>& d, const T* u, T* out, int nr, cudaStream_t st,
                         cudaEvent_t* ev = nullptr);
-constexpr int kMaxRhs64 = 4, kMaxRhs32 = 8;
+constexpr int kMaxRhs64 = 4, kMaxRhs32 = 16;
+
+// Near field + evaluation + assembly of R complex64 right-hand sides (R = 8 or
+// 16) on the tensor cores (tcgen05, 3xTF32; device/near_tc.cu); same result as
+// the CUDA-core kernel up to FP32 rounding.
+template <int R>
+cudaError_t near_eval_tc(const ApplyData<float2>& d, const float2* u, float2* out, cudaStream_t st);
 
 // One scatterer of a multi-instance batch: its apply data and the offset of
 // its nodes in the batch's concatenated vectors.
