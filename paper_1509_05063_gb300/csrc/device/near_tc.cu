@@ -14,24 +14,29 @@
 // truncation (which is what the tensor core reads from an FP32 word) and lo
 // exact in FP32,
 //   D = A_hi B_hi + A_lo B_hi + A_hi B_lo  (the lo.lo term, 2^-22 relative, is dropped)
-// done as ONE accumulator of N = 4R columns: the K range is doubled, [A | A_lo]
-// against [[B_hi, B_lo]; [B_hi, 0]], and the two column halves are added in
-// the epilogue.
+// done with N = 4R columns: the K range is doubled, [A | A_lo] against
+// [[B_hi, B_lo]; [B_hi, 0]], and the two column halves are added in the
+// epilogue.  The four K steps of a chunk accumulate into four separate
+// tensor-memory accumulators, so that consecutive MMAs do not wait on one
+// another's result; the epilogue sums them.
 //
-// Pipeline (128 threads, thread t = row t of the tile; kTcStages shared-memory
-// stages of 8 complex columns): cp.async streams the raw weights of chunk
-// c + 2 into the canonical K-major no-swizzle layout (8-row x 16-byte core
-// matrices; LBO = 128 B between K-adjacent core matrices, SBO = 1024 B between
-// row groups) together with the chunk's input values u; for chunk c each
-// thread writes the lo part of its own row and the B rows are built from the
-// staged u; after one block barrier an elected thread issues the four
-// tcgen05.mma (M = 128, N = 4R, K = 8) of the chunk and commits them to the
-// stage's mbarrier, which every thread polls before it refills that stage.
-// The accumulator lives in tensor memory and is read back with tcgen05.ld; the
-// epilogue adds the CSR remainder and the local expansion Phi_q . gamma_c and
-// writes out_q = u_q + kappa^2 (near + far).
-// Every wait is bounded: on time-out the block sets *err, drains its copies,
-// frees its tensor memory and leaves its rows unwritten.
+// Pipeline (warp-specialised: 128 producer threads, thread t = row t of the
+// tile, plus one MMA warp; chunks of 8 complex columns): every producer keeps
+// the next kTcAhead chunks of its row (and one input value u_j[column]) in
+// flight in registers; for chunk c it waits until the MMAs of chunk
+// c - kTcStages have released the stage, writes the raw weights and their lo
+// parts into the stage in the canonical K-major no-swizzle layout (8-row x
+// 16-byte core matrices; LBO = 128 B between K-adjacent core matrices,
+// SBO = 1024 B between row groups), builds its B entries from the input
+// values and arrives on the stage's "full" mbarrier.  Lane 0 of the MMA warp
+// waits for "full", issues the chunk's four tcgen05.mma (M = 128, N = 4R,
+// K = 8) and commits them to the stage's "empty" mbarrier.  No block barrier
+// inside the loop.  The accumulators live in tensor memory and are read back
+// with tcgen05.ld; the epilogue adds the CSR remainder and the local expansion
+// Phi_q . gamma_c and writes out_q = u_q + kappa^2 (near + far).
+// Every wait is bounded: on time-out a thread leaves its loop and flags the
+// block, which then sets *err, lets its MMAs in flight finish (bounded), frees
+// its tensor memory and leaves its rows unwritten.
 #include <cstdint>
 
 #include "device/cplx.cuh"
@@ -40,10 +45,11 @@
 namespace lsd {
 namespace {
 
-constexpr int kTcRows = 128;          // rows per tile = MMA M
+constexpr int kTcRows = 128;          // rows per tile = MMA M = producer threads
+constexpr int kTcThreads = kTcRows + 32;   // + one warp whose lane 0 issues the MMAs
 constexpr int kTcKC = 8;              // complex columns per chunk
-constexpr int kTcStages = 4;
-constexpr int kTcAhead = 2;           // chunks loaded ahead of the one being prepared
+constexpr int kTcStages = 3;          // shared-memory stages (operand tiles of the MMAs in flight)
+constexpr int kTcAhead = 4;           // chunks held in registers ahead of the one being prepared
 constexpr int kTcKgroups = 2 * kTcKC / 2;  // 16-byte core-matrix columns per row: 4 raw + 4 lo
 constexpr int kTcSBO = kTcKgroups * 128;   // bytes between 8-row groups (A and B)
 constexpr int kTcSpin = 1 << 22;      // polls of an mbarrier before giving up
@@ -89,10 +95,15 @@ struct TcLayout {
   static constexpr int NN = 4 * R;                                 // MMA N
   static constexpr int kA = kTcRows * kTcKgroups * 16;             // 16 KB: 128 rows x 32 fp32
   static constexpr int kB = NN * kTcKgroups * 16;                  // NN rows x 32 fp32
-  static constexpr int kU = R * kTcKC * 8;                         // staged inputs of the chunk
-  static constexpr int kStage = kA + kB + kU;
-  static constexpr int kBytes = kTcStages * kStage + 128;          // + mbarriers, tensor-memory address, flag
-  static constexpr int kTmemCols = NN < 32 ? 32 : NN;              // power of two >= 32
+  static constexpr int kStage = kA + kB;
+  // four accumulators (one per K step of a chunk: independent MMA chains)
+  static constexpr int kTmemCols = 4 * NN < 32 ? 32 : 4 * NN;      // power of two >= 32
+  // at most 512 / kTmemCols blocks may share an SM's tensor memory: pad the
+  // shared memory so that no more blocks fit
+  static constexpr int kBlocksMax = 512 / kTmemCols;
+  static constexpr int kRaw = kTcStages * kStage + 128;            // + mbarriers, tensor-memory address, flag
+  static constexpr int kFloor = 232448 / (kBlocksMax + 1) + 1;     // 227 KB / (max + 1)
+  static constexpr int kBytes = kRaw > kFloor ? kRaw : kFloor;
 };
 
 // write (v.x, v.y) at B[n][kq], B[n][kq + 1] (kq even)
@@ -101,26 +112,30 @@ __device__ __forceinline__ void put_b(unsigned char* B, int n, int kq, float2 v)
 }
 
 template <int R>
-__global__ void __launch_bounds__(kTcRows) k_near_tc(const int2* __restrict__ items,
-                                                     const int64_t* __restrict__ occ_start,
-                                                     const int64_t* __restrict__ blk_off,
-                                                     const int* __restrict__ blk_seg, const float2* __restrict__ Wb,
-                                                     const int64_t* __restrict__ rem_row,
-                                                     const int* __restrict__ rem_col,
-                                                     const float2* __restrict__ rem_val,
-                                                     const float2* __restrict__ u, int64_t N,
-                                                     const float2* __restrict__ Phi, const float2* __restrict__ gamma,
-                                                     int nocc, int nfb2, float kappa2, float2* __restrict__ out,
-                                                     int* __restrict__ err) {
+__global__ void __launch_bounds__(kTcThreads) k_near_tc(const int2* __restrict__ items,
+                                                        const int64_t* __restrict__ occ_start,
+                                                        const int64_t* __restrict__ blk_off,
+                                                        const int* __restrict__ blk_seg,
+                                                        const float2* __restrict__ Wb,
+                                                        const int64_t* __restrict__ rem_row,
+                                                        const int* __restrict__ rem_col,
+                                                        const float2* __restrict__ rem_val,
+                                                        const float2* __restrict__ u, int64_t N,
+                                                        const float2* __restrict__ Phi,
+                                                        const float2* __restrict__ gamma, int nocc, int nfb2,
+                                                        float kappa2, float2* __restrict__ out,
+                                                        int* __restrict__ err) {
   using Lay = TcLayout<R>;
   constexpr int NN = Lay::NN;
-  static_assert(R * kTcKC <= kTcRows, "one staged input per thread");
+  static_assert(R * kTcKC <= kTcRows, "one input value per thread and chunk");
   extern __shared__ __align__(1024) unsigned char sm[];
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + kTcStages * Lay::kStage);
+  uint64_t* full = reinterpret_cast<uint64_t*>(sm + kTcStages * Lay::kStage);     // stage written (128 arrivals)
+  uint64_t* empty = full + kTcStages;                                             // stage read by the MMAs
   uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + kTcStages * Lay::kStage + 64);
-  int* sflag = reinterpret_cast<int*>(sm + kTcStages * Lay::kStage + 96);
+  int* sflag = reinterpret_cast<int*>(sm + kTcStages * Lay::kStage + 72);
 
   const int t = threadIdx.x, warp = t >> 5;
+  const bool producer = t < kTcRows;
   const int2 item = items[blockIdx.x];
   const int k = item.x;
   const int* sg = blk_seg + 6 * k;
@@ -130,10 +145,10 @@ __global__ void __launch_bounds__(kTcRows) k_near_tc(const int2* __restrict__ it
   const int64_t r0 = occ_start[k];
   const int nrow = int(occ_start[k + 1] - r0);
   const int row = item.y + t;
-  const bool valid = row < nrow;
+  const bool valid = producer && row < nrow;
   const float2* wrow = Wb + blk_off[k] + int64_t(valid ? row : item.y) * nblk;
   const int nchunk = (nblk + kTcKC - 1) / kTcKC;
-  // staged input of this thread: RHS j, column cc of every chunk
+  // input value of this thread: RHS j, column cc of every chunk
   const int uj = t % R, ucc = t / R;
 
   if (warp == 0) {
@@ -142,8 +157,10 @@ __global__ void __launch_bounds__(kTcRows) k_near_tc(const int2* __restrict__ it
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   if (t == 0) {
-    for (int s = 0; s < kTcStages; ++s)
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(s_u32(&mbar[s])), "r"(1) : "memory");
+    for (int s = 0; s < kTcStages; ++s) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(s_u32(&full[s])), "r"(kTcRows) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(s_u32(&empty[s])), "r"(1) : "memory");
+    }
     *sflag = 0;
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -151,108 +168,128 @@ __global__ void __launch_bounds__(kTcRows) k_near_tc(const int2* __restrict__ it
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tslot;
 
-  // raw weights of chunk c (k-groups 0..3 of row t) and its inputs -> stage c % kTcStages
-  auto issue = [&](int c) {
-    unsigned char* A = sm + (c % kTcStages) * Lay::kStage;
-    const int c0 = c * kTcKC;
+  if (producer) {
+    // chunk c of this thread: its row's 8 complex weights (4 x 16 B) and, for
+    // the first R * kTcKC threads, one input value u_j[column]; zero outside
+    auto load = [&](int c, float4 (&w)[kTcKC / 2], float2& uv) {
+      const int c0 = c * kTcKC;
 #pragma unroll
-    for (int p = 0; p < kTcKC / 2; ++p) {
-      const int col = c0 + 2 * p;
-      const bool in = valid && col < nblk;
-      const float2* src = wrow + (in ? col : 0);
-      const uint32_t dst = s_u32(A + (t >> 3) * kTcSBO + p * 128 + (t & 7) * 16);
-      asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" :: "r"(dst), "l"(src), "r"(in ? 16 : 0)
-                   : "memory");
-    }
-    if (t < R * kTcKC) {
-      const int col = c0 + ucc;
-      int64_t node = -1;
-      if (col < p0) { if (col < l0) node = sg[0] + col; }
-      else if (col < p0 + p1) { const int o = col - p0; if (o < l1) node = sg[2] + o; }
-      else if (col < nblk) { const int o = col - p0 - p1; if (o < l2) node = sg[4] + o; }
-      const float2* src = node >= 0 ? u + int64_t(uj) * N + node : u;
-      const uint32_t dst = s_u32(A + Lay::kA + Lay::kB + (ucc * R + uj) * 8);
-      asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" :: "r"(dst), "l"(src), "r"(node >= 0 ? 8 : 0)
-                   : "memory");
-    }
-  };
-  auto commit = [] { asm volatile("cp.async.commit_group;" ::: "memory"); };
-
-  // M = 128, N = NN, A and B TF32 (K-major), D FP32
-  const uint32_t idesc =
-      (1u << 4) | (2u << 7) | (2u << 10) | (uint32_t(NN >> 3) << 17) | (uint32_t(kTcRows >> 4) << 24);
-
-  for (int c = 0; c < kTcAhead; ++c) {
-    if (c < nchunk) issue(c);
-    commit();
-  }
-  bool ok = true;
-  int committed = 0;                       // chunks whose MMAs thread 0 has committed
-  for (int c = 0; c < nchunk; ++c) {
-    const int s = c % kTcStages;
-    // refill stage (c + kTcAhead) % kTcStages, last read by the MMAs of chunk c + kTcAhead - kTcStages
-    const int cl = c + kTcAhead - kTcStages;
-    if (cl >= 0 && !mbar_wait(s_u32(&mbar[cl % kTcStages]), (cl / kTcStages) & 1)) *sflag = 1;
-    if (c + kTcAhead < nchunk) issue(c + kTcAhead);
-    commit();
-    asm volatile("cp.async.wait_group %0;" :: "n"(kTcAhead) : "memory");
-    unsigned char* A = sm + s * Lay::kStage;
-    unsigned char* B = A + Lay::kA;
-    // lo part of this thread's row -> k-groups 4..7
-#pragma unroll
-    for (int p = 0; p < kTcKC / 2; ++p) {
-      const float4 x = *reinterpret_cast<const float4*>(A + (t >> 3) * kTcSBO + p * 128 + (t & 7) * 16);
-      *reinterpret_cast<float4*>(A + (t >> 3) * kTcSBO + (4 + p) * 128 + (t & 7) * 16) =
-          make_float4(lo_tf32(x.x), lo_tf32(x.y), lo_tf32(x.z), lo_tf32(x.w));
-    }
-    // B rows of chunk c: thread (cc, j) for complex column cc and RHS j (it staged that input itself)
-    if (t < R * kTcKC) {
-      const float2 v = *reinterpret_cast<const float2*>(A + Lay::kA + Lay::kB + (ucc * R + uj) * 8);
-      const float ur = v.x, ui = v.y;
-      const int j = uj, cc = ucc;
-      put_b(B, j, 2 * cc, make_float2(ur, -ui));
-      put_b(B, R + j, 2 * cc, make_float2(ui, ur));
-      put_b(B, 2 * R + j, 2 * cc, make_float2(lo_tf32(ur), lo_tf32(-ui)));
-      put_b(B, 3 * R + j, 2 * cc, make_float2(lo_tf32(ui), lo_tf32(ur)));
-      put_b(B, j, 16 + 2 * cc, make_float2(ur, -ui));      // rows against A_lo: B_hi, then zero
-      put_b(B, R + j, 16 + 2 * cc, make_float2(ui, ur));
-      put_b(B, 2 * R + j, 16 + 2 * cc, make_float2(0.f, 0.f));
-      put_b(B, 3 * R + j, 16 + 2 * cc, make_float2(0.f, 0.f));
-    }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
-    if (*sflag) { ok = false; break; }     // a wait above timed out (uniform after the barrier)
-    if (t == 0) {
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t a0 = s_u32(A), b0 = s_u32(B);
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {        // K = 8 per MMA: k-groups 2i, 2i + 1
-        const uint64_t da = s_desc(a0 + 2 * i * 128, 128, kTcSBO);
-        const uint64_t db = s_desc(b0 + 2 * i * 128, 128, kTcSBO);
-        asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                     " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n"
-                     :: "r"(tmem), "l"(da), "l"(db), "r"(idesc), "r"((c > 0 || i > 0) ? 1 : 0) : "memory");
+      for (int p = 0; p < kTcKC / 2; ++p) {
+        const int col = c0 + 2 * p;
+        w[p] = (valid && col < nblk) ? __ldcs(reinterpret_cast<const float4*>(wrow + col))
+                                     : make_float4(0.f, 0.f, 0.f, 0.f);
       }
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                   :: "r"(s_u32(&mbar[s])) : "memory");
-      committed = c + 1;
+      uv = make_float2(0.f, 0.f);
+      if (t < R * kTcKC) {
+        const int col = c0 + ucc;
+        int64_t node = -1;
+        if (col < p0) { if (col < l0) node = sg[0] + col; }
+        else if (col < p0 + p1) { const int o = col - p0; if (o < l1) node = sg[2] + o; }
+        else if (col < nblk) { const int o = col - p0 - p1; if (o < l2) node = sg[4] + o; }
+        if (node >= 0) uv = u[int64_t(uj) * N + node];
+      }
+    };
+    // register ring of the next kTcAhead chunks (loads in flight while earlier chunks are written)
+    float4 wbuf[kTcAhead][kTcKC / 2];
+    float2 ubuf[kTcAhead];
+#pragma unroll
+    for (int q = 0; q < kTcAhead; ++q)
+      if (q < nchunk) load(q, wbuf[q], ubuf[q]);
+    bool live = true;
+    for (int cb = 0; cb < nchunk && live; cb += kTcAhead) {
+#pragma unroll
+      for (int q = 0; q < kTcAhead; ++q) {
+        const int c = cb + q;
+        if (c >= nchunk) break;
+        const int s = c % kTcStages;
+        // stage s was last read by the MMAs of chunk c - kTcStages
+        if (c >= kTcStages && !mbar_wait(s_u32(&empty[s]), ((c - kTcStages) / kTcStages) & 1)) {
+          *sflag = 1;
+          live = false;
+          break;
+        }
+        unsigned char* A = sm + s * Lay::kStage;
+        unsigned char* B = A + Lay::kA;
+        // raw weights -> k-groups 0..3 of row t, their lo parts -> k-groups 4..7
+#pragma unroll
+        for (int p = 0; p < kTcKC / 2; ++p) {
+          const float4 x = wbuf[q][p];
+          *reinterpret_cast<float4*>(A + (t >> 3) * kTcSBO + p * 128 + (t & 7) * 16) = x;
+          *reinterpret_cast<float4*>(A + (t >> 3) * kTcSBO + (4 + p) * 128 + (t & 7) * 16) =
+              make_float4(lo_tf32(x.x), lo_tf32(x.y), lo_tf32(x.z), lo_tf32(x.w));
+        }
+        // B rows of chunk c: thread (cc, j) for complex column cc and RHS j
+        if (t < R * kTcKC) {
+          const float ur = ubuf[q].x, ui = ubuf[q].y;
+          const int j = uj, cc = ucc;
+          put_b(B, j, 2 * cc, make_float2(ur, -ui));
+          put_b(B, R + j, 2 * cc, make_float2(ui, ur));
+          put_b(B, 2 * R + j, 2 * cc, make_float2(lo_tf32(ur), lo_tf32(-ui)));
+          put_b(B, 3 * R + j, 2 * cc, make_float2(lo_tf32(ui), lo_tf32(ur)));
+          put_b(B, j, 16 + 2 * cc, make_float2(ur, -ui));      // rows against A_lo: B_hi, then zero
+          put_b(B, R + j, 16 + 2 * cc, make_float2(ui, ur));
+          put_b(B, 2 * R + j, 16 + 2 * cc, make_float2(0.f, 0.f));
+          put_b(B, 3 * R + j, 16 + 2 * cc, make_float2(0.f, 0.f));
+        }
+        if (c + kTcAhead < nchunk) load(c + kTcAhead, wbuf[q], ubuf[q]);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(s_u32(&full[s])) : "memory");
+      }
+    }
+    // the last MMAs
+    if (live && nchunk > 0 &&
+        !mbar_wait(s_u32(&empty[(nchunk - 1) % kTcStages]), ((nchunk - 1) / kTcStages) & 1))
+      *sflag = 1;
+  } else {
+    // MMA warp (converged; lane 0 issues): four MMAs per chunk once its stage
+    // is written, into four accumulators (M = 128, N = NN, A and B TF32
+    // K-major, D FP32)
+    const bool leader = (t & 31) == 0;
+    const uint32_t idesc =
+        (1u << 4) | (2u << 7) | (2u << 10) | (uint32_t(NN >> 3) << 17) | (uint32_t(kTcRows >> 4) << 24);
+    for (int c = 0; c < nchunk; ++c) {
+      const int s = c % kTcStages;
+      const bool ready = mbar_wait(s_u32(&full[s]), (c / kTcStages) & 1);
+      if (!__all_sync(0xffffffffu, ready)) {
+        *sflag = 1;
+        break;
+      }
+      if (leader) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t a0 = s_u32(sm + s * Lay::kStage), b0 = a0 + Lay::kA;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {      // K = 8 per MMA: k-groups 2i, 2i + 1
+          const uint64_t da = s_desc(a0 + 2 * i * 128, 128, kTcSBO);
+          const uint64_t db = s_desc(b0 + 2 * i * 128, 128, kTcSBO);
+          asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                       " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n"
+                       :: "r"(tmem + uint32_t(i * NN)), "l"(da), "l"(db), "r"(idesc), "r"(c > 0 ? 1 : 0)
+                       : "memory");
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                     :: "r"(s_u32(&empty[s])) : "memory");
+      }
+      __syncwarp();
     }
   }
-  if (ok && nchunk > 0) {
-    if (t == 0 && !mbar_wait(s_u32(&mbar[(nchunk - 1) % kTcStages]), ((nchunk - 1) / kTcStages) & 1)) *sflag = 1;
-    __syncthreads();
-    ok = !*sflag;
-  }
-  asm volatile("cp.async.wait_all;" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  if (ok) {
+  const bool ok = *sflag == 0;
+  if (ok && producer) {
     float d[NN];
+#pragma unroll
+    for (int i = 0; i < NN; ++i) d[i] = 0.f;
     if (nchunk > 0) {
+#pragma unroll 1
+      for (int a = 0; a < 4; ++a)          // sum of the four accumulators
 #pragma unroll
-      for (int q = 0; q < NN / 16; ++q) tmem_load16(tmem + (uint32_t(warp * 32) << 16) + 16 * q, d + 16 * q);
-    } else {
+        for (int q = 0; q < NN / 16; ++q) {
+          float v[16];
+          tmem_load16(tmem + (uint32_t(warp * 32) << 16) + uint32_t(a * NN + 16 * q), v);
 #pragma unroll
-      for (int i = 0; i < NN; ++i) d[i] = 0.f;
+          for (int i = 0; i < 16; ++i) d[16 * q + i] += v[i];
+        }
     }
     if (valid) {
       float2 acc[R];
@@ -277,11 +314,13 @@ __global__ void __launch_bounds__(kTcRows) k_near_tc(const int2* __restrict__ it
         out[int64_t(j) * N + q] = make_float2(uq.x + kappa2 * acc[j].x, uq.y + kappa2 * acc[j].y);
       }
     }
-  } else if (t == 0) {
+  } else if (!ok && t == 0) {
     atomicExch(err, 1);
-    // let the MMAs still in flight finish (bounded) before the tensor memory is released
-    for (int c = committed > kTcStages ? committed - kTcStages : 0; c < committed; ++c)
-      mbar_wait(s_u32(&mbar[c % kTcStages]), (c / kTcStages) & 1);
+    // let MMAs still in flight finish (bounded) before the tensor memory is released
+    for (int s = 0; s < kTcStages; ++s) {
+      mbar_wait(s_u32(&empty[s]), 0);
+      mbar_wait(s_u32(&empty[s]), 1);
+    }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
@@ -302,7 +341,7 @@ cudaError_t near_eval_tc(const ApplyData<float2>& d, const float2* u, float2* ou
     attr = true;
   }
   if (d.n_items128 == 0) return cudaSuccess;
-  k_near_tc<R><<<d.n_items128, kTcRows, Lay::kBytes, st>>>(d.items128, d.occ_start, d.blk_off, d.blk_seg, d.Wb,
+  k_near_tc<R><<<d.n_items128, kTcThreads, Lay::kBytes, st>>>(d.items128, d.occ_start, d.blk_off, d.blk_seg, d.Wb,
                                                            d.rem_row, d.rem_col, d.rem_val, u, d.N, d.Phi, d.gamma,
                                                            d.nocc, d.nfb2, float(d.kappa2), out, d.tc_err);
   return cudaGetLastError();
