@@ -99,62 +99,74 @@ __global__ void __launch_bounds__(256) k_lattice_fill(int M, int n_lat, int Ne, 
 // G = N / 8 threads of the block (thread t): 2 radix-4 butterflies or 4
 // radix-2 butterflies per thread and stage.  Every stage reads all inputs to
 // registers, synchronises the block, then writes, so one buffer suffices.
-// tw[m] = exp(-2 pi i m / N); the inverse uses conjugate twiddles (no scaling).
+// tw[m * tws] = exp(-2 pi i m / N) (tws > 1: a sub-length transform on a
+// longer table); the inverse uses conjugate twiddles (no scaling).  Threads
+// with active == false only take part in the block barriers (every thread of
+// the block must call with the same N).
 template <typename T>
-__device__ void fft_smem(T* x, int N, int logN, bool inv, const T* __restrict__ tw, int t) {
+__device__ void fft_smem(T* x, int N, int logN, bool inv, const T* __restrict__ tw, int t, int tws = 1,
+                         bool active = true) {
   const int G = N / 8;
   int Ns = 1;
   if (logN & 1) {
     T a[8];
+    if (active) {
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      const int j = t + c * G;
-      a[2 * c] = x[j];
-      a[2 * c + 1] = x[j + N / 2];
+      for (int c = 0; c < 4; ++c) {
+        const int j = t + c * G;
+        a[2 * c] = x[j];
+        a[2 * c + 1] = x[j + N / 2];
+      }
     }
     __syncthreads();
+    if (active) {
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      const int j = t + c * G;
-      x[2 * j] = cadd(a[2 * c], a[2 * c + 1]);
-      x[2 * j + 1] = csub(a[2 * c], a[2 * c + 1]);
+      for (int c = 0; c < 4; ++c) {
+        const int j = t + c * G;
+        x[2 * j] = cadd(a[2 * c], a[2 * c + 1]);
+        x[2 * j + 1] = csub(a[2 * c], a[2 * c + 1]);
+      }
     }
     __syncthreads();
     Ns = 2;
   }
   for (; Ns < N; Ns *= 4) {
     T v[2][4];
-    const int tstep = N / (4 * Ns);
+    const int tstep = N / (4 * Ns) * tws;
+    if (active) {
 #pragma unroll
-    for (int c = 0; c < 2; ++c) {
-      const int j = t + c * G;
-      const int k = j & (Ns - 1);
+      for (int c = 0; c < 2; ++c) {
+        const int j = t + c * G;
+        const int k = j & (Ns - 1);
 #pragma unroll
-      for (int r = 0; r < 4; ++r) v[c][r] = x[j + r * (N / 4)];
-      if (Ns > 1) {
+        for (int r = 0; r < 4; ++r) v[c][r] = x[j + r * (N / 4)];
+        if (Ns > 1) {
 #pragma unroll
-        for (int r = 1; r < 4; ++r) {
-          T w = tw[r * k * tstep];
-          if (inv) w = cconj(w);
-          v[c][r] = cmul(v[c][r], w);
+          for (int r = 1; r < 4; ++r) {
+            T w = tw[r * k * tstep];
+            if (inv) w = cconj(w);
+            v[c][r] = cmul(v[c][r], w);
+          }
         }
+        const T s02 = cadd(v[c][0], v[c][2]), d02 = csub(v[c][0], v[c][2]);
+        const T s13 = cadd(v[c][1], v[c][3]), d13 = csub(v[c][1], v[c][3]);
+        const T rot = inv ? cmul_i(d13) : cmul_mi(d13);   // (-i or +i) (v1 - v3)
+        v[c][0] = cadd(s02, s13);
+        v[c][2] = csub(s02, s13);
+        v[c][1] = cadd(d02, rot);
+        v[c][3] = csub(d02, rot);
       }
-      const T s02 = cadd(v[c][0], v[c][2]), d02 = csub(v[c][0], v[c][2]);
-      const T s13 = cadd(v[c][1], v[c][3]), d13 = csub(v[c][1], v[c][3]);
-      const T rot = inv ? cmul_i(d13) : cmul_mi(d13);   // (-i or +i) (v1 - v3)
-      v[c][0] = cadd(s02, s13);
-      v[c][2] = csub(s02, s13);
-      v[c][1] = cadd(d02, rot);
-      v[c][3] = csub(d02, rot);
     }
     __syncthreads();
+    if (active) {
 #pragma unroll
-    for (int c = 0; c < 2; ++c) {
-      const int j = t + c * G;
-      const int k = j & (Ns - 1);
-      const int base = (j - k) * 4 + k;
+      for (int c = 0; c < 2; ++c) {
+        const int j = t + c * G;
+        const int k = j & (Ns - 1);
+        const int base = (j - k) * 4 + k;
 #pragma unroll
-      for (int r = 0; r < 4; ++r) x[base + r * Ns] = v[c][r];
+        for (int r = 0; r < 4; ++r) x[base + r * Ns] = v[c][r];
+      }
     }
     __syncthreads();
   }
@@ -259,12 +271,17 @@ __global__ void __launch_bounds__(kFftMaxM / 8) k_src_rows(int M, int logM, int 
   for (int b = threadIdx.x; b < M; b += blockDim.x) out[b] = s[b];
 }
 
-// spectra quarter layout: Q[l][k] for l, k in [0, M/2] (k fastest)
+// spectra quarter layout: Q[l][k] for l, k in [0, M/2] (k fastest).
+// The sources of a column sit only at a = k Ne (k = 0..L), so when Ne divides M
+// the length-M forward transform is a length-M/Ne transform of the L + 1 values
+// repeated Ne times: X[f] = Y[f mod (M/Ne)].  Ms = M/Ne (0: use the full
+// length), logMs its log2.
 template <typename T>
-__global__ void __launch_bounds__(1024) k_conv_cols(int M, int logM, int n_lat, int Ne, int L, int TC,
-                                                    const T* __restrict__ R_all, const T* __restrict__ Gq,
-                                                    const T* __restrict__ Dq, const T* __restrict__ tw,
-                                                    T* __restrict__ Vt_all, int64_t stride) {
+__global__ void __launch_bounds__(1024) k_conv_cols(int M, int logM, int n_lat, int Ne, int L, int TC, int Ms,
+                                                    int logMs, const T* __restrict__ R_all,
+                                                    const T* __restrict__ Gq, const T* __restrict__ Dq,
+                                                    const T* __restrict__ tw, T* __restrict__ Vt_all,
+                                                    int64_t stride) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const T* R = R_all + int64_t(blockIdx.y) * stride;
   T* Vt = Vt_all + int64_t(blockIdx.y) * stride;
@@ -272,33 +289,65 @@ __global__ void __launch_bounds__(1024) k_conv_cols(int M, int logM, int n_lat, 
   T* xd = xm + TC * M;                         // [TC][M]
   const int b0 = blockIdx.x * TC;
   const int half = M / 2;
-  for (int e = threadIdx.x; e < TC * M; e += blockDim.x) {
-    const int c = e / M, a = e % M;
-    T vm = czero(T{}), vd = czero(T{});
-    if (a % Ne == 0 && a / Ne <= L) {
-      const int k = a / Ne;
-      vm = R[int64_t(k) * M + b0 + c];
-      vd = R[(int64_t(L + 1) + k) * M + b0 + c];
-    }
-    xm[e] = vm;
-    xd[e] = vd;
-  }
-  __syncthreads();
   const int G = M / 8;
   const int c = threadIdx.x / G, t = threadIdx.x % G;
-  fft_smem<T>(xm + c * M, M, logM, false, tw, t);
-  fft_smem<T>(xd + c * M, M, logM, false, tw, t);
-  for (int e = threadIdx.x; e < TC * M; e += blockDim.x) {
-    const int cc = e / M, a = e % M;
-    const int b = b0 + cc;
-    const int kq = a <= half ? a : M - a;
-    const int lq = b <= half ? b : M - b;
-    const int64_t qi = int64_t(lq) * (half + 1) + kq;
-    T d = Dq[qi];
-    if (a > half) d = mk(-d.x, -d.y);          // dipole table is odd in the a offset
-    xm[e] = cfma(xd[e], d, cmul(xm[e], Gq[qi]));
+  if (Ms > 0) {
+    // short spectra: monopole in xd[c][0, Ms), dipole in xd[c][Ms, 2 Ms)
+    for (int e = threadIdx.x; e < TC * Ms; e += blockDim.x) {
+      const int cc = e / Ms, k = e % Ms;
+      T vm = czero(T{}), vd = czero(T{});
+      if (k <= L) {
+        vm = R[int64_t(k) * M + b0 + cc];
+        vd = R[(int64_t(L + 1) + k) * M + b0 + cc];
+      }
+      xd[cc * M + k] = vm;
+      xd[cc * M + Ms + k] = vd;
+    }
+    __syncthreads();
+    // two transforms of length Ms per column, by the column's first 2 Ms / 8 threads
+    const int Gs = Ms / 8;
+    const bool act = t < 2 * Gs;
+    const int which = t / Gs;                  // 0 monopole, 1 dipole
+    fft_smem<T>(xd + c * M + (act ? which : 0) * Ms, Ms, logMs, false, tw, act ? t % Gs : 0, M / Ms, act);
+    for (int e = threadIdx.x; e < TC * M; e += blockDim.x) {
+      const int cc = e / M, a = e % M;
+      const int b = b0 + cc;
+      const int kq = a <= half ? a : M - a;
+      const int lq = b <= half ? b : M - b;
+      const int64_t qi = int64_t(lq) * (half + 1) + kq;
+      T d = Dq[qi];
+      if (a > half) d = mk(-d.x, -d.y);        // dipole table is odd in the a offset
+      const int f = a & (Ms - 1);
+      xm[e] = cfma(xd[cc * M + Ms + f], d, cmul(xd[cc * M + f], Gq[qi]));
+    }
+    __syncthreads();
+  } else {
+    for (int e = threadIdx.x; e < TC * M; e += blockDim.x) {
+      const int cc = e / M, a = e % M;
+      T vm = czero(T{}), vd = czero(T{});
+      if (a % Ne == 0 && a / Ne <= L) {
+        const int k = a / Ne;
+        vm = R[int64_t(k) * M + b0 + cc];
+        vd = R[(int64_t(L + 1) + k) * M + b0 + cc];
+      }
+      xm[e] = vm;
+      xd[e] = vd;
+    }
+    __syncthreads();
+    fft_smem<T>(xm + c * M, M, logM, false, tw, t);
+    fft_smem<T>(xd + c * M, M, logM, false, tw, t);
+    for (int e = threadIdx.x; e < TC * M; e += blockDim.x) {
+      const int cc = e / M, a = e % M;
+      const int b = b0 + cc;
+      const int kq = a <= half ? a : M - a;
+      const int lq = b <= half ? b : M - b;
+      const int64_t qi = int64_t(lq) * (half + 1) + kq;
+      T d = Dq[qi];
+      if (a > half) d = mk(-d.x, -d.y);        // dipole table is odd in the a offset
+      xm[e] = cfma(xd[e], d, cmul(xm[e], Gq[qi]));
+    }
+    __syncthreads();
   }
-  __syncthreads();
   fft_smem<T>(xm + c * M, M, logM, true, tw, t);
   for (int e = threadIdx.x; e < TC * n_lat; e += blockDim.x) {
     const int a = e / TC, cc = e % TC;
@@ -344,8 +393,17 @@ cudaError_t lattice_conv(const ApplyData<T>& d, int nr, cudaStream_t st) {
   const int64_t stride = d.lattice_rows() * M;
   k_src_rows<T><<<dim3(d.L + 1, 2, nr), M / 8, M * sizeof(T), st>>>(M, d.logM, d.n_lat, d.Ne, d.L, d.occ_of_cell,
                                                                      d.sigma, d.n_es, d.nocc, d.tw, d.Sd, stride);
+  // short forward column transforms when the source rows (every Ne-th) fold to length M / Ne
+  int Ms = 0, logMs = 0;
+  if (M % d.Ne == 0 && d.L + 1 <= M / d.Ne) {
+    const int m = M / d.Ne;
+    if (m >= 16 && (m & (m - 1)) == 0) {
+      Ms = m;
+      while ((1 << logMs) < m) ++logMs;
+    }
+  }
   k_conv_cols<T><<<dim3(M / TC, nr), TC * (M / 8), size_t(2) * TC * M * sizeof(T), st>>>(
-      M, d.logM, d.n_lat, d.Ne, d.L, TC, d.Sd, d.Gq, d.Dq, d.tw, d.Sm, stride);
+      M, d.logM, d.n_lat, d.Ne, d.L, TC, Ms, logMs, d.Sd, d.Gq, d.Dq, d.tw, d.Sm, stride);
   k_inv_rows<T><<<dim3(d.n_lat, nr), M / 8, M * sizeof(T), st>>>(M, d.logM, d.n_lat, d.tw, d.Sm, d.Sd, stride);
   return cudaGetLastError();
 }
