@@ -41,7 +41,7 @@ KERNELS_PER_APPLY = 6    # projection, source rows (fill + row FFT), columns (FF
 # DRAM bytes (read + write) of one k_near_eval launch on the full-size kite workload, from the
 # ncu launch list of this bench (per-launch counters; keyed by the padded block-entry count
 # so that any other workload reports no traffic).  Re-measure whenever k_near_eval changes.
-NEAR_TRAFFIC = {357685015: {"fp64": 5.9356e9, "mixed": 2.9453e9}}
+NEAR_TRAFFIC = {357685015: {"fp64": 5.9051e9, "mixed": 2.9456e9, "tc16": 3.1729e9}}
 
 
 def hbm_peak():
@@ -318,7 +318,7 @@ def main():
     f64 = lambda: plan.apply(u, out, prec=LS_FP64)
     f32 = lambda: plan.apply(u32, out32, prec=LS_MIXED)
     # batched right-hand sides: one pass over the near-field weights serves all of them
-    NB32, NB64 = 8, 4
+    NB32, NB64 = 16, 4      # complex64: 16 RHS take the tensor-core near field
     ub32 = torch.from_numpy(W.random_density(N, nrhs=NB32, seed=W.SEED + 3 + rank)).to(dev, torch.complex64)
     ob32 = torch.empty_like(ub32)
     ub64 = torch.from_numpy(W.random_density(N, nrhs=NB64, seed=W.SEED + 5 + rank)).to(dev)
@@ -346,6 +346,10 @@ def main():
     for _ in range(args.steps):
         f32()
     st32, c32 = plan.stage_times(LS_MIXED)
+    plan.set_stage_timing(True)
+    for _ in range(nb_steps):
+        fb32()
+    stb, cb = plan.stage_times(LS_MIXED)
     plan.set_stage_timing(False)
 
     # end to end through the public API: pinned host input in, result out, every step
@@ -420,6 +424,12 @@ def main():
     lat_bytes = lambda cb: (2 * (info["L"] + 1) * M * cb * 2 + 2 * (M // 2 + 1) ** 2 * cb
                             + 2 * n_lat * M * cb * 2)
     apply_bytes64 = near_bytes(16) + N * 16 * 4 + lat_bytes(16)
+    # batched complex64 (tensor-core near field): weights once, per-RHS vectors, Phi once
+    near_bytes_b = nnz * 8 + N * nfb2 * 8 + N * 12 + NB32 * (2 * N * 8 + nocc * nfb2 * 8)
+    t_near_b = stb[4] / max(cb, 1) * 1e-3
+    ach_b = near_bytes_b / t_near_b / 1e9
+    # whole batched apply: near field + per-RHS projection input, lattice passes and spectra
+    apply_bytes_b = near_bytes_b + NB32 * (N * 8 + lat_bytes(8))
     stage_names = ["es_project", "lattice_fill(fused)", "lattice_fft_conv", "local_coeffs", "near_eval"]
 
     cpu = None
@@ -457,7 +467,15 @@ def main():
                                "bytes_per_launch": near_bytes(8), "traffic": traffic.get("mixed"),
                                "launch_ms": t_near32 * 1e3}},
         "batched": {"unit": "RHS-matvecs/s",
-                    "mixed": {"nrhs": NB32, "value": world * nb_steps * NB32 / (msb32 * 1e-3), "dtype": "f32"},
+                    "mixed": {"nrhs": NB32, "value": world * nb_steps * NB32 / (msb32 * 1e-3), "dtype": "f32",
+                              "ms_per_apply": msb32 / nb_steps,
+                              "roofline": {"bound": "hbm", "kernel": "k_near_tc<16> (tcgen05, 3xTF32)",
+                                           "achieved": ach_b, "peak": peak, "unit": "GB/s", "frac": ach_b / peak,
+                                           "peak_source": peak_src, "bytes_per_launch": near_bytes_b,
+                                           "traffic": traffic.get("tc16") if NB32 == 16 else None,
+                                           "launch_ms": t_near_b * 1e3},
+                              "apply_hbm_frac": (apply_bytes_b / (msb32 / nb_steps * 1e-3) / 1e9) / peak,
+                              "stages_ms": dict(zip(stage_names, [float(x) / max(cb, 1) for x in stb]))},
                     "fp64": {"nrhs": NB64, "value": world * nb_steps * NB64 / (msb64 * 1e-3), "dtype": "f64"}},
         "stages_ms": {"fp64": dict(zip(stage_names, [float(x) / max(c64, 1) for x in st64])),
                       "mixed": dict(zip(stage_names, [float(x) / max(c32, 1) for x in st32]))},
