@@ -236,6 +236,21 @@ const char* ls_batch_last_error(ls_batch b);
  * cudaMalloc / cudaFree). */
 ls_status ls_apply_noalloc(ls_plan plan, const void* u_dev, void* Au_dev, ls_precision prec, void* stream);
 
+/* Device-side failure detection.  The tensor-core near field (8 and 16
+ * complex64 right-hand sides per apply) waits on shared-memory barriers
+ * (mbarrier) inside the kernel; every such wait gives up after a bounded
+ * number of polls, records the time-out in a plan-owned device flag, frees
+ * its tensor memory and leaves the rows of its work item unwritten, so that
+ * the context stays usable.  ls_plan_device_status synchronises the device,
+ * returns LS_ERR_TIMEOUT (message in ls_last_error) if a time-out was
+ * recorded since the last call, and clears the flag; ls_solve and
+ * ls_batch_solve check it before returning.  ls_set_wait_limit sets the polls
+ * per wait (default 4194304, a few milliseconds); 0 makes every wait give up
+ * at once, which exercises the failure path without a stuck device.  It
+ * synchronises the device and drops the plan's captured applies. */
+ls_status ls_plan_device_status(ls_plan plan);
+ls_status ls_set_wait_limit(ls_plan plan, int polls);
+
 /* Per-stage device timing of ls_apply with CUDA events recorded on the call's
  * stream (measurement aid; enabling it makes ls_apply wait for each apply).
  * Stages: 0 equivalent-source projection, 1 lattice fill, 2 lattice FFT

@@ -986,7 +986,8 @@ ls_status ls_solve(ls_plan plan, const void* uinc, void* u, int nrhs, double tol
     info->residual = worst;
     info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   }
-  return result;
+  const ls_status dev = ls_plan_device_status(plan);
+  return dev != LS_OK ? dev : result;
 }
 
 ls_status ls_farfield(ls_plan plan, const void* u, int nrhs, const double* dirs_host, int ndir, void* A,
@@ -1008,6 +1009,26 @@ ls_status ls_farfield(ls_plan plan, const void* u, int nrhs, const double* dirs_
                       ndir, k, make_double2(c.real(), c.imag()), static_cast<double2*>(A), st));
   LS_CU(cudaStreamSynchronize(st));
   return LS_OK;
+}
+
+ls_status ls_set_wait_limit(ls_plan plan, int polls) {
+  if (!plan) return LS_ERR_INVALID;
+  if (polls < 0) return fail(plan, LS_ERR_INVALID, "ls_set_wait_limit: polls must be >= 0");
+  LS_CU(cudaDeviceSynchronize());   // no captured apply may still run with the old limit
+  plan->d32.tc_spin = polls;
+  plan->d64.tc_spin = polls;
+  plan->graphs.clear();             // captured applies hold the old limit
+  return LS_OK;
+}
+
+ls_status ls_plan_device_status(ls_plan plan) {
+  if (!plan) return LS_ERR_INVALID;
+  int flag = 0;
+  LS_CU(cudaMemcpy(&flag, plan->d32.tc_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (!flag) return LS_OK;
+  LS_CU(cudaMemset(plan->d32.tc_err, 0, sizeof(int)));
+  return fail(plan, LS_ERR_TIMEOUT, "a device-side wait of the tensor-core near field timed out; "
+                                    "the rows of the affected work items were not written");
 }
 
 ls_status ls_set_stage_timing(ls_plan plan, int enable) {
@@ -1349,6 +1370,8 @@ ls_status ls_batch_solve(ls_batch b, const void* uinc, void* u, double tol, int 
       per[i].residual = S.res_per.empty() ? 0 : S.res_per[i];
       per[i].seconds = secs;
     }
+  for (ls_plan p : b->plans)
+    if (ls_plan_device_status(p) != LS_OK) return fail(b, LS_ERR_TIMEOUT, p->err);
   return s;
 }
 

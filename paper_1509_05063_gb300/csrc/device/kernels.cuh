@@ -35,6 +35,7 @@ struct ApplyData {
   const int2* items128 = nullptr;       // 128-row items (tensor-core near field, 8 or 16 complex64 RHS)
   int n_items128 = 0;
   int* tc_err = nullptr;                // set by the tensor-core near field when a wait times out
+  int tc_spin = 1 << 22;                // polls of each mbarrier wait before it gives up
   const T* Wb = nullptr;                // blocks, row-major per cell
   const int64_t* rem_row = nullptr;     // N + 1
   const int* rem_col = nullptr;

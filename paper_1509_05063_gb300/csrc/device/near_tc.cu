@@ -52,7 +52,6 @@ constexpr int kTcStages = 3;          // shared-memory stages (operand tiles of 
 constexpr int kTcAhead = 4;           // chunks held in registers ahead of the one being prepared
 constexpr int kTcKgroups = 2 * kTcKC / 2;  // 16-byte core-matrix columns per row: 4 raw + 4 lo
 constexpr int kTcSBO = kTcKgroups * 128;   // bytes between 8-row groups (A and B)
-constexpr int kTcSpin = 1 << 22;      // polls of an mbarrier before giving up
 
 __device__ __forceinline__ uint32_t s_u32(const void* p) { return uint32_t(__cvta_generic_to_shared(p)); }
 
@@ -65,8 +64,9 @@ __device__ __forceinline__ uint64_t s_desc(uint32_t addr, uint32_t lbo, uint32_t
 // x - (x with the 13 low mantissa bits cleared): exact in FP32
 __device__ __forceinline__ float lo_tf32(float x) { return x - __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
 
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-  for (int it = 0; it < kTcSpin; ++it) {
+// poll an mbarrier phase at most `limit` times
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int limit) {
+  for (int it = 0; it < limit; ++it) {
     uint32_t done;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
@@ -124,7 +124,7 @@ __global__ void __launch_bounds__(kTcThreads) k_near_tc(const int2* __restrict__
                                                         const float2* __restrict__ Phi,
                                                         const float2* __restrict__ gamma, int nocc, int nfb2,
                                                         float kappa2, float2* __restrict__ out,
-                                                        int* __restrict__ err) {
+                                                        int* __restrict__ err, int spin) {
   using Lay = TcLayout<R>;
   constexpr int NN = Lay::NN;
   static_assert(R * kTcKC <= kTcRows, "one input value per thread and chunk");
@@ -203,7 +203,7 @@ __global__ void __launch_bounds__(kTcThreads) k_near_tc(const int2* __restrict__
         if (c >= nchunk) break;
         const int s = c % kTcStages;
         // stage s was last read by the MMAs of chunk c - kTcStages
-        if (c >= kTcStages && !mbar_wait(s_u32(&empty[s]), ((c - kTcStages) / kTcStages) & 1)) {
+        if (c >= kTcStages && !mbar_wait(s_u32(&empty[s]), ((c - kTcStages) / kTcStages) & 1, spin)) {
           *sflag = 1;
           live = false;
           break;
@@ -238,7 +238,7 @@ __global__ void __launch_bounds__(kTcThreads) k_near_tc(const int2* __restrict__
     }
     // the last MMAs
     if (live && nchunk > 0 &&
-        !mbar_wait(s_u32(&empty[(nchunk - 1) % kTcStages]), ((nchunk - 1) / kTcStages) & 1))
+        !mbar_wait(s_u32(&empty[(nchunk - 1) % kTcStages]), ((nchunk - 1) / kTcStages) & 1, spin))
       *sflag = 1;
   } else {
     // MMA warp (converged; lane 0 issues): four MMAs per chunk once its stage
@@ -249,7 +249,7 @@ __global__ void __launch_bounds__(kTcThreads) k_near_tc(const int2* __restrict__
         (1u << 4) | (2u << 7) | (2u << 10) | (uint32_t(NN >> 3) << 17) | (uint32_t(kTcRows >> 4) << 24);
     for (int c = 0; c < nchunk; ++c) {
       const int s = c % kTcStages;
-      const bool ready = mbar_wait(s_u32(&full[s]), (c / kTcStages) & 1);
+      const bool ready = mbar_wait(s_u32(&full[s]), (c / kTcStages) & 1, spin);
       if (!__all_sync(0xffffffffu, ready)) {
         *sflag = 1;
         break;
@@ -318,8 +318,8 @@ __global__ void __launch_bounds__(kTcThreads) k_near_tc(const int2* __restrict__
     atomicExch(err, 1);
     // let MMAs still in flight finish (bounded) before the tensor memory is released
     for (int s = 0; s < kTcStages; ++s) {
-      mbar_wait(s_u32(&empty[s]), 0);
-      mbar_wait(s_u32(&empty[s]), 1);
+      mbar_wait(s_u32(&empty[s]), 0, spin);
+      mbar_wait(s_u32(&empty[s]), 1, spin);
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -343,7 +343,8 @@ cudaError_t near_eval_tc(const ApplyData<float2>& d, const float2* u, float2* ou
   if (d.n_items128 == 0) return cudaSuccess;
   k_near_tc<R><<<d.n_items128, kTcThreads, Lay::kBytes, st>>>(d.items128, d.occ_start, d.blk_off, d.blk_seg, d.Wb,
                                                            d.rem_row, d.rem_col, d.rem_val, u, d.N, d.Phi, d.gamma,
-                                                           d.nocc, d.nfb2, float(d.kappa2), out, d.tc_err);
+                                                           d.nocc, d.nfb2, float(d.kappa2), out, d.tc_err,
+                                                              d.tc_spin);
   return cudaGetLastError();
 }
 

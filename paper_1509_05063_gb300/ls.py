@@ -87,6 +87,8 @@ _SIGS = {
     "ls_apply_noalloc": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
     "ls_check_cells": ([C.POINTER(Geometry), N2FN, C.c_void_p, C.c_double, C.POINTER(Options), C.c_void_p]),
     "ls_get_stage_times": ([C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
+    "ls_plan_device_status": ([C.c_void_p]),
+    "ls_set_wait_limit": ([C.c_void_p, C.c_int]),
     "ls_batch_create": ([C.c_void_p, C.c_int, C.POINTER(C.c_void_p)]),
     "ls_batch_offsets": ([C.c_void_p, C.c_void_p]),
     "ls_batch_apply": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
@@ -254,6 +256,14 @@ class Plan:
         _check(_lib.ls_apply_noalloc(self._h, C.c_void_p(u.data_ptr()), C.c_void_p(out.data_ptr()), prec,
                                      _stream(stream)), self._h)
         return out
+
+    def device_status(self):
+        """Raise LSError (status 5) if a device-side wait timed out since the last check."""
+        _check(_lib.ls_plan_device_status(self._h), self._h)
+
+    def set_wait_limit(self, polls: int):
+        """Polls per device-side wait of the tensor-core near field (0: every wait gives up)."""
+        _check(_lib.ls_set_wait_limit(self._h, int(polls)), self._h)
 
     def set_stage_timing(self, enable: bool):
         _check(_lib.ls_set_stage_timing(self._h, int(enable)), self._h)

@@ -1,0 +1,47 @@
+"""Device-side failure detection of the tensor-core near field, without a GPU
+fault: every mbarrier wait in that kernel is bounded; with the limit set to 0
+polls every wait gives up at once, the kernel records the time-out in the
+plan's device flag, frees its tensor memory and returns, and the host reports
+LS_ERR_TIMEOUT.  Afterwards the context is still usable and the same plan gives
+correct results again."""
+import numpy as np
+import pytest
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def plan():
+    from paper_1509_05063_gb300 import Plan
+    wl = W.place_cells(W.kite(n1=512, n2=17, h=0.025, kappa=6.0, collar_w=0.07, tau0=0.4, tau1=0.9, R_a=6,
+                              R_b=5, R_cart=4, n_rho=32, N_tau=48), L=17, m=8, center=(-0.25, 0.0), N_eq=8)
+    p = Plan(wl, W.n2_of(wl))
+    yield p
+    p.close()
+
+
+def test_timeout_is_reported_and_recovered(plan):
+    from paper_1509_05063_gb300 import LS_MIXED, LSError
+    U = torch.from_numpy(W.random_density(plan.N, nrhs=16, seed=W.SEED + 31)).to("cuda:0", torch.complex64)
+    good = plan.apply(U, prec=LS_MIXED)
+    plan.device_status()                                   # nothing recorded
+    plan.set_wait_limit(0)
+    try:
+        plan.apply(U, prec=LS_MIXED)
+        with pytest.raises(LSError) as e:
+            plan.device_status()
+        assert e.value.status == 5
+        plan.device_status()                               # the flag was cleared
+        ui = torch.from_numpy(np.stack([W.plane_wave(plan.kappa, (1.0, 0.0), plan.nodes()[0])] * 16))
+        with pytest.raises(LSError) as e:
+            plan.solve(ui.to("cuda:0"), tol=1e-8, prec=LS_MIXED, max_iter=5)
+        assert e.value.status == 5
+    finally:
+        plan.set_wait_limit(1 << 22)
+    again = plan.apply(U, prec=LS_MIXED)
+    plan.device_status()
+    assert torch.equal(again, good)

@@ -69,6 +69,8 @@ def test_invalid_arguments_return_status(lib):
     assert lib.ls_batch_apply(None, None, None, 0, None) == 1
     assert lib.ls_batch_solve(None, None, None, 1e-10, 10, 10, 0, None, None, None) == 1
     assert lib.ls_batch_destroy(None) == 0
+    assert lib.ls_plan_device_status(None) == 1
+    assert lib.ls_set_wait_limit(None, 0) == 1
 
 
 def _small_disc():
