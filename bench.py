@@ -231,12 +231,12 @@ def run_batch(n_inst, dev, barrier, timed):
     b.solve(ui, tol=1e-3, prec=LS_MIXED, max_iter=3)
     barrier()
     t0 = time.perf_counter()
-    _, info = b.solve(ui, tol=1e-10, prec=LS_MIXED, max_iter=4000, restart=100)
+    _, info = b.solve(ui, tol=1e-10, prec=LS_MIXED, max_iter=4000, restart=30)
     barrier()
     t_b = time.perf_counter() - t0
     t0 = time.perf_counter()
     for p, x in zip(plans, b.split(ui)):
-        p.solve(x.contiguous(), tol=1e-10, prec=LS_MIXED, max_iter=4000, restart=100)
+        p.solve(x.contiguous(), tol=1e-10, prec=LS_MIXED, max_iter=4000, restart=30)
     barrier()
     t_s = time.perf_counter() - t0
     out["solve_mixed"] = {"tol": 1e-10, "makespan_s": t_b, "separate_solves_s": t_s,
@@ -374,11 +374,11 @@ def main():
         plan.solve(ui, tol=1e-4, prec=LS_FP64, max_iter=5)      # allocate work space
         barrier()
         t0 = time.perf_counter()
-        s64, i64 = plan.solve(ui, tol=1e-10, prec=LS_FP64, max_iter=800, restart=100)
+        s64, i64 = plan.solve(ui, tol=1e-10, prec=LS_FP64, max_iter=800, restart=200)
         barrier()
         t64 = time.perf_counter() - t0
         t0 = time.perf_counter()
-        s32, i32 = plan.solve(ui, tol=1e-10, prec=LS_MIXED, max_iter=800, restart=100)
+        s32, i32 = plan.solve(ui, tol=1e-10, prec=LS_MIXED, max_iter=800, restart=30)
         barrier()
         t32 = time.perf_counter() - t0
         diff = float(torch.linalg.vector_norm(s32 - s64) / torch.linalg.vector_norm(s64))
@@ -388,10 +388,10 @@ def main():
         UI = torch.from_numpy(np.stack([W.plane_wave(wl.kappa, (math.cos(t), math.sin(t)), xy) for t in th])).to(dev)
         barrier()
         t0 = time.perf_counter()
-        sb32, ib32 = plan.solve(UI, tol=1e-10, prec=LS_MIXED, max_iter=800, restart=100)
+        sb32, ib32 = plan.solve(UI, tol=1e-10, prec=LS_MIXED, max_iter=800, restart=30)
         barrier()
         tb32 = time.perf_counter() - t0
-        solve = {"tol": 1e-10, "fp64_s": t64, "fp64_iterations": i64["iterations"],
+        solve = {"tol": 1e-10, "restart_fp64": 200, "restart_mixed": 30, "fp64_s": t64, "fp64_iterations": i64["iterations"],
                  "fp64_residual": i64["residual"], "fp64_converged": i64["converged"],
                  "mixed_s": t32, "mixed_inner_iterations": i32["iterations"],
                  "mixed_refinements": i32["refinements"], "mixed_residual": i32["residual"],

@@ -81,11 +81,25 @@ struct Krylov {
   float2 *c64a = nullptr, *c64b = nullptr;
   double2* pin_h = nullptr;     // pinned host copies of h and the norms (async D2H)
   double* pin_n = nullptr;
+  // pipelined GMRES: Gram-Schmidt coefficients (two passes) and norms of every
+  // iteration of a cycle, on the device and mirrored in pinned memory
+  double2* hk = nullptr;        // [iteration][pass][RHS][restart + 3]
+  double* nk = nullptr;         // [iteration][RHS]
+  double2* pin_hk = nullptr;
+  double* pin_nk = nullptr;
+  static constexpr int kEvents = 4;
+  cudaEvent_t ev[kEvents] = {};
   void free_pinned() {
     if (pin_h) cudaFreeHost(pin_h);
     if (pin_n) cudaFreeHost(pin_n);
+    if (pin_hk) cudaFreeHost(pin_hk);
+    if (pin_nk) cudaFreeHost(pin_nk);
     pin_h = nullptr;
     pin_n = nullptr;
+    pin_hk = nullptr;
+    pin_nk = nullptr;
+    for (auto& e : ev)
+      if (e) { cudaEventDestroy(e); e = nullptr; }
   }
 };
 
@@ -687,13 +701,23 @@ ls_status ensure_krylov(DevOwner* plan, Krylov& K, int restart, const Layout& la
   K.dpartial = plan->alloc<double>(size_t(Rw) * nb, &st);
   K.c64a = plan->alloc<float2>(size_t(Tw), &st);
   K.c64b = plan->alloc<float2>(size_t(Tw), &st);
+  const size_t nhk = size_t(restart) * 2 * Rw * (restart + 3), nnk = size_t(restart) * Rw;
+  K.hk = plan->alloc<double2>(nhk, &st);
+  K.nk = plan->alloc<double>(nnk, &st);
   if (st != LS_OK) return st;
   K.free_pinned();
   if (cudaMallocHost(&K.pin_h, size_t(Rw) * (restart + 3) * sizeof(double2)) != cudaSuccess ||
-      cudaMallocHost(&K.pin_n, size_t(Rw) * sizeof(double)) != cudaSuccess) {
+      cudaMallocHost(&K.pin_n, size_t(Rw) * sizeof(double)) != cudaSuccess ||
+      cudaMallocHost(&K.pin_hk, nhk * sizeof(double2)) != cudaSuccess ||
+      cudaMallocHost(&K.pin_nk, nnk * sizeof(double)) != cudaSuccess) {
     cudaGetLastError();
     return fail(plan, LS_ERR_NOMEM, "pinned host staging");
   }
+  for (auto& e : K.ev)
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(plan, LS_ERR_CUDA, "event creation");
+    }
   K.restart = restart;
   K.R = Rw;
   K.total = Tw;
@@ -853,6 +877,158 @@ ls_status gmres_lockstep(DevOwner* plan, Krylov& K, const Layout& lay, Op op, co
   }
 }
 
+// Pipelined lock-step GMRES(m): the same iteration as gmres_lockstep, but the
+// host never waits for the iteration it has just queued.  Every iteration runs
+// two full classical Gram-Schmidt passes (CGS2, so that no host decision sits
+// between the passes), normalises on the device (v_{k+1} = w / ||w||), and
+// queues an asynchronous copy of its coefficients to pinned memory plus an
+// event; the host queues up to kLag iterations ahead and builds the Hessenberg
+// columns, Givens rotations and residual estimates of the earlier iterations
+// while the device works.  An RHS found converged stops taking part in later
+// queued applies (op's need flags); iterations queued past its convergence are
+// discarded (their columns are never used).  Used for the complex64
+// correction solves of the mixed refinement, where the apply is short and a
+// host round trip per iteration would leave the GPU idle.
+template <typename Op>
+ls_status gmres_lockstep_async(DevOwner* plan, Krylov& K, const Layout& lay, Op op, const double2* B, double2* X,
+                               double tol, int max_iter, int restart, cudaStream_t st, int* iters, double* relres) {
+  constexpr int kLag = 2;
+  static_assert(kLag < Krylov::kEvents, "event ring");
+  const int R = lay.R;
+  const int64_t vs = lay.total;
+  double2* V = K.V;
+  double2* Wv = K.w;
+  double2* Rv = K.r;
+  const int m = restart;
+  const int nbmax = lsd::gram_blocks(K.max_len);
+  const int hstride = m + 3;
+  auto part_of = [&](int r) { return K.partial + size_t(r) * nbmax * hstride; };
+  auto dp_of = [&](int r) { return K.dpartial + size_t(r) * nbmax; };
+  auto hslot = [&](int k, int pass, int r) { return K.hk + ((size_t(k) * 2 + pass) * R + r) * hstride; };
+  auto O = [&](int r) { return lay.off[r]; };
+  auto Ln = [&](int r) { return lay.len[r]; };
+  double* nrm = K.pin_n;
+  std::vector<double> bnorm(R);
+  LS_CU(layout_norms(K, lay, B, st));
+  bnorm.assign(nrm, nrm + R);
+  for (int r = 0; r < R; ++r) {
+    iters[r] = 0;
+    relres[r] = 0;
+    if (bnorm[r] == 0.0) LS_CU(cudaMemsetAsync(X + O(r), 0, Ln(r) * sizeof(double2), st));
+  }
+  std::vector<std::vector<cd>> H(R, std::vector<cd>(size_t(m + 1) * m)), cs(R, std::vector<cd>(m)),
+      sn(R, std::vector<cd>(m)), g(R, std::vector<cd>(m + 1));
+  std::vector<int> k_used(R);
+  std::vector<char> done(R), active(R);
+  std::vector<std::vector<char>> queued_for(m, std::vector<char>(R));
+  int total = 0;
+  for (;;) {
+    // true residuals
+    LS_CU(op(X, Wv, nullptr));
+    LS_CU(lsd::sub(B, Wv, Rv, vs, st));
+    LS_CU(layout_norms(K, lay, Rv, st));
+    bool all_done = true;
+    for (int r = 0; r < R; ++r) {
+      relres[r] = bnorm[r] > 0 ? nrm[r] / bnorm[r] : 0.0;
+      done[r] = relres[r] <= tol;
+      all_done = all_done && done[r];
+    }
+    if (all_done) return LS_OK;
+    if (total >= max_iter) return fail(plan, LS_ERR_NOCONV, "GMRES reached max_iter");
+    std::vector<double> beta(nrm, nrm + R);
+    for (int r = 0; r < R; ++r) {
+      double2* v0 = V + O(r);
+      if (done[r]) {
+        LS_CU(cudaMemsetAsync(v0, 0, Ln(r) * sizeof(double2), st));
+      } else {
+        LS_CU(lsd::scale_into(Rv + O(r), K.dnorm + r, v0, Ln(r), st));
+        std::fill(H[r].begin(), H[r].end(), cd(0));
+        std::fill(g[r].begin(), g[r].end(), cd(0));
+        g[r][0] = beta[r];
+      }
+      active[r] = !done[r];
+      k_used[r] = 0;
+    }
+    int queued = 0, handled = 0;
+    bool stop = false;
+    for (;;) {
+      // queue iterations ahead of the host
+      while (!stop && queued < m && queued - handled < kLag && total + (queued - handled) < max_iter) {
+        const int k = queued;
+        bool any = false;
+        for (int r = 0; r < R; ++r) { queued_for[k][r] = active[r]; any = any || active[r]; }
+        if (!any) break;
+        LS_CU(op(V + k * vs, Wv, queued_for[k].data()));
+        for (int r = 0; r < R; ++r) {
+          if (!queued_for[k][r]) continue;
+          for (int pass = 0; pass < 2; ++pass) {
+            LS_CU(lsd::gram(V + O(r), k + 1, vs, Wv + O(r), Ln(r), part_of(r), hslot(k, pass, r), st));
+            LS_CU(lsd::axpy_multi(V + O(r), k + 1, vs, hslot(k, pass, r), Wv + O(r), K.apart, Ln(r), st));
+          }
+          LS_CU(lsd::norm2(Wv + O(r), Ln(r), dp_of(r), K.nk + size_t(k) * R + r, st));
+          LS_CU(lsd::scale_into(Wv + O(r), K.nk + size_t(k) * R + r, V + (k + 1) * vs + O(r), Ln(r), st));
+        }
+        LS_CU(cudaMemcpyAsync(K.pin_hk + size_t(k) * 2 * R * hstride, hslot(k, 0, 0),
+                              size_t(2) * R * hstride * sizeof(double2), cudaMemcpyDeviceToHost, st));
+        LS_CU(cudaMemcpyAsync(K.pin_nk + size_t(k) * R, K.nk + size_t(k) * R, R * sizeof(double),
+                              cudaMemcpyDeviceToHost, st));
+        LS_CU(cudaEventRecord(K.ev[k % Krylov::kEvents], st));
+        ++queued;
+      }
+      if (handled == queued) break;
+      // the oldest queued iteration: Hessenberg column, Givens rotation, residual estimate
+      const int k = handled;
+      LS_CU(cudaEventSynchronize(K.ev[k % Krylov::kEvents]));
+      bool any_active = false;
+      for (int r = 0; r < R; ++r) {
+        if (!queued_for[k][r] || !active[r]) continue;
+        const double2* h1 = K.pin_hk + (size_t(k) * 2 * R + r) * hstride;
+        const double2* h2 = K.pin_hk + ((size_t(k) * 2 + 1) * R + r) * hstride;
+        std::vector<cd>& Hr = H[r];
+        for (int j = 0; j <= k; ++j) Hr[size_t(j) * m + k] = cd(h1[j].x + h2[j].x, h1[j].y + h2[j].y);
+        const double hk1 = K.pin_nk[size_t(k) * R + r];
+        Hr[size_t(k + 1) * m + k] = hk1;
+        for (int j = 0; j < k; ++j) {
+          const cd t = std::conj(cs[r][j]) * Hr[size_t(j) * m + k] + std::conj(sn[r][j]) * Hr[size_t(j + 1) * m + k];
+          Hr[size_t(j + 1) * m + k] = -sn[r][j] * Hr[size_t(j) * m + k] + cs[r][j] * Hr[size_t(j + 1) * m + k];
+          Hr[size_t(j) * m + k] = t;
+        }
+        const cd a = Hr[size_t(k) * m + k], bb = Hr[size_t(k + 1) * m + k];
+        const double den = std::sqrt(std::norm(a) + std::norm(bb));
+        cs[r][k] = den > 0 ? a / den : cd(1);
+        sn[r][k] = den > 0 ? bb / den : cd(0);
+        Hr[size_t(k) * m + k] = den;
+        Hr[size_t(k + 1) * m + k] = 0;
+        g[r][k + 1] = -sn[r][k] * g[r][k];
+        g[r][k] = std::conj(cs[r][k]) * g[r][k];
+        ++iters[r];
+        k_used[r] = k + 1;
+        if (std::abs(g[r][k + 1]) / bnorm[r] <= tol || hk1 == 0.0) active[r] = 0;
+      }
+      for (int r = 0; r < R; ++r) any_active = any_active || active[r];
+      ++handled;
+      ++total;
+      if (!any_active || handled == m || total >= max_iter) stop = true;
+      if (stop) break;
+    }
+    LS_CU(cudaStreamSynchronize(st));           // iterations queued past the stop are discarded
+    // back substitution and x_r += V_r y_r
+    for (int r = 0; r < R; ++r) {
+      const int ku = k_used[r];
+      if (done[r] || ku == 0) continue;
+      std::vector<cd> y(ku);
+      for (int i = ku - 1; i >= 0; --i) {
+        cd sacc = g[r][i];
+        for (int j = i + 1; j < ku; ++j) sacc -= H[r][size_t(i) * m + j] * y[j];
+        y[i] = sacc / H[r][size_t(i) * m + i];
+      }
+      double2* hy = K.h + size_t(r) * hstride;
+      LS_CU(cudaMemcpyAsync(hy, y.data(), ku * sizeof(double2), cudaMemcpyHostToDevice, st));
+      LS_CU(lsd::combine(V + O(r), ku, vs, hy, X + O(r), Ln(r), st));
+    }
+  }
+}
+
 struct SolveStats {
   int iterations = 0, refinements = 0;
   double worst = 0;
@@ -911,8 +1087,8 @@ ls_status solve_lockstep(DevOwner* plan, Krylov& K, const Layout& lay, Op64 op64
     S.refinements++;
     const double inner_tol = std::max(1e-5, 0.3 * tol / rel);
     LS_CU(cudaMemsetAsync(Cor, 0, size_t(lay.total) * sizeof(double2), st));
-    const ls_status s = gmres_lockstep(plan, K, lay, op32, Res, Cor, inner_tol, std::max(1, max_iter - inner_total),
-                                       restart, st, it.data(), rr.data());
+    const ls_status s = gmres_lockstep_async(plan, K, lay, op32, Res, Cor, inner_tol,
+                                             std::max(1, max_iter - inner_total), restart, st, it.data(), rr.data());
     int mx = 0;
     for (int r = 0; r < R; ++r) { S.iterations += it[r]; S.it_per[r] += it[r]; mx = std::max(mx, it[r]); }
     inner_total += mx;
