@@ -96,8 +96,11 @@ struct TcLayout {
   static constexpr int kA = kTcRows * kTcKgroups * 16;             // 16 KB: 128 rows x 32 fp32
   static constexpr int kB = NN * kTcKgroups * 16;                  // NN rows x 32 fp32
   static constexpr int kStage = kA + kB;
-  // four accumulators (one per K step of a chunk: independent MMA chains)
-  static constexpr int kTmemCols = 4 * NN < 32 ? 32 : 4 * NN;      // power of two >= 32
+  // independent accumulators (MMA chains): the four K steps of a chunk, times
+  // two sets used by alternate chunks where tensor memory allows
+  static constexpr int kSets = R >= 16 ? 1 : 2;
+  static constexpr int kAcc = 4 * kSets;
+  static constexpr int kTmemCols = kAcc * NN < 32 ? 32 : kAcc * NN;  // power of two >= 32
   // at most 512 / kTmemCols blocks may share an SM's tensor memory: pad the
   // shared memory so that no more blocks fit
   static constexpr int kBlocksMax = 512 / kTmemCols;
@@ -263,7 +266,8 @@ __global__ void __launch_bounds__(kTcThreads) k_near_tc(const int2* __restrict__
           const uint64_t db = s_desc(b0 + 2 * i * 128, 128, kTcSBO);
           asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
                        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n"
-                       :: "r"(tmem + uint32_t(i * NN)), "l"(da), "l"(db), "r"(idesc), "r"(c > 0 ? 1 : 0)
+                       :: "r"(tmem + uint32_t(((c % Lay::kSets) * 4 + i) * NN)), "l"(da), "l"(db), "r"(idesc),
+                          "r"(c >= Lay::kSets ? 1 : 0)
                        : "memory");
         }
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
@@ -282,7 +286,7 @@ __global__ void __launch_bounds__(kTcThreads) k_near_tc(const int2* __restrict__
     for (int i = 0; i < NN; ++i) d[i] = 0.f;
     if (nchunk > 0) {
 #pragma unroll 1
-      for (int a = 0; a < 4; ++a)          // sum of the four accumulators
+      for (int a = 0; a < (nchunk < Lay::kSets ? 4 * nchunk : Lay::kAcc); ++a)   // sum of the accumulators used
 #pragma unroll
         for (int q = 0; q < NN / 16; ++q) {
           float v[16];
