@@ -162,7 +162,10 @@ ls_status ls_apply(ls_plan plan, const void* u_dev, void* Au_dev, int nrhs,
  * LS_FP64: restarted GMRES with the FP64 apply.  LS_MIXED: FP64 iterative
  * refinement r = uinc - A_64 u whose correction equations are solved by GMRES
  * with the complex64 apply (Arnoldi vectors in FP64).  Stops when
- * ||uinc - A u|| / ||uinc|| <= tol for every RHS.  Synchronises the stream.
+ * ||uinc - A u|| / ||uinc|| <= tol for every RHS.  Right-hand sides are solved
+ * in lock-step batches (4 for LS_FP64, 16 for LS_MIXED); a right-hand side of
+ * a later batch whose initial guess is zero starts from the least-squares
+ * combination of the earlier batches' solutions.  Synchronises the stream.
  * Errors: LS_ERR_NOCONV if max_iter is reached (u holds the last iterate). */
 ls_status ls_solve(ls_plan plan, const void* uinc_dev, void* u_dev, int nrhs, double tol,
                    int max_iter, int restart, ls_precision prec, ls_solve_info* info,

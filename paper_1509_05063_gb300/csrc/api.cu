@@ -165,6 +165,8 @@ struct ls_plan_s : DevOwner {
   // plan-wide device arrays
   double *x = nullptr, *y = nullptr, *ffw = nullptr;
   Krylov K;                         // solve work space (lazily sized)
+  double2 *seed_h = nullptr, *seed_part = nullptr;   // initial guesses from earlier right-hand sides
+  int seed_cap = 0;
   double* dirs = nullptr;
   int dirs_cap = 0;
   ls_plan_info_t info{};
@@ -1097,6 +1099,84 @@ ls_status solve_lockstep(DevOwner* plan, Krylov& K, const Layout& lay, Op64 op64
   }
 }
 
+// Initial guesses for the right-hand sides [r0, r0 + R) of one ls_solve call
+// from the solutions of its earlier right-hand sides [0, r0): since
+// A x_j = b_j, the residual of x0 = sum_j c_j x_j is b - sum_j c_j b_j, so c
+// solves the least-squares problem min || b - B_prev c || through the normal
+// equations (Gram matrix of the earlier right-hand sides, regularised by
+// 1e-12 of its largest diagonal entry: a guess, not a solution).  Only
+// right-hand sides whose initial guess is zero are seeded; the residual never
+// exceeds that of the zero guess.
+ls_status seed_from_previous(ls_plan plan, const double2* B, double2* X, int r0, int R, int64_t N,
+                             std::vector<cd>& G, cudaStream_t st) {
+  const int nb = lsd::gram_blocks(N);
+  if (plan->seed_cap < r0 + 1) {
+    ls_status s = LS_OK;
+    plan->seed_h = plan->alloc<double2>(size_t(r0 + 1) * 2, &s);
+    plan->seed_part = plan->alloc<double2>(size_t(nb) * (r0 + 1) * 2, &s);
+    if (s != LS_OK) return s;
+    plan->seed_cap = (r0 + 1) * 2;
+  }
+  // Gram matrix G[i][j] = <b_i, b_j> of the earlier right-hand sides (columns added as r0 grows)
+  const int old = int(std::lround(std::sqrt(double(G.size()))));
+  std::vector<cd> Gn(size_t(r0) * r0);
+  for (int i = 0; i < old; ++i)
+    for (int j = 0; j < old; ++j) Gn[size_t(i) * r0 + j] = G[size_t(i) * old + j];
+  std::vector<cd> col(r0 + 1);
+  for (int j = old; j < r0; ++j) {
+    LS_CU(lsd::gram(B, r0, N, B + int64_t(j) * N, N, plan->seed_part, plan->seed_h, st));
+    LS_CU(cudaMemcpyAsync(col.data(), plan->seed_h, r0 * sizeof(double2), cudaMemcpyDeviceToHost, st));
+    LS_CU(cudaStreamSynchronize(st));
+    for (int i = 0; i < r0; ++i) {
+      Gn[size_t(i) * r0 + j] = col[i];
+      Gn[size_t(j) * r0 + i] = std::conj(col[i]);
+    }
+  }
+  G.swap(Gn);
+  // Cholesky of G + eps I
+  double dmax = 0;
+  for (int i = 0; i < r0; ++i) dmax = std::max(dmax, G[size_t(i) * r0 + i].real());
+  std::vector<cd> Lc(G);
+  for (int i = 0; i < r0; ++i) Lc[size_t(i) * r0 + i] += 1e-12 * dmax;
+  for (int j = 0; j < r0; ++j) {
+    double d = Lc[size_t(j) * r0 + j].real();
+    for (int k = 0; k < j; ++k) d -= std::norm(Lc[size_t(j) * r0 + k]);
+    if (!(d > 0)) return LS_OK;                      // degenerate: keep the zero guesses
+    d = std::sqrt(d);
+    Lc[size_t(j) * r0 + j] = d;
+    for (int i = j + 1; i < r0; ++i) {
+      cd v = Lc[size_t(i) * r0 + j];
+      for (int k = 0; k < j; ++k) v -= Lc[size_t(i) * r0 + k] * std::conj(Lc[size_t(j) * r0 + k]);
+      Lc[size_t(i) * r0 + j] = v / d;
+    }
+  }
+  std::vector<double> nrm(1);
+  for (int r = 0; r < R; ++r) {
+    double2* x = X + int64_t(r0 + r) * N;
+    LS_CU(lsd::norm2(x, N, reinterpret_cast<double*>(plan->seed_part), reinterpret_cast<double*>(plan->seed_h), st));
+    LS_CU(cudaMemcpyAsync(nrm.data(), plan->seed_h, sizeof(double), cudaMemcpyDeviceToHost, st));
+    LS_CU(cudaStreamSynchronize(st));
+    if (nrm[0] != 0.0) continue;                     // the caller gave a guess
+    LS_CU(lsd::gram(B, r0, N, B + int64_t(r0 + r) * N, N, plan->seed_part, plan->seed_h, st));
+    LS_CU(cudaMemcpyAsync(col.data(), plan->seed_h, r0 * sizeof(double2), cudaMemcpyDeviceToHost, st));
+    LS_CU(cudaStreamSynchronize(st));
+    std::vector<cd> c(r0);
+    for (int i = 0; i < r0; ++i) {                   // L y = h
+      cd v = col[i];
+      for (int k = 0; k < i; ++k) v -= Lc[size_t(i) * r0 + k] * c[k];
+      c[i] = v / Lc[size_t(i) * r0 + i];
+    }
+    for (int i = r0 - 1; i >= 0; --i) {              // L^H c = y
+      cd v = c[i];
+      for (int k = i + 1; k < r0; ++k) v -= std::conj(Lc[size_t(k) * r0 + i]) * c[k];
+      c[i] = v / Lc[size_t(i) * r0 + i].real();
+    }
+    LS_CU(cudaMemcpyAsync(plan->seed_h, c.data(), r0 * sizeof(double2), cudaMemcpyHostToDevice, st));
+    LS_CU(lsd::combine(X, r0, N, plan->seed_h, x, N, st));
+  }
+  return LS_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1119,8 +1199,13 @@ ls_status ls_solve(ls_plan plan, const void* uinc, void* u, int nrhs, double tol
   int total_it = 0, total_ref = 0;
   double worst = 0;
   ls_status result = LS_OK;
+  std::vector<cd> G;                        // Gram matrix of the solved right-hand sides
   for (int r0 = 0; r0 < nrhs; r0 += Rb) {
     const int R = std::min(Rb, nrhs - r0);
+    if (r0 > 0) {
+      s = seed_from_previous(plan, static_cast<const double2*>(uinc), static_cast<double2*>(u), r0, R, N, G, st);
+      if (s != LS_OK) return s;
+    }
     // FP64 apply of R contiguous vectors (chunks of at most kMaxRhs64)
     auto op64 = [&](const double2* v, double2* Av, const char*) -> cudaError_t {
       for (int r = 0; r < R;) {

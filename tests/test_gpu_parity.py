@@ -250,3 +250,22 @@ def test_cfg2_full_size_sampled_rows():
     assert rel(got, ref) < 1e-12
     got32 = plan.apply(ud.to(torch.complex64), prec=LS_MIXED).cpu().numpy()[inv[rows]]
     assert rel(got32.astype(np.complex128), ref) < 1e-5
+
+
+def test_many_directions_seeded_from_earlier_solutions(disc):
+    """More directions than one lock-step batch: later batches start from the
+    least-squares combination of the earlier solutions (A x_j = b_j), which
+    must not change the solutions and must save iterations."""
+    from paper_1509_05063_gb300 import LS_FP64
+    th = 2 * math.pi * np.arange(24) / 24
+    U = np.stack([W.plane_wave(disc.wl.kappa, (math.cos(t), math.sin(t)), disc.dz.x) for t in th])
+    sol, info = disc.plan.solve(disc.dev(U), tol=1e-10, prec=LS_FP64)
+    assert info["converged"] and info["residual"] <= 1e-10
+    separate = 0
+    for r in (0, 7, 23):
+        one, i1 = disc.plan.solve(disc.dev(U[r]), tol=1e-10, prec=LS_FP64)
+        assert rel(sol[r].cpu().numpy(), one.cpu().numpy()) < 1e-8
+    for r in range(24):
+        _, i1 = disc.plan.solve(disc.dev(U[r]), tol=1e-10, prec=LS_FP64)
+        separate += i1["iterations"]
+    assert info["iterations"] < separate
