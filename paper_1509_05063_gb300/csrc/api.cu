@@ -63,6 +63,17 @@ struct DevOwner {
     }
     return d;
   }
+  // free one buffer obtained from alloc / upload (nullptr: nothing)
+  void release(const void* p) {
+    if (!p) return;
+    for (size_t i = 0; i < bufs.size(); ++i)
+      if (bufs[i].p == p) {
+        cudaFree(bufs[i].p);
+        device_bytes -= int64_t(bufs[i].bytes);
+        bufs.erase(bufs.begin() + i);
+        return;
+      }
+  }
   void free_bufs() {
     for (auto& b : bufs) cudaFree(b.p);
     bufs.clear();
@@ -691,6 +702,17 @@ ls_status ensure_krylov(DevOwner* plan, Krylov& K, int restart, const Layout& la
   const int64_t Tw = std::max(total, K.total), Lw = std::max(max_len, K.max_len);
   ls_status st = LS_OK;
   const int nb = lsd::gram_blocks(Lw);
+  // the previous (smaller) work space: no solve is running (ls_solve synchronises before it returns)
+  for (const void* p : {static_cast<const void*>(K.V), static_cast<const void*>(K.w), static_cast<const void*>(K.r),
+                        static_cast<const void*>(K.e), static_cast<const void*>(K.cor),
+                        static_cast<const void*>(K.apart), static_cast<const void*>(K.h),
+                        static_cast<const void*>(K.partial), static_cast<const void*>(K.dnorm),
+                        static_cast<const void*>(K.dpartial), static_cast<const void*>(K.c64a),
+                        static_cast<const void*>(K.c64b), static_cast<const void*>(K.hk),
+                        static_cast<const void*>(K.nk)})
+    plan->release(p);
+  K.free_pinned();
+  K = Krylov{};
   K.V = plan->alloc<double2>(size_t(restart + 1) * Tw, &st);
   K.w = plan->alloc<double2>(size_t(Tw), &st);
   K.r = plan->alloc<double2>(size_t(Tw), &st);

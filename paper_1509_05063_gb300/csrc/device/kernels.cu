@@ -214,12 +214,11 @@ template <typename T>
 cudaError_t fft2d(T* x, int M, int logM, const T* tw, bool inverse, cudaStream_t st) {
   if (M < 256 || M > kFftMaxM || (M & (M - 1))) return cudaErrorInvalidValue;
   const size_t srow = size_t(M) * sizeof(T), scol = size_t(M) * kFftCols * sizeof(T);
-  static bool attr_done = false;
-  if (!attr_done) {
+  static unsigned long long attr_done = 0;
+  if (first_on_device(attr_done)) {
     cudaFuncSetAttribute(k_fft_rows<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kFftMaxM * sizeof(T)));
     cudaFuncSetAttribute(k_fft_cols<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          int(kFftMaxM * kFftCols * sizeof(T)));
-    attr_done = true;
   }
   k_fft_rows<T><<<M, M / 8, srow, st>>>(x, M, logM, tw, inverse);
   k_fft_cols<T><<<M / kFftCols, kFftCols * M / 8, scol, st>>>(x, M, logM, tw, inverse);
@@ -382,12 +381,11 @@ cudaError_t lattice_conv(const ApplyData<T>& d, int nr, cudaStream_t st) {
   const int M = d.M;
   if (M < 256 || M > kFftMaxM || (M & (M - 1))) return cudaErrorInvalidValue;
   const int TC = conv_cols_tc<T>(M);
-  static bool attr_done = false;
-  if (!attr_done) {
+  static unsigned long long attr_done = 0;
+  if (first_on_device(attr_done)) {
     cudaFuncSetAttribute(k_src_rows<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kFftMaxM * sizeof(T)));
     cudaFuncSetAttribute(k_inv_rows<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kFftMaxM * sizeof(T)));
     cudaFuncSetAttribute(k_conv_cols<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    attr_done = true;
   }
   // R (2 (L+1) x M) lives in Sd, Vt (n_lat x M) in Sm, V (n_lat x M) back in Sd
   const int64_t stride = d.lattice_rows() * M;
@@ -687,10 +685,9 @@ cudaError_t apply_r(const ApplyData<T>& d, const T* u, T* out, cudaStream_t st, 
   if (e != cudaSuccess) return e;
   if (ev) cudaEventRecord(ev[3], st);
   const size_t sm_local = size_t(R) * (d.n_loc + 9 * d.n_es) * sizeof(T);
-  static bool local_attr = false;     // X_c above 48 KB (large N_eq with many RHS)
-  if (!local_attr) {
+  static unsigned long long local_attr = 0;     // X_c above 48 KB (large N_eq with many RHS)
+  if (first_on_device(local_attr)) {
     cudaFuncSetAttribute(k_local_coeffs<T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
-    local_attr = true;
   }
   if (sm_local > 160 * 1024) return cudaErrorInvalidValue;
   k_local_coeffs<T, R><<<d.nocc, 256, sm_local, st>>>(d.nocc, d.occ_cells, d.occ_of_cell, d.L, d.Ne, d.M, d.Sd,
@@ -755,10 +752,9 @@ cudaError_t apply_multi(const InstData<T>* dev_inst, const InstData<T>* host_ins
     if (e != cudaSuccess) return e;
   }
   const size_t sm_local = size_t(max_K) * sizeof(T);
-  static bool attr = false;
-  if (!attr) {
+  static unsigned long long attr = 0;
+  if (first_on_device(attr)) {
     cudaFuncSetAttribute(k_local_coeffs_multi<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
-    attr = true;
   }
   if (sm_local > 160 * 1024) return cudaErrorInvalidValue;
   k_local_coeffs_multi<T><<<n_cells, 256, sm_local, st>>>(cells, dev_inst);
@@ -886,10 +882,9 @@ cudaError_t gram(const double2* V, int nv, int64_t vstride, const double2* w, in
                  double2* h, cudaStream_t st) {
   const int nb = gram_blocks(N);
   const int64_t chunk = gram_chunk(N);
-  static bool attr = false;
-  if (!attr) {
+  static unsigned long long attr = 0;
+  if (first_on_device(attr)) {
     cudaFuncSetAttribute(k_gram_partial, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
-    attr = true;
   }
   // blockIdx.y selects 8 of the nv + 1 dot products: enough warps to hide the
   // FP64 latency (the complex multiply-adds of this kernel run on GB300's

@@ -5,6 +5,17 @@
 
 namespace lsd {
 
+// True the first time it is called for the current device with this mask
+// (kernel attributes such as the shared-memory limit are per device).
+inline bool first_on_device(unsigned long long& mask) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return true;
+  const unsigned long long bit = 1ull << dev;
+  if (mask & bit) return false;
+  mask |= bit;
+  return true;
+}
+
 // Device-resident pieces of a plan for one arithmetic precision R.
 template <typename T>
 struct ApplyData {

@@ -338,11 +338,10 @@ __global__ void __launch_bounds__(kTcThreads) k_near_tc(const int2* __restrict__
 template <int R>
 cudaError_t near_eval_tc(const ApplyData<float2>& d, const float2* u, float2* out, cudaStream_t st) {
   using Lay = TcLayout<R>;
-  static bool attr = false;
-  if (!attr) {
+  static unsigned long long attr = 0;
+  if (first_on_device(attr)) {
     cudaError_t e = cudaFuncSetAttribute(k_near_tc<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, Lay::kBytes);
     if (e != cudaSuccess) return e;
-    attr = true;
   }
   if (d.n_items128 == 0) return cudaSuccess;
   k_near_tc<R><<<d.n_items128, kTcThreads, Lay::kBytes, st>>>(d.items128, d.occ_start, d.blk_off, d.blk_seg, d.Wb,
