@@ -22,7 +22,8 @@ The steps follow the paper's order and notation:
    (Fourier-Bessel) form J_n(kappa r) e^{i n theta} / J_|n|(kappa R_ref),
    |n| <= n_fb, which spans the same Helmholtz solutions but stays well
    conditioned for kappa H ~ 1; the fit uses every lattice point of the
-   closed cell (faces and interior).
+   closed cell (faces and interior).  local_basis="pw" keeps the literal plane
+   waves instead (the paper's form, for comparison).
 """
 from __future__ import annotations
 
@@ -105,9 +106,12 @@ def near_matrix(dz: Discretisation, cells: Cells, rows=None, chunk: int = 512):
 class Accelerator:
     """Far (non-adjacent) part of K via equivalent sources and the lattice FFT."""
 
-    def __init__(self, dz: Discretisation, cells: Cells | None = None):
+    def __init__(self, dz: Discretisation, cells: Cells | None = None, local_basis: str = "fb"):
         wl = dz.wl
         self.dz = dz
+        if local_basis not in ("fb", "pw"):
+            raise ValueError(local_basis)
+        self.local_basis = local_basis
         self.cells = cells if cells is not None else Cells(dz)
         k = self.kappa = wl.kappa
         Ne = self.Ne = wl.N_eq
@@ -137,7 +141,7 @@ class Accelerator:
         self.Rref = H / math.sqrt(2.0)
         xb = self.loc_a * self.delta - H / 2
         yb = self.loc_b * self.delta - H / 2
-        B = self._fb_basis(xb, yb)                                   # (n_loc, 2 nfb + 1)
+        B = self._local_basis(xb, yb)                                # (n_loc, 2 nfb + 1)
         self.Bpinv = _lstsq_apply(_svd(B), np.eye(self.n_loc))
         # neighbour tables T_o (n_loc, n_es) for offsets o in {-1,0,1}^2
         self.T = {}
@@ -157,7 +161,7 @@ class Accelerator:
             Gc = mono_kernel(k, self.coll[:, 0][:, None] - rx[None, :],
                              self.coll[:, 1][:, None] - ry[None, :])       # (ncoll, n_c)
             self.P[c] = _lstsq_apply(self.Asvd, Gc) * dz.wfac[mem][None, :]
-            self.Phi[c] = self._fb_basis(rx - H / 2, ry - H / 2)
+            self.Phi[c] = self._local_basis(rx - H / 2, ry - H / 2)
         # lattice FFT plan
         self.n_lat = L * Ne + 1
         self.M = _fft_size(2 * self.n_lat - 1)
@@ -201,6 +205,16 @@ class Accelerator:
         dip = dip_kernel(self.kappa, dax, dbx)
         val = np.where(np.asarray(kind) == 0, mono, dip)
         return np.where(zero, 0.0, val)
+
+    def _local_basis(self, x, y):
+        return self._fb_basis(x, y) if self.local_basis == "fb" else self._pw_basis(x, y)
+
+    def _pw_basis(self, x, y):
+        """The paper's literal form of Eq. PWE: plane waves exp(i kappa d_l . x) in
+        2 n_fb + 1 equally spaced directions d_l (comparison variant)."""
+        m = 2 * self.nfb + 1
+        th = 2 * math.pi * np.arange(m) / m
+        return np.exp(1j * self.kappa * (x[:, None] * np.cos(th)[None, :] + y[:, None] * np.sin(th)[None, :]))
 
     def _fb_basis(self, x, y):
         n = np.arange(-self.nfb, self.nfb + 1)
