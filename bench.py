@@ -41,7 +41,7 @@ KERNELS_PER_APPLY = 6    # projection, source rows (fill + row FFT), columns (FF
 # DRAM bytes (read + write) of one k_near_eval launch on the full-size kite workload, from the
 # ncu launch list of this bench (per-launch counters; keyed by the padded block-entry count
 # so that any other workload reports no traffic).  Re-measure whenever k_near_eval changes.
-NEAR_TRAFFIC = {357685015: {"fp64": 5.9051e9, "mixed": 2.9456e9, "tc16": 3.1729e9}}
+NEAR_TRAFFIC = {357685015: {"fp64": None, "mixed": 2.9456e9, "tc16": 3.1729e9}}
 
 
 def hbm_peak():
@@ -407,23 +407,26 @@ def main():
     nfb2 = 2 * info["n_fb"] + 1
     nocc = info["n_cells_occupied"]
 
-    def near_bytes(cb):   # algorithmic bytes of one k_near_eval launch, cb = bytes per complex:
+    def near_bytes(cb, wb=None):   # algorithmic bytes of one k_near_eval launch, cb = bytes per complex,
+        # wb = bytes per block weight (complex128 also reads Re + Im of each weight: 24 B):
         # dense per-cell weight blocks (+ the tiny CSR remainder, counted as blocks), u, Phi, gamma, out
-        return nnz * cb + N * cb + N * nfb2 * cb + N * 12 + nocc * nfb2 * cb + N * cb
+        return nnz * (wb or cb) + N * cb + N * nfb2 * cb + N * 12 + nocc * nfb2 * cb + N * cb
 
     peak, peak_src = hbm_peak()
     traffic = NEAR_TRAFFIC.get(nnz, {})
-    near_flops = nnz * 8 + N * nfb2 * 8          # complex multiply-adds of one launch
+    # FP64 flops of one launch: 3 FMAs per block weight (three-multiplication
+    # complex product), 4 per Phi-gamma term
+    near_flops = nnz * 6 + N * nfb2 * 8
     t_near64 = st64[4] / max(c64, 1) * 1e-3
     t_near32 = st32[4] / max(c32, 1) * 1e-3
-    ach64 = near_bytes(16) / t_near64 / 1e9
+    ach64 = near_bytes(16, 24) / t_near64 / 1e9
     ach32 = near_bytes(8) / t_near32 / 1e9
     M = info["fft_M"]
     n_lat = info["L"] * info["N_eq"] + 1
     # whole-apply byte model: u in, out, weights, projections, Phi, lattice passes, quarter spectra
     lat_bytes = lambda cb: (2 * (info["L"] + 1) * M * cb * 2 + 2 * (M // 2 + 1) ** 2 * cb
                             + 2 * n_lat * M * cb * 2)
-    apply_bytes64 = near_bytes(16) + N * 16 * 4 + lat_bytes(16)
+    apply_bytes64 = near_bytes(16, 24) + N * 16 * 4 + lat_bytes(16)
     # batched complex64 (tensor-core near field): weights once, per-RHS vectors, Phi once
     near_bytes_b = nnz * 8 + N * nfb2 * 8 + N * 12 + NB32 * (2 * N * 8 + nocc * nfb2 * 8)
     t_near_b = stb[4] / max(cb, 1) * 1e-3
@@ -447,7 +450,7 @@ def main():
         "config": {"workload": f"cfg2 kite kappa=20 N={N} nnz_near={nnz} lattice {M}x{M}",
                    "N": N, "nnz_near": nnz, "fft_M": M, "L": info["L"], "N_eq": info["N_eq"],
                    "n_fb": info["n_fb"], "parallelism": f"replicas x{world}",
-                   "l2": "inputs larger than L2 (near-field weights %.1f GB)" % (nnz * 20 / 1e9),
+                   "l2": "inputs larger than L2 (FP64 near-field weights %.1f GB)" % (nnz * 24 / 1e9),
                    "plan_seconds": info["plan_seconds"], "device_bytes": info["device_bytes"]},
         "e2e": {"value": world * args.steps / (ms_e2e * 1e-3), "unit": "matvecs/s",
                 "h2d_bytes_per_step": N * 16, "d2h_bytes_per_step": N * 16},
@@ -455,7 +458,7 @@ def main():
                      "achieved": near_flops / t_near64 / 1e12, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": near_flops / t_near64 / 1e12 / FP64_PEAK_TFLOPS, "traffic": traffic.get("fp64"),
                      "peak_source": "derived: 152 SMs x 2070 MHz x 2 FP64 FMA/clk/SM",
-                     "flops_per_launch": near_flops, "bytes_per_launch": near_bytes(16),
+                     "flops_per_launch": near_flops, "bytes_per_launch": near_bytes(16, 24),
                      "hbm_GBs": ach64, "hbm_frac": ach64 / peak, "hbm_peak": peak, "hbm_peak_source": peak_src,
                      "launch_ms": t_near64 * 1e3},
         "gpu_launches": KERNELS_PER_APPLY * args.steps,

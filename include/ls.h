@@ -193,10 +193,12 @@ ls_status ls_plan_destroy(ls_plan plan);
  * device.  Vectors of a batch are the instances' node vectors (ls_plan_nodes
  * order) concatenated in plan order; instance i starts at element off[i]
  * (ls_batch_offsets).  ls_batch_apply runs the projection, the local expansion
- * and the near-field correction of all instances as ONE kernel each, walking an
- * (instance, cell) work list, and the lattice convolution per instance;
- * repeated calls with the same buffers replay a CUDA graph.
- * Errors: LS_ERR_INVALID for null or empty arguments, LS_ERR_NOMEM / LS_ERR_CUDA
+ * and the near-field correction of all instances as ONE kernel each, walking
+ * (instance, projection piece / cell / row block) work lists, and the lattice
+ * convolution per instance; each instance sums exactly as ls_apply does for it
+ * alone; repeated calls with the same buffers replay a CUDA graph.
+ * Errors: LS_ERR_INVALID for null or empty arguments or a plan listed twice
+ * (its instances would share the plan's work arrays), LS_ERR_NOMEM / LS_ERR_CUDA
  * from allocation or upload; the message is in ls_batch_last_error (or, for a
  * failed ls_batch_create, ls_batch_last_error(NULL)). */
 typedef struct ls_batch_s* ls_batch;

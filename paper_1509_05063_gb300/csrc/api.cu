@@ -475,6 +475,57 @@ ls_status ls_plan_create(const ls_geometry* geom, ls_n2_fn n2, void* ctx, double
   const int* d_occ_of_cell = UP(int, occ_of_cell);
   const int* d_occ_of_node = UP(int, occ_of_node);
   const int64_t* d_P_off = UP(int64_t, P.P_off);
+  // projection pieces: each cell's nodes cut into np near-equal runs of at most
+  // kProjPiece, the longest runs first; cells of several pieces get np
+  // partial-sum slots
+  std::vector<int> pieces, piece_off(nocc, 0);
+  int n_slots = 0;
+  for (int k = 0; k < nocc; ++k) {
+    const int nc = int(occ_start[k + 1] - occ_start[k]);
+    const int np = std::max(1, (nc + lsd::kProjPiece - 1) / lsd::kProjPiece);
+    if (np > 0xffff) return bail(LS_ERR_INVALID, "a cell holds too many nodes");
+    piece_off[k] = n_slots;
+    if (np > 1) n_slots += np;
+    for (int q = 0; q < np; ++q) {
+      pieces.push_back(k);
+      pieces.push_back(int(int64_t(q) * nc / np));
+      pieces.push_back(int(int64_t(q + 1) * nc / np));
+      pieces.push_back((q << 16) | np);
+    }
+  }
+  {
+    const size_t n = pieces.size() / 4;
+    std::vector<size_t> idx(n);
+    for (size_t i = 0; i < n; ++i) idx[i] = i;
+    std::stable_sort(idx.begin(), idx.end(), [&](size_t x, size_t y) {
+      return pieces[4 * x + 2] - pieces[4 * x + 1] > pieces[4 * y + 2] - pieces[4 * y + 1];
+    });
+    std::vector<int> o(pieces.size());
+    for (size_t i = 0; i < n; ++i)
+      for (int c = 0; c < 4; ++c) o[4 * i + c] = pieces[4 * idx[i] + c];
+    pieces.swap(o);
+  }
+  std::vector<int> cell_pieces;
+  {
+    std::vector<int> by_size(nocc);
+    for (int k = 0; k < nocc; ++k) by_size[k] = k;
+    std::stable_sort(by_size.begin(), by_size.end(), [&](int x, int y) {
+      return occ_start[x + 1] - occ_start[x] > occ_start[y + 1] - occ_start[y];
+    });
+    for (int k : by_size) {
+      cell_pieces.push_back(k);
+      cell_pieces.push_back(0);
+      cell_pieces.push_back(int(occ_start[k + 1] - occ_start[k]));
+      cell_pieces.push_back(1);
+    }
+  }
+  const int* d_cell_pieces_raw = UP(int, cell_pieces);
+  const int4* d_cell_pieces = reinterpret_cast<const int4*>(d_cell_pieces_raw);
+  const int* d_pieces_raw = UP(int, pieces);
+  const int4* d_pieces = reinterpret_cast<const int4*>(d_pieces_raw);
+  const int* d_piece_off = UP(int, piece_off);
+  int* d_count64 = UP(int, std::vector<int>(nocc, 0));
+  int* d_count32 = UP(int, std::vector<int>(nocc, 0));
   std::vector<int> items, items32, items128;   // (occupied cell, first row) pairs, 16 / 32 / 128 rows each
   for (int k = 0; k < nocc; ++k)
     for (int64_t r = 0; r < occ_start[k + 1] - occ_start[k]; r += 16) {
@@ -482,8 +533,33 @@ ls_status ls_plan_create(const ls_geometry* geom, ls_n2_fn n2, void* ctx, double
       if (r % 32 == 0) { items32.push_back(k); items32.push_back(int(r)); }
       if (r % 128 == 0) { items128.push_back(k); items128.push_back(int(r)); }
     }
+  // heaviest work items first (rows x padded columns), so that the last wave of
+  // the grid holds the short ones.  For the FP64-bound and tensor-core grids;
+  // the HBM-bound complex64 grids on CUDA cores keep cell order, which streams
+  // the weights in address order.
+  auto heaviest_first = [&](std::vector<int>& v, int rows_per) {
+    const size_t n = v.size() / 2;
+    std::vector<std::pair<int64_t, size_t>> cost(n);
+    for (size_t i = 0; i < n; ++i) {
+      const int k = v[2 * i], r = v[2 * i + 1];
+      const int* sg = &blk_seg[6 * k];
+      const int64_t nblk = padded(sg[1]) + padded(sg[3]) + padded(sg[5]);
+      cost[i] = {std::min<int64_t>(rows_per, occ_start[k + 1] - occ_start[k] - r) * nblk, i};
+    }
+    std::stable_sort(cost.begin(), cost.end(), [](const auto& x, const auto& y) { return x.first > y.first; });
+    std::vector<int> o(v.size());
+    for (size_t i = 0; i < n; ++i) {
+      o[2 * i] = v[2 * cost[i].second];
+      o[2 * i + 1] = v[2 * cost[i].second + 1];
+    }
+    v.swap(o);
+  };
   const int* d_items_raw = UP(int, items);
   const int2* d_items = reinterpret_cast<const int2*>(d_items_raw);
+  heaviest_first(items, 16);
+  heaviest_first(items128, 128);
+  const int* d_items64_raw = UP(int, items);
+  const int2* d_items64 = reinterpret_cast<const int2*>(d_items64_raw);
   const int* d_items32_raw = UP(int, items32);
   const int2* d_items32 = reinterpret_cast<const int2*>(d_items32_raw);
   const int* d_items128_raw = UP(int, items128);
@@ -541,28 +617,66 @@ ls_status ls_plan_create(const ls_geometry* geom, ls_n2_fn n2, void* ctx, double
   a.M = M; a.n_lat = P.n_lat; a.logM = logM;
   a.occ_start = d_occ_start; a.occ_cells = d_occ_cells; a.occ_of_cell = d_occ_of_cell;
   a.occ_of_node = d_occ_of_node; a.P_off = d_P_off;
+  a.pieces = d_pieces; a.n_pieces = int(pieces.size() / 4); a.piece_off = d_piece_off; a.proj_count = d_count64;
+  a.cell_pieces = d_cell_pieces;
   a.blk_off = d_blk_off; a.blk_seg = d_blk_seg; a.rem_row = d_rem_row; a.rem_col = d_rem_col;
   a.max_nblk = max_nblk;
-  a.items = d_items; a.n_items = int(items.size() / 2);
+  a.items = d_items64; a.n_items = int(items.size() / 2);
   a.items32 = d_items32; a.n_items32 = int(items32.size() / 2);
+  // projections per cell stored [node][n_es] (thread per row of P_c reads
+  // consecutive entries); Re + Im of each entry for the three-multiplication product
+  auto node_major = [&](std::vector<cd>& Pm) {
+    std::vector<cd> t(Pm.size());
+    for (int k = 0; k < nocc; ++k) {
+      const int64_t base = P.P_off[k], nc = occ_start[k + 1] - occ_start[k];
+      for (int i = 0; i < P.n_es; ++i)
+        for (int64_t j = 0; j < nc; ++j) t[base + j * P.n_es + i] = Pm[base + i * nc + j];
+    }
+    Pm.swap(t);
+  };
+  node_major(P.P64);
+  node_major(P.P32);
   a.P = UP(double2, P.P64);
+  {
+    double* ps = plan->alloc<double>(P.P64.size(), &st);
+    if (st != LS_OK) return bail(st, plan->err);
+    const cudaError_t e = lsd::weight_sums(a.P, ps, int64_t(P.P64.size()), 0);
+    if (e != cudaSuccess) return bail(LS_ERR_CUDA, std::string("projection sums: ") + cudaGetErrorString(e));
+    a.Ps = ps;
+  }
   // local-expansion matrix [B^+ | -B^+ T_o ...]: one contraction with the cell's
   // lattice values and its 3 x 3 neighbours' strengths gives gamma_c
   const int n_lk = P.n_loc + 9 * P.n_es;
+  // stored transposed, [n_lk][nfb2] (thread per row n reads consecutive entries)
   std::vector<cd> LA(size_t(P.nfb2) * n_lk);
   for (int n = 0; n < P.nfb2; ++n) {
-    for (int p = 0; p < P.n_loc; ++p) LA[size_t(n) * n_lk + p] = P.Bpinv[size_t(n) * P.n_loc + p];
+    for (int p = 0; p < P.n_loc; ++p) LA[size_t(p) * P.nfb2 + n] = P.Bpinv[size_t(n) * P.n_loc + p];
     for (int o = 0; o < 9; ++o)
       for (int l = 0; l < P.n_es; ++l)
-        LA[size_t(n) * n_lk + P.n_loc + o * P.n_es + l] = -P.BT[(size_t(o) * P.nfb2 + n) * P.n_es + l];
+        LA[size_t(P.n_loc + o * P.n_es + l) * P.nfb2 + n] = -P.BT[(size_t(o) * P.nfb2 + n) * P.n_es + l];
   }
   a.LA = UP(double2, LA);
+  {
+    double* las = plan->alloc<double>(LA.size(), &st);
+    if (st != LS_OK) return bail(st, plan->err);
+    const cudaError_t e = lsd::weight_sums(a.LA, las, int64_t(LA.size()), 0);
+    if (e != cudaSuccess) return bail(LS_ERR_CUDA, std::string("local matrix sums: ") + cudaGetErrorString(e));
+    a.LAs = las;
+  }
   a.Phi = UP(double2, P.Phi);
   a.Wb = UP(double2, Wb);
+  {   // Re + Im of every block weight: the three-multiplication complex product
+    double* ws = plan->alloc<double>(size_t(blk_off[nocc]), &st);
+    if (st != LS_OK) return bail(st, plan->err);
+    const cudaError_t e = lsd::weight_sums(a.Wb, ws, blk_off[nocc], 0);
+    if (e != cudaSuccess) return bail(LS_ERR_CUDA, std::string("weight sums: ") + cudaGetErrorString(e));
+    a.Ws = ws;
+  }
   a.rem_val = UP(double2, rem_val);
   a.Gq = d_G64; a.Dq = d_D64; a.tw = d_tw64;
   a.kappa2 = kappa * kappa;
   a.sigma = plan->alloc<double2>(size_t(lsd::kMaxRhs64) * nocc * P.n_es, &st);
+  a.proj_part = plan->alloc<double2>(size_t(lsd::kMaxRhs64) * n_slots * P.n_es, &st);
   a.Sm = plan->alloc<double2>(lsd::kMaxRhs64 * a.lattice_rows() * M, &st);
   a.Sd = plan->alloc<double2>(lsd::kMaxRhs64 * a.lattice_rows() * M, &st);
   a.gamma = plan->alloc<double2>(size_t(lsd::kMaxRhs64) * nocc * P.nfb2, &st);
@@ -573,9 +687,11 @@ ls_status ls_plan_create(const ls_geometry* geom, ls_n2_fn n2, void* ctx, double
   b.M = a.M; b.n_lat = a.n_lat; b.logM = a.logM;
   b.occ_start = a.occ_start; b.occ_cells = a.occ_cells; b.occ_of_cell = a.occ_of_cell;
   b.occ_of_node = a.occ_of_node; b.P_off = a.P_off;
+  b.pieces = a.pieces; b.n_pieces = a.n_pieces; b.piece_off = a.piece_off; b.proj_count = d_count32;
+  b.cell_pieces = a.cell_pieces;
   b.blk_off = a.blk_off; b.blk_seg = a.blk_seg; b.rem_row = a.rem_row; b.rem_col = a.rem_col;
   b.max_nblk = a.max_nblk;
-  b.items = a.items; b.n_items = a.n_items;
+  b.items = d_items; b.n_items = a.n_items;
   b.items32 = a.items32; b.n_items32 = a.n_items32;
   b.items128 = d_items128; b.n_items128 = int(items128.size() / 2);
   b.tc_err = d_tc_err;
@@ -592,6 +708,7 @@ ls_status ls_plan_create(const ls_geometry* geom, ls_n2_fn n2, void* ctx, double
   b.tw = UP(float2, to32(tw));
   b.kappa2 = a.kappa2;
   b.sigma = plan->alloc<float2>(size_t(lsd::kMaxRhs32) * nocc * P.n_es, &st);
+  b.proj_part = plan->alloc<float2>(size_t(lsd::kMaxRhs32) * n_slots * P.n_es, &st);
   b.Sm = plan->alloc<float2>(lsd::kMaxRhs32 * b.lattice_rows() * M, &st);
   b.Sd = plan->alloc<float2>(lsd::kMaxRhs32 * b.lattice_rows() * M, &st);
   b.gamma = plan->alloc<float2>(size_t(lsd::kMaxRhs32) * nocc * P.nfb2, &st);
@@ -1407,6 +1524,11 @@ ls_status noalloc_apply(ls_plan plan, const lsd::ApplyData<T>& src, const void* 
   d.Sd = reinterpret_cast<T*>(p);
   p += up256(n_grid * sizeof(T));
   d.gamma = reinterpret_cast<T*>(p);
+  // the projection runs one block per whole cell: no partial sums or counters in plan memory
+  d.pieces = src.cell_pieces;
+  d.n_pieces = src.nocc;
+  d.proj_part = nullptr;
+  d.proj_count = nullptr;
   e = lsd::apply_one(d, static_cast<const T*>(u), static_cast<T*>(Au), st);
   if (e != cudaSuccess) return fail(plan, LS_ERR_CUDA, std::string("ls_apply_noalloc: ") + cudaGetErrorString(e));
   return LS_OK;
@@ -1427,13 +1549,17 @@ extern "C" ls_status ls_apply_noalloc(ls_plan plan, const void* u, void* Au, ls_
 // iterating in a lock-step solve): device arrays owned by the set.
 struct ActiveSet {
   std::vector<int> ids;
+  int2* pieces = nullptr;
+  int n_pieces = 0;
   int2* cells = nullptr;
   int n_cells = 0;
   int4* items = nullptr;
   int n_items = 0;
   void release() {
+    if (pieces) cudaFree(pieces);
     if (cells) cudaFree(cells);
     if (items) cudaFree(items);
+    pieces = nullptr;
     cells = nullptr;
     items = nullptr;
   }
@@ -1447,7 +1573,8 @@ struct ls_batch_s : DevOwner {
   const lsd::InstData<double2>* d64 = nullptr;
   const lsd::InstData<float2>* d32 = nullptr;
   std::vector<std::vector<int>> cells_of, items_of;  // host work lists per instance (pairs / quadruples)
-  int max_nes = 0, max_K = 0;
+  std::vector<std::vector<int>> piece_len;           // node count of each projection piece, per instance
+  int max_K = 0;
   std::map<std::vector<char>, int> set_of;           // instance subset -> index in sets
   std::vector<ActiveSet> sets;
   Krylov K;
@@ -1478,22 +1605,32 @@ int active_set(ls_batch b, const char* need, cudaError_t* err) {
   }
   ActiveSet a;
   std::vector<int> cells, items;
+  std::vector<std::pair<int, int2>> pcs;             // (node count, (instance, piece))
   for (int i = 0; i < n; ++i) {
     if (!key[i]) continue;
     a.ids.push_back(i);
     cells.insert(cells.end(), b->cells_of[i].begin(), b->cells_of[i].end());
     items.insert(items.end(), b->items_of[i].begin(), b->items_of[i].end());
+    for (size_t q = 0; q < b->piece_len[i].size(); ++q) pcs.push_back({b->piece_len[i][q], make_int2(i, int(q))});
   }
+  // the largest projection pieces of all active instances first
+  std::stable_sort(pcs.begin(), pcs.end(), [](const auto& x, const auto& y) { return x.first > y.first; });
+  std::vector<int2> pieces(pcs.size());
+  for (size_t q = 0; q < pcs.size(); ++q) pieces[q] = pcs[q].second;
+  a.n_pieces = int(pieces.size());
   a.n_cells = int(cells.size() / 2);
   a.n_items = int(items.size() / 4);
   *err = cudaSuccess;
   if (!cells.empty()) {
     *err = cudaMalloc(&a.cells, cells.size() * sizeof(int));
     if (*err == cudaSuccess) *err = cudaMalloc(&a.items, items.size() * sizeof(int));
+    if (*err == cudaSuccess) *err = cudaMalloc(&a.pieces, pieces.size() * sizeof(int2));
     if (*err == cudaSuccess)
       *err = cudaMemcpy(a.cells, cells.data(), cells.size() * sizeof(int), cudaMemcpyHostToDevice);
     if (*err == cudaSuccess)
       *err = cudaMemcpy(a.items, items.data(), items.size() * sizeof(int), cudaMemcpyHostToDevice);
+    if (*err == cudaSuccess)
+      *err = cudaMemcpy(a.pieces, pieces.data(), pieces.size() * sizeof(int2), cudaMemcpyHostToDevice);
     if (*err != cudaSuccess) {
       a.release();
       return -1;
@@ -1516,8 +1653,8 @@ cudaError_t batch_apply_t(ls_batch b, int prec, const lsd::InstData<T>* dI, cons
   const ActiveSet& a = b->sets[si];
   if (a.ids.empty()) return cudaSuccess;
   auto launch = [&](cudaStream_t s) {
-    return lsd::apply_multi<T>(dI, hI.data(), a.ids.data(), int(a.ids.size()), a.cells, a.n_cells, a.items,
-                               a.n_items, b->max_nes, b->max_K, u, out, s);
+    return lsd::apply_multi<T>(dI, hI.data(), a.ids.data(), int(a.ids.size()), a.pieces, a.n_pieces, a.cells,
+                               a.n_cells, a.items, a.n_items, b->max_K, u, out, s);
   };
   return b->graphs.run(GraphCache::Key(prec, si, static_cast<const void*>(u), static_cast<void*>(out)), launch, st);
 }
@@ -1538,8 +1675,13 @@ ls_status ls_batch_create(const ls_plan* plans, int n_plans, ls_batch* out) {
   if (!out) return LS_ERR_INVALID;
   *out = nullptr;
   if (!plans || n_plans < 1) return fail(nullptr, LS_ERR_INVALID, "ls_batch_create: no plans");
-  for (int i = 0; i < n_plans; ++i)
+  for (int i = 0; i < n_plans; ++i) {
     if (!plans[i]) return fail(nullptr, LS_ERR_INVALID, "ls_batch_create: null plan");
+    for (int j = 0; j < i; ++j)
+      if (plans[j] == plans[i])
+        return fail(nullptr, LS_ERR_INVALID, "ls_batch_create: a plan appears twice (instances would share its "
+                                             "work arrays)");
+  }
   auto* b = new (std::nothrow) ls_batch_s();
   if (!b) return fail(nullptr, LS_ERR_NOMEM, "ls_batch_create: host allocation");
   auto bail = [&](ls_status s) {
@@ -1556,7 +1698,6 @@ ls_status ls_batch_create(const ls_plan* plans, int n_plans, ls_batch* out) {
     b->h64.push_back({p->d64, b->off.back()});
     b->h32.push_back({p->d32, b->off.back()});
     b->off.push_back(b->off.back() + p->d64.N);
-    b->max_nes = std::max(b->max_nes, p->d64.n_es);
     b->max_K = std::max(b->max_K, p->d64.n_loc + 9 * p->d64.n_es);
     std::vector<int> cells, items;
     for (int k = 0; k < p->d64.nocc; ++k) { cells.push_back(i); cells.push_back(k); }
@@ -1569,8 +1710,16 @@ ls_status ls_batch_create(const ls_plan* plans, int n_plans, ls_batch* out) {
     for (size_t e = 0; e < it.size(); e += 2) {
       items.push_back(i); items.push_back(it[e]); items.push_back(it[e + 1]); items.push_back(0);
     }
+    std::vector<int> pc(size_t(4) * p->d64.n_pieces), len(p->d64.n_pieces);
+    if (cudaMemcpy(pc.data(), p->d64.pieces, pc.size() * sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) {
+      cudaGetLastError();
+      b->err = "ls_batch_create: reading a plan's projection pieces failed";
+      return bail(LS_ERR_CUDA);
+    }
+    for (int q = 0; q < p->d64.n_pieces; ++q) len[q] = pc[4 * q + 2] - pc[4 * q + 1];
     b->cells_of.push_back(std::move(cells));
     b->items_of.push_back(std::move(items));
+    b->piece_len.push_back(std::move(len));
   }
   int64_t n_cells = 0, n_items = 0;
   for (int i = 0; i < n_plans; ++i) {

@@ -19,43 +19,216 @@ template <typename T> struct RealOf;
 template <> struct RealOf<double2> { using R = double; };
 template <> struct RealOf<float2> { using R = float; };
 
-// ------------------------------------------------------------ ES projection
-// sigma_c = P_c u_c.  Block (cell, group of 8 rows of P_c), one warp per row:
-// lanes stride the cell's nodes (coalesced reads of P_c's row and of u_c),
-// then one warp reduction per RHS.
-template <typename T, int R>
-__device__ __forceinline__ void es_project_body(int k, int i, int nocc, const int64_t* __restrict__ occ_start,
-                                                const int64_t* __restrict__ P_off, const T* __restrict__ P,
-                                                const T* __restrict__ u, int64_t N, T* __restrict__ sigma,
-                                                int n_es) {
-  const int lane = threadIdx.x & 31;
-  if (k >= nocc || i >= n_es) return;
-  const int64_t s0 = occ_start[k];
-  const int nc = int(occ_start[k + 1] - s0);
-  const T* Pi = P + P_off[k] + int64_t(i) * nc;
-  T acc[R];
-#pragma unroll
-  for (int r = 0; r < R; ++r) acc[r] = czero(T{});
-#pragma unroll 4
-  for (int j = lane; j < nc; j += 32) {
-    const T pij = Pi[j];
-#pragma unroll
-    for (int r = 0; r < R; ++r) acc[r] = cfma(pij, u[r * N + s0 + j], acc[r]);
+// ------------------------------------------------------------ per-cell contractions
+// The projection and the local coefficients are small dense contractions per
+// cell, Y (n_out x R) = A (n_out x n_in) X (n_in x R), with A stored transposed
+// ([n_in][n_out]) and X staged in shared memory.  Thread t of the block owns
+// output o = t % n_out of segment s = t / n_out (S = blockDim / n_out segments)
+// and sums the inputs j = s, s + S, ... in increasing order; the S partial sums
+// are then added in segment order through shared memory.  No warp reductions,
+// every lane does useful work, and each output is summed the same way whatever R.
+//
+// Staged inputs: complex64 as is; complex128 as c = Re x and (c + d, d - c),
+// with the sum Re a + Im a of each matrix entry stored beside A, so that every
+// complex product takes three FP64 FMAs (Gauss's form, as in the near field).
+template <typename T> struct Staged;
+template <> struct Staged<float2> {
+  static constexpr int kBytes = 8;
+  float2* x;
+  int ld;
+  __device__ Staged(unsigned char* raw, int ld_) : x(reinterpret_cast<float2*>(raw)), ld(ld_) {}
+  __device__ void put(int r, int j, float2 v) const { x[r * ld + j] = v; }
+};
+template <> struct Staged<double2> {
+  static constexpr int kBytes = 24;
+  double* c;
+  double2* ef;
+  int ld;
+  // ld * R doubles of c first, then the pairs (16-byte aligned: ld is even)
+  __device__ Staged(unsigned char* raw, int ld_, int R)
+      : c(reinterpret_cast<double*>(raw)), ef(reinterpret_cast<double2*>(raw + size_t(R) * ld_ * 8)), ld(ld_) {}
+  __device__ void put(int r, int j, double2 v) const {
+    c[r * ld + j] = v.x;
+    ef[r * ld + j] = make_double2(v.x + v.y, v.y - v.x);
   }
+};
+
+template <typename T> struct CAcc;
+template <> struct CAcc<float2> {
+  float2 v;
+  __device__ void zero() { v = make_float2(0.f, 0.f); }
+  __device__ void mac(float2 a, double, const Staged<float2>& X, int r, int j) { v = cfma(a, X.x[r * X.ld + j], v); }
+  __device__ float2 value() const { return v; }
+};
+template <> struct CAcc<double2> {
+  double p, q, s;   // sum (a + b) c, sum b (c + d), sum a (d - c)
+  __device__ void zero() { p = q = s = 0.0; }
+  __device__ void mac(double2 a, double sa, const Staged<double2>& X, int r, int j) {
+    const double c = X.c[r * X.ld + j];
+    const double2 ef = X.ef[r * X.ld + j];
+    p = fma(sa, c, p);
+    q = fma(a.y, ef.x, q);
+    s = fma(a.x, ef.y, s);
+  }
+  __device__ double2 value() const { return make_double2(p - q, p + s); }
+};
+
+template <typename T>
+__device__ __forceinline__ Staged<T> staged_at(unsigned char* raw, int ld, int R) {
+  if constexpr (sizeof(T) == 16) return Staged<T>(raw, ld, R);
+  else return Staged<T>(raw, ld);
+}
+
+__device__ __forceinline__ const double* sa_base(const double* p, int64_t off) { return p ? p + off : nullptr; }
+
+// acc[r] += sum over j = j1, j1 + S, ... < j_end of A[j][o] X[r][j] (A row
+// length n_out; As = Re + Im of A for complex128).  Loads go out four at a
+// time; the sum runs in increasing j whatever R.
+template <typename T, int R>
+__device__ __forceinline__ void contract_segment(const T* __restrict__ A, const double* __restrict__ As, int n_out,
+                                                 int o, int j1, int j_end, int S, const Staged<T>& X,
+                                                 CAcc<T> (&acc)[R]) {
+  constexpr bool kC128 = sizeof(T) == 16;
+  constexpr int U = 4;
+  int j = j1;
+  for (; j + (U - 1) * S < j_end; j += U * S) {
+    T a[U];
+    double sa[U];
 #pragma unroll
-  for (int r = 0; r < R; ++r) {
-    const T v = warp_sum(acc[r]);
-    if (lane == 0) sigma[(int64_t(r) * nocc + k) * n_es + i] = v;
+    for (int v = 0; v < U; ++v) {
+      const int64_t e = int64_t(j + v * S) * n_out + o;
+      a[v] = A[e];
+      sa[v] = kC128 ? As[e] : 0.0;
+    }
+#pragma unroll
+    for (int v = 0; v < U; ++v)
+#pragma unroll
+      for (int r = 0; r < R; ++r) acc[r].mac(a[v], sa[v], X, r, j + v * S);
+  }
+  for (; j < j_end; j += S) {
+    const int64_t e = int64_t(j) * n_out + o;
+    const T a = A[e];
+    const double sa = kC128 ? As[e] : 0.0;
+#pragma unroll
+    for (int r = 0; r < R; ++r) acc[r].mac(a, sa, X, r, j);
   }
 }
 
+// the S partial sums of every (r, o) in segment order; red = [S][R][n_out]
 template <typename T, int R>
-__global__ void __launch_bounds__(256) k_es_project(int nocc, const int64_t* __restrict__ occ_start,
-                                                    const int64_t* __restrict__ P_off,
-                                                    const T* __restrict__ P, const T* __restrict__ u, int64_t N,
-                                                    T* __restrict__ sigma, int n_es) {
-  es_project_body<T, R>(blockIdx.x, blockIdx.y * 8 + (threadIdx.x >> 5), nocc, occ_start, P_off, P, u, N, sigma,
-                        n_es);
+__device__ __forceinline__ void segment_sums_out(const CAcc<T> (&acc)[R], unsigned char* raw, int n_out, int o, int sg,
+                                                 int S, T* __restrict__ out, int64_t r_stride) {
+  T* red = reinterpret_cast<T*>(raw);
+  __syncthreads();                                    // the staged inputs are no longer read
+  if (sg < S) {
+#pragma unroll
+    for (int r = 0; r < R; ++r) red[(sg * R + r) * n_out + o] = acc[r].value();
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < R * n_out; e += blockDim.x) {
+    const int r = e / n_out, oo = e - r * n_out;
+    T v = red[r * n_out + oo];
+    for (int g = 1; g < S; ++g) v = cadd(v, red[(g * R + r) * n_out + oo]);
+    out[int64_t(r) * r_stride + oo] = v;
+  }
+}
+
+// bytes of staged inputs per chunk of the projection (the cell's nodes): a
+// whole piece of kProjPiece nodes for up to 4 complex128 or 16 complex64 RHS
+constexpr int kProjStage = 32768;
+static_assert(kProjPiece <= (kProjStage / (kMaxRhs64 * 24) & ~1) && kProjPiece <= kProjStage / (kMaxRhs32 * 8),
+              "a projection piece fits one staging chunk");
+
+// shared memory of a 256-thread contraction block: the staged inputs, then the
+// S x R x n_out <= 256 R partial sums in the same space
+template <typename T>
+size_t contraction_smem(int R, size_t stage_bytes) {
+  const size_t red = size_t(256) * R * sizeof(T);
+  return red > stage_bytes ? red : stage_bytes;
+}
+
+// ------------------------------------------------------------ ES projection
+// sigma_c = P_c u_c (P_c: n_es x nc, stored [nc][n_es], Ps = Re + Im of P_c for
+// complex128).  The body sums the nodes [jb, je) of cell k into out[r * r_stride
+// + i]; the nodes are staged in chunks of CJ (the inputs of thread segment s stay
+// j - jb = s mod S across chunks).
+template <typename T, int R>
+__device__ __forceinline__ void es_project_body(int k, int jb, int je, const int64_t* __restrict__ occ_start,
+                                                const int64_t* __restrict__ P_off, const T* __restrict__ P,
+                                                const double* __restrict__ Ps, const T* __restrict__ u, int64_t N,
+                                                T* __restrict__ out, int64_t r_stride, int n_es) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int CJ = kProjStage / (R * Staged<T>::kBytes) & ~1;
+  const int64_t s0 = occ_start[k] + jb;
+  const int nc = je - jb;
+  const int64_t pk = P_off[k] + int64_t(jb) * n_es;
+  const T* Pk = P + pk;
+  const double* Psk = sizeof(T) == 16 ? Ps + pk : nullptr;   // null for complex64
+  const int S = blockDim.x / n_es, t = threadIdx.x, o = t % n_es, sg = t / n_es;
+  const Staged<T> X = staged_at<T>(smem_raw, CJ, R);
+  CAcc<T> acc[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) acc[r].zero();
+  for (int j0 = 0; j0 < nc; j0 += CJ) {
+    const int cl = min(CJ, nc - j0);
+    __syncthreads();
+    for (int e = t; e < R * cl; e += blockDim.x) {
+      const int r = e / cl, j = e - r * cl;
+      X.put(r, j, u[int64_t(r) * N + s0 + j0 + j]);
+    }
+    __syncthreads();
+    if (sg < S) contract_segment<T, R>(Pk + int64_t(j0) * n_es, sa_base(Psk, int64_t(j0) * n_es), n_es, o,
+                                       (sg - j0 % S + S) % S, cl, S, X, acc);
+  }
+  segment_sums_out<T, R>(acc, smem_raw, n_es, o, sg, S, out, r_stride);
+}
+
+// One block per piece (cell k, nodes [jb, je), piece p of np), pieces of at most
+// kProjPiece nodes, the largest first.  A cell of one piece writes sigma
+// directly; otherwise each piece writes its partial sums to its slot, and the
+// last piece of the cell to finish (counted on count[k]) adds the slots in piece
+// order and resets the count: the result does not depend on which piece ends
+// last, nor on R.
+template <typename T, int R>
+__device__ __forceinline__ void es_project_piece(const int4 pc, const int* __restrict__ piece_off, int nocc,
+                                                 const int64_t* __restrict__ occ_start,
+                                                 const int64_t* __restrict__ P_off, const T* __restrict__ P,
+                                                 const double* __restrict__ Ps, const T* __restrict__ u, int64_t N,
+                                                 T* __restrict__ sigma, T* __restrict__ part, int* __restrict__ count,
+                                                 int n_es) {
+  const int k = pc.x, p = pc.w >> 16, np = pc.w & 0xffff;
+  if (np == 1) {
+    es_project_body<T, R>(k, pc.y, pc.z, occ_start, P_off, P, Ps, u, N, sigma + int64_t(k) * n_es,
+                          int64_t(nocc) * n_es, n_es);
+    return;
+  }
+  T* slots = part + int64_t(piece_off[k]) * R * n_es;          // [piece][r][i]
+  es_project_body<T, R>(k, pc.y, pc.z, occ_start, P_off, P, Ps, u, N, slots + int64_t(p) * R * n_es, n_es, n_es);
+  __shared__ int last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(count + k, 1) == np - 1;
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  for (int e = threadIdx.x; e < R * n_es; e += blockDim.x) {
+    T v = __ldcg(slots + e);
+    for (int q = 1; q < np; ++q) v = cadd(v, __ldcg(slots + int64_t(q) * R * n_es + e));
+    const int r = e / n_es, i = e - r * n_es;
+    sigma[(int64_t(r) * nocc + k) * n_es + i] = v;
+  }
+  if (threadIdx.x == 0) count[k] = 0;
+}
+
+template <typename T, int R>
+__global__ void __launch_bounds__(256) k_es_project(const int4* __restrict__ pieces, const int* __restrict__ piece_off,
+                                                    int nocc, const int64_t* __restrict__ occ_start,
+                                                    const int64_t* __restrict__ P_off, const T* __restrict__ P,
+                                                    const double* __restrict__ Ps, const T* __restrict__ u, int64_t N,
+                                                    T* __restrict__ sigma, T* __restrict__ part,
+                                                    int* __restrict__ count, int n_es) {
+  es_project_piece<T, R>(pieces[blockIdx.x], piece_off, nocc, occ_start, P_off, P, Ps, u, N, sigma, part, count,
+                         n_es);
 }
 
 // ------------------------------------------------------------ lattice sources
@@ -418,27 +591,27 @@ __global__ void __launch_bounds__(256) k_spectral(int64_t n, T* __restrict__ Sm,
 // gamma_c = B^+ V_c - sum_o (B^+ T_o) sigma_{c+o} as one contraction per cell
 //   gamma_c (nfb2 x R) = LA (nfb2 x K) X_c (K x R),  K = n_loc + 9 n_es,
 // where X_c stacks the cell's (Ne+1)^2 lattice values and the strengths of its
-// 3 x 3 neighbours (zero for empty or missing neighbours).  One block per
-// occupied cell and all R right-hand sides: X_c is gathered into shared memory
-// once ([r][k], conflict-free), then one warp per row n of LA: lanes stride k
-// (coalesced reads of the row, each serving all R), one warp reduction per
-// RHS.  Every (cell, RHS) is summed the same way whatever R.
+// 3 x 3 neighbours (zero for empty or missing neighbours).  LA is stored
+// transposed ([K][nfb2], LAs = Re + Im for complex128) and shared by every cell.
+// One block per occupied cell and all R right-hand sides: X_c is staged once,
+// then the per-cell contraction above (thread per output row and segment).
 template <typename T, int R>
 __device__ __forceinline__ void local_coeffs_body(int k, int nocc, const int* __restrict__ occ_cells,
                                                   const int* __restrict__ occ_of_cell, int L, int Ne, int M,
                                                   const T* __restrict__ V_all, const T* __restrict__ LA,
-                                                  const T* __restrict__ sigma_all, int n_es, int nfb2,
-                                                  T* __restrict__ gamma_all, int64_t stride) {
+                                                  const double* __restrict__ LAs, const T* __restrict__ sigma_all,
+                                                  int n_es, int nfb2, T* __restrict__ gamma_all, int64_t stride) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* X = reinterpret_cast<T*>(smem_raw);           // [R][K]
   const int n_loc = (Ne + 1) * (Ne + 1);
   const int n_nb = 9 * n_es;
   const int K = n_loc + n_nb;
+  const int ld = (K + 1) & ~1;
+  const Staged<T> X = staged_at<T>(smem_raw, ld, R);
   const int c = occ_cells[k], ci = c % L, cj = c / L;
   for (int e = threadIdx.x; e < R * n_loc; e += blockDim.x) {
     const int r = e / n_loc, p = e - r * n_loc;
     const int a = p / (Ne + 1), b = p - a * (Ne + 1);
-    X[r * K + p] = V_all[int64_t(r) * stride + int64_t(ci * Ne + a) * M + cj * Ne + b];
+    X.put(r, p, V_all[int64_t(r) * stride + int64_t(ci * Ne + a) * M + cj * Ne + b]);
   }
   for (int e = threadIdx.x; e < R * n_nb; e += blockDim.x) {
     const int r = e / n_nb, q = e - r * n_nb;
@@ -449,36 +622,30 @@ __device__ __forceinline__ void local_coeffs_body(int k, int nocc, const int* __
       const int occ = occ_of_cell[nj * L + ni];
       if (occ >= 0) v = sigma_all[(int64_t(r) * nocc + occ) * n_es + l];
     }
-    X[r * K + n_loc + q] = v;
+    X.put(r, n_loc + q, v);
   }
   __syncthreads();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int n = warp; n < nfb2; n += 8) {
-    const T* la = LA + int64_t(n) * K;
-    T acc[R];
+  const int S = blockDim.x / nfb2, t = threadIdx.x, o = t % nfb2, sg = t / nfb2;
+  CAcc<T> acc[R];
 #pragma unroll
-    for (int r = 0; r < R; ++r) acc[r] = czero(T{});
-#pragma unroll 4
-    for (int kk = lane; kk < K; kk += 32) {
-      const T w = la[kk];
-#pragma unroll
-      for (int r = 0; r < R; ++r) acc[r] = cfma(w, X[r * K + kk], acc[r]);
-    }
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-      const T v = warp_sum(acc[r]);
-      if (lane == 0) gamma_all[(int64_t(r) * nocc + k) * nfb2 + n] = v;
-    }
-  }
+  for (int r = 0; r < R; ++r) acc[r].zero();
+  if (sg < S) contract_segment<T, R>(LA, LAs, nfb2, o, sg, K, S, X, acc);
+  segment_sums_out<T, R>(acc, smem_raw, nfb2, o, sg, S, gamma_all + int64_t(k) * nfb2, int64_t(nocc) * nfb2);
+}
+
+// shared memory of the local-coefficient kernels (K = n_loc + 9 n_es inputs)
+template <typename T>
+size_t local_smem(int R, int K) {
+  return contraction_smem<T>(R, size_t(R) * ((K + 1) & ~1) * Staged<T>::kBytes);
 }
 
 template <typename T, int R>
 __global__ void __launch_bounds__(256) k_local_coeffs(int nocc, const int* __restrict__ occ_cells,
                                                       const int* __restrict__ occ_of_cell, int L, int Ne, int M,
                                                       const T* __restrict__ V_all, const T* __restrict__ LA,
-                                                      const T* __restrict__ sigma_all, int n_es, int nfb2,
-                                                      T* __restrict__ gamma_all, int64_t stride) {
-  local_coeffs_body<T, R>(blockIdx.x, nocc, occ_cells, occ_of_cell, L, Ne, M, V_all, LA, sigma_all, n_es, nfb2,
+                                                      const double* __restrict__ LAs, const T* __restrict__ sigma_all,
+                                                      int n_es, int nfb2, T* __restrict__ gamma_all, int64_t stride) {
+  local_coeffs_body<T, R>(blockIdx.x, nocc, occ_cells, occ_of_cell, L, Ne, M, V_all, LA, LAs, sigma_all, n_es, nfb2,
                           gamma_all, stride);
 }
 
@@ -500,24 +667,44 @@ __global__ void __launch_bounds__(256) k_local_coeffs(int nocc, const int* __res
 // single-RHS results bit for bit.
 constexpr int kNearSmem = 32768;   // bytes of staged input values per chunk
 
-// acc[i][r] += sum over the chunk's columns t of W[row_i][c0 + t] us[r][t] for
-// the first NR rows of the warp
-template <typename T, int R, int NRW, int NR>
-__device__ __forceinline__ void near_chunk(const T* __restrict__ wk, const int* rows, int nblk, int c0, int cl,
-                                           const T* us, int CH, int lane, T (&acc)[NRW][R]) {
-  const T* w[NR];
+// complex128: a complex product with three real multiplications (Gauss's
+// form).  Weight w = a + ib comes with s = a + b (Ws), the staged value x = c + id
+// as c and (c + d, d - c).  P += s c, Q += b (c + d), S += a (d - c); then
+// Re(w x) = P - Q and Im(w x) = P + S.  Three FP64 FMAs per product instead of
+// four: the kernel is bound by the FP64 pipe, not by the extra 8 bytes read.
+// Sums run over the chunk's columns t of W[row_i][c0 + t] x_r[t] for the first
+// NR rows of the warp.
+template <int R, int NRW, int NR>
+__device__ __forceinline__ void near_chunk_gauss(const double2* __restrict__ wk, const double* __restrict__ wsk,
+                                                 const int* rows, int nblk, int c0, int cl,
+                                                 const double* usc, const double2* usef, int CH, int lane,
+                                                 double (&P)[NRW][R], double (&Q)[NRW][R], double (&S)[NRW][R]) {
+  const double2* w[NR];
+  const double* ws[NR];
 #pragma unroll
-  for (int i = 0; i < NR; ++i) w[i] = wk + int64_t(rows[i]) * nblk + c0;
+  for (int i = 0; i < NR; ++i) {
+    w[i] = wk + int64_t(rows[i]) * nblk + c0;
+    ws[i] = wsk + int64_t(rows[i]) * nblk + c0;
+  }
 #pragma unroll 2
   for (int t = lane; t < cl; t += 32) {
-    T a[NR];
+    double2 a[NR];
+    double sa[NR];
 #pragma unroll
-    for (int i = 0; i < NR; ++i) a[i] = w[i][t];
+    for (int i = 0; i < NR; ++i) {
+      a[i] = w[i][t];
+      sa[i] = ws[i][t];
+    }
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-      const T x = us[r * CH + t];
+      const double c = usc[r * CH + t];
+      const double2 ef = usef[r * CH + t];
 #pragma unroll
-      for (int i = 0; i < NR; ++i) acc[i][r] = cfma(a[i], x, acc[i][r]);
+      for (int i = 0; i < NR; ++i) {
+        P[i][r] = fma(sa[i], c, P[i][r]);
+        Q[i][r] = fma(a[i].y, ef.x, Q[i][r]);
+        S[i][r] = fma(a[i].x, ef.y, S[i][r]);
+      }
     }
   }
 }
@@ -552,15 +739,28 @@ __device__ __forceinline__ void near_chunk_pairs(const float2* __restrict__ wk, 
 template <typename T, int R, int NRW>
 __device__ __forceinline__ void near_eval_body(const int2 item, const int64_t* __restrict__ occ_start,
                                                const int64_t* __restrict__ blk_off, const int* __restrict__ blk_seg,
-                                               const T* __restrict__ Wb, const int64_t* __restrict__ rem_row,
+                                               const T* __restrict__ Wb, const double* __restrict__ Ws,
+                                               const int64_t* __restrict__ rem_row,
                                                const int* __restrict__ rem_col, const T* __restrict__ rem_val,
                                                const T* __restrict__ u, int64_t N, const T* __restrict__ Phi,
                                                const T* __restrict__ gamma, int nocc, int nfb2,
                                                typename RealOf<T>::R kappa2, T* __restrict__ out) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* us = reinterpret_cast<T*>(smem_raw);               // [rhs][column]
-  constexpr int CH = kNearSmem / int(R * sizeof(T));    // columns per chunk (a multiple of 64)
-  static_assert(CH % 64 == 0, "chunks must start at multiples of 64 columns");
+  constexpr bool kC128 = sizeof(T) == 16;
+  // columns per chunk (a multiple of 64); complex128 stages 24 bytes per value
+  constexpr int CH = kC128 ? kNearSmem / (R * 24) / 64 * 64 : kNearSmem / int(R * sizeof(T));
+  static_assert(CH % 64 == 0 && CH > 0, "chunks must start at multiples of 64 columns");
+  T* us = reinterpret_cast<T*>(smem_raw);               // complex64: [rhs][column]
+  double* usc = reinterpret_cast<double*>(smem_raw);    // complex128: c = Re x, [rhs][column]
+  double2* usef = reinterpret_cast<double2*>(smem_raw + size_t(R) * CH * sizeof(double));   // (c + d, d - c)
+  auto put = [&](int r, int col, T v) {
+    if constexpr (kC128) {
+      usc[r * CH + col] = v.x;
+      usef[r * CH + col] = make_double2(v.x + v.y, v.y - v.x);
+    } else {
+      us[r * CH + col] = v;
+    }
+  };
   const int k = item.x;
   const int* sg = blk_seg + 6 * k;
   const int l0 = sg[1], l1 = sg[3], l2 = sg[5];
@@ -583,6 +783,12 @@ __device__ __forceinline__ void near_eval_body(const int2 item, const int64_t* _
   for (int i = 0; i < NRW; ++i)
 #pragma unroll
     for (int r = 0; r < R; ++r) acc[i][r] = czero(T{});
+  constexpr int GN = kC128 ? NRW : 1, GR = kC128 ? R : 1;    // three-multiplication sums (complex128)
+  double gP[GN][GR], gQ[GN][GR], gS[GN][GR];
+#pragma unroll
+  for (int i = 0; i < GN; ++i)
+#pragma unroll
+    for (int r = 0; r < GR; ++r) gP[i][r] = gQ[i][r] = gS[i][r] = 0.0;
   for (int c0 = 0; c0 < nblk; c0 += CH) {
     const int cl = min(CH, nblk - c0);
     __syncthreads();
@@ -593,7 +799,7 @@ __device__ __forceinline__ void near_eval_body(const int2 item, const int64_t* _
         if (cc < p0) { if (cc < l0) v = u[sg[0] + cc]; }
         else if (cc < p0 + p1) { const int o = cc - p0; if (o < l1) v = u[sg[2] + o]; }
         else { const int o = cc - p0 - p1; if (o < l2) v = u[sg[4] + o]; }
-        us[col] = v;
+        put(0, col, v);
       }
     } else {
       // us[r * CH + col]: one contiguous run per RHS (conflict-free reads)
@@ -606,20 +812,27 @@ __device__ __forceinline__ void near_eval_body(const int2 item, const int64_t* _
           if (cc < p0) { if (cc < l0) v = ur[sg[0] + cc]; }
           else if (cc < p0 + p1) { const int o = cc - p0; if (o < l1) v = ur[sg[2] + o]; }
           else { const int o = cc - p0 - p1; if (o < l2) v = ur[sg[4] + o]; }
-          us[r * CH + col] = v;
+          put(r, col, v);
         }
       }
     }
     __syncthreads();
-    if constexpr (sizeof(T) == 16) {
+    if constexpr (kC128) {
       // FP64 is bound by the FP64 pipe: a warp skips its rows past the end of the cell
       static_assert(NRW == 2, "the FP64 variant takes two rows per warp");
-      if (valid[1]) near_chunk<T, R, NRW, 2>(wk, rows, nblk, c0, cl, us, CH, lane, acc);
-      else if (valid[0]) near_chunk<T, R, NRW, 1>(wk, rows, nblk, c0, cl, us, CH, lane, acc);
+      const double* wsk = Ws + blk_off[k];
+      if (valid[1]) near_chunk_gauss<R, NRW, 2>(wk, wsk, rows, nblk, c0, cl, usc, usef, CH, lane, gP, gQ, gS);
+      else if (valid[0]) near_chunk_gauss<R, NRW, 1>(wk, wsk, rows, nblk, c0, cl, usc, usef, CH, lane, gP, gQ, gS);
     } else {
       // complex64 is bound by HBM: a row past the end re-reads cached weights
       near_chunk_pairs<R, NRW>(wk, rows, nblk, c0, cl, us, CH, lane, acc);
     }
+  }
+  if constexpr (kC128) {
+#pragma unroll
+    for (int i = 0; i < NRW; ++i)
+#pragma unroll
+      for (int r = 0; r < R; ++r) acc[i][r] = mk(gP[i][r] - gQ[i][r], gP[i][r] + gS[i][r]);
   }
 #pragma unroll
   for (int i = 0; i < NRW; ++i) {
@@ -637,12 +850,39 @@ __device__ __forceinline__ void near_eval_body(const int2 item, const int64_t* _
 #pragma unroll
       for (int r = 0; r < R; ++r) acc[i][r] = cfma(p, gamma[(int64_t(r) * nocc + k) * nfb2 + n], acc[i][r]);
     }
+    if constexpr (!kC128) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const T v = warp_sum(acc[i][r]);
+        if (lane == 0) {
+          const T uq = u[r * N + q];
+          out[r * N + q] = mk(uq.x + kappa2 * v.x, uq.y + kappa2 * v.y);
+        }
+      }
+    }
+  }
+  if constexpr (kC128) {
+    // One transposed warp reduction per RHS over the four values (Re, Im of the
+    // two rows): exchange halves across lanes 16 apart, then one value across
+    // lanes 8 apart, then butterflies; 6 FP64 adds per lane instead of 20.
+    // Lane 8 j ends up with the whole sum of value j.
+    const bool hi16 = lane & 16, hi8 = lane & 8;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-      const T v = warp_sum(acc[i][r]);
-      if (lane == 0) {
-        const T uq = u[r * N + q];
-        out[r * N + q] = mk(uq.x + kappa2 * v.x, uq.y + kappa2 * v.y);
+      double a = hi16 ? acc[1][r].x : acc[0][r].x, b = hi16 ? acc[1][r].y : acc[0][r].y;
+      const double c = hi16 ? acc[0][r].x : acc[1][r].x, d = hi16 ? acc[0][r].y : acc[1][r].y;
+      a += __shfl_xor_sync(0xffffffffu, c, 16);
+      b += __shfl_xor_sync(0xffffffffu, d, 16);
+      double x = hi8 ? b : a;
+      x += __shfl_xor_sync(0xffffffffu, hi8 ? a : b, 8);
+      x += __shfl_xor_sync(0xffffffffu, x, 4);
+      x += __shfl_xor_sync(0xffffffffu, x, 2);
+      x += __shfl_xor_sync(0xffffffffu, x, 1);
+      const int comp = (lane >> 3) & 1;
+      if ((lane & 7) == 0 && (hi16 ? valid[1] : valid[0])) {
+        const int64_t q = r0 + (hi16 ? rows[1] : rows[0]);
+        const double uq = reinterpret_cast<const double*>(u + r * N + q)[comp];
+        reinterpret_cast<double*>(out + r * N + q)[comp] = uq + kappa2 * x;
       }
     }
   }
@@ -650,11 +890,12 @@ __device__ __forceinline__ void near_eval_body(const int2 item, const int64_t* _
 
 #define LS_NEAR_ARGS                                                                                          \
   const int2 *__restrict__ items, const int64_t *__restrict__ occ_start, const int64_t *__restrict__ blk_off,     \
-      const int *__restrict__ blk_seg, const T *__restrict__ Wb, const int64_t *__restrict__ rem_row,             \
+      const int *__restrict__ blk_seg, const T *__restrict__ Wb, const double *__restrict__ Ws,                   \
+      const int64_t *__restrict__ rem_row,                                                                        \
       const int *__restrict__ rem_col, const T *__restrict__ rem_val, const T *__restrict__ u, int64_t N,         \
       const T *__restrict__ Phi, const T *__restrict__ gamma, int nocc, int nfb2,                                 \
       typename RealOf<T>::R kappa2, T *__restrict__ out
-#define LS_NEAR_PASS items[blockIdx.x], occ_start, blk_off, blk_seg, Wb, rem_row, rem_col, rem_val, u, N, Phi, gamma, nocc, nfb2, \
+#define LS_NEAR_PASS items[blockIdx.x], occ_start, blk_off, blk_seg, Wb, Ws, rem_row, rem_col, rem_val, u, N, Phi, gamma, nocc, nfb2, \
                      kappa2, out
 // two rows per warp, 16-row items: registers left to the compiler
 template <typename T, int R>
@@ -677,21 +918,22 @@ constexpr int near_rows_per_warp() { return sizeof(T) == 8 && R >= 2 ? 4 : 2; }
 template <typename T, int R>
 cudaError_t apply_r(const ApplyData<T>& d, const T* u, T* out, cudaStream_t st, cudaEvent_t* ev) {
   if (ev) cudaEventRecord(ev[0], st);
-  k_es_project<T, R><<<dim3(d.nocc, (d.n_es + 7) / 8), 256, 0, st>>>(d.nocc, d.occ_start, d.P_off, d.P, u, d.N,
-                                                                     d.sigma, d.n_es);
+  k_es_project<T, R><<<d.n_pieces, 256, contraction_smem<T>(R, kProjStage), st>>>(
+      d.pieces, d.piece_off, d.nocc, d.occ_start, d.P_off, d.P, d.Ps, u, d.N, d.sigma, d.proj_part, d.proj_count,
+      d.n_es);
   if (ev) cudaEventRecord(ev[1], st);
   if (ev) cudaEventRecord(ev[2], st);        // the lattice fill is fused into k_src_rows
   cudaError_t e = lattice_conv(d, R, st);
   if (e != cudaSuccess) return e;
   if (ev) cudaEventRecord(ev[3], st);
-  const size_t sm_local = size_t(R) * (d.n_loc + 9 * d.n_es) * sizeof(T);
+  const size_t sm_local = local_smem<T>(R, d.n_loc + 9 * d.n_es);
   static unsigned long long local_attr = 0;     // X_c above 48 KB (large N_eq with many RHS)
   if (first_on_device(local_attr)) {
     cudaFuncSetAttribute(k_local_coeffs<T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
   }
   if (sm_local > 160 * 1024) return cudaErrorInvalidValue;
   k_local_coeffs<T, R><<<d.nocc, 256, sm_local, st>>>(d.nocc, d.occ_cells, d.occ_of_cell, d.L, d.Ne, d.M, d.Sd,
-                                                       d.LA, d.sigma, d.n_es, d.nfb2, d.gamma,
+                                                       d.LA, d.LAs, d.sigma, d.n_es, d.nfb2, d.gamma,
                                                        d.lattice_rows() * d.M);
   if (ev) cudaEventRecord(ev[4], st);
   if constexpr (sizeof(T) == 8 && R >= 8) {
@@ -699,25 +941,27 @@ cudaError_t apply_r(const ApplyData<T>& d, const T* u, T* out, cudaStream_t st, 
     if (e2 != cudaSuccess) return e2;
   } else if constexpr (near_rows_per_warp<T, R>() == 4)
     k_near_eval4<T, R><<<d.n_items32, 256, kNearSmem, st>>>(d.items32, d.occ_start, d.blk_off, d.blk_seg, d.Wb,
-                                                            d.rem_row, d.rem_col, d.rem_val, u, d.N, d.Phi,
+                                                            d.Ws, d.rem_row, d.rem_col, d.rem_val, u, d.N, d.Phi,
                                                             d.gamma, d.nocc, d.nfb2,
                                                             typename RealOf<T>::R(d.kappa2), out);
   else
     k_near_eval<T, R><<<d.n_items, 256, kNearSmem, st>>>(d.items, d.occ_start, d.blk_off, d.blk_seg, d.Wb,
-                                                         d.rem_row, d.rem_col, d.rem_val, u, d.N, d.Phi, d.gamma,
+                                                         d.Ws, d.rem_row, d.rem_col, d.rem_val, u, d.N, d.Phi, d.gamma,
                                                          d.nocc, d.nfb2, typename RealOf<T>::R(d.kappa2), out);
   if (ev) cudaEventRecord(ev[5], st);
   return cudaGetLastError();
 }
 
 // ------------------------------------------------------------ multi-instance batch
+// work = (instance, projection piece of that instance): the same pieces as the
+// single-instance apply, so every instance sums as it does alone
 template <typename T>
-__global__ void __launch_bounds__(256) k_es_project_multi(const int2* __restrict__ cells,
+__global__ void __launch_bounds__(256) k_es_project_multi(const int2* __restrict__ work,
                                                           const InstData<T>* __restrict__ I, const T* __restrict__ u) {
-  const int2 c = cells[blockIdx.x];
-  const ApplyData<T>& d = I[c.x].d;
-  es_project_body<T, 1>(c.y, blockIdx.y * 8 + (threadIdx.x >> 5), d.nocc, d.occ_start, d.P_off, d.P,
-                        u + I[c.x].off, d.N, d.sigma, d.n_es);
+  const int2 w = work[blockIdx.x];
+  const ApplyData<T>& d = I[w.x].d;
+  es_project_piece<T, 1>(d.pieces[w.y], d.piece_off, d.nocc, d.occ_start, d.P_off, d.P, d.Ps, u + I[w.x].off, d.N,
+                         d.sigma, d.proj_part, d.proj_count, d.n_es);
 }
 
 template <typename T>
@@ -725,8 +969,8 @@ __global__ void __launch_bounds__(256) k_local_coeffs_multi(const int2* __restri
                                                             const InstData<T>* __restrict__ I) {
   const int2 c = cells[blockIdx.x];
   const ApplyData<T>& d = I[c.x].d;
-  local_coeffs_body<T, 1>(c.y, d.nocc, d.occ_cells, d.occ_of_cell, d.L, d.Ne, d.M, d.Sd, d.LA, d.sigma, d.n_es,
-                          d.nfb2, d.gamma, d.lattice_rows() * d.M);
+  local_coeffs_body<T, 1>(c.y, d.nocc, d.occ_cells, d.occ_of_cell, d.L, d.Ne, d.M, d.Sd, d.LA, d.LAs, d.sigma,
+                          d.n_es, d.nfb2, d.gamma, d.lattice_rows() * d.M);
 }
 
 template <typename T>
@@ -736,22 +980,22 @@ __global__ void __launch_bounds__(256) k_near_eval_multi(const int4* __restrict_
   const int4 it = items[blockIdx.x];
   const ApplyData<T>& d = I[it.x].d;
   const int64_t off = I[it.x].off;
-  near_eval_body<T, 1, 2>(make_int2(it.y, it.z), d.occ_start, d.blk_off, d.blk_seg, d.Wb, d.rem_row, d.rem_col,
-                          d.rem_val, u + off, d.N, d.Phi, d.gamma, d.nocc, d.nfb2,
+  near_eval_body<T, 1, 2>(make_int2(it.y, it.z), d.occ_start, d.blk_off, d.blk_seg, d.Wb, d.Ws, d.rem_row,
+                          d.rem_col, d.rem_val, u + off, d.N, d.Phi, d.gamma, d.nocc, d.nfb2,
                           typename RealOf<T>::R(d.kappa2), out + off);
 }
 
 template <typename T>
 cudaError_t apply_multi(const InstData<T>* dev_inst, const InstData<T>* host_inst, const int* ids, int n_ids,
-                        const int2* cells, int n_cells, const int4* items, int n_items, int max_nes, int max_K,
-                        const T* u, T* out, cudaStream_t st) {
-  if (n_ids <= 0 || n_cells <= 0 || n_items <= 0) return cudaSuccess;
-  k_es_project_multi<T><<<dim3(n_cells, (max_nes + 7) / 8), 256, 0, st>>>(cells, dev_inst, u);
+                        const int2* pieces, int n_pieces, const int2* cells, int n_cells, const int4* items,
+                        int n_items, int max_K, const T* u, T* out, cudaStream_t st) {
+  if (n_ids <= 0 || n_pieces <= 0 || n_cells <= 0 || n_items <= 0) return cudaSuccess;
+  k_es_project_multi<T><<<n_pieces, 256, contraction_smem<T>(1, kProjStage), st>>>(pieces, dev_inst, u);
   for (int j = 0; j < n_ids; ++j) {
     cudaError_t e = lattice_conv(host_inst[ids[j]].d, 1, st);
     if (e != cudaSuccess) return e;
   }
-  const size_t sm_local = size_t(max_K) * sizeof(T);
+  const size_t sm_local = local_smem<T>(1, max_K);
   static unsigned long long attr = 0;
   if (first_on_device(attr)) {
     cudaFuncSetAttribute(k_local_coeffs_multi<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
@@ -763,11 +1007,11 @@ cudaError_t apply_multi(const InstData<T>* dev_inst, const InstData<T>* host_ins
 }
 
 template cudaError_t apply_multi<double2>(const InstData<double2>*, const InstData<double2>*, const int*, int,
-                                          const int2*, int, const int4*, int, int, int, const double2*, double2*,
-                                          cudaStream_t);
+                                          const int2*, int, const int2*, int, const int4*, int, int, const double2*,
+                                          double2*, cudaStream_t);
 template cudaError_t apply_multi<float2>(const InstData<float2>*, const InstData<float2>*, const int*, int,
-                                         const int2*, int, const int4*, int, int, int, const float2*, float2*,
-                                         cudaStream_t);
+                                         const int2*, int, const int2*, int, const int4*, int, int, const float2*,
+                                         float2*, cudaStream_t);
 
 template <typename T>
 cudaError_t apply_batch(const ApplyData<T>& d, const T* u, T* out, int nr, cudaStream_t st, cudaEvent_t* ev) {
@@ -1021,6 +1265,19 @@ __global__ void k_add(double2* __restrict__ x, const double2* __restrict__ e, in
 }
 cudaError_t add_inplace(double2* x, const double2* e, int64_t N, cudaStream_t st) {
   k_add<<<grid_for(N), 256, 0, st>>>(x, e, N);
+  return cudaGetLastError();
+}
+
+__global__ void k_weight_sums(const double2* __restrict__ w, double* __restrict__ sum, int64_t n) {
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+    const double2 v = w[i];
+    sum[i] = v.x + v.y;
+  }
+}
+
+cudaError_t weight_sums(const double2* w, double* s, int64_t n, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  k_weight_sums<<<grid_for(n), 256, 0, st>>>(w, s, n);
   return cudaGetLastError();
 }
 

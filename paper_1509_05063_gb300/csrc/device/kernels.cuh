@@ -26,8 +26,16 @@ struct ApplyData {
   const int* occ_of_cell = nullptr;     // L*L: occupied index or -1
   const int* occ_of_node = nullptr;     // N: occupied index of the node's cell
   const int64_t* P_off = nullptr;       // nocc + 1
-  const T* P = nullptr;                 // projections
-  const T* LA = nullptr;                // nfb2 x (n_loc + 9 n_es): [B^+ | -B^+ T_0 ... -B^+ T_8]
+  const T* P = nullptr;                 // projections, per cell [node][n_es]
+  const double* Ps = nullptr;           // complex128 only: Re + Im of every entry of P
+  const int4* pieces = nullptr;         // projection work: (cell, first node, end node, piece | pieces << 16)
+  int n_pieces = 0;                     // ... at most kProjPiece nodes each, largest first
+  const int* piece_off = nullptr;       // nocc: first partial-sum slot of a cell cut into several pieces
+  int* proj_count = nullptr;            // nocc: pieces of the cell finished in this apply (0 between applies)
+  T* proj_part = nullptr;               // partial sums: slots x max_rhs x n_es
+  const int4* cell_pieces = nullptr;    // nocc pieces of one whole cell each (no partial sums), largest first
+  const T* LA = nullptr;                // [B^+ | -B^+ T_0 ... -B^+ T_8] (nfb2 x (n_loc + 9 n_es)) stored transposed
+  const double* LAs = nullptr;          // complex128 only: Re + Im of every entry of LA
   const T* Phi = nullptr;               // N x nfb2
   const T* Gq = nullptr;                // (M/2+1)^2 quarter spectra, [l][k], scaled by 1/M^2
   const T* Dq = nullptr;
@@ -48,6 +56,7 @@ struct ApplyData {
   int* tc_err = nullptr;                // set by the tensor-core near field when a wait times out
   int tc_spin = 1 << 22;                // polls of each mbarrier wait before it gives up
   const T* Wb = nullptr;                // blocks, row-major per cell
+  const double* Ws = nullptr;           // complex128 only: Re + Im of every block weight (same layout as Wb)
   const int64_t* rem_row = nullptr;     // N + 1
   const int* rem_col = nullptr;
   const T* rem_val = nullptr;
@@ -79,6 +88,7 @@ template <typename T>
 cudaError_t apply_batch(const ApplyData<T>& d, const T* u, T* out, int nr, cudaStream_t st,
                         cudaEvent_t* ev = nullptr);
 constexpr int kMaxRhs64 = 4, kMaxRhs32 = 16;
+constexpr int kProjPiece = 128;    // nodes per projection block at most
 
 // Near field + evaluation + assembly of R complex64 right-hand sides (R = 8 or
 // 16) on the tensor cores (tcgen05, 3xTF32; device/near_tc.cu); same result as
@@ -98,14 +108,16 @@ struct InstData {
 // right-hand side each; u, out: the concatenated vectors; the other instances'
 // parts of out are left untouched).  The projection, the local expansion and
 // the near field each run as ONE launch walking work lists over those
-// instances -- cells = (instance, occupied cell), items = (instance, occupied
-// cell, first of 16 rows, unused) -- and the lattice convolution runs per
-// instance (its size differs).  dev_inst is a device copy of host_inst; ids is
-// a host array; max_nes / max_K are the largest n_es and n_loc + 9 n_es.
+// instances -- pieces = (instance, projection piece of the instance), cells =
+// (instance, occupied cell), items = (instance, occupied cell, first of 16
+// rows, unused) -- and the lattice convolution runs per instance (its size
+// differs).  dev_inst is a device copy of host_inst; ids is a host array; max_K
+// is the largest n_loc + 9 n_es.  No plan may appear twice among the instances
+// (they would share its work arrays).
 template <typename T>
 cudaError_t apply_multi(const InstData<T>* dev_inst, const InstData<T>* host_inst, const int* ids, int n_ids,
-                        const int2* cells, int n_cells, const int4* items, int n_items, int max_nes, int max_K,
-                        const T* u, T* out, cudaStream_t st);
+                        const int2* pieces, int n_pieces, const int2* cells, int n_cells, const int4* items,
+                        int n_items, int max_K, const T* u, T* out, cudaStream_t st);
 
 // 2-D FFT of an M x M array in place (rows then columns), forward or inverse
 // (unscaled).
@@ -130,6 +142,8 @@ cudaError_t sub(const double2* a, const double2* b, double2* out, int64_t N, cud
 cudaError_t to_c64(const double2* a, float2* b, int64_t N, cudaStream_t st);
 cudaError_t to_c128(const float2* a, double2* b, int64_t N, cudaStream_t st);
 cudaError_t add_inplace(double2* x, const double2* e, int64_t N, cudaStream_t st);
+// s[i] = Re w[i] + Im w[i] (the third weight of the three-multiplication complex product)
+cudaError_t weight_sums(const double2* w, double* s, int64_t n, cudaStream_t st);
 
 cudaError_t farfield(int64_t N, const double* x, const double* y, const double* ffw,
                      const double2* u, int nrhs, const double* dirs, int ndir, double kappa,

@@ -66,6 +66,9 @@ def test_invalid_arguments_return_status(lib):
     hb = C.c_void_p()
     assert lib.ls_batch_create(None, 0, C.byref(hb)) == 1
     assert b"no plans" in lib.ls_batch_last_error(None)
+    same = (C.c_void_p * 2)(0x1000, 0x1000)       # rejected before either handle is used
+    assert lib.ls_batch_create(same, 2, C.byref(hb)) == 1
+    assert b"appears twice" in lib.ls_batch_last_error(None)
     assert lib.ls_batch_apply(None, None, None, 0, None) == 1
     assert lib.ls_batch_solve(None, None, None, 1e-10, 10, 10, 0, None, None, None) == 1
     assert lib.ls_batch_destroy(None) == 0
