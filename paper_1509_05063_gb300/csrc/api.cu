@@ -114,6 +114,20 @@ struct Krylov {
   }
 };
 
+// The work vectors of the pipelined GMRES in the arithmetic of T: complex128
+// uses the buffers as allocated; complex64 (the correction solves of mixed
+// precision) reuses the same storage at half the element size.
+template <typename T>
+struct KrylovView {
+  T *V, *w, *r, *apart;
+};
+template <typename T> KrylovView<T> krylov_view(Krylov& K);
+template <> KrylovView<double2> krylov_view<double2>(Krylov& K) { return {K.V, K.w, K.r, K.apart}; }
+template <> KrylovView<float2> krylov_view<float2>(Krylov& K) {
+  return {reinterpret_cast<float2*>(K.V), reinterpret_cast<float2*>(K.w), reinterpret_cast<float2*>(K.r),
+          reinterpret_cast<float2*>(K.apart)};
+}
+
 // CUDA graphs of a launch sequence keyed by (precision, batch, input, output):
 // the first call with a key launches directly, the second captures the
 // sequence on a private stream and launches the graph, later calls replay it.
@@ -867,7 +881,8 @@ ls_status ensure_krylov(DevOwner* plan, Krylov& K, int restart, const Layout& la
 }
 
 // nrm[r] = ||base_r|| for every RHS of the layout (one host synchronisation)
-cudaError_t layout_norms(Krylov& K, const Layout& lay, const double2* base, cudaStream_t st) {
+template <typename T>
+cudaError_t layout_norms(Krylov& K, const Layout& lay, const T* base, cudaStream_t st) {
   const int64_t nbmax = lsd::gram_blocks(K.max_len);
   for (int r = 0; r < lay.R; ++r) {
     cudaError_t e = lsd::norm2(base + lay.off[r], lay.len[r], K.dpartial + size_t(r) * nbmax, K.dnorm + r, st);
@@ -1030,16 +1045,17 @@ ls_status gmres_lockstep(DevOwner* plan, Krylov& K, const Layout& lay, Op op, co
 // discarded (their columns are never used).  Used for the complex64
 // correction solves of the mixed refinement, where the apply is short and a
 // host round trip per iteration would leave the GPU idle.
-template <typename Op>
-ls_status gmres_lockstep_async(DevOwner* plan, Krylov& K, const Layout& lay, Op op, const double2* B, double2* X,
+template <typename T, typename Op>
+ls_status gmres_lockstep_async(DevOwner* plan, Krylov& K, const Layout& lay, Op op, const T* B, T* X,
                                double tol, int max_iter, int restart, cudaStream_t st, int* iters, double* relres) {
   constexpr int kLag = 2;
   static_assert(kLag < Krylov::kEvents, "event ring");
   const int R = lay.R;
   const int64_t vs = lay.total;
-  double2* V = K.V;
-  double2* Wv = K.w;
-  double2* Rv = K.r;
+  const KrylovView<T> KV = krylov_view<T>(K);
+  T* V = KV.V;
+  T* Wv = KV.w;
+  T* Rv = KV.r;
   const int m = restart;
   const int nbmax = lsd::gram_blocks(K.max_len);
   const int hstride = m + 3;
@@ -1055,7 +1071,7 @@ ls_status gmres_lockstep_async(DevOwner* plan, Krylov& K, const Layout& lay, Op 
   for (int r = 0; r < R; ++r) {
     iters[r] = 0;
     relres[r] = 0;
-    if (bnorm[r] == 0.0) LS_CU(cudaMemsetAsync(X + O(r), 0, Ln(r) * sizeof(double2), st));
+    if (bnorm[r] == 0.0) LS_CU(cudaMemsetAsync(X + O(r), 0, Ln(r) * sizeof(T), st));
   }
   std::vector<std::vector<cd>> H(R, std::vector<cd>(size_t(m + 1) * m)), cs(R, std::vector<cd>(m)),
       sn(R, std::vector<cd>(m)), g(R, std::vector<cd>(m + 1));
@@ -1078,9 +1094,9 @@ ls_status gmres_lockstep_async(DevOwner* plan, Krylov& K, const Layout& lay, Op 
     if (total >= max_iter) return fail(plan, LS_ERR_NOCONV, "GMRES reached max_iter");
     std::vector<double> beta(nrm, nrm + R);
     for (int r = 0; r < R; ++r) {
-      double2* v0 = V + O(r);
+      T* v0 = V + O(r);
       if (done[r]) {
-        LS_CU(cudaMemsetAsync(v0, 0, Ln(r) * sizeof(double2), st));
+        LS_CU(cudaMemsetAsync(v0, 0, Ln(r) * sizeof(T), st));
       } else {
         LS_CU(lsd::scale_into(Rv + O(r), K.dnorm + r, v0, Ln(r), st));
         std::fill(H[r].begin(), H[r].end(), cd(0));
@@ -1104,7 +1120,7 @@ ls_status gmres_lockstep_async(DevOwner* plan, Krylov& K, const Layout& lay, Op 
           if (!queued_for[k][r]) continue;
           for (int pass = 0; pass < 2; ++pass) {
             LS_CU(lsd::gram(V + O(r), k + 1, vs, Wv + O(r), Ln(r), part_of(r), hslot(k, pass, r), st));
-            LS_CU(lsd::axpy_multi(V + O(r), k + 1, vs, hslot(k, pass, r), Wv + O(r), K.apart, Ln(r), st));
+            LS_CU(lsd::axpy_multi(V + O(r), k + 1, vs, hslot(k, pass, r), Wv + O(r), KV.apart, Ln(r), st));
           }
           LS_CU(lsd::norm2(Wv + O(r), Ln(r), dp_of(r), K.nk + size_t(k) * R + r, st));
           LS_CU(lsd::scale_into(Wv + O(r), K.nk + size_t(k) * R + r, V + (k + 1) * vs + O(r), Ln(r), st));
@@ -1227,13 +1243,20 @@ ls_status solve_lockstep(DevOwner* plan, Krylov& K, const Layout& lay, Op64 op64
     }
     S.refinements++;
     const double inner_tol = std::max(1e-5, 0.3 * tol / rel);
-    LS_CU(cudaMemsetAsync(Cor, 0, size_t(lay.total) * sizeof(double2), st));
-    const ls_status s = gmres_lockstep_async(plan, K, lay, op32, Res, Cor, inner_tol,
-                                             std::max(1, max_iter - inner_total), restart, st, it.data(), rr.data());
+    // the correction equation A e = r entirely in complex64 (apply, basis,
+    // Gram-Schmidt, restarts; partial sums and the Hessenberg in FP64)
+    float2* Res32 = K.c64a;
+    float2* Cor32 = K.c64b;
+    LS_CU(lsd::to_c64(Res, Res32, lay.total, st));
+    LS_CU(cudaMemsetAsync(Cor32, 0, size_t(lay.total) * sizeof(float2), st));
+    const ls_status s = gmres_lockstep_async<float2>(plan, K, lay, op32, Res32, Cor32, inner_tol,
+                                                     std::max(1, max_iter - inner_total), restart, st, it.data(),
+                                                     rr.data());
     int mx = 0;
     for (int r = 0; r < R; ++r) { S.iterations += it[r]; S.it_per[r] += it[r]; mx = std::max(mx, it[r]); }
     inner_total += mx;
     if (s != LS_OK && s != LS_ERR_NOCONV) return s;
+    LS_CU(lsd::to_c128(Cor32, Cor, lay.total, st));
     LS_CU(lsd::add_inplace(X, Cor, lay.total, st));
   }
 }
@@ -1356,16 +1379,15 @@ ls_status ls_solve(ls_plan plan, const void* uinc, void* u, int nrhs, double tol
       }
       return cudaSuccess;
     };
-    // complex64 apply of R contiguous complex128 vectors (cast in, batched apply, cast out)
-    auto op32 = [&](const double2* v, double2* Av, const char*) -> cudaError_t {
-      cudaError_t e = lsd::to_c64(v, plan->K.c64a, int64_t(R) * N, st);
+    // complex64 apply of R contiguous complex64 vectors (chunks of at most kMaxRhs32)
+    auto op32 = [&](const float2* v, float2* Av, const char*) -> cudaError_t {
+      cudaError_t e = cudaSuccess;
       for (int r = 0; r < R && e == cudaSuccess;) {
         int nr = lsd::kMaxRhs32;
         while (nr > R - r) nr /= 2;
-        e = run_apply(plan, LS_MIXED, plan->d32, plan->K.c64a + r * N, plan->K.c64b + r * N, nr, st);
+        e = run_apply(plan, LS_MIXED, plan->d32, v + r * N, Av + r * N, nr, st);
         r += nr;
       }
-      if (e == cudaSuccess) e = lsd::to_c128(plan->K.c64b, Av, int64_t(R) * N, st);
       return e;
     };
     SolveStats Sb;
@@ -1779,11 +1801,8 @@ ls_status ls_batch_solve(ls_batch b, const void* uinc, void* u, double tol, int 
   auto op64 = [&](const double2* v, double2* Av, const char* need) -> cudaError_t {
     return batch_apply_t(b, LS_FP64, b->d64, b->h64, v, Av, st, need);
   };
-  auto op32 = [&](const double2* v, double2* Av, const char* need) -> cudaError_t {
-    cudaError_t e = lsd::to_c64(v, b->K.c64a, lay.total, st);
-    if (e == cudaSuccess) e = batch_apply_t(b, LS_MIXED, b->d32, b->h32, b->K.c64a, b->K.c64b, st, need);
-    if (e == cudaSuccess) e = lsd::to_c128(b->K.c64b, Av, lay.total, st);
-    return e;
+  auto op32 = [&](const float2* v, float2* Av, const char* need) -> cudaError_t {
+    return batch_apply_t(b, LS_MIXED, b->d32, b->h32, v, Av, st, need);
   };
   SolveStats S;
   s = solve_lockstep(b, b->K, lay, op64, op32, prec, static_cast<const double2*>(uinc), static_cast<double2*>(u), tol,

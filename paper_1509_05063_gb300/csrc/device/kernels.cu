@@ -1074,25 +1074,26 @@ __device__ __forceinline__ double2 block_sum(double2 v, double2* red) {
 // h[j] = <V_j, w> for j < nv and h[nv].x = ||w||^2, in one pass over V: each
 // block owns a contiguous chunk of the index range (w chunk in shared memory),
 // each warp reduces whole vectors with shuffles only.
-__global__ void __launch_bounds__(kRedThreads) k_gram_partial(const double2* __restrict__ V, int nv,
-                                                              int64_t vstride, const double2* __restrict__ w,
+template <typename T>
+__global__ void __launch_bounds__(kRedThreads) k_gram_partial(const T* __restrict__ V, int nv,
+                                                              int64_t vstride, const T* __restrict__ w,
                                                               int64_t N, int64_t chunk,
                                                               double2* __restrict__ partial) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  double2* ws = reinterpret_cast<double2*>(smem_raw);
+  T* ws = reinterpret_cast<T*>(smem_raw);
   const int64_t i0 = int64_t(blockIdx.x) * chunk;
   const int n = int(i0 < N ? (N - i0 < chunk ? N - i0 : chunk) : 0);
   for (int i = threadIdx.x; i < n; i += blockDim.x) ws[i] = w[i0 + i];
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   for (int j = blockIdx.y * nw + warp; j <= nv && j < (blockIdx.y + 1) * nw; j += nw) {
-    double2 acc = make_double2(0, 0);
+    T acc = czero(T{});
     if (j < nv) {
-      const double2* vj = V + int64_t(j) * vstride + i0;
-      double2 a1 = make_double2(0, 0), a2 = make_double2(0, 0), a3 = make_double2(0, 0);
+      const T* vj = V + int64_t(j) * vstride + i0;
+      T a1 = czero(T{}), a2 = czero(T{}), a3 = czero(T{});
       int i = lane;
       for (; i + 96 < n; i += 128) {
-        const double2 v0 = vj[i], v1 = vj[i + 32], v2 = vj[i + 64], v3 = vj[i + 96];
+        const T v0 = vj[i], v1 = vj[i + 32], v2 = vj[i + 64], v3 = vj[i + 96];
         acc = cfma(cconj(v0), ws[i], acc);
         a1 = cfma(cconj(v1), ws[i + 32], a1);
         a2 = cfma(cconj(v2), ws[i + 64], a2);
@@ -1104,7 +1105,7 @@ __global__ void __launch_bounds__(kRedThreads) k_gram_partial(const double2* __r
       for (int i = lane; i < n; i += 32) acc.x = fma(ws[i].x, ws[i].x, fma(ws[i].y, ws[i].y, acc.x));
     }
     acc = warp_sum(acc);
-    if (lane == 0) partial[int64_t(blockIdx.x) * (nv + 1) + j] = acc;
+    if (lane == 0) partial[int64_t(blockIdx.x) * (nv + 1) + j] = make_double2(acc.x, acc.y);
   }
 }
 
@@ -1122,48 +1123,63 @@ static int64_t gram_chunk(int64_t N) {
   return (N + nb - 1) / nb;
 }
 
-cudaError_t gram(const double2* V, int nv, int64_t vstride, const double2* w, int64_t N, double2* partial,
-                 double2* h, cudaStream_t st) {
+template <typename T>
+cudaError_t gram_t(const T* V, int nv, int64_t vstride, const T* w, int64_t N, double2* partial, double2* h,
+                   cudaStream_t st) {
   const int nb = gram_blocks(N);
   const int64_t chunk = gram_chunk(N);
   static unsigned long long attr = 0;
   if (first_on_device(attr)) {
-    cudaFuncSetAttribute(k_gram_partial, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
+    cudaFuncSetAttribute(k_gram_partial<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
   }
   // blockIdx.y selects 8 of the nv + 1 dot products: enough warps to hide the
   // FP64 latency (the complex multiply-adds of this kernel run on GB300's
   // narrow FP64 pipe)
   const int ng = (nv + 1 + kRedThreads / 32 - 1) / (kRedThreads / 32);
-  k_gram_partial<<<dim3(nb, ng), kRedThreads, chunk * sizeof(double2), st>>>(V, nv, vstride, w, N, chunk, partial);
+  k_gram_partial<T><<<dim3(nb, ng), kRedThreads, chunk * sizeof(T), st>>>(V, nv, vstride, w, N, chunk, partial);
   k_gram_reduce<<<nv + 1, 32, 0, st>>>(partial, nb, nv + 1, h);
   return cudaGetLastError();
+}
+cudaError_t gram(const double2* V, int nv, int64_t vstride, const double2* w, int64_t N, double2* partial,
+                 double2* h, cudaStream_t st) {
+  return gram_t(V, nv, vstride, w, N, partial, h, st);
+}
+cudaError_t gram(const float2* V, int nv, int64_t vstride, const float2* w, int64_t N, double2* partial, double2* h,
+                 cudaStream_t st) {
+  return gram_t(V, nv, vstride, w, N, partial, h, st);
 }
 
 // w -= sum_j h_j V_j, the sum over j split into G groups (blockIdx.y) so that
 // G x N threads keep GB300's FP64 pipe and HBM busy; group sums go to
 // part[g][i] and k_axpy_finish adds them in a fixed order (deterministic).
-__global__ void __launch_bounds__(256) k_axpy_multi(const double2* __restrict__ V, int nv, int64_t vstride,
-                                                    const double2* __restrict__ h, double2* __restrict__ part,
-                                                    int64_t N) {
+// coefficient h (always complex128) in the arithmetic of T
+template <typename T> __device__ __forceinline__ T coef(double2 h);
+template <> __device__ __forceinline__ double2 coef<double2>(double2 h) { return h; }
+template <> __device__ __forceinline__ float2 coef<float2>(double2 h) { return make_float2(float(h.x), float(h.y)); }
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_axpy_multi(const T* __restrict__ V, int nv, int64_t vstride,
+                                                    const double2* __restrict__ h, T* __restrict__ part, int64_t N) {
   const int G = gridDim.y, g = blockIdx.y;
   const int j0 = (nv * g) / G, j1 = (nv * (g + 1)) / G;
   for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < N; i += int64_t(gridDim.x) * blockDim.x) {
-    double2 a0 = make_double2(0, 0), a1 = make_double2(0, 0);
+    T a0 = czero(T{}), a1 = czero(T{});
     int j = j0;
     for (; j + 1 < j1; j += 2) {
-      const double2 v0 = V[int64_t(j) * vstride + i], v1 = V[int64_t(j + 1) * vstride + i];
-      a0 = cfma(h[j], v0, a0);
-      a1 = cfma(h[j + 1], v1, a1);
+      const T v0 = V[int64_t(j) * vstride + i], v1 = V[int64_t(j + 1) * vstride + i];
+      a0 = cfma(coef<T>(h[j]), v0, a0);
+      a1 = cfma(coef<T>(h[j + 1]), v1, a1);
     }
-    if (j < j1) a0 = cfma(h[j], V[int64_t(j) * vstride + i], a0);
+    if (j < j1) a0 = cfma(coef<T>(h[j]), V[int64_t(j) * vstride + i], a0);
     part[int64_t(g) * N + i] = cadd(a0, a1);
   }
 }
 
-__global__ void __launch_bounds__(256) k_axpy_finish(const double2* __restrict__ part, int G, double2* __restrict__ w,
+template <typename T>
+__global__ void __launch_bounds__(256) k_axpy_finish(const T* __restrict__ part, int G, T* __restrict__ w,
                                                      int64_t N) {
   for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < N; i += int64_t(gridDim.x) * blockDim.x) {
-    double2 s = part[i];
+    T s = part[i];
     for (int g = 1; g < G; ++g) s = cadd(s, part[int64_t(g) * N + i]);
     w[i] = csub(w[i], s);
   }
@@ -1175,21 +1191,31 @@ static unsigned grid_for(int64_t N) {
   return unsigned(b < 1 ? 1 : b);
 }
 
-cudaError_t axpy_multi(const double2* V, int nv, int64_t vstride, const double2* h, double2* w, double2* part,
-                       int64_t N, cudaStream_t st) {
+template <typename T>
+cudaError_t axpy_multi_t(const T* V, int nv, int64_t vstride, const double2* h, T* w, T* part, int64_t N,
+                         cudaStream_t st) {
   const int G = nv >= 32 ? kAxpyGroups : (nv >= 8 ? 2 : 1);
-  k_axpy_multi<<<dim3(grid_for(N), G), 256, 0, st>>>(V, nv, vstride, h, part, N);
-  k_axpy_finish<<<grid_for(N), 256, 0, st>>>(part, G, w, N);
+  k_axpy_multi<T><<<dim3(grid_for(N), G), 256, 0, st>>>(V, nv, vstride, h, part, N);
+  k_axpy_finish<T><<<grid_for(N), 256, 0, st>>>(part, G, w, N);
   return cudaGetLastError();
 }
+cudaError_t axpy_multi(const double2* V, int nv, int64_t vstride, const double2* h, double2* w, double2* part,
+                       int64_t N, cudaStream_t st) {
+  return axpy_multi_t(V, nv, vstride, h, w, part, N, st);
+}
+cudaError_t axpy_multi(const float2* V, int nv, int64_t vstride, const double2* h, float2* w, float2* part,
+                       int64_t N, cudaStream_t st) {
+  return axpy_multi_t(V, nv, vstride, h, w, part, N, st);
+}
 
-__global__ void __launch_bounds__(kRedThreads) k_norm_partial(const double2* __restrict__ w, int64_t N,
+template <typename T>
+__global__ void __launch_bounds__(kRedThreads) k_norm_partial(const T* __restrict__ w, int64_t N,
                                                               double* __restrict__ partial) {
   __shared__ double2 red[32];
-  double2 acc = make_double2(0, 0);
+  T acc = czero(T{});
   for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < N; i += int64_t(gridDim.x) * blockDim.x)
     acc.x = fma(w[i].x, w[i].x, fma(w[i].y, w[i].y, acc.x));
-  const double2 s = block_sum(acc, red);
+  const double2 s = block_sum(make_double2(acc.x, 0.0), red);
   if (threadIdx.x == 0) partial[blockIdx.x] = s.x;
 }
 
@@ -1200,46 +1226,66 @@ __global__ void k_norm_reduce(const double* __restrict__ partial, int nb, double
   if (threadIdx.x == 0) out[0] = sqrt(s.x);
 }
 
-cudaError_t norm2(const double2* w, int64_t N, double* partial, double* out, cudaStream_t st) {
+template <typename T>
+cudaError_t norm2_t(const T* w, int64_t N, double* partial, double* out, cudaStream_t st) {
   const int nb = gram_blocks(N);
-  k_norm_partial<<<nb, kRedThreads, 0, st>>>(w, N, partial);
+  k_norm_partial<T><<<nb, kRedThreads, 0, st>>>(w, N, partial);
   k_norm_reduce<<<1, 32, 0, st>>>(partial, nb, out);
   return cudaGetLastError();
 }
+cudaError_t norm2(const double2* w, int64_t N, double* partial, double* out, cudaStream_t st) {
+  return norm2_t(w, N, partial, out, st);
+}
+cudaError_t norm2(const float2* w, int64_t N, double* partial, double* out, cudaStream_t st) {
+  return norm2_t(w, N, partial, out, st);
+}
 
-__global__ void k_scale_into(const double2* __restrict__ w, const double* __restrict__ nrm, double2* __restrict__ v,
-                             int64_t N) {
-  const double s = nrm[0] > 0 ? 1.0 / nrm[0] : 0.0;
+template <typename T>
+__global__ void k_scale_into(const T* __restrict__ w, const double* __restrict__ nrm, T* __restrict__ v, int64_t N) {
+  const typename RealOf<T>::R s(nrm[0] > 0 ? 1.0 / nrm[0] : 0.0);
   for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < N; i += int64_t(gridDim.x) * blockDim.x)
     v[i] = cscale(w[i], s);
 }
-
 cudaError_t scale_into(const double2* w, const double* nrm, double2* v, int64_t N, cudaStream_t st) {
-  k_scale_into<<<grid_for(N), 256, 0, st>>>(w, nrm, v, N);
+  k_scale_into<double2><<<grid_for(N), 256, 0, st>>>(w, nrm, v, N);
+  return cudaGetLastError();
+}
+cudaError_t scale_into(const float2* w, const double* nrm, float2* v, int64_t N, cudaStream_t st) {
+  k_scale_into<float2><<<grid_for(N), 256, 0, st>>>(w, nrm, v, N);
   return cudaGetLastError();
 }
 
-__global__ void k_combine(const double2* __restrict__ V, int k, int64_t vstride, const double2* __restrict__ y,
-                          double2* __restrict__ x, int64_t N) {
+template <typename T>
+__global__ void k_combine(const T* __restrict__ V, int k, int64_t vstride, const double2* __restrict__ y,
+                          T* __restrict__ x, int64_t N) {
   for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < N; i += int64_t(gridDim.x) * blockDim.x) {
-    double2 acc = x[i];
-    for (int j = 0; j < k; ++j) acc = cfma(y[j], V[int64_t(j) * vstride + i], acc);
+    T acc = x[i];
+    for (int j = 0; j < k; ++j) acc = cfma(coef<T>(y[j]), V[int64_t(j) * vstride + i], acc);
     x[i] = acc;
   }
 }
-
 cudaError_t combine(const double2* V, int k, int64_t vstride, const double2* y, double2* x, int64_t N,
                     cudaStream_t st) {
-  k_combine<<<grid_for(N), 256, 0, st>>>(V, k, vstride, y, x, N);
+  k_combine<double2><<<grid_for(N), 256, 0, st>>>(V, k, vstride, y, x, N);
+  return cudaGetLastError();
+}
+cudaError_t combine(const float2* V, int k, int64_t vstride, const double2* y, float2* x, int64_t N,
+                    cudaStream_t st) {
+  k_combine<float2><<<grid_for(N), 256, 0, st>>>(V, k, vstride, y, x, N);
   return cudaGetLastError();
 }
 
-__global__ void k_sub(const double2* __restrict__ a, const double2* __restrict__ b, double2* __restrict__ o, int64_t N) {
+template <typename T>
+__global__ void k_sub(const T* __restrict__ a, const T* __restrict__ b, T* __restrict__ o, int64_t N) {
   for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < N; i += int64_t(gridDim.x) * blockDim.x)
     o[i] = csub(a[i], b[i]);
 }
 cudaError_t sub(const double2* a, const double2* b, double2* out, int64_t N, cudaStream_t st) {
-  k_sub<<<grid_for(N), 256, 0, st>>>(a, b, out, N);
+  k_sub<double2><<<grid_for(N), 256, 0, st>>>(a, b, out, N);
+  return cudaGetLastError();
+}
+cudaError_t sub(const float2* a, const float2* b, float2* out, int64_t N, cudaStream_t st) {
+  k_sub<float2><<<grid_for(N), 256, 0, st>>>(a, b, out, N);
   return cudaGetLastError();
 }
 
