@@ -87,6 +87,8 @@ struct Krylov {
   int64_t total = 0, max_len = 0;
   double2 *V = nullptr, *w = nullptr, *r = nullptr, *e = nullptr, *cor = nullptr, *h = nullptr, *partial = nullptr;
   double2* apart = nullptr;     // kAxpyGroups x max_len partial sums of the Arnoldi update
+  double* vs = nullptr;         // FP64 solve: Re + Im of every basis entry (same layout as V)
+  double* h3 = nullptr;         // FP64 solve: coefficient triplets of the update, R x (restart + 3) x 3
   double* dnorm = nullptr;
   double* dpartial = nullptr;
   float2 *c64a = nullptr, *c64b = nullptr;
@@ -840,7 +842,8 @@ ls_status ensure_krylov(DevOwner* plan, Krylov& K, int restart, const Layout& la
                         static_cast<const void*>(K.partial), static_cast<const void*>(K.dnorm),
                         static_cast<const void*>(K.dpartial), static_cast<const void*>(K.c64a),
                         static_cast<const void*>(K.c64b), static_cast<const void*>(K.hk),
-                        static_cast<const void*>(K.nk)})
+                        static_cast<const void*>(K.nk), static_cast<const void*>(K.vs),
+                        static_cast<const void*>(K.h3)})
     plan->release(p);
   K.free_pinned();
   K = Krylov{};
@@ -850,6 +853,8 @@ ls_status ensure_krylov(DevOwner* plan, Krylov& K, int restart, const Layout& la
   K.e = plan->alloc<double2>(size_t(Tw), &st);
   K.cor = plan->alloc<double2>(size_t(Tw), &st);
   K.apart = plan->alloc<double2>(size_t(lsd::kAxpyGroups) * Lw, &st);
+  K.vs = plan->alloc<double>(size_t(restart + 1) * Tw, &st);
+  K.h3 = plan->alloc<double>(size_t(Rw) * (restart + 3) * 3, &st);
   K.h = plan->alloc<double2>(size_t(Rw) * (restart + 3), &st);
   K.partial = plan->alloc<double2>(size_t(Rw) * nb * (restart + 3), &st);
   K.dnorm = plan->alloc<double>(Rw, &st);
@@ -901,7 +906,8 @@ cudaError_t layout_norms(Krylov& K, const Layout& lay, const T* base, cudaStream
 // with one host synchronisation for all of them.  Classical Gram-Schmidt with
 // selective re-orthogonalisation (a second pass only when the first removed
 // more than 1 - 1/sqrt(2) of ||w||), Givens rotations on the host, true
-// residual checked at every restart.  Stops when every RHS has
+// residual checked at every restart.  The basis is stored with Re + Im of
+// every entry, so the Gram and update products take three FP64 FMAs each.  Stops when every RHS has
 // ||b - A x|| / ||b|| <= tol; iters[r] counts the iterations of RHS r.
 template <typename Op>
 ls_status gmres_lockstep(DevOwner* plan, Krylov& K, const Layout& lay, Op op, const double2* B, double2* X,
@@ -909,12 +915,14 @@ ls_status gmres_lockstep(DevOwner* plan, Krylov& K, const Layout& lay, Op op, co
   const int R = lay.R;
   const int64_t vs = lay.total;                      // stride between basis slots
   double2* V = K.V;
+  double* VS = K.vs;                                 // Re + Im of every basis entry
   double2* Wv = K.w;
   double2* Rv = K.r;
   const int m = restart;
   const int nbmax = lsd::gram_blocks(K.max_len);
   const int hstride = m + 3;
   auto h_of = [&](int r) { return K.h + size_t(r) * hstride; };
+  auto h3_of = [&](int r) { return K.h3 + size_t(r) * hstride * 3; };
   auto part_of = [&](int r) { return K.partial + size_t(r) * nbmax * hstride; };
   auto dn_of = [&](int r) { return K.dnorm + r; };
   auto dp_of = [&](int r) { return K.dpartial + size_t(r) * nbmax; };
@@ -952,8 +960,9 @@ ls_status gmres_lockstep(DevOwner* plan, Krylov& K, const Layout& lay, Op op, co
       double2* v0 = V + O(r);
       if (done[r]) {
         LS_CU(cudaMemsetAsync(v0, 0, Ln(r) * sizeof(double2), st));
+        LS_CU(cudaMemsetAsync(VS + O(r), 0, Ln(r) * sizeof(double), st));
       } else {
-        LS_CU(lsd::scale_into(Rv + O(r), dn_of(r), v0, Ln(r), st));
+        LS_CU(lsd::scale_into_sums(Rv + O(r), dn_of(r), v0, VS + O(r), Ln(r), st));
         std::fill(H[r].begin(), H[r].end(), cd(0));
         std::fill(g[r].begin(), g[r].end(), cd(0));
         g[r][0] = nrm[r];
@@ -970,8 +979,8 @@ ls_status gmres_lockstep(DevOwner* plan, Krylov& K, const Layout& lay, Op op, co
         for (int r = 0; r < R; ++r) {
           if (!again[r]) continue;
           any = true;
-          LS_CU(lsd::gram(V + O(r), k + 1, vs, Wv + O(r), Ln(r), part_of(r), h_of(r), st));
-          LS_CU(lsd::axpy_multi(V + O(r), k + 1, vs, h_of(r), Wv + O(r), K.apart, Ln(r), st));
+          LS_CU(lsd::gram3(V + O(r), VS + O(r), k + 1, vs, Wv + O(r), Ln(r), part_of(r), h_of(r), h3_of(r), st));
+          LS_CU(lsd::axpy3_multi(V + O(r), VS + O(r), k + 1, vs, h3_of(r), Wv + O(r), K.apart, Ln(r), st));
           LS_CU(lsd::norm2(Wv + O(r), Ln(r), dp_of(r), dn_of(r), st));
         }
         if (!any) break;
@@ -989,13 +998,15 @@ ls_status gmres_lockstep(DevOwner* plan, Krylov& K, const Layout& lay, Op op, co
       bool any_active = false;
       for (int r = 0; r < R; ++r) {
         double2* vn = V + (k + 1) * vs + O(r);
+        double* vsn = VS + (k + 1) * vs + O(r);
         if (!active[r]) {
           LS_CU(cudaMemsetAsync(vn, 0, Ln(r) * sizeof(double2), st));
+          LS_CU(cudaMemsetAsync(vsn, 0, Ln(r) * sizeof(double), st));
           continue;
         }
         std::vector<cd>& Hr = H[r];
         Hr[size_t(k + 1) * m + k] = hk1[r];
-        LS_CU(lsd::scale_into(Wv + O(r), dn_of(r), vn, Ln(r), st));
+        LS_CU(lsd::scale_into_sums(Wv + O(r), dn_of(r), vn, vsn, Ln(r), st));
         for (int j = 0; j < k; ++j) {
           const cd t = std::conj(cs[r][j]) * Hr[size_t(j) * m + k] + std::conj(sn[r][j]) * Hr[size_t(j + 1) * m + k];
           Hr[size_t(j + 1) * m + k] = -sn[r][j] * Hr[size_t(j) * m + k] + cs[r][j] * Hr[size_t(j + 1) * m + k];
@@ -1043,7 +1054,8 @@ ls_status gmres_lockstep(DevOwner* plan, Krylov& K, const Layout& lay, Op op, co
 // while the device works.  An RHS found converged stops taking part in later
 // queued applies (op's need flags); iterations queued past its convergence are
 // discarded (their columns are never used).  Used for the complex64
-// correction solves of the mixed refinement, where the apply is short and a
+// correction solves of the mixed refinement (T = float2: complex64 basis and
+// vectors, FP64 partial sums and Hessenberg), where the apply is short and a
 // host round trip per iteration would leave the GPU idle.
 template <typename T, typename Op>
 ls_status gmres_lockstep_async(DevOwner* plan, Krylov& K, const Layout& lay, Op op, const T* B, T* X,

@@ -1109,13 +1109,81 @@ __global__ void __launch_bounds__(kRedThreads) k_gram_partial(const T* __restric
   }
 }
 
-// one warp per dot product: lanes stride over the per-block partial sums
-__global__ void k_gram_reduce(const double2* __restrict__ partial, int nblk, int nv1, double2* __restrict__ h) {
+// Complex128 Gram coefficients against a basis stored with S_j = Re V_j + Im V_j:
+// conj(v) w = conj(conj(w) v), and conj(w) v takes three real multiplications
+// with the staged w-side values (c, c - d, -c - d) (w = c + i d, v = a + i b):
+// P += (a + b) c, Q += b (c - d), T += a (-c - d); Re = P - Q, Im = -(P + T).
+// Row nv is ||w||^2 = ((c - d)^2 + (c + d)^2) / 2.
+__global__ void __launch_bounds__(kRedThreads) k_gram3_partial(const double2* __restrict__ V,
+                                                               const double* __restrict__ S, int nv,
+                                                               int64_t vstride, const double2* __restrict__ w,
+                                                               int64_t N, int64_t chunk,
+                                                               double2* __restrict__ partial) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double2* wq = reinterpret_cast<double2*>(smem_raw);              // (c - d, -c - d)
+  double* wc = reinterpret_cast<double*>(smem_raw + chunk * sizeof(double2));   // c
+  const int64_t i0 = int64_t(blockIdx.x) * chunk;
+  const int n = int(i0 < N ? (N - i0 < chunk ? N - i0 : chunk) : 0);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const double2 v = w[i0 + i];
+    wc[i] = v.x;
+    wq[i] = make_double2(v.x - v.y, -v.x - v.y);
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int j = blockIdx.y * nw + warp; j <= nv && j < (blockIdx.y + 1) * nw; j += nw) {
+    double2 acc = make_double2(0, 0);
+    if (j < nv) {
+      const double2* vj = V + int64_t(j) * vstride + i0;
+      const double* sj = S + int64_t(j) * vstride + i0;
+      double P[4] = {0, 0, 0, 0}, Q[4] = {0, 0, 0, 0}, T[4] = {0, 0, 0, 0};
+      int i = lane;
+      for (; i + 96 < n; i += 128) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const double2 v = vj[i + 32 * u];
+          const double sv = sj[i + 32 * u];
+          const double2 q = wq[i + 32 * u];
+          P[u] = fma(sv, wc[i + 32 * u], P[u]);
+          Q[u] = fma(v.y, q.x, Q[u]);
+          T[u] = fma(v.x, q.y, T[u]);
+        }
+      }
+      for (; i < n; i += 32) {
+        const double2 v = vj[i];
+        const double2 q = wq[i];
+        P[0] = fma(sj[i], wc[i], P[0]);
+        Q[0] = fma(v.y, q.x, Q[0]);
+        T[0] = fma(v.x, q.y, T[0]);
+      }
+      const double p = (P[0] + P[1]) + (P[2] + P[3]), q = (Q[0] + Q[1]) + (Q[2] + Q[3]);
+      const double t = (T[0] + T[1]) + (T[2] + T[3]);
+      acc = make_double2(p - q, -(p + t));
+    } else {
+      for (int i = lane; i < n; i += 32) acc.x = fma(wq[i].x, wq[i].x, fma(wq[i].y, wq[i].y, acc.x));
+      acc.x *= 0.5;
+    }
+    acc = warp_sum(acc);
+    if (lane == 0) partial[int64_t(blockIdx.x) * (nv + 1) + j] = acc;
+  }
+}
+
+// one warp per dot product: lanes stride over the per-block partial sums; with
+// h3, also the triplet (Re h, Im h - Re h, Re h + Im h) of every coefficient
+__global__ void k_gram_reduce(const double2* __restrict__ partial, int nblk, int nv1, double2* __restrict__ h,
+                              double* __restrict__ h3 = nullptr) {
   const int j = blockIdx.x;
   double2 s = make_double2(0, 0);
   for (int b = threadIdx.x; b < nblk; b += 32) s = cadd(s, partial[int64_t(b) * nv1 + j]);
   s = warp_sum(s);
-  if (threadIdx.x == 0) h[j] = s;
+  if (threadIdx.x == 0) {
+    h[j] = s;
+    if (h3) {
+      h3[3 * j] = s.x;
+      h3[3 * j + 1] = s.y - s.x;
+      h3[3 * j + 2] = s.x + s.y;
+    }
+  }
 }
 
 static int64_t gram_chunk(int64_t N) {
@@ -1147,6 +1215,19 @@ cudaError_t gram(const double2* V, int nv, int64_t vstride, const double2* w, in
 cudaError_t gram(const float2* V, int nv, int64_t vstride, const float2* w, int64_t N, double2* partial, double2* h,
                  cudaStream_t st) {
   return gram_t(V, nv, vstride, w, N, partial, h, st);
+}
+cudaError_t gram3(const double2* V, const double* S, int nv, int64_t vstride, const double2* w, int64_t N,
+                  double2* partial, double2* h, double* h3, cudaStream_t st) {
+  const int nb = gram_blocks(N);
+  const int64_t chunk = gram_chunk(N);
+  static unsigned long long attr = 0;
+  if (first_on_device(attr)) {
+    cudaFuncSetAttribute(k_gram3_partial, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
+  }
+  const int ng = (nv + 1 + kRedThreads / 32 - 1) / (kRedThreads / 32);
+  k_gram3_partial<<<dim3(nb, ng), kRedThreads, chunk * 24, st>>>(V, S, nv, vstride, w, N, chunk, partial);
+  k_gram_reduce<<<nv + 1, 32, 0, st>>>(partial, nb, nv + 1, h, h3);
+  return cudaGetLastError();
 }
 
 // w -= sum_j h_j V_j, the sum over j split into G groups (blockIdx.y) so that
@@ -1208,6 +1289,46 @@ cudaError_t axpy_multi(const float2* V, int nv, int64_t vstride, const double2* 
   return axpy_multi_t(V, nv, vstride, h, w, part, N, st);
 }
 
+// w -= sum_j h_j V_j with the basis sums S_j and the coefficient triplets h3
+// (e, f - e, e + f) of h_j = e + i f: P += e S, Q += (e + f) Im V, T += (f - e) Re V;
+// h_j V_j summed = (P - Q) + i (P + T).  Groups as in k_axpy_multi.
+__global__ void __launch_bounds__(256) k_axpy3_multi(const double2* __restrict__ V, const double* __restrict__ S,
+                                                     int nv, int64_t vstride, const double* __restrict__ h3,
+                                                     double2* __restrict__ part, int64_t N) {
+  const int G = gridDim.y, g = blockIdx.y;
+  const int j0 = (nv * g) / G, j1 = (nv * (g + 1)) / G;
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < N; i += int64_t(gridDim.x) * blockDim.x) {
+    double P0 = 0, Q0 = 0, T0 = 0, P1 = 0, Q1 = 0, T1 = 0;
+    int j = j0;
+    for (; j + 1 < j1; j += 2) {
+      const double2 v0 = V[int64_t(j) * vstride + i], v1 = V[int64_t(j + 1) * vstride + i];
+      const double s0 = S[int64_t(j) * vstride + i], s1 = S[int64_t(j + 1) * vstride + i];
+      P0 = fma(h3[3 * j], s0, P0);
+      Q0 = fma(h3[3 * j + 2], v0.y, Q0);
+      T0 = fma(h3[3 * j + 1], v0.x, T0);
+      P1 = fma(h3[3 * j + 3], s1, P1);
+      Q1 = fma(h3[3 * j + 5], v1.y, Q1);
+      T1 = fma(h3[3 * j + 4], v1.x, T1);
+    }
+    if (j < j1) {
+      const double2 v0 = V[int64_t(j) * vstride + i];
+      P0 = fma(h3[3 * j], S[int64_t(j) * vstride + i], P0);
+      Q0 = fma(h3[3 * j + 2], v0.y, Q0);
+      T0 = fma(h3[3 * j + 1], v0.x, T0);
+    }
+    const double p = P0 + P1;
+    part[int64_t(g) * N + i] = make_double2(p - (Q0 + Q1), p + (T0 + T1));
+  }
+}
+
+cudaError_t axpy3_multi(const double2* V, const double* S, int nv, int64_t vstride, const double* h3, double2* w,
+                        double2* part, int64_t N, cudaStream_t st) {
+  const int G = nv >= 32 ? kAxpyGroups : (nv >= 8 ? 2 : 1);
+  k_axpy3_multi<<<dim3(grid_for(N), G), 256, 0, st>>>(V, S, nv, vstride, h3, part, N);
+  k_axpy_finish<double2><<<grid_for(N), 256, 0, st>>>(part, G, w, N);
+  return cudaGetLastError();
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kRedThreads) k_norm_partial(const T* __restrict__ w, int64_t N,
                                                               double* __restrict__ partial) {
@@ -1252,6 +1373,20 @@ cudaError_t scale_into(const double2* w, const double* nrm, double2* v, int64_t 
 }
 cudaError_t scale_into(const float2* w, const double* nrm, float2* v, int64_t N, cudaStream_t st) {
   k_scale_into<float2><<<grid_for(N), 256, 0, st>>>(w, nrm, v, N);
+  return cudaGetLastError();
+}
+
+__global__ void k_scale_into_sums(const double2* __restrict__ w, const double* __restrict__ nrm,
+                                  double2* __restrict__ v, double* __restrict__ S, int64_t N) {
+  const double s = nrm[0] > 0 ? 1.0 / nrm[0] : 0.0;
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < N; i += int64_t(gridDim.x) * blockDim.x) {
+    const double2 x = cscale(w[i], s);
+    v[i] = x;
+    S[i] = x.x + x.y;
+  }
+}
+cudaError_t scale_into_sums(const double2* w, const double* nrm, double2* v, double* S, int64_t N, cudaStream_t st) {
+  k_scale_into_sums<<<grid_for(N), 256, 0, st>>>(w, nrm, v, S, N);
   return cudaGetLastError();
 }
 

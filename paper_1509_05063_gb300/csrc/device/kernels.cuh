@@ -139,6 +139,15 @@ cudaError_t scale_into(const double2* w, const double* nrm, double2* v, int64_t 
 cudaError_t combine(const double2* V, int k, int64_t vstride, const double2* y, double2* x, int64_t N,
                     cudaStream_t st);
 cudaError_t sub(const double2* a, const double2* b, double2* out, int64_t N, cudaStream_t st);
+// Complex128 Gram-Schmidt on a basis stored with S_j = Re V_j + Im V_j beside
+// every vector (three FP64 FMAs per complex product instead of four): gram3
+// also writes h3 = (Re h_j, Im h_j - Re h_j, Re h_j + Im h_j), which axpy3_multi
+// takes; scale_into_sums writes v = w / nrm and its sums S.
+cudaError_t gram3(const double2* V, const double* S, int nv, int64_t vstride, const double2* w, int64_t N,
+                  double2* partial, double2* h, double* h3, cudaStream_t st);
+cudaError_t axpy3_multi(const double2* V, const double* S, int nv, int64_t vstride, const double* h3, double2* w,
+                        double2* part, int64_t N, cudaStream_t st);
+cudaError_t scale_into_sums(const double2* w, const double* nrm, double2* v, double* S, int64_t N, cudaStream_t st);
 // The same on complex64 vectors (the correction solves of mixed precision):
 // complex64 arithmetic per element, the Gram and norm partial sums and the
 // coefficients h, y, nrm in FP64.
