@@ -231,15 +231,15 @@ def run_batch(n_inst, dev, barrier, timed):
     b.solve(ui, tol=1e-3, prec=LS_MIXED, max_iter=3)
     barrier()
     t0 = time.perf_counter()
-    _, info = b.solve(ui, tol=1e-10, prec=LS_MIXED, max_iter=4000, restart=30)
+    _, info = b.solve(ui, tol=1e-10, prec=LS_MIXED, max_iter=4000, restart=100)
     barrier()
     t_b = time.perf_counter() - t0
     t0 = time.perf_counter()
     for p, x in zip(plans, b.split(ui)):
-        p.solve(x.contiguous(), tol=1e-10, prec=LS_MIXED, max_iter=4000, restart=30)
+        p.solve(x.contiguous(), tol=1e-10, prec=LS_MIXED, max_iter=4000, restart=100)
     barrier()
     t_s = time.perf_counter() - t0
-    out["solve_mixed"] = {"tol": 1e-10, "makespan_s": t_b, "separate_solves_s": t_s,
+    out["solve_mixed"] = {"tol": 1e-10, "restart": 100, "makespan_s": t_b, "separate_solves_s": t_s,
                           "converged": info["converged"], "residual": info["residual"],
                           "iterations_each": [r["iterations"] for r in info["per_instance"]]}
     b.close()

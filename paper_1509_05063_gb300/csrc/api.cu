@@ -116,20 +116,6 @@ struct Krylov {
   }
 };
 
-// The work vectors of the pipelined GMRES in the arithmetic of T: complex128
-// uses the buffers as allocated; complex64 (the correction solves of mixed
-// precision) reuses the same storage at half the element size.
-template <typename T>
-struct KrylovView {
-  T *V, *w, *r, *apart;
-};
-template <typename T> KrylovView<T> krylov_view(Krylov& K);
-template <> KrylovView<double2> krylov_view<double2>(Krylov& K) { return {K.V, K.w, K.r, K.apart}; }
-template <> KrylovView<float2> krylov_view<float2>(Krylov& K) {
-  return {reinterpret_cast<float2*>(K.V), reinterpret_cast<float2*>(K.w), reinterpret_cast<float2*>(K.r),
-          reinterpret_cast<float2*>(K.apart)};
-}
-
 // CUDA graphs of a launch sequence keyed by (precision, batch, input, output):
 // the first call with a key launches directly, the second captures the
 // sequence on a private stream and launches the graph, later calls replay it.
@@ -886,8 +872,7 @@ ls_status ensure_krylov(DevOwner* plan, Krylov& K, int restart, const Layout& la
 }
 
 // nrm[r] = ||base_r|| for every RHS of the layout (one host synchronisation)
-template <typename T>
-cudaError_t layout_norms(Krylov& K, const Layout& lay, const T* base, cudaStream_t st) {
+cudaError_t layout_norms(Krylov& K, const Layout& lay, const double2* base, cudaStream_t st) {
   const int64_t nbmax = lsd::gram_blocks(K.max_len);
   for (int r = 0; r < lay.R; ++r) {
     cudaError_t e = lsd::norm2(base + lay.off[r], lay.len[r], K.dpartial + size_t(r) * nbmax, K.dnorm + r, st);
@@ -1053,27 +1038,28 @@ ls_status gmres_lockstep(DevOwner* plan, Krylov& K, const Layout& lay, Op op, co
 // columns, Givens rotations and residual estimates of the earlier iterations
 // while the device works.  An RHS found converged stops taking part in later
 // queued applies (op's need flags); iterations queued past its convergence are
-// discarded (their columns are never used).  Used for the complex64
-// correction solves of the mixed refinement (T = float2: complex64 basis and
-// vectors, FP64 partial sums and Hessenberg), where the apply is short and a
-// host round trip per iteration would leave the GPU idle.
-template <typename T, typename Op>
-ls_status gmres_lockstep_async(DevOwner* plan, Krylov& K, const Layout& lay, Op op, const T* B, T* X,
+// discarded (their columns are never used).  Used for the correction solves
+// of the mixed refinement (complex64 apply, FP64 basis stored with its Re + Im
+// sums), where the apply is short and a host round trip per iteration would
+// leave the GPU idle.
+template <typename Op>
+ls_status gmres_lockstep_async(DevOwner* plan, Krylov& K, const Layout& lay, Op op, const double2* B, double2* X,
                                double tol, int max_iter, int restart, cudaStream_t st, int* iters, double* relres) {
   constexpr int kLag = 2;
   static_assert(kLag < Krylov::kEvents, "event ring");
   const int R = lay.R;
   const int64_t vs = lay.total;
-  const KrylovView<T> KV = krylov_view<T>(K);
-  T* V = KV.V;
-  T* Wv = KV.w;
-  T* Rv = KV.r;
+  double2* V = K.V;
+  double* VS = K.vs;                                 // Re + Im of every basis entry
+  double2* Wv = K.w;
+  double2* Rv = K.r;
   const int m = restart;
   const int nbmax = lsd::gram_blocks(K.max_len);
   const int hstride = m + 3;
   auto part_of = [&](int r) { return K.partial + size_t(r) * nbmax * hstride; };
   auto dp_of = [&](int r) { return K.dpartial + size_t(r) * nbmax; };
   auto hslot = [&](int k, int pass, int r) { return K.hk + ((size_t(k) * 2 + pass) * R + r) * hstride; };
+  auto h3_of = [&](int r) { return K.h3 + size_t(r) * hstride * 3; };   // per pass, used right away
   auto O = [&](int r) { return lay.off[r]; };
   auto Ln = [&](int r) { return lay.len[r]; };
   double* nrm = K.pin_n;
@@ -1083,7 +1069,7 @@ ls_status gmres_lockstep_async(DevOwner* plan, Krylov& K, const Layout& lay, Op 
   for (int r = 0; r < R; ++r) {
     iters[r] = 0;
     relres[r] = 0;
-    if (bnorm[r] == 0.0) LS_CU(cudaMemsetAsync(X + O(r), 0, Ln(r) * sizeof(T), st));
+    if (bnorm[r] == 0.0) LS_CU(cudaMemsetAsync(X + O(r), 0, Ln(r) * sizeof(double2), st));
   }
   std::vector<std::vector<cd>> H(R, std::vector<cd>(size_t(m + 1) * m)), cs(R, std::vector<cd>(m)),
       sn(R, std::vector<cd>(m)), g(R, std::vector<cd>(m + 1));
@@ -1106,11 +1092,12 @@ ls_status gmres_lockstep_async(DevOwner* plan, Krylov& K, const Layout& lay, Op 
     if (total >= max_iter) return fail(plan, LS_ERR_NOCONV, "GMRES reached max_iter");
     std::vector<double> beta(nrm, nrm + R);
     for (int r = 0; r < R; ++r) {
-      T* v0 = V + O(r);
+      double2* v0 = V + O(r);
       if (done[r]) {
-        LS_CU(cudaMemsetAsync(v0, 0, Ln(r) * sizeof(T), st));
+        LS_CU(cudaMemsetAsync(v0, 0, Ln(r) * sizeof(double2), st));
+        LS_CU(cudaMemsetAsync(VS + O(r), 0, Ln(r) * sizeof(double), st));
       } else {
-        LS_CU(lsd::scale_into(Rv + O(r), K.dnorm + r, v0, Ln(r), st));
+        LS_CU(lsd::scale_into_sums(Rv + O(r), K.dnorm + r, v0, VS + O(r), Ln(r), st));
         std::fill(H[r].begin(), H[r].end(), cd(0));
         std::fill(g[r].begin(), g[r].end(), cd(0));
         g[r][0] = beta[r];
@@ -1131,11 +1118,13 @@ ls_status gmres_lockstep_async(DevOwner* plan, Krylov& K, const Layout& lay, Op 
         for (int r = 0; r < R; ++r) {
           if (!queued_for[k][r]) continue;
           for (int pass = 0; pass < 2; ++pass) {
-            LS_CU(lsd::gram(V + O(r), k + 1, vs, Wv + O(r), Ln(r), part_of(r), hslot(k, pass, r), st));
-            LS_CU(lsd::axpy_multi(V + O(r), k + 1, vs, hslot(k, pass, r), Wv + O(r), KV.apart, Ln(r), st));
+            LS_CU(lsd::gram3(V + O(r), VS + O(r), k + 1, vs, Wv + O(r), Ln(r), part_of(r), hslot(k, pass, r),
+                             h3_of(r), st));
+            LS_CU(lsd::axpy3_multi(V + O(r), VS + O(r), k + 1, vs, h3_of(r), Wv + O(r), K.apart, Ln(r), st));
           }
           LS_CU(lsd::norm2(Wv + O(r), Ln(r), dp_of(r), K.nk + size_t(k) * R + r, st));
-          LS_CU(lsd::scale_into(Wv + O(r), K.nk + size_t(k) * R + r, V + (k + 1) * vs + O(r), Ln(r), st));
+          LS_CU(lsd::scale_into_sums(Wv + O(r), K.nk + size_t(k) * R + r, V + (k + 1) * vs + O(r),
+                                     VS + (k + 1) * vs + O(r), Ln(r), st));
         }
         LS_CU(cudaMemcpyAsync(K.pin_hk + size_t(k) * 2 * R * hstride, hslot(k, 0, 0),
                               size_t(2) * R * hstride * sizeof(double2), cudaMemcpyDeviceToHost, st));
@@ -1255,20 +1244,16 @@ ls_status solve_lockstep(DevOwner* plan, Krylov& K, const Layout& lay, Op64 op64
     }
     S.refinements++;
     const double inner_tol = std::max(1e-5, 0.3 * tol / rel);
-    // the correction equation A e = r entirely in complex64 (apply, basis,
-    // Gram-Schmidt, restarts; partial sums and the Hessenberg in FP64)
-    float2* Res32 = K.c64a;
-    float2* Cor32 = K.c64b;
-    LS_CU(lsd::to_c64(Res, Res32, lay.total, st));
-    LS_CU(cudaMemsetAsync(Cor32, 0, size_t(lay.total) * sizeof(float2), st));
-    const ls_status s = gmres_lockstep_async<float2>(plan, K, lay, op32, Res32, Cor32, inner_tol,
-                                                     std::max(1, max_iter - inner_total), restart, st, it.data(),
-                                                     rr.data());
+    // the correction equation A e = r with the complex64 apply; basis and
+    // Gram-Schmidt in FP64 (a complex64 basis loses the small remainder of
+    // w - V h near stagnation: hard instances then took four times the iterations)
+    LS_CU(cudaMemsetAsync(Cor, 0, size_t(lay.total) * sizeof(double2), st));
+    const ls_status s = gmres_lockstep_async(plan, K, lay, op32, Res, Cor, inner_tol,
+                                             std::max(1, max_iter - inner_total), restart, st, it.data(), rr.data());
     int mx = 0;
     for (int r = 0; r < R; ++r) { S.iterations += it[r]; S.it_per[r] += it[r]; mx = std::max(mx, it[r]); }
     inner_total += mx;
     if (s != LS_OK && s != LS_ERR_NOCONV) return s;
-    LS_CU(lsd::to_c128(Cor32, Cor, lay.total, st));
     LS_CU(lsd::add_inplace(X, Cor, lay.total, st));
   }
 }
@@ -1391,15 +1376,16 @@ ls_status ls_solve(ls_plan plan, const void* uinc, void* u, int nrhs, double tol
       }
       return cudaSuccess;
     };
-    // complex64 apply of R contiguous complex64 vectors (chunks of at most kMaxRhs32)
-    auto op32 = [&](const float2* v, float2* Av, const char*) -> cudaError_t {
-      cudaError_t e = cudaSuccess;
+    // complex64 apply of R contiguous complex128 vectors (cast in, batched apply, cast out)
+    auto op32 = [&](const double2* v, double2* Av, const char*) -> cudaError_t {
+      cudaError_t e = lsd::to_c64(v, plan->K.c64a, int64_t(R) * N, st);
       for (int r = 0; r < R && e == cudaSuccess;) {
         int nr = lsd::kMaxRhs32;
         while (nr > R - r) nr /= 2;
-        e = run_apply(plan, LS_MIXED, plan->d32, v + r * N, Av + r * N, nr, st);
+        e = run_apply(plan, LS_MIXED, plan->d32, plan->K.c64a + r * N, plan->K.c64b + r * N, nr, st);
         r += nr;
       }
+      if (e == cudaSuccess) e = lsd::to_c128(plan->K.c64b, Av, int64_t(R) * N, st);
       return e;
     };
     SolveStats Sb;
@@ -1813,8 +1799,11 @@ ls_status ls_batch_solve(ls_batch b, const void* uinc, void* u, double tol, int 
   auto op64 = [&](const double2* v, double2* Av, const char* need) -> cudaError_t {
     return batch_apply_t(b, LS_FP64, b->d64, b->h64, v, Av, st, need);
   };
-  auto op32 = [&](const float2* v, float2* Av, const char* need) -> cudaError_t {
-    return batch_apply_t(b, LS_MIXED, b->d32, b->h32, v, Av, st, need);
+  auto op32 = [&](const double2* v, double2* Av, const char* need) -> cudaError_t {
+    cudaError_t e = lsd::to_c64(v, b->K.c64a, lay.total, st);
+    if (e == cudaSuccess) e = batch_apply_t(b, LS_MIXED, b->d32, b->h32, b->K.c64a, b->K.c64b, st, need);
+    if (e == cudaSuccess) e = lsd::to_c128(b->K.c64b, Av, lay.total, st);
+    return e;
   };
   SolveStats S;
   s = solve_lockstep(b, b->K, lay, op64, op32, prec, static_cast<const double2*>(uinc), static_cast<double2*>(u), tol,
