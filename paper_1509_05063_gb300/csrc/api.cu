@@ -682,6 +682,8 @@ ls_status ls_plan_create(const ls_geometry* geom, ls_n2_fn n2, void* ctx, double
   a.Sm = plan->alloc<double2>(lsd::kMaxRhs64 * a.lattice_rows() * M, &st);
   a.Sd = plan->alloc<double2>(lsd::kMaxRhs64 * a.lattice_rows() * M, &st);
   a.gamma = plan->alloc<double2>(size_t(lsd::kMaxRhs64) * nocc * P.nfb2, &st);
+  a.utc = plan->alloc<double>(size_t(lsd::kMaxRhs64) * N, &st);
+  a.utef = plan->alloc<double2>(size_t(lsd::kMaxRhs64) * N, &st);
   if (st != LS_OK) return bail(st, plan->err);
   // complex64 apply data
   auto& b = plan->d32;
@@ -1544,11 +1546,14 @@ ls_status noalloc_apply(ls_plan plan, const lsd::ApplyData<T>& src, const void* 
   d.Sd = reinterpret_cast<T*>(p);
   p += up256(n_grid * sizeof(T));
   d.gamma = reinterpret_cast<T*>(p);
-  // the projection runs one block per whole cell: no partial sums or counters in plan memory
+  // the projection runs one block per whole cell (no partial sums or counters
+  // in plan memory) and the near field forms its staged inputs itself
   d.pieces = src.cell_pieces;
   d.n_pieces = src.nocc;
   d.proj_part = nullptr;
   d.proj_count = nullptr;
+  d.utc = nullptr;
+  d.utef = nullptr;
   e = lsd::apply_one(d, static_cast<const T*>(u), static_cast<T*>(Au), st);
   if (e != cudaSuccess) return fail(plan, LS_ERR_CUDA, std::string("ls_apply_noalloc: ") + cudaGetErrorString(e));
   return LS_OK;

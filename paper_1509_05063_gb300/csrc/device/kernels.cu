@@ -156,7 +156,8 @@ template <typename T, int R>
 __device__ __forceinline__ void es_project_body(int k, int jb, int je, const int64_t* __restrict__ occ_start,
                                                 const int64_t* __restrict__ P_off, const T* __restrict__ P,
                                                 const double* __restrict__ Ps, const T* __restrict__ u, int64_t N,
-                                                T* __restrict__ out, int64_t r_stride, int n_es) {
+                                                T* __restrict__ out, int64_t r_stride, int n_es,
+                                                double* __restrict__ utc, double2* __restrict__ utef) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int CJ = kProjStage / (R * Staged<T>::kBytes) & ~1;
   const int64_t s0 = occ_start[k] + jb;
@@ -174,7 +175,15 @@ __device__ __forceinline__ void es_project_body(int k, int jb, int je, const int
     __syncthreads();
     for (int e = t; e < R * cl; e += blockDim.x) {
       const int r = e / cl, j = e - r * cl;
-      X.put(r, j, u[int64_t(r) * N + s0 + j0 + j]);
+      const int64_t q = int64_t(r) * N + s0 + j0 + j;
+      const T v = u[q];
+      X.put(r, j, v);
+      if constexpr (sizeof(T) == 16) {
+        if (utc) {                                 // the near field's staged forms of the input
+          utc[q] = v.x;
+          utef[q] = make_double2(v.x + v.y, v.y - v.x);
+        }
+      }
     }
     __syncthreads();
     if (sg < S) contract_segment<T, R>(Pk + int64_t(j0) * n_es, sa_base(Psk, int64_t(j0) * n_es), n_es, o,
@@ -195,15 +204,16 @@ __device__ __forceinline__ void es_project_piece(const int4 pc, const int* __res
                                                  const int64_t* __restrict__ P_off, const T* __restrict__ P,
                                                  const double* __restrict__ Ps, const T* __restrict__ u, int64_t N,
                                                  T* __restrict__ sigma, T* __restrict__ part, int* __restrict__ count,
-                                                 int n_es) {
+                                                 int n_es, double* __restrict__ utc, double2* __restrict__ utef) {
   const int k = pc.x, p = pc.w >> 16, np = pc.w & 0xffff;
   if (np == 1) {
     es_project_body<T, R>(k, pc.y, pc.z, occ_start, P_off, P, Ps, u, N, sigma + int64_t(k) * n_es,
-                          int64_t(nocc) * n_es, n_es);
+                          int64_t(nocc) * n_es, n_es, utc, utef);
     return;
   }
   T* slots = part + int64_t(piece_off[k]) * R * n_es;          // [piece][r][i]
-  es_project_body<T, R>(k, pc.y, pc.z, occ_start, P_off, P, Ps, u, N, slots + int64_t(p) * R * n_es, n_es, n_es);
+  es_project_body<T, R>(k, pc.y, pc.z, occ_start, P_off, P, Ps, u, N, slots + int64_t(p) * R * n_es, n_es, n_es,
+                        utc, utef);
   __shared__ int last;
   __threadfence();
   __syncthreads();
@@ -226,9 +236,10 @@ __global__ void __launch_bounds__(256) k_es_project(const int4* __restrict__ pie
                                                     const int64_t* __restrict__ P_off, const T* __restrict__ P,
                                                     const double* __restrict__ Ps, const T* __restrict__ u, int64_t N,
                                                     T* __restrict__ sigma, T* __restrict__ part,
-                                                    int* __restrict__ count, int n_es) {
+                                                    int* __restrict__ count, int n_es, double* __restrict__ utc,
+                                                    double2* __restrict__ utef) {
   es_project_piece<T, R>(pieces[blockIdx.x], piece_off, nocc, occ_start, P_off, P, Ps, u, N, sigma, part, count,
-                         n_es);
+                         n_es, utc, utef);
 }
 
 // ------------------------------------------------------------ lattice sources
@@ -542,11 +553,12 @@ __global__ void __launch_bounds__(kFftMaxM / 8) k_inv_rows(int M, int logM, int 
   for (int b = threadIdx.x; b < n_lat; b += blockDim.x) V[a * M + b] = s[b];
 }
 
+// columns per block of the column pass: one, so that the M blocks of M / 8
+// threads are all resident at once, several per SM (wider blocks left SMs idle:
+// complex64 with 8 columns ran 128 blocks; complex128 with 4 ran 1.7 waves)
 template <typename T>
-int conv_cols_tc(int M) {
-  int tc = 1024 / (M / 8);
-  while (tc > 1 && size_t(2) * tc * M * sizeof(T) > 200 * 1024) tc /= 2;
-  return tc;
+int conv_cols_tc(int) {
+  return 1;
 }
 
 template <typename T>
@@ -742,7 +754,9 @@ __device__ __forceinline__ void near_eval_body(const int2 item, const int64_t* _
                                                const T* __restrict__ Wb, const double* __restrict__ Ws,
                                                const int64_t* __restrict__ rem_row,
                                                const int* __restrict__ rem_col, const T* __restrict__ rem_val,
-                                               const T* __restrict__ u, int64_t N, const T* __restrict__ Phi,
+                                               const T* __restrict__ u, const double* __restrict__ utc,
+                                               const double2* __restrict__ utef, int64_t N,
+                                               const T* __restrict__ Phi,
                                                const T* __restrict__ gamma, int nocc, int nfb2,
                                                typename RealOf<T>::R kappa2, T* __restrict__ out) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -792,7 +806,23 @@ __device__ __forceinline__ void near_eval_body(const int2 item, const int64_t* _
   for (int c0 = 0; c0 < nblk; c0 += CH) {
     const int cl = min(CH, nblk - c0);
     __syncthreads();
-    if constexpr (R == 1) {
+    // node index of column cc of the block (-1: padding)
+    auto node_of = [&](int cc) -> int {
+      if (cc < p0) return cc < l0 ? sg[0] + cc : -1;
+      if (cc < p0 + p1) { const int o = cc - p0; return o < l1 ? sg[2] + o : -1; }
+      const int o = cc - p0 - p1;
+      return o < l2 ? sg[4] + o : -1;
+    };
+    if (kC128 && utc) {
+      // complex128 with the staged forms written by the projection: plain copies
+#pragma unroll 1
+      for (int r = 0; r < R; ++r)
+        for (int col = threadIdx.x; col < cl; col += blockDim.x) {
+          const int q = node_of(c0 + col);
+          usc[r * CH + col] = q >= 0 ? utc[int64_t(r) * N + q] : 0.0;
+          usef[r * CH + col] = q >= 0 ? utef[int64_t(r) * N + q] : make_double2(0.0, 0.0);
+        }
+    } else if constexpr (R == 1) {
       for (int col = threadIdx.x; col < cl; col += blockDim.x) {   // us[col]
         const int cc = c0 + col;
         T v = czero(T{});
@@ -892,10 +922,11 @@ __device__ __forceinline__ void near_eval_body(const int2 item, const int64_t* _
   const int2 *__restrict__ items, const int64_t *__restrict__ occ_start, const int64_t *__restrict__ blk_off,     \
       const int *__restrict__ blk_seg, const T *__restrict__ Wb, const double *__restrict__ Ws,                   \
       const int64_t *__restrict__ rem_row,                                                                        \
-      const int *__restrict__ rem_col, const T *__restrict__ rem_val, const T *__restrict__ u, int64_t N,         \
+      const int *__restrict__ rem_col, const T *__restrict__ rem_val, const T *__restrict__ u,                    \
+      const double *__restrict__ utc, const double2 *__restrict__ utef, int64_t N,                                \
       const T *__restrict__ Phi, const T *__restrict__ gamma, int nocc, int nfb2,                                 \
       typename RealOf<T>::R kappa2, T *__restrict__ out
-#define LS_NEAR_PASS items[blockIdx.x], occ_start, blk_off, blk_seg, Wb, Ws, rem_row, rem_col, rem_val, u, N, Phi, gamma, nocc, nfb2, \
+#define LS_NEAR_PASS items[blockIdx.x], occ_start, blk_off, blk_seg, Wb, Ws, rem_row, rem_col, rem_val, u, utc, utef, N, Phi, gamma, nocc, nfb2, \
                      kappa2, out
 // two rows per warp, 16-row items: registers left to the compiler
 template <typename T, int R>
@@ -920,7 +951,7 @@ cudaError_t apply_r(const ApplyData<T>& d, const T* u, T* out, cudaStream_t st, 
   if (ev) cudaEventRecord(ev[0], st);
   k_es_project<T, R><<<d.n_pieces, 256, contraction_smem<T>(R, kProjStage), st>>>(
       d.pieces, d.piece_off, d.nocc, d.occ_start, d.P_off, d.P, d.Ps, u, d.N, d.sigma, d.proj_part, d.proj_count,
-      d.n_es);
+      d.n_es, d.utc, d.utef);
   if (ev) cudaEventRecord(ev[1], st);
   if (ev) cudaEventRecord(ev[2], st);        // the lattice fill is fused into k_src_rows
   cudaError_t e = lattice_conv(d, R, st);
@@ -941,12 +972,12 @@ cudaError_t apply_r(const ApplyData<T>& d, const T* u, T* out, cudaStream_t st, 
     if (e2 != cudaSuccess) return e2;
   } else if constexpr (near_rows_per_warp<T, R>() == 4)
     k_near_eval4<T, R><<<d.n_items32, 256, kNearSmem, st>>>(d.items32, d.occ_start, d.blk_off, d.blk_seg, d.Wb,
-                                                            d.Ws, d.rem_row, d.rem_col, d.rem_val, u, d.N, d.Phi,
+                                                            d.Ws, d.rem_row, d.rem_col, d.rem_val, u, d.utc, d.utef, d.N, d.Phi,
                                                             d.gamma, d.nocc, d.nfb2,
                                                             typename RealOf<T>::R(d.kappa2), out);
   else
     k_near_eval<T, R><<<d.n_items, 256, kNearSmem, st>>>(d.items, d.occ_start, d.blk_off, d.blk_seg, d.Wb,
-                                                         d.Ws, d.rem_row, d.rem_col, d.rem_val, u, d.N, d.Phi, d.gamma,
+                                                         d.Ws, d.rem_row, d.rem_col, d.rem_val, u, d.utc, d.utef, d.N, d.Phi, d.gamma,
                                                          d.nocc, d.nfb2, typename RealOf<T>::R(d.kappa2), out);
   if (ev) cudaEventRecord(ev[5], st);
   return cudaGetLastError();
@@ -961,7 +992,7 @@ __global__ void __launch_bounds__(256) k_es_project_multi(const int2* __restrict
   const int2 w = work[blockIdx.x];
   const ApplyData<T>& d = I[w.x].d;
   es_project_piece<T, 1>(d.pieces[w.y], d.piece_off, d.nocc, d.occ_start, d.P_off, d.P, d.Ps, u + I[w.x].off, d.N,
-                         d.sigma, d.proj_part, d.proj_count, d.n_es);
+                         d.sigma, d.proj_part, d.proj_count, d.n_es, d.utc, d.utef);
 }
 
 template <typename T>
@@ -981,7 +1012,7 @@ __global__ void __launch_bounds__(256) k_near_eval_multi(const int4* __restrict_
   const ApplyData<T>& d = I[it.x].d;
   const int64_t off = I[it.x].off;
   near_eval_body<T, 1, 2>(make_int2(it.y, it.z), d.occ_start, d.blk_off, d.blk_seg, d.Wb, d.Ws, d.rem_row,
-                          d.rem_col, d.rem_val, u + off, d.N, d.Phi, d.gamma, d.nocc, d.nfb2,
+                          d.rem_col, d.rem_val, u + off, d.utc, d.utef, d.N, d.Phi, d.gamma, d.nocc, d.nfb2,
                           typename RealOf<T>::R(d.kappa2), out + off);
 }
 

@@ -57,6 +57,8 @@ struct ApplyData {
   int tc_spin = 1 << 22;                // polls of each mbarrier wait before it gives up
   const T* Wb = nullptr;                // blocks, row-major per cell
   const double* Ws = nullptr;           // complex128 only: Re + Im of every block weight (same layout as Wb)
+  double* utc = nullptr;                // complex128 only (null: formed in the near field): the input's
+  double2* utef = nullptr;              // staged forms c and (c + d, d - c), written by the projection
   const int64_t* rem_row = nullptr;     // N + 1
   const int* rem_col = nullptr;
   const T* rem_val = nullptr;
