@@ -933,6 +933,11 @@ template <typename T, int R>
 __global__ void __launch_bounds__(256) k_near_eval(LS_NEAR_ARGS) {
   near_eval_body<T, R, 2>(LS_NEAR_PASS);
 }
+// single-RHS complex128: five blocks per SM (the FP64 pipe hides more latency)
+template <typename T, int R>
+__global__ void __launch_bounds__(256, 5) k_near_eval5(LS_NEAR_ARGS) {
+  near_eval_body<T, R, 2>(LS_NEAR_PASS);
+}
 // four rows per warp, 32-row items: two blocks per SM
 template <typename T, int R>
 __global__ void __launch_bounds__(256, 2) k_near_eval4(LS_NEAR_ARGS) {
@@ -975,6 +980,11 @@ cudaError_t apply_r(const ApplyData<T>& d, const T* u, T* out, cudaStream_t st, 
                                                             d.Ws, d.rem_row, d.rem_col, d.rem_val, u, d.utc, d.utef, d.N, d.Phi,
                                                             d.gamma, d.nocc, d.nfb2,
                                                             typename RealOf<T>::R(d.kappa2), out);
+  else if constexpr (sizeof(T) == 16 && R == 1)
+    k_near_eval5<T, R><<<d.n_items, 256, kNearSmem, st>>>(d.items, d.occ_start, d.blk_off, d.blk_seg, d.Wb,
+                                                          d.Ws, d.rem_row, d.rem_col, d.rem_val, u, d.utc, d.utef,
+                                                          d.N, d.Phi, d.gamma, d.nocc, d.nfb2,
+                                                          typename RealOf<T>::R(d.kappa2), out);
   else
     k_near_eval<T, R><<<d.n_items, 256, kNearSmem, st>>>(d.items, d.occ_start, d.blk_off, d.blk_seg, d.Wb,
                                                          d.Ws, d.rem_row, d.rem_col, d.rem_val, u, d.utc, d.utef, d.N, d.Phi, d.gamma,
