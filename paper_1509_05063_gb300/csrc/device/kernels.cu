@@ -2,12 +2,14 @@
 // of the GMRES solve.  One template per arithmetic precision: T = double2
 // (complex128 path) or float2 (complex64 inner path of mixed precision).
 //
-// Apply pipeline for one right-hand side (Eq. VolInt-Adj-NonAdj):
+// Apply pipeline for one or more right-hand sides (Eq. VolInt-Adj-NonAdj):
 //   k_es_project      sigma_c = P_c u_c            (equivalent-source fit)
-//   k_lattice_fill    sigma -> monopole / dipole lattice arrays (face points)
-//   fft2d x2, k_spectral, fft2d^-1   lattice convolution with G and dG/dz_1
+//   k_src_rows        sigma -> monopole / dipole face rows of the lattice, FFT along b
+//   k_conv_cols       column FFTs, product with the spectra of G and dG/dz_1, inverse
+//   k_inv_rows        inverse FFT along b of the kept rows (lattice values V)
 //   k_local_coeffs    gamma_c = B^+ V_c - sum_o (B^+ T_o) sigma_{c+o}
 //   k_near_eval       out_q = u_q + kappa^2 (sum_l W_ql u_l + Phi_q . gamma_c)
+//                     (k_near_tc: the same for 8 or 16 complex64 RHS on the tensor cores)
 #include <cstdio>
 
 #include "cplx.cuh"
@@ -242,41 +244,6 @@ __global__ void __launch_bounds__(256) k_es_project(const int4* __restrict__ pie
                          n_es, utc, utef);
 }
 
-// ------------------------------------------------------------ lattice sources
-// Face lattice point (a, b) with a = f Ne gathers the strengths of every cell
-// whose x-face passes through it (left face of cell f, right face of cell f-1;
-// the top point of a face is shared with the cell above).
-template <typename T>
-__global__ void __launch_bounds__(256) k_lattice_fill(int M, int n_lat, int Ne, int L,
-                                                      const int* __restrict__ occ_of_cell,
-                                                      const T* __restrict__ sigma, int n_es,
-                                                      T* __restrict__ Sm, T* __restrict__ Sd) {
-  const int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (idx >= int64_t(M) * M) return;
-  const int a = int(idx / M), b = int(idx % M);
-  T sm = czero(T{}), sd = czero(T{});
-  if (a < n_lat && b < n_lat && a % Ne == 0) {
-    const int fa = a / Ne;
-    for (int side = 0; side < 2; ++side) {
-      const int ci = fa - side;
-      if (ci < 0 || ci >= L) continue;
-      const int cjb = b / Ne, kb = b % Ne;
-      for (int t = 0; t < 2; ++t) {
-        if (t == 1 && kb != 0) break;
-        const int cj = cjb - t, k = kb + t * Ne;
-        if (cj < 0 || cj >= L) continue;
-        const int occ = occ_of_cell[cj * L + ci];
-        if (occ < 0) continue;
-        const T* s = sigma + int64_t(occ) * n_es;
-        sm = cadd(sm, s[side * (Ne + 1) + k]);
-        sd = cadd(sd, s[(2 + side) * (Ne + 1) + k]);
-      }
-    }
-  }
-  Sm[idx] = sm;
-  Sd[idx] = sd;
-}
-
 // ------------------------------------------------------------ Stockham FFT
 // In-place radix-4 (plus one radix-2 stage when log2 N is odd) Stockham
 // autosort transform of one length-N sequence held in shared memory, run by
@@ -414,6 +381,9 @@ cudaError_t fft2d(T* x, int M, int logM, const T* tw, bool inverse, cudaStream_t
 // padded lattice, and only the n_lat x n_lat corner of the result is read.
 //  k_src_rows  : gather sigma of face row k (monopole or dipole) into shared
 //                memory and FFT it along b              -> R[k][b], (L+1) x M x 2
+//                (face point (k Ne, b) takes the strengths of the left face of
+//                cell k and the right face of cell k - 1; the top point of a
+//                face is shared with the cell above)
 //  k_conv_cols : per column b, scatter the L + 1 rows to a, FFT along a (both
 //                source kinds), multiply by the kernel spectra (stored as a
 //                quarter using the even / odd symmetry of the tables), inverse
@@ -589,14 +559,6 @@ cudaError_t lattice_conv(const ApplyData<T>& d, int nr, cudaStream_t st) {
       M, d.logM, d.n_lat, d.Ne, d.L, TC, Ms, logMs, d.Sd, d.Gq, d.Dq, d.tw, d.Sm, stride);
   k_inv_rows<T><<<dim3(d.n_lat, nr), M / 8, M * sizeof(T), st>>>(M, d.logM, d.n_lat, d.tw, d.Sm, d.Sd, stride);
   return cudaGetLastError();
-}
-
-// ------------------------------------------------------------ spectral product
-template <typename T>
-__global__ void __launch_bounds__(256) k_spectral(int64_t n, T* __restrict__ Sm, const T* __restrict__ Sd,
-                                                  const T* __restrict__ Gh, const T* __restrict__ Dh) {
-  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (i < n) Sm[i] = cfma(Sd[i], Dh[i], cmul(Sm[i], Gh[i]));
 }
 
 // ------------------------------------------------------------ local expansion
