@@ -275,7 +275,7 @@ def main():
     import numpy as np
     import torch
     import workloads as W
-    from paper_1509_05063_gb300 import LS_FP64, LS_MIXED, Plan
+    from paper_1509_05063_gb300 import LS_FP64, LS_MIXED, LS_MIXED32, Plan
 
     rank, world, local = dist_info()
     if world > 1:
@@ -391,6 +391,15 @@ def main():
         sb32, ib32 = plan.solve(UI, tol=1e-10, prec=LS_MIXED, max_iter=800, restart=30)
         barrier()
         tb32 = time.perf_counter() - t0
+        # LS_MIXED32: complex64 Arnoldi vectors in the correction solves as well
+        t0 = time.perf_counter()
+        s3, i3 = plan.solve(ui, tol=1e-10, prec=LS_MIXED32, max_iter=800, restart=30)
+        barrier()
+        t3 = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        sb3, ib3 = plan.solve(UI, tol=1e-10, prec=LS_MIXED32, max_iter=800, restart=30)
+        barrier()
+        tb3 = time.perf_counter() - t0
         solve = {"tol": 1e-10, "restart_fp64": 200, "restart_mixed": 30, "fp64_s": t64, "fp64_iterations": i64["iterations"],
                  "fp64_residual": i64["residual"], "fp64_converged": i64["converged"],
                  "mixed_s": t32, "mixed_inner_iterations": i32["iterations"],
@@ -398,7 +407,10 @@ def main():
                  "mixed_converged": i32["converged"], "mixed_vs_fp64_solution_rel": diff,
                  "directions": D, "mixed_block_s": tb32, "mixed_block_per_rhs_s": tb32 / D,
                  "mixed_block_converged": ib32["converged"], "mixed_block_residual": ib32["residual"],
-                 "mixed_block_inner_iterations": ib32["iterations"]}
+                 "mixed_block_inner_iterations": ib32["iterations"],
+                 "mixed32_s": t3, "mixed32_inner_iterations": i3["iterations"], "mixed32_residual": i3["residual"],
+                 "mixed32_converged": i3["converged"], "mixed32_block_s": tb3,
+                 "mixed32_block_converged": ib3["converged"], "mixed32_block_residual": ib3["residual"]}
 
     batch = run_batch(args.batch, dev, barrier, timed) if args.batch > 0 else None
 

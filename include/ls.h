@@ -48,7 +48,13 @@ typedef enum {
   LS_ERR_UNSUPPORTED = 6   /* feature not built (e.g. dim = 3)                 */
 } ls_status;
 
-typedef enum { LS_FP64 = 0, LS_MIXED = 1 } ls_precision;
+/* LS_FP64: complex128 throughout.  LS_MIXED: complex64 apply inside FP64
+ * iterative refinement (Arnoldi vectors of the correction solves in FP64).
+ * LS_MIXED32 (ls_solve and ls_batch_solve only): as LS_MIXED with the
+ * correction solves' Arnoldi vectors in complex64 too -- faster where the
+ * Arnoldi step costs as much as the apply (many right-hand sides in lock-step),
+ * slower to converge on problems whose correction solves stagnate. */
+typedef enum { LS_FP64 = 0, LS_MIXED = 1, LS_MIXED32 = 2 } ls_precision;
 
 typedef enum { LS_DISC = 0, LS_KITE = 1 } ls_shape;
 
@@ -161,9 +167,10 @@ ls_status ls_apply(ls_plan plan, const void* u_dev, void* Au_dev, int nrhs,
  * uinc, u: complex128 device arrays (u: initial guess in, solution out).
  * LS_FP64: restarted GMRES with the FP64 apply.  LS_MIXED: FP64 iterative
  * refinement r = uinc - A_64 u whose correction equations are solved by GMRES
- * with the complex64 apply (Arnoldi vectors in FP64).  Stops when
- * ||uinc - A u|| / ||uinc|| <= tol for every RHS.  Right-hand sides are solved
- * in lock-step batches (4 for LS_FP64, 16 for LS_MIXED); a right-hand side of
+ * with the complex64 apply (Arnoldi vectors in FP64; LS_MIXED32: in complex64).
+ * Stops when ||uinc - A u|| / ||uinc|| <= tol for every RHS (the FP64 residual
+ * whatever the precision).  Right-hand sides are solved in lock-step batches
+ * (4 for LS_FP64, 16 for the mixed precisions); a right-hand side of
  * a later batch whose initial guess is zero starts from the least-squares
  * combination of the earlier batches' solutions.  Synchronises the stream.
  * Errors: LS_ERR_NOCONV if max_iter is reached (u holds the last iterate). */

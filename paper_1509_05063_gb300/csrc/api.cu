@@ -874,7 +874,8 @@ ls_status ensure_krylov(DevOwner* plan, Krylov& K, int restart, const Layout& la
 }
 
 // nrm[r] = ||base_r|| for every RHS of the layout (one host synchronisation)
-cudaError_t layout_norms(Krylov& K, const Layout& lay, const double2* base, cudaStream_t st) {
+template <typename T>
+cudaError_t layout_norms(Krylov& K, const Layout& lay, const T* base, cudaStream_t st) {
   const int64_t nbmax = lsd::gram_blocks(K.max_len);
   for (int r = 0; r < lay.R; ++r) {
     cudaError_t e = lsd::norm2(base + lay.off[r], lay.len[r], K.dpartial + size_t(r) * nbmax, K.dnorm + r, st);
@@ -1044,17 +1045,26 @@ ls_status gmres_lockstep(DevOwner* plan, Krylov& K, const Layout& lay, Op op, co
 // of the mixed refinement (complex64 apply, FP64 basis stored with its Re + Im
 // sums), where the apply is short and a host round trip per iteration would
 // leave the GPU idle.
-template <typename Op>
-ls_status gmres_lockstep_async(DevOwner* plan, Krylov& K, const Layout& lay, Op op, const double2* B, double2* X,
+template <typename T, typename Op>
+ls_status gmres_lockstep_async(DevOwner* plan, Krylov& K, const Layout& lay, Op op, const T* B, T* X,
                                double tol, int max_iter, int restart, cudaStream_t st, int* iters, double* relres) {
   constexpr int kLag = 2;
   static_assert(kLag < Krylov::kEvents, "event ring");
   const int R = lay.R;
   const int64_t vs = lay.total;
-  double2* V = K.V;
-  double* VS = K.vs;                                 // Re + Im of every basis entry
-  double2* Wv = K.w;
-  double2* Rv = K.r;
+  // complex128: the buffers as allocated, the basis with its Re + Im sums;
+  // complex64 (LS_MIXED32): the same storage at half the element size
+  constexpr bool kC128 = sizeof(T) == 16;
+  T* V = reinterpret_cast<T*>(K.V);
+  double* VS = K.vs;
+  T* Wv = reinterpret_cast<T*>(K.w);
+  T* Rv = reinterpret_cast<T*>(K.r);
+  T* apart = reinterpret_cast<T*>(K.apart);
+  // basis vector v = w / nrm into slot (offset into V)
+  auto new_basis = [&](const T* w, const double* nrm, int64_t slot, int64_t len) -> cudaError_t {
+    if constexpr (kC128) return lsd::scale_into_sums(w, nrm, V + slot, VS + slot, len, st);
+    else return lsd::scale_into(w, nrm, V + slot, len, st);
+  };
   const int m = restart;
   const int nbmax = lsd::gram_blocks(K.max_len);
   const int hstride = m + 3;
@@ -1071,7 +1081,7 @@ ls_status gmres_lockstep_async(DevOwner* plan, Krylov& K, const Layout& lay, Op 
   for (int r = 0; r < R; ++r) {
     iters[r] = 0;
     relres[r] = 0;
-    if (bnorm[r] == 0.0) LS_CU(cudaMemsetAsync(X + O(r), 0, Ln(r) * sizeof(double2), st));
+    if (bnorm[r] == 0.0) LS_CU(cudaMemsetAsync(X + O(r), 0, Ln(r) * sizeof(T), st));
   }
   std::vector<std::vector<cd>> H(R, std::vector<cd>(size_t(m + 1) * m)), cs(R, std::vector<cd>(m)),
       sn(R, std::vector<cd>(m)), g(R, std::vector<cd>(m + 1));
@@ -1094,12 +1104,11 @@ ls_status gmres_lockstep_async(DevOwner* plan, Krylov& K, const Layout& lay, Op 
     if (total >= max_iter) return fail(plan, LS_ERR_NOCONV, "GMRES reached max_iter");
     std::vector<double> beta(nrm, nrm + R);
     for (int r = 0; r < R; ++r) {
-      double2* v0 = V + O(r);
       if (done[r]) {
-        LS_CU(cudaMemsetAsync(v0, 0, Ln(r) * sizeof(double2), st));
-        LS_CU(cudaMemsetAsync(VS + O(r), 0, Ln(r) * sizeof(double), st));
+        LS_CU(cudaMemsetAsync(V + O(r), 0, Ln(r) * sizeof(T), st));
+        if (kC128) LS_CU(cudaMemsetAsync(VS + O(r), 0, Ln(r) * sizeof(double), st));
       } else {
-        LS_CU(lsd::scale_into_sums(Rv + O(r), K.dnorm + r, v0, VS + O(r), Ln(r), st));
+        LS_CU(new_basis(Rv + O(r), K.dnorm + r, O(r), Ln(r)));
         std::fill(H[r].begin(), H[r].end(), cd(0));
         std::fill(g[r].begin(), g[r].end(), cd(0));
         g[r][0] = beta[r];
@@ -1120,13 +1129,17 @@ ls_status gmres_lockstep_async(DevOwner* plan, Krylov& K, const Layout& lay, Op 
         for (int r = 0; r < R; ++r) {
           if (!queued_for[k][r]) continue;
           for (int pass = 0; pass < 2; ++pass) {
-            LS_CU(lsd::gram3(V + O(r), VS + O(r), k + 1, vs, Wv + O(r), Ln(r), part_of(r), hslot(k, pass, r),
-                             h3_of(r), st));
-            LS_CU(lsd::axpy3_multi(V + O(r), VS + O(r), k + 1, vs, h3_of(r), Wv + O(r), K.apart, Ln(r), st));
+            if constexpr (kC128) {
+              LS_CU(lsd::gram3(V + O(r), VS + O(r), k + 1, vs, Wv + O(r), Ln(r), part_of(r), hslot(k, pass, r),
+                               h3_of(r), st));
+              LS_CU(lsd::axpy3_multi(V + O(r), VS + O(r), k + 1, vs, h3_of(r), Wv + O(r), apart, Ln(r), st));
+            } else {
+              LS_CU(lsd::gram(V + O(r), k + 1, vs, Wv + O(r), Ln(r), part_of(r), hslot(k, pass, r), st));
+              LS_CU(lsd::axpy_multi(V + O(r), k + 1, vs, hslot(k, pass, r), Wv + O(r), apart, Ln(r), st));
+            }
           }
           LS_CU(lsd::norm2(Wv + O(r), Ln(r), dp_of(r), K.nk + size_t(k) * R + r, st));
-          LS_CU(lsd::scale_into_sums(Wv + O(r), K.nk + size_t(k) * R + r, V + (k + 1) * vs + O(r),
-                                     VS + (k + 1) * vs + O(r), Ln(r), st));
+          LS_CU(new_basis(Wv + O(r), K.nk + size_t(k) * R + r, (k + 1) * vs + O(r), Ln(r)));
         }
         LS_CU(cudaMemcpyAsync(K.pin_hk + size_t(k) * 2 * R * hstride, hslot(k, 0, 0),
                               size_t(2) * R * hstride * sizeof(double2), cudaMemcpyDeviceToHost, st));
@@ -1200,10 +1213,10 @@ struct SolveStats {
 // op64.  Mixed: FP64 iterative refinement r = b - A_64 x (op64), lock-step
 // GMRES on op32 (complex64 apply) to a loose tolerance, x += correction, until
 // the FP64 residual of every RHS is <= tol.
-template <typename Op64, typename Op32>
-ls_status solve_lockstep(DevOwner* plan, Krylov& K, const Layout& lay, Op64 op64, Op32 op32, ls_precision prec,
-                         const double2* B, double2* X, double tol, int max_iter, int restart, cudaStream_t st,
-                         SolveStats& S) {
+template <typename Op64, typename Op32, typename Op32f>
+ls_status solve_lockstep(DevOwner* plan, Krylov& K, const Layout& lay, Op64 op64, Op32 op32, Op32f op32f,
+                         ls_precision prec, const double2* B, double2* X, double tol, int max_iter, int restart,
+                         cudaStream_t st, SolveStats& S) {
   const int R = lay.R;
   std::vector<int> it(R);
   std::vector<double> rr(R);
@@ -1249,9 +1262,20 @@ ls_status solve_lockstep(DevOwner* plan, Krylov& K, const Layout& lay, Op64 op64
     // the correction equation A e = r with the complex64 apply; basis and
     // Gram-Schmidt in FP64 (a complex64 basis loses the small remainder of
     // w - V h near stagnation: hard instances then took four times the iterations)
-    LS_CU(cudaMemsetAsync(Cor, 0, size_t(lay.total) * sizeof(double2), st));
-    const ls_status s = gmres_lockstep_async(plan, K, lay, op32, Res, Cor, inner_tol,
-                                             std::max(1, max_iter - inner_total), restart, st, it.data(), rr.data());
+    const int inner_max = std::max(1, max_iter - inner_total);
+    ls_status s = LS_OK;
+    if (prec == LS_MIXED32) {
+      // complex64 right-hand side, correction and Krylov basis
+      LS_CU(lsd::to_c64(Res, K.c64a, lay.total, st));
+      LS_CU(cudaMemsetAsync(K.c64b, 0, size_t(lay.total) * sizeof(float2), st));
+      s = gmres_lockstep_async<float2>(plan, K, lay, op32f, K.c64a, K.c64b, inner_tol, inner_max, restart, st,
+                                       it.data(), rr.data());
+      if (s == LS_OK || s == LS_ERR_NOCONV) LS_CU(lsd::to_c128(K.c64b, Cor, lay.total, st));
+    } else {
+      LS_CU(cudaMemsetAsync(Cor, 0, size_t(lay.total) * sizeof(double2), st));
+      s = gmres_lockstep_async<double2>(plan, K, lay, op32, Res, Cor, inner_tol, inner_max, restart, st, it.data(),
+                                        rr.data());
+    }
     int mx = 0;
     for (int r = 0; r < R; ++r) { S.iterations += it[r]; S.it_per[r] += it[r]; mx = std::max(mx, it[r]); }
     inner_total += mx;
@@ -1347,7 +1371,8 @@ ls_status ls_solve(ls_plan plan, const void* uinc, void* u, int nrhs, double tol
   if (!plan) return LS_ERR_INVALID;
   if (!uinc || !u || nrhs < 0 || !(tol > 0) || max_iter < 1 || restart < 1)
     return fail(plan, LS_ERR_INVALID, "ls_solve: bad arguments");
-  if (prec != LS_FP64 && prec != LS_MIXED) return fail(plan, LS_ERR_INVALID, "ls_solve: bad precision");
+  if (prec != LS_FP64 && prec != LS_MIXED && prec != LS_MIXED32)
+    return fail(plan, LS_ERR_INVALID, "ls_solve: bad precision");
   const auto t0 = std::chrono::steady_clock::now();
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int64_t N = plan->d64.N;
@@ -1390,8 +1415,19 @@ ls_status ls_solve(ls_plan plan, const void* uinc, void* u, int nrhs, double tol
       if (e == cudaSuccess) e = lsd::to_c128(plan->K.c64b, Av, int64_t(R) * N, st);
       return e;
     };
+    // complex64 apply of R contiguous complex64 vectors (the LS_MIXED32 correction solves)
+    auto op32f = [&](const float2* v, float2* Av, const char*) -> cudaError_t {
+      cudaError_t e = cudaSuccess;
+      for (int r = 0; r < R && e == cudaSuccess;) {
+        int nr = lsd::kMaxRhs32;
+        while (nr > R - r) nr /= 2;
+        e = run_apply(plan, LS_MIXED, plan->d32, v + r * N, Av + r * N, nr, st);
+        r += nr;
+      }
+      return e;
+    };
     SolveStats Sb;
-    s = solve_lockstep(plan, plan->K, uniform_layout(R, N), op64, op32, prec,
+    s = solve_lockstep(plan, plan->K, uniform_layout(R, N), op64, op32, op32f, prec,
                        static_cast<const double2*>(uinc) + int64_t(r0) * N, static_cast<double2*>(u) + int64_t(r0) * N,
                        tol, max_iter, restart, st, Sb);
     total_it += Sb.iterations;
@@ -1795,7 +1831,8 @@ ls_status ls_batch_solve(ls_batch b, const void* uinc, void* u, double tol, int 
   if (!b) return LS_ERR_INVALID;
   if (!uinc || !u || !(tol > 0) || max_iter < 1 || restart < 1)
     return fail(b, LS_ERR_INVALID, "ls_batch_solve: bad arguments");
-  if (prec != LS_FP64 && prec != LS_MIXED) return fail(b, LS_ERR_INVALID, "ls_batch_solve: bad precision");
+  if (prec != LS_FP64 && prec != LS_MIXED && prec != LS_MIXED32)
+    return fail(b, LS_ERR_INVALID, "ls_batch_solve: bad precision");
   const auto t0 = std::chrono::steady_clock::now();
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const Layout lay = batch_layout(b);
@@ -1810,8 +1847,11 @@ ls_status ls_batch_solve(ls_batch b, const void* uinc, void* u, double tol, int 
     if (e == cudaSuccess) e = lsd::to_c128(b->K.c64b, Av, lay.total, st);
     return e;
   };
+  auto op32f = [&](const float2* v, float2* Av, const char* need) -> cudaError_t {
+    return batch_apply_t(b, LS_MIXED, b->d32, b->h32, v, Av, st, need);
+  };
   SolveStats S;
-  s = solve_lockstep(b, b->K, lay, op64, op32, prec, static_cast<const double2*>(uinc), static_cast<double2*>(u), tol,
+  s = solve_lockstep(b, b->K, lay, op64, op32, op32f, prec, static_cast<const double2*>(uinc), static_cast<double2*>(u), tol,
                      max_iter, restart, st, S);
   const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   if (info) {

@@ -1215,6 +1215,10 @@ cudaError_t gram(const double2* V, int nv, int64_t vstride, const double2* w, in
                  double2* h, cudaStream_t st) {
   return gram_t(V, nv, vstride, w, N, partial, h, st);
 }
+cudaError_t gram(const float2* V, int nv, int64_t vstride, const float2* w, int64_t N, double2* partial, double2* h,
+                 cudaStream_t st) {
+  return gram_t(V, nv, vstride, w, N, partial, h, st);
+}
 cudaError_t gram3(const double2* V, const double* S, int nv, int64_t vstride, const double2* w, int64_t N,
                   double2* partial, double2* h, double* h3, cudaStream_t st) {
   const int nb = gram_blocks(N);
@@ -1235,6 +1239,7 @@ cudaError_t gram3(const double2* V, const double* S, int nv, int64_t vstride, co
 // coefficient h (always complex128) in the arithmetic of T
 template <typename T> __device__ __forceinline__ T coef(double2 h);
 template <> __device__ __forceinline__ double2 coef<double2>(double2 h) { return h; }
+template <> __device__ __forceinline__ float2 coef<float2>(double2 h) { return make_float2(float(h.x), float(h.y)); }
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_axpy_multi(const T* __restrict__ V, int nv, int64_t vstride,
@@ -1279,6 +1284,10 @@ cudaError_t axpy_multi_t(const T* V, int nv, int64_t vstride, const double2* h, 
   return cudaGetLastError();
 }
 cudaError_t axpy_multi(const double2* V, int nv, int64_t vstride, const double2* h, double2* w, double2* part,
+                       int64_t N, cudaStream_t st) {
+  return axpy_multi_t(V, nv, vstride, h, w, part, N, st);
+}
+cudaError_t axpy_multi(const float2* V, int nv, int64_t vstride, const double2* h, float2* w, float2* part,
                        int64_t N, cudaStream_t st) {
   return axpy_multi_t(V, nv, vstride, h, w, part, N, st);
 }
@@ -1351,6 +1360,9 @@ cudaError_t norm2_t(const T* w, int64_t N, double* partial, double* out, cudaStr
 cudaError_t norm2(const double2* w, int64_t N, double* partial, double* out, cudaStream_t st) {
   return norm2_t(w, N, partial, out, st);
 }
+cudaError_t norm2(const float2* w, int64_t N, double* partial, double* out, cudaStream_t st) {
+  return norm2_t(w, N, partial, out, st);
+}
 
 template <typename T>
 __global__ void k_scale_into(const T* __restrict__ w, const double* __restrict__ nrm, T* __restrict__ v, int64_t N) {
@@ -1360,6 +1372,10 @@ __global__ void k_scale_into(const T* __restrict__ w, const double* __restrict__
 }
 cudaError_t scale_into(const double2* w, const double* nrm, double2* v, int64_t N, cudaStream_t st) {
   k_scale_into<double2><<<grid_for(N), 256, 0, st>>>(w, nrm, v, N);
+  return cudaGetLastError();
+}
+cudaError_t scale_into(const float2* w, const double* nrm, float2* v, int64_t N, cudaStream_t st) {
+  k_scale_into<float2><<<grid_for(N), 256, 0, st>>>(w, nrm, v, N);
   return cudaGetLastError();
 }
 
@@ -1391,6 +1407,11 @@ cudaError_t combine(const double2* V, int k, int64_t vstride, const double2* y, 
   k_combine<double2><<<grid_for(N), 256, 0, st>>>(V, k, vstride, y, x, N);
   return cudaGetLastError();
 }
+cudaError_t combine(const float2* V, int k, int64_t vstride, const double2* y, float2* x, int64_t N,
+                    cudaStream_t st) {
+  k_combine<float2><<<grid_for(N), 256, 0, st>>>(V, k, vstride, y, x, N);
+  return cudaGetLastError();
+}
 
 template <typename T>
 __global__ void k_sub(const T* __restrict__ a, const T* __restrict__ b, T* __restrict__ o, int64_t N) {
@@ -1399,6 +1420,10 @@ __global__ void k_sub(const T* __restrict__ a, const T* __restrict__ b, T* __res
 }
 cudaError_t sub(const double2* a, const double2* b, double2* out, int64_t N, cudaStream_t st) {
   k_sub<double2><<<grid_for(N), 256, 0, st>>>(a, b, out, N);
+  return cudaGetLastError();
+}
+cudaError_t sub(const float2* a, const float2* b, float2* out, int64_t N, cudaStream_t st) {
+  k_sub<float2><<<grid_for(N), 256, 0, st>>>(a, b, out, N);
   return cudaGetLastError();
 }
 

@@ -150,6 +150,18 @@ cudaError_t gram3(const double2* V, const double* S, int nv, int64_t vstride, co
 cudaError_t axpy3_multi(const double2* V, const double* S, int nv, int64_t vstride, const double* h3, double2* w,
                         double2* part, int64_t N, cudaStream_t st);
 cudaError_t scale_into_sums(const double2* w, const double* nrm, double2* v, double* S, int64_t N, cudaStream_t st);
+// The same on complex64 vectors (the LS_MIXED32 correction solves): complex64
+// arithmetic per element, the Gram and norm partial sums and the coefficients
+// h, y, nrm in FP64.
+cudaError_t gram(const float2* V, int nv, int64_t vstride, const float2* w, int64_t N, double2* partial, double2* h,
+                 cudaStream_t st);
+cudaError_t axpy_multi(const float2* V, int nv, int64_t vstride, const double2* h, float2* w, float2* part,
+                       int64_t N, cudaStream_t st);
+cudaError_t norm2(const float2* w, int64_t N, double* partial, double* out, cudaStream_t st);
+cudaError_t scale_into(const float2* w, const double* nrm, float2* v, int64_t N, cudaStream_t st);
+cudaError_t combine(const float2* V, int k, int64_t vstride, const double2* y, float2* x, int64_t N,
+                    cudaStream_t st);
+cudaError_t sub(const float2* a, const float2* b, float2* out, int64_t N, cudaStream_t st);
 cudaError_t to_c64(const double2* a, float2* b, int64_t N, cudaStream_t st);
 cudaError_t to_c128(const float2* a, double2* b, int64_t N, cudaStream_t st);
 cudaError_t add_inplace(double2* x, const double2* e, int64_t N, cudaStream_t st);

@@ -62,11 +62,11 @@ def test_batch_apply_equals_single_applies(batch, prec_name):
             assert torch.equal(gi, ref)
 
 
-@pytest.mark.parametrize("prec_name", ["fp64", "mixed"])
+@pytest.mark.parametrize("prec_name", ["fp64", "mixed", "mixed32"])
 def test_batch_solve_matches_single_solves(batch, prec_name):
-    from paper_1509_05063_gb300 import LS_FP64, LS_MIXED
+    from paper_1509_05063_gb300 import LS_FP64, LS_MIXED, LS_MIXED32
     wls, plans, b = batch
-    prec = LS_FP64 if prec_name == "fp64" else LS_MIXED
+    prec = {"fp64": LS_FP64, "mixed": LS_MIXED, "mixed32": LS_MIXED32}[prec_name]
     parts = []
     for wl, p in zip(wls, plans):
         xy, _ = p.nodes()

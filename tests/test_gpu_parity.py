@@ -165,12 +165,12 @@ def test_mixed_solve_reaches_fp64_tolerance(disc):
     assert rel(s32.cpu().numpy(), s64.cpu().numpy()) < 1e-8
 
 
-@pytest.mark.parametrize("prec_name", ["fp64", "mixed"])
+@pytest.mark.parametrize("prec_name", ["fp64", "mixed", "mixed32"])
 def test_lockstep_multi_rhs_solve_equals_single_solves(disc, prec_name):
     """Three incident directions solved together (one batched apply per
     iteration, Arnoldi per RHS) give the single-RHS solutions."""
-    from paper_1509_05063_gb300 import LS_FP64, LS_MIXED
-    prec = LS_FP64 if prec_name == "fp64" else LS_MIXED
+    from paper_1509_05063_gb300 import LS_FP64, LS_MIXED, LS_MIXED32
+    prec = {"fp64": LS_FP64, "mixed": LS_MIXED, "mixed32": LS_MIXED32}[prec_name]
     dirs = [(1.0, 0.0), (0.6, 0.8), (-0.28, 0.96)]
     U = np.stack([W.plane_wave(disc.wl.kappa, d, disc.dz.x) for d in dirs])
     sol, info = disc.plan.solve(disc.dev(U), tol=1e-10, prec=prec)
@@ -208,6 +208,20 @@ def test_mixed_solution_and_far_field_within_1e10_of_fp64_oracle(disc):
     th = np.linspace(0, 2 * math.pi, 32, endpoint=False)
     ff = disc.plan.farfield(sol, np.stack([np.cos(th), np.sin(th)], -1)).cpu().numpy()[0]
     assert rel(ff, far_field(disc.dz, ref, th)) < 1e-10
+
+
+def test_mixed32_solution_within_1e10_of_fp64_oracle(disc):
+    """LS_MIXED32 (complex64 apply and complex64 Arnoldi vectors in the
+    correction solves, FP64 refinement) against the FP64 oracle's solution:
+    the outer FP64 residual decides, so the solution meets the same 1e-10."""
+    from paper_1509_05063_gb300 import LS_MIXED32, LSError
+    ui = W.plane_wave(disc.wl.kappa, (0.6, 0.8), disc.dz.x)
+    ref, _, _ = gmres(disc.op.apply, ui, tol=1e-14, restart=200)
+    sol, info = disc.plan.solve(disc.dev(ui), tol=1e-12, prec=LS_MIXED32)
+    assert info["converged"] and info["refinements"] >= 2 and info["residual"] <= 1e-12
+    assert rel(sol.cpu().numpy(), disc.to_plan(ref)) < 1e-10
+    with pytest.raises(LSError):      # solve-only precision
+        disc.plan.apply(torch.zeros(disc.plan.N, dtype=torch.complex64, device="cuda:0"), prec=LS_MIXED32)
 
 
 def test_cfg1_solution_against_bessel_series():
