@@ -459,7 +459,7 @@ def main():
         "metric": METRIC, "value": value, "unit": "matvecs/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms64 / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"cfg2 kite kappa=20 N={N} nnz_near={nnz} lattice {M}x{M}",
+        "config": {"workload": f"cfg2 kite kappa=20 N={N}",
                    "N": N, "nnz_near": nnz, "fft_M": M, "L": info["L"], "N_eq": info["N_eq"],
                    "n_fb": info["n_fb"], "parallelism": f"replicas x{world}",
                    "l2": "inputs larger than L2 (FP64 near-field weights %.1f GB)" % (nnz * 24 / 1e9),
