@@ -154,8 +154,11 @@ class Discretisation:
     ix * cart_ny + iy order.
     """
 
-    def __init__(self, wl: Workload):
+    def __init__(self, wl: Workload, interp=None):
         self.wl = wl
+        # None: degree-p Lagrange interpolation in the singular rules; (F, pf):
+        # the Fourier-refined comparison variant (see quadrature.py)
+        self.interp = interp
         n1, n2 = wl.n1, wl.n2
         ii, jj = np.meshgrid(np.arange(n1), np.arange(n2), indexing="ij")
         ii, jj = ii.ravel(), jj.ravel()

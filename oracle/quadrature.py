@@ -19,7 +19,12 @@ rule, the (1 - eta) part by the regular rule on the patch grid.
 * off-grid values phi_k are obtained by tensor-product Lagrange interpolation of
   degree p on the patch grid (reading of the paper's "Fourier refined polynomial
   interpolation"; one-sided near the ends of the transverse direction,
-  periodic along the collar).
+  periodic along the collar).  A comparison variant takes the paper's words
+  literally (Discretisation(..., interp=(F, pf))): the samples are first refined
+  F-fold by band-limited (FFT) interpolation, then Lagrange of degree pf on the
+  refined grid; along the collar (periodic) and along both axes of the
+  Cartesian patch (whose density vanishes near the edges of its grid), while
+  the transverse collar direction keeps degree-p Lagrange.
 
 All rules act in grid-index units (see geometry.py); a rule returns, for one
 target, node ids and coefficients c such that the rule equals sum c[k] u[ids[k]]
@@ -74,23 +79,72 @@ def stencil_start(x, p: int):
 
 
 # ---------------------------------------------------------------- interpolation
-def window_accumulate(f, a, b, sa, sb, oa, ob, Wa, Wb, p):
+def window_accumulate(f, a, b, sa, sb, oa, ob, Wa, Wb, p, pb=None):
     """sum over quadrature points of f * l_i(a) l_j(b) into per-target windows.
 
     f, a, b, sa, sb: (T, P) values, positions and stencil starts; oa, ob: (T,)
-    window origins.  Returns (T, Wa, Wb): coefficient of grid point
-    (oa + i, ob + j) in the interpolated quadrature sum."""
+    window origins; degree p along a and pb (default p) along b.  Returns
+    (T, Wa, Wb): coefficient of grid point (oa + i, ob + j) in the
+    interpolated quadrature sum."""
+    pb = p if pb is None else pb
     T, P = a.shape
     la = lagrange(a, sa, p)                      # (T, P, p+1)
-    lb = lagrange(b, sb, p)
+    lb = lagrange(b, sb, pb)
     Ma = np.zeros((T, P, Wa), np.complex128)
     Mb = np.zeros((T, P, Wb))
     ia = (sa - oa[:, None])[..., None] + np.arange(p + 1)
-    ib = (sb - ob[:, None])[..., None] + np.arange(p + 1)
+    ib = (sb - ob[:, None])[..., None] + np.arange(pb + 1)
     # the p+1 stencil columns of one point are distinct, so plain assignment suffices
     np.put_along_axis(Ma, ia, la * f[..., None], axis=2)
     np.put_along_axis(Mb, ib, lb, axis=2)
     return np.matmul(np.swapaxes(Ma, 1, 2), Mb)   # (T, Wa, Wb)
+
+
+def trig_kernel(t, n: int):
+    """Band-limited interpolation kernel of n periodic unit-spaced samples at
+    offset t: (1/n) sum over the n lowest frequencies of exp(2 pi i k t / n),
+    the Nyquist term of even n split symmetrically; closed forms
+    sin(pi t) / (n sin(pi t / n)) (n odd) and sin(pi t) / (n tan(pi t / n)) (n
+    even).  1 at t = 0 (mod n), 0 at the other integers."""
+    t = np.asarray(t, np.float64)
+    tm = t - n * np.round(t / n)                 # in [-n/2, n/2]
+    small = np.abs(tm) < 1e-12
+    tt = np.where(small, 0.5, tm)
+    den = n * (np.sin(np.pi * tt / n) if n % 2 else np.tan(np.pi * tt / n))
+    return np.where(small, 1.0, np.sin(np.pi * tt) / den)
+
+
+def refine_matrix(origin, W: int, n: int, F: int):
+    """(T, W, n): the band-limited interpolant of n periodic coarse samples at
+    the fine points (origin + m) / F, m < W, as weights on the coarse samples."""
+    m = np.asarray(origin)[:, None] + np.arange(W)
+    return trig_kernel(m[:, :, None] / F - np.arange(n)[None, None, :], n)
+
+
+def fourier_windows(f, a, b, a_c, b_c, Ra, Rb, p, F, pf, na, nb, refine_b):
+    """Windows of the Fourier-refined variant.  Along a (periodic, na samples):
+    degree-pf Lagrange at a F on the F-fold refined grid, then the refined
+    samples as band-limited interpolants of the coarse ones; along b the same
+    when refine_b (nb samples), else degree-p Lagrange on the coarse lines
+    (clamped to 0..nb-1).  a_c, b_c: (T,) window centres (coarse index units).
+    Returns (T, na, Wb) windows with origins 0 (and Wb = nb)."""
+    af = a * F
+    saf = stencil_start(af, pf)
+    oaf = np.floor((a_c - Ra) * F).astype(np.int64) - pf // 2 - 1
+    Waf = 2 * int(math.ceil(Ra * F)) + pf + 4
+    if refine_b:
+        bf = b * F
+        sbf = stencil_start(bf, pf)
+        obf = np.floor((b_c - Rb) * F).astype(np.int64) - pf // 2 - 1
+        Wbf = 2 * int(math.ceil(Rb * F)) + pf + 4
+        Mf = window_accumulate(f, af, bf, saf, sbf, oaf, obf, Waf, Wbf, pf)
+        Db = refine_matrix(obf, Wbf, nb, F)                 # (T, Wbf, nb)
+        Mf = np.matmul(Mf, Db)                               # (T, Waf, nb)
+    else:
+        sb = np.clip(stencil_start(b, p), 0, nb - 1 - p)
+        Mf = window_accumulate(f, af, b, saf, sb, oaf, np.zeros(len(a), np.int64), Waf, nb, pf, p)
+    Da = refine_matrix(oaf, Waf, na, F)                      # (T, Waf, na)
+    return np.matmul(np.swapaxes(Da, 1, 2), Mf)               # (T, na, nb)
 
 
 # ---------------------------------------------------------------- rules
@@ -139,6 +193,13 @@ def polar_rule(dz, chart: int, tgt, ax, bx):
     else:
         Y, J = geo.cart_map(wl, a, b)
     f = w * J * green(wl.kappa, dz.x[tgt][:, None, :], Y)
+    fr = getattr(dz, "interp", None)
+    if fr is not None:
+        F, pf = fr
+        na, nb = (wl.n1, wl.n2) if chart == 0 else (wl.cart_nx, wl.cart_ny)
+        Mw = fourier_windows(f, a, b, ax, bx, Ra, Rb, p, F, pf, na, nb, refine_b=chart == 1)
+        z = np.zeros(len(tgt), np.int64)
+        return window_triplets(dz, chart, Mw, z, z)
     sa = stencil_start(a, p)
     sb = stencil_start(b, p)
     oa = np.floor(ax - Ra).astype(np.int64) - p // 2 - 1
@@ -242,6 +303,13 @@ def boundary_rule(dz, tgt, i, j: int):
     b = np.broadcast_to(bl[B], a.shape)
     Y, J = geo.collar_map(wl, a, b)
     f = w1 * J * green(wl.kappa, dz.x[tgt][:, None, :], Y)
+    fr = getattr(dz, "interp", None)
+    if fr is not None:
+        F, pf = fr
+        Mw = fourier_windows(f, a, b, i.astype(np.float64), np.full(len(tgt), float(j)), Ra, Rb, p, F, pf,
+                             wl.n1, wl.n2, refine_b=False)
+        z = np.zeros(len(tgt), np.int64)
+        return window_triplets(dz, 0, Mw, z, z)
     sa = stencil_start(a, p)
     sb = np.clip(stencil_start(b, p), 0, wl.n2 - 1 - p)
     oa = i - int(math.ceil(Ra)) - p // 2 - 1
