@@ -106,11 +106,14 @@ def near_matrix(dz: Discretisation, cells: Cells, rows=None, chunk: int = 512):
 class Accelerator:
     """Far (non-adjacent) part of K via equivalent sources and the lattice FFT."""
 
-    def __init__(self, dz: Discretisation, cells: Cells | None = None, local_basis: str = "fb"):
+    def __init__(self, dz: Discretisation, cells: Cells | None = None, local_basis: str = "fb",
+                 local_points: str = "cell"):
         wl = dz.wl
         self.dz = dz
         if local_basis not in ("fb", "pw"):
             raise ValueError(local_basis)
+        if local_points not in ("cell", "boundary", "two_faces"):
+            raise ValueError(local_points)
         self.local_basis = local_basis
         self.cells = cells if cells is not None else Cells(dz)
         k = self.kappa = wl.kappa
@@ -132,10 +135,17 @@ class Accelerator:
         self.coll = self._collocation(ncoll)
         A = self._es_field(self.coll[:, 0], self.coll[:, 1])        # (ncoll, n_es)
         self.Asvd = _svd(A)
-        # closed-cell lattice points (p = a * (Ne + 1) + b) relative to the corner
+        # lattice points of the local fit relative to the corner: the closed cell
+        # (faces and interior; the build's reading), or comparison variants: its
+        # boundary only (the points on all four faces), or only the two
+        # x1-faces that carry equivalent sources (the paper-literal two-face data)
         la, lb = np.meshgrid(np.arange(Ne + 1), np.arange(Ne + 1), indexing="ij")
-        self.loc_a, self.loc_b = la.ravel(), lb.ravel()
-        self.n_loc = (Ne + 1) ** 2
+        la, lb = la.ravel(), lb.ravel()
+        on_x1_face = (la == 0) | (la == Ne)
+        keep = {"cell": np.ones(la.shape, bool), "two_faces": on_x1_face,
+                "boundary": on_x1_face | (lb == 0) | (lb == Ne)}[local_points]
+        self.loc_a, self.loc_b = la[keep], lb[keep]
+        self.n_loc = len(self.loc_a)
         # local expansion (Fourier-Bessel form of Eq. PWE)
         self.nfb = wl.n_fb
         self.Rref = H / math.sqrt(2.0)

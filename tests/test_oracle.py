@@ -299,6 +299,25 @@ def test_literal_plane_waves_against_fourier_bessel_local_expansion():
     assert errs["pw"] > 10 * errs["fb"]
 
 
+def test_local_fit_points_boundary_suffices_two_faces_fail():
+    """Lattice points of the local fit: the closed cell (the build), its four
+    faces, or only the two x1-faces that carry equivalent sources (the
+    paper-literal two-face data).  Helmholtz data on the whole cell boundary
+    determine the local expansion (kappa H / sqrt(2) is below the first zero of
+    J_0), so the boundary fit reaches the closed-cell accuracy; two-face data
+    leave it underdetermined and the far part fails."""
+    dz = Discretisation(_accel_wl(12))
+    u = W.random_density(dz.N)[0]
+    errs = {}
+    for pts in ("cell", "boundary", "two_faces"):
+        acc = Accelerator(dz, local_points=pts)
+        vf = acc.apply_far(u)
+        ref = acc.direct_far(u)
+        errs[pts] = np.linalg.norm(vf - ref) / np.linalg.norm(ref)
+    assert errs["cell"] < 1e-10 and errs["boundary"] < 1e-10
+    assert errs["two_faces"] > 1e-2
+
+
 def test_fourier_refined_interpolation_variant(K1_level1, K1_level2):
     """The paper's Fourier refined polynomial interpolation taken literally
     (4-fold band-limited refinement of the samples, degree-5 Lagrange on the
