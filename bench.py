@@ -466,7 +466,7 @@ def main():
                    "plan_seconds": info["plan_seconds"], "device_bytes": info["device_bytes"]},
         "e2e": {"value": world * args.steps / (ms_e2e * 1e-3), "unit": "matvecs/s",
                 "h2d_bytes_per_step": N * 16, "d2h_bytes_per_step": N * 16},
-        "roofline": {"bound": "alu", "kernel": "k_near_eval<double2>",
+        "roofline": {"bound": "alu", "kernel": "k_near_eval5<double2,1>",
                      "achieved": near_flops / t_near64 / 1e12, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": near_flops / t_near64 / 1e12 / FP64_PEAK_TFLOPS, "traffic": traffic.get("fp64"),
                      "peak_source": "derived: 152 SMs x 2070 MHz x 2 FP64 FMA/clk/SM",
@@ -477,7 +477,7 @@ def main():
         "clocks": clocks,
         "mixed": {"value": world * args.steps / (ms32 * 1e-3), "unit": "matvecs/s", "dtype": "f32",
                   "ms_per_step": ms32 / args.steps,
-                  "roofline": {"bound": "hbm", "kernel": "k_near_eval<float2>", "achieved": ach32,
+                  "roofline": {"bound": "hbm", "kernel": "k_near_eval<float2,1>", "achieved": ach32,
                                "peak": peak, "unit": "GB/s", "frac": ach32 / peak, "peak_source": peak_src,
                                "bytes_per_launch": near_bytes(8), "traffic": traffic.get("mixed"),
                                "launch_ms": t_near32 * 1e3}},
