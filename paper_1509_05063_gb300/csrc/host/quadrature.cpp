@@ -32,13 +32,30 @@ static inline cd green(double kappa, double dx, double dy) {
   return cd(0.0, 0.25) * cd(::j0(z), ::y0(z));
 }
 
-static void lagrange(double x, int64_t start, int p, double* out) {
-  for (int k = 0; k <= p; ++k) {
-    double v = 1.0;
-    for (int m = 0; m <= p; ++m)
-      if (m != k) v *= (x - double(start + m)) / double(k - m);
-    out[k] = v;
+// 1 / prod_{m != k} (k - m) = (-1)^(p-k) / (k! (p-k)!) for the integer nodes 0..p
+struct LagrangeDen {
+  double c[32][32] = {};
+  LagrangeDen() {
+    double f[32];
+    f[0] = 1.0;
+    for (int i = 1; i < 32; ++i) f[i] = f[i - 1] * double(i);
+    for (int p = 0; p < 32; ++p)
+      for (int k = 0; k <= p; ++k) c[p][k] = ((p - k) % 2 ? -1.0 : 1.0) / (f[k] * f[p - k]);
   }
+};
+static const LagrangeDen kLagDen;
+
+// Lagrange basis on the integer nodes start..start+p at x:
+// l_k(x) = prod_{m != k} (x - x_m) / prod_{m != k} (k - m), the numerator from
+// prefix and suffix products (no division)
+static void lagrange(double x, int64_t start, int p, double* out) {
+  double d[32], pre[33], suf[33];
+  for (int m = 0; m <= p; ++m) d[m] = x - double(start + m);
+  pre[0] = 1.0;
+  for (int m = 0; m <= p; ++m) pre[m + 1] = pre[m] * d[m];
+  suf[p + 1] = 1.0;
+  for (int m = p; m >= 0; --m) suf[m] = suf[m + 1] * d[m];
+  for (int k = 0; k <= p; ++k) out[k] = pre[k] * suf[k + 1] * kLagDen.c[p][k];
 }
 
 namespace {
