@@ -90,10 +90,23 @@ struct RowBuilder {
   Window win;
   // polar template (relative offsets in unit disc) for the radial/angular rule
   std::vector<double> tr, tc, ts, tw;   // rho, cos, sin, weight (without Ra Rb)
+  // regular term G(h d) (1 - eta) of a Cartesian target and a Cartesian source
+  // at grid offset d = (da, db), |da|, |db| <= D: both factors depend on d only
+  int D = 0;
+  std::vector<cd> gcart;
 
   explicit RowBuilder(const Plan2D& plan)
       : P(plan), nd(plan.nodes), g(plan.geo.g), o(plan.opt) {
     Rbc = std::min(o.R_b, g.tau0 * (g.n2 - 1));
+    // the 3 x 3 block spans less than two cells each way from a target's cell
+    D = int(std::ceil(2.0 * o.H / g.h)) + 2;
+    gcart.assign(size_t(2 * D + 1) * (2 * D + 1), cd(0.0));
+    for (int da = -D; da <= D; ++da)
+      for (int db = -D; db <= D; ++db) {
+        const double ome = (da == 0 && db == 0) ? 0.0 : 1.0 - cutoff(std::hypot(double(da), double(db)) / o.R_cart,
+                                                                        o.chi_s0);
+        if (ome != 0.0) gcart[size_t(da + D) * (2 * D + 1) + (db + D)] = green(P.kappa, da * g.h, db * g.h) * ome;
+      }
     const int q = o.q_polar;
     for (int ks = 1; ks < o.n_rho; ++ks) {
       const double s = double(ks) / o.n_rho;
@@ -288,6 +301,14 @@ struct RowBuilder {
         const int nc = nj * nd.L + ni;
         for (int64_t l = nd.cell_start[nc]; l < nd.cell_start[nc + 1]; ++l) {
           if (nd.wfac[l] == 0.0) continue;
+          if (nd.chart[q] == 1 && nd.chart[l] == 1) {
+            const int64_t da = std::llround(nd.ga[l] - nd.ga[q]), db = std::llround(nd.gb[l] - nd.gb[q]);
+            if (std::abs(da) <= D && std::abs(db) <= D) {
+              const cd v = gcart[size_t(da + D) * (2 * D + 1) + (db + D)];
+              if (v != 0.0) ents.emplace_back(l, v * nd.wfac[l]);
+              continue;
+            }
+          }
           const double ome = 1.0 - eta(q, l);
           if (ome == 0.0) continue;
           ents.emplace_back(l, green(P.kappa, nd.x[q] - nd.x[l], nd.y[q] - nd.y[l]) * (nd.wfac[l] * ome));
