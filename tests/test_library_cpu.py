@@ -105,11 +105,12 @@ def test_host_plan_matches_oracle_discretisation(lib, make):
     assert np.max(np.abs(got - ref)) <= 1e-13 * np.max(np.abs(ref))
 
 
-def test_host_accelerator_matrices_reproduce_oracle_far_field(lib):
+@pytest.mark.parametrize("make", [_small_disc, _small_kite])
+def test_host_accelerator_matrices_reproduce_oracle_far_field(lib, make):
     """Run the accelerator's steps in numpy with the library's matrices (P_c,
     B^+, B^+ T_o, Phi, kernel tables) and compare with the oracle's far part."""
     from paper_1509_05063_gb300 import HostPlan
-    wl = _small_disc()
+    wl = make()
     hp = HostPlan(wl, W.n2_of(wl))
     xy, canon, _ = hp.nodes()
     dz = Discretisation(wl)
