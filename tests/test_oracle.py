@@ -351,3 +351,85 @@ def test_band_limited_kernel_reproduces_trigonometric_polynomials():
             ks = min(k, (n - 1) // 2)
             f = lambda t: np.cos(2 * np.pi * k * t / n) + 0.3 * np.sin(2 * np.pi * ks * t / n)
             assert np.max(np.abs(w @ f(j) - f(x))) < 1e-12
+
+
+# ---------------------------------------------------------------- 3-D references
+def _green3(kappa, d):
+    r = np.linalg.norm(d, axis=-1)
+    return np.exp(1j * kappa * r) / (4 * np.pi * r)
+
+
+def _sphere_dirs(nmu=60, nphi=120):
+    mu, wmu = np.polynomial.legendre.leggauss(nmu)
+    phi = 2 * np.pi * np.arange(nphi) / nphi
+    MU, PHI = np.meshgrid(mu, phi, indexing="ij")
+    st = np.sqrt(1 - MU ** 2)
+    s = np.stack([st * np.cos(PHI), st * np.sin(PHI), MU], -1).reshape(-1, 3)
+    w = (wmu[:, None] * np.full(nphi, 2 * np.pi / nphi)[None, :]).ravel()
+    return s, w
+
+
+def _ray_length(x, s, a):
+    """Distance from the interior point x to the sphere |y| = a along s."""
+    xs = s @ x
+    return -xs + np.sqrt(xs ** 2 - x @ x + a * a)
+
+
+def test_ball_volume_potential_against_quadrature_along_rays():
+    """Interior points: in spherical coordinates about the target the integral
+    of G over the ball is (1/4 pi) over directions of int_0^R rho exp(i k rho),
+    whose radial part is exact; Gauss-Legendre x trapezoid over directions."""
+    k, a = 2.0, 1.0
+    s, w = _sphere_dirs()
+    pts = np.array([[0.0, 0.0, 0.0], [0.3, -0.2, 0.4], [0.0, 0.0, 0.85], [-0.5, 0.5, 0.5]])
+    for x in pts:
+        R = _ray_length(x, s, a)
+        rad = np.exp(1j * k * R) * (R / (1j * k) + 1 / k ** 2) - 1 / k ** 2
+        got = np.sum(w * rad) / (4 * np.pi)
+        ref = exact.ball_volume_potential_const(k, a, x)
+        assert abs(got - ref) < 1e-11 * abs(ref)
+
+
+def test_sphere_series_reduces_to_plane_wave_and_obeys_optical_theorem():
+    """n = 1: the total field is exp(i kappa z) (Jacobi-Anger); n^2 = 2: the
+    scattered power from |f|^2 integrated over directions equals the
+    extinction (4 pi / kappa) Im f(0) (no absorption)."""
+    k, a = 2.0, 1.0
+    x = W.random_density(3 * 40, seed=7)[0].real.reshape(40, 3) * 1.2
+    assert np.max(np.abs(exact.sphere_total_field(k, 1.0, a, x) - np.exp(1j * k * x[:, 2]))) < 1e-12
+    mu, wmu = np.polynomial.legendre.leggauss(200)
+    f = exact.sphere_far_field(k, 2.0, a, np.arccos(mu))
+    scat = 2 * np.pi * np.sum(wmu * np.abs(f) ** 2)
+    ext = 4 * np.pi / k * exact.sphere_far_field(k, 2.0, a, 0.0).imag
+    assert abs(scat - ext) < 1e-12 * ext
+
+
+def test_sphere_series_satisfies_the_3d_lippmann_schwinger_equation():
+    """u - u^i = kappa^2 (n^2 - 1) int_ball G(x, y) u(y) dy (the 3-D volume
+    equation with m = 1 - n^2), with u the series inside the ball: at exterior
+    points by Gauss quadrature over the ball, at an interior point in spherical
+    coordinates about it (the rho^2 of the volume element cancels G's pole)."""
+    k, n2, a = 2.0, 2.0, 1.0
+    # exterior targets: smooth integrand over the ball
+    r, wr = np.polynomial.legendre.leggauss(48)
+    r, wr = (r + 1) * a / 2, wr * a / 2
+    s, ws = _sphere_dirs(48, 96)
+    Y = (r[:, None, None] * s[None, :, :]).reshape(-1, 3)
+    wY = (wr[:, None] * r[:, None] ** 2 * ws[None, :]).ravel()
+    uY = exact.sphere_total_field(k, n2, a, Y)
+    for x in (np.array([0.0, 0.0, 1.5]), np.array([1.2, -0.9, 0.4])):
+        lhs = exact.sphere_total_field(k, n2, a, x[None])[0] - np.exp(1j * k * x[2])
+        rhs = k ** 2 * (n2 - 1) * np.sum(wY * _green3(k, x[None] - Y) * uY)
+        assert abs(lhs - rhs) < 1e-11 * abs(lhs)
+    # interior target: rays from x, Gauss-Legendre in rho on [0, R(s)]
+    x = np.array([0.2, -0.1, 0.3])
+    s, ws = _sphere_dirs(40, 80)
+    R = _ray_length(x, s, a)
+    t, wt = np.polynomial.legendre.leggauss(40)
+    rho = (t[None, :] + 1) * R[:, None] / 2                          # (dirs, 40)
+    wrho = wt[None, :] * R[:, None] / 2
+    Yi = x[None, None, :] + rho[..., None] * s[:, None, :]
+    ui = exact.sphere_total_field(k, n2, a, Yi.reshape(-1, 3)).reshape(rho.shape)
+    integral = np.sum(ws[:, None] * wrho * rho * np.exp(1j * k * rho) / (4 * np.pi) * ui)
+    lhs = exact.sphere_total_field(k, n2, a, x[None])[0] - np.exp(1j * k * x[2])
+    assert abs(lhs - k ** 2 * (n2 - 1) * integral) < 1e-10 * abs(lhs)
