@@ -174,6 +174,36 @@ struct RowBuilder {
     flush_window(chart);
   }
 
+  // The Cartesian polar rule about a target on a Cartesian grid point: the
+  // template offsets, their Lagrange weights and G(x_q - y) depend only on the
+  // offset from the target, so the window (relative to the target) is computed
+  // once and shifted; only the node ids and the m omega factors differ per target.
+  std::vector<cd> cart_win;
+  int64_t cw_oa = 0, cw_ob = 0;
+  int cw_Wa = 0, cw_Wb = 0;
+
+  void polar_cart_grid(int64_t ia, int64_t ib) {
+    if (cart_win.empty()) {
+      const double R = o.R_cart;
+      const int p = o.p;
+      win.reset(int64_t(std::floor(-R)) - p / 2 - 1, int64_t(std::floor(-R)) - p / 2 - 1,
+                2 * int(std::ceil(R)) + p + 4, 2 * int(std::ceil(R)) + p + 4);
+      for (size_t t = 0; t < tr.size(); ++t) {
+        const double a = R * tr[t] * tc[t], b = R * tr[t] * ts[t];
+        const cd f = (tw[t] * R * R) * (g.h * g.h) * green(P.kappa, -a * g.h, -b * g.h);
+        win.add(p, a, b, int64_t(std::floor(a)) - p / 2, int64_t(std::floor(b)) - p / 2, f);
+      }
+      cart_win = win.v;
+      cw_oa = win.oa; cw_ob = win.ob; cw_Wa = win.Wa; cw_Wb = win.Wb;
+    }
+    win.oa = ia + cw_oa;
+    win.ob = ib + cw_ob;
+    win.Wa = cw_Wa;
+    win.Wb = cw_Wb;
+    win.v = cart_win;
+    flush_window(1);
+  }
+
   // split Newton-Cotes nodes across the collar for a target on line j
   std::map<double, double> split_nc(int j) const {
     const std::vector<double> nc = newton_cotes(o.Q);
@@ -316,7 +346,10 @@ struct RowBuilder {
       }
     }
     // singular rules
-    if (needs_cart_rule(q)) polar(1, q, nd.ga[q], nd.gb[q]);
+    if (needs_cart_rule(q)) {
+      if (nd.chart[q] == 1) polar_cart_grid(std::llround(nd.ga[q]), std::llround(nd.gb[q]));
+      else polar(1, q, nd.ga[q], nd.gb[q]);
+    }
     if (nd.chart[q] == 0) boundary(q, nd.gi[q], nd.gj[q]);
     else if (nd.cb[q] <= g.n2 - 1) polar(0, q, nd.ca[q], nd.cb[q]);
     std::sort(ents.begin(), ents.end(),
