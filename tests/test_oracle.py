@@ -433,3 +433,36 @@ def test_sphere_series_satisfies_the_3d_lippmann_schwinger_equation():
     integral = np.sum(ws[:, None] * wrho * rho * np.exp(1j * k * rho) / (4 * np.pi) * ui)
     lhs = exact.sphere_total_field(k, n2, a, x[None])[0] - np.exp(1j * k * x[2])
     assert abs(lhs - k ** 2 * (n2 - 1) * integral) < 1e-10 * abs(lhs)
+
+
+def test_ball_discretisation_pou_and_volume_integrals():
+    """3-D nodes (six cubed-sphere shell patches + interior grid): the surface
+    partition sums to one; the blended surface rule integrates the solid angle
+    4 pi with super-algebraic convergence; volume, |x|^2 and a plane wave over the ball converge at
+    high order to their exact values (4 pi/3, 4 pi/5, 4 pi (sin k - k cos k)/k^3)."""
+    import math
+    from oracle.geometry3d import Ball3, Discretisation3, face_direction, surface_pou
+    rng = np.random.default_rng(1)
+    d = rng.normal(size=(2000, 3))
+    d /= np.linalg.norm(d, axis=1)[:, None]
+    assert np.max(np.abs(sum(surface_pou(F, d, 0.25) for F in range(6)) - 1)) < 1e-14
+    # solid angle from the blended equiangular trapezoid rule
+    for nf, tol in ((33, 5e-5), (65, 2e-6), (129, 1e-9)):     # faster than any power of nf
+        g = np.linspace(-math.pi / 4 - 0.25, math.pi / 4 + 0.25, nf)
+        XI, ETA = np.meshgrid(g, g, indexing="ij")
+        tot = 0.0
+        for F in range(6):
+            dd, dom = face_direction(F, XI, ETA)
+            tot += np.sum(dom * surface_pou(F, dd, 0.25)) * (g[1] - g[0]) ** 2
+        assert abs(tot - 4 * math.pi) < tol * 4 * math.pi
+    k = 2.0
+    exact_vals = (4 * math.pi / 3, 4 * math.pi / 5, 4 * math.pi * (math.sin(k) - k * math.cos(k)) / k ** 3)
+    errs = []
+    for nf, ns, h in ((13, 5, 0.2), (25, 9, 0.1), (49, 17, 0.05)):
+        dz = Discretisation3(Ball3(n_f=nf, n_s=ns, h=h))
+        vals = (dz.integrate(lambda x: np.ones(len(x))), dz.integrate(lambda x: np.sum(x ** 2, 1)),
+                dz.integrate(lambda x: np.exp(1j * k * (0.6 * x[:, 0] + 0.8 * x[:, 2]))))
+        errs.append([abs(v - e) / abs(e) for v, e in zip(vals, exact_vals)])
+    errs = np.array(errs)
+    assert np.all(errs[-1] < 5e-5)
+    assert np.all(errs[0] / errs[1] > 8) and np.all(errs[1] / errs[2] > 30)
