@@ -136,6 +136,8 @@ class Discretisation3:
         depth = (b.a - np.linalg.norm(P, axis=-1)) / b.w
         omi = np.where(depth > 0, 1.0 - smooth_step((depth - b.tau0) / (b.tau1 - b.tau0)), 0.0)
         keep = omi > 0.0
+        self.grid_m = m                               # grid indices -m..m per axis
+        self.grid_omega = omi.reshape(GX.shape)       # omega_I on the whole grid (0 outside)
         X.append(P[keep])
         W.append(np.full(int(keep.sum()), b.h ** 3))
         OM.append(omi[keep])
