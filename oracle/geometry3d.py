@@ -116,7 +116,9 @@ class Discretisation3:
         ws = composite_nc(ns, b.Q) * (s[1] - s[0])
         XI, ETA, S = np.meshgrid(g, g, s, indexing="ij")
         WS = np.broadcast_to(ws, S.shape)
-        X, W, OM, CH, FC = [], [], [], [], []
+        self.g, self.dg, self.s, self.ds, self.half = g, dg, s, s[1] - s[0], half
+        X, W, OM, CH, FC, PS, IJK = [], [], [], [], [], [], []
+        II, JJ, KK = np.meshgrid(np.arange(nf), np.arange(nf), np.arange(ns), indexing="ij")
         for F in range(6):
             d, dom = face_direction(F, XI, ETA)
             r = b.a - S * b.w
@@ -128,6 +130,8 @@ class Discretisation3:
             OM.append(smooth_step((S[keep] - b.tau0) / (b.tau1 - b.tau0)))
             CH.append(np.zeros(int(keep.sum()), np.int8))
             FC.append(np.full(int(keep.sum()), F, np.int8))
+            PS.append(psi[keep])
+            IJK.append(np.stack([II[keep], JJ[keep], KK[keep]], -1))
         # interior Cartesian grid: omega_I = 1 - omega_B(depth / w), kept where > 0
         m = int(math.ceil(b.a / b.h))
         ax = b.h * np.arange(-m, m + 1)
@@ -143,6 +147,7 @@ class Discretisation3:
         OM.append(omi[keep])
         CH.append(np.ones(int(keep.sum()), np.int8))
         FC.append(np.full(int(keep.sum()), -1, np.int8))
+        gidx = np.stack(np.unravel_index(np.nonzero(keep)[0], GX.shape), -1)
         self.x = np.concatenate(X)
         self.w = np.concatenate(W)
         self.omega = np.concatenate(OM)
@@ -151,6 +156,14 @@ class Discretisation3:
         self.N = len(self.x)
         self.n_shell = int((self.chart == 0).sum())
         self.n_cart = self.N - self.n_shell
+        # shell nodes: partition share psi_F and face-grid indices; grid -> node maps
+        self.psi = np.concatenate(PS + [np.zeros(self.n_cart)])
+        self.fijk = np.concatenate(IJK + [np.full((self.n_cart, 3), -1)])
+        self.face_node = np.full((6, nf, nf, ns), -1, np.int64)
+        sh = np.arange(self.n_shell)
+        self.face_node[self.face[sh], self.fijk[sh, 0], self.fijk[sh, 1], self.fijk[sh, 2]] = sh
+        self.cart_node = np.full(GX.shape, -1, np.int64)
+        self.cart_node[gidx[:, 0], gidx[:, 1], gidx[:, 2]] = self.n_shell + np.arange(self.n_cart)
 
     def integrate(self, f):
         """sum_q w_q omega_q f(x_q) for values f (N,) or a callable of x (N, 3)."""
