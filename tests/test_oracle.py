@@ -509,3 +509,24 @@ def test_3d_operator_rows_against_ball_potential():
         ref = exact.ball_volume_potential_const(2.0, 1.0, dz.x[tg])
         errs.append(np.max(np.abs(K - ref)) / np.max(np.abs(ref)))
     assert errs[2] < 2e-4 and errs[0] / errs[1] > 8 and errs[1] / errs[2] > 8
+
+
+def test_sphere_series_satisfies_the_discrete_3d_equation():
+    """The 3-D operator with the penetrable sphere's material (n^2 = 2,
+    m = 1 - n^2): the exact series field u_e makes the residual
+    u_e + kappa^2 K[m u_e] - u^i at random shell and interior nodes fall at high
+    order as the grids are refined (the discrete equation converges to the
+    continuous one on its solution)."""
+    from oracle.geometry3d import Ball3, Discretisation3
+    from oracle.quadrature3d import k_row
+    rng = np.random.default_rng(5)
+    k, n2 = 2.0, 2.0
+    res = []
+    for nf, ns, h in ((13, 5, 0.2), (25, 9, 0.1), (49, 17, 0.05)):
+        dz = Discretisation3(Ball3(n_f=nf, n_s=ns, h=h))
+        tg = np.concatenate([rng.choice(dz.n_shell, 6, replace=False),
+                             dz.n_shell + rng.choice(dz.n_cart, 6, replace=False)])
+        ue = exact.sphere_total_field(k, n2, 1.0, dz.x)
+        r = [ue[q] + k * k * (k_row(dz, k, q) @ ((1 - n2) * ue)) - np.exp(1j * k * dz.x[q, 2]) for q in tg]
+        res.append(np.max(np.abs(r)))
+    assert res[2] < 5e-4 and res[0] / res[1] > 8 and res[1] / res[2] > 8
