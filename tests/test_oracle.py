@@ -530,3 +530,114 @@ def test_sphere_series_satisfies_the_discrete_3d_equation():
         r = [ue[q] + k * k * (k_row(dz, k, q) @ ((1 - n2) * ue)) - np.exp(1j * k * dz.x[q, 2]) for q in tg]
         res.append(np.max(np.abs(r)))
     assert res[2] < 5e-4 and res[0] / res[1] > 8 and res[1] / res[2] > 8
+
+
+# ---------------------------------------------------------------- the 3-D accelerator
+def test_3d_dipole_kernel_is_the_source_derivative_of_the_monopole():
+    """dip3 = dG/dz_1 (sign and factors) by a central difference in z_1."""
+    from oracle.accel3d import dip3, mono3
+    rng = np.random.default_rng(8)
+    d = rng.standard_normal((20, 3))
+    k, e = 3.0, 1e-5
+    fd = (mono3(k, d[:, 0] - e, d[:, 1], d[:, 2]) - mono3(k, d[:, 0] + e, d[:, 1], d[:, 2])) / (2 * e)
+    assert np.max(np.abs(dip3(k, d[:, 0], d[:, 1], d[:, 2]) - fd)) < 1e-8 * np.max(np.abs(fd))
+
+
+def test_spherical_wave_basis_expands_a_plane_wave():
+    """The local expansion's columns against the textbook plane-wave expansion
+    exp(i kappa d.x) = 4 pi sum_lm i^l j_l(kappa r) Y_lm(x^) conj(Y_lm(d)), with
+    Y_lm(d) read off the basis at r = R_ref (where the radial factor is 1), and
+    each column a Helmholtz solution (fourth-order finite-difference Laplacian
+    + kappa^2 at degree 6)."""
+    from scipy.special import spherical_jn
+    from oracle.accel3d import spherical_wave_basis
+    k, p, Rref = 2.0, 16, 0.4
+    rng = np.random.default_rng(9)
+    x = rng.uniform(-0.3, 0.3, (40, 3))
+    d = np.array([0.36, -0.48, 0.8])
+    B = spherical_wave_basis(k, x[:, 0], x[:, 1], x[:, 2], p, Rref)
+    Yd = spherical_wave_basis(k, *(Rref * d[:, None]), p, Rref)[0]
+    ls = np.concatenate([np.full(2 * l + 1, l) for l in range(p + 1)])
+    coef = 4 * np.pi * (1j ** ls) * np.conj(Yd) * spherical_jn(ls, k * Rref)
+    pw = np.exp(1j * k * x @ d)
+    assert np.max(np.abs(B @ coef - pw)) < 1e-12
+    p, e = 6, 2e-3                     # fourth-order 13-point Laplacian
+    f = lambda y: spherical_wave_basis(k, y[:, 0], y[:, 1], y[:, 2], p, Rref)
+    B = f(x)
+    lap = -90 * B
+    for ax in range(3):
+        for sgn, wt in ((1, 16), (-1, 16), (2, -1), (-2, -1)):
+            y = x.copy()
+            y[:, ax] += sgn * e
+            lap = lap + wt * f(y)
+    assert np.max(np.abs(lap / (12 * e * e) + k * k * B)) < 1e-6 * np.max(np.abs(B))
+
+
+def _acc3(x, wfac, Ne, L=6, **kw):
+    from oracle.accel3d import Accelerator3
+    return Accelerator3(x, wfac, 2.0, -1.13, 2.26 / L, L, Ne, **kw)
+
+
+def test_3d_lattice_fft_equals_the_direct_lattice_sum():
+    """The zero-padded 3-D FFT convolution (monopole and dipole tables) against
+    the brute-force sum of every equivalent source's field at every lattice
+    point (coincident pairs dropped), for random source strengths."""
+    from oracle.accel3d import dip3, mono3
+    rng = np.random.default_rng(10)
+    x = rng.uniform(-1.1, 1.1, (60, 3))
+    acc = _acc3(x, np.ones(60), 2, L=3, p=3)
+    sig = {c: rng.standard_normal(acc.n_es) + 1j * rng.standard_normal(acc.n_es) for c in acc.P}
+    V = acc.lattice_field(sig)
+    src, q, kind = [], [], []
+    for c, s in sig.items():
+        ijk = np.array([c % 3, (c // 3) % 3, c // 9])
+        src.append((ijk * acc.Ne + acc.es) * acc.delta)
+        q.append(s)
+        kind.append(acc.es_kind)
+    src, q, kind = np.concatenate(src), np.concatenate(q), np.concatenate(kind)
+    g = np.arange(acc.n_lat) * acc.delta
+    P = np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3)
+    d = [P[:, None, k] - src[None, :, k] for k in range(3)]
+    same = (np.abs(d[0]) < 1e-12) & (np.abs(d[1]) < 1e-12) & (np.abs(d[2]) < 1e-12)
+    d[0] = np.where(same, 1.0, d[0])
+    Gm = np.where(kind[None, :] == 0, mono3(2.0, *d), dip3(2.0, *d))
+    ref = (np.where(same, 0.0, Gm) @ q).reshape(V.shape)
+    assert np.max(np.abs(V - ref)) < 1e-12 * np.max(np.abs(ref))
+
+
+def test_3d_equivalent_source_fit_accuracy():
+    """Exterior field of one cube cell's two-face equivalent sources against
+    its true point sources, on the faces of the 5H cube around the cell: the
+    error falls fast with N_eq."""
+    from oracle.accel3d import mono3
+    rng = np.random.default_rng(11)
+    errs = []
+    for Ne in (4, 6, 8):
+        acc = _acc3(np.zeros((1, 3)), np.ones(1), Ne)
+        H = acc.H
+        src = rng.uniform(0, H, (30, 3))
+        qs = rng.standard_normal(30) + 1j * rng.standard_normal(30)
+        b = mono3(2.0, *(acc.coll[:, None, k] - src[None, :, k] for k in range(3))) @ qs
+        sig = _lstsq_apply(acc.Asvd, b[:, None])[:, 0]
+        pts = acc._collocation(9) * (5.0 / 3.0) + np.array([-1 / 3, -1 / 3, -1 / 3]) * H   # faces of [-2H, 3H]^3
+        true = mono3(2.0, *(pts[:, None, k] - src[None, :, k] for k in range(3))) @ qs
+        errs.append(np.max(np.abs(acc._es_field(pts) @ sig - true)) / np.max(np.abs(true)))
+    assert errs[0] > errs[1] > errs[2] and errs[2] < 1e-6
+
+
+def test_3d_accelerated_far_part_matches_direct_sum():
+    """The 3-D accelerator's non-adjacent part on the ball's nodes (weights
+    w omega m of the 3-D discretisation) against the exact non-adjacent sum:
+    the error falls with N_eq to 1e-7 (closed-cell fit data); the cell boundary
+    alone (the six faces' lattice points) also determines the local expansion."""
+    from oracle.geometry3d import Ball3, Discretisation3
+    dz = Discretisation3(Ball3(n_f=9, n_s=5, h=0.2))
+    wfac = dz.w * dz.omega * (1 - dz.b.n2c)
+    u = W.random_density(dz.N)[0]
+    errs = {}
+    for Ne, pts in ((4, "cell"), (6, "cell"), (8, "cell"), (8, "boundary")):
+        acc = _acc3(dz.x, wfac, Ne, local_points=pts)
+        ref = acc.direct_far(u)
+        errs[(Ne, pts)] = np.linalg.norm(acc.apply_far(u) - ref) / np.linalg.norm(ref)
+    assert errs[(4, "cell")] > 100 * errs[(6, "cell")] and errs[(8, "cell")] < 1e-6
+    assert errs[(8, "boundary")] < 1e-4
