@@ -295,6 +295,49 @@ ls_status ls_host_plan_accel(ls_host_plan h, int32_t* occ_cells, int64_t* P_off,
                              double* Bpinv, double* BT, double* Phi, double* Gtab, double* Dtab);
 ls_status ls_host_plan_destroy(ls_host_plan h);
 
+/* ---- 3-D accelerator setup (Section 5), host only -------------------------
+ * The dense pieces of the three-dimensional accelerator: two-face equivalent
+ * sources on cube cells and a 3-D lattice FFT, the extension of Section 3.2
+ * that Section 5 names.  Input: N nodes xyz (N x 3 row-major) with per-node
+ * factors wfac = w m omega (quadrature weight x contrast x partition of
+ * unity), the wavenumber kappa, the cell box (corner box0[3], side H, L cells
+ * per axis; every node must fall inside, LS_ERR_INVALID otherwise), N_eq
+ * lattice intervals per cell side (delta = H / N_eq), the local-expansion
+ * degree p (0 = 2 N_eq + 1; (p + 1)^2 must not exceed (N_eq + 1)^3), the
+ * collocation points per face side m_coll (0 = the smallest m with
+ * 6 m^2 >= 2 n_es, plus one), the SVD truncation rcond (0 = 1e-13) and the
+ * host threads (0 = all).  kappa sqrt(3) H / 2 must stay below pi.
+ *
+ * Contents (complex arrays interleaved doubles; the caller sizes its buffers
+ * from ls_host_accel3_sizes: [0] occupied cells, [1] n_es = 4 (N_eq + 1)^2,
+ * [2] nb = (p + 1)^2, [3] n_loc = (N_eq + 1)^3, [4] FFT size M (power of two
+ * >= 2 (L N_eq + 1) - 1, at most 512), [5] total length of P, [6] N):
+ *   occ_cells  occupied cell ids (k L + j) L + i, increasing;
+ *   node_order the nodes grouped by cell (stable within a cell);
+ *   P          per occupied cell c, P_c (n_es x n_c, row-major) at P_off[c];
+ *              column j acts on node node_order[start + j] and carries wfac;
+ *              rows: monopoles on face x_1 = 0 then x_1 = H, (b, c) row-major,
+ *              then the dipoles (d/dz_1) in the same order;
+ *   Bpinv      nb x n_loc, the least-squares inverse of the spherical-wave
+ *              basis j_l(kappa r) Ybar_l^m / j_l(kappa sqrt(3) H / 2) on the
+ *              cell's lattice points (a, b, c) in 0..N_eq, row-major;
+ *   BT         27 x nb x n_es, B^+ T_o for neighbour offset
+ *              (oi + 1) 9 + (oj + 1) 3 + (ok + 1);
+ *   Phi        N x nb, the basis at each node (input order) about its cell
+ *              centre;
+ *   Gtab, Dtab M^3 lattice tables of G and dG/dz_1 at offsets delta (a, b, c)
+ *              (indices wrap at M / 2), zero at the origin.
+ * Any output pointer may be NULL (that array is skipped).  The handle owns
+ * its memory until ls_host_accel3_destroy. */
+typedef struct ls_host_accel3_s* ls_host_accel3;
+ls_status ls_host_accel3_create(const double* xyz, const double* wfac, int64_t N, double kappa,
+                                const double* box0, double H, int L, int N_eq, int p, int m_coll,
+                                double rcond, int n_threads, ls_host_accel3* out);
+ls_status ls_host_accel3_sizes(ls_host_accel3 h, int64_t* sizes /* 7 */);
+ls_status ls_host_accel3_get(ls_host_accel3 h, int32_t* occ_cells, int64_t* P_off, int64_t* node_order,
+                             double* P, double* Bpinv, double* BT, double* Phi, double* Gtab, double* Dtab);
+ls_status ls_host_accel3_destroy(ls_host_accel3 h);
+
 const char* ls_status_string(ls_status s);
 
 /* Message of the last failure of this plan (or of the last failed

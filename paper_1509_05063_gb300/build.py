@@ -18,7 +18,8 @@ LIBDIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(LIBDIR, "libls_gb300.so")
 INCLUDE = os.path.join(ROOT, "include")
 
-HOST_SRC = ["host/geometry.cpp", "host/quadrature.cpp", "host/linalg.cpp", "host/accel_host.cpp"]
+HOST_SRC = ["host/geometry.cpp", "host/quadrature.cpp", "host/linalg.cpp", "host/accel_host.cpp",
+            "host/accel3_host.cpp"]
 CUDA_SRC = ["device/kernels.cu", "device/near_tc.cu", "api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

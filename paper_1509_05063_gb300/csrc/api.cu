@@ -377,6 +377,85 @@ ls_status ls_host_plan_destroy(ls_host_plan h) {
   return LS_OK;
 }
 
+}  // extern "C"
+
+struct ls_host_accel3_s {
+  lsh::Accel3 A;
+};
+
+extern "C" {
+
+ls_status ls_host_accel3_create(const double* xyz, const double* wfac, int64_t N, double kappa, const double* box0,
+                                double H, int L, int N_eq, int p, int m_coll, double rcond, int n_threads,
+                                ls_host_accel3* out) {
+  if (!out) return fail(nullptr, LS_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  if (!xyz || !wfac || !box0 || N <= 0) return fail(nullptr, LS_ERR_INVALID, "empty node set or NULL array");
+  if (!(kappa > 0) || !(H > 0) || L < 1 || N_eq < 1 || p < 0 || m_coll < 0 || rcond < 0)
+    return fail(nullptr, LS_ERR_INVALID, "invalid kappa, H, L, N_eq, p, m_coll or rcond");
+  ls_host_accel3 h = new (std::nothrow) ls_host_accel3_s;
+  if (!h) return fail(nullptr, LS_ERR_NOMEM, "host allocation failed");
+  lsh::Accel3& A = h->A;
+  A.kappa = kappa;
+  A.H = H;
+  A.L = L;
+  A.Ne = N_eq;
+  A.p = p;
+  A.m_coll = m_coll;
+  A.rcond = rcond;
+  for (int k = 0; k < 3; ++k) A.box0[k] = box0[k];
+  A.n_threads = n_threads > 0 ? n_threads : int(std::max(1u, std::thread::hardware_concurrency()));
+  try {
+    if (!lsh::build_accel3(A, xyz, wfac, N)) {
+      const std::string m = A.err;
+      delete h;
+      return fail(nullptr, LS_ERR_INVALID, m);
+    }
+  } catch (const std::bad_alloc&) {
+    delete h;
+    return fail(nullptr, LS_ERR_NOMEM, "host allocation failed");
+  }
+  *out = h;
+  return LS_OK;
+}
+
+ls_status ls_host_accel3_sizes(ls_host_accel3 h, int64_t* sizes) {
+  if (!h || !sizes) return LS_ERR_INVALID;
+  const lsh::Accel3& A = h->A;
+  sizes[0] = int64_t(A.occ_cells.size());
+  sizes[1] = A.n_es;
+  sizes[2] = A.nb;
+  sizes[3] = A.n_loc;
+  sizes[4] = A.M;
+  sizes[5] = A.P_off.empty() ? 0 : A.P_off.back();
+  sizes[6] = int64_t(A.node_order.size());
+  return LS_OK;
+}
+
+ls_status ls_host_accel3_get(ls_host_accel3 h, int32_t* occ_cells, int64_t* P_off, int64_t* node_order, double* P,
+                             double* Bpinv, double* BT, double* Phi, double* Gtab, double* Dtab) {
+  if (!h) return LS_ERR_INVALID;
+  const lsh::Accel3& A = h->A;
+  auto put = [](const auto& v, auto* dst) {
+    if (dst) std::memcpy(dst, v.data(), v.size() * sizeof(v[0]));
+  };
+  put(A.occ_cells, occ_cells);
+  put(A.P_off, P_off);
+  put(A.node_order, node_order);
+  put(A.P, P);
+  put(A.Bpinv, Bpinv);
+  put(A.BT, BT);
+  put(A.Phi, Phi);
+  put(A.Gtab, Gtab);
+  put(A.Dtab, Dtab);
+  return LS_OK;
+}
+
+ls_status ls_host_accel3_destroy(ls_host_accel3 h) {
+  delete h;
+  return LS_OK;
+}
+
 const char* ls_status_string(ls_status s) {
   switch (s) {
     case LS_OK: return "ok";

@@ -107,6 +107,24 @@ bool build_near(Plan2D& plan);
 bool check_cells(Plan2D& plan, int64_t* block_entries);
 bool build_accel(Plan2D& plan);
 
+// Dense pieces of the 3-D accelerator (Section 5) for a node set with weights
+// w m omega: cube cells of side H from corner box0, L per axis.
+struct Accel3 {
+  double kappa = 0, H = 0, box0[3] = {0, 0, 0}, rcond = 0;
+  int L = 0, Ne = 0, p = 0, m_coll = 0, n_threads = 1;
+  int n_es = 0, nb = 0, n_loc = 0, n_lat = 0, M = 0;
+  std::vector<int64_t> node_order;      // nodes grouped by cell (stable)
+  std::vector<int32_t> occ_cells;       // occupied cell ids (k L + j) L + i
+  std::vector<int64_t> P_off;           // per occupied cell, size nocc + 1
+  std::vector<cd> P;                    // P_c (n_es x n_c row-major), columns in node_order
+  std::vector<cd> Bpinv;                // nb x n_loc
+  std::vector<cd> BT;                   // 27 x nb x n_es
+  std::vector<cd> Phi;                  // N x nb (input node order)
+  std::vector<cd> Gtab, Dtab;           // M^3 kernel lattice tables ([da][db][dc])
+  std::string err;
+};
+bool build_accel3(Accel3& a, const double* xyz, const double* wfac, int64_t N);
+
 // Truncated thin SVD of a complex m x n matrix (m >= n), one-sided Jacobi.
 struct SVD {
   int m = 0, n = 0, k = 0;
@@ -115,6 +133,9 @@ struct SVD {
   std::vector<cd> V;      // n x k (column-major)
 };
 SVD svd_truncated(const std::vector<cd>& A_rowmajor, int m, int n, double rcond);
+// The same factorisation by column-pivoted Householder QR followed by one-sided
+// Jacobi on R^H (fewer, shorter sweeps; for the larger 3-D fits).
+SVD svd_truncated_qr(const std::vector<cd>& A_rowmajor, int m, int n, double rcond);
 // X = V S^-1 U^H B, B is m x nb row-major; result n x nb row-major.
 std::vector<cd> svd_solve(const SVD& f, const std::vector<cd>& B, int nb);
 

@@ -83,6 +83,11 @@ _SIGS = {
     "ls_host_plan_near": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "ls_host_plan_accel": ([C.c_void_p] + [C.c_void_p] * 8),
     "ls_host_plan_destroy": ([C.c_void_p]),
+    "ls_host_accel3_create": ([C.c_void_p, C.c_void_p, C.c_int64, C.c_double, C.c_void_p, C.c_double, C.c_int,
+                              C.c_int, C.c_int, C.c_int, C.c_double, C.c_int, C.POINTER(C.c_void_p)]),
+    "ls_host_accel3_sizes": ([C.c_void_p, C.c_void_p]),
+    "ls_host_accel3_get": ([C.c_void_p] + [C.c_void_p] * 9),
+    "ls_host_accel3_destroy": ([C.c_void_p]),
     "ls_set_stage_timing": ([C.c_void_p, C.c_int]),
     "ls_apply_noalloc": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
     "ls_check_cells": ([C.POINTER(Geometry), N2FN, C.c_void_p, C.c_double, C.POINTER(Options), C.c_void_p]),
@@ -335,6 +340,55 @@ class HostPlan:
     def close(self):
         if getattr(self, "_h", None):
             _lib.ls_host_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class HostAccel3:
+    """Host-only setup of the 3-D accelerator (ls_host_accel3_*) for a node set
+    xyz (N, 3) with factors wfac = w m omega; the matrices as numpy arrays."""
+
+    def __init__(self, xyz, wfac, kappa: float, box0, H: float, L: int, N_eq: int, p: int = 0,
+                 m_coll: int = 0, rcond: float = 0.0, n_threads: int = 0):
+        load_library()
+        xyz = np.ascontiguousarray(xyz, np.float64)
+        wfac = np.ascontiguousarray(wfac, np.float64)
+        b0 = np.ascontiguousarray(box0, np.float64)
+        if xyz.ndim != 2 or xyz.shape[1] != 3 or wfac.shape != (xyz.shape[0],) or b0.shape != (3,):
+            raise ValueError("xyz must be (N, 3), wfac (N,), box0 (3,)")
+        h = C.c_void_p()
+        st = _lib.ls_host_accel3_create(xyz.ctypes.data, wfac.ctypes.data, xyz.shape[0], float(kappa),
+                                        b0.ctypes.data, float(H), int(L), int(N_eq), int(p), int(m_coll),
+                                        float(rcond), int(n_threads), C.byref(h))
+        if st != 0:
+            raise LSError(st, _lib.ls_last_error(None).decode())
+        self._h = h
+        sz = np.zeros(7, np.int64)
+        _check(_lib.ls_host_accel3_sizes(h, sz.ctypes.data))
+        self.nocc, self.n_es, self.nb, self.n_loc, self.M, self.P_len, self.N = map(int, sz)
+
+    def get(self):
+        occ = np.zeros(self.nocc, np.int32)
+        P_off = np.zeros(self.nocc + 1, np.int64)
+        order = np.zeros(self.N, np.int64)
+        P = np.zeros(self.P_len, np.complex128)
+        Bp = np.zeros((self.nb, self.n_loc), np.complex128)
+        BT = np.zeros((27, self.nb, self.n_es), np.complex128)
+        Phi = np.zeros((self.N, self.nb), np.complex128)
+        G = np.zeros((self.M,) * 3, np.complex128)
+        D = np.zeros((self.M,) * 3, np.complex128)
+        _check(_lib.ls_host_accel3_get(self._h, occ.ctypes.data, P_off.ctypes.data, order.ctypes.data, P.ctypes.data,
+                                       Bp.ctypes.data, BT.ctypes.data, Phi.ctypes.data, G.ctypes.data, D.ctypes.data))
+        return dict(occ=occ, P_off=P_off, order=order, P=P, Bpinv=Bp, BT=BT, Phi=Phi, Gtab=G, Dtab=D)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.ls_host_accel3_destroy(self._h)
             self._h = None
 
     def __del__(self):

@@ -146,3 +146,66 @@ def test_host_accelerator_matrices_reproduce_oracle_far_field(lib, make):
         mem = np.nonzero(cell == c)[0]
         got[mem] = A["Phi"][mem] @ g
     assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 1e-11
+
+
+def _apply_far3(A, u, L, Ne, n_es, M):
+    """The 3-D accelerator's steps in numpy with the library's matrices."""
+    nf = (Ne + 1) ** 2
+    members, sig, pos = {}, {}, 0
+    for k, c in enumerate(A["occ"]):
+        n_c = (A["P_off"][k + 1] - A["P_off"][k]) // n_es
+        members[c] = A["order"][pos:pos + n_c]
+        pos += n_c
+        sig[c] = A["P"][A["P_off"][k]:A["P_off"][k + 1]].reshape(n_es, n_c) @ u[members[c]]
+    Sm = np.zeros((M,) * 3, complex)
+    Sd = np.zeros((M,) * 3, complex)
+    bb, cc = np.meshgrid(np.arange(Ne + 1), np.arange(Ne + 1), indexing="ij")
+    bb, cc = bb.ravel(), cc.ravel()
+    for c, s in sig.items():
+        i, j, k = c % L, (c // L) % L, c // (L * L)
+        for f in range(4):
+            np.add.at(Sm if f < 2 else Sd, (np.full(nf, (i + f % 2) * Ne), j * Ne + bb, k * Ne + cc),
+                      s[f * nf:(f + 1) * nf])
+    V = np.fft.ifftn(np.fft.fftn(Sm) * np.fft.fftn(A["Gtab"]) + np.fft.fftn(Sd) * np.fft.fftn(A["Dtab"]))
+    g = np.arange(Ne + 1)
+    la = np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3)
+    out = np.zeros(len(u), complex)
+    for c in sig:
+        ijk = np.array([c % L, (c // L) % L, c // (L * L)])
+        p = ijk * Ne + la
+        gam = A["Bpinv"] @ V[p[:, 0], p[:, 1], p[:, 2]]
+        for o in range(27):
+            nb = ijk + np.array([o // 9, (o // 3) % 3, o % 3]) - 1
+            if np.all((nb >= 0) & (nb < L)):
+                nc = int((nb[2] * L + nb[1]) * L + nb[0])
+                if nc in sig:
+                    gam = gam - A["BT"][o] @ sig[nc]
+        out[members[c]] = A["Phi"][members[c]] @ gam
+    return out
+
+
+def test_host_accel3_reproduces_oracle_far_field(lib):
+    """The library's 3-D accelerator setup (equivalent-source fits by a
+    QR-preconditioned Jacobi SVD, spherical-wave local expansion, 27 neighbour
+    tables, 3-D kernel lattice tables) run through the accelerator's steps in
+    numpy: equal to the oracle's 3-D far part up to the fits' truncation, and
+    to the exact non-adjacent sum within the equivalent-source error."""
+    from paper_1509_05063_gb300 import HostAccel3, LSError
+    from oracle.accel3d import Accelerator3
+    from oracle.geometry3d import Ball3, Discretisation3
+    dz = Discretisation3(Ball3(n_f=9, n_s=5, h=0.2))
+    wfac = dz.w * dz.omega * (1 - dz.b.n2c)
+    u = W.random_density(dz.N)[0]
+    L, Ne = 6, 6
+    ha = HostAccel3(dz.x, wfac, 2.0, [-1.13] * 3, 2.26 / L, L, Ne)
+    assert (ha.n_es, ha.nb, ha.n_loc, ha.M) == (4 * 49, 14 * 14, 343, 128)
+    got = _apply_far3(ha.get(), u, L, Ne, ha.n_es, ha.M)
+    acc = Accelerator3(dz.x, wfac, 2.0, -1.13, 2.26 / L, L, Ne)
+    ref = acc.apply_far(u)
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 1e-8
+    direct = acc.direct_far(u)
+    assert np.linalg.norm(got - direct) / np.linalg.norm(direct) < 1e-5
+    with pytest.raises(LSError, match="outside"):
+        HostAccel3(dz.x, wfac, 2.0, [-0.5] * 3, 2.26 / L, L, Ne)
+    with pytest.raises(LSError, match="more terms"):
+        HostAccel3(dz.x, wfac, 2.0, [-1.13] * 3, 2.26 / L, L, 2, p=5)
