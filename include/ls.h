@@ -338,6 +338,52 @@ ls_status ls_host_accel3_get(ls_host_accel3 h, int32_t* occ_cells, int64_t* P_of
                              double* P, double* Bpinv, double* BT, double* Phi, double* Gtab, double* Dtab);
 ls_status ls_host_accel3_destroy(ls_host_accel3 h);
 
+/* ---- 3-D ball discretisation and interior singular rule (Section 5) ------
+ * The Nystrom nodes of a ball of radius a (host only).  Shell of thickness w:
+ * the six faces of a cubed sphere in equiangular coordinates (xi, eta) in
+ * [-pi/4 - delta, pi/4 + delta]^2 (face frames (e1, e2, e3), direction
+ * normalise(e3 + tan(xi) e1 + tan(eta) e2); faces +x, -x, +y, -y, +z, -z with
+ * e1, e2 = (y, z), (z, y), (z, x), (x, z), (x, y), (y, x)), blended on the
+ * sphere by the C-infinity partition psi_F (normalised products of cut-offs
+ * that vanish at the extended edges); n_f x n_f trapezoid points on each face,
+ * n_s depth lines s = 0..1 (r = a - s w) under composite Q-point Newton-Cotes
+ * (n_s - 1 a multiple of Q - 1); omega_B(s) = S((s - tau0) / (tau1 - tau0)).
+ * Interior: the grid h (i, j, k), |i|, |j|, |k| <= ceil(a / h), with
+ * omega_I = 1 - omega_B(depth / w) and weight h^3, kept where omega_I > 0.
+ * Shell nodes come first (face, then i, j, k), then the interior grid
+ * (lexicographic).  Per node: xyz (N x 3), quadrature weight w (Jacobian x
+ * rule x psi_F on the shell), omega, psi (0 on the interior), face (-1 on the
+ * interior), grid (N x 3: face-grid (i, j, k) on the shell, (i, j, k) +
+ * ceil(a / h) on the interior).  A smooth f integrates as sum w omega f.
+ * sizes: [0] N, [1] shell nodes, [2] interior nodes, [3] ceil(a / h).
+ * Invalid parameters return LS_ERR_INVALID with a message. */
+typedef struct {
+  double a, w;           /* radius, shell thickness (0 < w < a)                  */
+  int n_f, n_s, Q;       /* face points per side, depth lines, Newton-Cotes points */
+  double delta;          /* angular overlap of the faces (0 < delta < pi / 4)    */
+  double h;              /* interior grid spacing                               */
+  double tau0, tau1;     /* partition-of-unity transition, 0 < tau0 < tau1 < 1   */
+} ls_ball3;
+typedef struct ls_host_ball3_s* ls_host_ball3;
+ls_status ls_host_ball3_create(const ls_ball3* ball, ls_host_ball3* out);
+ls_status ls_host_ball3_sizes(ls_host_ball3 h, int64_t* sizes /* 4 */);
+ls_status ls_host_ball3_nodes(ls_host_ball3 h, double* xyz, double* w, double* omega, double* psi, int8_t* face,
+                              int32_t* grid);
+ls_status ls_host_ball3_destroy(ls_host_ball3 h);
+
+/* Coefficients c[o] of the interior singular rule for a target on a uniform
+ * grid of spacing h: int G(x, y) eta(|y - x| / (R h)) phi(y) dy is
+ * sum_o c[o] phi(x + o h) over offsets o in [-Wn, Wn]^3, Wn = ceil(R) + p/2 + 2,
+ * G = exp(i kappa r) / (4 pi r).  Spherical coordinates about x: radius
+ * rho = R s^q (grid units), n_rho - 1 trapezoid points s = 1..n_rho-1 / n_rho
+ * weighted by the cut-off chi(s^q) (1 up to chi_s0), n_mu Gauss-Legendre
+ * points in cos(theta), n_phi trapezoid points in the azimuth; phi at the
+ * rule's points by degree-p tensor Lagrange interpolation on the grid
+ * (stencil starting floor(t) - p/2 per axis).  win: (2 Wn + 1)^3 complex
+ * (interleaved doubles, [di][dj][dk]) or NULL to query Wn only. */
+ls_status ls_interior_window3(double kappa, double h, double R, int p, int q, int n_rho, int n_mu, int n_phi,
+                              double chi_s0, double* win, int* Wn);
+
 const char* ls_status_string(ls_status s);
 
 /* Message of the last failure of this plan (or of the last failed

@@ -456,6 +456,89 @@ ls_status ls_host_accel3_destroy(ls_host_accel3 h) {
   return LS_OK;
 }
 
+}  // extern "C"
+
+struct ls_host_ball3_s {
+  lsh::Ball3 B;
+};
+
+extern "C" {
+
+ls_status ls_host_ball3_create(const ls_ball3* ball, ls_host_ball3* out) {
+  if (!out) return fail(nullptr, LS_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  if (!ball) return fail(nullptr, LS_ERR_INVALID, "ball is NULL");
+  ls_host_ball3 h = new (std::nothrow) ls_host_ball3_s;
+  if (!h) return fail(nullptr, LS_ERR_NOMEM, "host allocation failed");
+  lsh::Ball3& B = h->B;
+  B.a = ball->a;
+  B.w = ball->w;
+  B.n_f = ball->n_f;
+  B.n_s = ball->n_s;
+  B.Q = ball->Q;
+  B.delta = ball->delta;
+  B.h = ball->h;
+  B.tau0 = ball->tau0;
+  B.tau1 = ball->tau1;
+  try {
+    if (!lsh::build_ball3(B)) {
+      const std::string m = B.err;
+      delete h;
+      return fail(nullptr, LS_ERR_INVALID, m);
+    }
+  } catch (const std::bad_alloc&) {
+    delete h;
+    return fail(nullptr, LS_ERR_NOMEM, "host allocation failed");
+  }
+  *out = h;
+  return LS_OK;
+}
+
+ls_status ls_host_ball3_sizes(ls_host_ball3 h, int64_t* sizes) {
+  if (!h || !sizes) return LS_ERR_INVALID;
+  sizes[0] = h->B.N;
+  sizes[1] = h->B.n_shell;
+  sizes[2] = h->B.n_cart;
+  sizes[3] = h->B.grid_m;
+  return LS_OK;
+}
+
+ls_status ls_host_ball3_nodes(ls_host_ball3 h, double* xyz, double* w, double* omega, double* psi, int8_t* face,
+                              int32_t* grid) {
+  if (!h) return LS_ERR_INVALID;
+  const lsh::Ball3& B = h->B;
+  auto put = [](const auto& v, auto* dst) {
+    if (dst) std::memcpy(dst, v.data(), v.size() * sizeof(v[0]));
+  };
+  put(B.x, xyz);
+  put(B.w_q, w);
+  put(B.omega, omega);
+  put(B.psi, psi);
+  put(B.face, face);
+  put(B.grid, grid);
+  return LS_OK;
+}
+
+ls_status ls_host_ball3_destroy(ls_host_ball3 h) {
+  delete h;
+  return LS_OK;
+}
+
+ls_status ls_interior_window3(double kappa, double h, double R, int p, int q, int n_rho, int n_mu, int n_phi,
+                              double chi_s0, double* win, int* Wn) {
+  if (!Wn) return fail(nullptr, LS_ERR_INVALID, "Wn is NULL");
+  std::vector<lsh::cd> w;
+  std::string m;
+  try {
+    if (!lsh::interior_window3(kappa, h, R, p, q, n_rho, n_mu, n_phi, chi_s0, w, Wn, &m))
+      return fail(nullptr, LS_ERR_INVALID, m);
+  } catch (const std::bad_alloc&) {
+    return fail(nullptr, LS_ERR_NOMEM, "host allocation failed");
+  }
+  if (win) std::memcpy(win, w.data(), w.size() * sizeof(w[0]));
+  return LS_OK;
+}
+
 const char* ls_status_string(ls_status s) {
   switch (s) {
     case LS_OK: return "ok";

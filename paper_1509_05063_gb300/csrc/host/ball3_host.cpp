@@ -1,0 +1,215 @@
+// Three-dimensional discretisation of a penetrable ball (Section 5) and the
+// translation-invariant window of the interior singular rule, built on the
+// host.
+//
+// Shell: the six faces of a cubed sphere in equiangular coordinates
+// (xi, eta) in [-pi/4 - delta, pi/4 + delta]^2, blended on the sphere by a
+// C-infinity partition of unity psi_F (normalised products of cut-offs that
+// vanish to all orders at the extended edges); depth s in [0, 1], radius
+// r = a - s w; trapezoid rule in xi and eta, composite Q-point Newton-Cotes in
+// s; omega_B(s) = S((s - tau0) / (tau1 - tau0)).  Interior: the Cartesian grid
+// of spacing h with omega_I = 1 - omega_B(depth / w), kept where omega_I > 0.
+//
+// Interior singular rule: for a grid-point target the cut-off part of the
+// patch integral is taken in spherical coordinates about the target,
+// rho = R s^q (grid units), trapezoid rule in s, Gauss-Legendre in cos(theta),
+// trapezoid rule in the azimuth; the density at the off-grid points comes
+// from degree-p tensor-product Lagrange interpolation on the grid, so the rule
+// is a fixed window of coefficients over grid offsets.
+#include <cmath>
+
+#include "host_plan.hpp"
+
+namespace lsh {
+
+namespace {
+
+// face frames (e1, e2, e3); e3 is the face centre direction
+const double kFaces[6][3][3] = {
+    {{0, 1, 0}, {0, 0, 1}, {1, 0, 0}},  {{0, 0, 1}, {0, 1, 0}, {-1, 0, 0}}, {{0, 0, 1}, {1, 0, 0}, {0, 1, 0}},
+    {{1, 0, 0}, {0, 0, 1}, {0, -1, 0}}, {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}},  {{0, 1, 0}, {1, 0, 0}, {0, 0, -1}},
+};
+
+inline double dot3(const double* a, const double* b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+
+// direction of (xi, eta) on face F and the solid-angle element per dxi deta
+void face_direction(int F, double xi, double eta, double* d, double* dom) {
+  const double t1 = std::tan(xi), t2 = std::tan(eta);
+  const double nrm = std::sqrt(1.0 + t1 * t1 + t2 * t2);
+  for (int k = 0; k < 3; ++k) d[k] = (kFaces[F][2][k] + t1 * kFaces[F][0][k] + t2 * kFaces[F][1][k]) / nrm;
+  *dom = (1.0 + t1 * t1) * (1.0 + t2 * t2) / (nrm * nrm * nrm);
+}
+
+double face_bump(double xi, double eta, double delta) {
+  const double lo = M_PI / 4 - delta, hi = M_PI / 4 + delta;
+  return smooth_step((std::fabs(xi) - lo) / (hi - lo)) * smooth_step((std::fabs(eta) - lo) / (hi - lo));
+}
+
+// psi_F(d): face F's share of the partition of unity on the sphere
+double surface_pou(int F, const double* d, double delta) {
+  double num = 0, den = 0;
+  for (int G = 0; G < 6; ++G) {
+    const double z = dot3(d, kFaces[G][2]);
+    if (!(z > 1e-12)) continue;
+    const double b = face_bump(std::atan2(dot3(d, kFaces[G][0]), z), std::atan2(dot3(d, kFaces[G][1]), z), delta);
+    den += b;
+    if (G == F) num = b;
+  }
+  return num / den;
+}
+
+// Gauss-Legendre nodes and weights on [-1, 1] (Newton on P_n from the
+// Chebyshev-like first guesses), ascending.
+void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w) {
+  x.assign(n, 0.0);
+  w.assign(n, 0.0);
+  for (int i = 0; i < (n + 1) / 2; ++i) {
+    double z = std::cos(M_PI * (i + 0.75) / (n + 0.5)), dp = 1;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1, p1 = z;
+      for (int k = 2; k <= n; ++k) {
+        const double p2 = ((2.0 * k - 1) * z * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      dp = n * (z * p1 - p0) / (z * z - 1.0);
+      const double dz = p1 / dp;
+      z -= dz;
+      if (std::fabs(dz) < 1e-16) break;
+    }
+    // recompute the derivative at the converged root
+    double p0 = 1, p1 = z;
+    for (int k = 2; k <= n; ++k) {
+      const double p2 = ((2.0 * k - 1) * z * p1 - (k - 1.0) * p0) / k;
+      p0 = p1;
+      p1 = p2;
+    }
+    dp = n * (z * p1 - p0) / (z * z - 1.0);
+    x[i] = -z;
+    x[n - 1 - i] = z;
+    w[i] = w[n - 1 - i] = 2.0 / ((1.0 - z * z) * dp * dp);
+  }
+}
+
+// Lagrange weights of the integer nodes s..s+p at t
+void lagrange_row(double t, int64_t s, int p, double* L) {
+  for (int k = 0; k <= p; ++k) {
+    double v = 1;
+    for (int m = 0; m <= p; ++m)
+      if (m != k) v *= (t - double(s + m)) / double(k - m);
+    L[k] = v;
+  }
+}
+
+}  // namespace
+
+bool build_ball3(Ball3& B) {
+  const int nf = B.n_f, ns = B.n_s, Q = B.Q;
+  if (!(B.a > 0 && B.w > 0 && B.w < B.a && B.h > 0)) { B.err = "need a > 0, 0 < w < a, h > 0"; return false; }
+  if (nf < 2 || ns < 2 || Q < 2 || Q > 5 || (ns - 1) % (Q - 1)) {
+    B.err = "need n_f >= 2, 2 <= Q <= 5 and n_s - 1 a multiple of Q - 1";
+    return false;
+  }
+  if (!(B.delta > 0 && B.delta < M_PI / 4)) { B.err = "need 0 < delta < pi / 4"; return false; }
+  if (!(B.tau0 > 0 && B.tau0 < B.tau1 && B.tau1 < 1)) { B.err = "need 0 < tau0 < tau1 < 1"; return false; }
+  const double half = M_PI / 4 + B.delta;
+  const double dg = (2 * half) / (nf - 1);
+  const double ds = 1.0 / (ns - 1);
+  std::vector<double> g(nf), s(ns), ws(ns, 0.0);
+  for (int i = 0; i < nf; ++i) g[i] = i * dg - half;
+  g[nf - 1] = half;
+  for (int k = 0; k < ns; ++k) s[k] = k * ds;
+  s[ns - 1] = 1.0;
+  const std::vector<double> nc = newton_cotes(Q);
+  for (int blk = 0; blk < (ns - 1) / (Q - 1); ++blk)
+    for (int k = 0; k < Q; ++k) ws[blk * (Q - 1) + k] += nc[k];
+  for (double& v : ws) v *= (s[1] - s[0]);
+  auto clear = [&]() {
+    B.x.clear(); B.w_q.clear(); B.omega.clear(); B.psi.clear(); B.face.clear(); B.grid.clear();
+  };
+  clear();
+  for (int F = 0; F < 6; ++F)
+    for (int i = 0; i < nf; ++i)
+      for (int j = 0; j < nf; ++j) {
+        double d[3], dom;
+        face_direction(F, g[i], g[j], d, &dom);
+        const double psi = surface_pou(F, d, B.delta);
+        for (int k = 0; k < ns; ++k) {
+          const double r = B.a - s[k] * B.w;
+          const double wq = dg * dg * ws[k] * B.w * r * r * dom * psi;
+          if (!(wq > 0.0)) continue;
+          for (int c = 0; c < 3; ++c) B.x.push_back(r * d[c]);
+          B.w_q.push_back(wq);
+          B.omega.push_back(smooth_step((s[k] - B.tau0) / (B.tau1 - B.tau0)));
+          B.psi.push_back(psi);
+          B.face.push_back(int8_t(F));
+          B.grid.insert(B.grid.end(), {i, j, k});
+        }
+      }
+  B.n_shell = int64_t(B.w_q.size());
+  const int m = B.grid_m = int(std::ceil(B.a / B.h));
+  const double h3 = B.h * B.h * B.h;
+  for (int ix = -m; ix <= m; ++ix)
+    for (int iy = -m; iy <= m; ++iy)
+      for (int iz = -m; iz <= m; ++iz) {
+        const double p[3] = {B.h * ix, B.h * iy, B.h * iz};
+        const double depth = (B.a - std::sqrt(dot3(p, p))) / B.w;
+        const double om = depth > 0 ? 1.0 - smooth_step((depth - B.tau0) / (B.tau1 - B.tau0)) : 0.0;
+        if (!(om > 0.0)) continue;
+        B.x.insert(B.x.end(), p, p + 3);
+        B.w_q.push_back(h3);
+        B.omega.push_back(om);
+        B.psi.push_back(0.0);
+        B.face.push_back(int8_t(-1));
+        B.grid.insert(B.grid.end(), {ix + m, iy + m, iz + m});
+      }
+  B.N = int64_t(B.w_q.size());
+  B.n_cart = B.N - B.n_shell;
+  return true;
+}
+
+bool interior_window3(double kappa, double h, double R, int p, int q, int n_rho, int n_mu, int n_phi, double chi_s0,
+                      std::vector<cd>& win, int* Wn_out, std::string* err) {
+  if (!(kappa >= 0 && h > 0 && R > 0) || p < 1 || q < 1 || n_rho < 2 || n_mu < 1 || n_phi < 1 ||
+      !(chi_s0 >= 0 && chi_s0 < 1)) {
+    *err = "invalid interior rule parameters";
+    return false;
+  }
+  const int Wn = int(std::ceil(R)) + p / 2 + 2;
+  const int side = 2 * Wn + 1;
+  *Wn_out = Wn;
+  win.assign(size_t(side) * side * side, cd(0.0));
+  std::vector<double> mu, wmu;
+  gauss_legendre(n_mu, mu, wmu);
+  std::vector<double> La(p + 1), Lb(p + 1), Lc(p + 1);
+  for (int ir = 1; ir < n_rho; ++ir) {
+    const double sv = double(ir) / n_rho;
+    const double rho = R * std::pow(sv, q);
+    const double wr = (1.0 / n_rho) * R * q * std::pow(sv, q - 1) * cutoff(std::pow(sv, q), chi_s0);
+    if (wr == 0.0) continue;
+    // rho^2 h^3 G(rho h) = rho h^2 exp(i kappa rho h) / (4 pi)
+    const cd kern = std::polar(rho * h * h / (4 * M_PI), kappa * rho * h);
+    for (int im = 0; im < n_mu; ++im) {
+      const double st = std::sqrt(1 - mu[im] * mu[im]);
+      for (int ip = 0; ip < n_phi; ++ip) {
+        const double ph = 2 * M_PI * ip / n_phi;
+        const double o[3] = {rho * st * std::cos(ph), rho * st * std::sin(ph), rho * mu[im]};
+        const cd f = (wr * wmu[im] * (2 * M_PI / n_phi)) * kern;
+        int64_t s0[3];
+        for (int k = 0; k < 3; ++k) s0[k] = int64_t(std::floor(o[k])) - p / 2;
+        lagrange_row(o[0], s0[0], p, La.data());
+        lagrange_row(o[1], s0[1], p, Lb.data());
+        lagrange_row(o[2], s0[2], p, Lc.data());
+        for (int i = 0; i <= p; ++i)
+          for (int j = 0; j <= p; ++j) {
+            const cd fij = f * (La[i] * Lb[j]);
+            const size_t base = (size_t(s0[0] + i + Wn) * side + size_t(s0[1] + j + Wn)) * side;
+            for (int k = 0; k <= p; ++k) win[base + size_t(s0[2] + k + Wn)] += fij * Lc[k];
+          }
+      }
+    }
+  }
+  return true;
+}
+
+}  // namespace lsh

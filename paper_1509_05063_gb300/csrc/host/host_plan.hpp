@@ -125,6 +125,26 @@ struct Accel3 {
 };
 bool build_accel3(Accel3& a, const double* xyz, const double* wfac, int64_t N);
 
+// 3-D discretisation of a ball (Section 5): six blended cubed-sphere shell
+// faces, then the interior Cartesian grid.
+struct Ball3 {
+  double a = 1, w = 0.5, delta = 0.25, h = 0.1, tau0 = 0.3, tau1 = 0.95;
+  int n_f = 17, n_s = 9, Q = 5;
+  int64_t N = 0, n_shell = 0, n_cart = 0;
+  int grid_m = 0;                 // interior grid indices -m..m per axis
+  std::vector<double> x;          // N x 3
+  std::vector<double> w_q;        // quadrature weight
+  std::vector<double> omega, psi; // depth partition of unity, surface share (0 on the interior grid)
+  std::vector<int8_t> face;       // shell face 0..5, -1 interior
+  std::vector<int32_t> grid;      // N x 3: shell (i, j, k) on its face grid, interior (ix, iy, iz) + m
+  std::string err;
+};
+bool build_ball3(Ball3& b);
+// Window (2 Wn + 1)^3 of the interior singular rule's coefficients over grid
+// offsets ([di][dj][dk], offsets -Wn..Wn) for a grid-point target.
+bool interior_window3(double kappa, double h, double R, int p, int q, int n_rho, int n_mu, int n_phi, double chi_s0,
+                      std::vector<cd>& win, int* Wn, std::string* err);
+
 // Truncated thin SVD of a complex m x n matrix (m >= n), one-sided Jacobi.
 struct SVD {
   int m = 0, n = 0, k = 0;

@@ -88,6 +88,12 @@ _SIGS = {
     "ls_host_accel3_sizes": ([C.c_void_p, C.c_void_p]),
     "ls_host_accel3_get": ([C.c_void_p] + [C.c_void_p] * 9),
     "ls_host_accel3_destroy": ([C.c_void_p]),
+    "ls_host_ball3_create": ([C.c_void_p, C.POINTER(C.c_void_p)]),
+    "ls_host_ball3_sizes": ([C.c_void_p, C.c_void_p]),
+    "ls_host_ball3_nodes": ([C.c_void_p] + [C.c_void_p] * 6),
+    "ls_host_ball3_destroy": ([C.c_void_p]),
+    "ls_interior_window3": ([C.c_double, C.c_double, C.c_double, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
+                             C.c_double, C.c_void_p, C.POINTER(C.c_int)]),
     "ls_set_stage_timing": ([C.c_void_p, C.c_int]),
     "ls_apply_noalloc": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
     "ls_check_cells": ([C.POINTER(Geometry), N2FN, C.c_void_p, C.c_double, C.POINTER(Options), C.c_void_p]),
@@ -396,6 +402,64 @@ class HostAccel3:
             self.close()
         except Exception:
             pass
+
+
+class Ball3Params(C.Structure):
+    _fields_ = [("a", C.c_double), ("w", C.c_double), ("n_f", C.c_int), ("n_s", C.c_int), ("Q", C.c_int),
+                ("delta", C.c_double), ("h", C.c_double), ("tau0", C.c_double), ("tau1", C.c_double)]
+
+
+class HostBall3:
+    """Host-only 3-D ball discretisation (ls_host_ball3_*): nodes, weights,
+    partitions of unity and grid indices as numpy arrays."""
+
+    def __init__(self, a=1.0, w=0.5, n_f=17, n_s=9, Q=5, delta=0.25, h=0.1, tau0=0.3, tau1=0.95):
+        load_library()
+        prm = Ball3Params(float(a), float(w), int(n_f), int(n_s), int(Q), float(delta), float(h), float(tau0),
+                          float(tau1))
+        hd = C.c_void_p()
+        st = _lib.ls_host_ball3_create(C.byref(prm), C.byref(hd))
+        if st != 0:
+            raise LSError(st, _lib.ls_last_error(None).decode())
+        self._h = hd
+        sz = np.zeros(4, np.int64)
+        _check(_lib.ls_host_ball3_sizes(hd, sz.ctypes.data))
+        self.N, self.n_shell, self.n_cart, self.grid_m = map(int, sz)
+
+    def nodes(self):
+        x = np.zeros((self.N, 3))
+        w = np.zeros(self.N)
+        om = np.zeros(self.N)
+        psi = np.zeros(self.N)
+        face = np.zeros(self.N, np.int8)
+        grid = np.zeros((self.N, 3), np.int32)
+        _check(_lib.ls_host_ball3_nodes(self._h, x.ctypes.data, w.ctypes.data, om.ctypes.data, psi.ctypes.data,
+                                        face.ctypes.data, grid.ctypes.data))
+        return dict(x=x, w=w, omega=om, psi=psi, face=face, grid=grid)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.ls_host_ball3_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def interior_window3(kappa, h, R=3.0, p=5, q=3, n_rho=16, n_mu=16, n_phi=32, chi_s0=0.1):
+    """Window (2 Wn + 1)^3 of the 3-D interior singular rule (ls_interior_window3)."""
+    load_library()
+    Wn = C.c_int()
+    args = (float(kappa), float(h), float(R), int(p), int(q), int(n_rho), int(n_mu), int(n_phi), float(chi_s0))
+    st = _lib.ls_interior_window3(*args, None, C.byref(Wn))
+    if st != 0:
+        raise LSError(st, _lib.ls_last_error(None).decode())
+    win = np.zeros((2 * Wn.value + 1,) * 3, np.complex128)
+    _check(_lib.ls_interior_window3(*args, win.ctypes.data, C.byref(Wn)))
+    return win, Wn.value
 
 
 class Batch:

@@ -209,3 +209,41 @@ def test_host_accel3_reproduces_oracle_far_field(lib):
         HostAccel3(dz.x, wfac, 2.0, [-0.5] * 3, 2.26 / L, L, Ne)
     with pytest.raises(LSError, match="more terms"):
         HostAccel3(dz.x, wfac, 2.0, [-1.13] * 3, 2.26 / L, L, 2, p=5)
+
+
+def test_host_ball3_matches_oracle_discretisation(lib):
+    """The library's 3-D ball discretisation (six blended cubed-sphere shell
+    faces, interior grid) node for node against the oracle's: positions,
+    weights, partitions of unity, faces and grid indices."""
+    from paper_1509_05063_gb300 import HostBall3, LSError
+    from oracle.geometry3d import Ball3, Discretisation3
+    for nf, ns, h in ((9, 5, 0.2), (25, 9, 0.1)):
+        dz = Discretisation3(Ball3(n_f=nf, n_s=ns, h=h))
+        hb = HostBall3(n_f=nf, n_s=ns, h=h)
+        assert (hb.N, hb.n_shell, hb.grid_m) == (dz.N, dz.n_shell, dz.grid_m)
+        nd = hb.nodes()
+        assert np.max(np.abs(nd["x"] - dz.x)) < 1e-15
+        assert np.max(np.abs(nd["w"] - dz.w) / dz.w) < 1e-14
+        assert np.max(np.abs(nd["omega"] - dz.omega)) < 1e-15
+        assert np.max(np.abs(nd["psi"] - dz.psi)) < 1e-15
+        assert np.array_equal(nd["face"], dz.face)
+        assert np.array_equal(nd["grid"][:dz.n_shell], dz.fijk[:dz.n_shell])
+        assert np.array_equal(nd["grid"][dz.n_shell:], np.rint(dz.x[dz.n_shell:] / h).astype(int) + dz.grid_m)
+    with pytest.raises(LSError, match="multiple of Q - 1"):
+        HostBall3(n_s=8)
+    with pytest.raises(LSError, match="tau0"):
+        HostBall3(tau0=0.9, tau1=0.5)
+
+
+def test_host_interior_window3_matches_oracle(lib):
+    """The library's window of the 3-D interior singular rule against the
+    oracle's (same rule, same interpolation), at two wavenumbers and spacings."""
+    from paper_1509_05063_gb300 import LSError, interior_window3
+    from oracle.quadrature3d import interior_singular_window
+    for k, h in ((2.0, 0.1), (5.0, 0.05)):
+        w0, W0 = interior_singular_window(k, h, 3.0, 5)
+        w1, W1 = interior_window3(k, h, 3.0, 5)
+        assert W1 == W0
+        assert np.max(np.abs(w1 - w0)) < 1e-13 * np.max(np.abs(w0))
+    with pytest.raises(LSError, match="interior rule"):
+        interior_window3(2.0, -0.1)
