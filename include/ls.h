@@ -371,6 +371,37 @@ ls_status ls_host_ball3_nodes(ls_host_ball3 h, double* xyz, double* w, double* o
                               int32_t* grid);
 ls_status ls_host_ball3_destroy(ls_host_ball3 h);
 
+/* One row of the 3-D operator K (Section 5) at node q of a ball:
+ * K[u](x_q) = sum_n row[n] u[n] with u the density at the nodes (the contrast
+ * m = 1 - n^2 is applied by the caller: the discrete equation is
+ * u + kappa^2 K[m u] = u^i).  The row is the sum of
+ *  - the interior patch's spherical rule about x_q (as ls_interior_window3,
+ *    at any position), when its cut-off ball reaches interior nodes;
+ *  - on every shell face whose extended chart holds x_q's direction: for a
+ *    shell target, polar coordinates (rho = rc sigma^q, n_sig - 1 trapezoid
+ *    points in sigma, n_th in the angle) in the face parameters about the
+ *    target, times the split Newton-Cotes rule across the depth over the lines
+ *    within rs of the target's line; for an interior target above the chart's
+ *    bottom, an ellipsoidal spherical rule in the face's index space (semi-axes
+ *    rc, rc, min(rs, tau0 (n_s - 1))), points past the bottom line dropped;
+ *    degree-p Lagrange interpolation along the surface and degree
+ *    min(p, n_s - 1) (clamped stencil) across the depth;
+ *  - the regular sum w omega G (1 - eta) over every node, eta the product
+ *    cut-offs of the rules applied.
+ * rules NULL selects the defaults R = 3, p = 5, q = 3, n_rho = 16, n_mu = 16,
+ * n_phi = 32, rc = rs = 6, n_sig = 20, n_th = 32, chi_s0 = 0.1.  row: N
+ * complex (interleaved doubles); eta: N doubles or NULL. */
+typedef struct {
+  double R;              /* interior cut-off radius (grid units)                */
+  int p, q;              /* Lagrange degree, radial map rho = r s^q             */
+  int n_rho, n_mu, n_phi;
+  double rc, rs;         /* shell cut-off: along the surface / across the depth  */
+  int n_sig, n_th;
+  double chi_s0;         /* cut-off plateau                                     */
+} ls_rules3;
+ls_status ls_host_ball3_row(ls_host_ball3 h, double kappa, const ls_rules3* rules, int64_t q, double* row,
+                            double* eta);
+
 /* Coefficients c[o] of the interior singular rule for a target on a uniform
  * grid of spacing h: int G(x, y) eta(|y - x| / (R h)) phi(y) dy is
  * sum_o c[o] phi(x + o h) over offsets o in [-Wn, Wn]^3, Wn = ceil(R) + p/2 + 2,

@@ -519,6 +519,34 @@ ls_status ls_host_ball3_nodes(ls_host_ball3 h, double* xyz, double* w, double* o
   return LS_OK;
 }
 
+ls_status ls_host_ball3_row(ls_host_ball3 h, double kappa, const ls_rules3* rules, int64_t q, double* row,
+                            double* eta) {
+  if (!h || !row) return fail(nullptr, LS_ERR_INVALID, "NULL handle or row");
+  if (!(kappa >= 0)) return fail(nullptr, LS_ERR_INVALID, "kappa must be >= 0");
+  lsh::Rules3 ru;
+  if (rules) {
+    ru.R = rules->R;
+    ru.p = rules->p;
+    ru.q = rules->q;
+    ru.n_rho = rules->n_rho;
+    ru.n_mu = rules->n_mu;
+    ru.n_phi = rules->n_phi;
+    ru.rc = rules->rc;
+    ru.rs = rules->rs;
+    ru.n_sig = rules->n_sig;
+    ru.n_th = rules->n_th;
+    ru.chi_s0 = rules->chi_s0;
+  }
+  std::string m;
+  try {
+    if (!lsh::ball3_row(h->B, kappa, ru, q, reinterpret_cast<lsh::cd*>(row), eta, &m))
+      return fail(nullptr, LS_ERR_INVALID, m);
+  } catch (const std::bad_alloc&) {
+    return fail(nullptr, LS_ERR_NOMEM, "host allocation failed");
+  }
+  return LS_OK;
+}
+
 ls_status ls_host_ball3_destroy(ls_host_ball3 h) {
   delete h;
   return LS_OK;

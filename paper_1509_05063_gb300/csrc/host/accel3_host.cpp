@@ -173,7 +173,8 @@ bool build_accel3(Accel3& A3, const double* xyz, const double* wfac, int64_t N) 
   // neighbour tables T_o and BT_o = B^+ T_o, o index (oi + 1) 9 + (oj + 1) 3 + (ok + 1)
   auto table = [&](int da, int db, int dc, int kind) -> cd {
     if (da == 0 && db == 0 && dc == 0) return cd(0.0);
-    return kind == 0 ? mono3(kappa, da * delta, db * delta, dc * delta) : dip3(kappa, da * delta, db * delta, dc * delta);
+    const double dx = da * delta, dy = db * delta, dz = dc * delta;
+    return kind == 0 ? mono3(kappa, dx, dy, dz) : dip3(kappa, dx, dy, dz);
   };
   A3.BT.assign(size_t(27) * nb * n_es, cd(0.0));
   parallel_for(A3.n_threads, 27, 1, [&](int64_t o0, int64_t o1) {

@@ -17,6 +17,7 @@
 // from degree-p tensor-product Lagrange interpolation on the grid, so the rule
 // is a fixed window of coefficients over grid offsets.
 #include <cmath>
+#include <map>
 
 #include "host_plan.hpp"
 
@@ -165,6 +166,16 @@ bool build_ball3(Ball3& B) {
       }
   B.N = int64_t(B.w_q.size());
   B.n_cart = B.N - B.n_shell;
+  B.face_node.assign(size_t(6) * nf * nf * ns, -1);
+  const int side = 2 * m + 1;
+  B.cart_node.assign(size_t(side) * side * side, -1);
+  for (int64_t n = 0; n < B.N; ++n) {
+    const int32_t* gi = &B.grid[3 * n];
+    if (n < B.n_shell)
+      B.face_node[((size_t(B.face[n]) * nf + gi[0]) * nf + gi[1]) * ns + gi[2]] = n;
+    else
+      B.cart_node[(size_t(gi[0]) * side + gi[1]) * side + gi[2]] = n;
+  }
   return true;
 }
 
@@ -209,6 +220,208 @@ bool interior_window3(double kappa, double h, double R, int p, int q, int n_rho,
       }
     }
   }
+  return true;
+}
+
+namespace {
+
+// Split Newton-Cotes lines and weights across the depth for a target on line
+// j of lines 0..nb-1 (Eq. VolInt-Adj-Sing-MultiSplit): composite Q-point
+// blocks outward from j, and each interval left over near an end gets a
+// Q-point rule on fractional lines.
+std::map<double, double> split_nc(int j, int nb, int Q) {
+  const std::vector<double> nc = newton_cotes(Q);
+  std::map<double, double> out;
+  const int L1 = j / (Q - 1);
+  for (int l = 1; l <= L1; ++l)
+    for (int mm = 0; mm < Q; ++mm) out[double(j - l * (Q - 1) + mm)] += nc[mm];
+  const int I1 = j - L1 * (Q - 1);
+  for (int i = 1; i <= I1; ++i)
+    for (int mm = 0; mm < Q; ++mm) out[(j - L1 * (Q - 1) - i) + double(mm) / (Q - 1)] += nc[mm] / (Q - 1);
+  const int top = nb - 1;
+  const int L2 = (top - j) / (Q - 1);
+  for (int l = 1; l <= L2; ++l)
+    for (int mm = 0; mm < Q; ++mm) out[double(j + (l - 1) * (Q - 1) + mm)] += nc[mm];
+  const int I2 = (top - j) - L2 * (Q - 1);
+  for (int i = 1; i <= I2; ++i)
+    for (int mm = 0; mm < Q; ++mm) out[(j + L2 * (Q - 1) + (i - 1)) + double(mm) / (Q - 1)] += nc[mm] / (Q - 1);
+  return out;
+}
+
+// row[node] += f * La Lb Lc * factor[node] over the tensor stencil of one
+// point; node_of maps grid (na, nb, nc) to a node id or -1.
+inline void scatter(cd* row, const int64_t* node_of, int na, int nb, int nc, const int64_t* st, const double* La,
+                    const double* Lb, const double* Lc, int pa, int pc, cd f, const std::vector<double>& factor) {
+  for (int i = 0; i <= pa; ++i) {
+    const int64_t ia = st[0] + i;
+    if (ia < 0 || ia >= na) continue;
+    for (int j = 0; j <= pa; ++j) {
+      const int64_t ib = st[1] + j;
+      if (ib < 0 || ib >= nb) continue;
+      const cd fij = f * (La[i] * Lb[j]);
+      for (int k = 0; k <= pc; ++k) {
+        const int64_t ic = st[2] + k;
+        if (ic < 0 || ic >= nc) continue;
+        const int64_t n = node_of[(size_t(ia) * nb + size_t(ib)) * nc + size_t(ic)];
+        if (n >= 0) row[n] += fij * Lc[k] * factor[n];
+      }
+    }
+  }
+}
+
+}  // namespace
+
+bool ball3_row(const Ball3& B, double kappa, const Rules3& ru, int64_t qn, cd* row, double* eta_out,
+               std::string* err) {
+  if (qn < 0 || qn >= B.N) { *err = "node index out of range"; return false; }
+  if (!(ru.R > 0 && ru.rc > 0 && ru.rs > 0) || ru.p < 1 || ru.q < 1 || ru.n_rho < 2 || ru.n_mu < 1 ||
+      ru.n_phi < 1 || ru.n_sig < 2 || ru.n_th < 1 || !(ru.chi_s0 >= 0 && ru.chi_s0 < 1)) {
+    *err = "invalid rule parameters";
+    return false;
+  }
+  const int64_t N = B.N;
+  const int nf = B.n_f, ns = B.n_s, p = ru.p, ps = std::min(ru.p, ns - 1);
+  const double h = B.h;
+  const double half = M_PI / 4 + B.delta, dg = (2 * half) / (nf - 1), ds = 1.0 / (ns - 1);
+  const double* x = &B.x[3 * qn];
+  std::vector<double> eta(N, 0.0), fac_shell(N), fac_cart(N);
+  for (int64_t n = 0; n < N; ++n) {
+    fac_shell[n] = B.psi[n] * B.omega[n];
+    fac_cart[n] = B.omega[n];
+  }
+  std::fill(row, row + N, cd(0.0));
+  std::vector<double> mu, wmu;
+  gauss_legendre(ru.n_mu, mu, wmu);
+  std::vector<double> La(p + 1), Lb(p + 1), Lc(p + 1);
+  auto chi = [&](double v) { return cutoff(v, ru.chi_s0); };
+  // ---- interior patch: spherical rule about x, if it reaches interior nodes
+  bool reach = false;
+  for (int64_t n = B.n_shell; n < N && !reach; ++n) {
+    const double dx = B.x[3 * n] - x[0], dy = B.x[3 * n + 1] - x[1], dz = B.x[3 * n + 2] - x[2];
+    reach = std::sqrt(dx * dx + dy * dy + dz * dz) < ru.R * h;
+  }
+  if (reach) {
+    const int side = 2 * B.grid_m + 1;
+    for (int ir = 1; ir < ru.n_rho; ++ir) {
+      const double sv = double(ir) / ru.n_rho, rho = ru.R * std::pow(sv, ru.q);
+      const double wr = (1.0 / ru.n_rho) * ru.R * ru.q * std::pow(sv, ru.q - 1) * chi(std::pow(sv, ru.q));
+      const cd kern = std::polar(rho * h * h / (4 * M_PI), kappa * rho * h);
+      for (int im = 0; im < ru.n_mu; ++im) {
+        const double st = std::sqrt(1 - mu[im] * mu[im]);
+        for (int ip = 0; ip < ru.n_phi; ++ip) {
+          const double ph = 2 * M_PI * ip / ru.n_phi;
+          const double d[3] = {st * std::cos(ph), st * std::sin(ph), mu[im]};
+          const cd f = (wr * wmu[im] * (2 * M_PI / ru.n_phi)) * kern;
+          double c[3];
+          int64_t s0[3];
+          for (int k = 0; k < 3; ++k) {
+            c[k] = x[k] / h + B.grid_m + rho * d[k];
+            s0[k] = int64_t(std::floor(c[k])) - p / 2;
+          }
+          lagrange_row(c[0], s0[0], p, La.data());
+          lagrange_row(c[1], s0[1], p, Lb.data());
+          lagrange_row(c[2], s0[2], p, Lc.data());
+          scatter(row, B.cart_node.data(), side, side, side, s0, La.data(), Lb.data(), Lc.data(), p, p, f, fac_cart);
+        }
+      }
+    }
+    for (int64_t n = B.n_shell; n < N; ++n) {
+      const double dx = B.x[3 * n] - x[0], dy = B.x[3 * n + 1] - x[1], dz = B.x[3 * n + 2] - x[2];
+      eta[n] = chi(std::sqrt(dx * dx + dy * dy + dz * dz) / (ru.R * h));
+    }
+  }
+  // ---- shell patches: a rule on every face whose extended chart holds x
+  const double r_x = std::sqrt(dot3(x, x));
+  const double s_x = (B.a - r_x) / B.w;
+  const bool is_shell = qn < B.n_shell;
+  if (s_x < 1.0) {
+    const double dirx[3] = {x[0] / r_x, x[1] / r_x, x[2] / r_x};
+    for (int G = 0; G < 6; ++G) {
+      const double zc = dot3(dirx, kFaces[G][2]);
+      if (zc <= 1e-12) continue;
+      const double xi = std::atan2(dot3(dirx, kFaces[G][0]), zc), et = std::atan2(dot3(dirx, kFaces[G][1]), zc);
+      const double cx = (xi + half) / dg, cy = (et + half) / dg;
+      if (!(cx >= 0.0 && cx <= nf - 1 && cy >= 0.0 && cy <= nf - 1)) continue;
+      // rule points in face-grid index coordinates (ti, tj, tk) and weights wq
+      std::vector<double> ti, tj, tk, wq;
+      if (is_shell) {
+        const int k0 = B.grid[3 * qn + 2];
+        const std::map<double, double> lines = split_nc(k0, ns, B.Q);
+        for (const auto& [t, wl] : lines) {
+          if (!(std::fabs(t - k0) < ru.rs)) continue;
+          const double wsl = wl * chi((t - k0) / ru.rs);
+          for (int is = 1; is < ru.n_sig; ++is) {
+            const double sg = double(is) / ru.n_sig, rho = ru.rc * std::pow(sg, ru.q);
+            const double wsg = (1.0 / ru.n_sig) * ru.rc * ru.q * std::pow(sg, ru.q - 1) * chi(std::pow(sg, ru.q));
+            for (int it = 0; it < ru.n_th; ++it) {
+              const double th = 2 * M_PI * it / ru.n_th;
+              ti.push_back(cx + rho * std::cos(th));
+              tj.push_back(cy + rho * std::sin(th));
+              tk.push_back(t);
+              wq.push_back(wsl * wsg * (2 * M_PI / ru.n_th) * rho);
+            }
+          }
+        }
+      } else {
+        const double cz = s_x / ds, rsp = std::min(ru.rs, B.tau0 * (ns - 1));
+        for (int ir = 1; ir < ru.n_rho; ++ir) {
+          const double sv = double(ir) / ru.n_rho, rho = std::pow(sv, ru.q);
+          const double wr = (1.0 / ru.n_rho) * ru.q * std::pow(sv, ru.q - 1) * chi(rho);
+          for (int im = 0; im < ru.n_mu; ++im) {
+            const double st = std::sqrt(1 - mu[im] * mu[im]);
+            for (int ip = 0; ip < ru.n_phi; ++ip) {
+              const double ph = 2 * M_PI * ip / ru.n_phi;
+              const double tkv = cz + rsp * rho * mu[im];
+              ti.push_back(cx + ru.rc * rho * st * std::cos(ph));
+              tj.push_back(cy + ru.rc * rho * st * std::sin(ph));
+              tk.push_back(tkv);
+              // past the chart's bottom line phi_F is exactly zero: drop the point
+              const double wv = wr * wmu[im] * (2 * M_PI / ru.n_phi) * rho * rho * ru.rc * ru.rc * rsp;
+              wq.push_back(tkv <= ns - 1 ? wv : 0.0);
+            }
+          }
+        }
+      }
+      const int64_t* node_of = &B.face_node[size_t(G) * nf * nf * ns];
+      for (size_t r = 0; r < wq.size(); ++r) {
+        double dd[3], dom;
+        face_direction(G, ti[r] * dg - half, tj[r] * dg - half, dd, &dom);
+        const double rp = B.a - tk[r] * ds * B.w;
+        const double y[3] = {rp * dd[0], rp * dd[1], rp * dd[2]};
+        const double J = B.w * rp * rp * dom * dg * dg * ds;
+        const double dist = std::sqrt((y[0] - x[0]) * (y[0] - x[0]) + (y[1] - x[1]) * (y[1] - x[1]) +
+                                      (y[2] - x[2]) * (y[2] - x[2]));
+        const cd f = std::polar(wq[r] * J / (4 * M_PI * dist), kappa * dist);
+        int64_t s0[3];
+        s0[0] = int64_t(std::floor(ti[r])) - p / 2;
+        s0[1] = int64_t(std::floor(tj[r])) - p / 2;
+        s0[2] = std::min<int64_t>(std::max<int64_t>(int64_t(std::floor(tk[r])) - ps / 2, 0), ns - 1 - ps);
+        lagrange_row(ti[r], s0[0], p, La.data());
+        lagrange_row(tj[r], s0[1], p, Lb.data());
+        lagrange_row(tk[r], s0[2], ps, Lc.data());
+        scatter(row, node_of, nf, nf, ns, s0, La.data(), Lb.data(), Lc.data(), p, ps, f, fac_shell);
+      }
+      for (int64_t n = 0; n < B.n_shell; ++n) {
+        if (B.face[n] != G) continue;
+        const double fi = B.grid[3 * n], fj = B.grid[3 * n + 1], fk = B.grid[3 * n + 2];
+        if (is_shell) {
+          const int k0 = B.grid[3 * qn + 2];
+          eta[n] = chi(std::hypot(fi - cx, fj - cy) / ru.rc) * chi((fk - k0) / ru.rs);
+        } else {
+          const double cz = s_x / ds, rsp = std::min(ru.rs, B.tau0 * (ns - 1));
+          const double a = (fi - cx) / ru.rc, b = (fj - cy) / ru.rc, c = (fk - cz) / rsp;
+          eta[n] = chi(std::sqrt(a * a + b * b + c * c));
+        }
+      }
+    }
+  }
+  // ---- regular rule with (1 - eta)
+  for (int64_t n = 0; n < N; ++n) {
+    const double dx = B.x[3 * n] - x[0], dy = B.x[3 * n + 1] - x[1], dz = B.x[3 * n + 2] - x[2];
+    const double dist = std::sqrt(dx * dx + dy * dy + dz * dz);
+    if (dist > 0) row[n] += std::polar(B.w_q[n] * B.omega[n] * (1.0 - eta[n]) / (4 * M_PI * dist), kappa * dist);
+  }
+  if (eta_out) std::copy(eta.begin(), eta.end(), eta_out);
   return true;
 }
 

@@ -137,9 +137,23 @@ struct Ball3 {
   std::vector<double> omega, psi; // depth partition of unity, surface share (0 on the interior grid)
   std::vector<int8_t> face;       // shell face 0..5, -1 interior
   std::vector<int32_t> grid;      // N x 3: shell (i, j, k) on its face grid, interior (ix, iy, iz) + m
+  std::vector<int64_t> face_node; // [F][i][j][k] -> node or -1 (6 n_f n_f n_s)
+  std::vector<int64_t> cart_node; // [ix][iy][iz] -> node or -1 ((2m + 1)^3)
   std::string err;
 };
 bool build_ball3(Ball3& b);
+// Parameters of the 3-D singular rules (index units of the grids).
+struct Rules3 {
+  double R = 3.0;                          // interior cut-off radius (grid units)
+  int p = 5, q = 3, n_rho = 16, n_mu = 16, n_phi = 32;
+  double rc = 6.0, rs = 6.0;               // shell cut-off: along the surface / across the depth
+  int n_sig = 20, n_th = 32;
+  double chi_s0 = 0.1;
+};
+// Row of the 3-D operator K at node qn: K[u](x_q) = sum_n row[n] u[n] (contrast
+// folded in by the caller); eta (optional, N) receives the cut-off values of
+// every rule applied.
+bool ball3_row(const Ball3& b, double kappa, const Rules3& ru, int64_t qn, cd* row, double* eta, std::string* err);
 // Window (2 Wn + 1)^3 of the interior singular rule's coefficients over grid
 // offsets ([di][dj][dk], offsets -Wn..Wn) for a grid-point target.
 bool interior_window3(double kappa, double h, double R, int p, int q, int n_rho, int n_mu, int n_phi, double chi_s0,

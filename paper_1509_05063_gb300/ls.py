@@ -92,6 +92,7 @@ _SIGS = {
     "ls_host_ball3_sizes": ([C.c_void_p, C.c_void_p]),
     "ls_host_ball3_nodes": ([C.c_void_p] + [C.c_void_p] * 6),
     "ls_host_ball3_destroy": ([C.c_void_p]),
+    "ls_host_ball3_row": ([C.c_void_p, C.c_double, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
     "ls_interior_window3": ([C.c_double, C.c_double, C.c_double, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
                              C.c_double, C.c_void_p, C.POINTER(C.c_int)]),
     "ls_set_stage_timing": ([C.c_void_p, C.c_int]),
@@ -409,6 +410,12 @@ class Ball3Params(C.Structure):
                 ("delta", C.c_double), ("h", C.c_double), ("tau0", C.c_double), ("tau1", C.c_double)]
 
 
+class Rules3Params(C.Structure):
+    _fields_ = [("R", C.c_double), ("p", C.c_int), ("q", C.c_int), ("n_rho", C.c_int), ("n_mu", C.c_int),
+                ("n_phi", C.c_int), ("rc", C.c_double), ("rs", C.c_double), ("n_sig", C.c_int), ("n_th", C.c_int),
+                ("chi_s0", C.c_double)]
+
+
 class HostBall3:
     """Host-only 3-D ball discretisation (ls_host_ball3_*): nodes, weights,
     partitions of unity and grid indices as numpy arrays."""
@@ -436,6 +443,21 @@ class HostBall3:
         _check(_lib.ls_host_ball3_nodes(self._h, x.ctypes.data, w.ctypes.data, om.ctypes.data, psi.ctypes.data,
                                         face.ctypes.data, grid.ctypes.data))
         return dict(x=x, w=w, omega=om, psi=psi, face=face, grid=grid)
+
+    def row(self, kappa: float, q: int, rules: dict | None = None):
+        """Row q of the 3-D operator K (ls_host_ball3_row) and the cut-off values eta."""
+        prm = None
+        if rules is not None:
+            d = dict(R=3.0, p=5, q=3, n_rho=16, n_mu=16, n_phi=32, rc=6.0, rs=6.0, n_sig=20, n_th=32, chi_s0=0.1)
+            d.update(rules)
+            prm = Rules3Params(**d)
+        row = np.zeros(self.N, np.complex128)
+        eta = np.zeros(self.N)
+        st = _lib.ls_host_ball3_row(self._h, float(kappa), C.byref(prm) if prm is not None else None, int(q),
+                                    row.ctypes.data, eta.ctypes.data)
+        if st != 0:
+            raise LSError(st, _lib.ls_last_error(None).decode())
+        return row, eta
 
     def close(self):
         if getattr(self, "_h", None):

@@ -247,3 +247,25 @@ def test_host_interior_window3_matches_oracle(lib):
         assert np.max(np.abs(w1 - w0)) < 1e-13 * np.max(np.abs(w0))
     with pytest.raises(LSError, match="interior rule"):
         interior_window3(2.0, -0.1)
+
+
+def test_host_ball3_rows_match_oracle(lib):
+    """Rows of the library's 3-D operator (interior spherical rule, shell
+    boundary and interior-type rules with split Newton-Cotes, regular sums with
+    1 - eta) against the oracle's rows at random shell and interior targets."""
+    from paper_1509_05063_gb300 import HostBall3, LSError
+    from oracle.geometry3d import Ball3, Discretisation3
+    from oracle.quadrature3d import k_row
+    rng = np.random.default_rng(12)
+    for nf, ns, h, n in ((13, 5, 0.2, 4), (25, 9, 0.1, 3)):
+        dz = Discretisation3(Ball3(n_f=nf, n_s=ns, h=h))
+        hb = HostBall3(n_f=nf, n_s=ns, h=h)
+        tg = np.concatenate([rng.choice(dz.n_shell, n, replace=False),
+                             dz.n_shell + rng.choice(dz.n_cart, n, replace=False)])
+        for q in tg:
+            ref = k_row(dz, 2.0, int(q))
+            got, eta = hb.row(2.0, int(q))
+            assert np.max(np.abs(got - ref)) < 1e-13 * np.max(np.abs(ref))
+            assert eta.min() >= 0.0 and eta.max() <= 1.0
+    with pytest.raises(LSError, match="out of range"):
+        hb.row(2.0, hb.N)
