@@ -402,6 +402,22 @@ typedef struct {
 ls_status ls_host_ball3_row(ls_host_ball3 h, double kappa, const ls_rules3* rules, int64_t q, double* row,
                             double* eta);
 
+/* Adjacent part of the 3-D operator (Section 5 with the adjacency of
+ * Section 3.2) for the rows listed (rows NULL: every node, in node order):
+ * every singular rule of the row plus the regular (1 - eta) terms of the
+ * nodes in the 3 x 3 x 3 block of cube cells (side H, L per axis from corner
+ * box0[3]) around the target's cell.  The far part (every node outside that
+ * block, weight w omega m G) is the accelerator's (ls_host_accel3_*).  Every
+ * cut-off eta must vanish outside the block: LS_ERR_INVALID otherwise, as
+ * when a node lies outside the cell box.  The result is kept in the handle
+ * (replacing an earlier one) as a CSR matrix over the listed rows with sorted
+ * columns; *nnz receives its entry count.  ls_host_ball3_near_get copies it:
+ * rowptr (n_rows + 1), col (nnz), val (nnz complex, interleaved doubles);
+ * any pointer may be NULL. */
+ls_status ls_host_ball3_near(ls_host_ball3 h, double kappa, const ls_rules3* rules, const double* box0, double H,
+                             int L, const int64_t* rows, int64_t n_rows, int n_threads, int64_t* nnz);
+ls_status ls_host_ball3_near_get(ls_host_ball3 h, int64_t* rowptr, int32_t* col, double* val);
+
 /* Coefficients c[o] of the interior singular rule for a target on a uniform
  * grid of spacing h: int G(x, y) eta(|y - x| / (R h)) phi(y) dy is
  * sum_o c[o] phi(x + o h) over offsets o in [-Wn, Wn]^3, Wn = ceil(R) + p/2 + 2,

@@ -519,31 +519,61 @@ ls_status ls_host_ball3_nodes(ls_host_ball3 h, double* xyz, double* w, double* o
   return LS_OK;
 }
 
+
+static lsh::Rules3 rules_from(const ls_rules3* r) {
+  lsh::Rules3 ru;
+  if (r) {
+    ru.R = r->R;
+    ru.p = r->p;
+    ru.q = r->q;
+    ru.n_rho = r->n_rho;
+    ru.n_mu = r->n_mu;
+    ru.n_phi = r->n_phi;
+    ru.rc = r->rc;
+    ru.rs = r->rs;
+    ru.n_sig = r->n_sig;
+    ru.n_th = r->n_th;
+    ru.chi_s0 = r->chi_s0;
+  }
+  return ru;
+}
+
 ls_status ls_host_ball3_row(ls_host_ball3 h, double kappa, const ls_rules3* rules, int64_t q, double* row,
                             double* eta) {
   if (!h || !row) return fail(nullptr, LS_ERR_INVALID, "NULL handle or row");
   if (!(kappa >= 0)) return fail(nullptr, LS_ERR_INVALID, "kappa must be >= 0");
-  lsh::Rules3 ru;
-  if (rules) {
-    ru.R = rules->R;
-    ru.p = rules->p;
-    ru.q = rules->q;
-    ru.n_rho = rules->n_rho;
-    ru.n_mu = rules->n_mu;
-    ru.n_phi = rules->n_phi;
-    ru.rc = rules->rc;
-    ru.rs = rules->rs;
-    ru.n_sig = rules->n_sig;
-    ru.n_th = rules->n_th;
-    ru.chi_s0 = rules->chi_s0;
-  }
   std::string m;
   try {
-    if (!lsh::ball3_row(h->B, kappa, ru, q, reinterpret_cast<lsh::cd*>(row), eta, &m))
+    if (!lsh::ball3_row(h->B, kappa, rules_from(rules), q, reinterpret_cast<lsh::cd*>(row), eta, &m))
       return fail(nullptr, LS_ERR_INVALID, m);
   } catch (const std::bad_alloc&) {
     return fail(nullptr, LS_ERR_NOMEM, "host allocation failed");
   }
+  return LS_OK;
+}
+
+ls_status ls_host_ball3_near(ls_host_ball3 h, double kappa, const ls_rules3* rules, const double* box0, double H,
+                             int L, const int64_t* rows, int64_t n_rows, int n_threads, int64_t* nnz) {
+  if (!h || !box0 || !nnz) return fail(nullptr, LS_ERR_INVALID, "NULL handle, box0 or nnz");
+  if (!(kappa >= 0) || (rows && n_rows < 0)) return fail(nullptr, LS_ERR_INVALID, "invalid kappa or row count");
+  const int nt = n_threads > 0 ? n_threads : int(std::max(1u, std::thread::hardware_concurrency()));
+  std::string m;
+  try {
+    if (!lsh::ball3_near(h->B, kappa, rules_from(rules), box0, H, L, rows, n_rows, nt, &m))
+      return fail(nullptr, LS_ERR_INVALID, m);
+  } catch (const std::bad_alloc&) {
+    return fail(nullptr, LS_ERR_NOMEM, "host allocation failed");
+  }
+  *nnz = h->B.near_rowptr.back();
+  return LS_OK;
+}
+
+ls_status ls_host_ball3_near_get(ls_host_ball3 h, int64_t* rowptr, int32_t* col, double* val) {
+  if (!h || h->B.near_rowptr.empty()) return fail(nullptr, LS_ERR_INVALID, "no near field built");
+  const lsh::Ball3& B = h->B;
+  if (rowptr) std::memcpy(rowptr, B.near_rowptr.data(), B.near_rowptr.size() * sizeof(int64_t));
+  if (col) std::memcpy(col, B.near_col.data(), B.near_col.size() * sizeof(int32_t));
+  if (val) std::memcpy(val, B.near_val.data(), B.near_val.size() * sizeof(lsh::cd));
   return LS_OK;
 }
 

@@ -16,6 +16,8 @@
 // trapezoid rule in the azimuth; the density at the off-grid points comes
 // from degree-p tensor-product Lagrange interpolation on the grid, so the rule
 // is a fixed window of coefficients over grid offsets.
+#include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <map>
 
@@ -248,9 +250,33 @@ std::map<double, double> split_nc(int j, int nb, int Q) {
   return out;
 }
 
-// row[node] += f * La Lb Lc * factor[node] over the tensor stencil of one
+// Sparse accumulator over node ids: a dense scratch with a list of the
+// entries touched, for the singular parts of one row and their cut-offs.
+struct RowAcc {
+  std::vector<cd> v;
+  std::vector<double> eta;
+  std::vector<char> seen, eseen;
+  std::vector<int64_t> idx, eidx;
+  explicit RowAcc(int64_t N) : v(N, cd(0.0)), eta(N, 0.0), seen(N, 0), eseen(N, 0) {}
+  void add(int64_t n, cd x) {
+    if (!seen[n]) { seen[n] = 1; idx.push_back(n); }
+    v[n] += x;
+  }
+  void set_eta(int64_t n, double e) {
+    if (!eseen[n]) { eseen[n] = 1; eidx.push_back(n); }
+    eta[n] = e;
+  }
+  void clear() {
+    for (int64_t n : idx) { v[n] = 0.0; seen[n] = 0; }
+    for (int64_t n : eidx) { eta[n] = 0.0; eseen[n] = 0; }
+    idx.clear();
+    eidx.clear();
+  }
+};
+
+// acc[node] += f * La Lb Lc * factor[node] over the tensor stencil of one
 // point; node_of maps grid (na, nb, nc) to a node id or -1.
-inline void scatter(cd* row, const int64_t* node_of, int na, int nb, int nc, const int64_t* st, const double* La,
+inline void scatter(RowAcc& acc, const int64_t* node_of, int na, int nb, int nc, const int64_t* st, const double* La,
                     const double* Lb, const double* Lc, int pa, int pc, cd f, const std::vector<double>& factor) {
   for (int i = 0; i <= pa; ++i) {
     const int64_t ia = st[0] + i;
@@ -263,45 +289,58 @@ inline void scatter(cd* row, const int64_t* node_of, int na, int nb, int nc, con
         const int64_t ic = st[2] + k;
         if (ic < 0 || ic >= nc) continue;
         const int64_t n = node_of[(size_t(ia) * nb + size_t(ib)) * nc + size_t(ic)];
-        if (n >= 0) row[n] += fij * Lc[k] * factor[n];
+        if (n >= 0) acc.add(n, fij * Lc[k] * factor[n]);
       }
     }
   }
 }
 
-}  // namespace
-
-bool ball3_row(const Ball3& B, double kappa, const Rules3& ru, int64_t qn, cd* row, double* eta_out,
-               std::string* err) {
-  if (qn < 0 || qn >= B.N) { *err = "node index out of range"; return false; }
+bool check_rules(const Rules3& ru, std::string* err) {
   if (!(ru.R > 0 && ru.rc > 0 && ru.rs > 0) || ru.p < 1 || ru.q < 1 || ru.n_rho < 2 || ru.n_mu < 1 ||
       ru.n_phi < 1 || ru.n_sig < 2 || ru.n_th < 1 || !(ru.chi_s0 >= 0 && ru.chi_s0 < 1)) {
     *err = "invalid rule parameters";
     return false;
   }
-  const int64_t N = B.N;
+  return true;
+}
+
+// Index range [lo, hi] of a window |i - c| <= r clipped to 0..n-1.
+inline void window(double c, double r, int n, int* lo, int* hi) {
+  *lo = std::max(0, int(std::floor(c - r)));
+  *hi = std::min(n - 1, int(std::ceil(c + r)));
+}
+
+// The singular parts of row qn (every rule that reaches x_q) and the cut-off
+// values eta of the rules applied, accumulated sparsely.
+void singular_parts(const Ball3& B, double kappa, const Rules3& ru, int64_t qn, RowAcc& acc) {
   const int nf = B.n_f, ns = B.n_s, p = ru.p, ps = std::min(ru.p, ns - 1);
   const double h = B.h;
   const double half = M_PI / 4 + B.delta, dg = (2 * half) / (nf - 1), ds = 1.0 / (ns - 1);
   const double* x = &B.x[3 * qn];
-  std::vector<double> eta(N, 0.0), fac_shell(N), fac_cart(N);
-  for (int64_t n = 0; n < N; ++n) {
-    fac_shell[n] = B.psi[n] * B.omega[n];
-    fac_cart[n] = B.omega[n];
-  }
-  std::fill(row, row + N, cd(0.0));
+  std::vector<double> fac_shell(B.psi.size()), fac_cart(B.omega);
+  for (size_t n = 0; n < fac_shell.size(); ++n) fac_shell[n] = B.psi[n] * B.omega[n];
   std::vector<double> mu, wmu;
   gauss_legendre(ru.n_mu, mu, wmu);
   std::vector<double> La(p + 1), Lb(p + 1), Lc(p + 1);
   auto chi = [&](double v) { return cutoff(v, ru.chi_s0); };
-  // ---- interior patch: spherical rule about x, if it reaches interior nodes
-  bool reach = false;
-  for (int64_t n = B.n_shell; n < N && !reach; ++n) {
-    const double dx = B.x[3 * n] - x[0], dy = B.x[3 * n + 1] - x[1], dz = B.x[3 * n + 2] - x[2];
-    reach = std::sqrt(dx * dx + dy * dy + dz * dz) < ru.R * h;
+  // ---- interior patch: spherical rule about x, if its ball reaches interior nodes
+  const int side = 2 * B.grid_m + 1;
+  double cg[3];
+  int lo[3], hi[3];
+  for (int k = 0; k < 3; ++k) {
+    cg[k] = x[k] / h + B.grid_m;
+    window(cg[k], ru.R, side, &lo[k], &hi[k]);
   }
+  bool reach = false;
+  for (int i = lo[0]; i <= hi[0]; ++i)
+    for (int j = lo[1]; j <= hi[1]; ++j)
+      for (int k = lo[2]; k <= hi[2]; ++k) {
+        const int64_t n = B.cart_node[(size_t(i) * side + j) * side + k];
+        if (n < 0) continue;
+        const double dx = B.x[3 * n] - x[0], dy = B.x[3 * n + 1] - x[1], dz = B.x[3 * n + 2] - x[2];
+        reach = reach || std::sqrt(dx * dx + dy * dy + dz * dz) < ru.R * h;
+      }
   if (reach) {
-    const int side = 2 * B.grid_m + 1;
     for (int ir = 1; ir < ru.n_rho; ++ir) {
       const double sv = double(ir) / ru.n_rho, rho = ru.R * std::pow(sv, ru.q);
       const double wr = (1.0 / ru.n_rho) * ru.R * ru.q * std::pow(sv, ru.q - 1) * chi(std::pow(sv, ru.q));
@@ -315,113 +354,224 @@ bool ball3_row(const Ball3& B, double kappa, const Rules3& ru, int64_t qn, cd* r
           double c[3];
           int64_t s0[3];
           for (int k = 0; k < 3; ++k) {
-            c[k] = x[k] / h + B.grid_m + rho * d[k];
+            c[k] = cg[k] + rho * d[k];
             s0[k] = int64_t(std::floor(c[k])) - p / 2;
           }
           lagrange_row(c[0], s0[0], p, La.data());
           lagrange_row(c[1], s0[1], p, Lb.data());
           lagrange_row(c[2], s0[2], p, Lc.data());
-          scatter(row, B.cart_node.data(), side, side, side, s0, La.data(), Lb.data(), Lc.data(), p, p, f, fac_cart);
+          scatter(acc, B.cart_node.data(), side, side, side, s0, La.data(), Lb.data(), Lc.data(), p, p, f, fac_cart);
         }
       }
     }
-    for (int64_t n = B.n_shell; n < N; ++n) {
-      const double dx = B.x[3 * n] - x[0], dy = B.x[3 * n + 1] - x[1], dz = B.x[3 * n + 2] - x[2];
-      eta[n] = chi(std::sqrt(dx * dx + dy * dy + dz * dz) / (ru.R * h));
-    }
+    for (int i = lo[0]; i <= hi[0]; ++i)
+      for (int j = lo[1]; j <= hi[1]; ++j)
+        for (int k = lo[2]; k <= hi[2]; ++k) {
+          const int64_t n = B.cart_node[(size_t(i) * side + j) * side + k];
+          if (n < 0) continue;
+          const double dx = B.x[3 * n] - x[0], dy = B.x[3 * n + 1] - x[1], dz = B.x[3 * n + 2] - x[2];
+          const double e = chi(std::sqrt(dx * dx + dy * dy + dz * dz) / (ru.R * h));
+          if (e > 0) acc.set_eta(n, e);
+        }
   }
   // ---- shell patches: a rule on every face whose extended chart holds x
   const double r_x = std::sqrt(dot3(x, x));
   const double s_x = (B.a - r_x) / B.w;
   const bool is_shell = qn < B.n_shell;
-  if (s_x < 1.0) {
-    const double dirx[3] = {x[0] / r_x, x[1] / r_x, x[2] / r_x};
-    for (int G = 0; G < 6; ++G) {
-      const double zc = dot3(dirx, kFaces[G][2]);
-      if (zc <= 1e-12) continue;
-      const double xi = std::atan2(dot3(dirx, kFaces[G][0]), zc), et = std::atan2(dot3(dirx, kFaces[G][1]), zc);
-      const double cx = (xi + half) / dg, cy = (et + half) / dg;
-      if (!(cx >= 0.0 && cx <= nf - 1 && cy >= 0.0 && cy <= nf - 1)) continue;
-      // rule points in face-grid index coordinates (ti, tj, tk) and weights wq
-      std::vector<double> ti, tj, tk, wq;
-      if (is_shell) {
-        const int k0 = B.grid[3 * qn + 2];
-        const std::map<double, double> lines = split_nc(k0, ns, B.Q);
-        for (const auto& [t, wl] : lines) {
-          if (!(std::fabs(t - k0) < ru.rs)) continue;
-          const double wsl = wl * chi((t - k0) / ru.rs);
-          for (int is = 1; is < ru.n_sig; ++is) {
-            const double sg = double(is) / ru.n_sig, rho = ru.rc * std::pow(sg, ru.q);
-            const double wsg = (1.0 / ru.n_sig) * ru.rc * ru.q * std::pow(sg, ru.q - 1) * chi(std::pow(sg, ru.q));
-            for (int it = 0; it < ru.n_th; ++it) {
-              const double th = 2 * M_PI * it / ru.n_th;
-              ti.push_back(cx + rho * std::cos(th));
-              tj.push_back(cy + rho * std::sin(th));
-              tk.push_back(t);
-              wq.push_back(wsl * wsg * (2 * M_PI / ru.n_th) * rho);
-            }
-          }
-        }
-      } else {
-        const double cz = s_x / ds, rsp = std::min(ru.rs, B.tau0 * (ns - 1));
-        for (int ir = 1; ir < ru.n_rho; ++ir) {
-          const double sv = double(ir) / ru.n_rho, rho = std::pow(sv, ru.q);
-          const double wr = (1.0 / ru.n_rho) * ru.q * std::pow(sv, ru.q - 1) * chi(rho);
-          for (int im = 0; im < ru.n_mu; ++im) {
-            const double st = std::sqrt(1 - mu[im] * mu[im]);
-            for (int ip = 0; ip < ru.n_phi; ++ip) {
-              const double ph = 2 * M_PI * ip / ru.n_phi;
-              const double tkv = cz + rsp * rho * mu[im];
-              ti.push_back(cx + ru.rc * rho * st * std::cos(ph));
-              tj.push_back(cy + ru.rc * rho * st * std::sin(ph));
-              tk.push_back(tkv);
-              // past the chart's bottom line phi_F is exactly zero: drop the point
-              const double wv = wr * wmu[im] * (2 * M_PI / ru.n_phi) * rho * rho * ru.rc * ru.rc * rsp;
-              wq.push_back(tkv <= ns - 1 ? wv : 0.0);
-            }
+  if (!(s_x < 1.0)) return;
+  const double dirx[3] = {x[0] / r_x, x[1] / r_x, x[2] / r_x};
+  for (int G = 0; G < 6; ++G) {
+    const double zc = dot3(dirx, kFaces[G][2]);
+    if (zc <= 1e-12) continue;
+    const double xi = std::atan2(dot3(dirx, kFaces[G][0]), zc), et = std::atan2(dot3(dirx, kFaces[G][1]), zc);
+    const double cx = (xi + half) / dg, cy = (et + half) / dg;
+    if (!(cx >= 0.0 && cx <= nf - 1 && cy >= 0.0 && cy <= nf - 1)) continue;
+    // rule points in face-grid index coordinates (ti, tj, tk) and weights wq
+    std::vector<double> ti, tj, tk, wq;
+    const int k0 = is_shell ? B.grid[3 * qn + 2] : 0;
+    const double cz = s_x / ds, rsp = std::min(ru.rs, B.tau0 * (ns - 1));
+    if (is_shell) {
+      const std::map<double, double> lines = split_nc(k0, ns, B.Q);
+      for (const auto& [t, wl] : lines) {
+        if (!(std::fabs(t - k0) < ru.rs)) continue;
+        const double wsl = wl * chi((t - k0) / ru.rs);
+        for (int is = 1; is < ru.n_sig; ++is) {
+          const double sg = double(is) / ru.n_sig, rho = ru.rc * std::pow(sg, ru.q);
+          const double wsg = (1.0 / ru.n_sig) * ru.rc * ru.q * std::pow(sg, ru.q - 1) * chi(std::pow(sg, ru.q));
+          for (int it = 0; it < ru.n_th; ++it) {
+            const double th = 2 * M_PI * it / ru.n_th;
+            ti.push_back(cx + rho * std::cos(th));
+            tj.push_back(cy + rho * std::sin(th));
+            tk.push_back(t);
+            wq.push_back(wsl * wsg * (2 * M_PI / ru.n_th) * rho);
           }
         }
       }
-      const int64_t* node_of = &B.face_node[size_t(G) * nf * nf * ns];
-      for (size_t r = 0; r < wq.size(); ++r) {
-        double dd[3], dom;
-        face_direction(G, ti[r] * dg - half, tj[r] * dg - half, dd, &dom);
-        const double rp = B.a - tk[r] * ds * B.w;
-        const double y[3] = {rp * dd[0], rp * dd[1], rp * dd[2]};
-        const double J = B.w * rp * rp * dom * dg * dg * ds;
-        const double dist = std::sqrt((y[0] - x[0]) * (y[0] - x[0]) + (y[1] - x[1]) * (y[1] - x[1]) +
-                                      (y[2] - x[2]) * (y[2] - x[2]));
-        const cd f = std::polar(wq[r] * J / (4 * M_PI * dist), kappa * dist);
-        int64_t s0[3];
-        s0[0] = int64_t(std::floor(ti[r])) - p / 2;
-        s0[1] = int64_t(std::floor(tj[r])) - p / 2;
-        s0[2] = std::min<int64_t>(std::max<int64_t>(int64_t(std::floor(tk[r])) - ps / 2, 0), ns - 1 - ps);
-        lagrange_row(ti[r], s0[0], p, La.data());
-        lagrange_row(tj[r], s0[1], p, Lb.data());
-        lagrange_row(tk[r], s0[2], ps, Lc.data());
-        scatter(row, node_of, nf, nf, ns, s0, La.data(), Lb.data(), Lc.data(), p, ps, f, fac_shell);
-      }
-      for (int64_t n = 0; n < B.n_shell; ++n) {
-        if (B.face[n] != G) continue;
-        const double fi = B.grid[3 * n], fj = B.grid[3 * n + 1], fk = B.grid[3 * n + 2];
-        if (is_shell) {
-          const int k0 = B.grid[3 * qn + 2];
-          eta[n] = chi(std::hypot(fi - cx, fj - cy) / ru.rc) * chi((fk - k0) / ru.rs);
-        } else {
-          const double cz = s_x / ds, rsp = std::min(ru.rs, B.tau0 * (ns - 1));
-          const double a = (fi - cx) / ru.rc, b = (fj - cy) / ru.rc, c = (fk - cz) / rsp;
-          eta[n] = chi(std::sqrt(a * a + b * b + c * c));
+    } else {
+      for (int ir = 1; ir < ru.n_rho; ++ir) {
+        const double sv = double(ir) / ru.n_rho, rho = std::pow(sv, ru.q);
+        const double wr = (1.0 / ru.n_rho) * ru.q * std::pow(sv, ru.q - 1) * chi(rho);
+        for (int im = 0; im < ru.n_mu; ++im) {
+          const double st = std::sqrt(1 - mu[im] * mu[im]);
+          for (int ip = 0; ip < ru.n_phi; ++ip) {
+            const double ph = 2 * M_PI * ip / ru.n_phi;
+            const double tkv = cz + rsp * rho * mu[im];
+            ti.push_back(cx + ru.rc * rho * st * std::cos(ph));
+            tj.push_back(cy + ru.rc * rho * st * std::sin(ph));
+            tk.push_back(tkv);
+            // past the chart's bottom line phi_F is exactly zero: drop the point
+            const double wv = wr * wmu[im] * (2 * M_PI / ru.n_phi) * rho * rho * ru.rc * ru.rc * rsp;
+            wq.push_back(tkv <= ns - 1 ? wv : 0.0);
+          }
         }
       }
     }
+    const int64_t* node_of = &B.face_node[size_t(G) * nf * nf * ns];
+    for (size_t r = 0; r < wq.size(); ++r) {
+      double dd[3], dom;
+      face_direction(G, ti[r] * dg - half, tj[r] * dg - half, dd, &dom);
+      const double rp = B.a - tk[r] * ds * B.w;
+      const double y[3] = {rp * dd[0], rp * dd[1], rp * dd[2]};
+      const double J = B.w * rp * rp * dom * dg * dg * ds;
+      const double dist = std::sqrt((y[0] - x[0]) * (y[0] - x[0]) + (y[1] - x[1]) * (y[1] - x[1]) +
+                                    (y[2] - x[2]) * (y[2] - x[2]));
+      const cd f = std::polar(wq[r] * J / (4 * M_PI * dist), kappa * dist);
+      int64_t s0[3];
+      s0[0] = int64_t(std::floor(ti[r])) - p / 2;
+      s0[1] = int64_t(std::floor(tj[r])) - p / 2;
+      s0[2] = std::min<int64_t>(std::max<int64_t>(int64_t(std::floor(tk[r])) - ps / 2, 0), ns - 1 - ps);
+      lagrange_row(ti[r], s0[0], p, La.data());
+      lagrange_row(tj[r], s0[1], p, Lb.data());
+      lagrange_row(tk[r], s0[2], ps, Lc.data());
+      scatter(acc, node_of, nf, nf, ns, s0, La.data(), Lb.data(), Lc.data(), p, ps, f, fac_shell);
+    }
+    // cut-off values on this face's nodes (zero outside the windows)
+    int ilo, ihi, jlo, jhi, klo, khi;
+    window(cx, ru.rc, nf, &ilo, &ihi);
+    window(cy, ru.rc, nf, &jlo, &jhi);
+    if (is_shell) window(double(k0), ru.rs, ns, &klo, &khi);
+    else window(cz, rsp, ns, &klo, &khi);
+    for (int i = ilo; i <= ihi; ++i)
+      for (int j = jlo; j <= jhi; ++j)
+        for (int k = klo; k <= khi; ++k) {
+          const int64_t n = node_of[(size_t(i) * nf + j) * ns + k];
+          if (n < 0) continue;
+          double e;
+          if (is_shell) {
+            e = chi(std::hypot(i - cx, j - cy) / ru.rc) * chi(double(k - k0) / ru.rs);
+          } else {
+            const double a = (i - cx) / ru.rc, b = (j - cy) / ru.rc, c = (k - cz) / rsp;
+            e = chi(std::sqrt(a * a + b * b + c * c));
+          }
+          if (e > 0) acc.set_eta(n, e);
+        }
   }
-  // ---- regular rule with (1 - eta)
-  for (int64_t n = 0; n < N; ++n) {
+}
+
+}  // namespace
+
+bool ball3_row(const Ball3& B, double kappa, const Rules3& ru, int64_t qn, cd* row, double* eta_out,
+               std::string* err) {
+  if (qn < 0 || qn >= B.N) { *err = "node index out of range"; return false; }
+  if (!check_rules(ru, err)) return false;
+  RowAcc acc(B.N);
+  singular_parts(B, kappa, ru, qn, acc);
+  const double* x = &B.x[3 * qn];
+  for (int64_t n = 0; n < B.N; ++n) {
+    row[n] = acc.v[n];
     const double dx = B.x[3 * n] - x[0], dy = B.x[3 * n + 1] - x[1], dz = B.x[3 * n + 2] - x[2];
     const double dist = std::sqrt(dx * dx + dy * dy + dz * dz);
-    if (dist > 0) row[n] += std::polar(B.w_q[n] * B.omega[n] * (1.0 - eta[n]) / (4 * M_PI * dist), kappa * dist);
+    if (dist > 0)
+      row[n] += std::polar(B.w_q[n] * B.omega[n] * (1.0 - acc.eta[n]) / (4 * M_PI * dist), kappa * dist);
   }
-  if (eta_out) std::copy(eta.begin(), eta.end(), eta_out);
+  if (eta_out) std::copy(acc.eta.begin(), acc.eta.end(), eta_out);
+  return true;
+}
+
+bool ball3_near(Ball3& B, double kappa, const Rules3& ru, const double* box0, double H, int L, const int64_t* rows,
+                int64_t n_rows, int n_threads, std::string* err) {
+  if (!check_rules(ru, err)) return false;
+  if (!(H > 0) || L < 1) { *err = "invalid cell box"; return false; }
+  const int64_t N = B.N;
+  // cells of the nodes and the nodes of each cell
+  const int64_t ncell = int64_t(L) * L * L;
+  std::vector<int32_t> cijk(3 * N);
+  std::vector<int64_t> start(ncell + 1, 0), members(N);
+  for (int64_t n = 0; n < N; ++n) {
+    for (int k = 0; k < 3; ++k) {
+      const double t = std::floor((B.x[3 * n + k] - box0[k]) / H);
+      if (!(t >= 0 && t < L)) { *err = "nodes outside the cell box"; return false; }
+      cijk[3 * n + k] = int32_t(t);
+    }
+    ++start[(int64_t(cijk[3 * n + 2]) * L + cijk[3 * n + 1]) * L + cijk[3 * n] + 1];
+  }
+  for (int64_t c = 0; c < ncell; ++c) start[c + 1] += start[c];
+  {
+    std::vector<int64_t> fill(start.begin(), start.end() - 1);
+    for (int64_t n = 0; n < N; ++n)
+      members[fill[(int64_t(cijk[3 * n + 2]) * L + cijk[3 * n + 1]) * L + cijk[3 * n]]++] = n;
+  }
+  std::vector<int64_t> all;
+  if (!rows) {
+    all.resize(N);
+    for (int64_t n = 0; n < N; ++n) all[n] = n;
+    rows = all.data();
+    n_rows = N;
+  }
+  for (int64_t r = 0; r < n_rows; ++r)
+    if (rows[r] < 0 || rows[r] >= N) { *err = "row index out of range"; return false; }
+  std::vector<std::vector<int32_t>> cols(n_rows);
+  std::vector<std::vector<cd>> vals(n_rows);
+  std::atomic<bool> bad(false);
+  parallel_for(n_threads, n_rows, 16, [&](int64_t r0, int64_t r1) {
+    RowAcc acc(N);
+    std::vector<char> in_block(N, 0);
+    std::vector<int64_t> block;
+    for (int64_t r = r0; r < r1 && !bad; ++r) {
+      const int64_t qn = rows[r];
+      const double* x = &B.x[3 * qn];
+      acc.clear();
+      singular_parts(B, kappa, ru, qn, acc);
+      // regular (1 - eta) terms over the 3 x 3 x 3 cell block N(x)
+      block.clear();
+      for (int di = -1; di <= 1; ++di)
+        for (int dj = -1; dj <= 1; ++dj)
+          for (int dk = -1; dk <= 1; ++dk) {
+            const int i = cijk[3 * qn] + di, j = cijk[3 * qn + 1] + dj, k = cijk[3 * qn + 2] + dk;
+            if (i < 0 || j < 0 || k < 0 || i >= L || j >= L || k >= L) continue;
+            const int64_t c = (int64_t(k) * L + j) * L + i;
+            for (int64_t t = start[c]; t < start[c + 1]; ++t) block.push_back(members[t]);
+          }
+      for (int64_t n : block) {
+        in_block[n] = 1;
+        const double dx = B.x[3 * n] - x[0], dy = B.x[3 * n + 1] - x[1], dz = B.x[3 * n + 2] - x[2];
+        const double dist = std::sqrt(dx * dx + dy * dy + dz * dz);
+        if (dist > 0)
+          acc.add(n, std::polar(B.w_q[n] * B.omega[n] * (1.0 - acc.eta[n]) / (4 * M_PI * dist), kappa * dist));
+      }
+      for (int64_t n : acc.eidx)
+        if (acc.eta[n] > 0 && !in_block[n]) bad = true;
+      for (int64_t n : block) in_block[n] = 0;
+      std::vector<int64_t> idx = acc.idx;
+      std::sort(idx.begin(), idx.end());
+      cols[r].reserve(idx.size());
+      vals[r].reserve(idx.size());
+      for (int64_t n : idx) {
+        cols[r].push_back(int32_t(n));
+        vals[r].push_back(acc.v[n]);
+      }
+    }
+  });
+  if (bad) { *err = "cut-off support leaves the 3 x 3 x 3 cell block: enlarge H or shrink the rules"; return false; }
+  B.near_rows.assign(rows, rows + n_rows);
+  B.near_rowptr.assign(n_rows + 1, 0);
+  for (int64_t r = 0; r < n_rows; ++r) B.near_rowptr[r + 1] = B.near_rowptr[r] + int64_t(cols[r].size());
+  B.near_col.resize(B.near_rowptr[n_rows]);
+  B.near_val.resize(B.near_rowptr[n_rows]);
+  for (int64_t r = 0; r < n_rows; ++r) {
+    std::copy(cols[r].begin(), cols[r].end(), B.near_col.begin() + B.near_rowptr[r]);
+    std::copy(vals[r].begin(), vals[r].end(), B.near_val.begin() + B.near_rowptr[r]);
+  }
   return true;
 }
 

@@ -139,6 +139,10 @@ struct Ball3 {
   std::vector<int32_t> grid;      // N x 3: shell (i, j, k) on its face grid, interior (ix, iy, iz) + m
   std::vector<int64_t> face_node; // [F][i][j][k] -> node or -1 (6 n_f n_f n_s)
   std::vector<int64_t> cart_node; // [ix][iy][iz] -> node or -1 ((2m + 1)^3)
+  // near-field rows (ball3_near): CSR over the requested rows
+  std::vector<int64_t> near_rows, near_rowptr;
+  std::vector<int32_t> near_col;
+  std::vector<cd> near_val;
   std::string err;
 };
 bool build_ball3(Ball3& b);
@@ -154,6 +158,12 @@ struct Rules3 {
 // folded in by the caller); eta (optional, N) receives the cut-off values of
 // every rule applied.
 bool ball3_row(const Ball3& b, double kappa, const Rules3& ru, int64_t qn, cd* row, double* eta, std::string* err);
+// Adjacent part of the 3-D operator for the given rows (all rows when rows is
+// NULL): every singular rule plus the regular (1 - eta) terms of the nodes in
+// the 3 x 3 x 3 block of cells (side H, L per axis from box0) around the
+// target; fails when a cut-off reaches outside that block.  Stored in b.near_*.
+bool ball3_near(Ball3& b, double kappa, const Rules3& ru, const double* box0, double H, int L, const int64_t* rows,
+                int64_t n_rows, int n_threads, std::string* err);
 // Window (2 Wn + 1)^3 of the interior singular rule's coefficients over grid
 // offsets ([di][dj][dk], offsets -Wn..Wn) for a grid-point target.
 bool interior_window3(double kappa, double h, double R, int p, int q, int n_rho, int n_mu, int n_phi, double chi_s0,

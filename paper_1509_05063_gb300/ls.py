@@ -93,6 +93,9 @@ _SIGS = {
     "ls_host_ball3_nodes": ([C.c_void_p] + [C.c_void_p] * 6),
     "ls_host_ball3_destroy": ([C.c_void_p]),
     "ls_host_ball3_row": ([C.c_void_p, C.c_double, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
+    "ls_host_ball3_near": ([C.c_void_p, C.c_double, C.c_void_p, C.c_void_p, C.c_double, C.c_int, C.c_void_p,
+                            C.c_int64, C.c_int, C.POINTER(C.c_int64)]),
+    "ls_host_ball3_near_get": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "ls_interior_window3": ([C.c_double, C.c_double, C.c_double, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
                              C.c_double, C.c_void_p, C.POINTER(C.c_int)]),
     "ls_set_stage_timing": ([C.c_void_p, C.c_int]),
@@ -444,13 +447,37 @@ class HostBall3:
                                         face.ctypes.data, grid.ctypes.data))
         return dict(x=x, w=w, omega=om, psi=psi, face=face, grid=grid)
 
+    @staticmethod
+    def _rules(rules):
+        if rules is None:
+            return None
+        d = dict(R=3.0, p=5, q=3, n_rho=16, n_mu=16, n_phi=32, rc=6.0, rs=6.0, n_sig=20, n_th=32, chi_s0=0.1)
+        d.update(rules)
+        return Rules3Params(**d)
+
+    def near(self, kappa: float, box0, H: float, L: int, rows=None, rules: dict | None = None, n_threads: int = 0):
+        """Adjacent part of the 3-D operator over the listed rows (ls_host_ball3_near) as a
+        scipy CSR matrix (len(rows) x N)."""
+        import scipy.sparse as sp
+        prm = self._rules(rules)
+        b0 = np.ascontiguousarray(box0, np.float64)
+        r = None if rows is None else np.ascontiguousarray(rows, np.int64)
+        nnz = C.c_int64()
+        st = _lib.ls_host_ball3_near(self._h, float(kappa), C.byref(prm) if prm is not None else None,
+                                     b0.ctypes.data, float(H), int(L), None if r is None else r.ctypes.data,
+                                     0 if r is None else len(r), int(n_threads), C.byref(nnz))
+        if st != 0:
+            raise LSError(st, _lib.ls_last_error(None).decode())
+        n_rows = self.N if r is None else len(r)
+        rowptr = np.zeros(n_rows + 1, np.int64)
+        col = np.zeros(nnz.value, np.int32)
+        val = np.zeros(nnz.value, np.complex128)
+        _check(_lib.ls_host_ball3_near_get(self._h, rowptr.ctypes.data, col.ctypes.data, val.ctypes.data))
+        return sp.csr_matrix((val, col, rowptr), shape=(n_rows, self.N))
+
     def row(self, kappa: float, q: int, rules: dict | None = None):
         """Row q of the 3-D operator K (ls_host_ball3_row) and the cut-off values eta."""
-        prm = None
-        if rules is not None:
-            d = dict(R=3.0, p=5, q=3, n_rho=16, n_mu=16, n_phi=32, rc=6.0, rs=6.0, n_sig=20, n_th=32, chi_s0=0.1)
-            d.update(rules)
-            prm = Rules3Params(**d)
+        prm = self._rules(rules)
         row = np.zeros(self.N, np.complex128)
         eta = np.zeros(self.N)
         st = _lib.ls_host_ball3_row(self._h, float(kappa), C.byref(prm) if prm is not None else None, int(q),

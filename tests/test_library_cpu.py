@@ -269,3 +269,41 @@ def test_host_ball3_rows_match_oracle(lib):
             assert eta.min() >= 0.0 and eta.max() <= 1.0
     with pytest.raises(LSError, match="out of range"):
         hb.row(2.0, hb.N)
+
+
+def test_host_ball3_near_plus_exact_far_sum_is_the_row(lib):
+    """The library's adjacent part of the 3-D operator (singular rules plus the
+    regular terms of the 3 x 3 x 3 cell block) plus the exact non-adjacent sum
+    equals the oracle's whole row, and its entries inside the block equal the
+    row's; a cut-off reaching past the block is rejected.  Cut-off radii of 3
+    index units keep the support inside cells of side 0.32 at this level."""
+    from paper_1509_05063_gb300 import HostBall3, LSError
+    from oracle.accel3d import Accelerator3
+    from oracle.geometry3d import Ball3, Discretisation3
+    from oracle.quadrature3d import Rules3, k_row
+    dz = Discretisation3(Ball3(n_f=25, n_s=9, h=0.1))
+    hb = HostBall3(n_f=25, n_s=9, h=0.1)
+    L, H, x0 = 7, 2.26 / 7, -1.13
+    rng = np.random.default_rng(13)
+    rows = np.concatenate([rng.choice(dz.n_shell, 4, replace=False),
+                           dz.n_shell + rng.choice(dz.n_cart, 4, replace=False)])
+    near = hb.near(2.0, [x0] * 3, H, L, rows=rows, rules=dict(rc=3.0, rs=3.0))
+    wfac = dz.w * dz.omega
+    acc = Accelerator3(dz.x, wfac, 2.0, x0, H, L, 2, p=2)
+    u = W.random_density(dz.N)[0]
+    far = acc.direct_far(u, rows=rows)
+    ru = Rules3(rc=3.0, rs=3.0)
+    for i, q in enumerate(rows):
+        ref = k_row(dz, 2.0, int(q), ru)
+        got = near[i].toarray()[0]
+        assert abs(got @ u + far[i] - ref @ u) < 1e-13 * np.sum(np.abs(ref * u))
+        blk = acc.cells.near_mask([q])[0]
+        assert np.max(np.abs(got[blk] - ref[blk])) < 1e-14 * np.max(np.abs(ref))
+    # the whole accelerated 3-D operator on the host: adjacent part plus the
+    # library's equivalent-source far part (N_eq = 6)
+    from paper_1509_05063_gb300 import HostAccel3
+    ha = HostAccel3(dz.x, wfac, 2.0, [x0] * 3, H, L, 6)
+    far_es = _apply_far3(ha.get(), u, L, 6, ha.n_es, ha.M)[rows]
+    assert np.linalg.norm(far_es - far) < 1e-5 * np.linalg.norm(far)
+    with pytest.raises(LSError, match="3 x 3 x 3"):
+        hb.near(2.0, [x0] * 3, H, L, rows=rows)          # default radii 6 reach past the block
