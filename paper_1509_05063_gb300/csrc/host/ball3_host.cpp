@@ -563,15 +563,20 @@ bool ball3_near(Ball3& B, double kappa, const Rules3& ru, const double* box0, do
     }
   });
   if (bad) { *err = "cut-off support leaves the 3 x 3 x 3 cell block: enlarge H or shrink the rules"; return false; }
-  B.near_rows.assign(rows, rows + n_rows);
-  B.near_rowptr.assign(n_rows + 1, 0);
-  for (int64_t r = 0; r < n_rows; ++r) B.near_rowptr[r + 1] = B.near_rowptr[r] + int64_t(cols[r].size());
-  B.near_col.resize(B.near_rowptr[n_rows]);
-  B.near_val.resize(B.near_rowptr[n_rows]);
+  // assemble into fresh arrays and swap them in, so that a failed call leaves
+  // the previous result intact
+  std::vector<int64_t> nrows(rows, rows + n_rows), rowptr(n_rows + 1, 0);
+  for (int64_t r = 0; r < n_rows; ++r) rowptr[r + 1] = rowptr[r] + int64_t(cols[r].size());
+  std::vector<int32_t> col(rowptr[n_rows]);
+  std::vector<cd> val(rowptr[n_rows]);
   for (int64_t r = 0; r < n_rows; ++r) {
-    std::copy(cols[r].begin(), cols[r].end(), B.near_col.begin() + B.near_rowptr[r]);
-    std::copy(vals[r].begin(), vals[r].end(), B.near_val.begin() + B.near_rowptr[r]);
+    std::copy(cols[r].begin(), cols[r].end(), col.begin() + rowptr[r]);
+    std::copy(vals[r].begin(), vals[r].end(), val.begin() + rowptr[r]);
   }
+  B.near_rows.swap(nrows);
+  B.near_rowptr.swap(rowptr);
+  B.near_col.swap(col);
+  B.near_val.swap(val);
   return true;
 }
 

@@ -9,6 +9,8 @@
 // Newton-Cotes weight across; Cartesian = h^2.
 #include <algorithm>
 #include <cmath>
+#include <exception>
+#include <mutex>
 #include <numeric>
 #include <thread>
 
@@ -172,17 +174,28 @@ void parallel_for(int n_threads, int64_t n, int64_t chunk,
                   const std::function<void(int64_t, int64_t)>& fn) {
   if (n <= 0) return;
   if (n_threads <= 1 || n <= chunk) { fn(0, n); return; }
+  // An exception in a worker (an allocation failure) stops the remaining
+  // chunks and is rethrown here, in the calling thread.
   std::atomic<int64_t> next(0);
+  std::exception_ptr first;
+  std::mutex mu;
   std::vector<std::thread> th;
   for (int t = 0; t < n_threads; ++t)
     th.emplace_back([&]() {
-      for (;;) {
-        const int64_t s = next.fetch_add(chunk);
-        if (s >= n) break;
-        fn(s, std::min(n, s + chunk));
+      try {
+        for (;;) {
+          const int64_t s = next.fetch_add(chunk);
+          if (s >= n) break;
+          fn(s, std::min(n, s + chunk));
+        }
+      } catch (...) {
+        next = n;
+        std::lock_guard<std::mutex> lk(mu);
+        if (!first) first = std::current_exception();
       }
     });
   for (auto& t : th) t.join();
+  if (first) std::rethrow_exception(first);
 }
 
 // ---------------------------------------------------------------- node set
