@@ -413,9 +413,14 @@ ls_status ls_host_ball3_row(ls_host_ball3 h, double kappa, const ls_rules3* rule
  * (replacing an earlier one) as a CSR matrix over the listed rows with sorted
  * columns; *nnz receives its entry count.  ls_host_ball3_near_get copies it:
  * rowptr (n_rows + 1), col (nnz), val (nnz complex, interleaved doubles);
- * any pointer may be NULL. */
+ * any pointer may be NULL.  stencils_only != 0 stores instead only the
+ * singular parts and the sparse correction -eta w omega G (entries where a
+ * cut-off is positive): the adjacent part is then that matrix plus the plain
+ * sum of w omega G over the block's other nodes, which a caller computes on
+ * the fly. */
 ls_status ls_host_ball3_near(ls_host_ball3 h, double kappa, const ls_rules3* rules, const double* box0, double H,
-                             int L, const int64_t* rows, int64_t n_rows, int n_threads, int64_t* nnz);
+                             int L, const int64_t* rows, int64_t n_rows, int stencils_only, int n_threads,
+                             int64_t* nnz);
 ls_status ls_host_ball3_near_get(ls_host_ball3 h, int64_t* rowptr, int32_t* col, double* val);
 
 /* Coefficients c[o] of the interior singular rule for a target on a uniform

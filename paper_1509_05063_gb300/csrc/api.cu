@@ -553,13 +553,14 @@ ls_status ls_host_ball3_row(ls_host_ball3 h, double kappa, const ls_rules3* rule
 }
 
 ls_status ls_host_ball3_near(ls_host_ball3 h, double kappa, const ls_rules3* rules, const double* box0, double H,
-                             int L, const int64_t* rows, int64_t n_rows, int n_threads, int64_t* nnz) {
+                             int L, const int64_t* rows, int64_t n_rows, int stencils_only, int n_threads,
+                             int64_t* nnz) {
   if (!h || !box0 || !nnz) return fail(nullptr, LS_ERR_INVALID, "NULL handle, box0 or nnz");
   if (!(kappa >= 0) || (rows && n_rows < 0)) return fail(nullptr, LS_ERR_INVALID, "invalid kappa or row count");
   const int nt = n_threads > 0 ? n_threads : int(std::max(1u, std::thread::hardware_concurrency()));
   std::string m;
   try {
-    if (!lsh::ball3_near(h->B, kappa, rules_from(rules), box0, H, L, rows, n_rows, nt, &m))
+    if (!lsh::ball3_near(h->B, kappa, rules_from(rules), box0, H, L, rows, n_rows, stencils_only != 0, nt, &m))
       return fail(nullptr, LS_ERR_INVALID, m);
   } catch (const std::bad_alloc&) {
     return fail(nullptr, LS_ERR_NOMEM, "host allocation failed");

@@ -489,7 +489,7 @@ bool ball3_row(const Ball3& B, double kappa, const Rules3& ru, int64_t qn, cd* r
 }
 
 bool ball3_near(Ball3& B, double kappa, const Rules3& ru, const double* box0, double H, int L, const int64_t* rows,
-                int64_t n_rows, int n_threads, std::string* err) {
+                int64_t n_rows, bool stencils_only, int n_threads, std::string* err) {
   if (!check_rules(ru, err)) return false;
   if (!(H > 0) || L < 1) { *err = "invalid cell box"; return false; }
   const int64_t N = B.N;
@@ -542,12 +542,22 @@ bool ball3_near(Ball3& B, double kappa, const Rules3& ru, const double* box0, do
             const int64_t c = (int64_t(k) * L + j) * L + i;
             for (int64_t t = start[c]; t < start[c + 1]; ++t) block.push_back(members[t]);
           }
-      for (int64_t n : block) {
-        in_block[n] = 1;
-        const double dx = B.x[3 * n] - x[0], dy = B.x[3 * n + 1] - x[1], dz = B.x[3 * n + 2] - x[2];
-        const double dist = std::sqrt(dx * dx + dy * dy + dz * dz);
-        if (dist > 0)
-          acc.add(n, std::polar(B.w_q[n] * B.omega[n] * (1.0 - acc.eta[n]) / (4 * M_PI * dist), kappa * dist));
+      for (int64_t n : block) in_block[n] = 1;
+      if (stencils_only) {
+        // the sparse correction -eta w omega G; the caller adds w omega G over the block
+        for (int64_t n : acc.eidx) {
+          const double dx = B.x[3 * n] - x[0], dy = B.x[3 * n + 1] - x[1], dz = B.x[3 * n + 2] - x[2];
+          const double dist = std::sqrt(dx * dx + dy * dy + dz * dz);
+          if (dist > 0 && acc.eta[n] > 0)
+            acc.add(n, std::polar(-B.w_q[n] * B.omega[n] * acc.eta[n] / (4 * M_PI * dist), kappa * dist));
+        }
+      } else {
+        for (int64_t n : block) {
+          const double dx = B.x[3 * n] - x[0], dy = B.x[3 * n + 1] - x[1], dz = B.x[3 * n + 2] - x[2];
+          const double dist = std::sqrt(dx * dx + dy * dy + dz * dz);
+          if (dist > 0)
+            acc.add(n, std::polar(B.w_q[n] * B.omega[n] * (1.0 - acc.eta[n]) / (4 * M_PI * dist), kappa * dist));
+        }
       }
       for (int64_t n : acc.eidx)
         if (acc.eta[n] > 0 && !in_block[n]) bad = true;

@@ -162,8 +162,10 @@ bool ball3_row(const Ball3& b, double kappa, const Rules3& ru, int64_t qn, cd* r
 // NULL): every singular rule plus the regular (1 - eta) terms of the nodes in
 // the 3 x 3 x 3 block of cells (side H, L per axis from box0) around the
 // target; fails when a cut-off reaches outside that block.  Stored in b.near_*.
+// stencils_only: store only the singular parts and the sparse correction
+// -eta w omega G, leaving the block's plain regular sum w omega G to the caller.
 bool ball3_near(Ball3& b, double kappa, const Rules3& ru, const double* box0, double H, int L, const int64_t* rows,
-                int64_t n_rows, int n_threads, std::string* err);
+                int64_t n_rows, bool stencils_only, int n_threads, std::string* err);
 // Window (2 Wn + 1)^3 of the interior singular rule's coefficients over grid
 // offsets ([di][dj][dk], offsets -Wn..Wn) for a grid-point target.
 bool interior_window3(double kappa, double h, double R, int p, int q, int n_rho, int n_mu, int n_phi, double chi_s0,

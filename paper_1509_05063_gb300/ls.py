@@ -94,7 +94,7 @@ _SIGS = {
     "ls_host_ball3_destroy": ([C.c_void_p]),
     "ls_host_ball3_row": ([C.c_void_p, C.c_double, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
     "ls_host_ball3_near": ([C.c_void_p, C.c_double, C.c_void_p, C.c_void_p, C.c_double, C.c_int, C.c_void_p,
-                            C.c_int64, C.c_int, C.POINTER(C.c_int64)]),
+                            C.c_int64, C.c_int, C.c_int, C.POINTER(C.c_int64)]),
     "ls_host_ball3_near_get": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "ls_interior_window3": ([C.c_double, C.c_double, C.c_double, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
                              C.c_double, C.c_void_p, C.POINTER(C.c_int)]),
@@ -455,9 +455,11 @@ class HostBall3:
         d.update(rules)
         return Rules3Params(**d)
 
-    def near(self, kappa: float, box0, H: float, L: int, rows=None, rules: dict | None = None, n_threads: int = 0):
+    def near(self, kappa: float, box0, H: float, L: int, rows=None, rules: dict | None = None, n_threads: int = 0,
+             stencils_only: bool = False):
         """Adjacent part of the 3-D operator over the listed rows (ls_host_ball3_near) as a
-        scipy CSR matrix (len(rows) x N)."""
+        scipy CSR matrix (len(rows) x N); stencils_only: the singular parts and the sparse
+        -eta w omega G correction only."""
         import scipy.sparse as sp
         prm = self._rules(rules)
         b0 = np.ascontiguousarray(box0, np.float64)
@@ -465,7 +467,8 @@ class HostBall3:
         nnz = C.c_int64()
         st = _lib.ls_host_ball3_near(self._h, float(kappa), C.byref(prm) if prm is not None else None,
                                      b0.ctypes.data, float(H), int(L), None if r is None else r.ctypes.data,
-                                     0 if r is None else len(r), int(n_threads), C.byref(nnz))
+                                     0 if r is None else len(r), int(bool(stencils_only)), int(n_threads),
+                                     C.byref(nnz))
         if st != 0:
             raise LSError(st, _lib.ls_last_error(None).decode())
         n_rows = self.N if r is None else len(r)

@@ -299,6 +299,16 @@ def test_host_ball3_near_plus_exact_far_sum_is_the_row(lib):
         assert abs(got @ u + far[i] - ref @ u) < 1e-13 * np.sum(np.abs(ref * u))
         blk = acc.cells.near_mask([q])[0]
         assert np.max(np.abs(got[blk] - ref[blk])) < 1e-14 * np.max(np.abs(ref))
+    # stored stencils plus the block's plain regular sum computed on the fly
+    st = hb.near(2.0, [x0] * 3, H, L, rows=rows, rules=dict(rc=3.0, rs=3.0), stencils_only=True)
+    assert st.nnz < near.nnz / 2
+    for i, q in enumerate(rows):
+        blk = np.nonzero(acc.cells.near_mask([q])[0])[0]
+        blk = blk[blk != q]
+        dist = np.linalg.norm(dz.x[blk] - dz.x[q], axis=1)
+        reg = wfac[blk] * np.exp(2j * dist) / (4 * np.pi * dist)
+        full = near[i].toarray()[0] @ u
+        assert abs(st[i].toarray()[0] @ u + reg @ u[blk] - full) < 1e-13 * np.sum(np.abs(near[i].toarray()[0] * u))
     # the whole accelerated 3-D operator on the host: adjacent part plus the
     # library's equivalent-source far part (N_eq = 6)
     from paper_1509_05063_gb300 import HostAccel3
