@@ -128,7 +128,7 @@ bool build_ball3(Ball3& B) {
     for (int k = 0; k < Q; ++k) ws[blk * (Q - 1) + k] += nc[k];
   for (double& v : ws) v *= (s[1] - s[0]);
   auto clear = [&]() {
-    B.x.clear(); B.w_q.clear(); B.omega.clear(); B.psi.clear(); B.face.clear(); B.grid.clear();
+    B.x.clear(); B.w_q.clear(); B.omega.clear(); B.psi.clear(); B.face.clear(); B.grid.clear(); B.psi_omega.clear();
   };
   clear();
   for (int F = 0; F < 6; ++F)
@@ -168,6 +168,8 @@ bool build_ball3(Ball3& B) {
       }
   B.N = int64_t(B.w_q.size());
   B.n_cart = B.N - B.n_shell;
+  B.psi_omega.resize(B.N);
+  for (int64_t n = 0; n < B.N; ++n) B.psi_omega[n] = B.psi[n] * B.omega[n];
   B.face_node.assign(size_t(6) * nf * nf * ns, -1);
   const int side = 2 * m + 1;
   B.cart_node.assign(size_t(side) * side * side, -1);
@@ -295,6 +297,56 @@ inline void scatter(RowAcc& acc, const int64_t* node_of, int na, int nb, int nc,
   }
 }
 
+// Dense accumulation window over grid indices [o, o + n) per axis: the rule
+// points' interpolation stencils land here without node lookups; flush()
+// hands the nonzero cells to the row (skipping indices outside the grid and
+// grid points that are not nodes).  A stencil that leaves the window (never
+// expected: the window is sized from the rule's reach) goes to the row
+// directly.
+struct Win3 {
+  int64_t o[3] = {0, 0, 0};
+  int n[3] = {0, 0, 0};
+  std::vector<cd> a;
+  void reset(int64_t o0, int64_t o1, int64_t o2, int n0, int n1, int n2) {
+    o[0] = o0; o[1] = o1; o[2] = o2;
+    n[0] = n0; n[1] = n1; n[2] = n2;
+    a.assign(size_t(n0) * n1 * n2, cd(0.0));
+  }
+  bool inside(const int64_t* st, int pa, int pc) const {
+    return st[0] >= o[0] && st[0] + pa < o[0] + n[0] && st[1] >= o[1] && st[1] + pa < o[1] + n[1] &&
+           st[2] >= o[2] && st[2] + pc < o[2] + n[2];
+  }
+  // a[i][j][k] += f La[i] Lb[j] Lc[k] over the stencil starting at st
+  void add(const int64_t* st, const double* La, const double* Lb, const double* Lc, int pa, int pc, cd f) {
+    for (int i = 0; i <= pa; ++i) {
+      const size_t bi = size_t(st[0] + i - o[0]) * n[1];
+      for (int j = 0; j <= pa; ++j) {
+        const cd fij = f * (La[i] * Lb[j]);
+        cd* row = &a[(bi + size_t(st[1] + j - o[1])) * n[2] + size_t(st[2] - o[2])];
+        for (int k = 0; k <= pc; ++k) row[k] += fij * Lc[k];
+      }
+    }
+  }
+  void flush(RowAcc& acc, const int64_t* node_of, int na, int nb, int nc, const std::vector<double>& factor) const {
+    for (int i = 0; i < n[0]; ++i) {
+      const int64_t gi = o[0] + i;
+      if (gi < 0 || gi >= na) continue;
+      for (int j = 0; j < n[1]; ++j) {
+        const int64_t gj = o[1] + j;
+        if (gj < 0 || gj >= nb) continue;
+        for (int k = 0; k < n[2]; ++k) {
+          const int64_t gk = o[2] + k;
+          if (gk < 0 || gk >= nc) continue;
+          const cd v = a[(size_t(i) * n[1] + j) * n[2] + k];
+          if (v == 0.0) continue;
+          const int64_t nd = node_of[(size_t(gi) * nb + size_t(gj)) * nc + size_t(gk)];
+          if (nd >= 0) acc.add(nd, v * factor[nd]);
+        }
+      }
+    }
+  }
+};
+
 bool check_rules(const Rules3& ru, std::string* err) {
   if (!(ru.R > 0 && ru.rc > 0 && ru.rs > 0) || ru.p < 1 || ru.q < 1 || ru.n_rho < 2 || ru.n_mu < 1 ||
       ru.n_phi < 1 || ru.n_sig < 2 || ru.n_th < 1 || !(ru.chi_s0 >= 0 && ru.chi_s0 < 1)) {
@@ -317,8 +369,8 @@ void singular_parts(const Ball3& B, double kappa, const Rules3& ru, int64_t qn, 
   const double h = B.h;
   const double half = M_PI / 4 + B.delta, dg = (2 * half) / (nf - 1), ds = 1.0 / (ns - 1);
   const double* x = &B.x[3 * qn];
-  std::vector<double> fac_shell(B.psi.size()), fac_cart(B.omega);
-  for (size_t n = 0; n < fac_shell.size(); ++n) fac_shell[n] = B.psi[n] * B.omega[n];
+  const std::vector<double>& fac_shell = B.psi_omega;   // phi_F / u on the face grids
+  const std::vector<double>& fac_cart = B.omega;        // phi_I / u on the interior grid
   std::vector<double> mu, wmu;
   gauss_legendre(ru.n_mu, mu, wmu);
   std::vector<double> La(p + 1), Lb(p + 1), Lc(p + 1);
@@ -341,6 +393,10 @@ void singular_parts(const Ball3& B, double kappa, const Rules3& ru, int64_t qn, 
         reach = reach || std::sqrt(dx * dx + dy * dy + dz * dz) < ru.R * h;
       }
   if (reach) {
+    Win3 w;
+    const int wn = 2 * int(std::ceil(ru.R)) + p + 4;
+    w.reset(int64_t(std::floor(cg[0] - ru.R)) - p / 2 - 1, int64_t(std::floor(cg[1] - ru.R)) - p / 2 - 1,
+            int64_t(std::floor(cg[2] - ru.R)) - p / 2 - 1, wn, wn, wn);
     for (int ir = 1; ir < ru.n_rho; ++ir) {
       const double sv = double(ir) / ru.n_rho, rho = ru.R * std::pow(sv, ru.q);
       const double wr = (1.0 / ru.n_rho) * ru.R * ru.q * std::pow(sv, ru.q - 1) * chi(std::pow(sv, ru.q));
@@ -360,10 +416,14 @@ void singular_parts(const Ball3& B, double kappa, const Rules3& ru, int64_t qn, 
           lagrange_row(c[0], s0[0], p, La.data());
           lagrange_row(c[1], s0[1], p, Lb.data());
           lagrange_row(c[2], s0[2], p, Lc.data());
-          scatter(acc, B.cart_node.data(), side, side, side, s0, La.data(), Lb.data(), Lc.data(), p, p, f, fac_cart);
+          if (w.inside(s0, p, p)) w.add(s0, La.data(), Lb.data(), Lc.data(), p, p, f);
+          else
+            scatter(acc, B.cart_node.data(), side, side, side, s0, La.data(), Lb.data(), Lc.data(), p, p, f,
+                    fac_cart);
         }
       }
     }
+    w.flush(acc, B.cart_node.data(), side, side, side, fac_cart);
     for (int i = lo[0]; i <= hi[0]; ++i)
       for (int j = lo[1]; j <= hi[1]; ++j)
         for (int k = lo[2]; k <= hi[2]; ++k) {
@@ -427,6 +487,27 @@ void singular_parts(const Ball3& B, double kappa, const Rules3& ru, int64_t qn, 
       }
     }
     const int64_t* node_of = &B.face_node[size_t(G) * nf * nf * ns];
+    Win3 w;
+    const int wn = 2 * int(std::ceil(ru.rc)) + p + 4;
+    w.reset(int64_t(std::floor(cx - ru.rc)) - p / 2 - 1, int64_t(std::floor(cy - ru.rc)) - p / 2 - 1, 0, wn, wn, ns);
+    // plane accumulator for the points of one depth line (boundary rule)
+    std::vector<cd> plane(size_t(wn) * wn, cd(0.0));
+    double line_t = -1.0;
+    int64_t line_s = 0;
+    std::vector<double> Lline(ps + 1);
+    bool plane_used = false;
+    auto spread_line = [&]() {
+      if (!plane_used) return;
+      for (int i = 0; i < wn; ++i)
+        for (int j = 0; j < wn; ++j) {
+          cd& v = plane[size_t(i) * wn + j];
+          if (v == 0.0) continue;
+          cd* dst = &w.a[(size_t(i) * wn + j) * ns + size_t(line_s)];
+          for (int k = 0; k <= ps; ++k) dst[k] += v * Lline[k];
+          v = 0.0;
+        }
+      plane_used = false;
+    };
     for (size_t r = 0; r < wq.size(); ++r) {
       double dd[3], dom;
       face_direction(G, ti[r] * dg - half, tj[r] * dg - half, dd, &dom);
@@ -442,9 +523,29 @@ void singular_parts(const Ball3& B, double kappa, const Rules3& ru, int64_t qn, 
       s0[2] = std::min<int64_t>(std::max<int64_t>(int64_t(std::floor(tk[r])) - ps / 2, 0), ns - 1 - ps);
       lagrange_row(ti[r], s0[0], p, La.data());
       lagrange_row(tj[r], s0[1], p, Lb.data());
-      lagrange_row(tk[r], s0[2], ps, Lc.data());
-      scatter(acc, node_of, nf, nf, ns, s0, La.data(), Lb.data(), Lc.data(), p, ps, f, fac_shell);
+      if (!w.inside(s0, p, ps)) {
+        lagrange_row(tk[r], s0[2], ps, Lc.data());
+        scatter(acc, node_of, nf, nf, ns, s0, La.data(), Lb.data(), Lc.data(), p, ps, f, fac_shell);
+      } else if (is_shell) {
+        if (tk[r] != line_t) {
+          spread_line();
+          line_t = tk[r];
+          line_s = s0[2];
+          lagrange_row(tk[r], s0[2], ps, Lline.data());
+        }
+        for (int i = 0; i <= p; ++i) {
+          cd* prow = &plane[size_t(s0[0] + i - w.o[0]) * wn + size_t(s0[1] - w.o[1])];
+          const cd fi = f * La[i];
+          for (int j = 0; j <= p; ++j) prow[j] += fi * Lb[j];
+        }
+        plane_used = true;
+      } else {
+        lagrange_row(tk[r], s0[2], ps, Lc.data());
+        w.add(s0, La.data(), Lb.data(), Lc.data(), p, ps, f);
+      }
     }
+    spread_line();
+    w.flush(acc, node_of, nf, nf, ns, fac_shell);
     // cut-off values on this face's nodes (zero outside the windows)
     int ilo, ihi, jlo, jhi, klo, khi;
     window(cx, ru.rc, nf, &ilo, &ihi);

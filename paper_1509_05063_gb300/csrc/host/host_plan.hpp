@@ -135,6 +135,7 @@ struct Ball3 {
   std::vector<double> x;          // N x 3
   std::vector<double> w_q;        // quadrature weight
   std::vector<double> omega, psi; // depth partition of unity, surface share (0 on the interior grid)
+  std::vector<double> psi_omega;  // psi omega (the shell's density factor)
   std::vector<int8_t> face;       // shell face 0..5, -1 interior
   std::vector<int32_t> grid;      // N x 3: shell (i, j, k) on its face grid, interior (ix, iy, iz) + m
   std::vector<int64_t> face_node; // [F][i][j][k] -> node or -1 (6 n_f n_f n_s)
