@@ -364,7 +364,10 @@ inline void window(double c, double r, int n, int* lo, int* hi) {
 
 // The singular parts of row qn (every rule that reaches x_q) and the cut-off
 // values eta of the rules applied, accumulated sparsely.
-void singular_parts(const Ball3& B, double kappa, const Rules3& ru, int64_t qn, RowAcc& acc) {
+// iwin: the interior rule's window for grid-point targets (interior_window3 with
+// the same rule), or null to evaluate the rule about each target.
+void singular_parts(const Ball3& B, double kappa, const Rules3& ru, int64_t qn, RowAcc& acc,
+                    const std::vector<cd>* iwin = nullptr, int iwn = 0) {
   const int nf = B.n_f, ns = B.n_s, p = ru.p, ps = std::min(ru.p, ns - 1);
   const double h = B.h;
   const double half = M_PI / 4 + B.delta, dg = (2 * half) / (nf - 1), ds = 1.0 / (ns - 1);
@@ -392,7 +395,27 @@ void singular_parts(const Ball3& B, double kappa, const Rules3& ru, int64_t qn, 
         const double dx = B.x[3 * n] - x[0], dy = B.x[3 * n + 1] - x[1], dz = B.x[3 * n + 2] - x[2];
         reach = reach || std::sqrt(dx * dx + dy * dy + dz * dz) < ru.R * h;
       }
-  if (reach) {
+  if (reach && iwin && qn >= B.n_shell) {
+    // a grid-point target: the rule is the shared window, shifted
+    const int ws = 2 * iwn + 1;
+    const int64_t g[3] = {B.grid[3 * qn], B.grid[3 * qn + 1], B.grid[3 * qn + 2]};
+    for (int i = 0; i < ws; ++i) {
+      const int64_t gi = g[0] + i - iwn;
+      if (gi < 0 || gi >= side) continue;
+      for (int j = 0; j < ws; ++j) {
+        const int64_t gj = g[1] + j - iwn;
+        if (gj < 0 || gj >= side) continue;
+        for (int k = 0; k < ws; ++k) {
+          const int64_t gk = g[2] + k - iwn;
+          if (gk < 0 || gk >= side) continue;
+          const cd c = (*iwin)[(size_t(i) * ws + j) * ws + k];
+          if (c == 0.0) continue;
+          const int64_t n = B.cart_node[(size_t(gi) * side + size_t(gj)) * side + size_t(gk)];
+          if (n >= 0) acc.add(n, c * fac_cart[n]);
+        }
+      }
+    }
+  } else if (reach) {
     Win3 w;
     const int wn = 2 * int(std::ceil(ru.R)) + p + 4;
     w.reset(int64_t(std::floor(cg[0] - ru.R)) - p / 2 - 1, int64_t(std::floor(cg[1] - ru.R)) - p / 2 - 1,
@@ -424,6 +447,8 @@ void singular_parts(const Ball3& B, double kappa, const Rules3& ru, int64_t qn, 
       }
     }
     w.flush(acc, B.cart_node.data(), side, side, side, fac_cart);
+  }
+  if (reach) {
     for (int i = lo[0]; i <= hi[0]; ++i)
       for (int j = lo[1]; j <= hi[1]; ++j)
         for (int k = lo[2]; k <= hi[2]; ++k) {
@@ -624,6 +649,10 @@ bool ball3_near(Ball3& B, double kappa, const Rules3& ru, const double* box0, do
   std::vector<std::vector<int32_t>> cols(n_rows);
   std::vector<std::vector<cd>> vals(n_rows);
   std::atomic<bool> bad(false);
+  std::vector<cd> iwin;
+  int iwn = 0;
+  if (!interior_window3(kappa, B.h, ru.R, ru.p, ru.q, ru.n_rho, ru.n_mu, ru.n_phi, ru.chi_s0, iwin, &iwn, err))
+    return false;
   parallel_for(n_threads, n_rows, 16, [&](int64_t r0, int64_t r1) {
     RowAcc acc(N);
     std::vector<char> in_block(N, 0);
@@ -632,7 +661,7 @@ bool ball3_near(Ball3& B, double kappa, const Rules3& ru, const double* box0, do
       const int64_t qn = rows[r];
       const double* x = &B.x[3 * qn];
       acc.clear();
-      singular_parts(B, kappa, ru, qn, acc);
+      singular_parts(B, kappa, ru, qn, acc, &iwin, iwn);
       // regular (1 - eta) terms over the 3 x 3 x 3 cell block N(x)
       block.clear();
       for (int di = -1; di <= 1; ++di)
