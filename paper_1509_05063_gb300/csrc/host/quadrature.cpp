@@ -345,6 +345,10 @@ struct RowBuilder {
         }
       }
     }
+    // The regular entries are in increasing column order (neighbour cells in
+    // increasing id, each cell's nodes contiguous): only the singular rules'
+    // entries need sorting before the merge.
+    const size_t nreg = ents.size();
     // singular rules
     if (needs_cart_rule(q)) {
       if (nd.chart[q] == 1) polar_cart_grid(std::llround(nd.ga[q]), std::llround(nd.gb[q]));
@@ -352,8 +356,9 @@ struct RowBuilder {
     }
     if (nd.chart[q] == 0) boundary(q, nd.gi[q], nd.gj[q]);
     else if (nd.cb[q] <= g.n2 - 1) polar(0, q, nd.ca[q], nd.cb[q]);
-    std::sort(ents.begin(), ents.end(),
-              [](const std::pair<int64_t, cd>& a, const std::pair<int64_t, cd>& b) { return a.first < b.first; });
+    auto by_col = [](const std::pair<int64_t, cd>& a, const std::pair<int64_t, cd>& b) { return a.first < b.first; };
+    std::sort(ents.begin() + nreg, ents.end(), by_col);
+    std::inplace_merge(ents.begin(), ents.begin() + nreg, ents.end(), by_col);
     size_t w = 0;
     for (size_t r = 0; r < ents.size(); ++r) {
       if (w > 0 && ents[w - 1].first == ents[r].first) ents[w - 1].second += ents[r].second;
@@ -437,12 +442,16 @@ bool build_near(Plan2D& plan) {
   const int64_t nnz = plan.rowptr[N];
   plan.col.resize(nnz);
   plan.val.resize(nnz);
-  int64_t pos = 0;
-  for (int64_t ck = 0; ck < nchunks; ++ck) {
-    std::copy(ccol[ck].begin(), ccol[ck].end(), plan.col.begin() + pos);
-    std::copy(cval[ck].begin(), cval[ck].end(), plan.val.begin() + pos);
-    pos += int64_t(ccol[ck].size());
-  }
+  std::vector<int64_t> pos(nchunks + 1, 0);
+  for (int64_t ck = 0; ck < nchunks; ++ck) pos[ck + 1] = pos[ck] + int64_t(ccol[ck].size());
+  parallel_for(plan.n_threads, nchunks, 16, [&](int64_t c0, int64_t c1) {
+    for (int64_t ck = c0; ck < c1; ++ck) {
+      std::copy(ccol[ck].begin(), ccol[ck].end(), plan.col.begin() + pos[ck]);
+      std::copy(cval[ck].begin(), cval[ck].end(), plan.val.begin() + pos[ck]);
+      std::vector<int32_t>().swap(ccol[ck]);
+      std::vector<cd>().swap(cval[ck]);
+    }
+  });
   return true;
 }
 
