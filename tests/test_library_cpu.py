@@ -101,8 +101,12 @@ def test_host_plan_matches_oracle_discretisation(lib, make):
     rows = np.arange(dz.N) if dz.N < 2000 else W.random_rows(dz.N, 300)
     ref = near_matrix(dz, cells, rows=rows)[:, canon].toarray()
     inv = np.argsort(canon)
-    got = hp.near()[inv[rows]].toarray()
+    near = hp.near()
+    got = near[inv[rows]].toarray()
     assert np.max(np.abs(got - ref)) <= 1e-13 * np.max(np.abs(ref))
+    # every row's columns strictly increase (sorted, each column once)
+    for r in range(0, hp.N, max(1, hp.N // 500)):
+        assert np.all(np.diff(near.indices[near.indptr[r]:near.indptr[r + 1]]) > 0)
 
 
 @pytest.mark.parametrize("make", [_small_disc, _small_kite])
