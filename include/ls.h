@@ -56,13 +56,16 @@ typedef enum {
  * slower to converge on problems whose correction solves stagnate. */
 typedef enum { LS_FP64 = 0, LS_MIXED = 1, LS_MIXED32 = 2 } ls_precision;
 
-typedef enum { LS_DISC = 0, LS_KITE = 1 } ls_shape;
+typedef enum { LS_DISC = 0, LS_KITE = 1, LS_FOURIER_STAR = 2 } ls_shape;
 
 typedef struct ls_plan_s* ls_plan;
 
 /* Scatterer and Nystrom grid (Section 2).  The boundary curve is
  *   disc : gamma(s) = (cx, cy) + a (cos s, sin s),              params = {a, cx, cy}
  *   kite : gamma(s) = (cx, cy) + c (cos s + 0.65 cos 2s - 0.65, 1.5 sin s), params = {c, cx, cy}
+ *   star : gamma(s) = (cx, cy) + r(s) (cos s, sin s), r(s) = a0 + sum_{k=1..5} c_k cos(k s),
+ *          params = {a0, cx, cy, c1, c2, c3, c4, c5}; r must stay positive (LS_ERR_INVALID
+ *          otherwise) and collar_w below the smallest radius of curvature of the convex parts
  * The collar chart is X(a, b) = gamma(2 pi a / n1) - (b / (n2 - 1)) collar_w nu(s),
  * 0 <= a < n1 (periodic), 0 <= b <= n2 - 1, nu the outward normal; the interior
  * chart is the Cartesian grid (cart_x0 + i h, cart_y0 + j h), 0 <= i < cart_nx,

@@ -38,6 +38,19 @@ def curve(wl: Workload, s):
         g = np.stack([cx + sc * (c1 + 0.65 * c2 - 0.65), cy + sc * 1.5 * s1], -1)
         g1 = np.stack([sc * (-s1 - 1.3 * s2), sc * 1.5 * c1], -1)
         g2 = np.stack([sc * (-c1 - 2.6 * c2), -sc * 1.5 * s1], -1)
+    elif wl.shape == "star":
+        # gamma = c + r(s) (cos s, sin s), r = a0 + sum_k c_k cos(k s), k = 1..5
+        a0, cx, cy = wl.shape_params[:3]
+        ck = np.zeros(5)
+        ck[:len(wl.shape_params) - 3] = wl.shape_params[3:]
+        k = np.arange(1, 6)
+        ks = np.multiply.outer(s, k)
+        r = a0 + np.cos(ks) @ ck
+        r1 = -np.sin(ks) @ (k * ck)
+        r2 = -np.cos(ks) @ (k * k * ck)
+        g = np.stack([cx + r * c1, cy + r * s1], -1)
+        g1 = np.stack([r1 * c1 - r * s1, r1 * s1 + r * c1], -1)
+        g2 = np.stack([r2 * c1 - 2 * r1 * s1 - r * c1, r2 * s1 + 2 * r1 * c1 - r * s1], -1)
     else:
         raise ValueError(wl.shape)
     return g, g1, g2

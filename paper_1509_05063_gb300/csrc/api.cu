@@ -233,7 +233,16 @@ std::vector<std::complex<float>> to32(const std::vector<cd>& v) {
 ls_status validate(const ls_geometry* g, const ls_options* o, double kappa) {
   if (!g || !o) return LS_ERR_INVALID;
   if (g->dim != 2) return LS_ERR_UNSUPPORTED;
-  if (g->shape != LS_DISC && g->shape != LS_KITE) return LS_ERR_INVALID;
+  if (g->shape != LS_DISC && g->shape != LS_KITE && g->shape != LS_FOURIER_STAR) return LS_ERR_INVALID;
+  if (g->shape == LS_FOURIER_STAR) {
+    // star-shaped: r(s) > 0 on a fine sample
+    for (int i = 0; i < 4096; ++i) {
+      const double s = 2.0 * M_PI * i / 4096;
+      double r = g->params[0];
+      for (int k = 1; k <= 5; ++k) r += g->params[2 + k] * std::cos(k * s);
+      if (!(r > 0)) return LS_ERR_INVALID;
+    }
+  }
   if (g->n1 < 8 || g->n2 < 2 || g->collar_w <= 0 || g->h <= 0 || g->cart_nx < 1 || g->cart_ny < 1)
     return LS_ERR_INVALID;
   if (!(kappa > 0)) return LS_ERR_INVALID;

@@ -27,6 +27,20 @@ void Geometry::curve(double s, double* gm, double* g1, double* g2) const {
     gm[0] = cx + a * c1; gm[1] = cy + a * s1;
     g1[0] = -a * s1;     g1[1] = a * c1;
     g2[0] = -a * c1;     g2[1] = -a * s1;
+  } else if (g.shape == LS_FOURIER_STAR) {
+    // r(s) = a0 + sum_k c_k cos(k s), gamma = c + r (cos s, sin s)
+    double r = g.params[0], r1 = 0, r2 = 0;
+    for (int k = 1; k <= 5; ++k) {
+      const double ck = g.params[2 + k], ckc = std::cos(k * s), cks = std::sin(k * s);
+      r += ck * ckc;
+      r1 -= k * ck * cks;
+      r2 -= double(k) * k * ck * ckc;
+    }
+    const double cx = g.params[1], cy = g.params[2];
+    gm[0] = cx + r * c1;                 gm[1] = cy + r * s1;
+    g1[0] = r1 * c1 - r * s1;            g1[1] = r1 * s1 + r * c1;
+    g2[0] = r2 * c1 - 2 * r1 * s1 - r * c1;
+    g2[1] = r2 * s1 + 2 * r1 * c1 - r * s1;
   } else {  // kite
     const double sc = g.params[0], cx = g.params[1], cy = g.params[2];
     const double c2 = std::cos(2 * s), s2 = std::sin(2 * s);

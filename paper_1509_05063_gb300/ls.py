@@ -14,7 +14,7 @@ import numpy as np
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
 LS_FP64, LS_MIXED, LS_MIXED32 = 0, 1, 2   # LS_MIXED32: solves only (complex64 Arnoldi vectors too)
-_SHAPES = {"disc": 0, "kite": 1}
+_SHAPES = {"disc": 0, "kite": 1, "star": 2}
 _STATUS = {0: "ok", 1: "invalid argument", 2: "out of memory", 3: "CUDA error", 4: "no convergence",
            5: "device wait timed out", 6: "unsupported"}
 

@@ -49,6 +49,10 @@ def test_invalid_arguments_return_status(lib):
     assert lib.ls_host_plan_create(C.byref(g), cb, None, wl.kappa, C.byref(o), C.byref(h)) == 6
     g.dim = 2
     assert lib.ls_host_plan_create(C.byref(g), cb, None, -1.0, C.byref(o), C.byref(h)) == 1
+    gs = b.geometry_from(wl)
+    gs.shape = 2                                  # Fourier star with r(s) < 0 somewhere
+    gs.params[0], gs.params[7] = 0.5, 0.6
+    assert lib.ls_host_plan_create(C.byref(gs), cb, None, wl.kappa, C.byref(o), C.byref(h)) == 1
     o.L = 2            # cells too large for the box -> nodes outside
     assert lib.ls_host_plan_create(C.byref(g), cb, None, wl.kappa, C.byref(o), C.byref(h)) == 1
     assert b"outside" in lib.ls_last_error(None)
@@ -86,7 +90,12 @@ def _small_kite():
                                 R_b=5, R_cart=4, n_rho=32, N_tau=48), L=17, m=8, center=(-0.25, 0.0), N_eq=8)
 
 
-@pytest.mark.parametrize("make", [_small_disc, _small_kite])
+def _small_star():
+    return W.place_cells(W.star(level=1, kappa=2.0, n2c=2.0, tau0=0.3, tau1=0.95, R_a=4, R_b=2, R_cart=3, p=7,
+                                n_rho=48, N_tau=64), L=7, m=4, N_eq=8)
+
+
+@pytest.mark.parametrize("make", [_small_disc, _small_kite, _small_star])
 def test_host_plan_matches_oracle_discretisation(lib, make):
     from paper_1509_05063_gb300 import HostPlan
     wl = make()
@@ -109,7 +118,7 @@ def test_host_plan_matches_oracle_discretisation(lib, make):
         assert np.all(np.diff(near.indices[near.indptr[r]:near.indptr[r + 1]]) > 0)
 
 
-@pytest.mark.parametrize("make", [_small_disc, _small_kite])
+@pytest.mark.parametrize("make", [_small_disc, _small_kite, _small_star])
 def test_host_accelerator_matrices_reproduce_oracle_far_field(lib, make):
     """Run the accelerator's steps in numpy with the library's matrices (P_c,
     B^+, B^+ T_o, Phi, kernel tables) and compare with the oracle's far part."""

@@ -145,11 +145,34 @@ def test_collar_chart_is_a_valid_parametrisation():
     assert np.all(Jk > 0)
 
 
-@pytest.mark.parametrize("shape", ["disc", "kite"])
+def test_star_curve_derivatives_and_collar():
+    """The Fourier star's gamma' and gamma'' against central differences of
+    gamma, and its collar chart: points on line b lie at depth (b / (n2 - 1)) w
+    below the boundary, with a positive Jacobian."""
+    wl = W.star(level=1, coeffs=(0.05, 0.0, 0.03, 0.0, 0.1))
+    s = np.linspace(0.1, 6.2, 37)
+    e = 1e-4
+    g, g1, g2 = geo.curve(wl, s)
+    gp, _, _ = geo.curve(wl, s + e)
+    gm, _, _ = geo.curve(wl, s - e)
+    assert np.max(np.abs((gp - gm) / (2 * e) - g1)) < 1e-7
+    assert np.max(np.abs((gp - 2 * g + gm) / e ** 2 - g2)) < 1e-5
+    a = np.linspace(0, wl.n1 - 1, 91)
+    X, J = geo.collar_map(wl, a, np.full(91, 2.0))
+    _, d = geo.closest_point(wl, X)
+    assert np.allclose(d, 2.0 / (wl.n2 - 1) * wl.collar_w, atol=1e-12)
+    assert np.all(J > 0)
+
+
+@pytest.mark.parametrize("shape", ["disc", "kite", "star"])
 def test_node_weights_integrate_the_area(shape):
     if shape == "disc":
         wl, area = disc_wl(2), math.pi
         tol = 1e-4
+    elif shape == "star":
+        # r = 1 + 0.1 cos 5s: area = pi a0^2 + (pi / 2) sum c_k^2
+        wl = W.star(level=2, R_a=4, R_b=4, R_cart=6, p=7, tau0=0.3, tau1=0.95)
+        area, tol = math.pi + 0.5 * math.pi * 0.1 ** 2, 3e-4
     else:
         wl = W.kite(n1=512, n2=17, h=0.02, kappa=2.0, R_b=4, tau0=0.4, tau1=0.9, collar_w=0.07)
         area, tol = 1.5 * math.pi, 2e-4

@@ -22,7 +22,7 @@ import numpy as np
 
 SEED = 150905063
 
-SHAPES = {"disc": 0, "kite": 1}
+SHAPES = {"disc": 0, "kite": 1, "star": 2}
 N2_KINDS = {"const": 0, "gauss": 1, "sincos": 2}
 
 
@@ -33,6 +33,8 @@ class Workload:
     Geometry: boundary curve gamma(s), s in [0, 2pi).
       disc : shape_params = (a, cx, cy)      gamma = c + a(cos s, sin s)
       kite : shape_params = (scale, cx, cy)  gamma = c + scale(cos s + 0.65 cos 2s - 0.65, 1.5 sin s)
+      star : shape_params = (a0, cx, cy, c1, ..., c5)  gamma = c + r(s)(cos s, sin s),
+             r(s) = a0 + sum_k c_k cos(k s)
     Collar (boundary) chart: X(a, b) = gamma(2 pi a / n1) - (b / (n2 - 1)) * collar_w * nu,
       a in [0, n1) periodic, b in [0, n2 - 1]; b = 0 lies on the boundary.
     Interior chart: Cartesian grid x = cart_x0 + i h, y = cart_y0 + j h,
@@ -173,6 +175,22 @@ def disc(level: int = 1, kappa: float = 2.0, n2c: float = 2.0, a: float = 1.0,
                   Q=Q, **kw)
     if accel:
         wl = wl.replace(**accel)
+    return wl
+
+
+def star(level: int = 1, kappa: float = 2.0, n2c: float = 2.0, a0: float = 1.0, coeffs=(0.0, 0.0, 0.0, 0.0, 0.1),
+         Q: int = 5, **kw) -> Workload:
+    """Penetrable Fourier star r(s) = a0 + sum_k c_k cos(k s) (default a five-pointed
+    star, c_5 = 0.1), constant n^2 inside, grids as for the disc of the same level."""
+    n1 = 32 * 2 ** level
+    n2 = (Q - 1) * 2 ** level + 1
+    w = kw.pop("collar_w", 0.2 * a0)
+    h = kw.pop("h", 2 * math.pi * a0 / n1)
+    rmax = a0 + sum(abs(c) for c in coeffs)
+    x0, nx = _cart_grid_for(h, -rmax, rmax)
+    wl = Workload(name=f"star_l{level}", shape="star", shape_params=(a0, 0.0, 0.0, *coeffs),
+                  kappa=kappa, n2_kind="const", n2_params=(n2c,), collar_w=w,
+                  n1=n1, n2=n2, h=h, cart_x0=x0, cart_y0=x0, cart_nx=nx, cart_ny=nx, Q=Q, **kw)
     return wl
 
 
