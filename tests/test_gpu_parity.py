@@ -283,3 +283,17 @@ def test_many_directions_seeded_from_earlier_solutions(disc):
         _, i1 = disc.plan.solve(disc.dev(U[r]), tol=1e-10, prec=LS_FP64)
         separate += i1["iterations"]
     assert info["iterations"] < separate
+
+
+def test_fp64_apply_on_a_fourier_star_matches_oracle():
+    """A third scatterer shape through the same device path: the cosine Fourier
+    star r = 1 + 0.1 cos 5s (n^2 = 2), FP64 apply against the oracle's
+    accelerated operator."""
+    from paper_1509_05063_gb300 import LS_FP64
+    wl = W.place_cells(W.star(level=1, kappa=2.0, n2c=2.0, tau0=0.3, tau1=0.95, R_a=4, R_b=2, R_cart=3, p=7,
+                              n_rho=48, N_tau=64), L=7, m=4, N_eq=8)
+    c = Case(wl)
+    ref = c.to_plan(c.op.apply(c.u[0]))
+    got = c.plan.apply(c.dev(c.u[0]), prec=LS_FP64).cpu().numpy()
+    assert rel(got, ref) < 1e-11
+    c.plan.close()
