@@ -330,6 +330,12 @@ def test_host_ball3_near_plus_exact_far_sum_is_the_row(lib):
     assert np.linalg.norm(far_es - far) < 1e-5 * np.linalg.norm(far)
     with pytest.raises(LSError, match="3 x 3 x 3"):
         hb.near(2.0, [x0] * 3, H, L, rows=rows)          # default radii 6 reach past the block
+    with pytest.raises(LSError, match="outside the cell box"):
+        hb.near(2.0, [-0.5] * 3, H, L, rows=rows, rules=dict(rc=3.0, rs=3.0))
+    with pytest.raises(LSError, match="out of range"):
+        hb.near(2.0, [x0] * 3, H, L, rows=[hb.N], rules=dict(rc=3.0, rs=3.0))
+    with pytest.raises(LSError, match="rule parameters"):
+        hb.near(2.0, [x0] * 3, H, L, rows=rows, rules=dict(n_rho=1))
 
 
 def test_native_3d_operator_solves_the_sphere_problem(lib):
