@@ -275,6 +275,12 @@ def test_host_ball3_rows_match_oracle(lib):
         hb = HostBall3(n_f=nf, n_s=ns, h=h)
         tg = np.concatenate([rng.choice(dz.n_shell, n, replace=False),
                              dz.n_shell + rng.choice(dz.n_cart, n, replace=False)])
+        # targets whose direction lies in three face charts at once (a cube corner)
+        corner = dz.x @ (np.ones(3) / np.sqrt(3)) / np.maximum(np.linalg.norm(dz.x, axis=1), 1e-300)
+        shell_c = int(np.argmax(np.where(np.arange(dz.N) < dz.n_shell, corner, -1)))
+        deep = np.linalg.norm(dz.x, axis=1) > 1.0 - dz.b.w              # interior nodes under the shell
+        inner_c = int(np.argmax(np.where((np.arange(dz.N) >= dz.n_shell) & deep, corner, -1)))
+        tg = np.concatenate([tg, [shell_c, inner_c]])
         for q in tg:
             ref = k_row(dz, 2.0, int(q))
             got, eta = hb.row(2.0, int(q))
