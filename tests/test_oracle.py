@@ -518,17 +518,24 @@ def test_3d_operator_rows_against_ball_potential():
     split Newton-Cotes across the depth -- on every face chart holding the
     target, the interior-type rule on the shell charts for interior targets,
     and the regular sums with 1 - eta): K[1] at random shell and interior
-    nodes against the closed-form ball potential, converging as the grids are
-    refined."""
+    nodes, and at cube-corner targets held by three face charts, against the
+    closed-form ball potential, converging as the grids are refined."""
     from oracle.geometry3d import Ball3, Discretisation3
     from oracle.quadrature3d import k_row
     rng = np.random.default_rng(3)
     errs = []
     for nf, ns, h in ((13, 5, 0.2), (25, 9, 0.1), (49, 17, 0.05)):
         dz = Discretisation3(Ball3(n_f=nf, n_s=ns, h=h))
+        # plus the shell node and the interior node under the shell nearest the
+        # (1, 1, 1) direction, where three face charts overlap
+        corner = dz.x @ (np.ones(3) / np.sqrt(3)) / np.maximum(np.linalg.norm(dz.x, axis=1), 1e-300)
+        idx = np.arange(dz.N)
+        deep = np.linalg.norm(dz.x, axis=1) > 1.0 - dz.b.w
         tg = np.concatenate([rng.choice(dz.n_shell, 6, replace=False),
-                             dz.n_shell + rng.choice(dz.n_cart, 6, replace=False)])
-        K = np.array([k_row(dz, 2.0, q) @ np.ones(dz.N) for q in tg])
+                             dz.n_shell + rng.choice(dz.n_cart, 6, replace=False),
+                             [np.argmax(np.where(idx < dz.n_shell, corner, -1)),
+                              np.argmax(np.where((idx >= dz.n_shell) & deep, corner, -1))]])
+        K = np.array([k_row(dz, 2.0, int(q)) @ np.ones(dz.N) for q in tg])
         ref = exact.ball_volume_potential_const(2.0, 1.0, dz.x[tg])
         errs.append(np.max(np.abs(K - ref)) / np.max(np.abs(ref)))
     assert errs[2] < 2e-4 and errs[0] / errs[1] > 8 and errs[1] / errs[2] > 8
