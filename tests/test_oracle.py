@@ -245,6 +245,34 @@ def test_volume_potential_converges_at_order_Q():
     assert errs[-1, 1] < 1e-7
 
 
+def test_paper_disc_problem_tracks_its_convergence_table():
+    """The scattering problem of Table Disc-Q5-K5 (Section 3.3): unit disc,
+    acoustic size kappa a = 10 with a the diameter (kappa = 5), n = sqrt 2,
+    plane wave along x, Q = 5, dense oracle solves on levels 1 and 2 (797 and
+    3053 nodes) with the order study's rules.  The relative L2 error against
+    the Bessel series lies at or below the paper's at the same number of
+    unknowns (its table log-interpolated; measured 2.85e-2 and 3.83e-3 against
+    6.8e-2 and 3.9e-3), and falls at the table's pre-asymptotic pace (2.9
+    here, 2.54 in the table between its second and third grids).  (The next
+    level, 11 961 nodes, gives 2.49e-4 and order 3.94 against the table's
+    3.80; its dense solve takes minutes, so it is not run here.)"""
+    g = GOLDEN["disc_Q5_kappa5_n_sqrt2"]
+    nu, e2 = np.log(g["unknowns"]), np.log(g["eps2"])
+    errs = []
+    for level in (1, 2):
+        wl = k1_order_workload(level).replace(kappa=5.0, n2_params=(2.0,), p=7 if level == 1 else 9)
+        dz = Discretisation(wl)
+        A = DirectOperator(dz, dense_limit=5000).dense_A()
+        ui = W.plane_wave(5.0, (1, 0), dz.x)
+        u = np.linalg.solve(A, ui)
+        ue = exact.disc_total_field(5.0, 2.0, 1.0, dz.x)
+        err = np.linalg.norm(u - ue) / np.linalg.norm(ue)
+        paper = math.exp(np.interp(math.log(dz.N), nu, e2))
+        assert err <= 1.2 * paper, (dz.N, err, paper)
+        errs.append(err)
+    assert math.log2(errs[0] / errs[1]) > 2.5
+
+
 def test_disc_solution_against_bessel_series(K1_level1, K1_level2):
     """Section 3.3 Example 1 style check: penetrable disc, n^2 = 2, kappa = 2."""
     errs, its = [], []
