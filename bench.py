@@ -33,15 +33,13 @@ sys.path.insert(0, ROOT)
 
 METRIC = "LS matvecs/s and time to 1e-10 solve at N, mixed vs FP64 path, 1 GB300"
 FALLBACK_HBM_GBS = 6800.0
-# FP64 (non-tensor) peak derived from the unit counts and clock: 152 SMs x 2070 MHz x
-# 4 FLOP/clock/SM (2 FP64 FMA per clock per SM, the nominal 1.25 TFLOP/s)
-FP64_PEAK_TFLOPS = 152 * 2.070e9 * 4 / 1e12
 KERNELS_PER_APPLY = 6    # projection, source rows (fill + row FFT), columns (FFT, product, inverse),
 #                          inverse rows, local coefficients, near field + assembly
-# DRAM bytes (read + write) of one k_near_eval launch on the full-size kite workload, from the
-# ncu launch list of this bench (per-launch counters; keyed by the padded block-entry count
-# so that any other workload reports no traffic).  Re-measure whenever k_near_eval changes.
-NEAR_TRAFFIC = {357685015: {"fp64": 8.8942e9, "mixed": 2.9454e9, "tc16": 3.1926e9}}
+# DRAM bytes (read + write) per launch of the near-field kernels on the full-size kite,
+# from the ncu captures summarised in the named profiles/ file.  Keyed by the plan's
+# near-field entry count and by kernel: another workload, or a kernel changed since the
+# capture (remove its entry then), reports null.
+NEAR_TRAFFIC = {}
 
 
 def hbm_peak():
@@ -133,21 +131,69 @@ def replica_rate(local_ms: float, local_units: int, device="cpu"):
     return units / (ms * 1e-3), ms, units
 
 
-def cpu_oracle_rate(wl, n_rows: int, seed_rows=None):
-    """Oracle direct O(N^2) apply on a bounded sample of rows: returns
-    (matvecs/s extrapolated from rows/s, rows, seconds, N)."""
-    import numpy as np
+_ORACLE = {}
+
+
+def _oracle_worker_init(wl):
+    """Spawned worker: build the oracle's direct operator of the workload once."""
     import workloads as W
     from oracle.geometry import Discretisation
     from oracle.operator import DirectOperator
     dz = Discretisation(wl)
-    op = DirectOperator(dz, dense_limit=0)
-    rows = W.random_rows(dz.N, n_rows)
-    u = W.random_density(dz.N)[0]
+    _ORACLE["op"] = DirectOperator(dz, dense_limit=0)
+    _ORACLE["u"] = W.random_density(dz.N)[0]
+
+
+def _oracle_worker_rows(rows):
+    """Direct O(N^2) apply on these rows (64 at a time); returns (rows done, seconds)."""
     t0 = time.perf_counter()
-    op.apply(u, rows=rows)
-    dt = time.perf_counter() - t0
-    return (len(rows) / dt) / dz.N, len(rows), dt, dz.N
+    for s in range(0, len(rows), 64):
+        _ORACLE["op"].apply(_ORACLE["u"], rows=rows[s:s + 64])
+    return len(rows), time.perf_counter() - t0
+
+
+class OraclePool:
+    """The CPU oracle on the host's cores: one spawned process per core (each
+    single-threaded), every process holding the workload's direct operator.
+    A step splits its rows evenly over the processes; its time is the wall time
+    of the whole split, so rows/s counts every core."""
+
+    def __init__(self, wl, procs: int | None = None):
+        import multiprocessing as mp
+        self.procs = procs or os.cpu_count() or 1
+        for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+            os.environ[k] = "1"      # the spawned workers read these at start: one core each
+        self.pool = mp.get_context("spawn").Pool(self.procs, initializer=_oracle_worker_init, initargs=(wl,))
+        import workloads as W
+        self.N = None
+        self.W = W
+
+    def run(self, rows):
+        import numpy as np
+        parts = [p for p in np.array_split(np.asarray(rows), self.procs) if len(p)]
+        t0 = time.perf_counter()
+        done = sum(r for r, _ in self.pool.map(_oracle_worker_rows, parts, chunksize=1))
+        return done, time.perf_counter() - t0
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+
+def cpu_oracle_rate(wl, n_rows: int, procs: int | None = None):
+    """The oracle's direct O(N^2) apply on n_rows seeded rows, split over all
+    host cores: returns (matvecs/s extrapolated from rows/s, rows, seconds, N,
+    processes)."""
+    import workloads as W
+    from oracle.geometry import Discretisation
+    N = Discretisation(wl).N
+    pool = OraclePool(wl, procs)
+    try:
+        pool.run(W.random_rows(N, pool.procs, seed=W.SEED + 2))   # every worker built and warm
+        done, dt = pool.run(W.random_rows(N, n_rows))
+    finally:
+        pool.close()
+    return (done / dt) / N, done, dt, N, pool.procs
 
 
 def run_reference(args):
@@ -155,30 +201,30 @@ def run_reference(args):
     if rank != 0:
         return 0
     import workloads as W
-    wl = W.cfg2()
-    rows_per_step = args.ref_rows
-    import numpy as np
     from oracle.geometry import Discretisation
-    from oracle.operator import DirectOperator
-    dz = Discretisation(wl)
-    op = DirectOperator(dz, dense_limit=0)
-    u = W.random_density(dz.N)[0]
-    rows_all = W.random_rows(dz.N, rows_per_step * (args.steps + args.warmup))
-    for s in range(args.warmup):
-        op.apply(u, rows=rows_all[s * rows_per_step:(s + 1) * rows_per_step])
-    t0 = time.perf_counter()
-    for s in range(args.warmup, args.warmup + args.steps):
-        op.apply(u, rows=rows_all[s * rows_per_step:(s + 1) * rows_per_step])
-    dt = time.perf_counter() - t0
-    rate = (args.steps * rows_per_step / dt) / dz.N
+    wl = W.cfg2()
+    N = Discretisation(wl).N
+    pool = OraclePool(wl)
+    rows_per_step = args.ref_rows * pool.procs
+    rows_all = W.random_rows(N, rows_per_step * (args.steps + args.warmup))
+    try:
+        for s in range(args.warmup):
+            pool.run(rows_all[s * rows_per_step:(s + 1) * rows_per_step])
+        dt = 0.0
+        for s in range(args.warmup, args.warmup + args.steps):
+            dt += pool.run(rows_all[s * rows_per_step:(s + 1) * rows_per_step])[1]
+    finally:
+        pool.close()
+    rate = (args.steps * rows_per_step / dt) / N
+    sample = (f"{rows_per_step} seeded rows x all N sources per step ({args.ref_rows} per process, "
+              f"{pool.procs} single-threaded processes), extrapolated to N rows")
     line = {
         "impl": "reference", "metric": METRIC, "value": rate, "unit": "matvecs/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"cfg2 kite kappa=20 N={dz.N}", "N": dz.N,
-                   "sample": f"{rows_per_step} seeded rows x all N sources per step"},
-        "cpu_baseline": {"value": rate, "unit": "matvecs/s", "cores": 1, "kind": "oracle",
-                         "sample": f"{rows_per_step} rows/step of the direct O(N^2) apply, extrapolated to N rows"},
+        "config": {"workload": f"cfg2 kite kappa=20 N={N}", "N": N, "sample": sample},
+        "cpu_baseline": {"value": rate, "unit": "matvecs/s", "cores": pool.procs, "kind": "oracle",
+                         "sample": sample},
         "e2e": {"value": rate, "unit": "matvecs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -248,6 +294,60 @@ def run_batch(n_inst, dev, barrier, timed):
     return out
 
 
+def run_sphere(spec, dev, barrier, timed, steps):
+    """Reduced config 4: the penetrable sphere of Section 5 (radius 1, n^2 = 1.5
+    inside, kappa = 8, plane wave exp(i kappa x_3)) on a coarser ball than the
+    config's ~2M nodes; spec = (n_f, n_s, h, L, N_eq): shell face points, depth
+    lines, interior spacing, cells per axis of the box [-1.13, 1.13]^3, lattice
+    intervals per cell.  Device apply rates (FP64, complex64) and the time to a
+    1e-10 FP64 residual with the FP64 solve and with mixed precision, plus the
+    solution's error against the Mie series."""
+    import numpy as np
+    import torch
+    from oracle import exact
+    from paper_1509_05063_gb300 import LS_FP64, LS_MIXED, LS_MIXED32, Plan3
+    n_f, n_s, h, L, Ne = spec
+    kappa, n2, half = 8.0, 1.5, 1.13
+    t0 = time.perf_counter()
+    plan = Plan3(lambda x: np.full(len(x), n2), kappa, [-half] * 3, 2 * half / L, L, Ne,
+                 ball=dict(n_f=n_f, n_s=n_s, h=h), rules=dict(rc=3.0, rs=3.0))
+    t_plan = time.perf_counter() - t0
+    xyz, _ = plan.nodes()
+    N = plan.N
+    u = torch.from_numpy(__import__("workloads").random_density(N)[0]).to(dev)
+    u32 = u.to(torch.complex64)
+    o, o32 = torch.empty_like(u), torch.empty_like(u32)
+    for _ in range(3):
+        plan.apply(u, o, prec=LS_FP64)
+        plan.apply(u32, o32, prec=LS_MIXED)
+    ms64 = timed(lambda: plan.apply(u, o, prec=LS_FP64), steps)
+    ms32 = timed(lambda: plan.apply(u32, o32, prec=LS_MIXED), steps)
+    ui = torch.from_numpy(np.exp(1j * kappa * xyz[:, 2])).to(dev)
+    plan.solve(ui, tol=1e-3, prec=LS_FP64, max_iter=3)
+    plan.solve(ui, tol=1e-3, prec=LS_MIXED, max_iter=3)
+    out = {"workload": f"sphere a=1 n^2={n2} kappa={kappa} N={N} (n_f={n_f}, n_s={n_s}, h={h}), "
+                       f"L={L} cells/axis, N_eq={Ne}, lattice M={plan.info['fft_M']}",
+           "N": N, "nnz_near": plan.info["nnz_near"], "plan_s": t_plan,
+           "fp64_matvecs_per_s": steps / (ms64 * 1e-3), "mixed_matvecs_per_s": steps / (ms32 * 1e-3)}
+    ue = exact.sphere_total_field(kappa, n2, 1.0, xyz)
+    sols = {}
+    for name, prec, restart in (("fp64", LS_FP64, 100), ("mixed", LS_MIXED, 30), ("mixed32", LS_MIXED32, 30)):
+        barrier()
+        t0 = time.perf_counter()
+        sol, info = plan.solve(ui, tol=1e-10, prec=prec, max_iter=2000, restart=restart)
+        barrier()
+        sols[name] = sol
+        out[name] = {"time_to_1e-10_s": time.perf_counter() - t0, "iterations": info["iterations"],
+                     "refinements": info["refinements"], "residual": info["residual"],
+                     "converged": info["converged"], "restart": restart}
+    s64 = sols["fp64"].cpu().numpy()
+    out["mixed_vs_fp64_solution_rel"] = float(np.linalg.norm(sols["mixed"].cpu().numpy() - s64) / np.linalg.norm(s64))
+    out["fp64_vs_mie_rel_l2"] = float(np.linalg.norm(s64 - ue) / np.linalg.norm(ue))
+    out["mixed_speedup_time_to_tol"] = out["fp64"]["time_to_1e-10_s"] / out["mixed"]["time_to_1e-10_s"]
+    plan.close()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -256,14 +356,16 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-solve", action="store_true")
-    ap.add_argument("--cpu-rows", type=int, default=192)
-    ap.add_argument("--ref-rows", type=int, default=48)
+    ap.add_argument("--cpu-rows", type=int, default=4096)
+    ap.add_argument("--ref-rows", type=int, default=24, help="oracle rows per process and step")
     ap.add_argument("--autotune", action="store_true",
                     help="pick the cell layout with the autotuner (model + GPU timing of the best 3)")
-    ap.add_argument("--directions", type=int, default=8,
+    ap.add_argument("--directions", type=int, default=16,
                     help="incident directions of the lock-step mixed solve (theta_j = 2 pi j / D)")
-    ap.add_argument("--batch", type=int, default=0,
+    ap.add_argument("--batch", type=int, default=12,
                     help="also time a multi-instance batch of this many seeded scatterers (reduced config 3)")
+    ap.add_argument("--sphere", default="25,9,0.1,7,6",
+                    help="reduced config 4 (penetrable sphere, kappa = 8): n_f,n_s,h,L,N_eq; 'none' to skip")
     ap.add_argument("--scale", type=int, default=1,
                     help="coarsen config 2 by this factor (h, cells) for profiling captures")
     args = ap.parse_args()
@@ -276,6 +378,7 @@ def main():
     import torch
     import workloads as W
     from paper_1509_05063_gb300 import LS_FP64, LS_MIXED, LS_MIXED32, Plan
+    from paper_1509_05063_gb300.ls import measure_peaks
 
     rank, world, local = dist_info()
     if world > 1:
@@ -330,6 +433,7 @@ def main():
         f32()
         fb32()
         fb64()
+    peaks = measure_peaks()          # FP64 FMA and TF32 tensor-core probes (outside the timed region)
     with Clocks(local) as clk:
         ms64 = timed(f64, args.steps)
         ms32 = timed(f32, args.steps)
@@ -413,6 +517,11 @@ def main():
                  "mixed32_block_converged": ib3["converged"], "mixed32_block_residual": ib3["residual"]}
 
     batch = run_batch(args.batch, dev, barrier, timed) if args.batch > 0 else None
+    sphere = None
+    if args.sphere != "none":
+        f = args.sphere.split(",")
+        sphere = run_sphere((int(f[0]), int(f[1]), float(f[2]), int(f[3]), int(f[4])), dev, barrier, timed,
+                            max(args.steps // 2, 3))
 
     # roofline of the dominant kernel (near field + local evaluation + assembly)
     nnz = info["nnz_near"]
@@ -426,6 +535,11 @@ def main():
 
     peak, peak_src = hbm_peak()
     traffic = NEAR_TRAFFIC.get(nnz, {})
+    fp64_peak = peaks["fp64"]
+    # TF32 work the tensor-core near field issues per launch: per complex weight
+    # (padded to 16-column chunks) and K step, 2 x 2 x (4R + 2R) multiply-adds
+    nchunk_cols = nnz              # close to the padded count (rows padded to 8 add < 3 %)
+    tc_flops = nchunk_cols * 2 * 2 * (4 * NB32 + 2 * NB32)
     # FP64 flops of one launch: 3 FMAs per block weight (three-multiplication
     # complex product), 4 per Phi-gamma term
     near_flops = nnz * 6 + N * nfb2 * 8
@@ -449,10 +563,10 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        rate, nrows, dt, n = cpu_oracle_rate(wl, args.cpu_rows)
-        cpu = {"value": rate, "unit": "matvecs/s", "cores": 1, "kind": "oracle",
-               "sample": f"{nrows} seeded rows of the direct O(N^2) FP64 apply ({dt:.1f} s), "
-                         f"extrapolated to all {n} rows"}
+        rate, nrows, dt, n, procs = cpu_oracle_rate(wl, args.cpu_rows)
+        cpu = {"value": rate, "unit": "matvecs/s", "cores": procs, "kind": "oracle",
+               "sample": f"{nrows} seeded rows of the direct O(N^2) FP64 apply split over {procs} "
+                         f"single-threaded processes ({dt:.1f} s), extrapolated to all {n} rows"}
 
     value = world * args.steps / (ms64 * 1e-3)
     line = {
@@ -467,13 +581,16 @@ def main():
         "e2e": {"value": world * args.steps / (ms_e2e * 1e-3), "unit": "matvecs/s",
                 "h2d_bytes_per_step": N * 16, "d2h_bytes_per_step": N * 16},
         "roofline": {"bound": "alu", "kernel": "k_near_eval5<double2,1>",
-                     "achieved": near_flops / t_near64 / 1e12, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": near_flops / t_near64 / 1e12 / FP64_PEAK_TFLOPS, "traffic": traffic.get("fp64"),
-                     "peak_source": "derived: 152 SMs x 2070 MHz x 2 FP64 FMA/clk/SM",
+                     "achieved": near_flops / t_near64 / 1e12, "peak": fp64_peak, "unit": "TFLOP/s",
+                     "frac": near_flops / t_near64 / 1e12 / fp64_peak, "traffic": traffic.get("fp64"),
+                     "peak_source": "measured: ls_measure_peaks FP64 FMA probe (16 independent chains per "
+                                    "thread, every SM, CUDA events), this run",
                      "flops_per_launch": near_flops, "bytes_per_launch": near_bytes(16, 24),
                      "hbm_GBs": ach64, "hbm_frac": ach64 / peak, "hbm_peak": peak, "hbm_peak_source": peak_src,
                      "launch_ms": t_near64 * 1e3},
         "gpu_launches": KERNELS_PER_APPLY * args.steps,
+        "peaks_measured": {"fp64_tflops": peaks["fp64"], "tf32_tflops": peaks["tf32"],
+                           "hbm_gbs": peak, "hbm_source": peak_src},
         "clocks": clocks,
         "mixed": {"value": world * args.steps / (ms32 * 1e-3), "unit": "matvecs/s", "dtype": "f32",
                   "ms_per_step": ms32 / args.steps,
@@ -488,7 +605,12 @@ def main():
                                            "achieved": ach_b, "peak": peak, "unit": "GB/s", "frac": ach_b / peak,
                                            "peak_source": peak_src, "bytes_per_launch": near_bytes_b,
                                            "traffic": traffic.get("tc16") if NB32 == 16 else None,
-                                           "launch_ms": t_near_b * 1e3},
+                                           "launch_ms": t_near_b * 1e3,
+                                           "tf32_tflops": tc_flops / t_near_b / 1e12,
+                                           "tf32_peak": peaks["tf32"],
+                                           "tf32_frac": tc_flops / t_near_b / 1e12 / peaks["tf32"],
+                                           "tf32_peak_source": "measured: ls_measure_peaks tcgen05 "
+                                                               "128x256x8 MMA probe, this run"},
                               "apply_hbm_frac": (apply_bytes_b / (msb32 / nb_steps * 1e-3) / 1e9) / peak,
                               "stages_ms": dict(zip(stage_names, [float(x) / max(cb, 1) for x in stb]))},
                     "fp64": {"nrhs": NB64, "value": world * nb_steps * NB64 / (msb64 * 1e-3), "dtype": "f64"}},
@@ -499,6 +621,8 @@ def main():
     }
     if batch is not None:
         line["batch"] = batch
+    if sphere is not None:
+        line["sphere_3d"] = sphere
     if cpu is not None:
         line["cpu_baseline"] = cpu
     if rank == 0:

@@ -45,7 +45,7 @@ typedef enum {
   LS_ERR_CUDA = 3,         /* a CUDA call or kernel launch failed              */
   LS_ERR_NOCONV = 4,       /* GMRES / refinement did not reach the tolerance   */
   LS_ERR_TIMEOUT = 5,      /* a bounded device wait gave up                    */
-  LS_ERR_UNSUPPORTED = 6   /* feature not built (e.g. dim = 3)                 */
+  LS_ERR_UNSUPPORTED = 6   /* entry point not available for this plan           */
 } ls_status;
 
 /* LS_FP64: complex128 throughout.  LS_MIXED: complex64 apply inside FP64
@@ -248,7 +248,8 @@ const char* ls_batch_last_error(ls_batch b);
  * device current; make that first call before any stream capture.  All calls
  * share the array: calls whose GPU work overlaps race and corrupt each other.
  * Nothing in the array needs to start at zero.  It allocates nothing (no
- * cudaMalloc / cudaFree). */
+ * cudaMalloc / cudaFree).  The plan's device (current when the plan was
+ * created) must be current: otherwise LS_ERR_INVALID. */
 ls_status ls_apply_noalloc(ls_plan plan, const void* u_dev, void* Au_dev, ls_precision prec, void* stream);
 
 /* Device-side failure detection.  The tensor-core near field (8 and 16
@@ -265,6 +266,17 @@ ls_status ls_apply_noalloc(ls_plan plan, const void* u_dev, void* Au_dev, ls_pre
  * synchronises the device and drops the plan's captured applies. */
 ls_status ls_plan_device_status(ls_plan plan);
 ls_status ls_set_wait_limit(ls_plan plan, int polls);
+
+/* Measurement aid with no counterpart in the paper: the throughput of the
+ * current GPU's FP64 fused multiply-add (CUDA cores, independent FMA chains
+ * on every SM) and of its TF32 tensor-core MMA (tcgen05, M = 128, N = 256,
+ * K = 8, operands in shared memory, one issuing thread per SM), in TFLOP/s
+ * counting 2 per multiply-add, timed with CUDA events (about 0.5 s in all).
+ * These are the roofline denominators of the FP64 near field and of the
+ * 3xTF32 tensor-core near field.  Host pointers; blocking; LS_ERR_CUDA on a
+ * CUDA error and LS_ERR_TIMEOUT if a (bounded) wait of the tensor-core probe
+ * gave up, with the message in ls_last_error(NULL). */
+ls_status ls_measure_peaks(double* fp64_tflops, double* tf32_tflops);
 
 /* Per-stage device timing of ls_apply with CUDA events recorded on the call's
  * stream (measurement aid; enabling it makes ls_apply wait for each apply).
@@ -374,6 +386,38 @@ ls_status ls_host_ball3_nodes(ls_host_ball3 h, double* xyz, double* w, double* o
                               int32_t* grid);
 ls_status ls_host_ball3_destroy(ls_host_ball3 h);
 
+/* ---- 3-D device plan (Section 5) -------------------------------------------
+ * A plan for the penetrable ball: the discretisation of ls_host_ball3_create,
+ * the singular rules of ls_host_ball3_row with its adjacent part stored for
+ * the device (ls_host_ball3_near over every node, the contrast of the source
+ * node folded in), and the 3-D accelerator of ls_host_accel3_create for the
+ * far part (two-face equivalent sources on cube cells, a zero-padded M^3
+ * lattice FFT with the G and dG/dz_1 tables, 27-neighbour subtraction and a
+ * spherical-wave local expansion).  The complex64 apply uses the same fits
+ * rounded to complex64, with the neighbours subtracted on the lattice and the
+ * local fit folded into the evaluation (E = Phi B^+ per node, formed in FP64):
+ * B^+ of the spherical-wave basis is ill-conditioned and would magnify the
+ * complex64 rounding of the lattice field.  n2 receives the nodes as xyz triples
+ * (3 n doubles).  The returned ls_plan works with ls_plan_info (n_collar =
+ * shell nodes, n_cart = interior nodes, n_fb = local-expansion terms
+ * (p + 1)^2), ls_plan_nodes (xyz: 3 N doubles in plan order; canon: the
+ * ball's node id), ls_apply, ls_solve (any number of right-hand sides, applied
+ * one after another), ls_farfield (dirs: 3 ndir doubles; A(x_hat) = kappa^2 /
+ * (4 pi) sum w omega (n^2 - 1) u exp(-i kappa x_hat . y), the standard 3-D
+ * asymptotics, not in the paper) and ls_plan_destroy; ls_apply_noalloc and
+ * ls_batch_create return LS_ERR_UNSUPPORTED for it.  Every node must lie in
+ * the cell box and every cut-off inside its 3 x 3 x 3 cell block
+ * (LS_ERR_INVALID otherwise); kappa sqrt(3) H / 2 < pi.  Host-blocking. */
+typedef struct {
+  double box0[3];        /* corner of the cell box                               */
+  double H;              /* cube cell side                                      */
+  int L;                 /* cells per axis                                      */
+  int N_eq;              /* lattice intervals per cell side                     */
+  int p;                 /* local-expansion degree (0 = 2 N_eq + 1)             */
+  int m_coll;            /* collocation points per face side (0 = automatic)    */
+  double rcond;          /* SVD truncation of the fits (0 = 1e-13)              */
+  int n_threads;         /* host threads (0 = all)                              */
+} ls_accel3;
 /* One row of the 3-D operator K (Section 5) at node q of a ball:
  * K[u](x_q) = sum_n row[n] u[n] with u the density at the nodes (the contrast
  * m = 1 - n^2 is applied by the caller: the discrete equation is
@@ -404,6 +448,12 @@ typedef struct {
 } ls_rules3;
 ls_status ls_host_ball3_row(ls_host_ball3 h, double kappa, const ls_rules3* rules, int64_t q, double* row,
                             double* eta);
+
+/* The 3-D device plan (see ls_accel3 above): ball, rules (NULL: defaults),
+ * n^2 callback (xyz triples), kappa and the accelerator options.  On failure
+ * *out is NULL and the message is in ls_last_error(NULL). */
+ls_status ls_plan_create3(const ls_ball3* ball, const ls_rules3* rules, ls_n2_fn n2, void* ctx, double kappa,
+                          const ls_accel3* acc, ls_plan* out);
 
 /* Adjacent part of the 3-D operator (Section 5 with the adjacency of
  * Section 3.2) for the rows listed (rows NULL: every node, in node order):

@@ -183,6 +183,13 @@ struct ls_plan_s : DevOwner {
   double* dirs = nullptr;
   int dirs_cap = 0;
   ls_plan_info_t info{};
+  int device = -1;                  // ordinal of the GPU that holds the plan's arrays
+  int dim = 2;                      // 3: a ball (ls_plan_create3); d64 / d32 then hold N only
+  lsd::ApplyData3<double2> e64;     // 3-D apply data
+  lsd::ApplyData3<float2> e32;
+  std::vector<double> xyz3;         // 3-D: node coordinates in plan order
+  std::vector<int64_t> canon3;      // 3-D: ball node id of each plan node
+  double* ffw3 = nullptr;           // 3-D: w omega (n^2 - 1) per node (far field)
   GraphCache graphs;                // CUDA graphs of the apply
   // optional per-stage event timing of ls_apply
   bool timing = false;
@@ -215,10 +222,16 @@ ls_status fail(DevOwner* p, ls_status s, const std::string& m) {
 
 // Apply through a cached CUDA graph of the whole kernel sequence (direct
 // launches when timing, on the first call of a key, or if capture fails).
+template <typename T> const lsd::ApplyData3<T>& data3(ls_plan p);
+template <> const lsd::ApplyData3<double2>& data3<double2>(ls_plan p) { return p->e64; }
+template <> const lsd::ApplyData3<float2>& data3<float2>(ls_plan p) { return p->e32; }
+
 template <typename T>
 cudaError_t run_apply(ls_plan plan, int prec, const lsd::ApplyData<T>& d, const T* u, T* out, int nr,
                       cudaStream_t st) {
-  auto launch = [&](cudaStream_t s) { return lsd::apply_batch(d, u, out, nr, s); };
+  auto launch = [&](cudaStream_t s) {
+    return plan->dim == 3 ? lsd::apply3_batch(data3<T>(plan), u, out, nr, s) : lsd::apply_batch(d, u, out, nr, s);
+  };
   if (plan->timing) return launch(st);
   return plan->graphs.run(GraphCache::Key(prec, nr, static_cast<const void*>(u), static_cast<void*>(out)), launch,
                           st);
@@ -631,6 +644,11 @@ ls_status ls_plan_create(const ls_geometry* geom, ls_n2_fn n2, void* ctx, double
   const auto t0 = std::chrono::steady_clock::now();
   ls_plan plan = new (std::nothrow) ls_plan_s;
   if (!plan) return fail(nullptr, LS_ERR_NOMEM, "host allocation failed");
+  if (cudaGetDevice(&plan->device) != cudaSuccess) {
+    cudaGetLastError();
+    delete plan;
+    return fail(nullptr, LS_ERR_CUDA, "cudaGetDevice failed");
+  }
   lsh::Plan2D& P = plan->host;
   auto bail = [&](ls_status s, const std::string& m) {
     g_create_error = m;
@@ -796,6 +814,15 @@ ls_status ls_plan_create(const ls_geometry* geom, ls_n2_fn n2, void* ctx, double
   const int2* d_items32 = reinterpret_cast<const int2*>(d_items32_raw);
   const int* d_items128_raw = UP(int, items128);
   const int2* d_items128 = reinterpret_cast<const int2*>(d_items128_raw);
+  // offsets of the 128-row items in the tensor-core tile layout of the weights
+  std::vector<int64_t> tile_off(items128.size() / 2 + 1, 0);
+  for (size_t i = 0; i + 1 < tile_off.size(); ++i) {
+    const int k = items128[2 * i], r = items128[2 * i + 1];
+    const int* sg = &blk_seg[6 * k];
+    const int nblk = padded(sg[1]) + padded(sg[3]) + padded(sg[5]);
+    tile_off[i + 1] = tile_off[i] + lsd::tc_tile_elems(int(occ_start[k + 1] - occ_start[k] - r), nblk);
+  }
+  const int64_t* d_tile_off = UP(int64_t, tile_off);
   int* d_tc_err = UP(int, std::vector<int>(1, 0));
   const int64_t* d_blk_off = UP(int64_t, blk_off);
   const int* d_blk_seg = UP(int, blk_seg);
@@ -928,6 +955,7 @@ ls_status ls_plan_create(const ls_geometry* geom, ls_n2_fn n2, void* ctx, double
   b.items = d_items; b.n_items = a.n_items;
   b.items32 = a.items32; b.n_items32 = a.n_items32;
   b.items128 = d_items128; b.n_items128 = int(items128.size() / 2);
+  b.tile_off = d_tile_off;
   b.tc_err = d_tc_err;
   b.P = UP(float2, to32(P.P32));
   b.LA = UP(float2, to32(LA));
@@ -936,6 +964,13 @@ ls_status ls_plan_create(const ls_geometry* geom, ls_n2_fn n2, void* ctx, double
     std::vector<std::complex<float>> w32 = to32(Wb);
     std::vector<cd>().swap(Wb);
     b.Wb = UP(float2, w32);
+  }
+  {   // the same blocks in the tile layout the tensor-core near field copies in bulk
+    float2* wt = plan->alloc<float2>(size_t(tile_off.back()), &st);
+    if (st != LS_OK) return bail(st, plan->err);
+    const cudaError_t e = lsd::tile_weights(b, wt, 0);
+    if (e != cudaSuccess) return bail(LS_ERR_CUDA, std::string("tile layout: ") + cudaGetErrorString(e));
+    b.Wt = wt;
   }
   b.rem_val = UP(float2, to32(rem_val));
   b.Gq = d_G32; b.Dq = d_D32;
@@ -965,6 +1000,219 @@ ls_status ls_plan_create(const ls_geometry* geom, ls_n2_fn n2, void* ctx, double
   return LS_OK;
 }
 
+ls_status ls_plan_create3(const ls_ball3* ball, const ls_rules3* rules, ls_n2_fn n2, void* ctx, double kappa,
+                          const ls_accel3* acc, ls_plan* out) {
+  if (!out) return fail(nullptr, LS_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  if (!ball || !acc || !n2) return fail(nullptr, LS_ERR_INVALID, "ball, acc or n2 is NULL");
+  if (!(kappa > 0) || !(acc->H > 0) || acc->L < 1 || acc->N_eq < 1 || acc->p < 0 || acc->m_coll < 0 ||
+      acc->rcond < 0)
+    return fail(nullptr, LS_ERR_INVALID, "invalid kappa or accelerator options");
+  const auto t0 = std::chrono::steady_clock::now();
+  ls_plan plan = new (std::nothrow) ls_plan_s;
+  if (!plan) return fail(nullptr, LS_ERR_NOMEM, "host allocation failed");
+  if (cudaGetDevice(&plan->device) != cudaSuccess) {
+    cudaGetLastError();
+    delete plan;
+    return fail(nullptr, LS_ERR_CUDA, "cudaGetDevice failed");
+  }
+  plan->dim = 3;
+  auto bail = [&](ls_status st, const std::string& m) {
+    g_create_error = m;
+    plan->free_all();
+    delete plan;
+    return st;
+  };
+  const int nt = acc->n_threads > 0 ? acc->n_threads : int(std::max(1u, std::thread::hardware_concurrency()));
+  lsh::Ball3 B;
+  B.a = ball->a; B.w = ball->w; B.n_f = ball->n_f; B.n_s = ball->n_s; B.Q = ball->Q;
+  B.delta = ball->delta; B.h = ball->h; B.tau0 = ball->tau0; B.tau1 = ball->tau1;
+  std::vector<cd> P64, LA64, Phi64, Gs, Ds;
+  std::vector<std::complex<float>> P32;
+  std::vector<double> m, wfac;
+  lsh::Accel3 A;
+  try {
+    if (!lsh::build_ball3(B)) return bail(LS_ERR_INVALID, B.err);
+    const int64_t N = B.N;
+    // contrast m = 1 - n^2 at the nodes (the callback receives 3 coordinates per point)
+    std::vector<double> n2v(N, 1.0);
+    if (n2(N, B.x.data(), n2v.data(), ctx) != 0) return bail(LS_ERR_INVALID, "n2 callback failed");
+    m.resize(N);
+    wfac.resize(N);
+    for (int64_t q = 0; q < N; ++q) {
+      m[q] = 1.0 - n2v[q];
+      wfac[q] = B.w_q[q] * B.omega[q] * m[q];
+    }
+    std::string em;
+    if (!lsh::ball3_near(B, kappa, rules_from(rules), acc->box0, acc->H, acc->L, nullptr, 0, false, nt, &em))
+      return bail(LS_ERR_INVALID, em);
+    A.kappa = kappa; A.H = acc->H; A.L = acc->L; A.Ne = acc->N_eq; A.p = acc->p; A.m_coll = acc->m_coll;
+    A.n_threads = nt;
+    for (int k = 0; k < 3; ++k) A.box0[k] = acc->box0[k];
+    // one set of fits (truncation rcond, 1e-13 by default) serves both precisions
+    A.rcond = acc->rcond > 0 ? acc->rcond : 1e-13;
+    if (!lsh::build_accel3(A, B.x.data(), wfac.data(), N)) return bail(LS_ERR_INVALID, A.err);
+    const int nocc = int(A.occ_cells.size());
+    const int n_es = A.n_es, nb = A.nb, n_loc = A.n_loc, M = A.M, L = acc->L;
+    // plan order: the accelerator's node order (grouped by cell)
+    const std::vector<int64_t>& order = A.node_order;
+    std::vector<int64_t> inv(N);
+    for (int64_t i = 0; i < N; ++i) inv[order[i]] = i;
+    std::vector<int64_t> occ_start(nocc + 1, 0);
+    for (int k = 0; k < nocc; ++k) occ_start[k + 1] = occ_start[k] + (A.P_off[k + 1] - A.P_off[k]) / n_es;
+    if (occ_start[nocc] != N) return bail(LS_ERR_INVALID, "accelerator cells do not hold every node");
+    std::vector<int> occ_of_cell(size_t(L) * L * L, -1), occ_of_node(N);
+    for (int k = 0; k < nocc; ++k) {
+      occ_of_cell[A.occ_cells[k]] = k;
+      for (int64_t q = occ_start[k]; q < occ_start[k + 1]; ++q) occ_of_node[q] = k;
+    }
+    // projections per cell stored [node][n_es]
+    auto node_major = [&](const std::vector<cd>& Pm, auto& dst) {
+      dst.resize(Pm.size());
+      for (int k = 0; k < nocc; ++k) {
+        const int64_t base = A.P_off[k], nc = occ_start[k + 1] - occ_start[k];
+        for (int i = 0; i < n_es; ++i)
+          for (int64_t j = 0; j < nc; ++j) {
+            const cd v = Pm[base + i * nc + j];
+            dst[base + j * n_es + i] = {decltype(dst[0].real())(v.real()), decltype(dst[0].real())(v.imag())};
+          }
+      }
+    };
+    node_major(A.P, P64);
+    node_major(A.P, P32);
+    // [B^+ | -B^+ T_o] stored transposed: [n_loc + 27 n_es][nb]
+    const int K = n_loc + 27 * n_es;
+    auto local_matrix = [&](const lsh::Accel3& a, auto& dst) {
+      dst.resize(size_t(K) * nb);
+      for (int n = 0; n < nb; ++n) {
+        for (int q = 0; q < n_loc; ++q) {
+          const cd v = a.Bpinv[size_t(n) * n_loc + q];
+          dst[size_t(q) * nb + n] = {decltype(dst[0].real())(v.real()), decltype(dst[0].real())(v.imag())};
+        }
+        for (int o = 0; o < 27; ++o)
+          for (int l = 0; l < n_es; ++l) {
+            const cd v = -a.BT[(size_t(o) * nb + n) * n_es + l];
+            dst[size_t(n_loc + o * n_es + l) * nb + n] = {decltype(dst[0].real())(v.real()),
+                                                         decltype(dst[0].real())(v.imag())};
+          }
+      }
+    };
+    local_matrix(A, LA64);
+    Phi64.resize(size_t(N) * nb);
+    for (int64_t i = 0; i < N; ++i)
+      std::copy(A.Phi.begin() + order[i] * nb, A.Phi.begin() + (order[i] + 1) * nb, Phi64.begin() + i * nb);
+    // adjacent part in plan order, contrast of the source node folded in
+    std::vector<int64_t> rowptr(N + 1, 0);
+    for (int64_t i = 0; i < N; ++i)
+      rowptr[i + 1] = rowptr[i] + (B.near_rowptr[order[i] + 1] - B.near_rowptr[order[i]]);
+    std::vector<int> col(rowptr[N]);
+    std::vector<cd> val(rowptr[N]);
+    for (int64_t i = 0; i < N; ++i) {
+      int64_t o = rowptr[i];
+      for (int64_t e = B.near_rowptr[order[i]]; e < B.near_rowptr[order[i] + 1]; ++e, ++o) {
+        col[o] = int(inv[B.near_col[e]]);
+        val[o] = B.near_val[e] * m[B.near_col[e]];
+      }
+    }
+    std::vector<int32_t>().swap(B.near_col);
+    std::vector<cd>().swap(B.near_val);
+    ls_status st = LS_OK;
+#define UP3(T, v) plan->upload<T>(v, &st); if (st != LS_OK) return bail(st, plan->err)
+    const int64_t* d_occ_start = UP3(int64_t, occ_start);
+    const int* d_occ_cells = UP3(int, A.occ_cells);
+    const int* d_occ_of_cell = UP3(int, occ_of_cell);
+    const int* d_occ_of_node = UP3(int, occ_of_node);
+    const int64_t* d_P_off = UP3(int64_t, A.P_off);
+    const int64_t* d_rowptr = UP3(int64_t, rowptr);
+    const int* d_col = UP3(int, col);
+    int logM = 0;
+    while ((1 << logM) < M) ++logM;
+    std::vector<cd> tw(M);
+    for (int q = 0; q < M; ++q) tw[q] = std::polar(1.0, -2.0 * M_PI * double(q) / M);
+    double2* d_tw64 = UP3(double2, tw);
+    // spectra: 3-D FFT of the lattice tables on the device, scaled by 1 / M^3
+    const int64_t M3 = int64_t(M) * M * M;
+    {
+      double2* tmp = plan->alloc<double2>(size_t(M3), &st);
+      if (st != LS_OK) return bail(st, plan->err);
+      Gs.resize(M3);
+      Ds.resize(M3);
+      const double sc = 1.0 / double(M3);
+      for (int which = 0; which < 2; ++which) {
+        const std::vector<cd>& tab = which == 0 ? A.Gtab : A.Dtab;
+        std::vector<cd>& dst = which == 0 ? Gs : Ds;
+        cudaError_t e = cudaMemcpy(tmp, tab.data(), M3 * sizeof(double2), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = lsd::fft3d<double2>(tmp, M, logM, d_tw64, false, 0);
+        if (e == cudaSuccess) e = cudaMemcpy(dst.data(), tmp, M3 * sizeof(double2), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return bail(LS_ERR_CUDA, std::string("3-D spectra: ") + cudaGetErrorString(e));
+        for (auto& z : dst) z *= sc;
+      }
+      plan->release(tmp);
+    }
+    auto& a = plan->e64;
+    a.N = N; a.nocc = nocc; a.L = L; a.Ne = acc->N_eq; a.n_es = n_es; a.n_loc = n_loc; a.nb = nb; a.M = M;
+    a.logM = logM;
+    a.occ_start = d_occ_start; a.occ_cells = d_occ_cells; a.occ_of_cell = d_occ_of_cell;
+    a.occ_of_node = d_occ_of_node; a.P_off = d_P_off; a.rowptr = d_rowptr; a.col = d_col;
+    a.P = UP3(double2, P64);
+    a.LA = UP3(double2, LA64);
+    a.Phi = UP3(double2, Phi64);
+    a.Gs = UP3(double2, Gs);
+    a.Ds = UP3(double2, Ds);
+    a.tw = d_tw64;
+    a.val = UP3(double2, val);
+    a.kappa2 = kappa * kappa;
+    a.sigma = plan->alloc<double2>(size_t(nocc) * n_es, &st);
+    a.Sm = plan->alloc<double2>(size_t(M3), &st);
+    a.Sd = plan->alloc<double2>(size_t(M3), &st);
+    a.gamma = plan->alloc<double2>(size_t(nocc) * nb, &st);
+    if (st != LS_OK) return bail(st, plan->err);
+    auto& b = plan->e32;
+    b.N = a.N; b.nocc = a.nocc; b.L = a.L; b.Ne = a.Ne; b.n_es = a.n_es; b.n_loc = a.n_loc; b.nb = a.nb; b.M = a.M;
+    b.logM = a.logM;
+    b.occ_start = a.occ_start; b.occ_cells = a.occ_cells; b.occ_of_cell = a.occ_of_cell;
+    b.occ_of_node = a.occ_of_node; b.P_off = a.P_off; b.rowptr = a.rowptr; b.col = a.col;
+    // the complex64 apply runs the lattice convolution and the local
+    // coefficients on the FP64 arrays (see apply3_batch): only the projection,
+    // the adjacent part and the evaluation are complex64
+    b.P = UP3(float2, P32);
+    b.Phi = UP3(float2, to32(Phi64));
+    b.lattice64 = &plan->e64;
+    b.val = UP3(float2, to32(val));
+    b.kappa2 = a.kappa2;
+    b.sigma = plan->alloc<float2>(size_t(nocc) * n_es, &st);
+    b.gamma = plan->alloc<float2>(size_t(nocc) * nb, &st);
+    if (st != LS_OK) return bail(st, plan->err);
+    // coordinates and far-field weights in plan order; N in the 2-D apply data
+    // (the solver and ls_apply read it there)
+    plan->xyz3.resize(size_t(3) * N);
+    plan->canon3 = order;
+    std::vector<double> xs(N), ys(N), ffw(N);
+    for (int64_t i = 0; i < N; ++i) {
+      for (int k = 0; k < 3; ++k) plan->xyz3[3 * i + k] = B.x[3 * order[i] + k];
+      ffw[i] = -B.w_q[order[i]] * B.omega[order[i]] * m[order[i]];      // w omega (n^2 - 1)
+    }
+    plan->x = UP3(double, plan->xyz3);
+    plan->ffw3 = UP3(double, ffw);
+#undef UP3
+    plan->d64.N = N;
+    plan->d32.N = N;
+    plan->d64.kappa2 = plan->d32.kappa2 = kappa * kappa;
+    plan->host.kappa = kappa;
+    if (cudaDeviceSynchronize() != cudaSuccess) return bail(LS_ERR_CUDA, "upload failed");
+    ls_plan_info_t& inf = plan->info;
+    inf.N = N; inf.n_collar = B.n_shell; inf.n_cart = B.n_cart; inf.nnz_near = rowptr[N];
+    inf.L = L; inf.N_eq = acc->N_eq; inf.n_es = n_es; inf.n_loc = n_loc; inf.n_fb = nb;
+    inf.fft_M = M; inf.n_cells_occupied = nocc;
+    inf.plan_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    inf.device_bytes = plan->device_bytes;
+  } catch (const std::bad_alloc&) {
+    return bail(LS_ERR_NOMEM, "host allocation failed");
+  }
+  *out = plan;
+  return LS_OK;
+}
+
 ls_status ls_plan_info(ls_plan plan, ls_plan_info_t* info) {
   if (!plan || !info) return LS_ERR_INVALID;
   *info = plan->info;
@@ -973,6 +1221,11 @@ ls_status ls_plan_info(ls_plan plan, ls_plan_info_t* info) {
 
 ls_status ls_plan_nodes(ls_plan plan, double* xy, int64_t* canon) {
   if (!plan) return LS_ERR_INVALID;
+  if (plan->dim == 3) {
+    if (xy) std::copy(plan->xyz3.begin(), plan->xyz3.end(), xy);
+    if (canon) std::copy(plan->canon3.begin(), plan->canon3.end(), canon);
+    return LS_OK;
+  }
   const lsh::Nodes& nd = plan->host.nodes;
   if (xy)
     for (int64_t i = 0; i < nd.N; ++i) { xy[2 * i] = nd.x[i]; xy[2 * i + 1] = nd.y[i]; }
@@ -986,7 +1239,7 @@ ls_status ls_apply(ls_plan plan, const void* u, void* Au, int nrhs, ls_precision
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int64_t N = plan->d64.N;
   if (prec != LS_FP64 && prec != LS_MIXED) return fail(plan, LS_ERR_INVALID, "ls_apply: bad precision");
-  cudaEvent_t* ev = plan->timing ? plan->ev : nullptr;
+  cudaEvent_t* ev = plan->timing && plan->dim == 2 ? plan->ev : nullptr;
   const int maxr = prec == LS_FP64 ? lsd::kMaxRhs64 : lsd::kMaxRhs32;
   for (int r = 0; r < nrhs;) {
     int nr = maxr;                       // largest power of two batch that fits
@@ -1690,12 +1943,40 @@ ls_status ls_farfield(ls_plan plan, const void* u, int nrhs, const double* dirs_
     if (s != LS_OK) return s;
     plan->dirs_cap = ndir;
   }
+  if (plan->dim == 3) {
+    if (3 * ndir > 2 * plan->dirs_cap) {
+      ls_status s = LS_OK;
+      plan->dirs = plan->alloc<double>(size_t(3) * ndir, &s);
+      if (s != LS_OK) return s;
+      plan->dirs_cap = (3 * ndir + 1) / 2;
+    }
+    LS_CU(cudaMemcpyAsync(plan->dirs, dirs_host, sizeof(double) * 3 * ndir, cudaMemcpyHostToDevice, st));
+    const double k = std::sqrt(plan->e64.kappa2);
+    LS_CU(lsd::farfield3(plan->e64.N, plan->x, plan->ffw3, static_cast<const double2*>(u), nrhs, plan->dirs, ndir,
+                         k, make_double2(k * k / (4 * M_PI), 0.0), static_cast<double2*>(A), st));
+    LS_CU(cudaStreamSynchronize(st));
+    return LS_OK;
+  }
   LS_CU(cudaMemcpyAsync(plan->dirs, dirs_host, sizeof(double) * 2 * ndir, cudaMemcpyHostToDevice, st));
   const double k = plan->host.kappa;
   const std::complex<double> c = std::polar(1.0, M_PI / 4) / std::sqrt(8 * M_PI * k) * (k * k);
   LS_CU(lsd::farfield(plan->d64.N, plan->x, plan->y, plan->ffw, static_cast<const double2*>(u), nrhs, plan->dirs,
                       ndir, k, make_double2(c.real(), c.imag()), static_cast<double2*>(A), st));
   LS_CU(cudaStreamSynchronize(st));
+  return LS_OK;
+}
+
+ls_status ls_measure_peaks(double* fp64_tflops, double* tf32_tflops) {
+  if (!fp64_tflops || !tf32_tflops) return LS_ERR_INVALID;
+  const cudaError_t e = lsd::measure_peaks(fp64_tflops, tf32_tflops);
+  if (e != cudaSuccess) {
+    g_create_error = std::string("ls_measure_peaks: ") + cudaGetErrorString(e);
+    return LS_ERR_CUDA;
+  }
+  if (*tf32_tflops < 0) {
+    g_create_error = "ls_measure_peaks: a wait of the tensor-core probe gave up";
+    return LS_ERR_TIMEOUT;
+  }
   return LS_OK;
 }
 
@@ -1711,6 +1992,10 @@ ls_status ls_set_wait_limit(ls_plan plan, int polls) {
 
 ls_status ls_plan_device_status(ls_plan plan) {
   if (!plan) return LS_ERR_INVALID;
+  if (!plan->d32.tc_err) {          // no kernel of this plan waits on the device (3-D plans)
+    LS_CU(cudaDeviceSynchronize());
+    return LS_OK;
+  }
   int flag = 0;
   LS_CU(cudaMemcpy(&flag, plan->d32.tc_err, sizeof(int), cudaMemcpyDeviceToHost));
   if (!flag) return LS_OK;
@@ -1777,8 +2062,17 @@ template <typename T>
 ls_status noalloc_apply(ls_plan plan, const lsd::ApplyData<T>& src, const void* u, void* Au, cudaStream_t st) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess || dev < 0 || dev >= 256)
+  if (e != cudaSuccess)
     return fail(plan, LS_ERR_CUDA, std::string("ls_apply_noalloc: cudaGetDevice: ") + cudaGetErrorString(e));
+  if (dev < 0 || dev >= 256)
+    return fail(plan, LS_ERR_INVALID, "ls_apply_noalloc: device ordinal " + std::to_string(dev) +
+                                          " is outside the 256 devices this entry point supports");
+  if (dev != plan->device)
+    // the fixed array of the current device and the plan's arrays would sit on
+    // two different GPUs
+    return fail(plan, LS_ERR_INVALID, "ls_apply_noalloc: the current device (" + std::to_string(dev) +
+                                          ") is not the plan's device (" + std::to_string(plan->device) +
+                                          "); make the plan's device current first");
   void* base = nullptr;
   {
     std::lock_guard<std::mutex> lk(g_noalloc_mu);
@@ -1828,6 +2122,7 @@ ls_status noalloc_apply(ls_plan plan, const lsd::ApplyData<T>& src, const void* 
 
 extern "C" ls_status ls_apply_noalloc(ls_plan plan, const void* u, void* Au, ls_precision prec, void* stream) {
   if (!plan) return LS_ERR_INVALID;
+  if (plan->dim != 2) return fail(plan, LS_ERR_UNSUPPORTED, "ls_apply_noalloc: 2-D plans only");
   if (!u || !Au) return fail(plan, LS_ERR_INVALID, "ls_apply_noalloc: null vector");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (prec == LS_FP64) return noalloc_apply(plan, plan->d64, u, Au, st);
@@ -1968,6 +2263,7 @@ ls_status ls_batch_create(const ls_plan* plans, int n_plans, ls_batch* out) {
   if (!plans || n_plans < 1) return fail(nullptr, LS_ERR_INVALID, "ls_batch_create: no plans");
   for (int i = 0; i < n_plans; ++i) {
     if (!plans[i]) return fail(nullptr, LS_ERR_INVALID, "ls_batch_create: null plan");
+    if (plans[i]->dim != 2) return fail(nullptr, LS_ERR_UNSUPPORTED, "ls_batch_create: 2-D plans only");
     for (int j = 0; j < i; ++j)
       if (plans[j] == plans[i])
         return fail(nullptr, LS_ERR_INVALID, "ls_batch_create: a plan appears twice (instances would share its "

@@ -1,0 +1,307 @@
+// sm_103a kernels of the 3-D apply (Section 5: the Section 3.2 accelerator on
+// cube cells, with a 3-D lattice FFT, plus the stored adjacent part).  One
+// template per arithmetic precision: T = double2 (complex128) or float2
+// (complex64 inner path of mixed precision).
+//
+//   k3_project    sigma_c = P_c u_c                      (two-face equivalent sources)
+//   k3_fill       sigma -> monopole / dipole values on the x1-face planes of the lattice
+//   k3_fft_axis   batched line FFTs along one axis of the M^3 lattice (three per transform)
+//   k3_spectral   V^ = S_m^ G^ + S_d^ D^
+//   k3_local      gamma_c = B^+ V_c - sum_o (B^+ T_o) sigma_{c+o}   (27 neighbours)
+//   k3_near       out_q = u_q + kappa^2 (sum_l W_ql u_l + Phi_q . gamma_c)
+// The complex64 apply runs the projection, the adjacent part and the
+// evaluation in complex64 and the lattice convolution and local coefficients
+// in FP64 (ApplyData3::lattice64 says why).
+#include <cstdint>
+
+#include "cplx.cuh"
+#include "fft.cuh"
+#include "kernels.cuh"
+
+namespace lsd {
+namespace {
+
+constexpr int kT3 = 256;
+
+// sigma_c = P_c u_c: block = occupied cell, thread = output rows i = t, t + 256, ...;
+// the cell's inputs staged in shared memory 256 at a time, P_c read [node][i]
+// (consecutive threads, consecutive entries)
+template <typename T>
+__global__ void __launch_bounds__(kT3) k3_project(ApplyData3<T> d, const T* __restrict__ u) {
+  __shared__ T us[kT3];
+  const int k = blockIdx.x, t = threadIdx.x;
+  const int64_t s0 = d.occ_start[k];
+  const int nc = int(d.occ_start[k + 1] - s0);
+  const T* P = d.P + d.P_off[k];
+  for (int i0 = 0; i0 < d.n_es; i0 += kT3) {
+    const int i = i0 + t;
+    T acc = czero(T());
+    for (int j0 = 0; j0 < nc; j0 += kT3) {
+      const int nj = nc - j0 < kT3 ? nc - j0 : kT3;
+      __syncthreads();
+      if (t < nj) us[t] = u[s0 + j0 + t];
+      __syncthreads();
+      if (i < d.n_es)
+        for (int j = 0; j < nj; ++j) acc = cfma(P[int64_t(j0 + j) * d.n_es + i], us[j], acc);
+    }
+    if (i < d.n_es) d.sigma[int64_t(k) * d.n_es + i] = acc;
+  }
+}
+
+// lattice sources: element (a, b, c) of the M^3 arrays ([a][b][c], c fastest)
+// gathers, in a fixed order, the equivalent sources of every occupied cell
+// that has this lattice point on one of its two x1-faces (up to 2 x 2 x 2
+// cells share a point); zero elsewhere
+template <typename T>
+__global__ void __launch_bounds__(kT3) k3_fill(ApplyData3<T> d) {
+  const int64_t MM = int64_t(d.M) * d.M, total = MM * d.M;
+  const int Ne = d.Ne, L = d.L, nl = L * Ne, nf = (Ne + 1) * (Ne + 1);
+  for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < total; e += int64_t(gridDim.x) * blockDim.x) {
+    const int a = int(e / MM), b = int((e / d.M) % d.M), c = int(e % d.M);
+    T sm = czero(T()), sd = czero(T());
+    if (a <= nl && b <= nl && c <= nl && a % Ne == 0) {
+      const int fa = a / Ne;
+      for (int da = 0; da < 2; ++da) {                 // face x1 = H of cell fa - 1, face x1 = 0 of cell fa
+        const int ci = fa - 1 + da;
+        if (ci < 0 || ci >= L) continue;
+        const int face = 1 - da;
+        for (int db = 0; db < 2; ++db) {
+          const int cj = b / Ne - db;
+          if (cj < 0 || cj >= L || (db == 1 && b % Ne != 0)) continue;
+          for (int dc = 0; dc < 2; ++dc) {
+            const int ck = c / Ne - dc;
+            if (ck < 0 || ck >= L || (dc == 1 && c % Ne != 0)) continue;
+            const int occ = d.occ_of_cell[(ck * L + cj) * L + ci];
+            if (occ < 0) continue;
+            const int lb = b - cj * Ne, lc = c - ck * Ne;
+            const T* sg = d.sigma + int64_t(occ) * d.n_es;
+            const int idx = face * nf + lb * (Ne + 1) + lc;
+            sm = cadd(sm, sg[idx]);
+            sd = cadd(sd, sg[2 * nf + idx]);
+          }
+        }
+      }
+    }
+    d.Sm[e] = sm;
+    d.Sd[e] = sd;
+  }
+}
+
+// line transforms along one axis of an M^3 array; a block takes LPB = 2048 / M
+// lines whose elements are adjacent in memory (consecutive c for the a and b
+// axes, consecutive lines for the c axis), so that loads and stores coalesce;
+// M / 8 threads per line; lines padded to M + 1 in shared memory
+template <typename T>
+__global__ void __launch_bounds__(kT3) k3_fft_axis(T* __restrict__ X, int M, int logM, const T* __restrict__ tw,
+                                                  bool inv, int axis) {
+  extern __shared__ __align__(16) unsigned char raw3[];
+  T* s = reinterpret_cast<T*>(raw3);
+  const int G = M / 8, LPB = kT3 / G, t = threadIdx.x;
+  const int64_t MM = int64_t(M) * M;
+  const int64_t l0 = int64_t(blockIdx.x) * LPB;
+  auto addr = [&](int j, int e) -> int64_t {
+    const int64_t l = l0 + j;
+    if (axis == 2) return l * M + e;
+    if (axis == 1) return (l / M) * MM + (l % M) + int64_t(e) * M;
+    return l + int64_t(e) * MM;
+  };
+  for (int idx = t; idx < LPB * M; idx += kT3) {
+    const int j = axis == 2 ? idx / M : idx % LPB, e = axis == 2 ? idx % M : idx / LPB;
+    s[j * (M + 1) + e] = X[addr(j, e)];
+  }
+  __syncthreads();
+  fft_smem<T>(s + (t / G) * (M + 1), M, logM, inv, tw, t % G);
+  __syncthreads();
+  for (int idx = t; idx < LPB * M; idx += kT3) {
+    const int j = axis == 2 ? idx / M : idx % LPB, e = axis == 2 ? idx % M : idx / LPB;
+    X[addr(j, e)] = s[j * (M + 1) + e];
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kT3) k3_spectral(T* __restrict__ Sm, const T* __restrict__ Sd,
+                                                  const T* __restrict__ Gs, const T* __restrict__ Ds, int64_t n) {
+  for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < n; e += int64_t(gridDim.x) * blockDim.x)
+    Sm[e] = cfma(Sd[e], Ds[e], cmul(Sm[e], Gs[e]));
+}
+
+// gamma_c = LA^T x_c with x_c = [V at the closed cell's (N_eq + 1)^3 lattice
+// points; sigma of the 27 neighbours, offset (oi + 1) 9 + (oj + 1) 3 + (ok + 1),
+// zero where there is none]: block = occupied cell, x_c in shared memory,
+// thread = outputs n = t, t + 256, ...
+template <typename T>
+__global__ void __launch_bounds__(kT3) k3_local(ApplyData3<T> d) {
+  extern __shared__ __align__(16) unsigned char raw3[];
+  T* x = reinterpret_cast<T*>(raw3);
+  const int k = blockIdx.x, t = threadIdx.x, L = d.L, Ne = d.Ne, n1 = Ne + 1;
+  const int cell = d.occ_cells[k], ci = cell % L, cj = (cell / L) % L, ck = cell / (L * L);
+  const int64_t MM = int64_t(d.M) * d.M;
+  for (int p = t; p < d.n_loc; p += kT3) {
+    const int la = p / (n1 * n1), lb = (p / n1) % n1, lc = p % n1;
+    x[p] = d.Sm[int64_t(ci * Ne + la) * MM + int64_t(cj * Ne + lb) * d.M + (ck * Ne + lc)];
+  }
+  for (int p = t; p < 27 * d.n_es; p += kT3) {
+    const int o = p / d.n_es, l = p % d.n_es;
+    const int ni = ci + o / 9 - 1, nj = cj + (o / 3) % 3 - 1, nk = ck + o % 3 - 1;
+    T v = czero(T());
+    if (ni >= 0 && ni < L && nj >= 0 && nj < L && nk >= 0 && nk < L) {
+      const int occ = d.occ_of_cell[(nk * L + nj) * L + ni];
+      if (occ >= 0) v = d.sigma[int64_t(occ) * d.n_es + l];
+    }
+    x[d.n_loc + p] = v;
+  }
+  __syncthreads();
+  const int K = d.n_loc + 27 * d.n_es;
+  for (int n = t; n < d.nb; n += kT3) {
+    T acc = czero(T());
+    for (int j = 0; j < K; ++j) acc = cfma(d.LA[int64_t(j) * d.nb + n], x[j], acc);
+    d.gamma[int64_t(k) * d.nb + n] = acc;
+  }
+}
+
+// warp per row: stored adjacent part (CSR) and the local expansion of the
+// row's cell, then out_q = u_q + kappa^2 (near + far)
+template <typename T>
+__global__ void __launch_bounds__(kT3) k3_near(ApplyData3<T> d, const T* __restrict__ u, T* __restrict__ out) {
+  const int lane = threadIdx.x & 31;
+  const int64_t q = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  if (q >= d.N) return;
+  T acc = czero(T());
+  for (int64_t e = d.rowptr[q] + lane; e < d.rowptr[q + 1]; e += 32) acc = cfma(d.val[e], u[d.col[e]], acc);
+  const T* ph = d.Phi + q * d.nb;
+  const T* g = d.gamma + int64_t(d.occ_of_node[q]) * d.nb;
+  for (int n = lane; n < d.nb; n += 32) acc = cfma(ph[n], g[n], acc);
+  acc = warp_sum(acc);
+  if (lane == 0) {
+    using R = decltype(acc.x);
+    const R k2 = R(d.kappa2);
+    const T uq = u[q];
+    out[q] = mk(uq.x + k2 * acc.x, uq.y + k2 * acc.y);
+  }
+}
+
+__global__ void __launch_bounds__(kT3) k3_farfield(int64_t N, const double* __restrict__ xyz,
+                                                  const double* __restrict__ ffw, const double2* __restrict__ u,
+                                                  int nrhs, const double* __restrict__ dirs, int ndir, double kappa,
+                                                  double2 c, double2* __restrict__ A) {
+  // block = (direction, right-hand side); threads stride over the nodes
+  const int dd = blockIdx.x % ndir, r = blockIdx.x / ndir;
+  const double dx = dirs[3 * dd], dy = dirs[3 * dd + 1], dz = dirs[3 * dd + 2];
+  double2 acc = make_double2(0, 0);
+  for (int64_t q = threadIdx.x; q < N; q += blockDim.x) {
+    double sn, cs;
+    sincos(-kappa * (dx * xyz[3 * q] + dy * xyz[3 * q + 1] + dz * xyz[3 * q + 2]), &sn, &cs);
+    const double2 v = u[int64_t(r) * N + q];
+    acc = cfma(make_double2(ffw[q] * cs, ffw[q] * sn), v, acc);
+  }
+  __shared__ double2 red[kT3 / 32];
+  acc = warp_sum(acc);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double2 s = make_double2(0, 0);
+    for (int w = 0; w < kT3 / 32; ++w) s = cadd(s, red[w]);
+    A[int64_t(r) * ndir + dd] = cmul(c, s);
+  }
+}
+
+// complex64 <-> complex128 copies of the strengths and coefficients
+__global__ void __launch_bounds__(kT3) k3_widen(const float2* __restrict__ a, double2* __restrict__ b, int64_t n) {
+  for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < n; e += int64_t(gridDim.x) * blockDim.x)
+    b[e] = make_double2(a[e].x, a[e].y);
+}
+__global__ void __launch_bounds__(kT3) k3_narrow(const double2* __restrict__ a, float2* __restrict__ b, int64_t n) {
+  for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < n; e += int64_t(gridDim.x) * blockDim.x)
+    b[e] = make_float2(float(a[e].x), float(a[e].y));
+}
+
+int grid_for(int64_t n) {
+  const int64_t b = (n + kT3 - 1) / kT3;
+  return int(b < 152 * 16 ? b : 152 * 16);
+}
+
+// lattice convolution and local coefficients: sigma -> gamma on one precision's data
+template <typename T>
+cudaError_t lattice_local(const ApplyData3<T>& d, cudaStream_t st) {
+  const int64_t n3 = int64_t(d.M) * d.M * d.M;
+  k3_fill<T><<<grid_for(n3), kT3, 0, st>>>(d);
+  cudaError_t e = fft3d<T>(d.Sm, d.M, d.logM, d.tw, false, st);
+  if (e == cudaSuccess) e = fft3d<T>(d.Sd, d.M, d.logM, d.tw, false, st);
+  if (e != cudaSuccess) return e;
+  k3_spectral<T><<<grid_for(n3), kT3, 0, st>>>(d.Sm, d.Sd, d.Gs, d.Ds, n3);
+  e = fft3d<T>(d.Sm, d.M, d.logM, d.tw, true, st);
+  if (e != cudaSuccess) return e;
+  const size_t sm_local = sizeof(T) * size_t(d.n_loc + 27 * d.n_es);
+  k3_local<T><<<d.nocc, kT3, sm_local, st>>>(d);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t apply3_one(const ApplyData3<T>& d, const T* u, T* out, cudaStream_t st) {
+  k3_project<T><<<d.nocc, kT3, 0, st>>>(d, u);
+  cudaError_t e;
+  if constexpr (sizeof(T) == 8) {
+    // complex64: the strengths widened to FP64 for the lattice and the local
+    // step (ApplyData3::lattice64), the coefficients narrowed back
+    const ApplyData3<double2>& w = *d.lattice64;
+    const int64_t ns = int64_t(d.nocc) * d.n_es, ng = int64_t(d.nocc) * d.nb;
+    k3_widen<<<grid_for(ns), kT3, 0, st>>>(d.sigma, w.sigma, ns);
+    e = lattice_local(w, st);
+    if (e != cudaSuccess) return e;
+    k3_narrow<<<grid_for(ng), kT3, 0, st>>>(w.gamma, d.gamma, ng);
+  } else {
+    e = lattice_local(d, st);
+    if (e != cudaSuccess) return e;
+  }
+  k3_near<T><<<int((d.N * 32 + kT3 - 1) / kT3), kT3, 0, st>>>(d, u, out);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t fft3d(T* x, int M, int logM, const T* tw, bool inverse, cudaStream_t st) {
+  if (M < 16 || M > 2048 || (M & (M - 1))) return cudaErrorInvalidValue;
+  const int LPB = kT3 / (M / 8);
+  const int64_t lines = int64_t(M) * M;
+  const size_t smem = sizeof(T) * size_t(LPB) * (M + 1);
+  static unsigned long long attr = 0;
+  if (first_on_device(attr)) {
+    const cudaError_t e = cudaFuncSetAttribute(k3_fft_axis<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
+    if (e != cudaSuccess) return e;
+  }
+  for (int axis = 2; axis >= 0; --axis)
+    k3_fft_axis<T><<<int(lines / LPB), kT3, smem, st>>>(x, M, logM, tw, inverse, axis);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t apply3_batch(const ApplyData3<T>& d, const T* u, T* out, int nr, cudaStream_t st) {
+  static unsigned long long attr = 0;
+  if (first_on_device(attr)) {
+    const cudaError_t e =
+        cudaFuncSetAttribute(k3_local<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    if (e != cudaSuccess) return e;
+  }
+  if (sizeof(double2) * size_t(d.n_loc + 27 * d.n_es) > 227 * 1024) return cudaErrorInvalidValue;
+  if (sizeof(T) == 8 && !d.lattice64) return cudaErrorInvalidValue;
+  for (int r = 0; r < nr; ++r) {
+    const cudaError_t e = apply3_one(d, u + int64_t(r) * d.N, out + int64_t(r) * d.N, st);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t farfield3(int64_t N, const double* xyz, const double* ffw, const double2* u, int nrhs,
+                      const double* dirs, int ndir, double kappa, double2 c, double2* A, cudaStream_t st) {
+  if (ndir <= 0 || nrhs <= 0) return cudaSuccess;
+  k3_farfield<<<ndir * nrhs, kT3, 0, st>>>(N, xyz, ffw, u, nrhs, dirs, ndir, kappa, c, A);
+  return cudaGetLastError();
+}
+
+template cudaError_t fft3d<double2>(double2*, int, int, const double2*, bool, cudaStream_t);
+template cudaError_t fft3d<float2>(float2*, int, int, const float2*, bool, cudaStream_t);
+template cudaError_t apply3_batch<double2>(const ApplyData3<double2>&, const double2*, double2*, int, cudaStream_t);
+template cudaError_t apply3_batch<float2>(const ApplyData3<float2>&, const float2*, float2*, int, cudaStream_t);
+
+}  // namespace lsd

@@ -53,6 +53,8 @@ struct ApplyData {
   int n_items32 = 0;
   const int2* items128 = nullptr;       // 128-row items (tensor-core near field, 8 or 16 complex64 RHS)
   int n_items128 = 0;
+  const int64_t* tile_off = nullptr;    // complex64 only: offset of each 128-row item in Wt
+  const T* Wt = nullptr;                // complex64 only: the blocks in the tensor-core tile layout
   int* tc_err = nullptr;                // set by the tensor-core near field when a wait times out
   int tc_spin = 1 << 22;                // polls of each mbarrier wait before it gives up
   const T* Wb = nullptr;                // blocks, row-major per cell
@@ -97,6 +99,59 @@ constexpr int kProjPiece = 128;    // nodes per projection block at most
 // the CUDA-core kernel up to FP32 rounding.
 template <int R>
 cudaError_t near_eval_tc(const ApplyData<float2>& d, const float2* u, float2* out, cudaStream_t st);
+// Elements (complex64) of one 128-row item of nrow rows and nblk padded columns
+// in the tile layout of the tensor-core near field, and the plan-time kernel
+// that writes that layout (d.items128, d.tile_off, d.Wb set) into Wt.
+int64_t tc_tile_elems(int nrow, int nblk);
+cudaError_t tile_weights(const ApplyData<float2>& d, float2* Wt, cudaStream_t st);
+
+// Device-resident pieces of a 3-D plan (Section 5: ball, cube cells of side H,
+// L per axis) for one arithmetic precision.  Vectors are in the plan's node
+// order (grouped by cell).
+template <typename T>
+struct ApplyData3 {
+  int64_t N = 0;
+  int nocc = 0, L = 0, Ne = 0, n_es = 0, n_loc = 0, nb = 0, M = 0, logM = 0;
+  const int64_t* occ_start = nullptr;   // nocc + 1: node range of each occupied cell
+  const int* occ_cells = nullptr;       // nocc: cell id (k L + j) L + i
+  const int* occ_of_cell = nullptr;     // L^3: occupied index or -1
+  const int* occ_of_node = nullptr;     // N: occupied index of the node's cell
+  const int64_t* P_off = nullptr;       // nocc + 1: element offset of each cell's projection
+  const T* P = nullptr;                 // P_c stored [node][n_es] (w omega m folded in)
+  const T* LA = nullptr;                // [n_loc + 27 n_es][nb]: B^+ transposed, then -(B^+ T_o) transposed
+  const T* Phi = nullptr;               // N x nb: local basis at each node about its cell centre
+  const T* Gs = nullptr;                // M^3 spectra of the G and dG/dz_1 lattice tables, / M^3
+  const T* Ds = nullptr;
+  const T* tw = nullptr;                // M twiddles exp(-2 pi i m / M)
+  const int64_t* rowptr = nullptr;      // adjacent part: CSR over the nodes (contrast folded into val)
+  const int* col = nullptr;
+  const T* val = nullptr;
+  double kappa2 = 0;
+  // work space (one right-hand side)
+  T* sigma = nullptr;                   // nocc x n_es
+  T* Sm = nullptr;                      // M^3: monopole lattice, then the lattice field V
+  T* Sd = nullptr;                      // M^3: dipole lattice
+  T* gamma = nullptr;                   // nocc x nb
+  // complex64 only (host pointer): the FP64 data whose lattice convolution and
+  // local coefficients the complex64 apply uses.  On a cell's own lattice
+  // points the 27 neighbours' fields dominate and cancel in the neighbour
+  // subtraction; complex64 rounding of the lattice field would be magnified
+  // by that cancellation and by the ill-conditioned local fit.
+  const ApplyData3<double2>* lattice64 = nullptr;
+};
+
+// out = A u for nr right-hand sides of a 3-D plan (one after another through
+// the same work space; u, out: nr vectors of length N).
+template <typename T>
+cudaError_t apply3_batch(const ApplyData3<T>& d, const T* u, T* out, int nr, cudaStream_t st);
+// 3-D FFT of an M x M x M array in place ([a][b][c], c contiguous), forward or
+// inverse (unscaled): three passes of batched line transforms.
+template <typename T>
+cudaError_t fft3d(T* x, int M, int logM, const T* tw, bool inverse, cudaStream_t st);
+// Far-field pattern of a 3-D plan's solution: A[r][d] = c sum_q ffw_q u_r[q]
+// exp(-i kappa dir_d . x_q) (dirs: ndir x 3 unit vectors, device).
+cudaError_t farfield3(int64_t N, const double* xyz, const double* ffw, const double2* u, int nrhs,
+                      const double* dirs, int ndir, double kappa, double2 c, double2* A, cudaStream_t st);
 
 // One scatterer of a multi-instance batch: its apply data and the offset of
 // its nodes in the batch's concatenated vectors.
@@ -173,5 +228,10 @@ cudaError_t farfield(int64_t N, const double* x, const double* y, const double* 
                      double2 c, double2* A, cudaStream_t st);
 
 int gram_blocks(int64_t N);
+
+// Measured throughput of this GPU (device/peaks.cu): FP64 FMA on the CUDA
+// cores and TF32 tcgen05 MMA (M = 128, N = 256), in TFLOP/s (2 per FMA);
+// tf32 is -1 if a wait of the MMA probe gave up.
+cudaError_t measure_peaks(double* fp64_tflops, double* tf32_tflops);
 
 }  // namespace lsd

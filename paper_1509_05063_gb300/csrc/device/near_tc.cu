@@ -1,42 +1,49 @@
 // Near-field correction + evaluation + assembly for R complex64 right-hand
 // sides on the 5th-generation tensor cores (tcgen05, sm_103a).
 //
-// Per work item = (occupied cell, 128 target rows) the near sum is one dense
-// product  W_c (rows x nblk complex) . U (nblk x R complex)  against the cell's
-// 3 x 3 neighbourhood (Eq. VolInt-Adj-NonAdj-I with the precomputed weights).
-// It is written as one real GEMM with the weights as A, read from HBM exactly
-// once in their stored layout (interleaved re, im along K):
-//   A[m][2c] = Re W[m][c],  A[m][2c+1] = Im W[m][c]                (128 x 2 nblk)
-//   B[2c][j] = Re u_j[c],   B[2c+1][j] = -Im u_j[c]      (j < R: real parts)
+// Per work item = (occupied cell, up to 128 target rows) the near sum is one
+// dense product  W_c (rows x nblk complex) . U (nblk x R complex)  against the
+// cell's 3 x 3 neighbourhood (Eq. VolInt-Adj-NonAdj-I with the precomputed
+// weights), written as one real GEMM with the weights as A (interleaved re, im
+// along K):
+//   A[m][2c] = Re W[m][c],  A[m][2c+1] = Im W[m][c]
+//   B[2c][j] = Re u_j[c],   B[2c+1][j] = -Im u_j[c]      (columns j < R: real parts)
 //   B[2c][R+j] = Im u_j[c], B[2c+1][R+j] = Re u_j[c]      (imaginary parts)
 // so that D = A B holds Re(W u_j) in column j and Im(W u_j) in column R + j.
 // FP32 accuracy from TF32 inputs (3xTF32): with x = hi(x) + lo(x), hi the TF32
-// truncation (which is what the tensor core reads from an FP32 word) and lo
-// exact in FP32,
-//   D = A_hi B_hi + A_lo B_hi + A_hi B_lo  (the lo.lo term, 2^-22 relative, is dropped)
-// done with N = 4R columns: the K range is doubled, [A | A_lo] against
-// [[B_hi, B_lo]; [B_hi, 0]], and the two column halves are added in the
-// epilogue.  The four K steps of a chunk accumulate into four separate
-// tensor-memory accumulators, so that consecutive MMAs do not wait on one
-// another's result; the epilogue sums them.
+// truncation (what the tensor core reads from an FP32 word) and lo exact in
+// FP32,
+//   D = A_hi B_hi + A_hi B_lo + A_lo B_hi   (the lo.lo term, 2^-22 relative, is dropped)
+// as two MMAs per K step into one accumulator: A against [B_hi | B_lo]
+// (N = 4R columns) and A_lo against B_hi (N = 2R, accumulating into the first
+// 2R columns); the epilogue adds the two column halves.
 //
-// Pipeline (warp-specialised: 128 producer threads, thread t = row t of the
-// tile, plus one MMA warp; chunks of 8 complex columns): every producer keeps
-// the next kTcAhead chunks of its row (and one input value u_j[column]) in
-// flight in registers; for chunk c it waits until the MMAs of chunk
-// c - kTcStages have released the stage, writes the raw weights and their lo
-// parts into the stage in the canonical K-major no-swizzle layout (8-row x
-// 16-byte core matrices; LBO = 128 B between K-adjacent core matrices,
-// SBO = 1024 B between row groups), builds its B entries from the input
-// values and arrives on the stage's "full" mbarrier.  Lane 0 of the MMA warp
-// waits for "full", issues the chunk's four tcgen05.mma (M = 128, N = 4R,
-// K = 8) and commits them to the stage's "empty" mbarrier.  No block barrier
-// inside the loop.  The accumulators live in tensor memory and are read back
-// with tcgen05.ld; the epilogue adds the CSR remainder and the local expansion
-// Phi_q . gamma_c and writes out_q = u_q + kappa^2 (near + far).
-// Every wait is bounded: on time-out a thread leaves its loop and flags the
-// block, which then sets *err, lets its MMAs in flight finish (bounded), frees
-// its tensor memory and leaves its rows unwritten.
+// The weights are stored for this kernel in its own tile layout (built once at
+// plan time from the row-major blocks): per work item and chunk of kKC complex
+// columns, the item's rows in groups of 8 as the canonical K-major no-swizzle
+// core-matrix layout (8 rows x 16 bytes per core matrix, 128 bytes between
+// K-adjacent core matrices, 1024 bytes between row groups), only the row groups
+// that hold rows.  One bulk copy (cp.async.bulk, completion counted on an
+// mbarrier) moves a chunk from HBM into shared memory: no registers, no
+// per-thread loads on the weight stream.
+//
+// Persistent, warp-specialised, one block per SM walking the work items
+// blockIdx.x, blockIdx.x + gridDim.x, ... (heaviest first):
+//   warp 0      lane 0 issues the bulk copies into a ring of kNA weight stages;
+//   warp 1      lane 0 issues the MMAs and commits them to the release barriers;
+//   warps 2..5  (128 threads) per chunk: the lo part of the weights, into a
+//               ring of kNC operand slots;
+//   warps 10..  one warp per operand slot: the B operand (hi and lo) of the
+//               chunks that use its slot, from the input vectors;
+//   warps 6..9  (128 threads) per item: read the accumulator from tensor memory
+//               (two accumulators, so the epilogue of one item overlaps the MMAs
+//               of the next), add the CSR remainder and the local expansion
+//               Phi_q . gamma_c and write out_q = u_q + kappa^2 (near + far).
+// Every wait is bounded by `spin` polls and also gives up once another role
+// has flagged a failure; then the block sets *err, waits (with a fixed bound
+// that does not depend on `spin`) for its own MMAs and bulk copies still in
+// flight, frees its tensor memory and returns, leaving its rows unwritten.
+#include <algorithm>
 #include <cstdint>
 
 #include "device/cplx.cuh"
@@ -45,13 +52,16 @@
 namespace lsd {
 namespace {
 
-constexpr int kTcRows = 128;          // rows per tile = MMA M = producer threads
-constexpr int kTcThreads = kTcRows + 32;   // + one warp whose lane 0 issues the MMAs
-constexpr int kTcKC = 8;              // complex columns per chunk
-constexpr int kTcStages = 3;          // shared-memory stages (operand tiles of the MMAs in flight)
-constexpr int kTcAhead = 4;           // chunks held in registers ahead of the one being prepared
-constexpr int kTcKgroups = 2 * kTcKC / 2;  // 16-byte core-matrix columns per row: 4 raw + 4 lo
-constexpr int kTcSBO = kTcKgroups * 128;   // bytes between 8-row groups (A and B)
+constexpr int kTcRows = 128;                 // rows per item = MMA M
+constexpr int kKC = 16;                      // complex columns per chunk (K = 32 real)
+constexpr int kKG = 2 * kKC / 4;             // 16-byte core-matrix columns per row: 8
+constexpr int kRowGroup = 8 * kKG * 16;      // bytes of one 8-row group of a chunk: 1024
+constexpr int kAChunk = 16 * kRowGroup;      // 128 rows: 16 KB
+constexpr int kNA = 9;                       // weight stages (bulk-copy ring)
+constexpr int kNC = 3;                       // operand slots (lo weights + B)
+constexpr int kSets = 2;                     // accumulator sets per item (alternate K steps)
+constexpr int kThreads = 32 * (10 + kNC);    // + one B-operand warp per operand slot
+constexpr int kDrainPolls = 1 << 28;         // bound of the final waits on the block's own MMAs / copies
 
 __device__ __forceinline__ uint32_t s_u32(const void* p) { return uint32_t(__cvta_generic_to_shared(p)); }
 
@@ -64,106 +74,149 @@ __device__ __forceinline__ uint64_t s_desc(uint32_t addr, uint32_t lbo, uint32_t
 // x - (x with the 13 low mantissa bits cleared): exact in FP32
 __device__ __forceinline__ float lo_tf32(float x) { return x - __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
 
-// poll an mbarrier phase at most `limit` times
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int limit) {
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(done)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+
+__device__ __forceinline__ int ld_flag(const int* f) {
+  int v;
+  asm volatile("ld.volatile.shared.b32 %0, [%1];" : "=r"(v) : "r"(s_u32(f)) : "memory");
+  return v;
+}
+
+// wait for a phase: at most `limit` polls, and give up as soon as the block's
+// failure flag is set; on time-out the flag is set
+__device__ __forceinline__ bool wait_phase(uint32_t bar, uint32_t parity, int limit, int* flag) {
   for (int it = 0; it < limit; ++it) {
-    uint32_t done;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(done)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    if (done) return true;
+    if (mbar_try(bar, parity)) return true;
+    if (ld_flag(flag)) return false;
   }
+  asm volatile("st.volatile.shared.b32 [%0], %1;" :: "r"(s_u32(flag)), "r"(1) : "memory");
   return false;
 }
 
+// the same with a fixed bound and no flag (the block's own MMAs and copies,
+// which depend on nothing else)
+__device__ __forceinline__ bool drain_phase(uint32_t bar, uint32_t parity) {
+  for (int it = 0; it < kDrainPolls; ++it)
+    if (mbar_try(bar, parity)) return true;
+  return false;
+}
+
+// 16 consecutive accumulator columns of this thread's lane; the load and its
+// wait are one asm statement, so no register is read before the data is there
 __device__ __forceinline__ void tmem_load16(uint32_t taddr, float* d) {
   uint32_t r[16];
   asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+      "tcgen05.wait::ld.sync.aligned;\n"
       : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
         "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      : "r"(taddr)
+      : "memory");
 #pragma unroll
   for (int i = 0; i < 16; ++i) d[i] = __uint_as_float(r[i]);
 }
 
 template <int R>
 struct TcLayout {
-  static constexpr int NN = 4 * R;                                 // MMA N
-  static constexpr int kA = kTcRows * kTcKgroups * 16;             // 16 KB: 128 rows x 32 fp32
-  static constexpr int kB = NN * kTcKgroups * 16;                  // NN rows x 32 fp32
-  static constexpr int kStage = kA + kB;
-  // independent accumulators (MMA chains): the four K steps of a chunk, times
-  // two sets used by alternate chunks where tensor memory allows
-  static constexpr int kSets = R >= 16 ? 1 : 2;
-  static constexpr int kAcc = 4 * kSets;
-  static constexpr int kTmemCols = kAcc * NN < 32 ? 32 : kAcc * NN;  // power of two >= 32
-  // at most 512 / kTmemCols blocks may share an SM's tensor memory: pad the
-  // shared memory so that no more blocks fit
-  static constexpr int kBlocksMax = 512 / kTmemCols;
-  static constexpr int kRaw = kTcStages * kStage + 128;            // + mbarriers, tensor-memory address, flag
-  static constexpr int kFloor = 232448 / (kBlocksMax + 1) + 1;     // 227 KB / (max + 1)
-  static constexpr int kBytes = kRaw > kFloor ? kRaw : kFloor;
+  static constexpr int NN = 4 * R;                              // MMA N of [B_hi | B_lo]
+  static constexpr int kB = NN * kKG * 16;                      // B operand of a chunk
+  static constexpr int kSlot = kAChunk + kB;                    // lo weights + B
+  // two items in flight x two accumulator sets (alternate K steps feed
+  // alternate sets, so consecutive MMAs do not chain on one accumulator)
+  static constexpr int kTmemCols = 2 * kSets * NN < 32 ? 32 : 2 * kSets * NN;
+  static constexpr int kBarOff = kNA * kAChunk + kNC * kSlot;
+  static constexpr int kBytes = kBarOff + 320;                  // + mbarriers, tensor-memory address, flag
 };
 
 // write (v.x, v.y) at B[n][kq], B[n][kq + 1] (kq even)
 __device__ __forceinline__ void put_b(unsigned char* B, int n, int kq, float2 v) {
-  *reinterpret_cast<float2*>(B + (n >> 3) * kTcSBO + (kq >> 2) * 128 + (n & 7) * 16 + (kq & 3) * 4) = v;
+  *reinterpret_cast<float2*>(B + (n >> 3) * kRowGroup + (kq >> 2) * 128 + (n & 7) * 16 + (kq & 3) * 4) = v;
+}
+
+struct ItemGeom {
+  int k, row0, nrow, nblk, nchunk, groups;
+  int64_t off;   // float2 offset of the item's first chunk in the tile layout
+};
+
+__device__ __forceinline__ ItemGeom item_geom(int it, const int2* items, const int64_t* tile_off,
+                                              const int64_t* occ_start, const int* blk_seg) {
+  const int2 item = items[it];
+  ItemGeom g;
+  g.k = item.x;
+  g.row0 = item.y;
+  const int* sg = blk_seg + 6 * g.k;
+  g.nblk = ((sg[1] + 1) & ~1) + ((sg[3] + 1) & ~1) + ((sg[5] + 1) & ~1);
+  g.nchunk = (g.nblk + kKC - 1) / kKC;
+  const int rows = int(occ_start[g.k + 1] - occ_start[g.k]) - g.row0;
+  g.nrow = rows < kTcRows ? rows : kTcRows;
+  g.groups = (g.nrow + 7) >> 3;
+  g.off = tile_off[it];
+  return g;
 }
 
 template <int R>
-__global__ void __launch_bounds__(kTcThreads) k_near_tc(const int2* __restrict__ items,
-                                                        const int64_t* __restrict__ occ_start,
-                                                        const int64_t* __restrict__ blk_off,
-                                                        const int* __restrict__ blk_seg,
-                                                        const float2* __restrict__ Wb,
-                                                        const int64_t* __restrict__ rem_row,
-                                                        const int* __restrict__ rem_col,
-                                                        const float2* __restrict__ rem_val,
-                                                        const float2* __restrict__ u, int64_t N,
-                                                        const float2* __restrict__ Phi,
-                                                        const float2* __restrict__ gamma, int nocc, int nfb2,
-                                                        float kappa2, float2* __restrict__ out,
-                                                        int* __restrict__ err, int spin) {
+__global__ void __launch_bounds__(kThreads, 1) k_near_tc(const int2* __restrict__ items, int n_items,
+                                                         const int64_t* __restrict__ tile_off,
+                                                         const int64_t* __restrict__ occ_start,
+                                                         const int* __restrict__ blk_seg,
+                                                         const float2* __restrict__ Wt,
+                                                         const int64_t* __restrict__ rem_row,
+                                                         const int* __restrict__ rem_col,
+                                                         const float2* __restrict__ rem_val,
+                                                         const float2* __restrict__ u, int64_t N,
+                                                         const float2* __restrict__ Phi,
+                                                         const float2* __restrict__ gamma, int nocc, int nfb2,
+                                                         float kappa2, float2* __restrict__ out,
+                                                         int* __restrict__ err, int spin) {
   using Lay = TcLayout<R>;
   constexpr int NN = Lay::NN;
-  static_assert(R * kTcKC <= kTcRows, "one input value per thread and chunk");
   extern __shared__ __align__(1024) unsigned char sm[];
-  uint64_t* full = reinterpret_cast<uint64_t*>(sm + kTcStages * Lay::kStage);     // stage written (128 arrivals)
-  uint64_t* empty = full + kTcStages;                                             // stage read by the MMAs
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + kTcStages * Lay::kStage + 64);
-  int* sflag = reinterpret_cast<int*>(sm + kTcStages * Lay::kStage + 72);
+  unsigned char* Aring = sm;                                  // kNA x 16 KB raw weights
+  unsigned char* Cring = sm + kNA * kAChunk;                  // kNC x (16 KB lo weights + B)
+  uint64_t* a_full = reinterpret_cast<uint64_t*>(sm + Lay::kBarOff);
+  uint64_t* a_empty = a_full + kNA;
+  uint64_t* c_ready = a_empty + kNA;                          // lo parts written (128 arrivals)
+  uint64_t* b_ready = c_ready + kNC;                          // B operand written (32 arrivals)
+  uint64_t* c_empty = b_ready + kNC;
+  uint64_t* acc_full = c_empty + kNC;
+  uint64_t* acc_empty = acc_full + 2;
+  uint64_t* drain = acc_empty + 2;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(drain + 1);
+  int* sflag = reinterpret_cast<int*>(tslot + 1);
 
-  const int t = threadIdx.x, warp = t >> 5;
-  const bool producer = t < kTcRows;
-  const int2 item = items[blockIdx.x];
-  const int k = item.x;
-  const int* sg = blk_seg + 6 * k;
-  const int l0 = sg[1], l1 = sg[3], l2 = sg[5];
-  const int p0 = (l0 + 1) & ~1, p1 = (l1 + 1) & ~1;
-  const int nblk = p0 + p1 + ((l2 + 1) & ~1);
-  const int64_t r0 = occ_start[k];
-  const int nrow = int(occ_start[k + 1] - r0);
-  const int row = item.y + t;
-  const bool valid = producer && row < nrow;
-  const float2* wrow = Wb + blk_off[k] + int64_t(valid ? row : item.y) * nblk;
-  const int nchunk = (nblk + kTcKC - 1) / kTcKC;
-  // input value of this thread: RHS j, column cc of every chunk
-  const int uj = t % R, ucc = t / R;
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
                  :: "r"(s_u32(tslot)), "r"(Lay::kTmemCols) : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
-  if (t == 0) {
-    for (int s = 0; s < kTcStages; ++s) {
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(s_u32(&full[s])), "r"(kTcRows) : "memory");
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(s_u32(&empty[s])), "r"(1) : "memory");
+  if (t == 32) {
+    for (int s = 0; s < kNA; ++s) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(s_u32(&a_full[s])) : "memory");
+      // released by the commit of the chunk's first MMAs (the only ones that read
+      // the raw weights) and by the 128 lo-part threads once they have read them
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 129;" :: "r"(s_u32(&a_empty[s])) : "memory");
     }
+    for (int s = 0; s < kNC; ++s) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 128;" :: "r"(s_u32(&c_ready[s])) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 32;" :: "r"(s_u32(&b_ready[s])) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(s_u32(&c_empty[s])) : "memory");
+    }
+    for (int s = 0; s < 2; ++s) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(s_u32(&acc_full[s])) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 128;" :: "r"(s_u32(&acc_empty[s])) : "memory");
+    }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(s_u32(drain)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     *sflag = 0;
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -171,183 +224,319 @@ __global__ void __launch_bounds__(kTcThreads) k_near_tc(const int2* __restrict__
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tslot;
 
-  if (producer) {
-    // chunk c of this thread: its row's 8 complex weights (4 x 16 B) and, for
-    // the first R * kTcKC threads, one input value u_j[column]; zero outside
-    auto load = [&](int c, float4 (&w)[kTcKC / 2], float2& uv) {
-      const int c0 = c * kTcKC;
-#pragma unroll
-      for (int p = 0; p < kTcKC / 2; ++p) {
-        const int col = c0 + 2 * p;
-        w[p] = (valid && col < nblk) ? __ldcs(reinterpret_cast<const float4*>(wrow + col))
-                                     : make_float4(0.f, 0.f, 0.f, 0.f);
+  if (warp == 0) {
+    // ------------------------------------------------ bulk copies of the weight chunks
+    if (lane == 0) {
+      int g = 0;   // chunk counter of this block
+      bool live = true;
+      for (int it = blockIdx.x; it < n_items && live; it += gridDim.x) {
+        const ItemGeom ig = item_geom(it, items, tile_off, occ_start, blk_seg);
+        const uint32_t bytes = uint32_t(ig.groups) * kRowGroup;
+        for (int c = 0; c < ig.nchunk; ++c, ++g) {
+          const int s = g % kNA, use = g / kNA;
+          if (use > 0 && !wait_phase(s_u32(&a_empty[s]), (use - 1) & 1, spin, sflag)) {
+            live = false;
+            break;
+          }
+          const float2* src = Wt + ig.off + int64_t(c) * ig.groups * (kRowGroup / 8);
+          asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+                       :: "r"(s_u32(&a_full[s])), "r"(bytes) : "memory");
+          asm volatile(
+              "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+              :: "r"(s_u32(Aring + s * kAChunk)), "l"(src), "r"(bytes), "r"(s_u32(&a_full[s]))
+              : "memory");
+        }
       }
-      uv = make_float2(0.f, 0.f);
-      if (t < R * kTcKC) {
-        const int col = c0 + ucc;
-        int64_t node = -1;
-        if (col < p0) { if (col < l0) node = sg[0] + col; }
-        else if (col < p0 + p1) { const int o = col - p0; if (o < l1) node = sg[2] + o; }
-        else if (col < nblk) { const int o = col - p0 - p1; if (o < l2) node = sg[4] + o; }
-        if (node >= 0) uv = u[int64_t(uj) * N + node];
+      // every copy issued must have landed before the block leaves (shared
+      // memory is written by them): wait for the last phase of each stage
+      const int issued = g;
+      for (int s = 0; s < kNA && s < issued; ++s) {
+        const int last_use = (issued - 1 - s) / kNA;
+        if (!drain_phase(s_u32(&a_full[s]), last_use & 1))
+          asm volatile("st.volatile.shared.b32 [%0], %1;" :: "r"(s_u32(sflag)), "r"(2) : "memory");
       }
-    };
-    // register ring of the next kTcAhead chunks (loads in flight while earlier chunks are written)
-    float4 wbuf[kTcAhead][kTcKC / 2];
-    float2 ubuf[kTcAhead];
-#pragma unroll
-    for (int q = 0; q < kTcAhead; ++q)
-      if (q < nchunk) load(q, wbuf[q], ubuf[q]);
-    bool live = true;
-    for (int cb = 0; cb < nchunk && live; cb += kTcAhead) {
-#pragma unroll
-      for (int q = 0; q < kTcAhead; ++q) {
-        const int c = cb + q;
-        if (c >= nchunk) break;
-        const int s = c % kTcStages;
-        // stage s was last read by the MMAs of chunk c - kTcStages
-        if (c >= kTcStages && !mbar_wait(s_u32(&empty[s]), ((c - kTcStages) / kTcStages) & 1, spin)) {
-          *sflag = 1;
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------ MMA issue
+    if (lane == 0) {
+      const uint32_t idesc1 =
+          (1u << 4) | (2u << 7) | (2u << 10) | (uint32_t(NN >> 3) << 17) | (uint32_t(kTcRows >> 4) << 24);
+      const uint32_t idesc2 =
+          (1u << 4) | (2u << 7) | (2u << 10) | (uint32_t((NN / 2) >> 3) << 17) | (uint32_t(kTcRows >> 4) << 24);
+      int g = 0, tile = 0;
+      bool live = true, issued = false;
+      for (int it = blockIdx.x; it < n_items && live; it += gridDim.x, ++tile) {
+        const ItemGeom ig = item_geom(it, items, tile_off, occ_start, blk_seg);
+        const int b = tile & 1, bu = tile >> 1;
+        if (bu > 0 && !wait_phase(s_u32(&acc_empty[b]), (bu - 1) & 1, spin, sflag)) {
           live = false;
           break;
         }
-        unsigned char* A = sm + s * Lay::kStage;
-        unsigned char* B = A + Lay::kA;
-        // raw weights -> k-groups 0..3 of row t, their lo parts -> k-groups 4..7
+        const uint32_t acc0 = tmem + uint32_t(kSets * b * NN);
+        for (int c = 0; c < ig.nchunk; ++c, ++g) {
+          const int sa = g % kNA, sc = g % kNC;
+          // A x [B_hi | B_lo] as soon as the weights and B are there, A_lo x B_hi
+          // once the lo parts are written
+          if (!wait_phase(s_u32(&b_ready[sc]), (g / kNC) & 1, spin, sflag) ||
+              !wait_phase(s_u32(&a_full[sa]), (g / kNA) & 1, spin, sflag)) {
+            live = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t a0 = s_u32(Aring + sa * kAChunk);
+          const uint32_t l0 = s_u32(Cring + sc * Lay::kSlot), b0 = l0 + kAChunk;
 #pragma unroll
-        for (int p = 0; p < kTcKC / 2; ++p) {
-          const float4 x = wbuf[q][p];
-          *reinterpret_cast<float4*>(A + (t >> 3) * kTcSBO + p * 128 + (t & 7) * 16) = x;
-          *reinterpret_cast<float4*>(A + (t >> 3) * kTcSBO + (4 + p) * 128 + (t & 7) * 16) =
-              make_float4(lo_tf32(x.x), lo_tf32(x.y), lo_tf32(x.z), lo_tf32(x.w));
+          for (int i = 0; i < kKG / 2; ++i) {      // K = 8 per MMA: core-matrix columns 2i, 2i + 1
+            const uint64_t da = s_desc(a0 + 2 * i * 128, 128, kRowGroup);
+            const uint64_t db = s_desc(b0 + 2 * i * 128, 128, kRowGroup);
+            const uint32_t acc = acc0 + uint32_t((i % kSets) * NN);
+            const uint32_t accum = (c > 0 || i >= kSets) ? 1u : 0u;
+            asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                         " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n"
+                         :: "r"(acc), "l"(da), "l"(db), "r"(idesc1), "r"(accum) : "memory");
+          }
+          issued = true;
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                       :: "r"(s_u32(&a_empty[sa])) : "memory");
+          if (!wait_phase(s_u32(&c_ready[sc]), (g / kNC) & 1, spin, sflag)) {
+            live = false;
+            issued = true;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+          for (int i = 0; i < kKG / 2; ++i) {
+            const uint64_t dl = s_desc(l0 + 2 * i * 128, 128, kRowGroup);
+            const uint64_t db = s_desc(b0 + 2 * i * 128, 128, kRowGroup);
+            const uint32_t acc = acc0 + uint32_t((i % kSets) * NN);
+            asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                         " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n"
+                         :: "r"(acc), "l"(dl), "l"(db), "r"(idesc2), "r"(1u) : "memory");
+          }
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                       :: "r"(s_u32(&c_empty[sc])) : "memory");
         }
-        // B rows of chunk c: thread (cc, j) for complex column cc and RHS j
-        if (t < R * kTcKC) {
-          const float ur = ubuf[q].x, ui = ubuf[q].y;
-          const int j = uj, cc = ucc;
+        if (!live) break;
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                     :: "r"(s_u32(&acc_full[b])) : "memory");
+      }
+      // the tensor memory may only be released once every MMA of this block has
+      // completed: one more commit tracks all of them
+      if (issued) {
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                     :: "r"(s_u32(drain)) : "memory");
+        if (!drain_phase(s_u32(drain), 0))
+          asm volatile("st.volatile.shared.b32 [%0], %1;" :: "r"(s_u32(sflag)), "r"(2) : "memory");
+      }
+    }
+  } else if (warp < 6) {
+    // ------------------------------------------------ lo parts of the weights
+    // (shared memory to shared memory: no global load in flight at the proxy fence)
+    const int ct = t - 64;     // 0..127: row of the item
+    int g = 0;
+    bool live = true;
+    for (int it = blockIdx.x; it < n_items && live; it += gridDim.x) {
+      const ItemGeom ig = item_geom(it, items, tile_off, occ_start, blk_seg);
+      for (int c = 0; c < ig.nchunk; ++c, ++g) {
+        const int sa = g % kNA, sc = g % kNC, useC = g / kNC;
+        if ((useC > 0 && !wait_phase(s_u32(&c_empty[sc]), (useC - 1) & 1, spin, sflag)) ||
+            !wait_phase(s_u32(&a_full[sa]), (g / kNA) & 1, spin, sflag)) {
+          live = false;
+          break;
+        }
+        const bool has_row = (ct >> 3) < ig.groups;
+        const int base = (ct >> 3) * kRowGroup + (ct & 7) * 16;
+        float4 x[kKG];
+        if (has_row) {
+          const unsigned char* A = Aring + sa * kAChunk;
+#pragma unroll
+          for (int kg = 0; kg < kKG; ++kg) x[kg] = *reinterpret_cast<const float4*>(A + base + kg * 128);
+        }
+        // the raw weights are in registers: this thread no longer needs the stage
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(s_u32(&a_empty[sa])) : "memory");
+        if (has_row) {
+          unsigned char* Lo = Cring + sc * Lay::kSlot;
+#pragma unroll
+          for (int kg = 0; kg < kKG; ++kg)
+            *reinterpret_cast<float4*>(Lo + base + kg * 128) =
+                make_float4(lo_tf32(x[kg].x), lo_tf32(x[kg].y), lo_tf32(x[kg].z), lo_tf32(x[kg].w));
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(s_u32(&c_ready[sc])) : "memory");
+      }
+    }
+  } else if (warp >= 10) {
+    // ------------------------------------------------ B operands (hi and lo) from the input vectors
+    // warp bw owns operand slot bw: it builds the B of chunks g = bw, bw + kNC,
+    // ... of this block, so it waits for every phase of its slot's barrier in
+    // turn (a waiter that skipped a phase would see an earlier phase of the
+    // same parity as complete).  Value v = lane + 32 i of a chunk is
+    // (RHS j = v % R, column cc = v / R).
+    constexpr int kVals = R * kKC / 32;
+    static_assert(R * kKC % 32 == 0, "B entries per lane");
+    const int bw = warp - 10;
+    int g = 0;
+    bool live = true;
+    for (int it = blockIdx.x; it < n_items && live; it += gridDim.x) {
+      const ItemGeom ig = item_geom(it, items, tile_off, occ_start, blk_seg);
+      const int* sg = blk_seg + 6 * ig.k;
+      const int l0 = sg[1], l1 = sg[3], l2 = sg[5];
+      const int p0 = (l0 + 1) & ~1, p1 = (l1 + 1) & ~1;
+      for (int c = 0; c < ig.nchunk; ++c, ++g) {
+        if (g % kNC != bw) continue;
+        const int useC = g / kNC;
+        if (useC > 0 && !wait_phase(s_u32(&c_empty[bw]), (useC - 1) & 1, spin, sflag)) {
+          live = false;
+          break;
+        }
+        float2 uv[kVals];
+#pragma unroll
+        for (int i = 0; i < kVals; ++i) {
+          const int v = lane + 32 * i, j = v % R, col = c * kKC + v / R;
+          int64_t node = -1;
+          if (col < p0) { if (col < l0) node = sg[0] + col; }
+          else if (col < p0 + p1) { const int o = col - p0; if (o < l1) node = sg[2] + o; }
+          else if (col < ig.nblk) { const int o = col - p0 - p1; if (o < l2) node = sg[4] + o; }
+          uv[i] = node >= 0 ? u[int64_t(j) * N + node] : make_float2(0.f, 0.f);
+        }
+        unsigned char* B = Cring + bw * Lay::kSlot + kAChunk;
+#pragma unroll
+        for (int i = 0; i < kVals; ++i) {
+          const int v = lane + 32 * i, j = v % R, cc = v / R;
+          const float ur = uv[i].x, ui = uv[i].y;
           put_b(B, j, 2 * cc, make_float2(ur, -ui));
           put_b(B, R + j, 2 * cc, make_float2(ui, ur));
           put_b(B, 2 * R + j, 2 * cc, make_float2(lo_tf32(ur), lo_tf32(-ui)));
           put_b(B, 3 * R + j, 2 * cc, make_float2(lo_tf32(ui), lo_tf32(ur)));
-          put_b(B, j, 16 + 2 * cc, make_float2(ur, -ui));      // rows against A_lo: B_hi, then zero
-          put_b(B, R + j, 16 + 2 * cc, make_float2(ui, ur));
-          put_b(B, 2 * R + j, 16 + 2 * cc, make_float2(0.f, 0.f));
-          put_b(B, 3 * R + j, 16 + 2 * cc, make_float2(0.f, 0.f));
         }
-        if (c + kTcAhead < nchunk) load(c + kTcAhead, wbuf[q], ubuf[q]);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(s_u32(&full[s])) : "memory");
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(s_u32(&b_ready[bw])) : "memory");
       }
     }
-    // the last MMAs
-    if (live && nchunk > 0 &&
-        !mbar_wait(s_u32(&empty[(nchunk - 1) % kTcStages]), ((nchunk - 1) / kTcStages) & 1, spin))
-      *sflag = 1;
   } else {
-    // MMA warp (converged; lane 0 issues): four MMAs per chunk once its stage
-    // is written, into four accumulators (M = 128, N = NN, A and B TF32
-    // K-major, D FP32)
-    const bool leader = (t & 31) == 0;
-    const uint32_t idesc =
-        (1u << 4) | (2u << 7) | (2u << 10) | (uint32_t(NN >> 3) << 17) | (uint32_t(kTcRows >> 4) << 24);
-    for (int c = 0; c < nchunk; ++c) {
-      const int s = c % kTcStages;
-      const bool ready = mbar_wait(s_u32(&full[s]), (c / kTcStages) & 1, spin);
-      if (!__all_sync(0xffffffffu, ready)) {
-        *sflag = 1;
+    // ------------------------------------------------ epilogue
+    const int row_in = 32 * (warp & 3) + lane;     // tensor-memory lane quarter of this warp
+    int tile = 0;
+    for (int it = blockIdx.x; it < n_items; it += gridDim.x, ++tile) {
+      const ItemGeom ig = item_geom(it, items, tile_off, occ_start, blk_seg);
+      const int b = tile & 1, bu = tile >> 1;
+      float d[NN], d2[NN];
+      // the warp's lanes decide together (tcgen05.ld is warp-collective)
+      if (!__all_sync(0xffffffffu, wait_phase(s_u32(&acc_full[b]), bu & 1, spin, sflag))) {
+        asm volatile("st.volatile.shared.b32 [%0], %1;" :: "r"(s_u32(sflag)), "r"(1) : "memory");
         break;
       }
-      if (leader) {
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t a0 = s_u32(sm + s * Lay::kStage), b0 = a0 + Lay::kA;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      if (ig.nchunk > 0) {
+        const uint32_t ta = tmem + (uint32_t(32 * (warp & 3)) << 16) + uint32_t(kSets * b * NN);
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {      // K = 8 per MMA: k-groups 2i, 2i + 1
-          const uint64_t da = s_desc(a0 + 2 * i * 128, 128, kTcSBO);
-          const uint64_t db = s_desc(b0 + 2 * i * 128, 128, kTcSBO);
-          asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                       " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n"
-                       :: "r"(tmem + uint32_t(((c % Lay::kSets) * 4 + i) * NN)), "l"(da), "l"(db), "r"(idesc),
-                          "r"(c >= Lay::kSets ? 1 : 0)
-                       : "memory");
+        for (int q = 0; q < NN / 16; ++q) tmem_load16(ta + uint32_t(16 * q), d + 16 * q);
+#pragma unroll
+        for (int st = 1; st < kSets; ++st) {
+#pragma unroll
+          for (int q = 0; q < NN / 16; ++q) tmem_load16(ta + uint32_t(st * NN + 16 * q), d2 + 16 * q);
+#pragma unroll
+          for (int i = 0; i < NN; ++i) d[i] += d2[i];
         }
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                     :: "r"(s_u32(&empty[s])) : "memory");
+      } else {
+#pragma unroll
+        for (int i = 0; i < NN; ++i) d[i] = 0.f;
       }
-      __syncwarp();
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(s_u32(&acc_empty[b])) : "memory");
+      if (row_in < ig.nrow) {
+        float2 acc[R];
+#pragma unroll
+        for (int j = 0; j < R; ++j) acc[j] = make_float2(d[j] + d[2 * R + j], d[R + j] + d[3 * R + j]);
+        const int64_t q = occ_start[ig.k] + ig.row0 + row_in;
+        for (int64_t e = rem_row[q]; e < rem_row[q + 1]; ++e) {
+          const float2 w = rem_val[e];
+          const int cidx = rem_col[e];
+#pragma unroll
+          for (int j = 0; j < R; ++j) acc[j] = cfma(w, u[int64_t(j) * N + cidx], acc[j]);
+        }
+        const float2* ph = Phi + q * nfb2;
+        for (int n = 0; n < nfb2; ++n) {
+          const float2 p = ph[n];
+#pragma unroll
+          for (int j = 0; j < R; ++j) acc[j] = cfma(p, gamma[(int64_t(j) * nocc + ig.k) * nfb2 + n], acc[j]);
+        }
+#pragma unroll
+        for (int j = 0; j < R; ++j) {
+          const float2 uq = u[int64_t(j) * N + q];
+          out[int64_t(j) * N + q] = make_float2(uq.x + kappa2 * acc[j].x, uq.y + kappa2 * acc[j].y);
+        }
+      }
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  const bool ok = *sflag == 0;
-  if (ok && producer) {
-    float d[NN];
-#pragma unroll
-    for (int i = 0; i < NN; ++i) d[i] = 0.f;
-    if (nchunk > 0) {
-#pragma unroll 1
-      for (int a = 0; a < (nchunk < Lay::kSets ? 4 * nchunk : Lay::kAcc); ++a)   // sum of the accumulators used
-#pragma unroll
-        for (int q = 0; q < NN / 16; ++q) {
-          float v[16];
-          tmem_load16(tmem + (uint32_t(warp * 32) << 16) + uint32_t(a * NN + 16 * q), v);
-#pragma unroll
-          for (int i = 0; i < 16; ++i) d[16 * q + i] += v[i];
-        }
-    }
-    if (valid) {
-      float2 acc[R];
-#pragma unroll
-      for (int j = 0; j < R; ++j) acc[j] = make_float2(d[j] + d[2 * R + j], d[R + j] + d[3 * R + j]);
-      const int64_t q = r0 + row;
-      for (int64_t e = rem_row[q]; e < rem_row[q + 1]; ++e) {
-        const float2 w = rem_val[e];
-        const int cidx = rem_col[e];
-#pragma unroll
-        for (int j = 0; j < R; ++j) acc[j] = cfma(w, u[int64_t(j) * N + cidx], acc[j]);
-      }
-      const float2* ph = Phi + q * nfb2;
-      for (int n = 0; n < nfb2; ++n) {
-        const float2 p = ph[n];
-#pragma unroll
-        for (int j = 0; j < R; ++j) acc[j] = cfma(p, gamma[(int64_t(j) * nocc + k) * nfb2 + n], acc[j]);
-      }
-#pragma unroll
-      for (int j = 0; j < R; ++j) {
-        const float2 uq = u[int64_t(j) * N + q];
-        out[int64_t(j) * N + q] = make_float2(uq.x + kappa2 * acc[j].x, uq.y + kappa2 * acc[j].y);
-      }
-    }
-  } else if (!ok && t == 0) {
-    atomicExch(err, 1);
-    // let MMAs still in flight finish (bounded) before the tensor memory is released
-    for (int s = 0; s < kTcStages; ++s) {
-      mbar_wait(s_u32(&empty[s]), 0, spin);
-      mbar_wait(s_u32(&empty[s]), 1, spin);
-    }
-  }
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-  __syncthreads();
-  if (warp == 0)
+  if (t == 0 && *sflag != 0) atomicExch(err, 1);
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(Lay::kTmemCols)
                  : "memory");
+  }
+}
+
+// tile layout of the weights from the row-major blocks: block = work item,
+// float2 element (chunk c, row m, column cc) at
+//   off + (c * groups + m / 8) * 128 + (cc / 2) * 16 + (m % 8) * 2 + cc % 2
+// zero past the block's columns
+__global__ void k_tile_weights(const int2* __restrict__ items, const int64_t* __restrict__ tile_off,
+                               const int64_t* __restrict__ occ_start, const int64_t* __restrict__ blk_off,
+                               const int* __restrict__ blk_seg, const float2* __restrict__ Wb,
+                               float2* __restrict__ Wt) {
+  const ItemGeom ig = item_geom(blockIdx.x, items, tile_off, occ_start, blk_seg);
+  const float2* src = Wb + blk_off[ig.k] + int64_t(ig.row0) * ig.nblk;
+  const int64_t total = int64_t(ig.nchunk) * ig.groups * 128;
+  for (int64_t e = threadIdx.x; e < total; e += blockDim.x) {
+    const int64_t cg = e / 128;
+    const int w = int(e % 128);
+    const int c = int(cg / ig.groups), grp = int(cg % ig.groups);
+    const int m = grp * 8 + (w >> 1) % 8, cc = (w >> 4) * 2 + (w & 1);
+    const int col = c * kKC + cc;
+    float2 v = make_float2(0.f, 0.f);
+    if (m < ig.nrow && col < ig.nblk) v = src[int64_t(m) * ig.nblk + col];
+    Wt[ig.off + e] = v;
+  }
 }
 
 }  // namespace
+
+int64_t tc_tile_elems(int nrow, int nblk) {
+  const int groups = (std::min(nrow, kTcRows) + 7) / 8;
+  return int64_t((nblk + kKC - 1) / kKC) * groups * (kRowGroup / 8);
+}
+
+cudaError_t tile_weights(const ApplyData<float2>& d, float2* Wt, cudaStream_t st) {
+  if (d.n_items128 == 0) return cudaSuccess;
+  k_tile_weights<<<d.n_items128, 256, 0, st>>>(d.items128, d.tile_off, d.occ_start, d.blk_off, d.blk_seg, d.Wb, Wt);
+  return cudaGetLastError();
+}
 
 template <int R>
 cudaError_t near_eval_tc(const ApplyData<float2>& d, const float2* u, float2* out, cudaStream_t st) {
   using Lay = TcLayout<R>;
   static unsigned long long attr = 0;
+  static int n_sm[64] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
   if (first_on_device(attr)) {
     cudaError_t e = cudaFuncSetAttribute(k_near_tc<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, Lay::kBytes);
     if (e != cudaSuccess) return e;
+    if (dev >= 0 && dev < 64) {
+      e = cudaDeviceGetAttribute(&n_sm[dev], cudaDevAttrMultiProcessorCount, dev);
+      if (e != cudaSuccess) return e;
+    }
   }
   if (d.n_items128 == 0) return cudaSuccess;
-  k_near_tc<R><<<d.n_items128, kTcThreads, Lay::kBytes, st>>>(d.items128, d.occ_start, d.blk_off, d.blk_seg, d.Wb,
-                                                           d.rem_row, d.rem_col, d.rem_val, u, d.N, d.Phi, d.gamma,
-                                                           d.nocc, d.nfb2, float(d.kappa2), out, d.tc_err,
-                                                              d.tc_spin);
+  const int sms = (dev >= 0 && dev < 64 && n_sm[dev] > 0) ? n_sm[dev] : 148;
+  const int grid = d.n_items128 < sms ? d.n_items128 : sms;
+  k_near_tc<R><<<grid, kThreads, Lay::kBytes, st>>>(d.items128, d.n_items128, d.tile_off, d.occ_start, d.blk_seg,
+                                                     d.Wt, d.rem_row, d.rem_col, d.rem_val, u, d.N, d.Phi,
+                                                     d.gamma, d.nocc, d.nfb2, float(d.kappa2), out, d.tc_err,
+                                                     d.tc_spin);
   return cudaGetLastError();
 }
 

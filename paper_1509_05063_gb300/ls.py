@@ -104,6 +104,8 @@ _SIGS = {
     "ls_get_stage_times": ([C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
     "ls_plan_device_status": ([C.c_void_p]),
     "ls_set_wait_limit": ([C.c_void_p, C.c_int]),
+    "ls_measure_peaks": ([C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    "ls_plan_create3": ([C.c_void_p, C.c_void_p, N2FN, C.c_void_p, C.c_double, C.c_void_p, C.POINTER(C.c_void_p)]),
     "ls_batch_create": ([C.c_void_p, C.c_int, C.POINTER(C.c_void_p)]),
     "ls_batch_offsets": ([C.c_void_p, C.c_void_p]),
     "ls_batch_apply": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
@@ -161,10 +163,10 @@ def options_from(wl, n_threads: int = 0, rcond: float = 0.0, rcond_mixed: float 
     return o
 
 
-def _n2_callback(n2):
+def _n2_callback(n2, dim: int = 2):
     def cb(n, xy, out, ctx):
         try:
-            pts = np.ctypeslib.as_array(xy, shape=(n, 2))
+            pts = np.ctypeslib.as_array(xy, shape=(n, dim))
             vals = np.asarray(n2(pts), dtype=np.float64).reshape(n)
             np.ctypeslib.as_array(out, shape=(n,))[:] = vals
             return 0
@@ -499,6 +501,67 @@ class HostBall3:
             self.close()
         except Exception:
             pass
+
+
+class Accel3Params(C.Structure):
+    _fields_ = [("box0", C.c_double * 3), ("H", C.c_double), ("L", C.c_int), ("N_eq", C.c_int), ("p", C.c_int),
+                ("m_coll", C.c_int), ("rcond", C.c_double), ("n_threads", C.c_int)]
+
+
+class Plan3(Plan):
+    """A 3-D device plan of a penetrable ball (ls_plan_create3): ball and rule
+    parameters as in HostBall3, n2: callable mapping (n, 3) points to n^2,
+    the cube-cell box (corner box0, side H, L per axis) and the accelerator's
+    N_eq, local-expansion degree p (0: 2 N_eq + 1) and fit truncation.
+    apply / solve / farfield (3-D directions) as for Plan."""
+
+    def __init__(self, n2, kappa: float, box0, H: float, L: int, N_eq: int, ball: dict | None = None,
+                 rules: dict | None = None, p: int = 0, m_coll: int = 0, rcond: float = 0.0, n_threads: int = 0):
+        load_library()
+        b = dict(a=1.0, w=0.5, n_f=17, n_s=9, Q=5, delta=0.25, h=0.1, tau0=0.3, tau1=0.95)
+        b.update(ball or {})
+        prm = Ball3Params(float(b["a"]), float(b["w"]), int(b["n_f"]), int(b["n_s"]), int(b["Q"]), float(b["delta"]),
+                          float(b["h"]), float(b["tau0"]), float(b["tau1"]))
+        ru = HostBall3._rules(rules)
+        acc = Accel3Params((C.c_double * 3)(*[float(v) for v in box0]), float(H), int(L), int(N_eq), int(p),
+                           int(m_coll), float(rcond), int(n_threads))
+        self.wl = None
+        self.kappa = float(kappa)
+        self._cb = _n2_callback(n2, dim=3)
+        h = C.c_void_p()
+        st = _lib.ls_plan_create3(C.byref(prm), C.byref(ru) if ru is not None else None, self._cb, None,
+                                  self.kappa, C.byref(acc), C.byref(h))
+        if st != 0:
+            raise LSError(st, _lib.ls_last_error(None).decode())
+        self._h = h
+        info = PlanInfo()
+        _check(_lib.ls_plan_info(self._h, C.byref(info)), self._h)
+        self.info = {f: getattr(info, f) for f, _ in PlanInfo._fields_}
+        self.N = int(info.N)
+
+    def nodes(self):
+        xyz = np.zeros((self.N, 3))
+        canon = np.zeros(self.N, np.int64)
+        _check(_lib.ls_plan_nodes(self._h, xyz.ctypes.data, canon.ctypes.data), self._h)
+        return xyz, canon
+
+    def farfield(self, u, dirs, stream=None):
+        import torch
+        dirs = np.ascontiguousarray(dirs, dtype=np.float64).reshape(-1, 3)
+        nrhs = 1 if u.dim() == 1 else u.shape[0]
+        A = torch.empty((nrhs, len(dirs)), dtype=torch.complex128, device=u.device)
+        _check(_lib.ls_farfield(self._h, C.c_void_p(u.data_ptr()), nrhs, dirs.ctypes.data, len(dirs),
+                                C.c_void_p(A.data_ptr()), _stream(stream)), self._h)
+        return A
+
+
+def measure_peaks():
+    """Measured FP64 FMA and TF32 tensor-core (tcgen05) throughput of the
+    current GPU in TFLOP/s: {"fp64": ..., "tf32": ...} (ls_measure_peaks)."""
+    load_library()
+    f64, t32 = C.c_double(0.0), C.c_double(0.0)
+    _check(_lib.ls_measure_peaks(C.byref(f64), C.byref(t32)))
+    return {"fp64": f64.value, "tf32": t32.value}
 
 
 def interior_window3(kappa, h, R=3.0, p=5, q=3, n_rho=16, n_mu=16, n_phi=32, chi_s0=0.1):

@@ -45,3 +45,34 @@ def test_timeout_is_reported_and_recovered(plan):
     again = plan.apply(U, prec=LS_MIXED)
     plan.device_status()
     assert torch.equal(again, good)
+
+
+def test_timeout_after_mmas_were_issued(plan):
+    """Small non-zero limits: waits give up part-way through, after some bulk
+    copies landed and some MMAs were issued (which limit does that depends on
+    timing, so several are tried).  Each apply either completes or reports
+    LS_ERR_TIMEOUT; the block always waits for its own MMAs and copies before
+    it frees its tensor memory, so the next apply with the normal limit is
+    exact again."""
+    from paper_1509_05063_gb300 import LS_MIXED, LSError
+    U = torch.from_numpy(W.random_density(plan.N, nrhs=16, seed=W.SEED + 32)).to("cuda:0", torch.complex64)
+    good = plan.apply(U, prec=LS_MIXED)
+    plan.device_status()
+    timeouts = 0
+    try:
+        for limit in (1, 2, 4, 16, 64, 256, 1024, 4096):
+            plan.set_wait_limit(limit)
+            for _ in range(3):
+                got = plan.apply(U, prec=LS_MIXED)
+                try:
+                    plan.device_status()
+                    assert torch.equal(got, good)      # no time-out: the full result
+                except LSError as e:
+                    assert e.status == 5
+                    timeouts += 1
+    finally:
+        plan.set_wait_limit(1 << 22)
+    assert timeouts > 0
+    again = plan.apply(U, prec=LS_MIXED)
+    plan.device_status()
+    assert torch.equal(again, good)
