@@ -965,12 +965,16 @@ ls_status ls_plan_create(const ls_geometry* geom, ls_n2_fn n2, void* ctx, double
     std::vector<cd>().swap(Wb);
     b.Wb = UP(float2, w32);
   }
-  {   // the same blocks in the tile layout the tensor-core near field copies in bulk
+  {   // the same blocks in the tile layout the tensor-core near field copies in
+      // bulk (split FP16, scaled per row), its row scales and per-RHS scales
     float2* wt = plan->alloc<float2>(size_t(tile_off.back()), &st);
+    float* rs = plan->alloc<float>(size_t(N), &st);
+    b.tc_tmax = plan->alloc<unsigned>(size_t(lsd::kMaxRhs32), &st);
     if (st != LS_OK) return bail(st, plan->err);
-    const cudaError_t e = lsd::tile_weights(b, wt, 0);
+    const cudaError_t e = lsd::tile_weights(b, wt, rs, 0);
     if (e != cudaSuccess) return bail(LS_ERR_CUDA, std::string("tile layout: ") + cudaGetErrorString(e));
     b.Wt = wt;
+    b.tc_rscale = rs;
   }
   b.rem_val = UP(float2, to32(rem_val));
   b.Gq = d_G32; b.Dq = d_D32;
@@ -1166,6 +1170,8 @@ ls_status ls_plan_create3(const ls_ball3* ball, const ls_rules3* rules, ls_n2_fn
     a.Sm = plan->alloc<double2>(size_t(M3), &st);
     a.Sd = plan->alloc<double2>(size_t(M3), &st);
     a.gamma = plan->alloc<double2>(size_t(nocc) * nb, &st);
+    a.X = plan->alloc<double2>(size_t(nocc) * K, &st);
+    a.part = plan->alloc<double2>(size_t(lsd::local3_slices(nocc, nb, K)) * nocc * nb, &st);
     if (st != LS_OK) return bail(st, plan->err);
     auto& b = plan->e32;
     b.N = a.N; b.nocc = a.nocc; b.L = a.L; b.Ne = a.Ne; b.n_es = a.n_es; b.n_loc = a.n_loc; b.nb = a.nb; b.M = a.M;

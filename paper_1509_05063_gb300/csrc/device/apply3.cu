@@ -7,7 +7,8 @@
 //   k3_fill       sigma -> monopole / dipole values on the x1-face planes of the lattice
 //   k3_fft_axis   batched line FFTs along one axis of the M^3 lattice (three per transform)
 //   k3_spectral   V^ = S_m^ G^ + S_d^ D^
-//   k3_local      gamma_c = B^+ V_c - sum_o (B^+ T_o) sigma_{c+o}   (27 neighbours)
+//   k3_gather, k3_gemm, k3_reduce
+//                 gamma_c = B^+ V_c - sum_o (B^+ T_o) sigma_{c+o}   (27 neighbours; one GEMM over cells)
 //   k3_near       out_q = u_q + kappa^2 (sum_l W_ql u_l + Phi_q . gamma_c)
 // The complex64 apply runs the projection, the adjacent part and the
 // evaluation in complex64 and the lattice convolution and local coefficients
@@ -125,17 +126,20 @@ __global__ void __launch_bounds__(kT3) k3_spectral(T* __restrict__ Sm, const T* 
     Sm[e] = cfma(Sd[e], Ds[e], cmul(Sm[e], Gs[e]));
 }
 
-// gamma_c = LA^T x_c with x_c = [V at the closed cell's (N_eq + 1)^3 lattice
-// points; sigma of the 27 neighbours, offset (oi + 1) 9 + (oj + 1) 3 + (ok + 1),
-// zero where there is none]: block = occupied cell, x_c in shared memory,
-// thread = outputs n = t, t + 256, ...
+// The local coefficients of every cell as one GEMM, gamma (cells x nb) =
+// X (cells x K) LA (K x nb), K = (N_eq + 1)^3 + 27 n_es, with X_c = [V at the
+// closed cell's lattice points; sigma of the 27 neighbours, offset
+// (oi + 1) 9 + (oj + 1) 3 + (ok + 1), zero where there is none].
+// k3_gather writes X; k3_gemm multiplies tiles of kGC cells x kGN outputs over
+// one of S slices of K (enough blocks to fill the GPU); k3_reduce adds the S
+// partial products in slice order.
 template <typename T>
-__global__ void __launch_bounds__(kT3) k3_local(ApplyData3<T> d) {
-  extern __shared__ __align__(16) unsigned char raw3[];
-  T* x = reinterpret_cast<T*>(raw3);
+__global__ void __launch_bounds__(kT3) k3_gather(ApplyData3<T> d) {
   const int k = blockIdx.x, t = threadIdx.x, L = d.L, Ne = d.Ne, n1 = Ne + 1;
   const int cell = d.occ_cells[k], ci = cell % L, cj = (cell / L) % L, ck = cell / (L * L);
   const int64_t MM = int64_t(d.M) * d.M;
+  const int K = d.n_loc + 27 * d.n_es;
+  T* x = d.X + int64_t(k) * K;
   for (int p = t; p < d.n_loc; p += kT3) {
     const int la = p / (n1 * n1), lb = (p / n1) % n1, lc = p % n1;
     x[p] = d.Sm[int64_t(ci * Ne + la) * MM + int64_t(cj * Ne + lb) * d.M + (ck * Ne + lc)];
@@ -150,13 +154,89 @@ __global__ void __launch_bounds__(kT3) k3_local(ApplyData3<T> d) {
     }
     x[d.n_loc + p] = v;
   }
-  __syncthreads();
+}
+
+constexpr int kGC = 32, kGN = 32, kGK = 16;   // GEMM tile: cells x outputs x K step
+
+// block (cell tile, output tile, slice s): thread (tc, tn) accumulates cells
+// tc, tc + 16 against outputs tn, tn + 16 over its slice of K.  Complex
+// products take three real multiplications (Gauss's form): with a + ib an
+// entry of LA and c + id one of X, staged as (a, b, a + b) and (c, c + d,
+// d - c), P += (a + b) c, Q += b (c + d), S += a (d - c) and the product is
+// (P - Q) + i (P + S).  On GB300's FP64 pipe that is 3 FMAs instead of 4.
+template <typename R>
+struct G3 {
+  R a, b, s;
+};
+template <typename T>
+__global__ void __launch_bounds__(kT3) k3_gemm(ApplyData3<T> d, int S) {
+  using R = decltype(T().x);
+  __shared__ G3<R> xs[kGK][kGC + 1];
+  __shared__ G3<R> as[kGK][kGN];
   const int K = d.n_loc + 27 * d.n_es;
-  for (int n = t; n < d.nb; n += kT3) {
-    T acc = czero(T());
-    for (int j = 0; j < K; ++j) acc = cfma(d.LA[int64_t(j) * d.nb + n], x[j], acc);
-    d.gamma[int64_t(k) * d.nb + n] = acc;
+  const int c0 = blockIdx.x * kGC, n0 = blockIdx.y * kGN, sl = blockIdx.z;
+  const int kper = (K + S - 1) / S, kb = sl * kper, ke = kb + kper < K ? kb + kper : K;
+  const int t = threadIdx.x, tc = t / 16, tn = t % 16;
+  R P[2][2], Q[2][2], U[2][2];
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 2; ++b) P[a][b] = Q[a][b] = U[a][b] = R(0);
+  for (int k0 = kb; k0 < ke; k0 += kGK) {
+    __syncthreads();
+    for (int i = t; i < kGK * kGC; i += kT3) {        // X tile: consecutive threads along K
+      const int kk = i % kGK, cc = i / kGK, c = c0 + cc, kg = k0 + kk;
+      const T v = (c < d.nocc && kg < ke) ? d.X[int64_t(c) * K + kg] : czero(T());
+      xs[kk][cc] = G3<R>{v.x, v.x + v.y, v.y - v.x};
+    }
+    for (int i = t; i < kGK * kGN; i += kT3) {        // LA tile: consecutive threads along the outputs
+      const int kk = i / kGN, nn = i % kGN, n = n0 + nn, kg = k0 + kk;
+      const T v = (n < d.nb && kg < ke) ? d.LA[int64_t(kg) * d.nb + n] : czero(T());
+      as[kk][nn] = G3<R>{v.x, v.y, v.x + v.y};
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < kGK; ++kk) {
+      const G3<R> x[2] = {xs[kk][tc], xs[kk][tc + 16]};
+      const G3<R> l[2] = {as[kk][tn], as[kk][tn + 16]};
+#pragma unroll
+      for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+          P[a][b] = fma(l[b].s, x[a].a, P[a][b]);     // (a + b) c
+          Q[a][b] = fma(l[b].b, x[a].b, Q[a][b]);     // b (c + d)
+          U[a][b] = fma(l[b].a, x[a].s, U[a][b]);     // a (d - c)
+        }
+    }
   }
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      const int c = c0 + tc + 16 * a, n = n0 + tn + 16 * b;
+      if (c < d.nocc && n < d.nb) d.part[(int64_t(sl) * d.nocc + c) * d.nb + n] = mk(P[a][b] - Q[a][b], P[a][b] + U[a][b]);
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kT3) k3_reduce(ApplyData3<T> d, int S) {
+  const int64_t n = int64_t(d.nocc) * d.nb;
+  for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < n; e += int64_t(gridDim.x) * blockDim.x) {
+    T v = d.part[e];
+    for (int sl = 1; sl < S; ++sl) v = cadd(v, d.part[int64_t(sl) * n + e]);
+    d.gamma[e] = v;
+  }
+}
+
+// slices of K for the local GEMM: about 8 blocks per SM in all, each slice at
+// least a few K steps long
+__host__ __device__ inline int local_slices(int nocc, int nb, int K) {
+  const int tiles = ((nocc + kGC - 1) / kGC) * ((nb + kGN - 1) / kGN);
+  int S = (152 * 8 + tiles - 1) / tiles;
+  const int smax = K / (4 * kGK) > 1 ? K / (4 * kGK) : 1;
+  if (S > smax) S = smax;
+  if (S > kLocalSlicesMax) S = kLocalSlicesMax;
+  return S < 1 ? 1 : S;
 }
 
 // warp per row: stored adjacent part (CSR) and the local expansion of the
@@ -231,8 +311,10 @@ cudaError_t lattice_local(const ApplyData3<T>& d, cudaStream_t st) {
   k3_spectral<T><<<grid_for(n3), kT3, 0, st>>>(d.Sm, d.Sd, d.Gs, d.Ds, n3);
   e = fft3d<T>(d.Sm, d.M, d.logM, d.tw, true, st);
   if (e != cudaSuccess) return e;
-  const size_t sm_local = sizeof(T) * size_t(d.n_loc + 27 * d.n_es);
-  k3_local<T><<<d.nocc, kT3, sm_local, st>>>(d);
+  const int K = d.n_loc + 27 * d.n_es, S = local_slices(d.nocc, d.nb, K);
+  k3_gather<T><<<d.nocc, kT3, 0, st>>>(d);
+  k3_gemm<T><<<dim3((d.nocc + kGC - 1) / kGC, (d.nb + kGN - 1) / kGN, S), kT3, 0, st>>>(d, S);
+  k3_reduce<T><<<grid_for(int64_t(d.nocc) * d.nb), kT3, 0, st>>>(d, S);
   return cudaGetLastError();
 }
 
@@ -259,6 +341,8 @@ cudaError_t apply3_one(const ApplyData3<T>& d, const T* u, T* out, cudaStream_t 
 
 }  // namespace
 
+int local3_slices(int nocc, int nb, int K) { return local_slices(nocc, nb, K); }
+
 template <typename T>
 cudaError_t fft3d(T* x, int M, int logM, const T* tw, bool inverse, cudaStream_t st) {
   if (M < 16 || M > 2048 || (M & (M - 1))) return cudaErrorInvalidValue;
@@ -277,13 +361,6 @@ cudaError_t fft3d(T* x, int M, int logM, const T* tw, bool inverse, cudaStream_t
 
 template <typename T>
 cudaError_t apply3_batch(const ApplyData3<T>& d, const T* u, T* out, int nr, cudaStream_t st) {
-  static unsigned long long attr = 0;
-  if (first_on_device(attr)) {
-    const cudaError_t e =
-        cudaFuncSetAttribute(k3_local<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-    if (e != cudaSuccess) return e;
-  }
-  if (sizeof(double2) * size_t(d.n_loc + 27 * d.n_es) > 227 * 1024) return cudaErrorInvalidValue;
   if (sizeof(T) == 8 && !d.lattice64) return cudaErrorInvalidValue;
   for (int r = 0; r < nr; ++r) {
     const cudaError_t e = apply3_one(d, u + int64_t(r) * d.N, out + int64_t(r) * d.N, st);

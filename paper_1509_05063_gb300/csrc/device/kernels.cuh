@@ -55,6 +55,8 @@ struct ApplyData {
   int n_items128 = 0;
   const int64_t* tile_off = nullptr;    // complex64 only: offset of each 128-row item in Wt
   const T* Wt = nullptr;                // complex64 only: the blocks in the tensor-core tile layout
+  const float* tc_rscale = nullptr;     // complex64 only: 1 / (power-of-two scale) of each near-field row
+  unsigned* tc_tmax = nullptr;          // complex64 only: per-RHS largest |Re|, |Im| of one apply (float bits)
   int* tc_err = nullptr;                // set by the tensor-core near field when a wait times out
   int tc_spin = 1 << 22;                // polls of each mbarrier wait before it gives up
   const T* Wb = nullptr;                // blocks, row-major per cell
@@ -95,7 +97,7 @@ constexpr int kMaxRhs64 = 4, kMaxRhs32 = 16;
 constexpr int kProjPiece = 128;    // nodes per projection block at most
 
 // Near field + evaluation + assembly of R complex64 right-hand sides (R = 8 or
-// 16) on the tensor cores (tcgen05, 3xTF32; device/near_tc.cu); same result as
+// 16) on the tensor cores (tcgen05, split FP16 with power-of-two scaling; device/near_tc.cu); same result as
 // the CUDA-core kernel up to FP32 rounding.
 template <int R>
 cudaError_t near_eval_tc(const ApplyData<float2>& d, const float2* u, float2* out, cudaStream_t st);
@@ -103,7 +105,7 @@ cudaError_t near_eval_tc(const ApplyData<float2>& d, const float2* u, float2* ou
 // in the tile layout of the tensor-core near field, and the plan-time kernel
 // that writes that layout (d.items128, d.tile_off, d.Wb set) into Wt.
 int64_t tc_tile_elems(int nrow, int nblk);
-cudaError_t tile_weights(const ApplyData<float2>& d, float2* Wt, cudaStream_t st);
+cudaError_t tile_weights(const ApplyData<float2>& d, float2* Wt, float* rscale, cudaStream_t st);
 
 // Device-resident pieces of a 3-D plan (Section 5: ball, cube cells of side H,
 // L per axis) for one arithmetic precision.  Vectors are in the plan's node
@@ -132,6 +134,8 @@ struct ApplyData3 {
   T* Sm = nullptr;                      // M^3: monopole lattice, then the lattice field V
   T* Sd = nullptr;                      // M^3: dipole lattice
   T* gamma = nullptr;                   // nocc x nb
+  T* X = nullptr;                       // FP64 data only: nocc x (n_loc + 27 n_es), inputs of the local step
+  T* part = nullptr;                    // FP64 data only: local3_slices x nocc x nb partial products
   // complex64 only (host pointer): the FP64 data whose lattice convolution and
   // local coefficients the complex64 apply uses.  On a cell's own lattice
   // points the 27 neighbours' fields dominate and cancel in the neighbour
@@ -139,6 +143,10 @@ struct ApplyData3 {
   // by that cancellation and by the ill-conditioned local fit.
   const ApplyData3<double2>* lattice64 = nullptr;
 };
+
+// K slices of the 3-D local-coefficient GEMM (sizes its partial-product array)
+constexpr int kLocalSlicesMax = 64;
+int local3_slices(int nocc, int nb, int K);
 
 // out = A u for nr right-hand sides of a 3-D plan (one after another through
 // the same work space; u, out: nr vectors of length N).

@@ -10,41 +10,47 @@
 //   B[2c][j] = Re u_j[c],   B[2c+1][j] = -Im u_j[c]      (columns j < R: real parts)
 //   B[2c][R+j] = Im u_j[c], B[2c+1][R+j] = Re u_j[c]      (imaginary parts)
 // so that D = A B holds Re(W u_j) in column j and Im(W u_j) in column R + j.
-// FP32 accuracy from TF32 inputs (3xTF32): with x = hi(x) + lo(x), hi the TF32
-// truncation (what the tensor core reads from an FP32 word) and lo exact in
-// FP32,
-//   D = A_hi B_hi + A_hi B_lo + A_lo B_hi   (the lo.lo term, 2^-22 relative, is dropped)
-// as two MMAs per K step into one accumulator: A against [B_hi | B_lo]
-// (N = 4R columns) and A_lo against B_hi (N = 2R, accumulating into the first
-// 2R columns); the epilogue adds the two column halves.
 //
-// The weights are stored for this kernel in its own tile layout (built once at
-// plan time from the row-major blocks): per work item and chunk of kKC complex
-// columns, the item's rows in groups of 8 as the canonical K-major no-swizzle
-// core-matrix layout (8 rows x 16 bytes per core matrix, 128 bytes between
-// K-adjacent core matrices, 1024 bytes between row groups), only the row groups
-// that hold rows.  One bulk copy (cp.async.bulk, completion counted on an
-// mbarrier) moves a chunk from HBM into shared memory: no registers, no
-// per-thread loads on the weight stream.
+// Split FP16 operands (kind::f16, FP32 accumulation).  A row's weights are
+// scaled by a power of two s_m that puts the row's largest magnitude in
+// [2^14, 2^15) and split as x s_m = hi + lo with hi = fp16(x s_m) and
+// lo = fp16(x s_m - hi), together 22 significant bits; right-hand side j is
+// scaled by a power of two t_j the same way.  Then
+//   D = A_hi B_hi + A_hi B_lo + A_lo B_hi    (the lo.lo term, 2^-22 relative, is dropped)
+// as two MMAs per K step into one accumulator: A_hi against [B_hi | B_lo]
+// (N = 4R columns) and A_lo against B_hi (N = 2R, accumulating into the first
+// 2R columns); the epilogue adds the two column halves and divides by s_m t_j.
+// An MMA instruction costs about the same time for N = 32 and N = 64 here, so
+// the work per byte of weights is set by the instruction count: FP16 takes
+// K = 16 per instruction where TF32 takes 8, which halves it, and the lo parts
+// come from HBM with the hi parts (the same 4 bytes per real weight as FP32),
+// so no thread touches the weight stream.
+//
+// Storage (built once at plan time from the row-major blocks): per work item
+// and chunk of kKC complex columns, the hi parts of the item's rows in groups
+// of 8 as the canonical K-major no-swizzle core-matrix layout (8 rows x 16
+// bytes per core matrix, 128 bytes between K-adjacent core matrices, 512
+// bytes between row groups), only the row groups that hold rows, then the lo
+// parts in the same layout.  Two bulk copies (cp.async.bulk, completion
+// counted on an mbarrier) move a chunk from HBM into a weight stage.
 //
 // Persistent, warp-specialised, one block per SM walking the work items
 // blockIdx.x, blockIdx.x + gridDim.x, ... (heaviest first):
 //   warp 0      lane 0 issues the bulk copies into a ring of kNA weight stages;
 //   warp 1      lane 0 issues the MMAs and commits them to the release barriers;
-//   warps 2..5  (128 threads) per chunk: the lo part of the weights, into a
-//               ring of kNC operand slots;
-//   warps 10..  one warp per operand slot: the B operand (hi and lo) of the
-//               chunks that use its slot, from the input vectors;
-//   warps 6..9  (128 threads) per item: read the accumulator from tensor memory
-//               (two accumulators, so the epilogue of one item overlaps the MMAs
-//               of the next), add the CSR remainder and the local expansion
-//               Phi_q . gamma_c and write out_q = u_q + kappa^2 (near + far).
+//   warps 2..5  (128 threads) per item: read the accumulator from tensor memory
+//               (two items in flight), add the CSR remainder and the local
+//               expansion Phi_q . gamma_c and write out_q = u_q + kappa^2 (near + far);
+//   warps 6..   one warp per operand slot: the B operand (scaled hi and lo) of
+//               the chunks that use its slot, from the input vectors.
 // Every wait is bounded by `spin` polls and also gives up once another role
 // has flagged a failure; then the block sets *err, waits (with a fixed bound
 // that does not depend on `spin`) for its own MMAs and bulk copies still in
 // flight, frees its tensor memory and returns, leaving its rows unwritten.
 #include <algorithm>
 #include <cstdint>
+
+#include <cuda_fp16.h>
 
 #include "device/cplx.cuh"
 #include "device/kernels.cuh"
@@ -54,13 +60,14 @@ namespace {
 
 constexpr int kTcRows = 128;                 // rows per item = MMA M
 constexpr int kKC = 16;                      // complex columns per chunk (K = 32 real)
-constexpr int kKG = 2 * kKC / 4;             // 16-byte core-matrix columns per row: 8
-constexpr int kRowGroup = 8 * kKG * 16;      // bytes of one 8-row group of a chunk: 1024
-constexpr int kAChunk = 16 * kRowGroup;      // 128 rows: 16 KB
-constexpr int kNA = 9;                       // weight stages (bulk-copy ring)
-constexpr int kNC = 3;                       // operand slots (lo weights + B)
+constexpr int kKG = 2 * kKC / 8;             // 16-byte core-matrix columns per row (8 fp16 each): 4
+constexpr int kRowGroup = 8 * kKG * 16;      // bytes of one 8-row group of a chunk (hi or lo): 512
+constexpr int kHalf = 16 * kRowGroup;        // 128 rows, hi or lo: 8 KB
+constexpr int kAStage = 2 * kHalf;           // a weight stage: hi, then lo
+constexpr int kNA = 12;                      // weight stages (bulk-copy ring)
+constexpr int kNC = 4;                       // B operand slots = B warps
 constexpr int kSets = 2;                     // accumulator sets per item (alternate K steps)
-constexpr int kThreads = 32 * (10 + kNC);    // + one B-operand warp per operand slot
+constexpr int kThreads = 32 * (6 + kNC);
 constexpr int kDrainPolls = 1 << 28;         // bound of the final waits on the block's own MMAs / copies
 
 __device__ __forceinline__ uint32_t s_u32(const void* p) { return uint32_t(__cvta_generic_to_shared(p)); }
@@ -71,16 +78,26 @@ __device__ __forceinline__ uint64_t s_desc(uint32_t addr, uint32_t lbo, uint32_t
          (uint64_t((sbo >> 4) & 0x3FFF) << 32) | (uint64_t(1) << 46);
 }
 
-// x - (x with the 13 low mantissa bits cleared): exact in FP32
-__device__ __forceinline__ float lo_tf32(float x) { return x - __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
-
+// one poll of an mbarrier phase.  try_wait may suspend the thread for a while
+// and, measured here, wakes it a few hundred cycles after the phase completes;
+// test_wait returns at once.  The latency-critical roles (bulk copies, MMA
+// issue, B operands) spin on test_wait; the epilogue, which waits a whole
+// item's main loop, sleeps in try_wait and leaves the issue slots to them.
+template <bool kSpin>
 __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
   uint32_t done;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(done)
-      : "r"(bar), "r"(parity)
-      : "memory");
+  if constexpr (kSpin)
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+  else
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
   return done != 0;
 }
 
@@ -90,14 +107,21 @@ __device__ __forceinline__ int ld_flag(const int* f) {
   return v;
 }
 
+__device__ __forceinline__ void set_flag(int* f, int v) {
+  asm volatile("st.volatile.shared.b32 [%0], %1;" :: "r"(s_u32(f)), "r"(v) : "memory");
+}
+
 // wait for a phase: at most `limit` polls, and give up as soon as the block's
-// failure flag is set; on time-out the flag is set
+// failure flag is set; on time-out the flag is set.  Every waiter below waits
+// for the phases of its barrier in order: one that skipped a phase would see
+// the earlier phase of the same parity as complete.
+template <bool kSpin = true>
 __device__ __forceinline__ bool wait_phase(uint32_t bar, uint32_t parity, int limit, int* flag) {
   for (int it = 0; it < limit; ++it) {
-    if (mbar_try(bar, parity)) return true;
+    if (mbar_try<kSpin>(bar, parity)) return true;
     if (ld_flag(flag)) return false;
   }
-  asm volatile("st.volatile.shared.b32 [%0], %1;" :: "r"(s_u32(flag)), "r"(1) : "memory");
+  set_flag(flag, 1);
   return false;
 }
 
@@ -105,7 +129,7 @@ __device__ __forceinline__ bool wait_phase(uint32_t bar, uint32_t parity, int li
 // which depend on nothing else)
 __device__ __forceinline__ bool drain_phase(uint32_t bar, uint32_t parity) {
   for (int it = 0; it < kDrainPolls; ++it)
-    if (mbar_try(bar, parity)) return true;
+    if (mbar_try<false>(bar, parity)) return true;
   return false;
 }
 
@@ -128,22 +152,26 @@ template <int R>
 struct TcLayout {
   static constexpr int NN = 4 * R;                              // MMA N of [B_hi | B_lo]
   static constexpr int kB = NN * kKG * 16;                      // B operand of a chunk
-  static constexpr int kSlot = kAChunk + kB;                    // lo weights + B
-  // two items in flight x two accumulator sets (alternate K steps feed
-  // alternate sets, so consecutive MMAs do not chain on one accumulator)
   static constexpr int kTmemCols = 2 * kSets * NN < 32 ? 32 : 2 * kSets * NN;
-  static constexpr int kBarOff = kNA * kAChunk + kNC * kSlot;
+  static constexpr int kBarOff = kNA * kAStage + kNC * kB;
   static constexpr int kBytes = kBarOff + 320;                  // + mbarriers, tensor-memory address, flag
 };
 
-// write (v.x, v.y) at B[n][kq], B[n][kq + 1] (kq even)
-__device__ __forceinline__ void put_b(unsigned char* B, int n, int kq, float2 v) {
-  *reinterpret_cast<float2*>(B + (n >> 3) * kRowGroup + (kq >> 2) * 128 + (n & 7) * 16 + (kq & 3) * 4) = v;
+// (hi, lo) fp16 split of a scaled value
+__device__ __forceinline__ void split16(float v, __half& hi, __half& lo) {
+  hi = __float2half_rn(v);
+  lo = __float2half_rn(v - __half2float(hi));
+}
+
+// write the fp16 pair (v0, v1) at B[n][kq], B[n][kq + 1] (kq even)
+__device__ __forceinline__ void put_b(unsigned char* B, int n, int kq, __half v0, __half v1) {
+  *reinterpret_cast<__half2*>(B + (n >> 3) * kRowGroup + (kq >> 3) * 128 + (n & 7) * 16 + (kq & 7) * 2) =
+      __halves2half2(v0, v1);
 }
 
 struct ItemGeom {
   int k, row0, nrow, nblk, nchunk, groups;
-  int64_t off;   // float2 offset of the item's first chunk in the tile layout
+  int64_t off;   // byte offset / 8 of the item's first chunk in the tile layout
 };
 
 __device__ __forceinline__ ItemGeom item_geom(int it, const int2* items, const int64_t* tile_off,
@@ -162,12 +190,35 @@ __device__ __forceinline__ ItemGeom item_geom(int it, const int2* items, const i
   return g;
 }
 
+// power-of-two scale that puts m (> 0, normal) in [2^14, 2^15): 2^(14 - floor(log2 m))
+__device__ __forceinline__ float pow2_scale(float m) {
+  if (!(m >= 1.17549435e-38f) || !(m < 3.0e38f)) return 1.f;
+  const int e = int((__float_as_uint(m) >> 23) & 0xFF) - 127;   // floor(log2 m)
+  return ldexpf(1.f, 14 - e < 126 ? 14 - e : 126);
+}
+
+// per right-hand side j (blockIdx.y): the largest |Re u_j[q]|, |Im u_j[q]|,
+// as the bits of a non-negative float (whose order is the integers' order)
+// maxed into tmax[j], which the caller zeroes first
+constexpr int kScaleBlocks = 32;
+__global__ void __launch_bounds__(256) k_rhs_max(const float2* __restrict__ u, int64_t N,
+                                                 unsigned* __restrict__ tmax) {
+  const float2* v = u + int64_t(blockIdx.y) * N;
+  float m = 0.f;
+  for (int64_t q = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; q < N; q += int64_t(gridDim.x) * blockDim.x)
+    m = fmaxf(m, fmaxf(fabsf(v[q].x), fabsf(v[q].y)));
+  for (int d = 16; d > 0; d >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, d));
+  if ((threadIdx.x & 31) == 0) atomicMax(&tmax[blockIdx.y], __float_as_uint(m));
+}
+
 template <int R>
 __global__ void __launch_bounds__(kThreads, 1) k_near_tc(const int2* __restrict__ items, int n_items,
                                                          const int64_t* __restrict__ tile_off,
                                                          const int64_t* __restrict__ occ_start,
                                                          const int* __restrict__ blk_seg,
-                                                         const float2* __restrict__ Wt,
+                                                         const unsigned char* __restrict__ Wt,
+                                                         const float* __restrict__ rscale,
+                                                         const unsigned* __restrict__ tmax,
                                                          const int64_t* __restrict__ rem_row,
                                                          const int* __restrict__ rem_col,
                                                          const float2* __restrict__ rem_val,
@@ -179,14 +230,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_near_tc(const int2* __restrict_
   using Lay = TcLayout<R>;
   constexpr int NN = Lay::NN;
   extern __shared__ __align__(1024) unsigned char sm[];
-  unsigned char* Aring = sm;                                  // kNA x 16 KB raw weights
-  unsigned char* Cring = sm + kNA * kAChunk;                  // kNC x (16 KB lo weights + B)
+  unsigned char* Aring = sm;                                  // kNA x (8 KB hi + 8 KB lo)
+  unsigned char* Bring = sm + kNA * kAStage;                  // kNC x B operand
   uint64_t* a_full = reinterpret_cast<uint64_t*>(sm + Lay::kBarOff);
   uint64_t* a_empty = a_full + kNA;
-  uint64_t* c_ready = a_empty + kNA;                          // lo parts written (128 arrivals)
-  uint64_t* b_ready = c_ready + kNC;                          // B operand written (32 arrivals)
-  uint64_t* c_empty = b_ready + kNC;
-  uint64_t* acc_full = c_empty + kNC;
+  uint64_t* b_ready = a_empty + kNA;                          // B written (32 arrivals)
+  uint64_t* b_empty = b_ready + kNC;                          // B read by the MMAs
+  uint64_t* acc_full = b_empty + kNC;
   uint64_t* acc_empty = acc_full + 2;
   uint64_t* drain = acc_empty + 2;
   uint32_t* tslot = reinterpret_cast<uint32_t*>(drain + 1);
@@ -202,14 +252,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_near_tc(const int2* __restrict_
   if (t == 32) {
     for (int s = 0; s < kNA; ++s) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(s_u32(&a_full[s])) : "memory");
-      // released by the commit of the chunk's first MMAs (the only ones that read
-      // the raw weights) and by the 128 lo-part threads once they have read them
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 129;" :: "r"(s_u32(&a_empty[s])) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(s_u32(&a_empty[s])) : "memory");
     }
     for (int s = 0; s < kNC; ++s) {
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 128;" :: "r"(s_u32(&c_ready[s])) : "memory");
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 32;" :: "r"(s_u32(&b_ready[s])) : "memory");
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(s_u32(&c_empty[s])) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(s_u32(&b_empty[s])) : "memory");
     }
     for (int s = 0; s < 2; ++s) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(s_u32(&acc_full[s])) : "memory");
@@ -231,20 +278,21 @@ __global__ void __launch_bounds__(kThreads, 1) k_near_tc(const int2* __restrict_
       bool live = true;
       for (int it = blockIdx.x; it < n_items && live; it += gridDim.x) {
         const ItemGeom ig = item_geom(it, items, tile_off, occ_start, blk_seg);
-        const uint32_t bytes = uint32_t(ig.groups) * kRowGroup;
+        const uint32_t half_bytes = uint32_t(ig.groups) * kRowGroup;
         for (int c = 0; c < ig.nchunk; ++c, ++g) {
           const int s = g % kNA, use = g / kNA;
           if (use > 0 && !wait_phase(s_u32(&a_empty[s]), (use - 1) & 1, spin, sflag)) {
             live = false;
             break;
           }
-          const float2* src = Wt + ig.off + int64_t(c) * ig.groups * (kRowGroup / 8);
-          asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
-                       :: "r"(s_u32(&a_full[s])), "r"(bytes) : "memory");
-          asm volatile(
-              "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-              :: "r"(s_u32(Aring + s * kAChunk)), "l"(src), "r"(bytes), "r"(s_u32(&a_full[s]))
-              : "memory");
+          const unsigned char* src = Wt + 8 * ig.off + int64_t(c) * 2 * half_bytes;
+          const uint32_t dst = s_u32(Aring + s * kAStage), bar = s_u32(&a_full[s]);
+          asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(bar), "r"(2 * half_bytes)
+                       : "memory");
+          asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                       :: "r"(dst), "l"(src), "r"(half_bytes), "r"(bar) : "memory");
+          asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                       :: "r"(dst + kHalf), "l"(src + half_bytes), "r"(half_bytes), "r"(bar) : "memory");
         }
       }
       // every copy issued must have landed before the block leaves (shared
@@ -252,17 +300,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_near_tc(const int2* __restrict_
       const int issued = g;
       for (int s = 0; s < kNA && s < issued; ++s) {
         const int last_use = (issued - 1 - s) / kNA;
-        if (!drain_phase(s_u32(&a_full[s]), last_use & 1))
-          asm volatile("st.volatile.shared.b32 [%0], %1;" :: "r"(s_u32(sflag)), "r"(2) : "memory");
+        if (!drain_phase(s_u32(&a_full[s]), last_use & 1)) set_flag(sflag, 2);
       }
     }
   } else if (warp == 1) {
     // ------------------------------------------------ MMA issue
     if (lane == 0) {
-      const uint32_t idesc1 =
-          (1u << 4) | (2u << 7) | (2u << 10) | (uint32_t(NN >> 3) << 17) | (uint32_t(kTcRows >> 4) << 24);
-      const uint32_t idesc2 =
-          (1u << 4) | (2u << 7) | (2u << 10) | (uint32_t((NN / 2) >> 3) << 17) | (uint32_t(kTcRows >> 4) << 24);
+      // kind::f16: D F32, A and B F16, both K-major
+      const uint32_t idesc1 = (1u << 4) | (uint32_t(NN >> 3) << 17) | (uint32_t(kTcRows >> 4) << 24);
+      const uint32_t idesc2 = (1u << 4) | (uint32_t((NN / 2) >> 3) << 17) | (uint32_t(kTcRows >> 4) << 24);
       int g = 0, tile = 0;
       bool live = true, issued = false;
       for (int it = blockIdx.x; it < n_items && live; it += gridDim.x, ++tile) {
@@ -274,47 +320,33 @@ __global__ void __launch_bounds__(kThreads, 1) k_near_tc(const int2* __restrict_
         }
         const uint32_t acc0 = tmem + uint32_t(kSets * b * NN);
         for (int c = 0; c < ig.nchunk; ++c, ++g) {
-          const int sa = g % kNA, sc = g % kNC;
-          // A x [B_hi | B_lo] as soon as the weights and B are there, A_lo x B_hi
-          // once the lo parts are written
-          if (!wait_phase(s_u32(&b_ready[sc]), (g / kNC) & 1, spin, sflag) ||
+          const int sa = g % kNA, sb = g % kNC;
+          if (!wait_phase(s_u32(&b_ready[sb]), (g / kNC) & 1, spin, sflag) ||
               !wait_phase(s_u32(&a_full[sa]), (g / kNA) & 1, spin, sflag)) {
             live = false;
             break;
           }
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-          const uint32_t a0 = s_u32(Aring + sa * kAChunk);
-          const uint32_t l0 = s_u32(Cring + sc * Lay::kSlot), b0 = l0 + kAChunk;
+          const uint32_t a0 = s_u32(Aring + sa * kAStage), b0 = s_u32(Bring + sb * Lay::kB);
 #pragma unroll
-          for (int i = 0; i < kKG / 2; ++i) {      // K = 8 per MMA: core-matrix columns 2i, 2i + 1
-            const uint64_t da = s_desc(a0 + 2 * i * 128, 128, kRowGroup);
+          for (int i = 0; i < kKG / 2; ++i) {      // K = 16 per MMA: core-matrix columns 2i, 2i + 1
+            const uint64_t dh = s_desc(a0 + 2 * i * 128, 128, kRowGroup);
+            const uint64_t dl = s_desc(a0 + kHalf + 2 * i * 128, 128, kRowGroup);
             const uint64_t db = s_desc(b0 + 2 * i * 128, 128, kRowGroup);
             const uint32_t acc = acc0 + uint32_t((i % kSets) * NN);
             const uint32_t accum = (c > 0 || i >= kSets) ? 1u : 0u;
             asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                         " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n"
-                         :: "r"(acc), "l"(da), "l"(db), "r"(idesc1), "r"(accum) : "memory");
+                         " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+                         :: "r"(acc), "l"(dh), "l"(db), "r"(idesc1), "r"(accum) : "memory");
+            asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                         " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+                         :: "r"(acc), "l"(dl), "l"(db), "r"(idesc2), "r"(1u) : "memory");
           }
           issued = true;
           asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
                        :: "r"(s_u32(&a_empty[sa])) : "memory");
-          if (!wait_phase(s_u32(&c_ready[sc]), (g / kNC) & 1, spin, sflag)) {
-            live = false;
-            issued = true;
-            break;
-          }
-          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-#pragma unroll
-          for (int i = 0; i < kKG / 2; ++i) {
-            const uint64_t dl = s_desc(l0 + 2 * i * 128, 128, kRowGroup);
-            const uint64_t db = s_desc(b0 + 2 * i * 128, 128, kRowGroup);
-            const uint32_t acc = acc0 + uint32_t((i % kSets) * NN);
-            asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                         " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n"
-                         :: "r"(acc), "l"(dl), "l"(db), "r"(idesc2), "r"(1u) : "memory");
-          }
           asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                       :: "r"(s_u32(&c_empty[sc])) : "memory");
+                       :: "r"(s_u32(&b_empty[sb])) : "memory");
         }
         if (!live) break;
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
@@ -325,56 +357,20 @@ __global__ void __launch_bounds__(kThreads, 1) k_near_tc(const int2* __restrict_
       if (issued) {
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
                      :: "r"(s_u32(drain)) : "memory");
-        if (!drain_phase(s_u32(drain), 0))
-          asm volatile("st.volatile.shared.b32 [%0], %1;" :: "r"(s_u32(sflag)), "r"(2) : "memory");
+        if (!drain_phase(s_u32(drain), 0)) set_flag(sflag, 2);
       }
     }
-  } else if (warp < 6) {
-    // ------------------------------------------------ lo parts of the weights
-    // (shared memory to shared memory: no global load in flight at the proxy fence)
-    const int ct = t - 64;     // 0..127: row of the item
-    int g = 0;
-    bool live = true;
-    for (int it = blockIdx.x; it < n_items && live; it += gridDim.x) {
-      const ItemGeom ig = item_geom(it, items, tile_off, occ_start, blk_seg);
-      for (int c = 0; c < ig.nchunk; ++c, ++g) {
-        const int sa = g % kNA, sc = g % kNC, useC = g / kNC;
-        if ((useC > 0 && !wait_phase(s_u32(&c_empty[sc]), (useC - 1) & 1, spin, sflag)) ||
-            !wait_phase(s_u32(&a_full[sa]), (g / kNA) & 1, spin, sflag)) {
-          live = false;
-          break;
-        }
-        const bool has_row = (ct >> 3) < ig.groups;
-        const int base = (ct >> 3) * kRowGroup + (ct & 7) * 16;
-        float4 x[kKG];
-        if (has_row) {
-          const unsigned char* A = Aring + sa * kAChunk;
-#pragma unroll
-          for (int kg = 0; kg < kKG; ++kg) x[kg] = *reinterpret_cast<const float4*>(A + base + kg * 128);
-        }
-        // the raw weights are in registers: this thread no longer needs the stage
-        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(s_u32(&a_empty[sa])) : "memory");
-        if (has_row) {
-          unsigned char* Lo = Cring + sc * Lay::kSlot;
-#pragma unroll
-          for (int kg = 0; kg < kKG; ++kg)
-            *reinterpret_cast<float4*>(Lo + base + kg * 128) =
-                make_float4(lo_tf32(x[kg].x), lo_tf32(x[kg].y), lo_tf32(x[kg].z), lo_tf32(x[kg].w));
-        }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(s_u32(&c_ready[sc])) : "memory");
-      }
-    }
-  } else if (warp >= 10) {
-    // ------------------------------------------------ B operands (hi and lo) from the input vectors
+  } else if (warp >= 6) {
+    // ------------------------------------------------ B operands (scaled hi and lo) from the input vectors
     // warp bw owns operand slot bw: it builds the B of chunks g = bw, bw + kNC,
-    // ... of this block, so it waits for every phase of its slot's barrier in
-    // turn (a waiter that skipped a phase would see an earlier phase of the
-    // same parity as complete).  Value v = lane + 32 i of a chunk is
-    // (RHS j = v % R, column cc = v / R).
+    // ... of this block.  Value v = lane + 32 i of a chunk is (RHS j = v % R,
+    // column cc = v / R).
     constexpr int kVals = R * kKC / 32;
     static_assert(R * kKC % 32 == 0, "B entries per lane");
-    const int bw = warp - 10;
+    const int bw = warp - 6;
+    float ts[R];
+#pragma unroll
+    for (int j = 0; j < R; ++j) ts[j] = pow2_scale(__uint_as_float(tmax[j]));
     int g = 0;
     bool live = true;
     for (int it = blockIdx.x; it < n_items && live; it += gridDim.x) {
@@ -384,8 +380,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_near_tc(const int2* __restrict_
       const int p0 = (l0 + 1) & ~1, p1 = (l1 + 1) & ~1;
       for (int c = 0; c < ig.nchunk; ++c, ++g) {
         if (g % kNC != bw) continue;
-        const int useC = g / kNC;
-        if (useC > 0 && !wait_phase(s_u32(&c_empty[bw]), (useC - 1) & 1, spin, sflag)) {
+        const int use = g / kNC;
+        if (use > 0 && !wait_phase(s_u32(&b_empty[bw]), (use - 1) & 1, spin, sflag)) {
           live = false;
           break;
         }
@@ -399,31 +395,38 @@ __global__ void __launch_bounds__(kThreads, 1) k_near_tc(const int2* __restrict_
           else if (col < ig.nblk) { const int o = col - p0 - p1; if (o < l2) node = sg[4] + o; }
           uv[i] = node >= 0 ? u[int64_t(j) * N + node] : make_float2(0.f, 0.f);
         }
-        unsigned char* B = Cring + bw * Lay::kSlot + kAChunk;
+        unsigned char* B = Bring + bw * Lay::kB;
 #pragma unroll
         for (int i = 0; i < kVals; ++i) {
           const int v = lane + 32 * i, j = v % R, cc = v / R;
-          const float ur = uv[i].x, ui = uv[i].y;
-          put_b(B, j, 2 * cc, make_float2(ur, -ui));
-          put_b(B, R + j, 2 * cc, make_float2(ui, ur));
-          put_b(B, 2 * R + j, 2 * cc, make_float2(lo_tf32(ur), lo_tf32(-ui)));
-          put_b(B, 3 * R + j, 2 * cc, make_float2(lo_tf32(ui), lo_tf32(ur)));
+          const float ur = uv[i].x * ts[j], ui = uv[i].y * ts[j];
+          __half rh, rl, ih, il, mh, ml;
+          split16(ur, rh, rl);
+          split16(ui, ih, il);
+          split16(-ui, mh, ml);
+          put_b(B, j, 2 * cc, rh, mh);             // real-part rows: (Re, -Im)
+          put_b(B, R + j, 2 * cc, ih, rh);         // imaginary-part rows: (Im, Re)
+          put_b(B, 2 * R + j, 2 * cc, rl, ml);
+          put_b(B, 3 * R + j, 2 * cc, il, rl);
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(s_u32(&b_ready[bw])) : "memory");
       }
     }
   } else {
-    // ------------------------------------------------ epilogue
+    // ------------------------------------------------ epilogue (warps 2..5)
     const int row_in = 32 * (warp & 3) + lane;     // tensor-memory lane quarter of this warp
+    float inv_t[R];
+#pragma unroll
+    for (int j = 0; j < R; ++j) inv_t[j] = 1.f / pow2_scale(__uint_as_float(tmax[j]));
     int tile = 0;
     for (int it = blockIdx.x; it < n_items; it += gridDim.x, ++tile) {
       const ItemGeom ig = item_geom(it, items, tile_off, occ_start, blk_seg);
       const int b = tile & 1, bu = tile >> 1;
       float d[NN], d2[NN];
       // the warp's lanes decide together (tcgen05.ld is warp-collective)
-      if (!__all_sync(0xffffffffu, wait_phase(s_u32(&acc_full[b]), bu & 1, spin, sflag))) {
-        asm volatile("st.volatile.shared.b32 [%0], %1;" :: "r"(s_u32(sflag)), "r"(1) : "memory");
+      if (!__all_sync(0xffffffffu, wait_phase<false>(s_u32(&acc_full[b]), bu & 1, spin, sflag))) {
+        set_flag(sflag, 1);
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -445,10 +448,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_near_tc(const int2* __restrict_
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(s_u32(&acc_empty[b])) : "memory");
       if (row_in < ig.nrow) {
+        const int64_t q = occ_start[ig.k] + ig.row0 + row_in;
+        const float rs = rscale[q];
         float2 acc[R];
 #pragma unroll
-        for (int j = 0; j < R; ++j) acc[j] = make_float2(d[j] + d[2 * R + j], d[R + j] + d[3 * R + j]);
-        const int64_t q = occ_start[ig.k] + ig.row0 + row_in;
+        for (int j = 0; j < R; ++j) {
+          const float f = rs * inv_t[j];
+          acc[j] = make_float2((d[j] + d[2 * R + j]) * f, (d[R + j] + d[3 * R + j]) * f);
+        }
         for (int64_t e = rem_row[q]; e < rem_row[q + 1]; ++e) {
           const float2 w = rem_val[e];
           const int cidx = rem_col[e];
@@ -479,39 +486,67 @@ __global__ void __launch_bounds__(kThreads, 1) k_near_tc(const int2* __restrict_
   }
 }
 
-// tile layout of the weights from the row-major blocks: block = work item,
-// float2 element (chunk c, row m, column cc) at
-//   off + (c * groups + m / 8) * 128 + (cc / 2) * 16 + (m % 8) * 2 + cc % 2
-// zero past the block's columns
-__global__ void k_tile_weights(const int2* __restrict__ items, const int64_t* __restrict__ tile_off,
-                               const int64_t* __restrict__ occ_start, const int64_t* __restrict__ blk_off,
-                               const int* __restrict__ blk_seg, const float2* __restrict__ Wb,
-                               float2* __restrict__ Wt) {
+// tile layout of the weights from the row-major blocks: block = work item.
+// Row scales first (s_m puts the row's largest |Re|, |Im| in [2^14, 2^15);
+// rscale[q] = 1 / s_m for the row's node q), then per chunk c and row group
+// the hi parts, then the lo parts: fp16 element (row m, real index k of the
+// chunk) at byte (c * 2 * groups + part * groups + m / 8) * 512 + (k / 8) * 128
+// + (m % 8) * 16 + (k % 8) * 2 from the item's start; zero past the columns
+__global__ void __launch_bounds__(256) k_tile_weights(const int2* __restrict__ items,
+                                                      const int64_t* __restrict__ tile_off,
+                                                      const int64_t* __restrict__ occ_start,
+                                                      const int64_t* __restrict__ blk_off,
+                                                      const int* __restrict__ blk_seg, const float2* __restrict__ Wb,
+                                                      unsigned char* __restrict__ Wt, float* __restrict__ rscale) {
+  __shared__ float srow[kTcRows];
   const ItemGeom ig = item_geom(blockIdx.x, items, tile_off, occ_start, blk_seg);
   const float2* src = Wb + blk_off[ig.k] + int64_t(ig.row0) * ig.nblk;
-  const int64_t total = int64_t(ig.nchunk) * ig.groups * 128;
+  for (int m = threadIdx.x; m < kTcRows; m += blockDim.x) {
+    float mx = 0.f;
+    if (m < ig.nrow)
+      for (int c = 0; c < ig.nblk; ++c) {
+        const float2 w = src[int64_t(m) * ig.nblk + c];
+        mx = fmaxf(mx, fmaxf(fabsf(w.x), fabsf(w.y)));
+      }
+    const float s = pow2_scale(mx);
+    srow[m] = s;
+    if (m < ig.nrow) rscale[occ_start[ig.k] + ig.row0 + m] = 1.f / s;
+  }
+  __syncthreads();
+  __half* dst = reinterpret_cast<__half*>(Wt + 8 * ig.off);
+  const int64_t per_half = int64_t(ig.groups) * kRowGroup / 2;   // fp16 elements of a chunk's hi (or lo) part
+  const int64_t total = int64_t(ig.nchunk) * 2 * per_half;
   for (int64_t e = threadIdx.x; e < total; e += blockDim.x) {
-    const int64_t cg = e / 128;
-    const int w = int(e % 128);
-    const int c = int(cg / ig.groups), grp = int(cg % ig.groups);
-    const int m = grp * 8 + (w >> 1) % 8, cc = (w >> 4) * 2 + (w & 1);
-    const int col = c * kKC + cc;
-    float2 v = make_float2(0.f, 0.f);
-    if (m < ig.nrow && col < ig.nblk) v = src[int64_t(m) * ig.nblk + col];
-    Wt[ig.off + e] = v;
+    const int64_t ch = e / (2 * per_half);
+    const int64_t w = e % (2 * per_half);
+    const int part = int(w / per_half);                  // 0 hi, 1 lo
+    const int64_t x = w % per_half;
+    const int grp = int(x / (kRowGroup / 2)), y = int(x % (kRowGroup / 2));
+    const int kgi = y / 64, m = grp * 8 + (y / 8) % 8, k = kgi * 8 + y % 8;
+    const int col = int(ch) * kKC + k / 2;
+    float v = 0.f;
+    if (m < ig.nrow && col < ig.nblk) {
+      const float2 wv = src[int64_t(m) * ig.nblk + col];
+      v = (k & 1 ? wv.y : wv.x) * srow[m];
+    }
+    __half hi, lo;
+    split16(v, hi, lo);
+    dst[e] = part == 0 ? hi : lo;
   }
 }
 
 }  // namespace
 
 int64_t tc_tile_elems(int nrow, int nblk) {
+  // hi and lo fp16 parts together take the bytes of the complex64 values
   const int groups = (std::min(nrow, kTcRows) + 7) / 8;
-  return int64_t((nblk + kKC - 1) / kKC) * groups * (kRowGroup / 8);
+  return int64_t((nblk + kKC - 1) / kKC) * groups * (2 * kRowGroup / 8);
 }
 
-cudaError_t tile_weights(const ApplyData<float2>& d, float2* Wt, cudaStream_t st) {
+cudaError_t tile_weights(const ApplyData<float2>& d, float2* Wt, float* rscale, cudaStream_t st) {
   if (d.n_items128 == 0) return cudaSuccess;
-  k_tile_weights<<<d.n_items128, 256, 0, st>>>(d.items128, d.tile_off, d.occ_start, d.blk_off, d.blk_seg, d.Wb, Wt);
+  k_tile_weights<<<d.n_items128, 256, 0, st>>>(d.items128, d.tile_off, d.occ_start, d.blk_off, d.blk_seg, d.Wb,
+                                               reinterpret_cast<unsigned char*>(Wt), rscale);
   return cudaGetLastError();
 }
 
@@ -531,10 +566,14 @@ cudaError_t near_eval_tc(const ApplyData<float2>& d, const float2* u, float2* ou
     }
   }
   if (d.n_items128 == 0) return cudaSuccess;
+  cudaError_t e0 = cudaMemsetAsync(d.tc_tmax, 0, sizeof(unsigned) * R, st);
+  if (e0 != cudaSuccess) return e0;
+  k_rhs_max<<<dim3(kScaleBlocks, R), 256, 0, st>>>(u, d.N, d.tc_tmax);
   const int sms = (dev >= 0 && dev < 64 && n_sm[dev] > 0) ? n_sm[dev] : 148;
   const int grid = d.n_items128 < sms ? d.n_items128 : sms;
   k_near_tc<R><<<grid, kThreads, Lay::kBytes, st>>>(d.items128, d.n_items128, d.tile_off, d.occ_start, d.blk_seg,
-                                                     d.Wt, d.rem_row, d.rem_col, d.rem_val, u, d.N, d.Phi,
+                                                     reinterpret_cast<const unsigned char*>(d.Wt), d.tc_rscale,
+                                                     d.tc_tmax, d.rem_row, d.rem_col, d.rem_val, u, d.N, d.Phi,
                                                      d.gamma, d.nocc, d.nfb2, float(d.kappa2), out, d.tc_err,
                                                      d.tc_spin);
   return cudaGetLastError();

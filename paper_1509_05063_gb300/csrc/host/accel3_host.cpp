@@ -177,7 +177,6 @@ bool build_accel3(Accel3& A3, const double* xyz, const double* wfac, int64_t N) 
     return kind == 0 ? mono3(kappa, dx, dy, dz) : dip3(kappa, dx, dy, dz);
   };
   A3.BT.assign(size_t(27) * nb * n_es, cd(0.0));
-  if (A3.keep_T) A3.T.assign(size_t(27) * n_loc * n_es, cd(0.0));
   parallel_for(A3.n_threads, 27, 1, [&](int64_t o0, int64_t o1) {
     for (int64_t o = o0; o < o1; ++o) {
       const int oi = int(o / 9) - 1, oj = int((o / 3) % 3) - 1, ok = int(o % 3) - 1;
@@ -190,7 +189,6 @@ bool build_accel3(Accel3& A3, const double* xyz, const double* wfac, int64_t N) 
                   table(a - (ea[l] + oi * Ne), b - (eb[l] + oj * Ne), c - (ec[l] + ok * Ne), ek[l]);
       const std::vector<cd> X = svd_solve(fB, T, n_es);
       std::copy(X.begin(), X.end(), A3.BT.begin() + size_t(o) * nb * n_es);
-      if (A3.keep_T) std::copy(T.begin(), T.end(), A3.T.begin() + size_t(o) * n_loc * n_es);
     }
   });
   // evaluation rows at the nodes (input order)

@@ -121,8 +121,6 @@ struct Accel3 {
   std::vector<cd> BT;                   // 27 x nb x n_es
   std::vector<cd> Phi;                  // N x nb (input node order)
   std::vector<cd> Gtab, Dtab;           // M^3 kernel lattice tables ([da][db][dc])
-  bool keep_T = false;                  // also keep the neighbour tables themselves:
-  std::vector<cd> T;                    // 27 x n_loc x n_es, T_o (when keep_T)
   std::string err;
 };
 bool build_accel3(Accel3& a, const double* xyz, const double* wfac, int64_t N);
