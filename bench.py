@@ -364,7 +364,7 @@ def main():
                     help="incident directions of the lock-step mixed solve (theta_j = 2 pi j / D)")
     ap.add_argument("--batch", type=int, default=12,
                     help="also time a multi-instance batch of this many seeded scatterers (reduced config 3)")
-    ap.add_argument("--sphere", default="25,9,0.1,7,6",
+    ap.add_argument("--sphere", default="25,9,0.1,7,4",
                     help="reduced config 4 (penetrable sphere, kappa = 8): n_f,n_s,h,L,N_eq; 'none' to skip")
     ap.add_argument("--scale", type=int, default=1,
                     help="coarsen config 2 by this factor (h, cells) for profiling captures")

@@ -14,6 +14,7 @@
 #include <tuple>
 #include <string>
 #include <thread>
+#include <queue>
 #include <vector>
 
 #include "device/kernels.cuh"
@@ -824,6 +825,43 @@ ls_status ls_plan_create(const ls_geometry* geom, ls_n2_fn n2, void* ctx, double
   }
   const int64_t* d_tile_off = UP(int64_t, tile_off);
   int* d_tc_err = UP(int, std::vector<int>(1, 0));
+  // the persistent tensor-core grid (one block per SM) takes its 128-row items
+  // from per-block lists balanced by longest-processing-time-first: an item
+  // costs its chunk count times the larger of the MMA issue time (a fixed
+  // number of instructions per chunk, whatever the rows) and the copy time of
+  // its row groups (half the MMA time for a chunk of 16 groups)
+  int n_sm = 0;
+  if (cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, plan->device) != cudaSuccess || n_sm <= 0)
+    return bail(LS_ERR_CUDA, "cudaDeviceGetAttribute(multiProcessorCount) failed");
+  const int n_it128 = int(items128.size() / 2);
+  const int tc_grid = std::max(1, std::min(n_it128, n_sm));
+  std::vector<int> tc_bptr(tc_grid + 1, 0), tc_blist(n_it128);
+  {
+    std::vector<std::pair<double, int>> cost(n_it128);
+    for (int i = 0; i < n_it128; ++i) {
+      const int k = items128[2 * i], r = items128[2 * i + 1];
+      const int* sg = &blk_seg[6 * k];
+      const int64_t nblk = padded(sg[1]) + padded(sg[3]) + padded(sg[5]);
+      const int64_t rows = std::min<int64_t>(128, occ_start[k + 1] - occ_start[k] - r);
+      cost[i] = {double((nblk + 15) / 16) * std::max(0.5, double((rows + 7) / 8) / 16.0), i};
+    }
+    std::stable_sort(cost.begin(), cost.end(), [](const auto& x, const auto& y) { return x.first > y.first; });
+    std::priority_queue<std::pair<double, int>, std::vector<std::pair<double, int>>, std::greater<>> load;
+    for (int b = 0; b < tc_grid; ++b) load.push({0.0, b});
+    std::vector<std::vector<int>> per(tc_grid);
+    for (const auto& c : cost) {
+      auto top = load.top();
+      load.pop();
+      per[top.second].push_back(c.second);
+      load.push({top.first + c.first, top.second});
+    }
+    for (int b = 0, n = 0; b < tc_grid; ++b) {
+      for (int i : per[b]) tc_blist[n++] = i;
+      tc_bptr[b + 1] = n;
+    }
+  }
+  const int* d_tc_bptr = UP(int, tc_bptr);
+  const int* d_tc_blist = UP(int, tc_blist);
   const int64_t* d_blk_off = UP(int64_t, blk_off);
   const int* d_blk_seg = UP(int, blk_seg);
   const int64_t* d_rem_row = UP(int64_t, rem_row);
@@ -956,6 +994,9 @@ ls_status ls_plan_create(const ls_geometry* geom, ls_n2_fn n2, void* ctx, double
   b.items32 = a.items32; b.n_items32 = a.n_items32;
   b.items128 = d_items128; b.n_items128 = int(items128.size() / 2);
   b.tile_off = d_tile_off;
+  b.tc_bptr = d_tc_bptr;
+  b.tc_blist = d_tc_blist;
+  b.tc_grid = tc_grid;
   b.tc_err = d_tc_err;
   b.P = UP(float2, to32(P.P32));
   b.LA = UP(float2, to32(LA));

@@ -5,8 +5,10 @@
 //
 //   k3_project    sigma_c = P_c u_c                      (two-face equivalent sources)
 //   k3_fill       sigma -> monopole / dipole values on the x1-face planes of the lattice
-//   k3_fft_axis   batched line FFTs along one axis of the M^3 lattice (three per transform)
-//   k3_spectral   V^ = S_m^ G^ + S_d^ D^
+//   k3_fft_axis   batched line FFTs along one axis of the M^3 lattice, over the
+//                 box of lines that can be nonzero (forward) or are read (inverse)
+//   k3_conv_a     the a-axis stage: forward lines of both arrays, V^ = S_m^ G^ + S_d^ D^,
+//                 inverse line, in one pass (k3_spectral when M > 1024)
 //   k3_gather, k3_gemm, k3_reduce
 //                 gamma_c = B^+ V_c - sum_o (B^+ T_o) sigma_{c+o}   (27 neighbours; one GEMM over cells)
 //   k3_near       out_q = u_q + kappa^2 (sum_l W_ql u_l + Phi_q . gamma_c)
@@ -88,34 +90,79 @@ __global__ void __launch_bounds__(kT3) k3_fill(ApplyData3<T> d) {
   }
 }
 
-// line transforms along one axis of an M^3 array; a block takes LPB = 2048 / M
-// lines whose elements are adjacent in memory (consecutive c for the a and b
-// axes, consecutive lines for the c axis), so that loads and stores coalesce;
-// M / 8 threads per line; lines padded to M + 1 in shared memory
+// line transforms along one axis of an M^3 array ([a][b][c], c fastest) over
+// a box of lines: line j = o n_in + i (o < n_out, i < n_in) has outer
+// coordinate o ostep and inner coordinate i, where (outer, inner) is (a, b)
+// for the c axis (axis 2), (a, c) for the b axis (1) and (b, c) for the a
+// axis (0).  A block takes LPB = 2048 / M consecutive lines of the box, M / 8
+// threads per line, lines padded to M + 1 in shared memory; loads and stores
+// run along c (within a line for axis 2, across consecutive lines otherwise),
+// so that they coalesce.  Lines outside the box are not touched: the lattice
+// convolution skips the lines it knows to be zero on input or unread later.
+struct LineBox {
+  int axis, n_out, ostep, n_in;
+};
+
+__device__ __forceinline__ int64_t line_addr(const LineBox& bx, int M, int64_t j, int e) {
+  const int64_t MM = int64_t(M) * M;
+  const int64_t o = (j / bx.n_in) * bx.ostep, i = j % bx.n_in;
+  if (bx.axis == 2) return o * MM + i * M + e;
+  if (bx.axis == 1) return o * MM + int64_t(e) * M + i;
+  return o * M + i + int64_t(e) * MM;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kT3) k3_fft_axis(T* __restrict__ X, int M, int logM, const T* __restrict__ tw,
-                                                  bool inv, int axis) {
+                                                  bool inv, LineBox bx) {
   extern __shared__ __align__(16) unsigned char raw3[];
   T* s = reinterpret_cast<T*>(raw3);
   const int G = M / 8, LPB = kT3 / G, t = threadIdx.x;
-  const int64_t MM = int64_t(M) * M;
-  const int64_t l0 = int64_t(blockIdx.x) * LPB;
-  auto addr = [&](int j, int e) -> int64_t {
-    const int64_t l = l0 + j;
-    if (axis == 2) return l * M + e;
-    if (axis == 1) return (l / M) * MM + (l % M) + int64_t(e) * M;
-    return l + int64_t(e) * MM;
-  };
+  const int64_t l0 = int64_t(blockIdx.x) * LPB, nl = int64_t(bx.n_out) * bx.n_in;
   for (int idx = t; idx < LPB * M; idx += kT3) {
-    const int j = axis == 2 ? idx / M : idx % LPB, e = axis == 2 ? idx % M : idx / LPB;
-    s[j * (M + 1) + e] = X[addr(j, e)];
+    const int j = bx.axis == 2 ? idx / M : idx % LPB, e = bx.axis == 2 ? idx % M : idx / LPB;
+    s[j * (M + 1) + e] = l0 + j < nl ? X[line_addr(bx, M, l0 + j, e)] : czero(T());
   }
   __syncthreads();
   fft_smem<T>(s + (t / G) * (M + 1), M, logM, inv, tw, t % G);
   __syncthreads();
   for (int idx = t; idx < LPB * M; idx += kT3) {
-    const int j = axis == 2 ? idx / M : idx % LPB, e = axis == 2 ? idx % M : idx / LPB;
-    X[addr(j, e)] = s[j * (M + 1) + e];
+    const int j = bx.axis == 2 ? idx / M : idx % LPB, e = bx.axis == 2 ? idx % M : idx / LPB;
+    if (l0 + j < nl) X[line_addr(bx, M, l0 + j, e)] = s[j * (M + 1) + e];
+  }
+}
+
+// the a-axis stage of the lattice convolution in one pass over the (b, c)
+// lines: forward transforms of a monopole and a dipole line, V^ = S_m^ G^ +
+// S_d^ D^, inverse transform, V written back into Sm for a <= a_max only (the
+// later stages read no more).  H = 1024 / M line pairs per block: shared
+// slots [0, H) hold monopole lines, [H, 2H) dipole lines.
+template <typename T>
+__global__ void __launch_bounds__(kT3) k3_conv_a(T* __restrict__ Sm, const T* __restrict__ Sd,
+                                                const T* __restrict__ Gs, const T* __restrict__ Ds, int M,
+                                                int logM, const T* __restrict__ tw, int a_max) {
+  extern __shared__ __align__(16) unsigned char raw3[];
+  T* s = reinterpret_cast<T*>(raw3);
+  const int G = M / 8, LPB = kT3 / G, H = LPB / 2, t = threadIdx.x;
+  const int64_t MM = int64_t(M) * M, l0 = int64_t(blockIdx.x) * H;
+  for (int idx = t; idx < LPB * M; idx += kT3) {
+    const int j = idx % LPB, e = idx / LPB;
+    s[j * (M + 1) + e] = (j < H ? Sm : Sd)[l0 + (j % H) + int64_t(e) * MM];
+  }
+  __syncthreads();
+  fft_smem<T>(s + (t / G) * (M + 1), M, logM, false, tw, t % G);
+  __syncthreads();
+  for (int idx = t; idx < H * M; idx += kT3) {
+    const int j = idx % H, e = idx / H;
+    const int64_t ad = l0 + j + int64_t(e) * MM;
+    T* v = s + j * (M + 1) + e;
+    *v = cfma(v[H * (M + 1)], Ds[ad], cmul(*v, Gs[ad]));
+  }
+  __syncthreads();
+  fft_smem<T>(s + (t / G) * (M + 1), M, logM, true, tw, t % G, 1, t / G < H);
+  __syncthreads();
+  for (int idx = t; idx < H * M; idx += kT3) {
+    const int j = idx % H, e = idx / H;
+    if (e <= a_max) Sm[l0 + j + int64_t(e) * MM] = s[j * (M + 1) + e];
   }
 }
 
@@ -300,16 +347,57 @@ int grid_for(int64_t n) {
   return int(b < 152 * 16 ? b : 152 * 16);
 }
 
-// lattice convolution and local coefficients: sigma -> gamma on one precision's data
+size_t fft_smem_bytes(int M, size_t elem) { return elem * size_t(kT3 / (M / 8)) * (M + 1); }
+
+template <typename T>
+cudaError_t fft_box(T* x, int M, int logM, const T* tw, bool inverse, LineBox bx, cudaStream_t st) {
+  static unsigned long long attr = 0;
+  if (first_on_device(attr)) {
+    const cudaError_t e = cudaFuncSetAttribute(k3_fft_axis<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
+    if (e != cudaSuccess) return e;
+  }
+  const int LPB = kT3 / (M / 8);
+  const int64_t lines = int64_t(bx.n_out) * bx.n_in;
+  k3_fft_axis<T><<<int((lines + LPB - 1) / LPB), kT3, fft_smem_bytes(M, sizeof(T)), st>>>(x, M, logM, tw, inverse, bx);
+  return cudaGetLastError();
+}
+
+// lattice convolution and local coefficients: sigma -> gamma on one
+// precision's data.  The sources sit on the x1-face planes a = f N_eq
+// (f = 0..L) inside [0, L N_eq]^3 and V is read inside [0, L N_eq]^3 only, so
+// the forward c and b stages run on the face planes' lines alone, the inverse
+// b and c stages on the lines with a (and b) <= L N_eq; the a stage (every
+// (b, c) line) carries the spectral product.
 template <typename T>
 cudaError_t lattice_local(const ApplyData3<T>& d, cudaStream_t st) {
   const int64_t n3 = int64_t(d.M) * d.M * d.M;
+  const int M = d.M, nl = d.L * d.Ne;
   k3_fill<T><<<grid_for(n3), kT3, 0, st>>>(d);
-  cudaError_t e = fft3d<T>(d.Sm, d.M, d.logM, d.tw, false, st);
-  if (e == cudaSuccess) e = fft3d<T>(d.Sd, d.M, d.logM, d.tw, false, st);
+  cudaError_t e = cudaSuccess;
+  T* const both[2] = {d.Sm, d.Sd};
+  for (T* x : both) {
+    if (e == cudaSuccess) e = fft_box<T>(x, M, d.logM, d.tw, false, LineBox{2, d.L + 1, d.Ne, nl + 1}, st);
+    if (e == cudaSuccess) e = fft_box<T>(x, M, d.logM, d.tw, false, LineBox{1, d.L + 1, d.Ne, M}, st);
+  }
   if (e != cudaSuccess) return e;
-  k3_spectral<T><<<grid_for(n3), kT3, 0, st>>>(d.Sm, d.Sd, d.Gs, d.Ds, n3);
-  e = fft3d<T>(d.Sm, d.M, d.logM, d.tw, true, st);
+  if (M <= 1024) {
+    static unsigned long long attr = 0;
+    if (first_on_device(attr)) {
+      e = cudaFuncSetAttribute(k3_conv_a<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
+      if (e != cudaSuccess) return e;
+    }
+    const int H = kT3 / (M / 8) / 2;
+    k3_conv_a<T><<<int(int64_t(M) * M / H), kT3, fft_smem_bytes(M, sizeof(T)), st>>>(d.Sm, d.Sd, d.Gs, d.Ds, M, d.logM,
+                                                                                   d.tw, nl);
+  } else {
+    for (T* x : both)
+      if (e == cudaSuccess) e = fft_box<T>(x, M, d.logM, d.tw, false, LineBox{0, M, 1, M}, st);
+    if (e != cudaSuccess) return e;
+    k3_spectral<T><<<grid_for(n3), kT3, 0, st>>>(d.Sm, d.Sd, d.Gs, d.Ds, n3);
+    e = fft_box<T>(d.Sm, M, d.logM, d.tw, true, LineBox{0, M, 1, M}, st);
+  }
+  if (e == cudaSuccess) e = fft_box<T>(d.Sm, M, d.logM, d.tw, true, LineBox{1, nl + 1, 1, M}, st);
+  if (e == cudaSuccess) e = fft_box<T>(d.Sm, M, d.logM, d.tw, true, LineBox{2, nl + 1, 1, nl + 1}, st);
   if (e != cudaSuccess) return e;
   const int K = d.n_loc + 27 * d.n_es, S = local_slices(d.nocc, d.nb, K);
   k3_gather<T><<<d.nocc, kT3, 0, st>>>(d);
@@ -346,17 +434,10 @@ int local3_slices(int nocc, int nb, int K) { return local_slices(nocc, nb, K); }
 template <typename T>
 cudaError_t fft3d(T* x, int M, int logM, const T* tw, bool inverse, cudaStream_t st) {
   if (M < 16 || M > 2048 || (M & (M - 1))) return cudaErrorInvalidValue;
-  const int LPB = kT3 / (M / 8);
-  const int64_t lines = int64_t(M) * M;
-  const size_t smem = sizeof(T) * size_t(LPB) * (M + 1);
-  static unsigned long long attr = 0;
-  if (first_on_device(attr)) {
-    const cudaError_t e = cudaFuncSetAttribute(k3_fft_axis<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
-    if (e != cudaSuccess) return e;
-  }
-  for (int axis = 2; axis >= 0; --axis)
-    k3_fft_axis<T><<<int(lines / LPB), kT3, smem, st>>>(x, M, logM, tw, inverse, axis);
-  return cudaGetLastError();
+  cudaError_t e = cudaSuccess;
+  for (int axis = 2; axis >= 0 && e == cudaSuccess; --axis)
+    e = fft_box<T>(x, M, logM, tw, inverse, LineBox{axis, M, 1, M}, st);
+  return e;
 }
 
 template <typename T>

@@ -54,6 +54,9 @@ struct ApplyData {
   const int2* items128 = nullptr;       // 128-row items (tensor-core near field, 8 or 16 complex64 RHS)
   int n_items128 = 0;
   const int64_t* tile_off = nullptr;    // complex64 only: offset of each 128-row item in Wt
+  const int* tc_bptr = nullptr;         // tensor-core grid: block b walks items tc_blist[tc_bptr[b] .. tc_bptr[b + 1])
+  const int* tc_blist = nullptr;
+  int tc_grid = 0;                      // blocks of the tensor-core grid (one per SM of the plan's device)
   const T* Wt = nullptr;                // complex64 only: the blocks in the tensor-core tile layout
   const float* tc_rscale = nullptr;     // complex64 only: 1 / (power-of-two scale) of each near-field row
   unsigned* tc_tmax = nullptr;          // complex64 only: per-RHS largest |Re|, |Im| of one apply (float bits)

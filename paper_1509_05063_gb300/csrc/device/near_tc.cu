@@ -34,8 +34,8 @@
 // parts in the same layout.  Two bulk copies (cp.async.bulk, completion
 // counted on an mbarrier) move a chunk from HBM into a weight stage.
 //
-// Persistent, warp-specialised, one block per SM walking the work items
-// blockIdx.x, blockIdx.x + gridDim.x, ... (heaviest first):
+// Persistent, warp-specialised, one block per SM walking its own list of work
+// items (lists balanced at plan time, longest first):
 //   warp 0      lane 0 issues the bulk copies into a ring of kNA weight stages;
 //   warp 1      lane 0 issues the MMAs and commits them to the release barriers;
 //   warps 2..5  (128 threads) per item: read the accumulator from tensor memory
@@ -212,7 +212,8 @@ __global__ void __launch_bounds__(256) k_rhs_max(const float2* __restrict__ u, i
 }
 
 template <int R>
-__global__ void __launch_bounds__(kThreads, 1) k_near_tc(const int2* __restrict__ items, int n_items,
+__global__ void __launch_bounds__(kThreads, 1) k_near_tc(const int2* __restrict__ items, const int* __restrict__ bptr,
+                                                         const int* __restrict__ blist,
                                                          const int64_t* __restrict__ tile_off,
                                                          const int64_t* __restrict__ occ_start,
                                                          const int* __restrict__ blk_seg,
@@ -243,6 +244,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_near_tc(const int2* __restrict_
   int* sflag = reinterpret_cast<int*>(tslot + 1);
 
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  const int p_begin = bptr[blockIdx.x], p_end = bptr[blockIdx.x + 1];   // this block's items
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
@@ -276,7 +278,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_near_tc(const int2* __restrict_
     if (lane == 0) {
       int g = 0;   // chunk counter of this block
       bool live = true;
-      for (int it = blockIdx.x; it < n_items && live; it += gridDim.x) {
+      for (int ip = p_begin; ip < p_end && live; ++ip) {
+        const int it = blist[ip];
         const ItemGeom ig = item_geom(it, items, tile_off, occ_start, blk_seg);
         const uint32_t half_bytes = uint32_t(ig.groups) * kRowGroup;
         for (int c = 0; c < ig.nchunk; ++c, ++g) {
@@ -311,7 +314,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_near_tc(const int2* __restrict_
       const uint32_t idesc2 = (1u << 4) | (uint32_t((NN / 2) >> 3) << 17) | (uint32_t(kTcRows >> 4) << 24);
       int g = 0, tile = 0;
       bool live = true, issued = false;
-      for (int it = blockIdx.x; it < n_items && live; it += gridDim.x, ++tile) {
+      for (int ip = p_begin; ip < p_end && live; ++ip, ++tile) {
+        const int it = blist[ip];
         const ItemGeom ig = item_geom(it, items, tile_off, occ_start, blk_seg);
         const int b = tile & 1, bu = tile >> 1;
         if (bu > 0 && !wait_phase(s_u32(&acc_empty[b]), (bu - 1) & 1, spin, sflag)) {
@@ -373,7 +377,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_near_tc(const int2* __restrict_
     for (int j = 0; j < R; ++j) ts[j] = pow2_scale(__uint_as_float(tmax[j]));
     int g = 0;
     bool live = true;
-    for (int it = blockIdx.x; it < n_items && live; it += gridDim.x) {
+    for (int ip = p_begin; ip < p_end && live; ++ip) {
+      const int it = blist[ip];
       const ItemGeom ig = item_geom(it, items, tile_off, occ_start, blk_seg);
       const int* sg = blk_seg + 6 * ig.k;
       const int l0 = sg[1], l1 = sg[3], l2 = sg[5];
@@ -420,7 +425,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_near_tc(const int2* __restrict_
 #pragma unroll
     for (int j = 0; j < R; ++j) inv_t[j] = 1.f / pow2_scale(__uint_as_float(tmax[j]));
     int tile = 0;
-    for (int it = blockIdx.x; it < n_items; it += gridDim.x, ++tile) {
+    for (int ip = p_begin; ip < p_end; ++ip, ++tile) {
+      const int it = blist[ip];
       const ItemGeom ig = item_geom(it, items, tile_off, occ_start, blk_seg);
       const int b = tile & 1, bu = tile >> 1;
       float d[NN], d2[NN];
@@ -569,9 +575,10 @@ cudaError_t near_eval_tc(const ApplyData<float2>& d, const float2* u, float2* ou
   cudaError_t e0 = cudaMemsetAsync(d.tc_tmax, 0, sizeof(unsigned) * R, st);
   if (e0 != cudaSuccess) return e0;
   k_rhs_max<<<dim3(kScaleBlocks, R), 256, 0, st>>>(u, d.N, d.tc_tmax);
-  const int sms = (dev >= 0 && dev < 64 && n_sm[dev] > 0) ? n_sm[dev] : 148;
-  const int grid = d.n_items128 < sms ? d.n_items128 : sms;
-  k_near_tc<R><<<grid, kThreads, Lay::kBytes, st>>>(d.items128, d.n_items128, d.tile_off, d.occ_start, d.blk_seg,
+  // the per-block item lists were balanced for the plan device's SM count
+  const int sms = (dev >= 0 && dev < 64 && n_sm[dev] > 0) ? n_sm[dev] : 0;
+  if (d.tc_grid <= 0 || d.tc_grid > sms || !d.tc_bptr || !d.tc_blist) return cudaErrorInvalidConfiguration;
+  k_near_tc<R><<<d.tc_grid, kThreads, Lay::kBytes, st>>>(d.items128, d.tc_bptr, d.tc_blist, d.tile_off, d.occ_start, d.blk_seg,
                                                      reinterpret_cast<const unsigned char*>(d.Wt), d.tc_rscale,
                                                      d.tc_tmax, d.rem_row, d.rem_col, d.rem_val, u, d.N, d.Phi,
                                                      d.gamma, d.nocc, d.nfb2, float(d.kappa2), out, d.tc_err,
