@@ -33,13 +33,17 @@ sys.path.insert(0, ROOT)
 
 METRIC = "LS matvecs/s and time to 1e-10 solve at N, mixed vs FP64 path, 1 GB300"
 FALLBACK_HBM_GBS = 6800.0
+FALLBACK_BF16_TFLOPS = 1900.0
 KERNELS_PER_APPLY = 6    # projection, source rows (fill + row FFT), columns (FFT, product, inverse),
 #                          inverse rows, local coefficients, near field + assembly
-# DRAM bytes (read + write) per launch of the near-field kernels on the full-size kite,
-# from the ncu captures summarised in the named profiles/ file.  Keyed by the plan's
-# near-field entry count and by kernel: another workload, or a kernel changed since the
-# capture (remove its entry then), reports null.
-NEAR_TRAFFIC = {}
+# DRAM bytes (read + write) per launch of the near-field kernels on the full-size kite
+# (358 205 610 near-field entries), from the ncu capture of the half-resolution kite
+# summarised in profiles/near_field_kite_dram.md, scaled to the full launch by the
+# ratio of algorithmic bytes (DRAM / algorithmic there: FP64 1.017, complex64 1.005,
+# tensor cores 1.067).  Keyed by the plan's near-field entry count and by kernel:
+# another workload, or a kernel changed since the capture (remove its entry then),
+# reports null.
+NEAR_TRAFFIC = {358205610: {"fp64": 8.892e9, "mixed": 2.955e9, "tc16": 3.218e9}}
 
 
 def hbm_peak():
@@ -53,6 +57,20 @@ def hbm_peak():
         except Exception:
             pass
     return FALLBACK_HBM_GBS, "fallback"
+
+
+def fp16_peak():
+    """Dense FP16/BF16 tensor peak (kind::f16 runs FP16 at the BF16 rate): the
+    measured burst figure of MEASURED_PEAKS.json, else the recipe's fallback."""
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            d = json.load(open(p))
+            if "bf16_tflops" in d:
+                return float(d["bf16_tflops"]), "measured (bf16 cuBLAS burst, the FP16 dense rate)"
+        except Exception:
+            pass
+    return FALLBACK_BF16_TFLOPS, "fallback"
 
 
 class Clocks:
@@ -536,10 +554,12 @@ def main():
     peak, peak_src = hbm_peak()
     traffic = NEAR_TRAFFIC.get(nnz, {})
     fp64_peak = peaks["fp64"]
-    # TF32 work the tensor-core near field issues per launch: per complex weight
-    # (padded to 16-column chunks) and K step, 2 x 2 x (4R + 2R) multiply-adds
+    # FP16 work the tensor-core near field issues per launch (kind::f16, split
+    # operands): per complex weight (2 real K entries) an MMA of N = 4R
+    # (A_hi against B_hi | B_lo) and one of N = 2R (A_lo against B_hi), 2 flops each
     nchunk_cols = nnz              # close to the padded count (rows padded to 8 add < 3 %)
     tc_flops = nchunk_cols * 2 * 2 * (4 * NB32 + 2 * NB32)
+    f16_peak, f16_src = fp16_peak()
     # FP64 flops of one launch: 3 FMAs per block weight (three-multiplication
     # complex product), 4 per Phi-gamma term
     near_flops = nnz * 6 + N * nfb2 * 8
@@ -583,8 +603,8 @@ def main():
         "roofline": {"bound": "alu", "kernel": "k_near_eval5<double2,1>",
                      "achieved": near_flops / t_near64 / 1e12, "peak": fp64_peak, "unit": "TFLOP/s",
                      "frac": near_flops / t_near64 / 1e12 / fp64_peak, "traffic": traffic.get("fp64"),
-                     "peak_source": "measured: ls_measure_peaks FP64 FMA probe (16 independent chains per "
-                                    "thread, every SM, CUDA events), this run",
+                     "peak_source": "measured: ls_measure_peaks FP64 FMA probe (best of 8, 16 and 32 "
+                                    "independent chains per thread, every SM, CUDA events), this run",
                      "flops_per_launch": near_flops, "bytes_per_launch": near_bytes(16, 24),
                      "hbm_GBs": ach64, "hbm_frac": ach64 / peak, "hbm_peak": peak, "hbm_peak_source": peak_src,
                      "launch_ms": t_near64 * 1e3},
@@ -601,16 +621,16 @@ def main():
         "batched": {"unit": "RHS-matvecs/s",
                     "mixed": {"nrhs": NB32, "value": world * nb_steps * NB32 / (msb32 * 1e-3), "dtype": "f32",
                               "ms_per_apply": msb32 / nb_steps,
-                              "roofline": {"bound": "hbm", "kernel": "k_near_tc<16> (tcgen05, 3xTF32)",
+                              "roofline": {"bound": "hbm",
+                                           "kernel": f"k_near_tc<{NB32}> (tcgen05 kind::f16, split FP16 operands)",
                                            "achieved": ach_b, "peak": peak, "unit": "GB/s", "frac": ach_b / peak,
                                            "peak_source": peak_src, "bytes_per_launch": near_bytes_b,
                                            "traffic": traffic.get("tc16") if NB32 == 16 else None,
                                            "launch_ms": t_near_b * 1e3,
-                                           "tf32_tflops": tc_flops / t_near_b / 1e12,
-                                           "tf32_peak": peaks["tf32"],
-                                           "tf32_frac": tc_flops / t_near_b / 1e12 / peaks["tf32"],
-                                           "tf32_peak_source": "measured: ls_measure_peaks tcgen05 "
-                                                               "128x256x8 MMA probe, this run"},
+                                           "tensor_tflops": tc_flops / t_near_b / 1e12,
+                                           "tensor_peak": f16_peak,
+                                           "tensor_frac": tc_flops / t_near_b / 1e12 / f16_peak,
+                                           "tensor_peak_source": f16_src},
                               "apply_hbm_frac": (apply_bytes_b / (msb32 / nb_steps * 1e-3) / 1e9) / peak,
                               "stages_ms": dict(zip(stage_names, [float(x) / max(cb, 1) for x in stb]))},
                     "fp64": {"nrhs": NB64, "value": world * nb_steps * NB64 / (msb64 * 1e-3), "dtype": "f64"}},

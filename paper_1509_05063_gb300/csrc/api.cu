@@ -1201,11 +1201,33 @@ ls_status ls_plan_create3(const ls_ball3* ball, const ls_rules3* rules, ls_n2_fn
     a.occ_of_node = d_occ_of_node; a.P_off = d_P_off; a.rowptr = d_rowptr; a.col = d_col;
     a.P = UP3(double2, P64);
     a.LA = UP3(double2, LA64);
+    {
+      std::vector<float> la6(size_t(6) * LA64.size());
+      for (size_t e = 0; e < LA64.size(); ++e) {
+        const double f[3] = {LA64[e].real() + LA64[e].imag(), LA64[e].imag(), LA64[e].real()};
+        for (int t = 0; t < 3; ++t) {
+          const float hi = float(f[t]);
+          la6[6 * e + 2 * t] = hi;
+          la6[6 * e + 2 * t + 1] = float(f[t] - double(hi));
+        }
+      }
+      a.LA6 = UP3(float, la6);
+    }
     a.Phi = UP3(double2, Phi64);
     a.Gs = UP3(double2, Gs);
     a.Ds = UP3(double2, Ds);
     a.tw = d_tw64;
-    a.val = UP3(double2, val);
+    {
+      // FP64 adjacent part in the three-multiplication form (a + b, b, a)
+      std::vector<double> v3(size_t(3) * val.size());
+      for (size_t e = 0; e < val.size(); ++e) {
+        v3[3 * e] = val[e].real() + val[e].imag();
+        v3[3 * e + 1] = val[e].imag();
+        v3[3 * e + 2] = val[e].real();
+      }
+      a.val3 = UP3(double, v3);
+    }
+    a.u3 = plan->alloc<double>(size_t(3) * N, &st);
     a.kappa2 = kappa * kappa;
     a.sigma = plan->alloc<double2>(size_t(nocc) * n_es, &st);
     a.Sm = plan->alloc<double2>(size_t(M3), &st);
@@ -1225,7 +1247,66 @@ ls_status ls_plan_create3(const ls_ball3* ball, const ls_rules3* rules, ls_n2_fn
     b.P = UP3(float2, P32);
     b.Phi = UP3(float2, to32(Phi64));
     b.lattice64 = &plan->e64;
-    b.val = UP3(float2, to32(val));
+    {
+      // complex64 adjacent part as one dense block per cell over its 27
+      // neighbours' nodes: nodes are grouped by cell in increasing cell id
+      // (x fastest), so cells (i - 1 .. i + 1, j', k') hold one contiguous
+      // node range; 9 ranges per cell.  Entries outside them (singular
+      // stencils reaching past the block) stay in a CSR remainder.
+      std::vector<int64_t> first_at(size_t(L) * L * L + 1, N);   // first node of the first cell >= id
+      for (int k = nocc - 1; k >= 0; --k) first_at[A.occ_cells[k]] = occ_start[k];
+      for (int64_t id = int64_t(L) * L * L - 1; id >= 0; --id)
+        if (occ_of_cell[id] < 0) first_at[id] = first_at[id + 1];
+      std::vector<int> seg(size_t(nocc) * 18, 0);
+      std::vector<int64_t> boff(nocc + 1, 0);
+      for (int k = 0; k < nocc; ++k) {
+        const int c = A.occ_cells[k], ci = c % L, cj = (c / L) % L, ck = c / (L * L);
+        int nblk = 0;
+        for (int s9 = 0; s9 < 9; ++s9) {
+          const int jj = cj + s9 % 3 - 1, kk = ck + s9 / 3 - 1;
+          int st0 = 0, len = 0;
+          if (jj >= 0 && jj < L && kk >= 0 && kk < L) {
+            const int64_t row = (int64_t(kk) * L + jj) * L;
+            const int64_t lo = first_at[row + std::max(ci - 1, 0)], hi = first_at[row + std::min(ci + 1, L - 1) + 1];
+            st0 = int(lo);
+            len = int(hi - lo);
+          }
+          seg[18 * k + 2 * s9] = st0;
+          seg[18 * k + 2 * s9 + 1] = len;
+          nblk += len;
+        }
+        boff[k + 1] = boff[k] + (occ_start[k + 1] - occ_start[k]) * nblk;
+      }
+      std::vector<std::complex<float>> wb(size_t(boff[nocc]), {0.f, 0.f});
+      std::vector<int64_t> rrow(N + 1, 0);
+      std::vector<int> rcol;
+      std::vector<cd> rval;
+      for (int k = 0; k < nocc; ++k) {
+        const int* sg = &seg[18 * k];
+        int nblk = 0;
+        for (int s9 = 0; s9 < 9; ++s9) nblk += sg[2 * s9 + 1];
+        for (int64_t q = occ_start[k]; q < occ_start[k + 1]; ++q) {
+          std::complex<float>* wrow = wb.data() + boff[k] + (q - occ_start[k]) * nblk;
+          for (int64_t e = rowptr[q]; e < rowptr[q + 1]; ++e) {
+            int pos = -1;
+            for (int s9 = 0, o = 0; s9 < 9; o += sg[2 * s9 + 1], ++s9)
+              if (col[e] >= sg[2 * s9] && col[e] < sg[2 * s9] + sg[2 * s9 + 1]) {
+                pos = o + col[e] - sg[2 * s9];
+                break;
+              }
+            if (pos >= 0) wrow[pos] += std::complex<float>(val[e]);
+            else { rcol.push_back(col[e]); rval.push_back(val[e]); }
+          }
+          rrow[q + 1] = int64_t(rcol.size());
+        }
+      }
+      b.Wb = UP3(float2, wb);
+      b.blk_off = UP3(int64_t, boff);
+      b.blk_seg = UP3(int, seg);
+      b.rowptr = UP3(int64_t, rrow);
+      b.col = UP3(int, rcol);
+      b.val = UP3(float2, to32(rval));
+    }
     b.kappa2 = a.kappa2;
     b.sigma = plan->alloc<float2>(size_t(nocc) * n_es, &st);
     b.gamma = plan->alloc<float2>(size_t(nocc) * nb, &st);
@@ -2308,14 +2389,16 @@ ls_status ls_batch_create(const ls_plan* plans, int n_plans, ls_batch* out) {
   if (!out) return LS_ERR_INVALID;
   *out = nullptr;
   if (!plans || n_plans < 1) return fail(nullptr, LS_ERR_INVALID, "ls_batch_create: no plans");
+  // handles are compared before any is dereferenced
   for (int i = 0; i < n_plans; ++i) {
     if (!plans[i]) return fail(nullptr, LS_ERR_INVALID, "ls_batch_create: null plan");
-    if (plans[i]->dim != 2) return fail(nullptr, LS_ERR_UNSUPPORTED, "ls_batch_create: 2-D plans only");
     for (int j = 0; j < i; ++j)
       if (plans[j] == plans[i])
         return fail(nullptr, LS_ERR_INVALID, "ls_batch_create: a plan appears twice (instances would share its "
                                              "work arrays)");
   }
+  for (int i = 0; i < n_plans; ++i)
+    if (plans[i]->dim != 2) return fail(nullptr, LS_ERR_UNSUPPORTED, "ls_batch_create: 2-D plans only");
   auto* b = new (std::nothrow) ls_batch_s();
   if (!b) return fail(nullptr, LS_ERR_NOMEM, "ls_batch_create: host allocation");
   auto bail = [&](ls_status s) {

@@ -9,12 +9,15 @@
 //                 box of lines that can be nonzero (forward) or are read (inverse)
 //   k3_conv_a     the a-axis stage: forward lines of both arrays, V^ = S_m^ G^ + S_d^ D^,
 //                 inverse line, in one pass (k3_spectral when M > 1024)
-//   k3_gather, k3_gemm, k3_reduce
+//   k3_gather, k3_gemm (FP64) or k3_gemm_df (double-float, complex64 apply), k3_reduce
 //                 gamma_c = B^+ V_c - sum_o (B^+ T_o) sigma_{c+o}   (27 neighbours; one GEMM over cells)
-//   k3_near       out_q = u_q + kappa^2 (sum_l W_ql u_l + Phi_q . gamma_c)
+//   k3_near       out_q = u_q + kappa^2 (sum_l W_ql u_l + Phi_q . gamma_c): FP64 from a CSR in
+//                 three-multiplication form, complex64 from dense per-cell blocks over the
+//                 27 neighbour cells' nodes plus a CSR remainder
 // The complex64 apply runs the projection, the adjacent part and the
-// evaluation in complex64 and the lattice convolution and local coefficients
-// in FP64 (ApplyData3::lattice64 says why).
+// evaluation in complex64, the lattice convolution in FP64 and the local
+// coefficients in double-float (ApplyData3::lattice64 says why).
+#include <algorithm>
 #include <cstdint>
 
 #include "cplx.cuh"
@@ -26,28 +29,53 @@ namespace {
 
 constexpr int kT3 = 256;
 
-// sigma_c = P_c u_c: block = occupied cell, thread = output rows i = t, t + 256, ...;
-// the cell's inputs staged in shared memory 256 at a time, P_c read [node][i]
-// (consecutive threads, consecutive entries)
+// sigma_c = P_c u_c: block = occupied cell, 1024 threads = output rows
+// i < n_es (a pass of up to 1024 rows at a time) x S = 1024 / rows segments
+// of the cell's nodes (node j in segment j mod S); the cell's inputs staged in
+// shared memory 1024 at a time, P_c read [node][i] (consecutive threads,
+// consecutive entries), the S partial sums added in segment order.  FP64:
+// also writes the staged input (c, c + d, d - c) of the adjacent part for the
+// cell's nodes.
+constexpr int kTP = 1024;
 template <typename T>
-__global__ void __launch_bounds__(kT3) k3_project(ApplyData3<T> d, const T* __restrict__ u) {
-  __shared__ T us[kT3];
+__global__ void __launch_bounds__(kTP) k3_project(ApplyData3<T> d, const T* __restrict__ u) {
+  __shared__ T us[kTP];
+  __shared__ T ps[kTP];
   const int k = blockIdx.x, t = threadIdx.x;
   const int64_t s0 = d.occ_start[k];
   const int nc = int(d.occ_start[k + 1] - s0);
   const T* P = d.P + d.P_off[k];
-  for (int i0 = 0; i0 < d.n_es; i0 += kT3) {
-    const int i = i0 + t;
+  const int ni = d.n_es < kTP ? d.n_es : kTP, S = kTP / ni;
+  const int il = t % ni, sg = t / ni;
+  for (int i0 = 0; i0 < d.n_es; i0 += ni) {
+    const int i = i0 + il;
     T acc = czero(T());
-    for (int j0 = 0; j0 < nc; j0 += kT3) {
-      const int nj = nc - j0 < kT3 ? nc - j0 : kT3;
+    for (int j0 = 0; j0 < nc; j0 += kTP) {
+      const int nj = nc - j0 < kTP ? nc - j0 : kTP;
       __syncthreads();
-      if (t < nj) us[t] = u[s0 + j0 + t];
+      if (t < nj) {
+        const T v = u[s0 + j0 + t];
+        us[t] = v;
+        if constexpr (sizeof(T) == 16)
+          if (i0 == 0) {                 // the staged input of the FP64 adjacent part
+            double* w = d.u3 + 3 * (s0 + j0 + t);
+            w[0] = v.x;
+            w[1] = v.x + v.y;
+            w[2] = v.y - v.x;
+          }
+      }
       __syncthreads();
-      if (i < d.n_es)
-        for (int j = 0; j < nj; ++j) acc = cfma(P[int64_t(j0 + j) * d.n_es + i], us[j], acc);
+      if (sg < S && i < d.n_es)
+        for (int j = sg; j < nj; j += S) acc = cfma(P[int64_t(j0 + j) * d.n_es + i], us[j], acc);
     }
-    if (i < d.n_es) d.sigma[int64_t(k) * d.n_es + i] = acc;
+    ps[t] = acc;
+    __syncthreads();
+    if (t < ni && i < d.n_es) {
+      T v = ps[t];
+      for (int q = 1; q < S; ++q) v = cadd(v, ps[q * ni + t]);
+      d.sigma[int64_t(k) * d.n_es + i] = v;
+    }
+    __syncthreads();
   }
 }
 
@@ -94,8 +122,10 @@ __global__ void __launch_bounds__(kT3) k3_fill(ApplyData3<T> d) {
 // a box of lines: line j = o n_in + i (o < n_out, i < n_in) has outer
 // coordinate o ostep and inner coordinate i, where (outer, inner) is (a, b)
 // for the c axis (axis 2), (a, c) for the b axis (1) and (b, c) for the a
-// axis (0).  A block takes LPB = 2048 / M consecutive lines of the box, M / 8
-// threads per line, lines padded to M + 1 in shared memory; loads and stores
+// axis (0).  A block takes LPB = blockDim.x / (M / 8) consecutive lines of the
+// box, M / 8 threads per line, lines padded to M + 1 in shared memory (LPB is
+// chosen per launch so that the lines spread over every SM: in FP64 a line
+// transform costs an SM's pipe about 700 cycles); loads and stores
 // run along c (within a line for axis 2, across consecutive lines otherwise),
 // so that they coalesce.  Lines outside the box are not touched: the lattice
 // convolution skips the lines it knows to be zero on input or unread later.
@@ -116,16 +146,16 @@ __global__ void __launch_bounds__(kT3) k3_fft_axis(T* __restrict__ X, int M, int
                                                   bool inv, LineBox bx) {
   extern __shared__ __align__(16) unsigned char raw3[];
   T* s = reinterpret_cast<T*>(raw3);
-  const int G = M / 8, LPB = kT3 / G, t = threadIdx.x;
+  const int G = M / 8, nt = blockDim.x, LPB = nt / G, t = threadIdx.x;
   const int64_t l0 = int64_t(blockIdx.x) * LPB, nl = int64_t(bx.n_out) * bx.n_in;
-  for (int idx = t; idx < LPB * M; idx += kT3) {
+  for (int idx = t; idx < LPB * M; idx += nt) {
     const int j = bx.axis == 2 ? idx / M : idx % LPB, e = bx.axis == 2 ? idx % M : idx / LPB;
     s[j * (M + 1) + e] = l0 + j < nl ? X[line_addr(bx, M, l0 + j, e)] : czero(T());
   }
   __syncthreads();
   fft_smem<T>(s + (t / G) * (M + 1), M, logM, inv, tw, t % G);
   __syncthreads();
-  for (int idx = t; idx < LPB * M; idx += kT3) {
+  for (int idx = t; idx < LPB * M; idx += nt) {
     const int j = bx.axis == 2 ? idx / M : idx % LPB, e = bx.axis == 2 ? idx % M : idx / LPB;
     if (l0 + j < nl) X[line_addr(bx, M, l0 + j, e)] = s[j * (M + 1) + e];
   }
@@ -134,24 +164,24 @@ __global__ void __launch_bounds__(kT3) k3_fft_axis(T* __restrict__ X, int M, int
 // the a-axis stage of the lattice convolution in one pass over the (b, c)
 // lines: forward transforms of a monopole and a dipole line, V^ = S_m^ G^ +
 // S_d^ D^, inverse transform, V written back into Sm for a <= a_max only (the
-// later stages read no more).  H = 1024 / M line pairs per block: shared
-// slots [0, H) hold monopole lines, [H, 2H) dipole lines.
+// later stages read no more).  H = blockDim.x / (M / 4) line pairs per block:
+// shared slots [0, H) hold monopole lines, [H, 2H) dipole lines.
 template <typename T>
 __global__ void __launch_bounds__(kT3) k3_conv_a(T* __restrict__ Sm, const T* __restrict__ Sd,
                                                 const T* __restrict__ Gs, const T* __restrict__ Ds, int M,
                                                 int logM, const T* __restrict__ tw, int a_max) {
   extern __shared__ __align__(16) unsigned char raw3[];
   T* s = reinterpret_cast<T*>(raw3);
-  const int G = M / 8, LPB = kT3 / G, H = LPB / 2, t = threadIdx.x;
+  const int G = M / 8, nt = blockDim.x, LPB = nt / G, H = LPB / 2, t = threadIdx.x;
   const int64_t MM = int64_t(M) * M, l0 = int64_t(blockIdx.x) * H;
-  for (int idx = t; idx < LPB * M; idx += kT3) {
+  for (int idx = t; idx < LPB * M; idx += nt) {
     const int j = idx % LPB, e = idx / LPB;
     s[j * (M + 1) + e] = (j < H ? Sm : Sd)[l0 + (j % H) + int64_t(e) * MM];
   }
   __syncthreads();
   fft_smem<T>(s + (t / G) * (M + 1), M, logM, false, tw, t % G);
   __syncthreads();
-  for (int idx = t; idx < H * M; idx += kT3) {
+  for (int idx = t; idx < H * M; idx += nt) {
     const int j = idx % H, e = idx / H;
     const int64_t ad = l0 + j + int64_t(e) * MM;
     T* v = s + j * (M + 1) + e;
@@ -160,7 +190,7 @@ __global__ void __launch_bounds__(kT3) k3_conv_a(T* __restrict__ Sm, const T* __
   __syncthreads();
   fft_smem<T>(s + (t / G) * (M + 1), M, logM, true, tw, t % G, 1, t / G < H);
   __syncthreads();
-  for (int idx = t; idx < H * M; idx += kT3) {
+  for (int idx = t; idx < H * M; idx += nt) {
     const int j = idx % H, e = idx / H;
     if (e <= a_max) Sm[l0 + j + int64_t(e) * MM] = s[j * (M + 1) + e];
   }
@@ -265,6 +295,106 @@ __global__ void __launch_bounds__(kT3) k3_gemm(ApplyData3<T> d, int S) {
     }
 }
 
+// The same GEMM for the complex64 apply in double-float arithmetic on the
+// FP32 pipe (GB300 issues 64 FP32 operations per FP64 FMA).  The local step
+// subtracts large, nearly equal terms, so its sums need about FP64 accuracy:
+// each complex product takes Gauss's three real products of the forms above,
+// every form split into FP32 hi + lo, and each real sum is a compensated dot
+// product (Ogita, Rump and Oishi's Dot2): the leading product ah xh goes into
+// the running sum through an error-free TwoSum, and its exact rounding error
+// (one FMA), the cross terms ah xl + al xh and the TwoSum error collect in a
+// second FP32 word.  Twelve FP32 operations per real product; the result is
+// as accurate as a sum computed in twice the FP32 precision.  The rounded
+// operations (__fmul_rn, __fadd_rn) keep the compiler from fusing them.
+struct DF6 {
+  float h[3], l[3];   // forms (0, 1, 2), hi and lo
+};
+
+__device__ __forceinline__ void dot2_step(float ah, float al, float xh, float xl, float& s, float& c) {
+  const float ph = __fmul_rn(ah, xh);
+  const float pe = fmaf(ah, xh, -ph);                   // exact: ah xh = ph + pe
+  c = __fadd_rn(c, pe);
+  c = fmaf(ah, xl, c);
+  c = fmaf(al, xh, c);
+  const float sn = __fadd_rn(s, ph);                    // TwoSum(s, ph) = sn + e
+  const float bp = __fsub_rn(sn, s);
+  const float e = __fadd_rn(__fsub_rn(s, __fsub_rn(sn, bp)), __fsub_rn(ph, bp));
+  s = sn;
+  c = __fadd_rn(c, e);
+}
+
+__global__ void __launch_bounds__(kT3) k3_gemm_df(ApplyData3<double2> d, int S) {
+  __shared__ DF6 xs[kGK][kGC + 1];
+  __shared__ DF6 as[kGK][kGN];
+  const int K = d.n_loc + 27 * d.n_es;
+  const int c0 = blockIdx.x * kGC, n0 = blockIdx.y * kGN, sl = blockIdx.z;
+  const int kper = (K + S - 1) / S, kb = sl * kper, ke = kb + kper < K ? kb + kper : K;
+  const int t = threadIdx.x, tc = t / 16, tn = t % 16;
+  float hs[2][2][3], hc[2][2][3];
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 2; ++b)
+#pragma unroll
+      for (int f = 0; f < 3; ++f) hs[a][b][f] = hc[a][b][f] = 0.f;
+  for (int k0 = kb; k0 < ke; k0 += kGK) {
+    __syncthreads();
+    for (int i = t; i < kGK * kGC; i += kT3) {        // X tile: forms (c, c + d, d - c), split
+      const int kk = i % kGK, cc = i / kGK, c = c0 + cc, kg = k0 + kk;
+      const double2 v = (c < d.nocc && kg < ke) ? d.X[int64_t(c) * K + kg] : make_double2(0, 0);
+      const double f[3] = {v.x, v.x + v.y, v.y - v.x};
+      DF6 w;
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        w.h[q] = float(f[q]);
+        w.l[q] = float(f[q] - double(w.h[q]));
+      }
+      xs[kk][cc] = w;
+    }
+    for (int i = t; i < kGK * kGN; i += kT3) {        // LA tile, already in the split forms
+      const int kk = i / kGN, nn = i % kGN, n = n0 + nn, kg = k0 + kk;
+      DF6 w;
+      if (n < d.nb && kg < ke) {
+        const float* src = d.LA6 + 6 * (int64_t(kg) * d.nb + n);
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+          w.h[q] = src[2 * q];
+          w.l[q] = src[2 * q + 1];
+        }
+      } else {
+#pragma unroll
+        for (int q = 0; q < 3; ++q) w.h[q] = w.l[q] = 0.f;
+      }
+      as[kk][nn] = w;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < kGK; ++kk) {
+      const DF6 x[2] = {xs[kk][tc], xs[kk][tc + 16]};
+      const DF6 l[2] = {as[kk][tn], as[kk][tn + 16]};
+#pragma unroll
+      for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+          // P: (a + b) c, Q: b (c + d), S: a (d - c)
+          dot2_step(l[b].h[0], l[b].l[0], x[a].h[0], x[a].l[0], hs[a][b][0], hc[a][b][0]);
+          dot2_step(l[b].h[1], l[b].l[1], x[a].h[1], x[a].l[1], hs[a][b][1], hc[a][b][1]);
+          dot2_step(l[b].h[2], l[b].l[2], x[a].h[2], x[a].l[2], hs[a][b][2], hc[a][b][2]);
+        }
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      const int c = c0 + tc + 16 * a, n = n0 + tn + 16 * b;
+      const double P = double(hs[a][b][0]) + double(hc[a][b][0]);
+      const double Q = double(hs[a][b][1]) + double(hc[a][b][1]);
+      const double U = double(hs[a][b][2]) + double(hc[a][b][2]);
+      if (c < d.nocc && n < d.nb) d.part[(int64_t(sl) * d.nocc + c) * d.nb + n] = make_double2(P - Q, P + U);
+    }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kT3) k3_reduce(ApplyData3<T> d, int S) {
   const int64_t n = int64_t(d.nocc) * d.nb;
@@ -294,7 +424,36 @@ __global__ void __launch_bounds__(kT3) k3_near(ApplyData3<T> d, const T* __restr
   const int64_t q = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
   if (q >= d.N) return;
   T acc = czero(T());
-  for (int64_t e = d.rowptr[q] + lane; e < d.rowptr[q + 1]; e += 32) acc = cfma(d.val[e], u[d.col[e]], acc);
+  if constexpr (sizeof(T) == 16) {
+    // three FMAs per complex product: P += (a + b) c, Q += b (c + d), S += a (d - c);
+    // Re = P - Q, Im = P + S (GB300's FP64 pipe, not HBM, bounds this loop)
+    double P = 0, Q = 0, S = 0;
+    for (int64_t e = d.rowptr[q] + lane; e < d.rowptr[q + 1]; e += 32) {
+      const double* w = d.val3 + 3 * e;
+      const double* x = d.u3 + 3 * int64_t(d.col[e]);
+      P = fma(w[0], x[0], P);
+      Q = fma(w[1], x[1], Q);
+      S = fma(w[2], x[2], S);
+    }
+    acc = mk(P - Q, P + S);
+  } else {
+    // complex64: the cell's dense block over its 9 neighbour node ranges
+    // (row r of cell k), then the CSR remainder
+    const int k = d.occ_of_node[q];
+    const int* sg = d.blk_seg + 18 * k;
+    int nblk = 0;
+#pragma unroll
+    for (int s9 = 0; s9 < 9; ++s9) nblk += sg[2 * s9 + 1];
+    const T* w = d.Wb + d.blk_off[k] + (q - d.occ_start[k]) * nblk;
+#pragma unroll 1
+    for (int s9 = 0; s9 < 9; ++s9) {
+      const int n0 = sg[2 * s9], len = sg[2 * s9 + 1];
+      const T* uu = u + n0;
+      for (int e = lane; e < len; e += 32) acc = cfma(w[e], uu[e], acc);
+      w += len;
+    }
+    for (int64_t e = d.rowptr[q] + lane; e < d.rowptr[q + 1]; e += 32) acc = cfma(d.val[e], u[d.col[e]], acc);
+  }
   const T* ph = d.Phi + q * d.nb;
   const T* g = d.gamma + int64_t(d.occ_of_node[q]) * d.nb;
   for (int n = lane; n < d.nb; n += 32) acc = cfma(ph[n], g[n], acc);
@@ -347,7 +506,17 @@ int grid_for(int64_t n) {
   return int(b < 152 * 16 ? b : 152 * 16);
 }
 
-size_t fft_smem_bytes(int M, size_t elem) { return elem * size_t(kT3 / (M / 8)) * (M + 1); }
+size_t fft_smem_bytes(int M, int lpb, size_t elem) { return elem * size_t(lpb) * (M + 1); }
+
+// lines per block of a line-transform launch over `lines` lines: a power of
+// two between 32 / (M / 8) (whole warps) and 2048 / M, as large as leaves at
+// least two blocks per SM
+int lines_per_block(int M, int64_t lines) {
+  const int G = M / 8, lo = G >= 32 ? 1 : 32 / G, hi = kT3 / G;
+  int lpb = hi;
+  while (lpb > lo && (lines + lpb - 1) / lpb < 2 * 152) lpb /= 2;
+  return lpb;
+}
 
 template <typename T>
 cudaError_t fft_box(T* x, int M, int logM, const T* tw, bool inverse, LineBox bx, cudaStream_t st) {
@@ -356,9 +525,10 @@ cudaError_t fft_box(T* x, int M, int logM, const T* tw, bool inverse, LineBox bx
     const cudaError_t e = cudaFuncSetAttribute(k3_fft_axis<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
     if (e != cudaSuccess) return e;
   }
-  const int LPB = kT3 / (M / 8);
   const int64_t lines = int64_t(bx.n_out) * bx.n_in;
-  k3_fft_axis<T><<<int((lines + LPB - 1) / LPB), kT3, fft_smem_bytes(M, sizeof(T)), st>>>(x, M, logM, tw, inverse, bx);
+  const int LPB = lines_per_block(M, lines);
+  k3_fft_axis<T><<<int((lines + LPB - 1) / LPB), LPB * (M / 8), fft_smem_bytes(M, LPB, sizeof(T)), st>>>(
+      x, M, logM, tw, inverse, bx);
   return cudaGetLastError();
 }
 
@@ -369,7 +539,7 @@ cudaError_t fft_box(T* x, int M, int logM, const T* tw, bool inverse, LineBox bx
 // b and c stages on the lines with a (and b) <= L N_eq; the a stage (every
 // (b, c) line) carries the spectral product.
 template <typename T>
-cudaError_t lattice_local(const ApplyData3<T>& d, cudaStream_t st) {
+cudaError_t lattice_local(const ApplyData3<T>& d, cudaStream_t st, bool df = false) {
   const int64_t n3 = int64_t(d.M) * d.M * d.M;
   const int M = d.M, nl = d.L * d.Ne;
   k3_fill<T><<<grid_for(n3), kT3, 0, st>>>(d);
@@ -386,9 +556,9 @@ cudaError_t lattice_local(const ApplyData3<T>& d, cudaStream_t st) {
       e = cudaFuncSetAttribute(k3_conv_a<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
       if (e != cudaSuccess) return e;
     }
-    const int H = kT3 / (M / 8) / 2;
-    k3_conv_a<T><<<int(int64_t(M) * M / H), kT3, fft_smem_bytes(M, sizeof(T)), st>>>(d.Sm, d.Sd, d.Gs, d.Ds, M, d.logM,
-                                                                                   d.tw, nl);
+    const int LPB = std::max(2, lines_per_block(M, 2 * int64_t(M) * M)), H = LPB / 2;
+    k3_conv_a<T><<<int(int64_t(M) * M / H), LPB * (M / 8), fft_smem_bytes(M, LPB, sizeof(T)), st>>>(
+        d.Sm, d.Sd, d.Gs, d.Ds, M, d.logM, d.tw, nl);
   } else {
     for (T* x : both)
       if (e == cudaSuccess) e = fft_box<T>(x, M, d.logM, d.tw, false, LineBox{0, M, 1, M}, st);
@@ -401,14 +571,20 @@ cudaError_t lattice_local(const ApplyData3<T>& d, cudaStream_t st) {
   if (e != cudaSuccess) return e;
   const int K = d.n_loc + 27 * d.n_es, S = local_slices(d.nocc, d.nb, K);
   k3_gather<T><<<d.nocc, kT3, 0, st>>>(d);
-  k3_gemm<T><<<dim3((d.nocc + kGC - 1) / kGC, (d.nb + kGN - 1) / kGN, S), kT3, 0, st>>>(d, S);
+  const dim3 grid((d.nocc + kGC - 1) / kGC, (d.nb + kGN - 1) / kGN, S);
+  if constexpr (sizeof(T) == 16) {
+    if (df) k3_gemm_df<<<grid, kT3, 0, st>>>(d, S);
+    else k3_gemm<T><<<grid, kT3, 0, st>>>(d, S);
+  } else {
+    k3_gemm<T><<<grid, kT3, 0, st>>>(d, S);
+  }
   k3_reduce<T><<<grid_for(int64_t(d.nocc) * d.nb), kT3, 0, st>>>(d, S);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t apply3_one(const ApplyData3<T>& d, const T* u, T* out, cudaStream_t st) {
-  k3_project<T><<<d.nocc, kT3, 0, st>>>(d, u);
+  k3_project<T><<<d.nocc, kTP, 0, st>>>(d, u);
   cudaError_t e;
   if constexpr (sizeof(T) == 8) {
     // complex64: the strengths widened to FP64 for the lattice and the local
@@ -416,7 +592,7 @@ cudaError_t apply3_one(const ApplyData3<T>& d, const T* u, T* out, cudaStream_t 
     const ApplyData3<double2>& w = *d.lattice64;
     const int64_t ns = int64_t(d.nocc) * d.n_es, ng = int64_t(d.nocc) * d.nb;
     k3_widen<<<grid_for(ns), kT3, 0, st>>>(d.sigma, w.sigma, ns);
-    e = lattice_local(w, st);
+    e = lattice_local(w, st, true);
     if (e != cudaSuccess) return e;
     k3_narrow<<<grid_for(ng), kT3, 0, st>>>(w.gamma, d.gamma, ng);
   } else {

@@ -124,26 +124,34 @@ struct ApplyData3 {
   const int64_t* P_off = nullptr;       // nocc + 1: element offset of each cell's projection
   const T* P = nullptr;                 // P_c stored [node][n_es] (w omega m folded in)
   const T* LA = nullptr;                // [n_loc + 27 n_es][nb]: B^+ transposed, then -(B^+ T_o) transposed
+  const float* LA6 = nullptr;           // FP64 data only: LA = a + ib as (a + b, b, a), each split into
+                                        // FP32 hi + lo, [K][nb][6] (the double-float local GEMM)
   const T* Phi = nullptr;               // N x nb: local basis at each node about its cell centre
   const T* Gs = nullptr;                // M^3 spectra of the G and dG/dz_1 lattice tables, / M^3
   const T* Ds = nullptr;
   const T* tw = nullptr;                // M twiddles exp(-2 pi i m / M)
   const int64_t* rowptr = nullptr;      // adjacent part: CSR over the nodes (contrast folded into val)
   const int* col = nullptr;
-  const T* val = nullptr;
+  const T* val = nullptr;               // complex64 data only: the CSR holds the remainder of the blocks
+  const T* Wb = nullptr;                // complex64 only: per cell a dense block [row][27-neighbour columns]
+  const int64_t* blk_off = nullptr;     // nocc: element offset of each cell's block in Wb
+  const int* blk_seg = nullptr;         // nocc x 9 x (first node, count): the neighbour column ranges
+  const double* val3 = nullptr;         // FP64 data only: (a + b, b, a) per entry of the values a + ib
   double kappa2 = 0;
   // work space (one right-hand side)
+  double* u3 = nullptr;                 // FP64 data only: N x (c, c + d, d - c) of the input c + id
   T* sigma = nullptr;                   // nocc x n_es
   T* Sm = nullptr;                      // M^3: monopole lattice, then the lattice field V
   T* Sd = nullptr;                      // M^3: dipole lattice
   T* gamma = nullptr;                   // nocc x nb
   T* X = nullptr;                       // FP64 data only: nocc x (n_loc + 27 n_es), inputs of the local step
   T* part = nullptr;                    // FP64 data only: local3_slices x nocc x nb partial products
-  // complex64 only (host pointer): the FP64 data whose lattice convolution and
-  // local coefficients the complex64 apply uses.  On a cell's own lattice
-  // points the 27 neighbours' fields dominate and cancel in the neighbour
-  // subtraction; complex64 rounding of the lattice field would be magnified
-  // by that cancellation and by the ill-conditioned local fit.
+  // complex64 only (host pointer): the FP64 data whose lattice convolution
+  // (FP64) and local coefficients (double-float GEMM) the complex64 apply
+  // uses.  On a cell's own lattice points the 27 neighbours' fields dominate
+  // and cancel in the neighbour subtraction; complex64 rounding of the lattice
+  // field or of the local step's sums would be magnified by that cancellation
+  // and by the ill-conditioned local fit.
   const ApplyData3<double2>* lattice64 = nullptr;
 };
 

@@ -66,7 +66,7 @@ constexpr int kHalf = 16 * kRowGroup;        // 128 rows, hi or lo: 8 KB
 constexpr int kAStage = 2 * kHalf;           // a weight stage: hi, then lo
 constexpr int kNA = 12;                      // weight stages (bulk-copy ring)
 constexpr int kNC = 4;                       // B operand slots = B warps
-constexpr int kSets = 2;                     // accumulator sets per item (alternate K steps)
+constexpr int kSets = 2;                     // accumulator sets per item (K step k uses set k mod kSets)
 constexpr int kThreads = 32 * (6 + kNC);
 constexpr int kDrainPolls = 1 << 28;         // bound of the final waits on the block's own MMAs / copies
 
@@ -337,8 +337,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_near_tc(const int2* __restrict_
             const uint64_t dh = s_desc(a0 + 2 * i * 128, 128, kRowGroup);
             const uint64_t dl = s_desc(a0 + kHalf + 2 * i * 128, 128, kRowGroup);
             const uint64_t db = s_desc(b0 + 2 * i * 128, 128, kRowGroup);
-            const uint32_t acc = acc0 + uint32_t((i % kSets) * NN);
-            const uint32_t accum = (c > 0 || i >= kSets) ? 1u : 0u;
+            const int ks = c * (kKG / 2) + i;        // K step of the item: accumulator set ks mod kSets
+            const uint32_t acc = acc0 + uint32_t((ks % kSets) * NN);
+            const uint32_t accum = ks >= kSets ? 1u : 0u;
             asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
                          " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
                          :: "r"(acc), "l"(dh), "l"(db), "r"(idesc1), "r"(accum) : "memory");
@@ -440,8 +441,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_near_tc(const int2* __restrict_
         const uint32_t ta = tmem + (uint32_t(32 * (warp & 3)) << 16) + uint32_t(kSets * b * NN);
 #pragma unroll
         for (int q = 0; q < NN / 16; ++q) tmem_load16(ta + uint32_t(16 * q), d + 16 * q);
+        const int used = ig.nchunk * (kKG / 2) < kSets ? ig.nchunk * (kKG / 2) : kSets;   // sets written
 #pragma unroll
         for (int st = 1; st < kSets; ++st) {
+          if (st >= used) break;
 #pragma unroll
           for (int q = 0; q < NN / 16; ++q) tmem_load16(ta + uint32_t(st * NN + 16 * q), d2 + 16 * q);
 #pragma unroll
