@@ -43,7 +43,7 @@ KERNELS_PER_APPLY = 6    # projection, source rows (fill + row FFT), columns (FF
 # tensor cores 1.067).  Keyed by the plan's near-field entry count and by kernel:
 # another workload, or a kernel changed since the capture (remove its entry then),
 # reports null.
-NEAR_TRAFFIC = {358205610: {"fp64": 8.892e9, "mixed": 2.955e9, "tc16": 3.218e9}}
+NEAR_TRAFFIC = {358205610: {"fp64": 8.892e9, "mixed": 2.955e9}}
 
 
 def hbm_peak():

@@ -36,13 +36,15 @@
 //
 // Persistent, warp-specialised, one block per SM walking its own list of work
 // items (lists balanced at plan time, longest first):
-//   warp 0      lane 0 issues the bulk copies into a ring of kNA weight stages;
+//   warp 0      lane 0 issues the bulk copies into a ring of kNA weight stages
+//               (L2 evict-first: the weights are read once);
 //   warp 1      lane 0 issues the MMAs and commits them to the release barriers;
 //   warps 2..5  (128 threads) per item: read the accumulator from tensor memory
 //               (two items in flight), add the CSR remainder and the local
 //               expansion Phi_q . gamma_c and write out_q = u_q + kappa^2 (near + far);
 //   warps 6..   one warp per operand slot: the B operand (scaled hi and lo) of
-//               the chunks that use its slot, from the input vectors.
+//               the chunks that use its slot, from the input vectors (gathers
+//               issued one owned chunk ahead).
 // Every wait is bounded by `spin` polls and also gives up once another role
 // has flagged a failure; then the block sets *err, waits (with a fixed bound
 // that does not depend on `spin`) for its own MMAs and bulk copies still in
@@ -276,6 +278,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_near_tc(const int2* __restrict_
   if (warp == 0) {
     // ------------------------------------------------ bulk copies of the weight chunks
     if (lane == 0) {
+      // the weights are read once: first in line for L2 eviction, so that the
+      // input vectors the B warps gather stay in L2 beside the stream
+      uint64_t stream_pol;
+      asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(stream_pol));
       int g = 0;   // chunk counter of this block
       bool live = true;
       for (int ip = p_begin; ip < p_end && live; ++ip) {
@@ -292,10 +298,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_near_tc(const int2* __restrict_
           const uint32_t dst = s_u32(Aring + s * kAStage), bar = s_u32(&a_full[s]);
           asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(bar), "r"(2 * half_bytes)
                        : "memory");
-          asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                       :: "r"(dst), "l"(src), "r"(half_bytes), "r"(bar) : "memory");
-          asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                       :: "r"(dst + kHalf), "l"(src + half_bytes), "r"(half_bytes), "r"(bar) : "memory");
+          asm volatile(
+              "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;"
+              :: "r"(dst), "l"(src), "r"(half_bytes), "r"(bar), "l"(stream_pol) : "memory");
+          asm volatile(
+              "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;"
+              :: "r"(dst + kHalf), "l"(src + half_bytes), "r"(half_bytes), "r"(bar), "l"(stream_pol) : "memory");
         }
       }
       // every copy issued must have landed before the block leaves (shared
@@ -371,11 +379,35 @@ __global__ void __launch_bounds__(kThreads, 1) k_near_tc(const int2* __restrict_
     // ... of this block.  Value v = lane + 32 i of a chunk is (RHS j = v % R,
     // column cc = v / R).
     constexpr int kVals = R * kKC / 32;
-    static_assert(R * kKC % 32 == 0, "B entries per lane");
+    static_assert(R * kKC % 32 == 0 && 32 % R == 0, "B entries per lane; RHS j = lane mod R");
     const int bw = warp - 6;
-    float ts[R];
+    const int j = lane % R;                        // this lane's right-hand side, for every value it moves
+    const float tsj = pow2_scale(__uint_as_float(tmax[j]));
+    const float2* uj = u + int64_t(j) * N;
+    // gathers of a chunk's inputs go out one owned chunk ahead: the loads of
+    // chunk g are in flight while chunk g - kNC is split into its slot
+    float2 cur[kVals], nxt[kVals];
+    int cur_use = -1;
+    auto build = [&](const float2* uv, int use) -> bool {
+      if (use > 0 && !wait_phase(s_u32(&b_empty[bw]), (use - 1) & 1, spin, sflag)) return false;
+      unsigned char* B = Bring + bw * Lay::kB;
 #pragma unroll
-    for (int j = 0; j < R; ++j) ts[j] = pow2_scale(__uint_as_float(tmax[j]));
+      for (int i = 0; i < kVals; ++i) {
+        const int cc = (lane + 32 * i) / R;
+        const float ur = uv[i].x * tsj, ui = uv[i].y * tsj;
+        __half rh, rl, ih, il, mh, ml;
+        split16(ur, rh, rl);
+        split16(ui, ih, il);
+        split16(-ui, mh, ml);
+        put_b(B, j, 2 * cc, rh, mh);             // real-part rows: (Re, -Im)
+        put_b(B, R + j, 2 * cc, ih, rh);         // imaginary-part rows: (Im, Re)
+        put_b(B, 2 * R + j, 2 * cc, rl, ml);
+        put_b(B, 3 * R + j, 2 * cc, il, rl);
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(s_u32(&b_ready[bw])) : "memory");
+      return true;
+    };
     int g = 0;
     bool live = true;
     for (int ip = p_begin; ip < p_end && live; ++ip) {
@@ -386,39 +418,25 @@ __global__ void __launch_bounds__(kThreads, 1) k_near_tc(const int2* __restrict_
       const int p0 = (l0 + 1) & ~1, p1 = (l1 + 1) & ~1;
       for (int c = 0; c < ig.nchunk; ++c, ++g) {
         if (g % kNC != bw) continue;
-        const int use = g / kNC;
-        if (use > 0 && !wait_phase(s_u32(&b_empty[bw]), (use - 1) & 1, spin, sflag)) {
-          live = false;
-          break;
-        }
-        float2 uv[kVals];
 #pragma unroll
         for (int i = 0; i < kVals; ++i) {
-          const int v = lane + 32 * i, j = v % R, col = c * kKC + v / R;
+          const int col = c * kKC + (lane + 32 * i) / R;
           int64_t node = -1;
           if (col < p0) { if (col < l0) node = sg[0] + col; }
           else if (col < p0 + p1) { const int o = col - p0; if (o < l1) node = sg[2] + o; }
           else if (col < ig.nblk) { const int o = col - p0 - p1; if (o < l2) node = sg[4] + o; }
-          uv[i] = node >= 0 ? u[int64_t(j) * N + node] : make_float2(0.f, 0.f);
+          nxt[i] = node >= 0 ? uj[node] : make_float2(0.f, 0.f);
         }
-        unsigned char* B = Bring + bw * Lay::kB;
+        if (cur_use >= 0 && !build(cur, cur_use)) {
+          live = false;
+          break;
+        }
 #pragma unroll
-        for (int i = 0; i < kVals; ++i) {
-          const int v = lane + 32 * i, j = v % R, cc = v / R;
-          const float ur = uv[i].x * ts[j], ui = uv[i].y * ts[j];
-          __half rh, rl, ih, il, mh, ml;
-          split16(ur, rh, rl);
-          split16(ui, ih, il);
-          split16(-ui, mh, ml);
-          put_b(B, j, 2 * cc, rh, mh);             // real-part rows: (Re, -Im)
-          put_b(B, R + j, 2 * cc, ih, rh);         // imaginary-part rows: (Im, Re)
-          put_b(B, 2 * R + j, 2 * cc, rl, ml);
-          put_b(B, 3 * R + j, 2 * cc, il, rl);
-        }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(s_u32(&b_ready[bw])) : "memory");
+        for (int i = 0; i < kVals; ++i) cur[i] = nxt[i];
+        cur_use = g / kNC;
       }
     }
+    if (live && cur_use >= 0) build(cur, cur_use);
   } else {
     // ------------------------------------------------ epilogue (warps 2..5)
     const int row_in = 32 * (warp & 3) + lane;     // tensor-memory lane quarter of this warp
