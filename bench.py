@@ -413,6 +413,9 @@ def main():
         from paper_1509_05063_gb300 import autotune
         wl, _ = autotune.tune(wl, W.n2_of(wl), target_eps=1e-9, measure_top=3)
     plan = Plan(wl, W.n2_of(wl))
+    # kernel variants of this plan (lattice column-pass width, complex64 RHS
+    # group and near-field unit) timed on this GPU; the fastest is kept
+    kernel_tune = plan.autotune(16)
     info = plan.info
     N = plan.N
     u = torch.from_numpy(W.random_density(N, seed=W.SEED + rank)[0]).to(dev)
@@ -558,7 +561,9 @@ def main():
     # operands): per complex weight (2 real K entries) an MMA of N = 4R
     # (A_hi against B_hi | B_lo) and one of N = 2R (A_lo against B_hi), 2 flops each
     nchunk_cols = nnz              # close to the padded count (rows padded to 8 add < 3 %)
-    tc_flops = nchunk_cols * 2 * 2 * (4 * NB32 + 2 * NB32)
+    G32 = min(NB32, kernel_tune["group32"])       # RHS per near-field launch (autotuned)
+    tc_used = kernel_tune["near_cuda32"] == 0 and G32 >= 8
+    tc_flops = nchunk_cols * 2 * 2 * (4 * G32 + 2 * G32)
     f16_peak, f16_src = fp16_peak()
     # FP64 flops of one launch: 3 FMAs per block weight (three-multiplication
     # complex product), 4 per Phi-gamma term
@@ -574,11 +579,11 @@ def main():
                             + 2 * n_lat * M * cb * 2)
     apply_bytes64 = near_bytes(16, 24) + N * 16 * 4 + lat_bytes(16)
     # batched complex64 (tensor-core near field): weights once, per-RHS vectors, Phi once
-    near_bytes_b = nnz * 8 + N * nfb2 * 8 + N * 12 + NB32 * (2 * N * 8 + nocc * nfb2 * 8)
+    near_bytes_b = nnz * 8 + N * nfb2 * 8 + N * 12 + G32 * (2 * N * 8 + nocc * nfb2 * 8)
     t_near_b = stb[4] / max(cb, 1) * 1e-3
     ach_b = near_bytes_b / t_near_b / 1e9
     # whole batched apply: near field + per-RHS projection input, lattice passes and spectra
-    apply_bytes_b = near_bytes_b + NB32 * (N * 8 + lat_bytes(8))
+    apply_bytes_b = near_bytes_b * (NB32 // G32) + NB32 * (N * 8 + lat_bytes(8))
     stage_names = ["es_project", "lattice_fill(fused)", "lattice_fft_conv", "local_coeffs", "near_eval"]
 
     cpu = None
@@ -621,16 +626,17 @@ def main():
         "batched": {"unit": "RHS-matvecs/s",
                     "mixed": {"nrhs": NB32, "value": world * nb_steps * NB32 / (msb32 * 1e-3), "dtype": "f32",
                               "ms_per_apply": msb32 / nb_steps,
-                              "roofline": {"bound": "hbm",
-                                           "kernel": f"k_near_tc<{NB32}> (tcgen05 kind::f16, split FP16 operands)",
-                                           "achieved": ach_b, "peak": peak, "unit": "GB/s", "frac": ach_b / peak,
-                                           "peak_source": peak_src, "bytes_per_launch": near_bytes_b,
-                                           "traffic": traffic.get("tc16") if NB32 == 16 else None,
-                                           "launch_ms": t_near_b * 1e3,
-                                           "tensor_tflops": tc_flops / t_near_b / 1e12,
-                                           "tensor_peak": f16_peak,
-                                           "tensor_frac": tc_flops / t_near_b / 1e12 / f16_peak,
-                                           "tensor_peak_source": f16_src},
+                              "roofline": dict({"bound": "hbm",
+                                                "kernel": (f"k_near_tc<{G32}> (tcgen05 kind::f16, split FP16 operands)"
+                                                           if tc_used else f"k_near_eval4<float2,{G32}> (CUDA cores)"),
+                                                "achieved": ach_b, "peak": peak, "unit": "GB/s", "frac": ach_b / peak,
+                                                "peak_source": peak_src, "bytes_per_launch": near_bytes_b,
+                                                "traffic": traffic.get("tc16") if tc_used and G32 == 16 else None,
+                                                "launch_ms": t_near_b * 1e3},
+                                               **({"tensor_tflops": tc_flops / t_near_b / 1e12,
+                                                   "tensor_peak": f16_peak,
+                                                   "tensor_frac": tc_flops / t_near_b / 1e12 / f16_peak,
+                                                   "tensor_peak_source": f16_src} if tc_used else {})),
                               "apply_hbm_frac": (apply_bytes_b / (msb32 / nb_steps * 1e-3) / 1e9) / peak,
                               "stages_ms": dict(zip(stage_names, [float(x) / max(cb, 1) for x in stb]))},
                     "fp64": {"nrhs": NB64, "value": world * nb_steps * NB64 / (msb64 * 1e-3), "dtype": "f64"}},
@@ -638,6 +644,7 @@ def main():
                       "mixed": dict(zip(stage_names, [float(x) / max(c32, 1) for x in st32]))},
         "apply_hbm_frac_fp64": (apply_bytes64 / (ms64 / args.steps * 1e-3) / 1e9) / peak,
         "time_to_tol": solve,
+        "kernel_autotune": kernel_tune,
     }
     if batch is not None:
         line["batch"] = batch

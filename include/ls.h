@@ -272,11 +272,37 @@ ls_status ls_set_wait_limit(ls_plan plan, int polls);
  * on every SM) and of its TF32 tensor-core MMA (tcgen05, M = 128, N = 256,
  * K = 8, operands in shared memory, one issuing thread per SM), in TFLOP/s
  * counting 2 per multiply-add, timed with CUDA events (about 0.5 s in all).
- * These are the roofline denominators of the FP64 near field and of the
- * 3xTF32 tensor-core near field.  Host pointers; blocking; LS_ERR_CUDA on a
+ * The FP64 figure is the roofline denominator of the FP64 kernels; the TF32
+ * one is reported beside the tensor-core near field (which runs kind::f16).  Host pointers; blocking; LS_ERR_CUDA on a
  * CUDA error and LS_ERR_TIMEOUT if a (bounded) wait of the tensor-core probe
  * gave up, with the message in ls_last_error(NULL). */
 ls_status ls_measure_peaks(double* fp64_tflops, double* tf32_tflops);
+
+/* Kernel-variant autotuner of a 2-D plan (measurement on the plan's GPU, no
+ * counterpart in the paper; the cell layout is chosen before plan creation,
+ * see the Python autotune module).  It times, with CUDA events on a private
+ * stream and scratch vectors it allocates and frees, the variants of the
+ * apply that give the same result up to rounding, and keeps the fastest in
+ * the plan:
+ *   - columns per block of the lattice column pass (1, 2, 4), FP64 and
+ *     complex64 separately (FP64: one apply of min(nrhs, 4) right-hand sides);
+ *   - for a complex64 apply of nrhs right-hand sides: the right-hand-side
+ *     group per near-field launch (16, 8 or 4) and, for groups of 8 or more,
+ *     tensor cores (split FP16) or CUDA cores for the near field.
+ * The plan's device must be current (LS_ERR_INVALID otherwise); 3-D plans
+ * return LS_ERR_UNSUPPORTED; nrhs in [1, 64].  Blocking; drops the plan's
+ * captured applies.  report (host, may be NULL) receives the choice and the
+ * default and best times in milliseconds. */
+typedef struct {
+  int nrhs;                     /* complex64 right-hand sides timed per apply */
+  int conv_cols64, conv_cols32; /* chosen columns per block of the lattice column pass */
+  int group32;                  /* chosen complex64 right-hand-side group */
+  int near_cuda32;              /* 1: CUDA-core complex64 near field for groups >= 8; 0: tensor cores */
+  int n_candidates;             /* variants timed */
+  double ms64_default, ms64_best;
+  double ms32_default, ms32_best;
+} ls_tune_report;
+ls_status ls_plan_autotune(ls_plan plan, int nrhs, ls_tune_report* report);
 
 /* Per-stage device timing of ls_apply with CUDA events recorded on the call's
  * stream (measurement aid; enabling it makes ls_apply wait for each apply).

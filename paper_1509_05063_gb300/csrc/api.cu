@@ -192,6 +192,7 @@ struct ls_plan_s : DevOwner {
   std::vector<int64_t> canon3;      // 3-D: ball node id of each plan node
   double* ffw3 = nullptr;           // 3-D: w omega (n^2 - 1) per node (far field)
   GraphCache graphs;                // CUDA graphs of the apply
+  int group32 = lsd::kMaxRhs32;     // complex64 right-hand sides per apply launch (ls_plan_autotune)
   // optional per-stage event timing of ls_apply
   bool timing = false;
   cudaEvent_t ev[lsd::kStages + 1] = {};
@@ -1234,6 +1235,7 @@ ls_status ls_plan_create3(const ls_ball3* ball, const ls_rules3* rules, ls_n2_fn
     a.Sd = plan->alloc<double2>(size_t(M3), &st);
     a.gamma = plan->alloc<double2>(size_t(nocc) * nb, &st);
     a.X = plan->alloc<double2>(size_t(nocc) * K, &st);
+    a.X6 = plan->alloc<float>(size_t(6) * nocc * K, &st);
     a.part = plan->alloc<double2>(size_t(lsd::local3_slices(nocc, nb, K)) * nocc * nb, &st);
     if (st != LS_OK) return bail(st, plan->err);
     auto& b = plan->e32;
@@ -1368,7 +1370,7 @@ ls_status ls_apply(ls_plan plan, const void* u, void* Au, int nrhs, ls_precision
   const int64_t N = plan->d64.N;
   if (prec != LS_FP64 && prec != LS_MIXED) return fail(plan, LS_ERR_INVALID, "ls_apply: bad precision");
   cudaEvent_t* ev = plan->timing && plan->dim == 2 ? plan->ev : nullptr;
-  const int maxr = prec == LS_FP64 ? lsd::kMaxRhs64 : lsd::kMaxRhs32;
+  const int maxr = prec == LS_FP64 ? lsd::kMaxRhs64 : plan->group32;
   for (int r = 0; r < nrhs;) {
     int nr = maxr;                       // largest power of two batch that fits
     while (nr > nrhs - r) nr /= 2;
@@ -2018,7 +2020,7 @@ ls_status ls_solve(ls_plan plan, const void* uinc, void* u, int nrhs, double tol
     auto op32 = [&](const double2* v, double2* Av, const char*) -> cudaError_t {
       cudaError_t e = lsd::to_c64(v, plan->K.c64a, int64_t(R) * N, st);
       for (int r = 0; r < R && e == cudaSuccess;) {
-        int nr = lsd::kMaxRhs32;
+        int nr = plan->group32;
         while (nr > R - r) nr /= 2;
         e = run_apply(plan, LS_MIXED, plan->d32, plan->K.c64a + r * N, plan->K.c64b + r * N, nr, st);
         r += nr;
@@ -2030,7 +2032,7 @@ ls_status ls_solve(ls_plan plan, const void* uinc, void* u, int nrhs, double tol
     auto op32f = [&](const float2* v, float2* Av, const char*) -> cudaError_t {
       cudaError_t e = cudaSuccess;
       for (int r = 0; r < R && e == cudaSuccess;) {
-        int nr = lsd::kMaxRhs32;
+        int nr = plan->group32;
         while (nr > R - r) nr /= 2;
         e = run_apply(plan, LS_MIXED, plan->d32, v + r * N, Av + r * N, nr, st);
         r += nr;
@@ -2130,6 +2132,122 @@ ls_status ls_plan_device_status(ls_plan plan) {
   LS_CU(cudaMemset(plan->d32.tc_err, 0, sizeof(int)));
   return fail(plan, LS_ERR_TIMEOUT, "a device-side wait of the tensor-core near field timed out; "
                                     "the rows of the affected work items were not written");
+}
+
+ls_status ls_plan_autotune(ls_plan plan, int nrhs, ls_tune_report* report) {
+  if (!plan) return LS_ERR_INVALID;
+  if (plan->dim != 2) return fail(plan, LS_ERR_UNSUPPORTED, "ls_plan_autotune: 2-D plans only");
+  if (nrhs < 1 || nrhs > 64) return fail(plan, LS_ERR_INVALID, "ls_plan_autotune: nrhs must be in [1, 64]");
+  int cur = -1;
+  LS_CU(cudaGetDevice(&cur));
+  if (cur != plan->device) return fail(plan, LS_ERR_INVALID, "ls_plan_autotune: the plan's device is not current");
+  const int64_t N = plan->d64.N;
+  const int n64 = std::min(nrhs, lsd::kMaxRhs64);
+  ls_status st = LS_OK;
+  // scratch inputs (finite, not zero) and outputs; released before returning
+  double2* u64 = plan->alloc<double2>(size_t(n64) * N, &st);
+  double2* o64 = plan->alloc<double2>(size_t(n64) * N, &st);
+  float2* u32 = plan->alloc<float2>(size_t(nrhs) * N, &st);
+  float2* o32 = plan->alloc<float2>(size_t(nrhs) * N, &st);
+  cudaStream_t ts = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  auto cleanup = [&]() {
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (ts) cudaStreamDestroy(ts);
+    const void* scratch[4] = {u64, o64, u32, o32};
+    for (const void* p : scratch) plan->release(p);
+  };
+  if (st != LS_OK) {
+    cleanup();
+    return fail(plan, st, "ls_plan_autotune: " + plan->err);
+  }
+  cudaError_t ce = cudaStreamCreateWithFlags(&ts, cudaStreamNonBlocking);
+  if (ce == cudaSuccess) ce = cudaEventCreate(&e0);
+  if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
+  if (ce == cudaSuccess) ce = cudaMemsetAsync(u64, 0x3c, size_t(n64) * N * sizeof(double2), ts);
+  if (ce == cudaSuccess) ce = cudaMemsetAsync(u32, 0x3c, size_t(nrhs) * N * sizeof(float2), ts);
+  // mean milliseconds of one call of f (2 untimed, 5 timed); < 0 on a launch error
+  auto timed = [&](auto f) -> double {
+    for (int i = 0; i < 2; ++i)
+      if (f() != cudaSuccess) return -1.0;
+    cudaEventRecord(e0, ts);
+    for (int i = 0; i < 5; ++i)
+      if (f() != cudaSuccess) return -1.0;
+    cudaEventRecord(e1, ts);
+    if (cudaEventSynchronize(e1) != cudaSuccess) return -1.0;
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    return ms / 5;
+  };
+  ls_tune_report r{};
+  r.nrhs = nrhs;
+  const int conv_opts[3] = {1, 2, 4};
+  if (ce == cudaSuccess) {
+    // FP64: columns per block of the column pass
+    const int keep = plan->d64.conv_tc;
+    double best = -1;
+    int best_tc = 1;
+    for (int tc : conv_opts) {
+      plan->d64.conv_tc = tc;
+      const double ms = timed([&] { return lsd::apply_batch(plan->d64, u64, o64, n64, ts); });
+      cudaGetLastError();
+      ++r.n_candidates;
+      if (ms < 0) continue;
+      if (tc == 1) r.ms64_default = ms;
+      if (best < 0 || ms < best) { best = ms; best_tc = tc; }
+    }
+    plan->d64.conv_tc = best > 0 ? best_tc : keep;
+    r.conv_cols64 = plan->d64.conv_tc > 0 ? plan->d64.conv_tc : 1;
+    r.ms64_best = best;
+    // complex64: columns per block x right-hand-side group x near-field unit
+    const int keep_tc = plan->d32.conv_tc, keep_group = plan->group32;
+    const bool keep_cuda = plan->d32.near_cuda;
+    best = -1;
+    int bt = 1, bg = keep_group;
+    bool bc = false;
+    for (int tc : conv_opts)
+      for (int grp = 16; grp >= 4; grp /= 2)
+        for (int cuda = 0; cuda < 2; ++cuda) {
+          if (grp > std::max(4, nrhs) || (cuda && grp < 8)) continue;
+          plan->d32.conv_tc = tc;
+          plan->d32.near_cuda = cuda != 0;
+          const double ms = timed([&] {
+            for (int q = 0; q < nrhs;) {
+              int nr = grp;
+              while (nr > nrhs - q) nr /= 2;
+              const cudaError_t e = lsd::apply_batch(plan->d32, u32 + int64_t(q) * N, o32 + int64_t(q) * N, nr, ts);
+              if (e != cudaSuccess) return e;
+              q += nr;
+            }
+            return cudaSuccess;
+          });
+          cudaGetLastError();
+          ++r.n_candidates;
+          if (ms < 0) continue;
+          if (tc == 1 && grp == std::min(keep_group, std::max(4, nrhs)) && !cuda) r.ms32_default = ms;
+          if (best < 0 || ms < best) { best = ms; bt = tc; bg = grp; bc = cuda != 0; }
+        }
+    plan->d32.conv_tc = best > 0 ? bt : keep_tc;
+    plan->d32.near_cuda = best > 0 ? bc : keep_cuda;
+    plan->group32 = best > 0 ? bg : keep_group;
+    r.conv_cols32 = plan->d32.conv_tc > 0 ? plan->d32.conv_tc : 1;
+    r.group32 = plan->group32;
+    r.near_cuda32 = plan->d32.near_cuda ? 1 : 0;
+    r.ms32_best = best;
+    ce = cudaStreamSynchronize(ts);
+  }
+  cleanup();
+  plan->graphs.clear();          // captured applies hold the previous variants
+  if (ce != cudaSuccess) return fail(plan, LS_ERR_CUDA, std::string("ls_plan_autotune: ") + cudaGetErrorString(ce));
+  if (plan->d32.tc_err) {
+    int flag = 0;
+    LS_CU(cudaMemcpy(&flag, plan->d32.tc_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (flag) return fail(plan, LS_ERR_TIMEOUT, "ls_plan_autotune: a device-side wait of the tensor-core near field "
+                                                "timed out; see ls_plan_device_status");
+  }
+  if (report) *report = r;
+  return LS_OK;
 }
 
 ls_status ls_set_stage_timing(ls_plan plan, int enable) {

@@ -133,31 +133,51 @@ struct LineBox {
   int axis, n_out, ostep, n_in;
 };
 
-__device__ __forceinline__ int64_t line_addr(const LineBox& bx, int M, int64_t j, int e) {
-  const int64_t MM = int64_t(M) * M;
-  const int64_t o = (j / bx.n_in) * bx.ostep, i = j % bx.n_in;
-  if (bx.axis == 2) return o * MM + i * M + e;
-  if (bx.axis == 1) return o * MM + int64_t(e) * M + i;
-  return o * M + i + int64_t(e) * MM;
+// address of element e of line lj of the box (lines fewer than 2^31)
+__device__ __forceinline__ int64_t line_addr(const LineBox& bx, int logM, int lj, int e) {
+  const int64_t o = int64_t(lj / bx.n_in) * bx.ostep, i = lj % bx.n_in;
+  if (bx.axis == 2) return (o << (2 * logM)) + (i << logM) + e;
+  if (bx.axis == 1) return (o << (2 * logM)) + (int64_t(e) << logM) + i;
+  return (o << logM) + i + (int64_t(e) << (2 * logM));
 }
+
+// Every thread moves exactly M / G = 8 elements of the block's lines
+// (LPB lines x M elements over LPB G threads); the eight loads of a thread are
+// issued together before any is used.
+constexpr int kLineEl = 8;
 
 template <typename T>
 __global__ void __launch_bounds__(kT3) k3_fft_axis(T* __restrict__ X, int M, int logM, const T* __restrict__ tw,
                                                   bool inv, LineBox bx) {
   extern __shared__ __align__(16) unsigned char raw3[];
   T* s = reinterpret_cast<T*>(raw3);
-  const int G = M / 8, nt = blockDim.x, LPB = nt / G, t = threadIdx.x;
-  const int64_t l0 = int64_t(blockIdx.x) * LPB, nl = int64_t(bx.n_out) * bx.n_in;
-  for (int idx = t; idx < LPB * M; idx += nt) {
-    const int j = bx.axis == 2 ? idx / M : idx % LPB, e = bx.axis == 2 ? idx % M : idx / LPB;
-    s[j * (M + 1) + e] = l0 + j < nl ? X[line_addr(bx, M, l0 + j, e)] : czero(T());
+  const int G = M / 8, nt = blockDim.x, LPB = nt / G, lg = __ffs(LPB) - 1, t = threadIdx.x;
+  const int l0 = blockIdx.x * LPB, nl = bx.n_out * bx.n_in;
+  auto je = [&](int idx, int& j, int& e) {
+    if (bx.axis == 2) { j = idx >> logM; e = idx & (M - 1); }
+    else { j = idx & (LPB - 1); e = idx >> lg; }
+  };
+  T v[kLineEl];
+#pragma unroll
+  for (int q = 0; q < kLineEl; ++q) {
+    int j, e;
+    je(t + q * nt, j, e);
+    v[q] = l0 + j < nl ? X[line_addr(bx, logM, l0 + j, e)] : czero(T());
+  }
+#pragma unroll
+  for (int q = 0; q < kLineEl; ++q) {
+    int j, e;
+    je(t + q * nt, j, e);
+    s[j * (M + 1) + e] = v[q];
   }
   __syncthreads();
   fft_smem<T>(s + (t / G) * (M + 1), M, logM, inv, tw, t % G);
   __syncthreads();
-  for (int idx = t; idx < LPB * M; idx += nt) {
-    const int j = bx.axis == 2 ? idx / M : idx % LPB, e = bx.axis == 2 ? idx % M : idx / LPB;
-    if (l0 + j < nl) X[line_addr(bx, M, l0 + j, e)] = s[j * (M + 1) + e];
+#pragma unroll
+  for (int q = 0; q < kLineEl; ++q) {
+    int j, e;
+    je(t + q * nt, j, e);
+    if (l0 + j < nl) X[line_addr(bx, logM, l0 + j, e)] = s[j * (M + 1) + e];
   }
 }
 
@@ -172,27 +192,44 @@ __global__ void __launch_bounds__(kT3) k3_conv_a(T* __restrict__ Sm, const T* __
                                                 int logM, const T* __restrict__ tw, int a_max) {
   extern __shared__ __align__(16) unsigned char raw3[];
   T* s = reinterpret_cast<T*>(raw3);
-  const int G = M / 8, nt = blockDim.x, LPB = nt / G, H = LPB / 2, t = threadIdx.x;
-  const int64_t MM = int64_t(M) * M, l0 = int64_t(blockIdx.x) * H;
-  for (int idx = t; idx < LPB * M; idx += nt) {
-    const int j = idx % LPB, e = idx / LPB;
-    s[j * (M + 1) + e] = (j < H ? Sm : Sd)[l0 + (j % H) + int64_t(e) * MM];
+  const int G = M / 8, nt = blockDim.x, LPB = nt / G, H = LPB / 2, lg = __ffs(LPB) - 1, t = threadIdx.x;
+  const int64_t l0 = int64_t(blockIdx.x) * H;
+  T v[kLineEl];
+#pragma unroll
+  for (int q = 0; q < kLineEl; ++q) {
+    const int idx = t + q * nt, j = idx & (LPB - 1), e = idx >> lg;
+    v[q] = (j < H ? Sm : Sd)[l0 + (j % H) + (int64_t(e) << (2 * logM))];
+  }
+#pragma unroll
+  for (int q = 0; q < kLineEl; ++q) {
+    const int idx = t + q * nt, j = idx & (LPB - 1), e = idx >> lg;
+    s[j * (M + 1) + e] = v[q];
   }
   __syncthreads();
   fft_smem<T>(s + (t / G) * (M + 1), M, logM, false, tw, t % G);
   __syncthreads();
-  for (int idx = t; idx < H * M; idx += nt) {
-    const int j = idx % H, e = idx / H;
-    const int64_t ad = l0 + j + int64_t(e) * MM;
-    T* v = s + j * (M + 1) + e;
-    *v = cfma(v[H * (M + 1)], Ds[ad], cmul(*v, Gs[ad]));
+  // H M = nt kLineEl / 2 products: four per thread, the spectra loaded together
+  T gs[kLineEl / 2], ds[kLineEl / 2];
+#pragma unroll
+  for (int q = 0; q < kLineEl / 2; ++q) {
+    const int idx = t + q * nt, j = idx % H, e = idx / H;
+    const int64_t ad = l0 + j + (int64_t(e) << (2 * logM));
+    gs[q] = Gs[ad];
+    ds[q] = Ds[ad];
+  }
+#pragma unroll
+  for (int q = 0; q < kLineEl / 2; ++q) {
+    const int idx = t + q * nt, j = idx % H, e = idx / H;
+    T* w = s + j * (M + 1) + e;
+    *w = cfma(w[H * (M + 1)], ds[q], cmul(*w, gs[q]));
   }
   __syncthreads();
   fft_smem<T>(s + (t / G) * (M + 1), M, logM, true, tw, t % G, 1, t / G < H);
   __syncthreads();
-  for (int idx = t; idx < H * M; idx += nt) {
-    const int j = idx % H, e = idx / H;
-    if (e <= a_max) Sm[l0 + j + int64_t(e) * MM] = s[j * (M + 1) + e];
+#pragma unroll
+  for (int q = 0; q < kLineEl / 2; ++q) {
+    const int idx = t + q * nt, j = idx % H, e = idx / H;
+    if (e <= a_max) Sm[l0 + j + (int64_t(e) << (2 * logM))] = s[j * (M + 1) + e];
   }
 }
 
@@ -211,15 +248,32 @@ __global__ void __launch_bounds__(kT3) k3_spectral(T* __restrict__ Sm, const T* 
 // one of S slices of K (enough blocks to fill the GPU); k3_reduce adds the S
 // partial products in slice order.
 template <typename T>
-__global__ void __launch_bounds__(kT3) k3_gather(ApplyData3<T> d) {
+__global__ void __launch_bounds__(kT3) k3_gather(ApplyData3<T> d, bool df) {
   const int k = blockIdx.x, t = threadIdx.x, L = d.L, Ne = d.Ne, n1 = Ne + 1;
   const int cell = d.occ_cells[k], ci = cell % L, cj = (cell / L) % L, ck = cell / (L * L);
   const int64_t MM = int64_t(d.M) * d.M;
   const int K = d.n_loc + 27 * d.n_es;
-  T* x = d.X + int64_t(k) * K;
+  // FP64 GEMM: X as is; double-float GEMM (FP64 data only): the forms
+  // (c, c + d, d - c) of each entry split into FP32 hi + lo, 6 floats
+  auto put = [&](int p, T v) {
+    if constexpr (sizeof(T) == 16) {
+      if (df) {
+        const double f[3] = {v.x, v.x + v.y, v.y - v.x};
+        float* w = d.X6 + 6 * (int64_t(k) * K + p);
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+          const float hi = float(f[q]);
+          w[2 * q] = hi;
+          w[2 * q + 1] = float(f[q] - double(hi));
+        }
+        return;
+      }
+    }
+    d.X[int64_t(k) * K + p] = v;
+  };
   for (int p = t; p < d.n_loc; p += kT3) {
     const int la = p / (n1 * n1), lb = (p / n1) % n1, lc = p % n1;
-    x[p] = d.Sm[int64_t(ci * Ne + la) * MM + int64_t(cj * Ne + lb) * d.M + (ck * Ne + lc)];
+    put(p, d.Sm[int64_t(ci * Ne + la) * MM + int64_t(cj * Ne + lb) * d.M + (ck * Ne + lc)]);
   }
   for (int p = t; p < 27 * d.n_es; p += kT3) {
     const int o = p / d.n_es, l = p % d.n_es;
@@ -229,7 +283,7 @@ __global__ void __launch_bounds__(kT3) k3_gather(ApplyData3<T> d) {
       const int occ = d.occ_of_cell[(nk * L + nj) * L + ni];
       if (occ >= 0) v = d.sigma[int64_t(occ) * d.n_es + l];
     }
-    x[d.n_loc + p] = v;
+    put(d.n_loc + p, v);
   }
 }
 
@@ -339,15 +393,19 @@ __global__ void __launch_bounds__(kT3) k3_gemm_df(ApplyData3<double2> d, int S) 
       for (int f = 0; f < 3; ++f) hs[a][b][f] = hc[a][b][f] = 0.f;
   for (int k0 = kb; k0 < ke; k0 += kGK) {
     __syncthreads();
-    for (int i = t; i < kGK * kGC; i += kT3) {        // X tile: forms (c, c + d, d - c), split
+    for (int i = t; i < kGK * kGC; i += kT3) {        // X tile, already in the split forms
       const int kk = i % kGK, cc = i / kGK, c = c0 + cc, kg = k0 + kk;
-      const double2 v = (c < d.nocc && kg < ke) ? d.X[int64_t(c) * K + kg] : make_double2(0, 0);
-      const double f[3] = {v.x, v.x + v.y, v.y - v.x};
       DF6 w;
+      if (c < d.nocc && kg < ke) {
+        const float* src = d.X6 + 6 * (int64_t(c) * K + kg);
 #pragma unroll
-      for (int q = 0; q < 3; ++q) {
-        w.h[q] = float(f[q]);
-        w.l[q] = float(f[q] - double(w.h[q]));
+        for (int q = 0; q < 3; ++q) {
+          w.h[q] = src[2 * q];
+          w.l[q] = src[2 * q + 1];
+        }
+      } else {
+#pragma unroll
+        for (int q = 0; q < 3; ++q) w.h[q] = w.l[q] = 0.f;
       }
       xs[kk][cc] = w;
     }
@@ -570,7 +628,7 @@ cudaError_t lattice_local(const ApplyData3<T>& d, cudaStream_t st, bool df = fal
   if (e == cudaSuccess) e = fft_box<T>(d.Sm, M, d.logM, d.tw, true, LineBox{2, nl + 1, 1, nl + 1}, st);
   if (e != cudaSuccess) return e;
   const int K = d.n_loc + 27 * d.n_es, S = local_slices(d.nocc, d.nb, K);
-  k3_gather<T><<<d.nocc, kT3, 0, st>>>(d);
+  k3_gather<T><<<d.nocc, kT3, 0, st>>>(d, df);
   const dim3 grid((d.nocc + kGC - 1) / kGC, (d.nb + kGN - 1) / kGN, S);
   if constexpr (sizeof(T) == 16) {
     if (df) k3_gemm_df<<<grid, kT3, 0, st>>>(d, S);

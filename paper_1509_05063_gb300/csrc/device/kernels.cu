@@ -460,7 +460,8 @@ template <typename T>
 cudaError_t lattice_conv(const ApplyData<T>& d, int nr, cudaStream_t st) {
   const int M = d.M;
   if (M < 256 || M > kFftMaxM || (M & (M - 1))) return cudaErrorInvalidValue;
-  const int TC = conv_cols_tc<T>(M);
+  const int TC = d.conv_tc > 0 ? d.conv_tc : conv_cols_tc<T>(M);
+  if (M % TC != 0 || TC * (M / 8) > 1024 || size_t(2) * TC * M * sizeof(T) > 200 * 1024) return cudaErrorInvalidValue;
   static unsigned long long attr_done = 0;
   if (first_on_device(attr_done)) {
     cudaFuncSetAttribute(k_src_rows<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kFftMaxM * sizeof(T)));
@@ -860,8 +861,15 @@ cudaError_t apply_r(const ApplyData<T>& d, const T* u, T* out, cudaStream_t st, 
                                                        d.lattice_rows() * d.M);
   if (ev) cudaEventRecord(ev[4], st);
   if constexpr (sizeof(T) == 8 && R >= 8) {
-    const cudaError_t e2 = near_eval_tc<R>(d, u, out, st);
-    if (e2 != cudaSuccess) return e2;
+    if (!d.near_cuda) {
+      const cudaError_t e2 = near_eval_tc<R>(d, u, out, st);
+      if (e2 != cudaSuccess) return e2;
+    } else {
+      k_near_eval4<T, R><<<d.n_items32, 256, kNearSmem, st>>>(d.items32, d.occ_start, d.blk_off, d.blk_seg, d.Wb,
+                                                              d.Ws, d.rem_row, d.rem_col, d.rem_val, u, d.utc, d.utef,
+                                                              d.N, d.Phi, d.gamma, d.nocc, d.nfb2,
+                                                              typename RealOf<T>::R(d.kappa2), out);
+    }
   } else if constexpr (near_rows_per_warp<T, R>() == 4)
     k_near_eval4<T, R><<<d.n_items32, 256, kNearSmem, st>>>(d.items32, d.occ_start, d.blk_off, d.blk_seg, d.Wb,
                                                             d.Ws, d.rem_row, d.rem_col, d.rem_val, u, d.utc, d.utef, d.N, d.Phi,

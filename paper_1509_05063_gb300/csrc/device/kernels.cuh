@@ -57,6 +57,9 @@ struct ApplyData {
   const int* tc_bptr = nullptr;         // tensor-core grid: block b walks items tc_blist[tc_bptr[b] .. tc_bptr[b + 1])
   const int* tc_blist = nullptr;
   int tc_grid = 0;                      // blocks of the tensor-core grid (one per SM of the plan's device)
+  // variants picked by ls_plan_autotune (same result up to rounding)
+  int conv_tc = 0;                      // columns per block of the lattice column pass (0: default, 1)
+  bool near_cuda = false;               // complex64, 8 or 16 RHS: CUDA-core near field instead of tensor cores
   const T* Wt = nullptr;                // complex64 only: the blocks in the tensor-core tile layout
   const float* tc_rscale = nullptr;     // complex64 only: 1 / (power-of-two scale) of each near-field row
   unsigned* tc_tmax = nullptr;          // complex64 only: per-RHS largest |Re|, |Im| of one apply (float bits)
@@ -145,6 +148,7 @@ struct ApplyData3 {
   T* Sd = nullptr;                      // M^3: dipole lattice
   T* gamma = nullptr;                   // nocc x nb
   T* X = nullptr;                       // FP64 data only: nocc x (n_loc + 27 n_es), inputs of the local step
+  float* X6 = nullptr;                  // FP64 data only: the same in the double-float GEMM's split forms
   T* part = nullptr;                    // FP64 data only: local3_slices x nocc x nb partial products
   // complex64 only (host pointer): the FP64 data whose lattice convolution
   // (FP64) and local coefficients (double-float GEMM) the complex64 apply

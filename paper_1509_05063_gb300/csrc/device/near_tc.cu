@@ -67,7 +67,8 @@ constexpr int kRowGroup = 8 * kKG * 16;      // bytes of one 8-row group of a ch
 constexpr int kHalf = 16 * kRowGroup;        // 128 rows, hi or lo: 8 KB
 constexpr int kAStage = 2 * kHalf;           // a weight stage: hi, then lo
 constexpr int kNA = 12;                      // weight stages (bulk-copy ring)
-constexpr int kNC = 4;                       // B operand slots = B warps
+constexpr int kNC = 6;                       // B operand slots = B warps
+constexpr int kAhead = 1;                    // owned chunks a B warp gathers ahead of its split (1 or 2)
 constexpr int kSets = 2;                     // accumulator sets per item (K step k uses set k mod kSets)
 constexpr int kThreads = 32 * (6 + kNC);
 constexpr int kDrainPolls = 1 << 28;         // bound of the final waits on the block's own MMAs / copies
@@ -156,7 +157,8 @@ struct TcLayout {
   static constexpr int kB = NN * kKG * 16;                      // B operand of a chunk
   static constexpr int kTmemCols = 2 * kSets * NN < 32 ? 32 : 2 * kSets * NN;
   static constexpr int kBarOff = kNA * kAStage + kNC * kB;
-  static constexpr int kBytes = kBarOff + 320;                  // + mbarriers, tensor-memory address, flag
+  // + mbarriers (2 kNA + 2 kNC + 5), tensor-memory address, flag
+  static constexpr int kBytes = kBarOff + 8 * (2 * kNA + 2 * kNC + 5) + 16;
 };
 
 // (hi, lo) fp16 split of a scaled value
@@ -384,10 +386,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_near_tc(const int2* __restrict_
     const int j = lane % R;                        // this lane's right-hand side, for every value it moves
     const float tsj = pow2_scale(__uint_as_float(tmax[j]));
     const float2* uj = u + int64_t(j) * N;
-    // gathers of a chunk's inputs go out one owned chunk ahead: the loads of
-    // chunk g are in flight while chunk g - kNC is split into its slot
-    float2 cur[kVals], nxt[kVals];
-    int cur_use = -1;
+    // gathers of a chunk's inputs go out kAhead owned chunks ahead: the loads
+    // of chunk g are in flight while chunks g - kNC, ... are split into the slot
+    float2 pa[kVals], pb[kVals], nx[kVals];
+    int ua = -1, ub = -1;                          // uses of the pending chunks (-1: none)
     auto build = [&](const float2* uv, int use) -> bool {
       if (use > 0 && !wait_phase(s_u32(&b_empty[bw]), (use - 1) & 1, spin, sflag)) return false;
       unsigned char* B = Bring + bw * Lay::kB;
@@ -425,18 +427,25 @@ __global__ void __launch_bounds__(kThreads, 1) k_near_tc(const int2* __restrict_
           if (col < p0) { if (col < l0) node = sg[0] + col; }
           else if (col < p0 + p1) { const int o = col - p0; if (o < l1) node = sg[2] + o; }
           else if (col < ig.nblk) { const int o = col - p0 - p1; if (o < l2) node = sg[4] + o; }
-          nxt[i] = node >= 0 ? uj[node] : make_float2(0.f, 0.f);
+          nx[i] = node >= 0 ? uj[node] : make_float2(0.f, 0.f);
         }
-        if (cur_use >= 0 && !build(cur, cur_use)) {
-          live = false;
-          break;
-        }
+        if constexpr (kAhead == 1) {
+          if (ua >= 0 && !build(pa, ua)) { live = false; break; }
 #pragma unroll
-        for (int i = 0; i < kVals; ++i) cur[i] = nxt[i];
-        cur_use = g / kNC;
+          for (int i = 0; i < kVals; ++i) pa[i] = nx[i];
+          ua = g / kNC;
+        } else {
+          if (ua >= 0 && !build(pa, ua)) { live = false; break; }
+#pragma unroll
+          for (int i = 0; i < kVals; ++i) { pa[i] = pb[i]; pb[i] = nx[i]; }
+          ua = ub;
+          ub = g / kNC;
+        }
       }
     }
-    if (live && cur_use >= 0) build(cur, cur_use);
+    if (live && ua >= 0) live = build(pa, ua);
+    if constexpr (kAhead == 2)
+      if (live && ub >= 0) build(pb, ub);
   } else {
     // ------------------------------------------------ epilogue (warps 2..5)
     const int row_in = 32 * (warp & 3) + lane;     // tensor-memory lane quarter of this warp

@@ -62,6 +62,12 @@ class SolveInfo(C.Structure):
                 ("seconds", C.c_double)]
 
 
+class TuneReport(C.Structure):
+    _fields_ = [("nrhs", C.c_int), ("conv_cols64", C.c_int), ("conv_cols32", C.c_int), ("group32", C.c_int),
+                ("near_cuda32", C.c_int), ("n_candidates", C.c_int), ("ms64_default", C.c_double),
+                ("ms64_best", C.c_double), ("ms32_default", C.c_double), ("ms32_best", C.c_double)]
+
+
 N2FN = C.CFUNCTYPE(C.c_int, C.c_int64, C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_void_p)
 
 _lib = None
@@ -105,6 +111,7 @@ _SIGS = {
     "ls_plan_device_status": ([C.c_void_p]),
     "ls_set_wait_limit": ([C.c_void_p, C.c_int]),
     "ls_measure_peaks": ([C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    "ls_plan_autotune": ([C.c_void_p, C.c_int, C.POINTER(TuneReport)]),
     "ls_plan_create3": ([C.c_void_p, C.c_void_p, N2FN, C.c_void_p, C.c_double, C.c_void_p, C.POINTER(C.c_void_p)]),
     "ls_batch_create": ([C.c_void_p, C.c_int, C.POINTER(C.c_void_p)]),
     "ls_batch_offsets": ([C.c_void_p, C.c_void_p]),
@@ -277,6 +284,15 @@ class Plan:
     def device_status(self):
         """Raise LSError (status 5) if a device-side wait timed out since the last check."""
         _check(_lib.ls_plan_device_status(self._h), self._h)
+
+    def autotune(self, nrhs: int = 16):
+        """Time the apply's kernel variants on this plan's GPU and keep the
+        fastest (ls_plan_autotune): lattice column-pass width (FP64 and
+        complex64), complex64 right-hand-side group and near-field unit.
+        Returns the choice and the default / best milliseconds."""
+        r = TuneReport()
+        _check(_lib.ls_plan_autotune(self._h, int(nrhs), C.byref(r)), self._h)
+        return {f: getattr(r, f) for f, _ in TuneReport._fields_}
 
     def set_wait_limit(self, polls: int):
         """Polls per device-side wait of the tensor-core near field (0: every wait gives up)."""
