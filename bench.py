@@ -40,10 +40,10 @@ KERNELS_PER_APPLY = 6    # projection, source rows (fill + row FFT), columns (FF
 # (358 205 610 near-field entries), from the ncu capture of the half-resolution kite
 # summarised in profiles/near_field_kite_dram.md, scaled to the full launch by the
 # ratio of algorithmic bytes (DRAM / algorithmic there: FP64 1.017, complex64 1.005,
-# tensor cores 1.067).  Keyed by the plan's near-field entry count and by kernel:
+# tensor cores 1.030).  Keyed by the plan's near-field entry count and by kernel:
 # another workload, or a kernel changed since the capture (remove its entry then),
 # reports null.
-NEAR_TRAFFIC = {358205610: {"fp64": 8.892e9, "mixed": 2.955e9}}
+NEAR_TRAFFIC = {358205610: {"fp64": 8.892e9, "mixed": 2.955e9, "tc16": 3.106e9}}
 
 
 def hbm_peak():
@@ -382,7 +382,7 @@ def main():
                     help="incident directions of the lock-step mixed solve (theta_j = 2 pi j / D)")
     ap.add_argument("--batch", type=int, default=12,
                     help="also time a multi-instance batch of this many seeded scatterers (reduced config 3)")
-    ap.add_argument("--sphere", default="25,9,0.1,7,4",
+    ap.add_argument("--sphere", default="49,17,0.05,14,4",
                     help="reduced config 4 (penetrable sphere, kappa = 8): n_f,n_s,h,L,N_eq; 'none' to skip")
     ap.add_argument("--scale", type=int, default=1,
                     help="coarsen config 2 by this factor (h, cells) for profiling captures")

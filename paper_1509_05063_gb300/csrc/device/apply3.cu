@@ -503,13 +503,21 @@ __global__ void __launch_bounds__(kT3) k3_near(ApplyData3<T> d, const T* __restr
 #pragma unroll
     for (int s9 = 0; s9 < 9; ++s9) nblk += sg[2 * s9 + 1];
     const T* w = d.Wb + d.blk_off[k] + (q - d.occ_start[k]) * nblk;
+    T acc2 = czero(T());                 // two chains: loads of the next entries overlap the FMAs
 #pragma unroll 1
     for (int s9 = 0; s9 < 9; ++s9) {
       const int n0 = sg[2 * s9], len = sg[2 * s9 + 1];
       const T* uu = u + n0;
-      for (int e = lane; e < len; e += 32) acc = cfma(w[e], uu[e], acc);
+      int e = lane;
+#pragma unroll 2
+      for (; e + 32 < len; e += 64) {
+        acc = cfma(w[e], uu[e], acc);
+        acc2 = cfma(w[e + 32], uu[e + 32], acc2);
+      }
+      if (e < len) acc = cfma(w[e], uu[e], acc);
       w += len;
     }
+    acc = cadd(acc, acc2);
     for (int64_t e = d.rowptr[q] + lane; e < d.rowptr[q + 1]; e += 32) acc = cfma(d.val[e], u[d.col[e]], acc);
   }
   const T* ph = d.Phi + q * d.nb;
