@@ -147,8 +147,9 @@ __device__ __forceinline__ int64_t line_addr(const LineBox& bx, int logM, int lj
 constexpr int kLineEl = 8;
 
 template <typename T>
-__global__ void __launch_bounds__(kT3) k3_fft_axis(T* __restrict__ X, int M, int logM, const T* __restrict__ tw,
-                                                  bool inv, LineBox bx) {
+__global__ void __launch_bounds__(kT3) k3_fft_axis(T* __restrict__ X0, T* __restrict__ X1, int M, int logM,
+                                                  const T* __restrict__ tw, bool inv, LineBox bx) {
+  T* __restrict__ X = blockIdx.y == 0 ? X0 : X1;     // the same pass over one or two arrays
   extern __shared__ __align__(16) unsigned char raw3[];
   T* s = reinterpret_cast<T*>(raw3);
   const int G = M / 8, nt = blockDim.x, LPB = nt / G, lg = __ffs(LPB) - 1, t = threadIdx.x;
@@ -585,7 +586,7 @@ int lines_per_block(int M, int64_t lines) {
 }
 
 template <typename T>
-cudaError_t fft_box(T* x, int M, int logM, const T* tw, bool inverse, LineBox bx, cudaStream_t st) {
+cudaError_t fft_box(T* x, T* x1, int M, int logM, const T* tw, bool inverse, LineBox bx, cudaStream_t st) {
   static unsigned long long attr = 0;
   if (first_on_device(attr)) {
     const cudaError_t e = cudaFuncSetAttribute(k3_fft_axis<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
@@ -593,8 +594,8 @@ cudaError_t fft_box(T* x, int M, int logM, const T* tw, bool inverse, LineBox bx
   }
   const int64_t lines = int64_t(bx.n_out) * bx.n_in;
   const int LPB = lines_per_block(M, lines);
-  k3_fft_axis<T><<<int((lines + LPB - 1) / LPB), LPB * (M / 8), fft_smem_bytes(M, LPB, sizeof(T)), st>>>(
-      x, M, logM, tw, inverse, bx);
+  const dim3 grid(unsigned((lines + LPB - 1) / LPB), x1 ? 2 : 1);
+  k3_fft_axis<T><<<grid, LPB * (M / 8), fft_smem_bytes(M, LPB, sizeof(T)), st>>>(x, x1, M, logM, tw, inverse, bx);
   return cudaGetLastError();
 }
 
@@ -610,11 +611,9 @@ cudaError_t lattice_local(const ApplyData3<T>& d, cudaStream_t st, bool df = fal
   const int M = d.M, nl = d.L * d.Ne;
   k3_fill<T><<<grid_for(n3), kT3, 0, st>>>(d);
   cudaError_t e = cudaSuccess;
-  T* const both[2] = {d.Sm, d.Sd};
-  for (T* x : both) {
-    if (e == cudaSuccess) e = fft_box<T>(x, M, d.logM, d.tw, false, LineBox{2, d.L + 1, d.Ne, nl + 1}, st);
-    if (e == cudaSuccess) e = fft_box<T>(x, M, d.logM, d.tw, false, LineBox{1, d.L + 1, d.Ne, M}, st);
-  }
+  // forward c and b passes of both arrays, two launches
+  e = fft_box<T>(d.Sm, d.Sd, M, d.logM, d.tw, false, LineBox{2, d.L + 1, d.Ne, nl + 1}, st);
+  if (e == cudaSuccess) e = fft_box<T>(d.Sm, d.Sd, M, d.logM, d.tw, false, LineBox{1, d.L + 1, d.Ne, M}, st);
   if (e != cudaSuccess) return e;
   if (M <= 1024) {
     static unsigned long long attr = 0;
@@ -626,14 +625,13 @@ cudaError_t lattice_local(const ApplyData3<T>& d, cudaStream_t st, bool df = fal
     k3_conv_a<T><<<int(int64_t(M) * M / H), LPB * (M / 8), fft_smem_bytes(M, LPB, sizeof(T)), st>>>(
         d.Sm, d.Sd, d.Gs, d.Ds, M, d.logM, d.tw, nl);
   } else {
-    for (T* x : both)
-      if (e == cudaSuccess) e = fft_box<T>(x, M, d.logM, d.tw, false, LineBox{0, M, 1, M}, st);
+    e = fft_box<T>(d.Sm, d.Sd, M, d.logM, d.tw, false, LineBox{0, M, 1, M}, st);
     if (e != cudaSuccess) return e;
     k3_spectral<T><<<grid_for(n3), kT3, 0, st>>>(d.Sm, d.Sd, d.Gs, d.Ds, n3);
-    e = fft_box<T>(d.Sm, M, d.logM, d.tw, true, LineBox{0, M, 1, M}, st);
+    e = fft_box<T>(d.Sm, nullptr, M, d.logM, d.tw, true, LineBox{0, M, 1, M}, st);
   }
-  if (e == cudaSuccess) e = fft_box<T>(d.Sm, M, d.logM, d.tw, true, LineBox{1, nl + 1, 1, M}, st);
-  if (e == cudaSuccess) e = fft_box<T>(d.Sm, M, d.logM, d.tw, true, LineBox{2, nl + 1, 1, nl + 1}, st);
+  if (e == cudaSuccess) e = fft_box<T>(d.Sm, nullptr, M, d.logM, d.tw, true, LineBox{1, nl + 1, 1, M}, st);
+  if (e == cudaSuccess) e = fft_box<T>(d.Sm, nullptr, M, d.logM, d.tw, true, LineBox{2, nl + 1, 1, nl + 1}, st);
   if (e != cudaSuccess) return e;
   const int K = d.n_loc + 27 * d.n_es, S = local_slices(d.nocc, d.nb, K);
   k3_gather<T><<<d.nocc, kT3, 0, st>>>(d, df);
@@ -678,7 +676,7 @@ cudaError_t fft3d(T* x, int M, int logM, const T* tw, bool inverse, cudaStream_t
   if (M < 16 || M > 2048 || (M & (M - 1))) return cudaErrorInvalidValue;
   cudaError_t e = cudaSuccess;
   for (int axis = 2; axis >= 0 && e == cudaSuccess; --axis)
-    e = fft_box<T>(x, M, logM, tw, inverse, LineBox{axis, M, 1, M}, st);
+    e = fft_box<T>(x, nullptr, M, logM, tw, inverse, LineBox{axis, M, 1, M}, st);
   return e;
 }
 
