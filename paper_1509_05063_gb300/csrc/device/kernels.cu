@@ -387,16 +387,22 @@ __global__ void __launch_bounds__(1024) k_conv_cols(int M, int logM, int n_lat, 
     const bool act = t < 2 * Gs;
     const int which = t / Gs;                  // 0 monopole, 1 dipole
     fft_smem<T>(xd + c * M + (act ? which : 0) * Ms, Ms, logMs, false, tw, act ? t % Gs : 0, M / Ms, act);
-    for (int e = threadIdx.x; e < TC * M; e += blockDim.x) {
-      const int cc = e / M, a = e % M;
-      const int b = b0 + cc;
-      const int kq = a <= half ? a : M - a;
-      const int lq = b <= half ? b : M - b;
+    // TC M products over TC M / 8 threads: eight per thread, the spectra loaded together
+    T gq[8], dq[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int e = threadIdx.x + q * blockDim.x, cc = e >> logM, a = e & (M - 1), b = b0 + cc;
+      const int kq = a <= half ? a : M - a, lq = b <= half ? b : M - b;
       const int64_t qi = int64_t(lq) * (half + 1) + kq;
-      T d = Dq[qi];
-      if (a > half) d = mk(-d.x, -d.y);        // dipole table is odd in the a offset
+      gq[q] = Gq[qi];
+      dq[q] = Dq[qi];
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int e = threadIdx.x + q * blockDim.x, cc = e >> logM, a = e & (M - 1);
+      const T d = a > half ? mk(-dq[q].x, -dq[q].y) : dq[q];   // dipole table is odd in the a offset
       const int f = a & (Ms - 1);
-      xm[e] = cfma(xd[cc * M + Ms + f], d, cmul(xd[cc * M + f], Gq[qi]));
+      xm[e] = cfma(xd[cc * M + Ms + f], d, cmul(xd[cc * M + f], gq[q]));
     }
     __syncthreads();
   } else {
@@ -414,15 +420,20 @@ __global__ void __launch_bounds__(1024) k_conv_cols(int M, int logM, int n_lat, 
     __syncthreads();
     fft_smem<T>(xm + c * M, M, logM, false, tw, t);
     fft_smem<T>(xd + c * M, M, logM, false, tw, t);
-    for (int e = threadIdx.x; e < TC * M; e += blockDim.x) {
-      const int cc = e / M, a = e % M;
-      const int b = b0 + cc;
-      const int kq = a <= half ? a : M - a;
-      const int lq = b <= half ? b : M - b;
+    T gq[8], dq[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int e = threadIdx.x + q * blockDim.x, cc = e >> logM, a = e & (M - 1), b = b0 + cc;
+      const int kq = a <= half ? a : M - a, lq = b <= half ? b : M - b;
       const int64_t qi = int64_t(lq) * (half + 1) + kq;
-      T d = Dq[qi];
-      if (a > half) d = mk(-d.x, -d.y);        // dipole table is odd in the a offset
-      xm[e] = cfma(xd[e], d, cmul(xm[e], Gq[qi]));
+      gq[q] = Gq[qi];
+      dq[q] = Dq[qi];
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int e = threadIdx.x + q * blockDim.x, a = e & (M - 1);
+      const T d = a > half ? mk(-dq[q].x, -dq[q].y) : dq[q];   // dipole table is odd in the a offset
+      xm[e] = cfma(xd[e], d, cmul(xm[e], gq[q]));
     }
     __syncthreads();
   }
@@ -442,7 +453,11 @@ __global__ void __launch_bounds__(kFftMaxM / 8) k_inv_rows(int M, int logM, int 
   const T* Vt = Vt_all + int64_t(blockIdx.y) * stride;
   T* V = V_all + int64_t(blockIdx.y) * stride;
   const int64_t a = blockIdx.x;
-  for (int b = threadIdx.x; b < M; b += blockDim.x) s[b] = Vt[a * M + b];
+  T v[8];                                      // M / 8 threads: eight loads each, issued together
+#pragma unroll
+  for (int q = 0; q < 8; ++q) v[q] = Vt[a * M + threadIdx.x + q * blockDim.x];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) s[threadIdx.x + q * blockDim.x] = v[q];
   __syncthreads();
   fft_smem<T>(s, M, logM, true, tw, threadIdx.x);
   for (int b = threadIdx.x; b < n_lat; b += blockDim.x) V[a * M + b] = s[b];
