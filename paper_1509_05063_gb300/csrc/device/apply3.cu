@@ -290,6 +290,9 @@ __global__ void __launch_bounds__(kT3) k3_gather(ApplyData3<T> d, bool df) {
 
 constexpr int kGC = 32, kGN = 32, kGK = 16;   // GEMM tile: cells x outputs x K step
 
+// K entries of each of the S slices: whole K steps; S of them cover K
+__host__ __device__ inline int slice_len(int K, int S) { return ((K + S - 1) / S + kGK - 1) / kGK * kGK; }
+
 // block (cell tile, output tile, slice s): thread (tc, tn) accumulates cells
 // tc, tc + 16 against outputs tn, tn + 16 over its slice of K.  Complex
 // products take three real multiplications (Gauss's form): with a + ib an
@@ -307,7 +310,7 @@ __global__ void __launch_bounds__(kT3) k3_gemm(ApplyData3<T> d, int S) {
   __shared__ G3<R> as[kGK][kGN];
   const int K = d.n_loc + 27 * d.n_es;
   const int c0 = blockIdx.x * kGC, n0 = blockIdx.y * kGN, sl = blockIdx.z;
-  const int kper = (K + S - 1) / S, kb = sl * kper, ke = kb + kper < K ? kb + kper : K;
+  const int kper = slice_len(K, S), kb = sl * kper, ke = kb + kper < K ? kb + kper : K;
   const int t = threadIdx.x, tc = t / 16, tn = t % 16;
   R P[2][2], Q[2][2], U[2][2];
 #pragma unroll
@@ -383,7 +386,7 @@ __global__ void __launch_bounds__(kT3) k3_gemm_df(ApplyData3<double2> d, int S) 
   __shared__ DF6 as[kGK][kGN];
   const int K = d.n_loc + 27 * d.n_es;
   const int c0 = blockIdx.x * kGC, n0 = blockIdx.y * kGN, sl = blockIdx.z;
-  const int kper = (K + S - 1) / S, kb = sl * kper, ke = kb + kper < K ? kb + kper : K;
+  const int kper = slice_len(K, S), kb = sl * kper, ke = kb + kper < K ? kb + kper : K;
   const int t = threadIdx.x, tc = t / 16, tn = t % 16;
   float hs[2][2][3], hc[2][2][3];
 #pragma unroll
@@ -472,7 +475,11 @@ __host__ __device__ inline int local_slices(int nocc, int nb, int K) {
   const int smax = K / (4 * kGK) > 1 ? K / (4 * kGK) : 1;
   if (S > smax) S = smax;
   if (S > kLocalSlicesMax) S = kLocalSlicesMax;
-  return S < 1 ? 1 : S;
+  if (S < 1) S = 1;
+  // whole K steps per slice (no step half padded with zeros), then as few
+  // slices as cover K with that length
+  const int len = slice_len(K, S);
+  return (K + len - 1) / len;
 }
 
 // warp per row: stored adjacent part (CSR) and the local expansion of the

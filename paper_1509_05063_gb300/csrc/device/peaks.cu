@@ -1,8 +1,8 @@
 // Throughput probes of this GPU's arithmetic units, for the roofline
 // denominators of the kernels that are not HBM-bound: FP64 fused multiply-add
-// on the CUDA cores, and TF32 MMA on the tensor cores (tcgen05, the rate the
-// 3xTF32 near field draws on).  Both run one launch over every SM and are
-// timed with CUDA events on the launching stream.
+// on the CUDA cores, and TF32 MMA on the tensor cores (tcgen05; a reference
+// rate beside the split-FP16 tensor-core near field).  Both run one launch
+// over every SM and are timed with CUDA events on the launching stream.
 #include <algorithm>
 #include <cstdint>
 

@@ -123,7 +123,7 @@ def test_batched_complex64_apply_equals_single(kite):
 @pytest.mark.parametrize("nrhs", [8, 16])
 @pytest.mark.parametrize("name", ["disc", "kite"])
 def test_tensor_core_near_field(name, nrhs, request):
-    """8 and 16 complex64 right-hand sides take the tcgen05 near field (3xTF32):
+    """8 and 16 complex64 right-hand sides take the tcgen05 near field (split FP16):
     every RHS agrees with its single (CUDA-core, FP32) apply to FP32 rounding
     and with the FP64 oracle within the mixed-precision bound."""
     from paper_1509_05063_gb300 import LS_MIXED
