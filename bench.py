@@ -46,6 +46,19 @@ KERNELS_PER_APPLY = 6    # projection, source rows (fill + row FFT), columns (FF
 NEAR_TRAFFIC = {358205610: {"fp64": 8.892e9, "mixed": 2.955e9, "tc16": 3.106e9}}
 
 
+def apply_bytes(info, cb, wb=None):
+    """Algorithmic HBM bytes of one single-RHS 2-D apply of a plan (cb bytes per
+    complex, wb per near-field weight): the near field (weights once, u, Phi,
+    gamma, metadata, out), the projection's input and staged forms, and the
+    lattice passes (source rows, quarter spectra, kept rows; each read and
+    written once)."""
+    N, nnz, nfb2, nocc = info["N"], info["nnz_near"], 2 * info["n_fb"] + 1, info["n_cells_occupied"]
+    M, n_lat = info["fft_M"], info["L"] * info["N_eq"] + 1
+    near = nnz * (wb or cb) + N * cb + N * nfb2 * cb + N * 12 + nocc * nfb2 * cb + N * cb
+    lattice = 2 * (info["L"] + 1) * M * cb * 2 + 2 * (M // 2 + 1) ** 2 * cb + 2 * n_lat * M * cb * 2
+    return near + N * cb * 4 + lattice
+
+
 def hbm_peak():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -287,6 +300,10 @@ def run_batch(n_inst, dev, barrier, timed):
         ms_s = timed(seq, steps)
         out[key] = {"batch_apply_ms": ms_b / steps, "instance_matvecs_per_s": n_inst * steps / (ms_b * 1e-3),
                     "separate_applies_ms": ms_s / steps}
+        if key == "mixed":
+            peak, _ = hbm_peak()
+            nbytes = sum(apply_bytes(p.info, 8) for p in plans)
+            out[key]["apply_hbm_frac"] = (nbytes / (ms_b / steps * 1e-3) / 1e9) / peak
     parts = []
     for wl, p in zip(insts, plans):
         xy, _ = p.nodes()
@@ -577,7 +594,8 @@ def main():
     # whole-apply byte model: u in, out, weights, projections, Phi, lattice passes, quarter spectra
     lat_bytes = lambda cb: (2 * (info["L"] + 1) * M * cb * 2 + 2 * (M // 2 + 1) ** 2 * cb
                             + 2 * n_lat * M * cb * 2)
-    apply_bytes64 = near_bytes(16, 24) + N * 16 * 4 + lat_bytes(16)
+    apply_bytes64 = apply_bytes(info, 16, 24)
+    apply_bytes32 = apply_bytes(info, 8)
     # batched complex64 (tensor-core near field): weights once, per-RHS vectors, Phi once
     near_bytes_b = nnz * 8 + N * nfb2 * 8 + N * 12 + G32 * (2 * N * 8 + nocc * nfb2 * 8)
     t_near_b = stb[4] / max(cb, 1) * 1e-3
@@ -619,6 +637,7 @@ def main():
         "clocks": clocks,
         "mixed": {"value": world * args.steps / (ms32 * 1e-3), "unit": "matvecs/s", "dtype": "f32",
                   "ms_per_step": ms32 / args.steps,
+                  "apply_hbm_frac": (apply_bytes32 / (ms32 / args.steps * 1e-3) / 1e9) / peak,
                   "roofline": {"bound": "hbm", "kernel": "k_near_eval<float2,1>", "achieved": ach32,
                                "peak": peak, "unit": "GB/s", "frac": ach32 / peak, "peak_source": peak_src,
                                "bytes_per_launch": near_bytes(8), "traffic": traffic.get("mixed"),
