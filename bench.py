@@ -281,7 +281,9 @@ def run_batch(n_inst, dev, barrier, timed):
     b = Batch(plans)
     out = {"instances": n_inst, "N_total": b.N, "N_each": [p.N for p in plans],
            "kappa_each": [round(wl.kappa, 3) for wl in insts], "shape_each": [wl.shape for wl in insts],
-           "plan_s_total": t_plan}
+           "plan_s_total": t_plan, "plan_s_each": [round(p.info["plan_seconds"], 3) for p in plans],
+           "plan_stage_s_total": {k: round(sum(p.info["stage_seconds"][k] for p in plans), 3)
+                                  for k in ("nodes", "near", "accel", "device")}}
     steps = 20
     for prec, dt, key in [(LS_FP64, torch.complex128, "fp64"), (LS_MIXED, torch.complex64, "mixed")]:
         u = torch.from_numpy(W.random_density(b.N)[0]).to(dev, dt)
@@ -362,7 +364,7 @@ def run_sphere(spec, dev, barrier, timed, steps):
     plan.solve(ui, tol=1e-3, prec=LS_MIXED, max_iter=3)
     out = {"workload": f"sphere a=1 n^2={n2} kappa={kappa} N={N} (n_f={n_f}, n_s={n_s}, h={h}), "
                        f"L={L} cells/axis, N_eq={Ne}, lattice M={plan.info['fft_M']}",
-           "N": N, "nnz_near": plan.info["nnz_near"], "plan_s": t_plan,
+           "N": N, "nnz_near": plan.info["nnz_near"], "plan_s": t_plan, "plan_stage_s": plan.info["stage_seconds"],
            "fp64_matvecs_per_s": steps / (ms64 * 1e-3), "mixed_matvecs_per_s": steps / (ms32 * 1e-3)}
     ue = exact.sphere_total_field(kappa, n2, 1.0, xyz)
     sols = {}
@@ -620,7 +622,8 @@ def main():
                    "N": N, "nnz_near": nnz, "fft_M": M, "L": info["L"], "N_eq": info["N_eq"],
                    "n_fb": info["n_fb"], "parallelism": f"replicas x{world}",
                    "l2": "inputs larger than L2 (FP64 near-field weights %.1f GB)" % (nnz * 24 / 1e9),
-                   "plan_seconds": info["plan_seconds"], "device_bytes": info["device_bytes"]},
+                   "plan_seconds": info["plan_seconds"], "plan_stage_seconds": info["stage_seconds"],
+                   "device_bytes": info["device_bytes"]},
         "e2e": {"value": world * args.steps / (ms_e2e * 1e-3), "unit": "matvecs/s",
                 "h2d_bytes_per_step": N * 16, "d2h_bytes_per_step": N * 16},
         "roofline": {"bound": "alu", "kernel": "k_near_eval5<double2,1>",

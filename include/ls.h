@@ -122,6 +122,10 @@ typedef struct {
   int n_cells_occupied;
   double plan_seconds;   /* host wall time of ls_plan_create                    */
   int64_t device_bytes;  /* device memory held by the plan                      */
+  double stage_seconds[4]; /* of plan_seconds: nodes and weights, near-field
+                            * weights (singular rules, adjacent part),
+                            * accelerator fits and tables, device setup
+                            * (uploads, device-built spectra and tiles)       */
 } ls_plan_info_t;
 
 typedef struct {

@@ -269,14 +269,29 @@ ls_status validate(const ls_geometry* g, const ls_options* o, double kappa) {
   return LS_OK;
 }
 
+double secs_since(std::chrono::steady_clock::time_point t) {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now() - t).count();
+}
+
+// host plan construction; stage (may be NULL) receives the seconds of the
+// nodes, near-field weights and accelerator steps
 ls_status build_host(lsh::Plan2D& P, const ls_geometry* geom, ls_n2_fn n2, void* ctx, double kappa,
-                     const ls_options* opt, std::string* msg) {
+                     const ls_options* opt, std::string* msg, double* stage = nullptr) {
   P.geo.g = *geom;
   P.opt = *opt;
   P.kappa = kappa;
   P.n_threads = opt->n_threads > 0 ? opt->n_threads : int(std::max(1u, std::thread::hardware_concurrency()));
   try {
-    if (!lsh::build_nodes(P, n2, ctx) || !lsh::build_near(P) || !lsh::build_accel(P)) {
+    auto t = std::chrono::steady_clock::now();
+    bool ok = lsh::build_nodes(P, n2, ctx);
+    if (stage) stage[0] = secs_since(t);
+    t = std::chrono::steady_clock::now();
+    ok = ok && lsh::build_near(P);
+    if (stage) stage[1] = secs_since(t);
+    t = std::chrono::steady_clock::now();
+    ok = ok && lsh::build_accel(P);
+    if (stage) stage[2] = secs_since(t);
+    if (!ok) {
       *msg = P.err;
       return LS_ERR_INVALID;
     }
@@ -658,11 +673,13 @@ ls_status ls_plan_create(const ls_geometry* geom, ls_n2_fn n2, void* ctx, double
     delete plan;
     return s;
   };
+  double stage[4] = {0, 0, 0, 0};
   {
     std::string m;
-    const ls_status hs = build_host(P, geom, n2, ctx, kappa, opt, &m);
+    const ls_status hs = build_host(P, geom, n2, ctx, kappa, opt, &m, stage);
     if (hs != LS_OK) return bail(hs, m);
   }
+  const auto t_dev = std::chrono::steady_clock::now();
   const lsh::Nodes& nd = P.nodes;
   const int64_t N = nd.N;
   const int nocc = int(P.occ_cells.size());
@@ -1036,6 +1053,8 @@ ls_status ls_plan_create(const ls_geometry* geom, ls_n2_fn n2, void* ctx, double
   inf.L = P.opt.L; inf.N_eq = P.Ne; inf.n_es = P.n_es; inf.n_loc = P.n_loc; inf.n_fb = P.opt.n_fb;
   inf.fft_M = M; inf.n_cells_occupied = nocc;
   inf.plan_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  stage[3] = secs_since(t_dev);
+  for (int k = 0; k < 4; ++k) inf.stage_seconds[k] = stage[k];
   inf.device_bytes = plan->device_bytes;
   std::vector<cd>().swap(P.P64);
   std::vector<cd>().swap(P.P32);
@@ -1077,6 +1096,8 @@ ls_status ls_plan_create3(const ls_ball3* ball, const ls_rules3* rules, ls_n2_fn
   std::vector<std::complex<float>> P32;
   std::vector<double> m, wfac;
   lsh::Accel3 A;
+  double stage[4] = {0, 0, 0, 0};
+  auto tst = std::chrono::steady_clock::now();
   try {
     if (!lsh::build_ball3(B)) return bail(LS_ERR_INVALID, B.err);
     const int64_t N = B.N;
@@ -1089,15 +1110,21 @@ ls_status ls_plan_create3(const ls_ball3* ball, const ls_rules3* rules, ls_n2_fn
       m[q] = 1.0 - n2v[q];
       wfac[q] = B.w_q[q] * B.omega[q] * m[q];
     }
+    stage[0] = secs_since(tst);
+    tst = std::chrono::steady_clock::now();
     std::string em;
     if (!lsh::ball3_near(B, kappa, rules_from(rules), acc->box0, acc->H, acc->L, nullptr, 0, false, nt, &em))
       return bail(LS_ERR_INVALID, em);
+    stage[1] = secs_since(tst);
+    tst = std::chrono::steady_clock::now();
     A.kappa = kappa; A.H = acc->H; A.L = acc->L; A.Ne = acc->N_eq; A.p = acc->p; A.m_coll = acc->m_coll;
     A.n_threads = nt;
     for (int k = 0; k < 3; ++k) A.box0[k] = acc->box0[k];
     // one set of fits (truncation rcond, 1e-13 by default) serves both precisions
     A.rcond = acc->rcond > 0 ? acc->rcond : 1e-13;
     if (!lsh::build_accel3(A, B.x.data(), wfac.data(), N)) return bail(LS_ERR_INVALID, A.err);
+    stage[2] = secs_since(tst);
+    tst = std::chrono::steady_clock::now();
     const int nocc = int(A.occ_cells.size());
     const int n_es = A.n_es, nb = A.nb, n_loc = A.n_loc, M = A.M, L = acc->L;
     // plan order: the accelerator's node order (grouped by cell)
@@ -1335,6 +1362,8 @@ ls_status ls_plan_create3(const ls_ball3* ball, const ls_rules3* rules, ls_n2_fn
     inf.L = L; inf.N_eq = acc->N_eq; inf.n_es = n_es; inf.n_loc = n_loc; inf.n_fb = nb;
     inf.fft_M = M; inf.n_cells_occupied = nocc;
     inf.plan_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    stage[3] = secs_since(tst);
+    for (int k = 0; k < 4; ++k) inf.stage_seconds[k] = stage[k];
     inf.device_bytes = plan->device_bytes;
   } catch (const std::bad_alloc&) {
     return bail(LS_ERR_NOMEM, "host allocation failed");

@@ -54,7 +54,13 @@ class PlanInfo(C.Structure):
     _fields_ = [("N", C.c_int64), ("n_collar", C.c_int64), ("n_cart", C.c_int64), ("nnz_near", C.c_int64),
                 ("L", C.c_int), ("N_eq", C.c_int), ("n_es", C.c_int), ("n_loc", C.c_int), ("n_fb", C.c_int),
                 ("fft_M", C.c_int), ("n_cells_occupied", C.c_int), ("plan_seconds", C.c_double),
-                ("device_bytes", C.c_int64)]
+                ("device_bytes", C.c_int64), ("stage_seconds", C.c_double * 4)]
+
+
+def _info_dict(info):
+    d = {f: getattr(info, f) for f, _ in PlanInfo._fields_}
+    d["stage_seconds"] = {k: float(v) for k, v in zip(("nodes", "near", "accel", "device"), info.stage_seconds)}
+    return d
 
 
 class SolveInfo(C.Structure):
@@ -218,7 +224,7 @@ class Plan:
         self._h = h
         info = PlanInfo()
         _check(_lib.ls_plan_info(self._h, C.byref(info)), self._h)
-        self.info = {f: getattr(info, f) for f, _ in PlanInfo._fields_}
+        self.info = _info_dict(info)
         self.N = int(info.N)
 
     def nodes(self):
@@ -552,7 +558,7 @@ class Plan3(Plan):
         self._h = h
         info = PlanInfo()
         _check(_lib.ls_plan_info(self._h, C.byref(info)), self._h)
-        self.info = {f: getattr(info, f) for f, _ in PlanInfo._fields_}
+        self.info = _info_dict(info)
         self.N = int(info.N)
 
     def nodes(self):
