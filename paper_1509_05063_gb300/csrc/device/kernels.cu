@@ -34,10 +34,6 @@ template <> struct RealOf<float2> { using R = float; };
 // Staged inputs: complex64 as is; complex128 as c = Re x and (c + d, d - c),
 // with the sum Re a + Im a of each matrix entry stored beside A, so that every
 // complex product takes three FP64 FMAs (Gauss's form, as in the near field).
-__device__ __forceinline__ float2 shfl_xor16(float2 v) {
-  return make_float2(__shfl_xor_sync(0xffffffffu, v.x, 16), __shfl_xor_sync(0xffffffffu, v.y, 16));
-}
-
 template <typename T> struct Staged;
 template <> struct Staged<float2> {
   static constexpr int kBytes = 8;
@@ -544,55 +540,6 @@ __device__ __forceinline__ void local_coeffs_body(int k, int nocc, const int* __
     X.put(r, n_loc + q, v);
   }
   __syncthreads();
-  if constexpr (sizeof(T) == 8) {
-    if (nfb2 <= 32 && blockDim.x == 256) {
-      // complex64: thread (o2, segment sg) = (t mod 16, t / 16) takes the two
-      // outputs o2 and o2 + 16 over the inputs j = sg, sg + 16, ..., so every
-      // staged value serves two outputs (eight FMAs per shared-memory load);
-      // segments 2g and 2g + 1 (lanes t and t ^ 16) fold by a shuffle, then
-      // the 8 folded sums add in segment order.  The order depends on nothing
-      // but the output, so any R gives the single-RHS sums bit for bit.
-      const int t = threadIdx.x, o2 = t & 15, sg = t >> 4;
-      const bool two = o2 + 16 < nfb2;
-      float2 a0[R], a1[R];
-#pragma unroll
-      for (int r = 0; r < R; ++r) a0[r] = a1[r] = make_float2(0.f, 0.f);
-#pragma unroll 2
-      for (int j = sg; j < K; j += 16) {
-        const float2 l0 = LA[int64_t(j) * nfb2 + o2];
-        const float2 l1 = two ? LA[int64_t(j) * nfb2 + o2 + 16] : make_float2(0.f, 0.f);
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-          const float2 x = X.x[r * X.ld + j];
-          a0[r] = cfma(l0, x, a0[r]);
-          a1[r] = cfma(l1, x, a1[r]);
-        }
-      }
-#pragma unroll
-      for (int r = 0; r < R; ++r) {
-        a0[r] = cadd(a0[r], shfl_xor16(a0[r]));
-        a1[r] = cadd(a1[r], shfl_xor16(a1[r]));
-      }
-      T* red = reinterpret_cast<T*>(smem_raw);        // [8][R][nfb2]
-      __syncthreads();                                // the staged inputs are no longer read
-      if ((sg & 1) == 0) {
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-          red[((sg >> 1) * R + r) * nfb2 + o2] = a0[r];
-          if (two) red[((sg >> 1) * R + r) * nfb2 + o2 + 16] = a1[r];
-        }
-      }
-      __syncthreads();
-      T* out = gamma_all + int64_t(k) * nfb2;
-      for (int e = t; e < R * nfb2; e += blockDim.x) {
-        const int r = e / nfb2, oo = e - r * nfb2;
-        T v = red[r * nfb2 + oo];
-        for (int g = 1; g < 8; ++g) v = cadd(v, red[(g * R + r) * nfb2 + oo]);
-        out[int64_t(r) * nocc * nfb2 + oo] = v;
-      }
-      return;
-    }
-  }
   const int S = blockDim.x / nfb2, t = threadIdx.x, o = t % nfb2, sg = t / nfb2;
   CAcc<T> acc[R];
 #pragma unroll
