@@ -1180,13 +1180,15 @@ ls_status ls_plan_create3(const ls_ball3* ball, const ls_rules3* rules, ls_n2_fn
       rowptr[i + 1] = rowptr[i] + (B.near_rowptr[order[i] + 1] - B.near_rowptr[order[i]]);
     std::vector<int> col(rowptr[N]);
     std::vector<cd> val(rowptr[N]);
-    for (int64_t i = 0; i < N; ++i) {
-      int64_t o = rowptr[i];
-      for (int64_t e = B.near_rowptr[order[i]]; e < B.near_rowptr[order[i] + 1]; ++e, ++o) {
-        col[o] = int(inv[B.near_col[e]]);
-        val[o] = B.near_val[e] * m[B.near_col[e]];
+    lsh::parallel_for(nt, N, 256, [&](int64_t i0, int64_t i1) {
+      for (int64_t i = i0; i < i1; ++i) {
+        int64_t o = rowptr[i];
+        for (int64_t e = B.near_rowptr[order[i]]; e < B.near_rowptr[order[i] + 1]; ++e, ++o) {
+          col[o] = int(inv[B.near_col[e]]);
+          val[o] = B.near_val[e] * m[B.near_col[e]];
+        }
       }
-    }
+    });
     std::vector<int32_t>().swap(B.near_col);
     std::vector<cd>().swap(B.near_val);
     ls_status st = LS_OK;
@@ -1245,16 +1247,10 @@ ls_status ls_plan_create3(const ls_ball3* ball, const ls_rules3* rules, ls_n2_fn
     a.Gs = UP3(double2, Gs);
     a.Ds = UP3(double2, Ds);
     a.tw = d_tw64;
-    {
-      // FP64 adjacent part in the three-multiplication form (a + b, b, a)
-      std::vector<double> v3(size_t(3) * val.size());
-      for (size_t e = 0; e < val.size(); ++e) {
-        v3[3 * e] = val[e].real() + val[e].imag();
-        v3[3 * e + 1] = val[e].imag();
-        v3[3 * e + 2] = val[e].real();
-      }
-      a.val3 = UP3(double, v3);
-    }
+    // the FP64 adjacent part in the three-multiplication form (a + b, b, a)
+    // is built on the device from the CSR values, with the complex64 blocks below
+    double* d_val3 = plan->alloc<double>(size_t(3) * val.size(), &st);
+    a.val3 = d_val3;
     a.u3 = plan->alloc<double>(size_t(3) * N, &st);
     a.kappa2 = kappa * kappa;
     a.sigma = plan->alloc<double2>(size_t(nocc) * n_es, &st);
@@ -1306,35 +1302,41 @@ ls_status ls_plan_create3(const ls_ball3* ball, const ls_rules3* rules, ls_n2_fn
         }
         boff[k + 1] = boff[k] + (occ_start[k + 1] - occ_start[k]) * nblk;
       }
-      std::vector<std::complex<float>> wb(size_t(boff[nocc]), {0.f, 0.f});
+      // both stored forms from the CSR on the device: val3, the dense blocks and
+      // the per-row count of entries outside them; then the remainder CSR
+#define CU3(call)                                                                        \
+  do {                                                                                   \
+    const cudaError_t e3_ = (call);                                                      \
+    if (e3_ != cudaSuccess) return bail(LS_ERR_CUDA, std::string(#call ": ") + cudaGetErrorString(e3_)); \
+  } while (0)
+      float2* d_wb = plan->alloc<float2>(size_t(boff[nocc]), &st);
+      const double2* d_val = UP3(double2, val);
+      std::vector<cd>().swap(val);
+      const int64_t* d_boff = UP3(int64_t, boff);
+      const int* d_seg = UP3(int, seg);
+      int64_t* d_rcount = plan->alloc<int64_t>(size_t(N), &st);
+      if (st != LS_OK) return bail(st, plan->err);
+      CU3(cudaMemset(d_wb, 0, sizeof(float2) * size_t(boff[nocc])));
+      CU3(lsd::near3_forms(N, d_occ_start, d_occ_of_node, d_rowptr, d_col, d_val, d_boff, d_seg, d_val3, d_wb,
+                             d_rcount, 0));
       std::vector<int64_t> rrow(N + 1, 0);
-      std::vector<int> rcol;
-      std::vector<cd> rval;
-      for (int k = 0; k < nocc; ++k) {
-        const int* sg = &seg[18 * k];
-        int nblk = 0;
-        for (int s9 = 0; s9 < 9; ++s9) nblk += sg[2 * s9 + 1];
-        for (int64_t q = occ_start[k]; q < occ_start[k + 1]; ++q) {
-          std::complex<float>* wrow = wb.data() + boff[k] + (q - occ_start[k]) * nblk;
-          for (int64_t e = rowptr[q]; e < rowptr[q + 1]; ++e) {
-            int pos = -1;
-            for (int s9 = 0, o = 0; s9 < 9; o += sg[2 * s9 + 1], ++s9)
-              if (col[e] >= sg[2 * s9] && col[e] < sg[2 * s9] + sg[2 * s9 + 1]) {
-                pos = o + col[e] - sg[2 * s9];
-                break;
-              }
-            if (pos >= 0) wrow[pos] += std::complex<float>(val[e]);
-            else { rcol.push_back(col[e]); rval.push_back(val[e]); }
-          }
-          rrow[q + 1] = int64_t(rcol.size());
-        }
-      }
-      b.Wb = UP3(float2, wb);
-      b.blk_off = UP3(int64_t, boff);
-      b.blk_seg = UP3(int, seg);
-      b.rowptr = UP3(int64_t, rrow);
-      b.col = UP3(int, rcol);
-      b.val = UP3(float2, to32(rval));
+      CU3(cudaMemcpy(rrow.data() + 1, d_rcount, sizeof(int64_t) * size_t(N), cudaMemcpyDeviceToHost));
+      for (int64_t q = 0; q < N; ++q) rrow[q + 1] += rrow[q];
+      plan->release(d_rcount);
+      const int64_t* d_rrow = UP3(int64_t, rrow);
+      int* d_rcol = plan->alloc<int>(size_t(rrow[N]), &st);
+      float2* d_rval = plan->alloc<float2>(size_t(rrow[N]), &st);
+      if (st != LS_OK) return bail(st, plan->err);
+      CU3(lsd::near3_remainder(N, d_occ_of_node, d_rowptr, d_col, d_val, d_seg, d_rrow, d_rcol, d_rval, 0));
+      CU3(cudaDeviceSynchronize());
+#undef CU3
+      plan->release(d_val);
+      b.Wb = d_wb;
+      b.blk_off = d_boff;
+      b.blk_seg = d_seg;
+      b.rowptr = d_rrow;
+      b.col = d_rcol;
+      b.val = d_rval;
     }
     b.kappa2 = a.kappa2;
     b.sigma = plan->alloc<float2>(size_t(nocc) * n_es, &st);

@@ -674,6 +674,73 @@ cudaError_t apply3_one(const ApplyData3<T>& d, const T* u, T* out, cudaStream_t 
   return cudaGetLastError();
 }
 
+// position of node c in a row's dense block (its 9 ranges (start, length)
+// concatenated in order), or -1 outside them
+__device__ __forceinline__ int block_pos(const int (&sg)[18], int c) {
+  int o = 0;
+#pragma unroll
+  for (int s9 = 0; s9 < 9; ++s9) {
+    if (c >= sg[2 * s9] && c < sg[2 * s9] + sg[2 * s9 + 1]) return o + c - sg[2 * s9];
+    o += sg[2 * s9 + 1];
+  }
+  return -1;
+}
+
+// thread per row: its entries in order (one-time plan construction)
+__global__ void __launch_bounds__(kT3) k3_near_forms(int64_t N, const int64_t* __restrict__ occ_start,
+                                                     const int* __restrict__ occ_of_node,
+                                                     const int64_t* __restrict__ rowptr, const int* __restrict__ col,
+                                                     const double2* __restrict__ val,
+                                                     const int64_t* __restrict__ blk_off,
+                                                     const int* __restrict__ blk_seg, double* __restrict__ val3,
+                                                     float2* __restrict__ Wb, int64_t* __restrict__ rem_count) {
+  const int64_t q = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (q >= N) return;
+  const int k = occ_of_node[q];
+  int sg[18], nblk = 0;
+#pragma unroll
+  for (int i = 0; i < 18; ++i) sg[i] = blk_seg[18 * k + i];
+#pragma unroll
+  for (int s9 = 0; s9 < 9; ++s9) nblk += sg[2 * s9 + 1];
+  float2* w = Wb + blk_off[k] + (q - occ_start[k]) * nblk;
+  int64_t cnt = 0;
+  for (int64_t e = rowptr[q]; e < rowptr[q + 1]; ++e) {
+    const double2 v = val[e];
+    val3[3 * e] = v.x + v.y;
+    val3[3 * e + 1] = v.y;
+    val3[3 * e + 2] = v.x;
+    const int pos = block_pos(sg, col[e]);
+    if (pos >= 0) {
+      const float2 o = w[pos];
+      w[pos] = make_float2(o.x + float(v.x), o.y + float(v.y));
+    } else {
+      ++cnt;
+    }
+  }
+  rem_count[q] = cnt;
+}
+
+__global__ void __launch_bounds__(kT3) k3_near_remainder(int64_t N, const int* __restrict__ occ_of_node,
+                                                         const int64_t* __restrict__ rowptr,
+                                                         const int* __restrict__ col, const double2* __restrict__ val,
+                                                         const int* __restrict__ blk_seg,
+                                                         const int64_t* __restrict__ rem_row, int* __restrict__ rem_col,
+                                                         float2* __restrict__ rem_val) {
+  const int64_t q = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (q >= N) return;
+  const int k = occ_of_node[q];
+  int sg[18];
+#pragma unroll
+  for (int i = 0; i < 18; ++i) sg[i] = blk_seg[18 * k + i];
+  int64_t o = rem_row[q];
+  for (int64_t e = rowptr[q]; e < rowptr[q + 1]; ++e)
+    if (block_pos(sg, col[e]) < 0) {
+      rem_col[o] = col[e];
+      rem_val[o] = make_float2(float(val[e].x), float(val[e].y));
+      ++o;
+    }
+}
+
 }  // namespace
 
 int local3_slices(int nocc, int nb, int K) { return local_slices(nocc, nb, K); }
@@ -695,6 +762,24 @@ cudaError_t apply3_batch(const ApplyData3<T>& d, const T* u, T* out, int nr, cud
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
+}
+
+cudaError_t near3_forms(int64_t N, const int64_t* occ_start, const int* occ_of_node, const int64_t* rowptr,
+                        const int* col, const double2* val, const int64_t* blk_off, const int* blk_seg, double* val3,
+                        float2* Wb, int64_t* rem_count, cudaStream_t st) {
+  if (N <= 0) return cudaSuccess;
+  k3_near_forms<<<unsigned((N + kT3 - 1) / kT3), kT3, 0, st>>>(N, occ_start, occ_of_node, rowptr, col, val, blk_off,
+                                                               blk_seg, val3, Wb, rem_count);
+  return cudaGetLastError();
+}
+
+cudaError_t near3_remainder(int64_t N, const int* occ_of_node, const int64_t* rowptr, const int* col,
+                            const double2* val, const int* blk_seg, const int64_t* rem_row, int* rem_col,
+                            float2* rem_val, cudaStream_t st) {
+  if (N <= 0) return cudaSuccess;
+  k3_near_remainder<<<unsigned((N + kT3 - 1) / kT3), kT3, 0, st>>>(N, occ_of_node, rowptr, col, val, blk_seg,
+                                                                   rem_row, rem_col, rem_val);
+  return cudaGetLastError();
 }
 
 cudaError_t farfield3(int64_t N, const double* xyz, const double* ffw, const double2* u, int nrhs,

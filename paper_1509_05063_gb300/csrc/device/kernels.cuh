@@ -171,6 +171,20 @@ cudaError_t apply3_batch(const ApplyData3<T>& d, const T* u, T* out, int nr, cud
 // inverse (unscaled): three passes of batched line transforms.
 template <typename T>
 cudaError_t fft3d(T* x, int M, int logM, const T* tw, bool inverse, cudaStream_t st);
+// Plan-time construction, on the device, of the 3-D adjacent part's stored
+// forms from its CSR (plan order; rowptr, col, val = a + ib, all device):
+// near3_forms writes val3 = (a + b, b, a) per entry, adds the entries that
+// fall in a row's 9 neighbour node ranges (blk_seg) into the complex64 dense
+// block Wb (zeroed by the caller; same order and rounding as a host loop over
+// the row) and counts the others per row (rem_count, N entries);
+// near3_remainder then writes those others, in row order, at rem_row (the
+// exclusive prefix sums of the counts).
+cudaError_t near3_forms(int64_t N, const int64_t* occ_start, const int* occ_of_node, const int64_t* rowptr,
+                        const int* col, const double2* val, const int64_t* blk_off, const int* blk_seg, double* val3,
+                        float2* Wb, int64_t* rem_count, cudaStream_t st);
+cudaError_t near3_remainder(int64_t N, const int* occ_of_node, const int64_t* rowptr, const int* col,
+                            const double2* val, const int* blk_seg, const int64_t* rem_row, int* rem_col,
+                            float2* rem_val, cudaStream_t st);
 // Far-field pattern of a 3-D plan's solution: A[r][d] = c sum_q ffw_q u_r[q]
 // exp(-i kappa dir_d . x_q) (dirs: ndir x 3 unit vectors, device).
 cudaError_t farfield3(int64_t N, const double* xyz, const double* ffw, const double2* u, int nrhs,
