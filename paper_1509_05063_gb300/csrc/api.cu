@@ -718,25 +718,46 @@ ls_status ls_plan_create(const ls_geometry* geom, ls_n2_fn n2, void* ctx, double
   }
   std::vector<cd> Wb(blk_off[nocc], cd(0.0));
   std::vector<int64_t> rem_row(N + 1, 0);
-  std::vector<int> rem_col;
-  std::vector<cd> rem_val;
-  for (int64_t q = 0; q < N; ++q) {
-    const int k = occ_of_node[q];
-    const int* sg = &blk_seg[6 * k];
-    const int nblk = padded(sg[1]) + padded(sg[3]) + padded(sg[5]);
-    cd* row = &Wb[blk_off[k] + (q - occ_start[k]) * nblk];
-    for (int64_t e = P.rowptr[q]; e < P.rowptr[q + 1]; ++e) {
-      const int col = P.col[e];
-      int pos = -1, base = 0;
-      for (int s = 0; s < 3; ++s) {
-        if (col >= sg[2 * s] && col < sg[2 * s] + sg[2 * s + 1]) { pos = base + col - sg[2 * s]; break; }
-        base += padded(sg[2 * s + 1]);
-      }
-      if (pos >= 0) row[pos] += P.val[e];
-      else { rem_col.push_back(col); rem_val.push_back(P.val[e]); }
+  // position of column col in row q's block, or -1 (the remainder)
+  auto block_pos = [&](int64_t q, int col) {
+    const int* sg = &blk_seg[6 * occ_of_node[q]];
+    int base = 0;
+    for (int s = 0; s < 3; ++s) {
+      if (col >= sg[2 * s] && col < sg[2 * s] + sg[2 * s + 1]) return base + col - sg[2 * s];
+      base += padded(sg[2 * s + 1]);
     }
-    rem_row[q + 1] = int64_t(rem_col.size());
-  }
+    return -1;
+  };
+  // rows in parallel (each row owns its block row); every row sums its entries in CSR order
+  lsh::parallel_for(P.n_threads, N, 512, [&](int64_t q0, int64_t q1) {
+    for (int64_t q = q0; q < q1; ++q) {
+      const int k = occ_of_node[q];
+      const int* sg = &blk_seg[6 * k];
+      const int nblk = padded(sg[1]) + padded(sg[3]) + padded(sg[5]);
+      cd* row = &Wb[blk_off[k] + (q - occ_start[k]) * nblk];
+      int64_t rem = 0;
+      for (int64_t e = P.rowptr[q]; e < P.rowptr[q + 1]; ++e) {
+        const int pos = block_pos(q, P.col[e]);
+        if (pos >= 0) row[pos] += P.val[e];
+        else ++rem;
+      }
+      rem_row[q + 1] = rem;
+    }
+  });
+  for (int64_t q = 0; q < N; ++q) rem_row[q + 1] += rem_row[q];
+  std::vector<int> rem_col(rem_row[N]);
+  std::vector<cd> rem_val(rem_row[N]);
+  lsh::parallel_for(P.n_threads, N, 512, [&](int64_t q0, int64_t q1) {
+    for (int64_t q = q0; q < q1; ++q) {
+      int64_t o = rem_row[q];
+      for (int64_t e = P.rowptr[q]; e < P.rowptr[q + 1]; ++e)
+        if (block_pos(q, P.col[e]) < 0) {
+          rem_col[o] = P.col[e];
+          rem_val[o] = P.val[e];
+          ++o;
+        }
+    }
+  });
   std::vector<int32_t>().swap(P.col);
   std::vector<cd>().swap(P.val);
   const int64_t* d_occ_start = UP(int64_t, occ_start);
