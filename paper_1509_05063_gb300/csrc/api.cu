@@ -2463,6 +2463,15 @@ struct ls_batch_s : DevOwner {
   std::vector<ActiveSet> sets;
   Krylov K;
   GraphCache graphs;
+  lsd::SideStreams side;                              // instances' lattice convolutions side by side
+  void release_side() {
+    for (int i = 0; i < side.n; ++i) {
+      if (side.s[i]) cudaStreamDestroy(side.s[i]);
+      if (side.join[i]) cudaEventDestroy(side.join[i]);
+    }
+    if (side.fork) cudaEventDestroy(side.fork);
+    side = lsd::SideStreams();
+  }
   void release_sets() {
     for (auto& a : sets) a.release();
     sets.clear();
@@ -2538,7 +2547,7 @@ cudaError_t batch_apply_t(ls_batch b, int prec, const lsd::InstData<T>* dI, cons
   if (a.ids.empty()) return cudaSuccess;
   auto launch = [&](cudaStream_t s) {
     return lsd::apply_multi<T>(dI, hI.data(), a.ids.data(), int(a.ids.size()), a.pieces, a.n_pieces, a.cells,
-                               a.n_cells, a.items, a.n_items, b->max_K, u, out, s);
+                               a.n_cells, a.items, a.n_items, b->max_K, u, out, s, b->side.n > 0 ? &b->side : nullptr);
   };
   return b->graphs.run(GraphCache::Key(prec, si, static_cast<const void*>(u), static_cast<void*>(out)), launch, st);
 }
@@ -2574,11 +2583,26 @@ ls_status ls_batch_create(const ls_plan* plans, int n_plans, ls_batch* out) {
   auto bail = [&](ls_status s) {
     g_create_error = b->err;
     b->release_sets();
+    b->release_side();
     b->free_bufs();
     delete b;
     return s;
   };
   b->plans.assign(plans, plans + n_plans);
+  if (n_plans > 1) {
+    const int w = std::min(n_plans, lsd::SideStreams::kMax);
+    bool ok = cudaEventCreateWithFlags(&b->side.fork, cudaEventDisableTiming) == cudaSuccess;
+    for (int i = 0; i < w && ok; ++i) {
+      ok = cudaStreamCreateWithFlags(&b->side.s[i], cudaStreamNonBlocking) == cudaSuccess &&
+           cudaEventCreateWithFlags(&b->side.join[i], cudaEventDisableTiming) == cudaSuccess;
+      b->side.n = i + 1;
+    }
+    if (!ok) {
+      cudaGetLastError();
+      b->err = "ls_batch_create: stream or event creation failed";
+      return bail(LS_ERR_CUDA);
+    }
+  }
   b->off.push_back(0);
   for (int i = 0; i < n_plans; ++i) {
     const ls_plan p = plans[i];
@@ -2704,6 +2728,7 @@ ls_status ls_batch_destroy(ls_batch b) {
   b->K.free_pinned();
   b->graphs.release();
   b->release_sets();
+  b->release_side();
   b->free_bufs();
   delete b;
   return LS_OK;

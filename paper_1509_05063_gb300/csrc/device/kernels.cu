@@ -939,12 +939,24 @@ __global__ void __launch_bounds__(256) k_near_eval_multi(const int4* __restrict_
 template <typename T>
 cudaError_t apply_multi(const InstData<T>* dev_inst, const InstData<T>* host_inst, const int* ids, int n_ids,
                         const int2* pieces, int n_pieces, const int2* cells, int n_cells, const int4* items,
-                        int n_items, int max_K, const T* u, T* out, cudaStream_t st) {
+                        int n_items, int max_K, const T* u, T* out, cudaStream_t st, const SideStreams* side) {
   if (n_ids <= 0 || n_pieces <= 0 || n_cells <= 0 || n_items <= 0) return cudaSuccess;
   k_es_project_multi<T><<<n_pieces, 256, contraction_smem<T>(1, kProjStage), st>>>(pieces, dev_inst, u);
-  for (int j = 0; j < n_ids; ++j) {
-    cudaError_t e = lattice_conv(host_inst[ids[j]].d, 1, st);
+  if (side && side->n > 0 && n_ids > 1) {
+    const int w = side->n < n_ids ? side->n : n_ids;
+    cudaError_t e = cudaEventRecord(side->fork, st);
+    for (int i = 0; i < w && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(side->s[i], side->fork, 0);
+    for (int j = 0; j < n_ids && e == cudaSuccess; ++j) e = lattice_conv(host_inst[ids[j]].d, 1, side->s[j % w]);
+    for (int i = 0; i < w && e == cudaSuccess; ++i) {
+      e = cudaEventRecord(side->join[i], side->s[i]);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(st, side->join[i], 0);
+    }
     if (e != cudaSuccess) return e;
+  } else {
+    for (int j = 0; j < n_ids; ++j) {
+      cudaError_t e = lattice_conv(host_inst[ids[j]].d, 1, st);
+      if (e != cudaSuccess) return e;
+    }
   }
   const size_t sm_local = local_smem<T>(1, max_K);
   static unsigned long long attr = 0;
@@ -959,10 +971,10 @@ cudaError_t apply_multi(const InstData<T>* dev_inst, const InstData<T>* host_ins
 
 template cudaError_t apply_multi<double2>(const InstData<double2>*, const InstData<double2>*, const int*, int,
                                           const int2*, int, const int2*, int, const int4*, int, int, const double2*,
-                                          double2*, cudaStream_t);
+                                          double2*, cudaStream_t, const SideStreams*);
 template cudaError_t apply_multi<float2>(const InstData<float2>*, const InstData<float2>*, const int*, int,
                                          const int2*, int, const int2*, int, const int4*, int, int, const float2*,
-                                         float2*, cudaStream_t);
+                                         float2*, cudaStream_t, const SideStreams*);
 
 template <typename T>
 cudaError_t apply_batch(const ApplyData<T>& d, const T* u, T* out, int nr, cudaStream_t st, cudaEvent_t* ev) {

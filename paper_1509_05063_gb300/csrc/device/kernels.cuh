@@ -208,10 +208,20 @@ struct InstData {
 // differs).  dev_inst is a device copy of host_inst; ids is a host array; max_K
 // is the largest n_loc + 9 n_es.  No plan may appear twice among the instances
 // (they would share its work arrays).
+// side (may be NULL): streams on which the instances' lattice convolutions run
+// side by side (each is a few small launches that leave most SMs idle), forked
+// from and joined back into st by events (also under stream capture).
+struct SideStreams {
+  static constexpr int kMax = 4;
+  cudaStream_t s[kMax] = {};
+  cudaEvent_t fork = nullptr, join[kMax] = {};
+  int n = 0;
+};
 template <typename T>
 cudaError_t apply_multi(const InstData<T>* dev_inst, const InstData<T>* host_inst, const int* ids, int n_ids,
                         const int2* pieces, int n_pieces, const int2* cells, int n_cells, const int4* items,
-                        int n_items, int max_K, const T* u, T* out, cudaStream_t st);
+                        int n_items, int max_K, const T* u, T* out, cudaStream_t st,
+                        const SideStreams* side = nullptr);
 
 // 2-D FFT of an M x M array in place (rows then columns), forward or inverse
 // (unscaled).
