@@ -292,7 +292,8 @@ ls_status ls_measure_peaks(double* fp64_tflops, double* tf32_tflops);
  *     complex64 separately (FP64: one apply of min(nrhs, 4) right-hand sides);
  *   - for a complex64 apply of nrhs right-hand sides: the right-hand-side
  *     group per near-field launch (16, 8 or 4) and, for groups of 8 or more,
- *     tensor cores (split FP16) or CUDA cores for the near field.
+ *     tensor cores (split FP16) or CUDA cores for the near field and for the
+ *     local-expansion coefficients.
  * The plan's device must be current (LS_ERR_INVALID otherwise); 3-D plans
  * return LS_ERR_UNSUPPORTED; nrhs in [1, 64].  Blocking; drops the plan's
  * captured applies.  report (host, may be NULL) receives the choice and the
@@ -303,6 +304,7 @@ typedef struct {
   int group32;                  /* chosen complex64 right-hand-side group */
   int near_cuda32;              /* 1: CUDA-core complex64 near field for groups >= 8; 0: tensor cores */
   int n_candidates;             /* variants timed */
+  int local_cuda32;             /* 1: CUDA-core complex64 local coefficients for groups >= 8; 0: tensor cores */
   double ms64_default, ms64_best;
   double ms32_default, ms32_best;
 } ls_tune_report;

@@ -1056,6 +1056,14 @@ ls_status ls_plan_create(const ls_geometry* geom, ls_n2_fn n2, void* ctx, double
     b.Wt = wt;
     b.tc_rscale = rs;
   }
+  if (P.nfb2 <= 32) {   // LA in the tile layout of the tensor-core local coefficients
+    const int Kl = P.n_loc + 9 * P.n_es;
+    unsigned char* lat = plan->alloc<unsigned char>(lsd::local_tc_bytes(Kl), &st);
+    if (st != LS_OK) return bail(st, plan->err);
+    const cudaError_t e = lsd::local_tc_tiles(b.LA, Kl, P.nfb2, lat, 0);
+    if (e != cudaSuccess) return bail(LS_ERR_CUDA, std::string("local tile layout: ") + cudaGetErrorString(e));
+    b.LAt = lat;
+  }
   b.rem_val = UP(float2, to32(rem_val));
   b.Gq = d_G32; b.Dq = d_D32;
   b.tw = UP(float2, to32(tw));
@@ -2258,12 +2266,17 @@ ls_status ls_plan_autotune(ls_plan plan, int nrhs, ls_tune_report* report) {
     best = -1;
     int bt = 1, bg = keep_group;
     bool bc = false;
+    const bool keep_lcuda = plan->d32.local_cuda;
+    bool blc = keep_lcuda;
     for (int tc : conv_opts)
       for (int grp = 16; grp >= 4; grp /= 2)
-        for (int cuda = 0; cuda < 2; ++cuda) {
-          if (grp > std::max(4, nrhs) || (cuda && grp < 8)) continue;
+        for (int var = 0; var < 4; ++var) {
+          // var bit 0: CUDA-core near field; bit 1: CUDA-core local coefficients (groups of 8 or 16)
+          const int cuda = var & 1, lcuda = var >> 1;
+          if (grp > std::max(4, nrhs) || (var && grp < 8) || (lcuda && !plan->d32.LAt)) continue;
           plan->d32.conv_tc = tc;
           plan->d32.near_cuda = cuda != 0;
+          plan->d32.local_cuda = lcuda != 0;
           const double ms = timed([&] {
             for (int q = 0; q < nrhs;) {
               int nr = grp;
@@ -2277,15 +2290,17 @@ ls_status ls_plan_autotune(ls_plan plan, int nrhs, ls_tune_report* report) {
           cudaGetLastError();
           ++r.n_candidates;
           if (ms < 0) continue;
-          if (tc == 1 && grp == std::min(keep_group, std::max(4, nrhs)) && !cuda) r.ms32_default = ms;
-          if (best < 0 || ms < best) { best = ms; bt = tc; bg = grp; bc = cuda != 0; }
+          if (tc == 1 && grp == std::min(keep_group, std::max(4, nrhs)) && var == 0) r.ms32_default = ms;
+          if (best < 0 || ms < best) { best = ms; bt = tc; bg = grp; bc = cuda != 0; blc = lcuda != 0; }
         }
     plan->d32.conv_tc = best > 0 ? bt : keep_tc;
     plan->d32.near_cuda = best > 0 ? bc : keep_cuda;
+    plan->d32.local_cuda = best > 0 ? blc : keep_lcuda;
     plan->group32 = best > 0 ? bg : keep_group;
     r.conv_cols32 = plan->d32.conv_tc > 0 ? plan->d32.conv_tc : 1;
     r.group32 = plan->group32;
     r.near_cuda32 = plan->d32.near_cuda ? 1 : 0;
+    r.local_cuda32 = plan->d32.local_cuda ? 1 : 0;
     r.ms32_best = best;
     ce = cudaStreamSynchronize(ts);
   }

@@ -871,9 +871,18 @@ cudaError_t apply_r(const ApplyData<T>& d, const T* u, T* out, cudaStream_t st, 
     cudaFuncSetAttribute(k_local_coeffs<T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
   }
   if (sm_local > 160 * 1024) return cudaErrorInvalidValue;
-  k_local_coeffs<T, R><<<d.nocc, 256, sm_local, st>>>(d.nocc, d.occ_cells, d.occ_of_cell, d.L, d.Ne, d.M, d.Sd,
-                                                       d.LA, d.LAs, d.sigma, d.n_es, d.nfb2, d.gamma,
-                                                       d.lattice_rows() * d.M);
+  bool local_done = false;
+  if constexpr (sizeof(T) == 8 && R >= 8) {
+    if (!d.local_cuda && d.LAt) {           // tensor cores (device/local_tc.cu)
+      const cudaError_t e3 = local_coeffs_tc<R>(d, st);
+      if (e3 != cudaSuccess) return e3;
+      local_done = true;
+    }
+  }
+  if (!local_done)
+    k_local_coeffs<T, R><<<d.nocc, 256, sm_local, st>>>(d.nocc, d.occ_cells, d.occ_of_cell, d.L, d.Ne, d.M, d.Sd,
+                                                         d.LA, d.LAs, d.sigma, d.n_es, d.nfb2, d.gamma,
+                                                         d.lattice_rows() * d.M);
   if (ev) cudaEventRecord(ev[4], st);
   if constexpr (sizeof(T) == 8 && R >= 8) {
     if (!d.near_cuda) {

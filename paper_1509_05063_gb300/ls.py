@@ -70,7 +70,8 @@ class SolveInfo(C.Structure):
 
 class TuneReport(C.Structure):
     _fields_ = [("nrhs", C.c_int), ("conv_cols64", C.c_int), ("conv_cols32", C.c_int), ("group32", C.c_int),
-                ("near_cuda32", C.c_int), ("n_candidates", C.c_int), ("ms64_default", C.c_double),
+                ("near_cuda32", C.c_int), ("n_candidates", C.c_int), ("local_cuda32", C.c_int),
+                ("ms64_default", C.c_double),
                 ("ms64_best", C.c_double), ("ms32_default", C.c_double), ("ms32_best", C.c_double)]
 
 
