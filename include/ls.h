@@ -288,12 +288,13 @@ ls_status ls_measure_peaks(double* fp64_tflops, double* tf32_tflops);
  * stream and scratch vectors it allocates and frees, the variants of the
  * apply that give the same result up to rounding, and keeps the fastest in
  * the plan:
- *   - columns per block of the lattice column pass (1, 2, 4), FP64 and
+ *   - columns per block of the lattice column pass (1, 2, 4, 8), FP64 and
  *     complex64 separately (FP64: one apply of min(nrhs, 4) right-hand sides);
  *   - for a complex64 apply of nrhs right-hand sides: the right-hand-side
  *     group per near-field launch (16, 8 or 4) and, for groups of 8 or more,
- *     tensor cores (split FP16) or CUDA cores for the near field and for the
- *     local-expansion coefficients.
+ *     tensor cores or CUDA cores for each of the near field (split FP16), the
+ *     local-expansion coefficients and the equivalent-source projection
+ *     (3xTF32).
  * The plan's device must be current (LS_ERR_INVALID otherwise); 3-D plans
  * return LS_ERR_UNSUPPORTED; nrhs in [1, 64].  Blocking; drops the plan's
  * captured applies.  report (host, may be NULL) receives the choice and the
@@ -305,10 +306,23 @@ typedef struct {
   int near_cuda32;              /* 1: CUDA-core complex64 near field for groups >= 8; 0: tensor cores */
   int n_candidates;             /* variants timed */
   int local_cuda32;             /* 1: CUDA-core complex64 local coefficients for groups >= 8; 0: tensor cores */
+  int proj_cuda32;              /* 1: CUDA-core complex64 projection for groups >= 8; 0: tensor cores */
   double ms64_default, ms64_best;
   double ms32_default, ms32_best;
 } ls_tune_report;
 ls_status ls_plan_autotune(ls_plan plan, int nrhs, ls_tune_report* report);
+
+/* Sets the kernel variants of a 2-D plan from a report (host, read only):
+ * conv_cols64 and conv_cols32 in {1, 2, 4, 8}, group32 in {4, 8, 16},
+ * near_cuda32, local_cuda32 and proj_cuda32 in {0, 1}; the other fields are
+ * ignored.  It re-applies a choice ls_plan_autotune made earlier (for
+ * instance in another process on the same kind of GPU) and pins variants for
+ * tests.  Every variant gives the same result up to rounding.  A plan whose
+ * tables do not fit a tensor-core unit (2 n_fb + 1 > 32 for the local
+ * coefficients, n_es > 64 for the projection) keeps the CUDA-core kernel
+ * there.  LS_ERR_INVALID on a null argument or a value outside these sets,
+ * LS_ERR_UNSUPPORTED for 3-D plans; drops the plan's captured applies. */
+ls_status ls_plan_set_variants(ls_plan plan, const ls_tune_report* variants);
 
 /* Per-stage device timing of ls_apply with CUDA events recorded on the call's
  * stream (measurement aid; enabling it makes ls_apply wait for each apply).

@@ -20,7 +20,7 @@ INCLUDE = os.path.join(ROOT, "include")
 
 HOST_SRC = ["host/geometry.cpp", "host/quadrature.cpp", "host/linalg.cpp", "host/accel_host.cpp",
             "host/accel3_host.cpp", "host/ball3_host.cpp"]
-CUDA_SRC = ["device/kernels.cu", "device/near_tc.cu", "device/local_tc.cu", "device/peaks.cu", "device/apply3.cu",
+CUDA_SRC = ["device/kernels.cu", "device/near_tc.cu", "device/contract_tc.cu", "device/peaks.cu", "device/apply3.cu",
             "api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -2242,7 +2242,7 @@ ls_status ls_plan_autotune(ls_plan plan, int nrhs, ls_tune_report* report) {
   };
   ls_tune_report r{};
   r.nrhs = nrhs;
-  const int conv_opts[3] = {1, 2, 4};
+  const int conv_opts[4] = {1, 2, 4, 8};
   if (ce == cudaSuccess) {
     // FP64: columns per block of the column pass
     const int keep = plan->d64.conv_tc;
@@ -2266,17 +2266,21 @@ ls_status ls_plan_autotune(ls_plan plan, int nrhs, ls_tune_report* report) {
     best = -1;
     int bt = 1, bg = keep_group;
     bool bc = false;
-    const bool keep_lcuda = plan->d32.local_cuda;
-    bool blc = keep_lcuda;
+    const bool keep_lcuda = plan->d32.local_cuda, keep_pcuda = plan->d32.proj_cuda;
+    bool blc = keep_lcuda, bpc = keep_pcuda;
     for (int tc : conv_opts)
       for (int grp = 16; grp >= 4; grp /= 2)
-        for (int var = 0; var < 4; ++var) {
-          // var bit 0: CUDA-core near field; bit 1: CUDA-core local coefficients (groups of 8 or 16)
-          const int cuda = var & 1, lcuda = var >> 1;
-          if (grp > std::max(4, nrhs) || (var && grp < 8) || (lcuda && !plan->d32.LAt)) continue;
+        for (int var = 0; var < 8; ++var) {
+          // var bit 0: CUDA-core near field; bit 1: CUDA-core local coefficients; bit 2: CUDA-core
+          // projection (groups of 8 or 16)
+          const int cuda = var & 1, lcuda = (var >> 1) & 1, pcuda = var >> 2;
+          if (grp > std::max(4, nrhs) || (var && grp < 8) || (lcuda && !plan->d32.LAt) ||
+              (pcuda && plan->d32.n_es > 64))
+            continue;
           plan->d32.conv_tc = tc;
           plan->d32.near_cuda = cuda != 0;
           plan->d32.local_cuda = lcuda != 0;
+          plan->d32.proj_cuda = pcuda != 0;
           const double ms = timed([&] {
             for (int q = 0; q < nrhs;) {
               int nr = grp;
@@ -2291,16 +2295,25 @@ ls_status ls_plan_autotune(ls_plan plan, int nrhs, ls_tune_report* report) {
           ++r.n_candidates;
           if (ms < 0) continue;
           if (tc == 1 && grp == std::min(keep_group, std::max(4, nrhs)) && var == 0) r.ms32_default = ms;
-          if (best < 0 || ms < best) { best = ms; bt = tc; bg = grp; bc = cuda != 0; blc = lcuda != 0; }
+          if (best < 0 || ms < best) {
+            best = ms;
+            bt = tc;
+            bg = grp;
+            bc = cuda != 0;
+            blc = lcuda != 0;
+            bpc = pcuda != 0;
+          }
         }
     plan->d32.conv_tc = best > 0 ? bt : keep_tc;
     plan->d32.near_cuda = best > 0 ? bc : keep_cuda;
     plan->d32.local_cuda = best > 0 ? blc : keep_lcuda;
+    plan->d32.proj_cuda = best > 0 ? bpc : keep_pcuda;
     plan->group32 = best > 0 ? bg : keep_group;
     r.conv_cols32 = plan->d32.conv_tc > 0 ? plan->d32.conv_tc : 1;
     r.group32 = plan->group32;
     r.near_cuda32 = plan->d32.near_cuda ? 1 : 0;
     r.local_cuda32 = plan->d32.local_cuda ? 1 : 0;
+    r.proj_cuda32 = plan->d32.proj_cuda ? 1 : 0;
     r.ms32_best = best;
     ce = cudaStreamSynchronize(ts);
   }
@@ -2314,6 +2327,27 @@ ls_status ls_plan_autotune(ls_plan plan, int nrhs, ls_tune_report* report) {
                                                 "timed out; see ls_plan_device_status");
   }
   if (report) *report = r;
+  return LS_OK;
+}
+
+ls_status ls_plan_set_variants(ls_plan plan, const ls_tune_report* v) {
+  if (!plan) return LS_ERR_INVALID;
+  if (plan->dim != 2) return fail(plan, LS_ERR_UNSUPPORTED, "ls_plan_set_variants: 2-D plans only");
+  if (!v) return fail(plan, LS_ERR_INVALID, "ls_plan_set_variants: null report");
+  auto cols_ok = [](int c) { return c == 1 || c == 2 || c == 4 || c == 8; };
+  auto flag_ok = [](int f) { return f == 0 || f == 1; };
+  if (!cols_ok(v->conv_cols64) || !cols_ok(v->conv_cols32) ||
+      (v->group32 != 4 && v->group32 != 8 && v->group32 != 16) || !flag_ok(v->near_cuda32) ||
+      !flag_ok(v->local_cuda32) || !flag_ok(v->proj_cuda32))
+    return fail(plan, LS_ERR_INVALID, "ls_plan_set_variants: columns must be 1, 2, 4 or 8, the group 4, 8 or 16, "
+                                      "the unit flags 0 or 1");
+  plan->d64.conv_tc = v->conv_cols64;
+  plan->d32.conv_tc = v->conv_cols32;
+  plan->group32 = v->group32;
+  plan->d32.near_cuda = v->near_cuda32 != 0;
+  plan->d32.local_cuda = v->local_cuda32 != 0;
+  plan->d32.proj_cuda = v->proj_cuda32 != 0;
+  plan->graphs.clear();          // captured applies hold the previous variants
   return LS_OK;
 }
 

@@ -245,6 +245,221 @@ __global__ void __launch_bounds__(kLT) k_local_tc(ApplyData<float2> d, const flo
   }
 }
 
+// Equivalent-source projection (Section 3.2: the strengths of cell c solve the
+// fit to the scaled field on the cell's nodes, sigma_c = P_c u_c with P_c the
+// fit's pseudo-inverse folded with the quadrature weights) for R = 8 or 16
+// right-hand sides:  one block per piece (cell k, nodes [jb, je)),
+// D (128 x 2R) = P' (128 x 2n) . [u_hi | u_lo] (2n x 2R) with u
+// interleaved along K (B[r][2j] = Re u_j, B[r][2j + 1] = Im u_j, the layout of
+// u in memory) and the rows of P' built from P_c as it is stored ([node][n_es]):
+// row i < n_es holds (Re P, -Im P) of output i, row 64 + i holds (Im P, Re P),
+// so row i of D is Re sigma_i and row 64 + i is Im sigma_i.  Rows n_es..63
+// and 64 + n_es..127 are zero.  3xTF32 as in the local step, here with both
+// MMAs on [B_hi | B_lo] (N = 2R: an MMA of M = 128 needs N >= 16, so the
+// A_lo . B_lo product of R = 8 comes for free; the epilogue adds columns r and
+// R + r).  Nodes are taken 16 per chunk (K = 32 real, four K steps of 8).
+// A cell of one piece writes sigma directly; a cell of several pieces writes
+// per-piece partial sums and the last piece to finish adds them in piece
+// order, as on the CUDA cores.  The apply passes whole cells, largest first:
+// the tensor cores take a long cell in stride, and without partial sums no
+// block waits on a merge.
+constexpr int kPB = 4096;                // B chunk: 2R <= 32 rows x 128 bytes
+constexpr int kPStage = 2 * kLA + kPB;   // one pipeline stage: P' hi, P' lo, [u_hi | u_lo]
+constexpr int kPSmem = 2 * kPStage + 64;
+
+template <int R>
+__global__ void __launch_bounds__(kLT) k_project_tc(const int4* __restrict__ pieces, const int* __restrict__ piece_off,
+                                                    int nocc, const int64_t* __restrict__ occ_start,
+                                                    const int64_t* __restrict__ P_off, const float2* __restrict__ P,
+                                                    const float2* __restrict__ u, int64_t N,
+                                                    float2* __restrict__ sigma, float2* __restrict__ part,
+                                                    int* __restrict__ count, int n_es, int* __restrict__ tc_err,
+                                                    int spin) {
+  extern __shared__ __align__(1024) unsigned char psm[];
+  uint64_t* bar = reinterpret_cast<uint64_t*>(psm + 2 * kPStage);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 2);
+  int* flag = reinterpret_cast<int*>(tslot + 1);
+  __shared__ int last;
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  const int4 pc = pieces[blockIdx.x];
+  const int k = pc.x, p = pc.w >> 16, np = pc.w & 0xffff;
+  const int nc = pc.z - pc.y, nch = (nc + kLChunk - 1) / kLChunk;
+  const int64_t s0 = occ_start[k] + pc.y;
+  const float2* Pk = P + P_off[k] + int64_t(pc.y) * n_es;
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" :: "r"(ls_u32(tslot)), "r"(32)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (t == 32) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(ls_u32(&bar[0])) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(ls_u32(&bar[1])) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    *flag = 0;
+  }
+  // zero the rows of P' that no output uses, in both stages (hi and lo)
+  for (int e = t; e < 2 * 2 * 2 * (64 - n_es) * 16; e += kLT) {
+    const int w = e & 15, row = (e >> 4) % (64 - n_es), q = (e >> 4) / (64 - n_es);   // q: stage, half, hi / lo
+    unsigned char* A = psm + (q >> 2) * kPStage + (q & 1) * kLA;
+    const int n = n_es + row + ((q >> 1) & 1) * 64;
+    *reinterpret_cast<float2*>(A + lt_off(n, 2 * w)) = make_float2(0.f, 0.f);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tslot;
+  // kind::tf32: D F32, A and B TF32, both K-major; M = 128, N = 2R
+  const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | (uint32_t((2 * R) >> 3) << 17) |
+                         (uint32_t(128 >> 4) << 24);
+  int issued = -1;
+
+  // the inputs of two chunks are in flight in registers: chunk c + 2 is loaded
+  // into the set chunk c was just stored from.  A warp takes 16 outputs x 2
+  // nodes of P (and 8 RHS x 4 nodes of u), so that its 8-byte shared-memory
+  // stores fall on every bank twice
+  constexpr int kPv = 4;                        // 8 node pairs x 4 blocks of 16 outputs x 32 / 256
+  const int nob = (n_es + 15) >> 4;
+  float2 pa[kPv], pb[kPv], ua = make_float2(0.f, 0.f), ub = make_float2(0.f, 0.f);
+  auto p_slot = [&](int i, int& o, int& jj) {
+    const int sl = t + i * kLT, unit = sl >> 5, ln = sl & 31;
+    o = (unit % nob) * 16 + (ln & 15);
+    jj = 2 * (unit / nob) + (ln >> 4);
+    return unit < 8 * nob && o < n_es;
+  };
+  const int ur = (lane & 7) + 8 * (warp % (R / 8)), ujj = (lane >> 3) + 4 * (warp / (R / 8));
+  auto load_chunk = [&](int c, float2 (&pv)[kPv], float2& uv) {
+#pragma unroll
+    for (int i = 0; i < kPv; ++i) {
+      int o, jj;
+      const bool ok = p_slot(i, o, jj) && c * kLChunk + jj < nc;
+      pv[i] = ok ? Pk[int64_t(c * kLChunk + jj) * n_es + o] : make_float2(0.f, 0.f);
+    }
+    const int j = c * kLChunk + ujj;
+    uv = (t < R * kLChunk && j < nc) ? u[int64_t(ur) * N + s0 + j] : make_float2(0.f, 0.f);
+  };
+  // wait until stage c & 1 is free, then split chunk c into it; false: a wait gave up
+  auto store_chunk = [&](int c, const float2 (&pv)[kPv], const float2& uv) {
+    const int s = c & 1;
+    if (c >= 2 && t == 0) {                     // the MMAs of chunk c - 2 have read stage s
+      bool ok = false;
+      for (int it = 0; it < spin && !ok; ++it) ok = lbar_try(ls_u32(&bar[s]), uint32_t((c - 2) >> 1) & 1u);
+      if (!ok) *flag = 1;
+    }
+    __syncthreads();
+    if (*flag) return false;
+    unsigned char* Ahi = psm + s * kPStage;
+    unsigned char* Alo = Ahi + kLA;
+    unsigned char* Bs = Ahi + 2 * kLA;
+#pragma unroll
+    for (int i = 0; i < kPv; ++i) {
+      int o, jj;
+      if (p_slot(i, o, jj)) {
+        float rh, rl, ih, il;
+        tsplit(pv[i].x, rh, rl);
+        tsplit(pv[i].y, ih, il);
+        *reinterpret_cast<float2*>(Ahi + lt_off(o, 2 * jj)) = make_float2(rh, -ih);
+        *reinterpret_cast<float2*>(Ahi + lt_off(64 + o, 2 * jj)) = make_float2(ih, rh);
+        *reinterpret_cast<float2*>(Alo + lt_off(o, 2 * jj)) = make_float2(rl, -il);
+        *reinterpret_cast<float2*>(Alo + lt_off(64 + o, 2 * jj)) = make_float2(il, rl);
+      }
+    }
+    if (t < R * kLChunk) {
+      float rh, rl, ih, il;
+      tsplit(uv.x, rh, rl);
+      tsplit(uv.y, ih, il);
+      *reinterpret_cast<float2*>(Bs + lt_off(ur, 2 * ujj)) = make_float2(rh, ih);
+      *reinterpret_cast<float2*>(Bs + lt_off(R + ur, 2 * ujj)) = make_float2(rl, il);
+    }
+    return true;
+  };
+  // thread 0 issues chunk c's MMAs once every thread has stored it
+  auto issue_chunk = [&](int c) {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (t == 0) {
+      const int s = c & 1;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t a0 = ls_u32(psm + s * kPStage), b0 = a0 + 2 * kLA;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {             // K = 8 per MMA: core-matrix columns 2i, 2i + 1
+        const uint64_t dh = ls_desc(a0 + 2 * i * 128), dl = ls_desc(a0 + kLA + 2 * i * 128);
+        const uint64_t db = ls_desc(b0 + 2 * i * 128);
+        const uint32_t accum = (c > 0 || i > 0) ? 1u : 0u;
+        asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                     " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n"
+                     :: "r"(tmem), "l"(dh), "l"(db), "r"(idesc), "r"(accum) : "memory");
+        asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                     " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n"
+                     :: "r"(tmem), "l"(dl), "l"(db), "r"(idesc), "r"(1u) : "memory");
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                   :: "r"(ls_u32(&bar[s])) : "memory");
+      issued = c;
+    }
+  };
+  if (nch > 0) load_chunk(0, pa, ua);
+  if (nch > 1) load_chunk(1, pb, ub);
+  for (int c = 0; c < nch; c += 2) {
+    if (!store_chunk(c, pa, ua)) break;
+    if (c + 2 < nch) load_chunk(c + 2, pa, ua);
+    issue_chunk(c);
+    if (c + 1 >= nch) break;
+    if (!store_chunk(c + 1, pb, ub)) break;
+    if (c + 3 < nch) load_chunk(c + 3, pb, ub);
+    issue_chunk(c + 1);
+  }
+  if (t == 0 && issued >= 0) {
+    bool ok = false;
+    for (int it = 0; it < kLDrain && !ok; ++it) ok = lbar_try(ls_u32(&bar[issued & 1]), uint32_t(issued >> 1) & 1u);
+    if (!ok || issued != nch - 1) *flag = 1;
+  }
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const bool good = *flag == 0 && nch > 0;
+  if (*flag && t == 0 && tc_err) atomicExch(tc_err, 1);
+  // a cell of one piece writes sigma ([r][cell][i]); otherwise slot p of the cell ([piece][r][i])
+  float2* out = np == 1 ? sigma + int64_t(k) * n_es : part + (int64_t(piece_off[k]) + p) * R * n_es;
+  const int64_t rs = np == 1 ? int64_t(nocc) * n_es : n_es;
+  if (warp < 4) {
+    const int m = 32 * warp + lane, o = m & 63, im = m >> 6;
+    float v[2 * R];
+    if (good) {
+      const uint32_t ta = tmem + (uint32_t(32 * warp) << 16);
+#pragma unroll
+      for (int q = 0; q < 2 * R; q += 16) tmem_ld16(ta + uint32_t(q), v + q);
+    } else {
+#pragma unroll
+      for (int q = 0; q < 2 * R; ++q) v[q] = 0.f;
+    }
+    if (o < n_es) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) reinterpret_cast<float*>(out + r * rs + o)[im] = v[r] + v[R + r];
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(32) : "memory");
+  }
+  if (np == 1) return;
+  __threadfence();
+  __syncthreads();
+  if (t == 0) last = atomicAdd(count + k, 1) == np - 1;
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  const float2* slots = part + int64_t(piece_off[k]) * R * n_es;
+  for (int e = t; e < R * n_es; e += kLT) {
+    float2 v = __ldcg(slots + e);
+    for (int q = 1; q < np; ++q) v = cadd(v, __ldcg(slots + int64_t(q) * R * n_es + e));
+    const int r = e / n_es, i = e - r * n_es;
+    sigma[(int64_t(r) * nocc + k) * n_es + i] = v;
+  }
+  if (t == 0) count[k] = 0;
+}
+
 // plan time: LA' in the tile layout, per chunk of 16 complex K columns the 64
 // hi rows then the 64 lo rows (row n < 32: (Re, -Im) of output n; 32 <= n < 64:
 // (Im, Re) of output n - 32), zero past K or nfb2
@@ -294,5 +509,22 @@ cudaError_t local_coeffs_tc(const ApplyData<float2>& d, cudaStream_t st) {
 
 template cudaError_t local_coeffs_tc<8>(const ApplyData<float2>&, cudaStream_t);
 template cudaError_t local_coeffs_tc<16>(const ApplyData<float2>&, cudaStream_t);
+
+template <int R>
+cudaError_t project_tc(const ApplyData<float2>& d, const float2* u, cudaStream_t st) {
+  static unsigned long long attr = 0;
+  if (first_on_device(attr)) {
+    const cudaError_t e = cudaFuncSetAttribute(k_project_tc<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, kPSmem);
+    if (e != cudaSuccess) return e;
+  }
+  if (d.n_es <= 0 || d.n_es > 64 || d.nocc <= 0 || !d.cell_pieces) return cudaErrorInvalidValue;
+  // one block per whole cell, largest first: no partial sums (a block streams its cell's chunks)
+  k_project_tc<R><<<d.nocc, kLT, kPSmem, st>>>(d.cell_pieces, d.piece_off, d.nocc, d.occ_start, d.P_off, d.P, u, d.N,
+                                               d.sigma, d.proj_part, d.proj_count, d.n_es, d.tc_err, d.tc_spin);
+  return cudaGetLastError();
+}
+
+template cudaError_t project_tc<8>(const ApplyData<float2>&, const float2*, cudaStream_t);
+template cudaError_t project_tc<16>(const ApplyData<float2>&, const float2*, cudaStream_t);
 
 }  // namespace lsd

@@ -301,6 +301,36 @@ cudaError_t fft2d(T* x, int M, int logM, const T* tw, bool inverse, cudaStream_t
   return cudaGetLastError();
 }
 
+// The lattice transforms' FFT per precision.  complex64: the radix-16
+// transform (fft16_smem, M / 16 threads a transform, padded layout), a third
+// faster on the 16-RHS lattice convolution than radix 4.  complex128: the
+// radix-4 transform (fft_smem, M / 8 threads, plain layout): FP64 values
+// sixteen a thread spill, and the FP64 pipe bounds these kernels either way
+// (the radix-16 form measured 0.197 against 0.173 ms for the FP64 convolution).
+template <typename T>
+struct LatFft;
+template <>
+struct LatFft<float2> {
+  static constexpr int kDiv = 16;              // values per thread and transform
+  static constexpr int kColThreads = 512;      // launch bound of the column pass
+  __host__ __device__ static constexpr int len(int N) { return fft16_len(N); }
+  __device__ static int at(int i) { return fpad(i); }
+  __device__ static void run(float2* x, int N, int logN, bool inv, const float2* tw, int t) {
+    (void)logN;
+    fft16_smem<float2>(x, N, inv, tw, t);
+  }
+};
+template <>
+struct LatFft<double2> {
+  static constexpr int kDiv = 8;
+  static constexpr int kColThreads = 1024;
+  __host__ __device__ static constexpr int len(int N) { return N; }
+  __device__ static int at(int i) { return i; }
+  __device__ static void run(double2* x, int N, int logN, bool inv, const double2* tw, int t) {
+    fft_smem<double2>(x, N, logN, inv, tw, t);
+  }
+};
+
 // ------------------------------------------------------------ pruned, fused lattice convolution
 // Sources live only on the L + 1 face rows a = k Ne (k = 0..L) of the M x M
 // padded lattice, and only the n_lat x n_lat corner of the result is read.
@@ -315,13 +345,13 @@ cudaError_t fft2d(T* x, int M, int logM, const T* tw, bool inverse, cudaStream_t
 //                FFT along a, keep a < n_lat            -> Vt[a][b], n_lat x M
 //  k_inv_rows  : inverse FFT along b of rows a < n_lat, keep b < n_lat -> V
 template <typename T>
-__global__ void __launch_bounds__(kFftMaxM / 8) k_src_rows(int M, int logM, int n_lat, int Ne, int L,
-                                                           const int* __restrict__ occ_of_cell,
-                                                           const T* __restrict__ sigma_all, int n_es, int nocc,
-                                                           const T* __restrict__ tw, T* __restrict__ R_all,
-                                                           int64_t stride) {
+__global__ void __launch_bounds__(kFftMaxM / LatFft<T>::kDiv) k_src_rows(int M, int logM, int n_lat, int Ne, int L,
+                                                            const int* __restrict__ occ_of_cell,
+                                                            const T* __restrict__ sigma_all, int n_es, int nocc,
+                                                            const T* __restrict__ tw, T* __restrict__ R_all,
+                                                            int64_t stride) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* s = reinterpret_cast<T*>(smem_raw);
+  T* s = reinterpret_cast<T*>(smem_raw);       // LatFft<T> layout
   const int k = blockIdx.x, kind = blockIdx.y;   // face row, 0 monopole / 1 dipole
   const T* sigma = sigma_all + int64_t(blockIdx.z) * nocc * n_es;
   T* R = R_all + int64_t(blockIdx.z) * stride;
@@ -341,12 +371,13 @@ __global__ void __launch_bounds__(kFftMaxM / 8) k_src_rows(int M, int logM, int 
         }
       }
     }
-    s[b] = v;
+    s[LatFft<T>::at(b)] = v;
   }
   __syncthreads();
-  fft_smem<T>(s, M, logM, false, tw, threadIdx.x);
+  LatFft<T>::run(s, M, logM, false, tw, threadIdx.x);
+  __syncthreads();
   T* out = R + (int64_t(kind) * (L + 1) + k) * M;
-  for (int b = threadIdx.x; b < M; b += blockDim.x) out[b] = s[b];
+  for (int b = threadIdx.x; b < M; b += blockDim.x) out[b] = s[LatFft<T>::at(b)];
 }
 
 // spectra quarter layout: Q[l][k] for l, k in [0, M/2] (k fastest).
@@ -355,7 +386,7 @@ __global__ void __launch_bounds__(kFftMaxM / 8) k_src_rows(int M, int logM, int 
 // repeated Ne times: X[f] = Y[f mod (M/Ne)].  Ms = M/Ne (0: use the full
 // length), logMs its log2.
 template <typename T>
-__global__ void __launch_bounds__(1024) k_conv_cols(int M, int logM, int n_lat, int Ne, int L, int TC, int Ms,
+__global__ void __launch_bounds__(LatFft<T>::kColThreads) k_conv_cols(int M, int logM, int n_lat, int Ne, int L, int TC, int Ms,
                                                     int logMs, const T* __restrict__ R_all,
                                                     const T* __restrict__ Gq, const T* __restrict__ Dq,
                                                     const T* __restrict__ tw, T* __restrict__ Vt_all,
@@ -363,14 +394,40 @@ __global__ void __launch_bounds__(1024) k_conv_cols(int M, int logM, int n_lat, 
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const T* R = R_all + int64_t(blockIdx.y) * stride;
   T* Vt = Vt_all + int64_t(blockIdx.y) * stride;
-  T* xm = reinterpret_cast<T*>(smem_raw);      // [TC][M]
-  T* xd = xm + TC * M;                         // [TC][M]
+  const int PM = LatFft<T>::len(M);            // one column in the LatFft<T> layout
+  T* xm = reinterpret_cast<T*>(smem_raw);      // [TC][PM]
+  T* xd = xm + TC * PM;                        // [TC][PM]
   const int b0 = blockIdx.x * TC;
   const int half = M / 2;
-  const int G = M / 8;
+  constexpr int kDiv = LatFft<T>::kDiv;
+  const int G = M / kDiv;                      // threads per column
   const int c = threadIdx.x / G, t = threadIdx.x % G;
+  // the spectral product of column element e (column e >> logM, row e & (M - 1)):
+  // monopole value vm times G^, plus dipole value vd times D^ (odd in the a offset)
+  auto product = [&](auto value_of) {
+#pragma unroll
+    for (int h2 = 0; h2 < kDiv / 8; ++h2) {    // kDiv products per thread, eight loads at a time
+      T gq[8], dq[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int e = threadIdx.x + (8 * h2 + q) * blockDim.x, cc = e >> logM, a = e & (M - 1), b = b0 + cc;
+        const int kq = a <= half ? a : M - a, lq = b <= half ? b : M - b;
+        const int64_t qi = int64_t(lq) * (half + 1) + kq;
+        gq[q] = Gq[qi];
+        dq[q] = Dq[qi];
+      }
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int e = threadIdx.x + (8 * h2 + q) * blockDim.x, cc = e >> logM, a = e & (M - 1);
+        const T d = a > half ? mk(-dq[q].x, -dq[q].y) : dq[q];
+        T vm, vd;
+        value_of(cc, a, vm, vd);
+        xm[cc * PM + LatFft<T>::at(a)] = cfma(vd, d, cmul(vm, gq[q]));
+      }
+    }
+  };
   if (Ms > 0) {
-    // short spectra: monopole in xd[c][0, Ms), dipole in xd[c][Ms, 2 Ms)
+    // short spectra: monopole in xd[c][0, Ms), dipole in xd[c][Ms, 2 Ms) (plain layout)
     for (int e = threadIdx.x; e < TC * Ms; e += blockDim.x) {
       const int cc = e / Ms, k = e % Ms;
       T vm = czero(T{}), vd = czero(T{});
@@ -378,32 +435,20 @@ __global__ void __launch_bounds__(1024) k_conv_cols(int M, int logM, int n_lat, 
         vm = R[int64_t(k) * M + b0 + cc];
         vd = R[(int64_t(L + 1) + k) * M + b0 + cc];
       }
-      xd[cc * M + k] = vm;
-      xd[cc * M + Ms + k] = vd;
+      xd[cc * PM + k] = vm;
+      xd[cc * PM + Ms + k] = vd;
     }
     __syncthreads();
     // two transforms of length Ms per column, by the column's first 2 Ms / 8 threads
     const int Gs = Ms / 8;
     const bool act = t < 2 * Gs;
     const int which = t / Gs;                  // 0 monopole, 1 dipole
-    fft_smem<T>(xd + c * M + (act ? which : 0) * Ms, Ms, logMs, false, tw, act ? t % Gs : 0, M / Ms, act);
-    // TC M products over TC M / 8 threads: eight per thread, the spectra loaded together
-    T gq[8], dq[8];
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const int e = threadIdx.x + q * blockDim.x, cc = e >> logM, a = e & (M - 1), b = b0 + cc;
-      const int kq = a <= half ? a : M - a, lq = b <= half ? b : M - b;
-      const int64_t qi = int64_t(lq) * (half + 1) + kq;
-      gq[q] = Gq[qi];
-      dq[q] = Dq[qi];
-    }
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const int e = threadIdx.x + q * blockDim.x, cc = e >> logM, a = e & (M - 1);
-      const T d = a > half ? mk(-dq[q].x, -dq[q].y) : dq[q];   // dipole table is odd in the a offset
+    fft_smem<T>(xd + c * PM + (act ? which : 0) * Ms, Ms, logMs, false, tw, act ? t % Gs : 0, M / Ms, act);
+    product([&](int cc, int a, T& vm, T& vd) {
       const int f = a & (Ms - 1);
-      xm[e] = cfma(xd[cc * M + Ms + f], d, cmul(xd[cc * M + f], gq[q]));
-    }
+      vm = xd[cc * PM + f];
+      vd = xd[cc * PM + Ms + f];
+    });
     __syncthreads();
   } else {
     for (int e = threadIdx.x; e < TC * M; e += blockDim.x) {
@@ -414,56 +459,50 @@ __global__ void __launch_bounds__(1024) k_conv_cols(int M, int logM, int n_lat, 
         vm = R[int64_t(k) * M + b0 + cc];
         vd = R[(int64_t(L + 1) + k) * M + b0 + cc];
       }
-      xm[e] = vm;
-      xd[e] = vd;
+      xm[cc * PM + LatFft<T>::at(a)] = vm;
+      xd[cc * PM + LatFft<T>::at(a)] = vd;
     }
     __syncthreads();
-    fft_smem<T>(xm + c * M, M, logM, false, tw, t);
-    fft_smem<T>(xd + c * M, M, logM, false, tw, t);
-    T gq[8], dq[8];
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const int e = threadIdx.x + q * blockDim.x, cc = e >> logM, a = e & (M - 1), b = b0 + cc;
-      const int kq = a <= half ? a : M - a, lq = b <= half ? b : M - b;
-      const int64_t qi = int64_t(lq) * (half + 1) + kq;
-      gq[q] = Gq[qi];
-      dq[q] = Dq[qi];
-    }
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const int e = threadIdx.x + q * blockDim.x, a = e & (M - 1);
-      const T d = a > half ? mk(-dq[q].x, -dq[q].y) : dq[q];   // dipole table is odd in the a offset
-      xm[e] = cfma(xd[e], d, cmul(xm[e], gq[q]));
-    }
+    LatFft<T>::run(xm + c * PM, M, logM, false, tw, t);
+    __syncthreads();
+    LatFft<T>::run(xd + c * PM, M, logM, false, tw, t);
+    __syncthreads();
+    product([&](int cc, int a, T& vm, T& vd) {
+      vm = xm[cc * PM + LatFft<T>::at(a)];
+      vd = xd[cc * PM + LatFft<T>::at(a)];
+    });
     __syncthreads();
   }
-  fft_smem<T>(xm + c * M, M, logM, true, tw, t);
+  LatFft<T>::run(xm + c * PM, M, logM, true, tw, t);
+  __syncthreads();
   for (int e = threadIdx.x; e < TC * n_lat; e += blockDim.x) {
     const int a = e / TC, cc = e % TC;
-    Vt[int64_t(a) * M + b0 + cc] = xm[cc * M + a];
+    Vt[int64_t(a) * M + b0 + cc] = xm[cc * PM + LatFft<T>::at(a)];
   }
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kFftMaxM / 8) k_inv_rows(int M, int logM, int n_lat, const T* __restrict__ tw,
-                                                           const T* __restrict__ Vt_all, T* __restrict__ V_all,
-                                                           int64_t stride) {
+__global__ void __launch_bounds__(kFftMaxM / LatFft<T>::kDiv) k_inv_rows(int M, int logM, int n_lat, const T* __restrict__ tw,
+                                                            const T* __restrict__ Vt_all, T* __restrict__ V_all,
+                                                            int64_t stride) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* s = reinterpret_cast<T*>(smem_raw);
+  T* s = reinterpret_cast<T*>(smem_raw);       // LatFft<T> layout
   const T* Vt = Vt_all + int64_t(blockIdx.y) * stride;
   T* V = V_all + int64_t(blockIdx.y) * stride;
   const int64_t a = blockIdx.x;
-  T v[8];                                      // M / 8 threads: eight loads each, issued together
+  constexpr int kDiv = LatFft<T>::kDiv;
+  T v[kDiv];                                   // M / kDiv threads: kDiv loads each, issued together
 #pragma unroll
-  for (int q = 0; q < 8; ++q) v[q] = Vt[a * M + threadIdx.x + q * blockDim.x];
+  for (int q = 0; q < kDiv; ++q) v[q] = Vt[a * M + threadIdx.x + q * blockDim.x];
 #pragma unroll
-  for (int q = 0; q < 8; ++q) s[threadIdx.x + q * blockDim.x] = v[q];
+  for (int q = 0; q < kDiv; ++q) s[LatFft<T>::at(threadIdx.x + q * blockDim.x)] = v[q];
   __syncthreads();
-  fft_smem<T>(s, M, logM, true, tw, threadIdx.x);
-  for (int b = threadIdx.x; b < n_lat; b += blockDim.x) V[a * M + b] = s[b];
+  LatFft<T>::run(s, M, logM, true, tw, threadIdx.x);
+  __syncthreads();
+  for (int b = threadIdx.x; b < n_lat; b += blockDim.x) V[a * M + b] = s[LatFft<T>::at(b)];
 }
 
-// columns per block of the column pass: one, so that the M blocks of M / 8
+// columns per block of the column pass: one, so that the M blocks of M / kDiv
 // threads are all resident at once, several per SM (wider blocks left SMs idle:
 // complex64 with 8 columns ran 128 blocks; complex128 with 4 ran 1.7 waves)
 template <typename T>
@@ -476,29 +515,33 @@ cudaError_t lattice_conv(const ApplyData<T>& d, int nr, cudaStream_t st) {
   const int M = d.M;
   if (M < 256 || M > kFftMaxM || (M & (M - 1))) return cudaErrorInvalidValue;
   const int TC = d.conv_tc > 0 ? d.conv_tc : conv_cols_tc<T>(M);
-  if (M % TC != 0 || TC * (M / 8) > 1024 || size_t(2) * TC * M * sizeof(T) > 200 * 1024) return cudaErrorInvalidValue;
+  constexpr int kDiv = LatFft<T>::kDiv;
+  const size_t pm = size_t(LatFft<T>::len(M)) * sizeof(T);   // one column or row in the LatFft<T> layout
+  if (M % TC != 0 || TC * (M / kDiv) > LatFft<T>::kColThreads || 2 * TC * pm > 200 * 1024)
+    return cudaErrorInvalidValue;
   static unsigned long long attr_done = 0;
   if (first_on_device(attr_done)) {
-    cudaFuncSetAttribute(k_src_rows<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kFftMaxM * sizeof(T)));
-    cudaFuncSetAttribute(k_inv_rows<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kFftMaxM * sizeof(T)));
+    const int prow = int(LatFft<T>::len(kFftMaxM) * sizeof(T));
+    cudaFuncSetAttribute(k_src_rows<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, prow);
+    cudaFuncSetAttribute(k_inv_rows<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, prow);
     cudaFuncSetAttribute(k_conv_cols<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   }
   // R (2 (L+1) x M) lives in Sd, Vt (n_lat x M) in Sm, V (n_lat x M) back in Sd
   const int64_t stride = d.lattice_rows() * M;
-  k_src_rows<T><<<dim3(d.L + 1, 2, nr), M / 8, M * sizeof(T), st>>>(M, d.logM, d.n_lat, d.Ne, d.L, d.occ_of_cell,
+  k_src_rows<T><<<dim3(d.L + 1, 2, nr), M / kDiv, pm, st>>>(M, d.logM, d.n_lat, d.Ne, d.L, d.occ_of_cell,
                                                                      d.sigma, d.n_es, d.nocc, d.tw, d.Sd, stride);
   // short forward column transforms when the source rows (every Ne-th) fold to length M / Ne
   int Ms = 0, logMs = 0;
   if (M % d.Ne == 0 && d.L + 1 <= M / d.Ne) {
     const int m = M / d.Ne;
-    if (m >= 16 && (m & (m - 1)) == 0) {
+    if (m >= 16 && m <= 4 * M / kDiv && (m & (m - 1)) == 0) {   // 2 m / 8 threads of the column's M / kDiv
       Ms = m;
       while ((1 << logMs) < m) ++logMs;
     }
   }
-  k_conv_cols<T><<<dim3(M / TC, nr), TC * (M / 8), size_t(2) * TC * M * sizeof(T), st>>>(
+  k_conv_cols<T><<<dim3(M / TC, nr), TC * (M / kDiv), 2 * TC * pm, st>>>(
       M, d.logM, d.n_lat, d.Ne, d.L, TC, Ms, logMs, d.Sd, d.Gq, d.Dq, d.tw, d.Sm, stride);
-  k_inv_rows<T><<<dim3(d.n_lat, nr), M / 8, M * sizeof(T), st>>>(M, d.logM, d.n_lat, d.tw, d.Sm, d.Sd, stride);
+  k_inv_rows<T><<<dim3(d.n_lat, nr), M / kDiv, pm, st>>>(M, d.logM, d.n_lat, d.tw, d.Sm, d.Sd, stride);
   return cudaGetLastError();
 }
 
@@ -857,9 +900,18 @@ constexpr int near_rows_per_warp() { return sizeof(T) == 8 && R >= 2 ? 4 : 2; }
 template <typename T, int R>
 cudaError_t apply_r(const ApplyData<T>& d, const T* u, T* out, cudaStream_t st, cudaEvent_t* ev) {
   if (ev) cudaEventRecord(ev[0], st);
-  k_es_project<T, R><<<d.n_pieces, 256, contraction_smem<T>(R, kProjStage), st>>>(
-      d.pieces, d.piece_off, d.nocc, d.occ_start, d.P_off, d.P, d.Ps, u, d.N, d.sigma, d.proj_part, d.proj_count,
-      d.n_es, d.utc, d.utef);
+  bool proj_done = false;
+  if constexpr (sizeof(T) == 8 && R >= 8) {
+    if (!d.proj_cuda && d.n_es <= 64) {     // tensor cores (device/contract_tc.cu)
+      const cudaError_t e0 = project_tc<R>(d, u, st);
+      if (e0 != cudaSuccess) return e0;
+      proj_done = true;
+    }
+  }
+  if (!proj_done)
+    k_es_project<T, R><<<d.n_pieces, 256, contraction_smem<T>(R, kProjStage), st>>>(
+        d.pieces, d.piece_off, d.nocc, d.occ_start, d.P_off, d.P, d.Ps, u, d.N, d.sigma, d.proj_part, d.proj_count,
+        d.n_es, d.utc, d.utef);
   if (ev) cudaEventRecord(ev[1], st);
   if (ev) cudaEventRecord(ev[2], st);        // the lattice fill is fused into k_src_rows
   cudaError_t e = lattice_conv(d, R, st);
@@ -873,7 +925,7 @@ cudaError_t apply_r(const ApplyData<T>& d, const T* u, T* out, cudaStream_t st, 
   if (sm_local > 160 * 1024) return cudaErrorInvalidValue;
   bool local_done = false;
   if constexpr (sizeof(T) == 8 && R >= 8) {
-    if (!d.local_cuda && d.LAt) {           // tensor cores (device/local_tc.cu)
+    if (!d.local_cuda && d.LAt) {           // tensor cores (device/contract_tc.cu)
       const cudaError_t e3 = local_coeffs_tc<R>(d, st);
       if (e3 != cudaSuccess) return e3;
       local_done = true;

@@ -61,6 +61,7 @@ struct ApplyData {
   int conv_tc = 0;                      // columns per block of the lattice column pass (0: default, 1)
   bool near_cuda = false;               // complex64, 8 or 16 RHS: CUDA-core near field instead of tensor cores
   bool local_cuda = false;              // complex64, 8 or 16 RHS: CUDA-core local coefficients instead of tensor cores
+  bool proj_cuda = false;               // complex64, 8 or 16 RHS: CUDA-core projection instead of tensor cores
   const unsigned char* LAt = nullptr;   // complex64 only: LA in the tensor-core tile layout (local_tc_tiles)
   const T* Wt = nullptr;                // complex64 only: the blocks in the tensor-core tile layout
   const float* tc_rscale = nullptr;     // complex64 only: 1 / (power-of-two scale) of each near-field row
@@ -114,7 +115,7 @@ cudaError_t near_eval_tc(const ApplyData<float2>& d, const float2* u, float2* ou
 // that writes that layout (d.items128, d.tile_off, d.Wb set) into Wt.
 int64_t tc_tile_elems(int nrow, int nblk);
 cudaError_t tile_weights(const ApplyData<float2>& d, float2* Wt, float* rscale, cudaStream_t st);
-// Local coefficients of 8 or 16 complex64 RHS on the tensor cores (device/local_tc.cu, 3xTF32):
+// Local coefficients of 8 or 16 complex64 RHS on the tensor cores (device/contract_tc.cu, 3xTF32):
 // the same contraction as k_local_coeffs with LA in the tile layout that local_tc_tiles writes at
 // plan time (local_tc_bytes(K) bytes, K = n_loc + 9 n_es; nfb2 <= 32).
 int local_tc_chunks(int K);
@@ -122,6 +123,11 @@ size_t local_tc_bytes(int K);
 cudaError_t local_tc_tiles(const float2* LA, int K, int nfb2, unsigned char* LAt, cudaStream_t st);
 template <int R>
 cudaError_t local_coeffs_tc(const ApplyData<float2>& d, cudaStream_t st);
+// Equivalent-source projection of 8 or 16 complex64 RHS on the tensor cores (device/contract_tc.cu,
+// 3xTF32): the sums of k_es_project, one block per whole cell (d.cell_pieces), P_c read as stored;
+// n_es <= 64.
+template <int R>
+cudaError_t project_tc(const ApplyData<float2>& d, const float2* u, cudaStream_t st);
 
 // Device-resident pieces of a 3-D plan (Section 5: ball, cube cells of side H,
 // L per axis) for one arithmetic precision.  Vectors are in the plan's node

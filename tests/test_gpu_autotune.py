@@ -24,11 +24,12 @@ def test_autotuned_plan_reproduces_the_default_variants():
     ref, tuned = Plan(wl, W.n2_of(wl)), Plan(wl, W.n2_of(wl))
     rep = tuned.autotune(16)
     assert rep["nrhs"] == 16
-    assert rep["conv_cols64"] in (1, 2, 4) and rep["conv_cols32"] in (1, 2, 4)
+    assert rep["conv_cols64"] in (1, 2, 4, 8) and rep["conv_cols32"] in (1, 2, 4, 8)
     assert rep["group32"] in (4, 8, 16) and rep["near_cuda32"] in (0, 1)
     assert rep["near_cuda32"] == 0 or rep["group32"] >= 8
     assert rep["local_cuda32"] in (0, 1) and (rep["local_cuda32"] == 0 or rep["group32"] >= 8)
-    assert rep["n_candidates"] >= 3 + 5
+    assert rep["proj_cuda32"] in (0, 1) and (rep["proj_cuda32"] == 0 or rep["group32"] >= 8)
+    assert rep["n_candidates"] >= 4 + 9
     assert 0 < rep["ms64_best"] <= rep["ms64_default"] and 0 < rep["ms32_best"] <= rep["ms32_default"]
     U = W.random_density(ref.N, nrhs=16, seed=W.SEED + 7)
     u64 = torch.from_numpy(U[0]).to("cuda:0")

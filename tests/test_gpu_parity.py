@@ -137,6 +137,37 @@ def test_tensor_core_near_field(name, nrhs, request):
         check_mixed(many[r], c.to_plan(c.op.apply(U[r])))
 
 
+@pytest.mark.parametrize("nrhs", [8, 16])
+def test_every_complex64_unit_variant(kite, nrhs):
+    """Pinned by ls_plan_set_variants, each tensor-core / CUDA-core choice for
+    the projection (3xTF32), local coefficients (3xTF32) and near field (split
+    FP16) reproduces the FP64 oracle within the mixed bound, element by
+    element, and the eight variants agree with one another to FP32 rounding."""
+    from paper_1509_05063_gb300 import LS_MIXED
+    U = W.random_density(kite.dz.N, nrhs=nrhs, seed=W.SEED + 13)
+    refs = [kite.to_plan(kite.op.apply(U[r])) for r in range(nrhs)]
+    Ud = kite.dev(U, torch.complex64)
+    outs = []
+    try:
+        for var in range(8):
+            kite.plan.set_variants(conv_cols32=1 + (var % 2), group32=nrhs, near_cuda32=var & 1,
+                                   local_cuda32=(var >> 1) & 1, proj_cuda32=var >> 2)
+            got = kite.plan.apply(Ud, prec=LS_MIXED).cpu().numpy()
+            for r in range(nrhs):
+                check_mixed(got[r], refs[r])
+            outs.append(got.astype(np.complex128))
+        for got in outs[1:]:
+            assert rel(got, outs[0]) < 2e-6
+        kite.plan.device_status()
+    finally:
+        kite.plan.set_variants()                # the plan's defaults: tensor cores, groups of 16
+    from paper_1509_05063_gb300 import LSError
+    with pytest.raises(LSError):
+        kite.plan.set_variants(group32=5)
+    with pytest.raises(LSError):
+        kite.plan.set_variants(proj_cuda32=2)
+
+
 @pytest.mark.parametrize("name", ["disc", "kite"])
 def test_mixed_apply_within_bound(name, request):
     c = request.getfixturevalue(name)

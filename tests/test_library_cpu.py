@@ -79,6 +79,7 @@ def test_invalid_arguments_return_status(lib):
     assert lib.ls_plan_device_status(None) == 1
     assert lib.ls_set_wait_limit(None, 0) == 1
     assert lib.ls_plan_autotune(None, 16, None) == 1
+    assert lib.ls_plan_set_variants(None, None) == 1
 
 
 def _small_disc():
