@@ -321,6 +321,37 @@ def test_cfg2_full_size_sampled_rows():
     plan.close()
 
 
+def test_largest_lattice_sampled_rows():
+    """A 65 x 65 cell layout (N_eq = 8: n_lat = 521) takes the largest lattice,
+    M = 2048, where the complex64 transform ends with its radix-8 pass: FP64,
+    one complex64 and 16 complex64 right-hand sides against oracle rows
+    computed one by one (near rows + the oracle accelerator's far part)."""
+    from paper_1509_05063_gb300 import LS_FP64, LS_MIXED, Plan
+    wl = W.place_cells(W.disc(level=3, kappa=2.0, n2c=2.0, collar_w=0.6, tau0=0.3, tau1=0.95, R_a=3, R_b=2,
+                              R_cart=2, n_rho=48, N_tau=64), L=65, m=3, N_eq=8)
+    plan = Plan(wl, W.n2_of(wl))
+    assert plan.info["fft_M"] == 2048
+    xy, canon = plan.nodes()
+    dz = Discretisation(wl)
+    rows = W.random_rows(dz.N, 48)
+    U = W.random_density(dz.N, nrhs=16, seed=W.SEED + 22)
+    cells = Cells(dz)
+    nm = near_matrix(dz, cells, rows=rows, chunk=16)
+    acc = Accelerator(dz, cells)
+    checked = (0, 7, 15)
+    ref = {r: U[r][rows] + wl.kappa ** 2 * (nm @ U[r] + acc.apply_far(U[r])[rows]) for r in checked}
+    sel = np.argsort(canon)[rows]
+    Ud = torch.from_numpy(np.ascontiguousarray(U[:, canon])).to("cuda:0")
+    got = plan.apply(Ud[0].contiguous(), prec=LS_FP64).cpu().numpy()[sel]
+    assert rel(got, ref[0]) < 1e-12
+    got32 = plan.apply(Ud[0].to(torch.complex64), prec=LS_MIXED).cpu().numpy()[sel]
+    check_mixed(got32, ref[0])
+    got16 = plan.apply(Ud.to(torch.complex64), prec=LS_MIXED).cpu().numpy()[:, sel]
+    for r in checked:
+        check_mixed(got16[r], ref[r])
+    plan.close()
+
+
 def test_many_directions_seeded_from_earlier_solutions(disc):
     """More directions than one lock-step batch: later batches start from the
     least-squares combination of the earlier solutions (A x_j = b_j), which
