@@ -1,6 +1,7 @@
 // C ABI of the library (include/ls.h): plan creation and upload, apply,
 // GMRES solve (FP64 and mixed complex64 + FP64 refinement) and far field.
 #include <algorithm>
+#include <array>
 #include <chrono>
 #include <cmath>
 #include <complex>
@@ -2488,13 +2489,18 @@ struct ActiveSet {
   int n_cells = 0;
   int4* items = nullptr;
   int n_items = 0;
+  int2* lat_lists = nullptr;           // the lattice work lists of every lattice size, back to back
+  std::vector<lsd::LatWork> lat;       // one per lattice size among the active instances
   void release() {
     if (pieces) cudaFree(pieces);
     if (cells) cudaFree(cells);
     if (items) cudaFree(items);
+    if (lat_lists) cudaFree(lat_lists);
     pieces = nullptr;
     cells = nullptr;
     items = nullptr;
+    lat_lists = nullptr;
+    lat.clear();
   }
 };
 
@@ -2512,15 +2518,6 @@ struct ls_batch_s : DevOwner {
   std::vector<ActiveSet> sets;
   Krylov K;
   GraphCache graphs;
-  lsd::SideStreams side;                              // instances' lattice convolutions side by side
-  void release_side() {
-    for (int i = 0; i < side.n; ++i) {
-      if (side.s[i]) cudaStreamDestroy(side.s[i]);
-      if (side.join[i]) cudaEventDestroy(side.join[i]);
-    }
-    if (side.fork) cudaEventDestroy(side.fork);
-    side = lsd::SideStreams();
-  }
   void release_sets() {
     for (auto& a : sets) a.release();
     sets.clear();
@@ -2562,7 +2559,45 @@ int active_set(ls_batch b, const char* need, cudaError_t* err) {
   a.n_pieces = int(pieces.size());
   a.n_cells = int(cells.size() / 2);
   a.n_items = int(items.size() / 4);
+  // lattice work lists per lattice size: (instance, face row), (instance, column), (instance, kept row)
+  std::map<int, std::vector<int>> by_M;
+  for (int i : a.ids) by_M[b->plans[i]->d64.M].push_back(i);
+  std::vector<int2> lat_lists;
+  std::vector<std::array<size_t, 3>> lat_off;
+  for (const auto& [M, group] : by_M) {
+    lsd::LatWork w;
+    w.M = M;
+    std::array<size_t, 3> o{};
+    o[0] = lat_lists.size();
+    for (int i : group)
+      for (int k = 0; k <= b->plans[i]->d64.L; ++k) lat_lists.push_back(make_int2(i, k));
+    o[1] = lat_lists.size();
+    for (int i : group)
+      for (int c = 0; c < M; ++c) lat_lists.push_back(make_int2(i, c));
+    o[2] = lat_lists.size();
+    for (int i : group)
+      for (int r = 0; r < b->plans[i]->d64.n_lat; ++r) lat_lists.push_back(make_int2(i, r));
+    w.n_src = int(o[1] - o[0]);
+    w.n_cols = int(o[2] - o[1]);
+    w.n_rows = int(lat_lists.size() - o[2]);
+    a.lat.push_back(w);
+    lat_off.push_back(o);
+  }
   *err = cudaSuccess;
+  if (!lat_lists.empty()) {
+    *err = cudaMalloc(&a.lat_lists, lat_lists.size() * sizeof(int2));
+    if (*err == cudaSuccess)
+      *err = cudaMemcpy(a.lat_lists, lat_lists.data(), lat_lists.size() * sizeof(int2), cudaMemcpyHostToDevice);
+    if (*err != cudaSuccess) {
+      a.release();
+      return -1;
+    }
+    for (size_t g = 0; g < a.lat.size(); ++g) {
+      a.lat[g].src = a.lat_lists + lat_off[g][0];
+      a.lat[g].cols = a.lat_lists + lat_off[g][1];
+      a.lat[g].rows = a.lat_lists + lat_off[g][2];
+    }
+  }
   if (!cells.empty()) {
     *err = cudaMalloc(&a.cells, cells.size() * sizeof(int));
     if (*err == cudaSuccess) *err = cudaMalloc(&a.items, items.size() * sizeof(int));
@@ -2587,7 +2622,7 @@ int active_set(ls_batch b, const char* need, cudaError_t* err) {
 // need: per-instance flags (nullptr = every instance); the apply covers only
 // the instances with need != 0.
 template <typename T>
-cudaError_t batch_apply_t(ls_batch b, int prec, const lsd::InstData<T>* dI, const std::vector<lsd::InstData<T>>& hI,
+cudaError_t batch_apply_t(ls_batch b, int prec, const lsd::InstData<T>* dI,
                           const T* u, T* out, cudaStream_t st, const char* need = nullptr) {
   cudaError_t err = cudaSuccess;
   const int si = active_set(b, need, &err);
@@ -2595,8 +2630,8 @@ cudaError_t batch_apply_t(ls_batch b, int prec, const lsd::InstData<T>* dI, cons
   const ActiveSet& a = b->sets[si];
   if (a.ids.empty()) return cudaSuccess;
   auto launch = [&](cudaStream_t s) {
-    return lsd::apply_multi<T>(dI, hI.data(), a.ids.data(), int(a.ids.size()), a.pieces, a.n_pieces, a.cells,
-                               a.n_cells, a.items, a.n_items, b->max_K, u, out, s, b->side.n > 0 ? &b->side : nullptr);
+    return lsd::apply_multi<T>(dI, int(a.ids.size()), a.pieces, a.n_pieces, a.cells, a.n_cells, a.items,
+                               a.n_items, b->max_K, a.lat.data(), int(a.lat.size()), u, out, s);
   };
   return b->graphs.run(GraphCache::Key(prec, si, static_cast<const void*>(u), static_cast<void*>(out)), launch, st);
 }
@@ -2632,26 +2667,11 @@ ls_status ls_batch_create(const ls_plan* plans, int n_plans, ls_batch* out) {
   auto bail = [&](ls_status s) {
     g_create_error = b->err;
     b->release_sets();
-    b->release_side();
     b->free_bufs();
     delete b;
     return s;
   };
   b->plans.assign(plans, plans + n_plans);
-  if (n_plans > 1) {
-    const int w = std::min(n_plans, lsd::SideStreams::kMax);
-    bool ok = cudaEventCreateWithFlags(&b->side.fork, cudaEventDisableTiming) == cudaSuccess;
-    for (int i = 0; i < w && ok; ++i) {
-      ok = cudaStreamCreateWithFlags(&b->side.s[i], cudaStreamNonBlocking) == cudaSuccess &&
-           cudaEventCreateWithFlags(&b->side.join[i], cudaEventDisableTiming) == cudaSuccess;
-      b->side.n = i + 1;
-    }
-    if (!ok) {
-      cudaGetLastError();
-      b->err = "ls_batch_create: stream or event creation failed";
-      return bail(LS_ERR_CUDA);
-    }
-  }
   b->off.push_back(0);
   for (int i = 0; i < n_plans; ++i) {
     const ls_plan p = plans[i];
@@ -2717,9 +2737,9 @@ ls_status ls_batch_apply(ls_batch b, const void* u, void* Au, ls_precision prec,
   if (!u || !Au) return fail(b, LS_ERR_INVALID, "ls_batch_apply: bad arguments");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (prec == LS_FP64)
-    LS_CU(batch_apply_t(b, prec, b->d64, b->h64, static_cast<const double2*>(u), static_cast<double2*>(Au), st));
+    LS_CU(batch_apply_t(b, prec, b->d64, static_cast<const double2*>(u), static_cast<double2*>(Au), st));
   else if (prec == LS_MIXED)
-    LS_CU(batch_apply_t(b, prec, b->d32, b->h32, static_cast<const float2*>(u), static_cast<float2*>(Au), st));
+    LS_CU(batch_apply_t(b, prec, b->d32, static_cast<const float2*>(u), static_cast<float2*>(Au), st));
   else
     return fail(b, LS_ERR_INVALID, "ls_batch_apply: bad precision");
   return LS_OK;
@@ -2738,16 +2758,16 @@ ls_status ls_batch_solve(ls_batch b, const void* uinc, void* u, double tol, int 
   ls_status s = ensure_krylov(b, b->K, restart, lay);
   if (s != LS_OK) return s;
   auto op64 = [&](const double2* v, double2* Av, const char* need) -> cudaError_t {
-    return batch_apply_t(b, LS_FP64, b->d64, b->h64, v, Av, st, need);
+    return batch_apply_t(b, LS_FP64, b->d64, v, Av, st, need);
   };
   auto op32 = [&](const double2* v, double2* Av, const char* need) -> cudaError_t {
     cudaError_t e = lsd::to_c64(v, b->K.c64a, lay.total, st);
-    if (e == cudaSuccess) e = batch_apply_t(b, LS_MIXED, b->d32, b->h32, b->K.c64a, b->K.c64b, st, need);
+    if (e == cudaSuccess) e = batch_apply_t(b, LS_MIXED, b->d32, b->K.c64a, b->K.c64b, st, need);
     if (e == cudaSuccess) e = lsd::to_c128(b->K.c64b, Av, lay.total, st);
     return e;
   };
   auto op32f = [&](const float2* v, float2* Av, const char* need) -> cudaError_t {
-    return batch_apply_t(b, LS_MIXED, b->d32, b->h32, v, Av, st, need);
+    return batch_apply_t(b, LS_MIXED, b->d32, v, Av, st, need);
   };
   SolveStats S;
   s = solve_lockstep(b, b->K, lay, op64, op32, op32f, prec, static_cast<const double2*>(uinc), static_cast<double2*>(u), tol,
@@ -2777,7 +2797,6 @@ ls_status ls_batch_destroy(ls_batch b) {
   b->K.free_pinned();
   b->graphs.release();
   b->release_sets();
-  b->release_side();
   b->free_bufs();
   delete b;
   return LS_OK;

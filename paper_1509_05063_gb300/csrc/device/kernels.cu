@@ -344,17 +344,13 @@ struct LatFft<double2> {
 //                quarter using the even / odd symmetry of the tables), inverse
 //                FFT along a, keep a < n_lat            -> Vt[a][b], n_lat x M
 //  k_inv_rows  : inverse FFT along b of rows a < n_lat, keep b < n_lat -> V
+// face row k of one right-hand side (sigma and R of that RHS), kind 0 monopole / 1 dipole
 template <typename T>
-__global__ void __launch_bounds__(kFftMaxM / LatFft<T>::kDiv) k_src_rows(int M, int logM, int n_lat, int Ne, int L,
-                                                            const int* __restrict__ occ_of_cell,
-                                                            const T* __restrict__ sigma_all, int n_es, int nocc,
-                                                            const T* __restrict__ tw, T* __restrict__ R_all,
-                                                            int64_t stride) {
+__device__ __forceinline__ void src_row_body(int M, int logM, int n_lat, int Ne, int L,
+                                             const int* __restrict__ occ_of_cell, const T* __restrict__ sigma,
+                                             int n_es, const T* __restrict__ tw, T* __restrict__ R, int k, int kind) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* s = reinterpret_cast<T*>(smem_raw);       // LatFft<T> layout
-  const int k = blockIdx.x, kind = blockIdx.y;   // face row, 0 monopole / 1 dipole
-  const T* sigma = sigma_all + int64_t(blockIdx.z) * nocc * n_es;
-  T* R = R_all + int64_t(blockIdx.z) * stride;
   for (int b = threadIdx.x; b < M; b += blockDim.x) {
     T v = czero(T{});
     if (b < n_lat) {
@@ -380,24 +376,31 @@ __global__ void __launch_bounds__(kFftMaxM / LatFft<T>::kDiv) k_src_rows(int M, 
   for (int b = threadIdx.x; b < M; b += blockDim.x) out[b] = s[LatFft<T>::at(b)];
 }
 
+template <typename T>
+__global__ void __launch_bounds__(kFftMaxM / LatFft<T>::kDiv) k_src_rows(int M, int logM, int n_lat, int Ne, int L,
+                                                            const int* __restrict__ occ_of_cell,
+                                                            const T* __restrict__ sigma_all, int n_es, int nocc,
+                                                            const T* __restrict__ tw, T* __restrict__ R_all,
+                                                            int64_t stride) {
+  src_row_body<T>(M, logM, n_lat, Ne, L, occ_of_cell, sigma_all + int64_t(blockIdx.z) * nocc * n_es, n_es, tw,
+                  R_all + int64_t(blockIdx.z) * stride, blockIdx.x, blockIdx.y);
+}
+
 // spectra quarter layout: Q[l][k] for l, k in [0, M/2] (k fastest).
 // The sources of a column sit only at a = k Ne (k = 0..L), so when Ne divides M
 // the length-M forward transform is a length-M/Ne transform of the L + 1 values
 // repeated Ne times: X[f] = Y[f mod (M/Ne)].  Ms = M/Ne (0: use the full
 // length), logMs its log2.
+// columns b0 .. b0 + TC - 1 of one right-hand side (R and Vt of that RHS)
 template <typename T>
-__global__ void __launch_bounds__(LatFft<T>::kColThreads) k_conv_cols(int M, int logM, int n_lat, int Ne, int L, int TC, int Ms,
-                                                    int logMs, const T* __restrict__ R_all,
-                                                    const T* __restrict__ Gq, const T* __restrict__ Dq,
-                                                    const T* __restrict__ tw, T* __restrict__ Vt_all,
-                                                    int64_t stride) {
+__device__ __forceinline__ void conv_cols_body(int M, int logM, int n_lat, int Ne, int L, int TC, int Ms, int logMs,
+                                               const T* __restrict__ R, const T* __restrict__ Gq,
+                                               const T* __restrict__ Dq, const T* __restrict__ tw,
+                                               T* __restrict__ Vt, int b0) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const T* R = R_all + int64_t(blockIdx.y) * stride;
-  T* Vt = Vt_all + int64_t(blockIdx.y) * stride;
   const int PM = LatFft<T>::len(M);            // one column in the LatFft<T> layout
   T* xm = reinterpret_cast<T*>(smem_raw);      // [TC][PM]
   T* xd = xm + TC * PM;                        // [TC][PM]
-  const int b0 = blockIdx.x * TC;
   const int half = M / 2;
   constexpr int kDiv = LatFft<T>::kDiv;
   const int G = M / kDiv;                      // threads per column
@@ -482,14 +485,21 @@ __global__ void __launch_bounds__(LatFft<T>::kColThreads) k_conv_cols(int M, int
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kFftMaxM / LatFft<T>::kDiv) k_inv_rows(int M, int logM, int n_lat, const T* __restrict__ tw,
-                                                            const T* __restrict__ Vt_all, T* __restrict__ V_all,
-                                                            int64_t stride) {
+__global__ void __launch_bounds__(LatFft<T>::kColThreads) k_conv_cols(int M, int logM, int n_lat, int Ne, int L, int TC, int Ms,
+                                                    int logMs, const T* __restrict__ R_all,
+                                                    const T* __restrict__ Gq, const T* __restrict__ Dq,
+                                                    const T* __restrict__ tw, T* __restrict__ Vt_all,
+                                                    int64_t stride) {
+  conv_cols_body<T>(M, logM, n_lat, Ne, L, TC, Ms, logMs, R_all + int64_t(blockIdx.y) * stride, Gq, Dq, tw,
+                    Vt_all + int64_t(blockIdx.y) * stride, blockIdx.x * TC);
+}
+
+// kept row a of one right-hand side (Vt and V of that RHS)
+template <typename T>
+__device__ __forceinline__ void inv_row_body(int M, int logM, int n_lat, const T* __restrict__ tw,
+                                             const T* __restrict__ Vt, T* __restrict__ V, int64_t a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* s = reinterpret_cast<T*>(smem_raw);       // LatFft<T> layout
-  const T* Vt = Vt_all + int64_t(blockIdx.y) * stride;
-  T* V = V_all + int64_t(blockIdx.y) * stride;
-  const int64_t a = blockIdx.x;
   constexpr int kDiv = LatFft<T>::kDiv;
   T v[kDiv];                                   // M / kDiv threads: kDiv loads each, issued together
 #pragma unroll
@@ -500,6 +510,28 @@ __global__ void __launch_bounds__(kFftMaxM / LatFft<T>::kDiv) k_inv_rows(int M, 
   LatFft<T>::run(s, M, logM, true, tw, threadIdx.x);
   __syncthreads();
   for (int b = threadIdx.x; b < n_lat; b += blockDim.x) V[a * M + b] = s[LatFft<T>::at(b)];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kFftMaxM / LatFft<T>::kDiv) k_inv_rows(int M, int logM, int n_lat, const T* __restrict__ tw,
+                                                            const T* __restrict__ Vt_all, T* __restrict__ V_all,
+                                                            int64_t stride) {
+  inv_row_body<T>(M, logM, n_lat, tw, Vt_all + int64_t(blockIdx.y) * stride, V_all + int64_t(blockIdx.y) * stride,
+                  blockIdx.x);
+}
+
+// Length of the short forward column transforms (0: none, full length): the
+// source rows sit on every Ne-th lattice row, so when Ne divides M the column
+// transform is a length-M/Ne transform repeated; it needs 2 (M/Ne) / 8 threads
+// of the column's M / kDiv.
+template <typename T>
+__host__ __device__ inline int short_len(int M, int Ne, int L, int& logMs) {
+  logMs = 0;
+  if (M % Ne != 0 || L + 1 > M / Ne) return 0;
+  const int m = M / Ne;
+  if (m < 16 || m > 4 * M / LatFft<T>::kDiv || (m & (m - 1)) != 0) return 0;
+  while ((1 << logMs) < m) ++logMs;
+  return m;
 }
 
 // columns per block of the column pass: one, so that the M blocks of M / kDiv
@@ -530,18 +562,61 @@ cudaError_t lattice_conv(const ApplyData<T>& d, int nr, cudaStream_t st) {
   const int64_t stride = d.lattice_rows() * M;
   k_src_rows<T><<<dim3(d.L + 1, 2, nr), M / kDiv, pm, st>>>(M, d.logM, d.n_lat, d.Ne, d.L, d.occ_of_cell,
                                                                      d.sigma, d.n_es, d.nocc, d.tw, d.Sd, stride);
-  // short forward column transforms when the source rows (every Ne-th) fold to length M / Ne
-  int Ms = 0, logMs = 0;
-  if (M % d.Ne == 0 && d.L + 1 <= M / d.Ne) {
-    const int m = M / d.Ne;
-    if (m >= 16 && m <= 4 * M / kDiv && (m & (m - 1)) == 0) {   // 2 m / 8 threads of the column's M / kDiv
-      Ms = m;
-      while ((1 << logMs) < m) ++logMs;
-    }
-  }
+  int logMs = 0;
+  const int Ms = short_len<T>(M, d.Ne, d.L, logMs);
   k_conv_cols<T><<<dim3(M / TC, nr), TC * (M / kDiv), 2 * TC * pm, st>>>(
       M, d.logM, d.n_lat, d.Ne, d.L, TC, Ms, logMs, d.Sd, d.Gq, d.Dq, d.tw, d.Sm, stride);
   k_inv_rows<T><<<dim3(d.n_lat, nr), M / kDiv, pm, st>>>(M, d.logM, d.n_lat, d.tw, d.Sm, d.Sd, stride);
+  return cudaGetLastError();
+}
+
+// The lattice convolutions of several instances of one lattice size at once
+// (one right-hand side each): work lists of (instance, face row), (instance,
+// column) and (instance, kept row); every block runs the same body as the
+// single-instance kernels on its instance's arrays, so each instance's result
+// is the single apply's bit for bit.
+template <typename T>
+__global__ void __launch_bounds__(kFftMaxM / LatFft<T>::kDiv) k_src_rows_multi(const int2* __restrict__ work,
+                                                                              const InstData<T>* __restrict__ I) {
+  const int2 w = work[blockIdx.x];
+  const ApplyData<T>& d = I[w.x].d;
+  src_row_body<T>(d.M, d.logM, d.n_lat, d.Ne, d.L, d.occ_of_cell, d.sigma, d.n_es, d.tw, d.Sd, w.y, blockIdx.y);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kFftMaxM / LatFft<T>::kDiv) k_conv_cols_multi(const int2* __restrict__ work,
+                                                                               const InstData<T>* __restrict__ I) {
+  const int2 w = work[blockIdx.x];
+  const ApplyData<T>& d = I[w.x].d;
+  int logMs = 0;
+  const int Ms = short_len<T>(d.M, d.Ne, d.L, logMs);
+  conv_cols_body<T>(d.M, d.logM, d.n_lat, d.Ne, d.L, 1, Ms, logMs, d.Sd, d.Gq, d.Dq, d.tw, d.Sm, w.y);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kFftMaxM / LatFft<T>::kDiv) k_inv_rows_multi(const int2* __restrict__ work,
+                                                                              const InstData<T>* __restrict__ I) {
+  const int2 w = work[blockIdx.x];
+  const ApplyData<T>& d = I[w.x].d;
+  inv_row_body<T>(d.M, d.logM, d.n_lat, d.tw, d.Sm, d.Sd, w.y);
+}
+
+template <typename T>
+cudaError_t lattice_conv_multi(const InstData<T>* I, const LatWork& w, cudaStream_t st) {
+  const int M = w.M;
+  if (M < 256 || M > kFftMaxM || (M & (M - 1))) return cudaErrorInvalidValue;
+  constexpr int kDiv = LatFft<T>::kDiv;
+  const size_t pm = size_t(LatFft<T>::len(M)) * sizeof(T);
+  static unsigned long long attr_done = 0;
+  if (first_on_device(attr_done)) {
+    const int prow = int(LatFft<T>::len(kFftMaxM) * sizeof(T));
+    cudaFuncSetAttribute(k_src_rows_multi<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, prow);
+    cudaFuncSetAttribute(k_conv_cols_multi<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * prow);
+    cudaFuncSetAttribute(k_inv_rows_multi<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, prow);
+  }
+  if (w.n_src > 0) k_src_rows_multi<T><<<dim3(w.n_src, 2), M / kDiv, pm, st>>>(w.src, I);
+  if (w.n_cols > 0) k_conv_cols_multi<T><<<w.n_cols, M / kDiv, 2 * pm, st>>>(w.cols, I);
+  if (w.n_rows > 0) k_inv_rows_multi<T><<<w.n_rows, M / kDiv, pm, st>>>(w.rows, I);
   return cudaGetLastError();
 }
 
@@ -985,8 +1060,11 @@ __global__ void __launch_bounds__(256) k_local_coeffs_multi(const int2* __restri
                           d.n_es, d.nfb2, d.gamma, d.lattice_rows() * d.M);
 }
 
+// five blocks per SM, as the single-instance kernels: the instance's fields
+// come from memory here, and at 52 registers the kernel fit only four blocks
+// and streamed the weights at 63% of HBM
 template <typename T>
-__global__ void __launch_bounds__(256) k_near_eval_multi(const int4* __restrict__ items,
+__global__ void __launch_bounds__(256, 5) k_near_eval_multi(const int4* __restrict__ items,
                                                          const InstData<T>* __restrict__ I, const T* __restrict__ u,
                                                          T* __restrict__ out) {
   const int4 it = items[blockIdx.x];
@@ -998,26 +1076,15 @@ __global__ void __launch_bounds__(256) k_near_eval_multi(const int4* __restrict_
 }
 
 template <typename T>
-cudaError_t apply_multi(const InstData<T>* dev_inst, const InstData<T>* host_inst, const int* ids, int n_ids,
+cudaError_t apply_multi(const InstData<T>* dev_inst, int n_ids,
                         const int2* pieces, int n_pieces, const int2* cells, int n_cells, const int4* items,
-                        int n_items, int max_K, const T* u, T* out, cudaStream_t st, const SideStreams* side) {
+                        int n_items, int max_K, const LatWork* lat, int n_lat_groups, const T* u, T* out,
+                        cudaStream_t st) {
   if (n_ids <= 0 || n_pieces <= 0 || n_cells <= 0 || n_items <= 0) return cudaSuccess;
   k_es_project_multi<T><<<n_pieces, 256, contraction_smem<T>(1, kProjStage), st>>>(pieces, dev_inst, u);
-  if (side && side->n > 0 && n_ids > 1) {
-    const int w = side->n < n_ids ? side->n : n_ids;
-    cudaError_t e = cudaEventRecord(side->fork, st);
-    for (int i = 0; i < w && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(side->s[i], side->fork, 0);
-    for (int j = 0; j < n_ids && e == cudaSuccess; ++j) e = lattice_conv(host_inst[ids[j]].d, 1, side->s[j % w]);
-    for (int i = 0; i < w && e == cudaSuccess; ++i) {
-      e = cudaEventRecord(side->join[i], side->s[i]);
-      if (e == cudaSuccess) e = cudaStreamWaitEvent(st, side->join[i], 0);
-    }
+  for (int g = 0; g < n_lat_groups; ++g) {
+    const cudaError_t e = lattice_conv_multi(dev_inst, lat[g], st);
     if (e != cudaSuccess) return e;
-  } else {
-    for (int j = 0; j < n_ids; ++j) {
-      cudaError_t e = lattice_conv(host_inst[ids[j]].d, 1, st);
-      if (e != cudaSuccess) return e;
-    }
   }
   const size_t sm_local = local_smem<T>(1, max_K);
   static unsigned long long attr = 0;
@@ -1030,12 +1097,12 @@ cudaError_t apply_multi(const InstData<T>* dev_inst, const InstData<T>* host_ins
   return cudaGetLastError();
 }
 
-template cudaError_t apply_multi<double2>(const InstData<double2>*, const InstData<double2>*, const int*, int,
-                                          const int2*, int, const int2*, int, const int4*, int, int, const double2*,
-                                          double2*, cudaStream_t, const SideStreams*);
-template cudaError_t apply_multi<float2>(const InstData<float2>*, const InstData<float2>*, const int*, int,
-                                         const int2*, int, const int2*, int, const int4*, int, int, const float2*,
-                                         float2*, cudaStream_t, const SideStreams*);
+template cudaError_t apply_multi<double2>(const InstData<double2>*, int,
+                                          const int2*, int, const int2*, int, const int4*, int, int, const LatWork*,
+                                          int, const double2*, double2*, cudaStream_t);
+template cudaError_t apply_multi<float2>(const InstData<float2>*, int,
+                                         const int2*, int, const int2*, int, const int4*, int, int, const LatWork*,
+                                         int, const float2*, float2*, cudaStream_t);
 
 template <typename T>
 cudaError_t apply_batch(const ApplyData<T>& d, const T* u, T* out, int nr, cudaStream_t st, cudaEvent_t* ev) {

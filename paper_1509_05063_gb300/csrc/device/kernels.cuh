@@ -214,30 +214,35 @@ struct InstData {
   int64_t off = 0;
 };
 
-// out = A_i u_i for the instances ids[0..n_ids) of a batch at once (one
+// The lattice convolutions of a batch's instances whose lattice size is M, as
+// three launches over work lists: src = (instance, face row k <= L), cols =
+// (instance, column b < M), rows = (instance, kept row a < n_lat).
+struct LatWork {
+  int M = 0;
+  const int2* src = nullptr;
+  int n_src = 0;
+  const int2* cols = nullptr;
+  int n_cols = 0;
+  const int2* rows = nullptr;
+  int n_rows = 0;
+};
+
+// out = A_i u_i for the n_ids active instances of a batch at once (one
 // right-hand side each; u, out: the concatenated vectors; the other instances'
 // parts of out are left untouched).  The projection, the local expansion and
 // the near field each run as ONE launch walking work lists over those
 // instances -- pieces = (instance, projection piece of the instance), cells =
 // (instance, occupied cell), items = (instance, occupied cell, first of 16
-// rows, unused) -- and the lattice convolution runs per instance (its size
-// differs).  dev_inst is a device copy of host_inst; ids is a host array; max_K
-// is the largest n_loc + 9 n_es.  No plan may appear twice among the instances
-// (they would share its work arrays).
-// side (may be NULL): streams on which the instances' lattice convolutions run
-// side by side (each is a few small launches that leave most SMs idle), forked
-// from and joined back into st by events (also under stream capture).
-struct SideStreams {
-  static constexpr int kMax = 4;
-  cudaStream_t s[kMax] = {};
-  cudaEvent_t fork = nullptr, join[kMax] = {};
-  int n = 0;
-};
+// rows, unused) -- and the lattice convolution as three launches per lattice
+// size (lat[0..n_lat_groups), covering the same instances).  dev_inst: the
+// batch's instance table on the device; max_K is the largest n_loc + 9 n_es.
+// No plan may appear twice among the instances (they would share its work
+// arrays).
 template <typename T>
-cudaError_t apply_multi(const InstData<T>* dev_inst, const InstData<T>* host_inst, const int* ids, int n_ids,
+cudaError_t apply_multi(const InstData<T>* dev_inst, int n_ids,
                         const int2* pieces, int n_pieces, const int2* cells, int n_cells, const int4* items,
-                        int n_items, int max_K, const T* u, T* out, cudaStream_t st,
-                        const SideStreams* side = nullptr);
+                        int n_items, int max_K, const LatWork* lat, int n_lat_groups, const T* u, T* out,
+                        cudaStream_t st);
 
 // 2-D FFT of an M x M array in place (rows then columns), forward or inverse
 // (unscaled).
