@@ -1042,8 +1042,17 @@ cudaError_t apply_r(const ApplyData<T>& d, const T* u, T* out, cudaStream_t st, 
 // ------------------------------------------------------------ multi-instance batch
 // work = (instance, projection piece of that instance): the same pieces as the
 // single-instance apply, so every instance sums as it does alone
+// blocks per SM the multi-instance projection and local step are compiled for:
+// reading the instance's fields from memory costs registers (48 against 32 in
+// the single-instance kernels); these caps keep the complex64 kernels near the
+// single-instance occupancy with at most 8 bytes spilled (the FP64 projection
+// keeps four blocks: at six it would spill 80 bytes)
 template <typename T>
-__global__ void __launch_bounds__(256) k_es_project_multi(const int2* __restrict__ work,
+constexpr int kProjMultiBlocks = sizeof(T) == 8 ? 6 : 4;
+constexpr int kLocalMultiBlocks = 7;
+
+template <typename T>
+__global__ void __launch_bounds__(256, kProjMultiBlocks<T>) k_es_project_multi(const int2* __restrict__ work,
                                                           const InstData<T>* __restrict__ I, const T* __restrict__ u) {
   const int2 w = work[blockIdx.x];
   const ApplyData<T>& d = I[w.x].d;
@@ -1052,7 +1061,7 @@ __global__ void __launch_bounds__(256) k_es_project_multi(const int2* __restrict
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_local_coeffs_multi(const int2* __restrict__ cells,
+__global__ void __launch_bounds__(256, kLocalMultiBlocks) k_local_coeffs_multi(const int2* __restrict__ cells,
                                                             const InstData<T>* __restrict__ I) {
   const int2 c = cells[blockIdx.x];
   const ApplyData<T>& d = I[c.x].d;
