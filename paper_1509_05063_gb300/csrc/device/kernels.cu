@@ -312,7 +312,8 @@ struct LatFft;
 template <>
 struct LatFft<float2> {
   static constexpr int kDiv = 16;              // values per thread and transform
-  static constexpr int kColThreads = 512;      // launch bound of the column pass
+  static constexpr int kColThreads = 256;      // launch bound of the column pass (at most 4 columns at M = 1024)
+  static constexpr int kColBlocks = 3;         // 80 registers: 3 blocks of 256 per SM instead of 2 at 128
   __host__ __device__ static constexpr int len(int N) { return fft16_len(N); }
   __device__ static int at(int i) { return fpad(i); }
   __device__ static void run(float2* x, int N, int logN, bool inv, const float2* tw, int t) {
@@ -324,6 +325,7 @@ template <>
 struct LatFft<double2> {
   static constexpr int kDiv = 8;
   static constexpr int kColThreads = 1024;
+  static constexpr int kColBlocks = 1;
   __host__ __device__ static constexpr int len(int N) { return N; }
   __device__ static int at(int i) { return i; }
   __device__ static void run(double2* x, int N, int logN, bool inv, const double2* tw, int t) {
@@ -485,7 +487,7 @@ __device__ __forceinline__ void conv_cols_body(int M, int logM, int n_lat, int N
 }
 
 template <typename T>
-__global__ void __launch_bounds__(LatFft<T>::kColThreads) k_conv_cols(int M, int logM, int n_lat, int Ne, int L, int TC, int Ms,
+__global__ void __launch_bounds__(LatFft<T>::kColThreads, LatFft<T>::kColBlocks) k_conv_cols(int M, int logM, int n_lat, int Ne, int L, int TC, int Ms,
                                                     int logMs, const T* __restrict__ R_all,
                                                     const T* __restrict__ Gq, const T* __restrict__ Dq,
                                                     const T* __restrict__ tw, T* __restrict__ Vt_all,
