@@ -294,7 +294,9 @@ ls_status ls_measure_peaks(double* fp64_tflops, double* tf32_tflops);
  *     group per near-field launch (16, 8 or 4) and, for groups of 8 or more,
  *     tensor cores or CUDA cores for each of the near field (split FP16), the
  *     local-expansion coefficients and the equivalent-source projection
- *     (3xTF32).
+ *     (3xTF32);
+ *   - then, for the chosen variants, the radix of the complex64 lattice
+ *     transforms: 16 (two radix-16 passes and one of radix M / 256) or 4.
  * The plan's device must be current (LS_ERR_INVALID otherwise); 3-D plans
  * return LS_ERR_UNSUPPORTED; nrhs in [1, 64].  Blocking; drops the plan's
  * captured applies.  report (host, may be NULL) receives the choice and the
@@ -307,6 +309,7 @@ typedef struct {
   int n_candidates;             /* variants timed */
   int local_cuda32;             /* 1: CUDA-core complex64 local coefficients for groups >= 8; 0: tensor cores */
   int proj_cuda32;              /* 1: CUDA-core complex64 projection for groups >= 8; 0: tensor cores */
+  int fft_radix32;              /* radix of the complex64 lattice transforms: 16 or 4 */
   double ms64_default, ms64_best;
   double ms32_default, ms32_best;
 } ls_tune_report;
@@ -314,8 +317,10 @@ ls_status ls_plan_autotune(ls_plan plan, int nrhs, ls_tune_report* report);
 
 /* Sets the kernel variants of a 2-D plan from a report (host, read only):
  * conv_cols64 and conv_cols32 in {1, 2, 4, 8}, group32 in {4, 8, 16},
- * near_cuda32, local_cuda32 and proj_cuda32 in {0, 1}; the other fields are
- * ignored.  It re-applies a choice ls_plan_autotune made earlier (for
+ * near_cuda32, local_cuda32 and proj_cuda32 in {0, 1}, fft_radix32 in
+ * {4, 16} (0: 16); the other fields are ignored.  The radix applies to the
+ * plan's own applies (a batch's multi-instance lattice passes use radix 16).
+ * It re-applies a choice ls_plan_autotune made earlier (for
  * instance in another process on the same kind of GPU) and pins variants for
  * tests.  Every variant gives the same result up to rounding.  A plan whose
  * tables do not fit a tensor-core unit (2 n_fb + 1 > 32 for the local

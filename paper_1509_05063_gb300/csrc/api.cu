@@ -2316,6 +2316,29 @@ ls_status ls_plan_autotune(ls_plan plan, int nrhs, ls_tune_report* report) {
     r.local_cuda32 = plan->d32.local_cuda ? 1 : 0;
     r.proj_cuda32 = plan->d32.proj_cuda ? 1 : 0;
     r.ms32_best = best;
+    // the lattice FFT's radix (16 or 4) for the chosen variants, on the same applies
+    if (best > 0) {
+      const bool keep_r4 = plan->d32.fft_r4;
+      double ms_r[2] = {-1, -1};
+      for (int r4 = 0; r4 < 2; ++r4) {
+        plan->d32.fft_r4 = r4 != 0;
+        ms_r[r4] = timed([&] {
+          for (int q = 0; q < nrhs;) {
+            int nr = plan->group32;
+            while (nr > nrhs - q) nr /= 2;
+            const cudaError_t e = lsd::apply_batch(plan->d32, u32 + int64_t(q) * N, o32 + int64_t(q) * N, nr, ts);
+            if (e != cudaSuccess) return e;
+            q += nr;
+          }
+          return cudaSuccess;
+        });
+        cudaGetLastError();
+        ++r.n_candidates;
+      }
+      plan->d32.fft_r4 = (ms_r[0] > 0 && ms_r[1] > 0) ? ms_r[1] < ms_r[0] : keep_r4;
+      if (ms_r[0] > 0 && ms_r[1] > 0) r.ms32_best = std::min(ms_r[0], ms_r[1]);
+    }
+    r.fft_radix32 = plan->d32.fft_r4 ? 4 : 16;
     ce = cudaStreamSynchronize(ts);
   }
   cleanup();
@@ -2339,15 +2362,17 @@ ls_status ls_plan_set_variants(ls_plan plan, const ls_tune_report* v) {
   auto flag_ok = [](int f) { return f == 0 || f == 1; };
   if (!cols_ok(v->conv_cols64) || !cols_ok(v->conv_cols32) ||
       (v->group32 != 4 && v->group32 != 8 && v->group32 != 16) || !flag_ok(v->near_cuda32) ||
-      !flag_ok(v->local_cuda32) || !flag_ok(v->proj_cuda32))
+      !flag_ok(v->local_cuda32) || !flag_ok(v->proj_cuda32) ||
+      (v->fft_radix32 != 0 && v->fft_radix32 != 4 && v->fft_radix32 != 16))
     return fail(plan, LS_ERR_INVALID, "ls_plan_set_variants: columns must be 1, 2, 4 or 8, the group 4, 8 or 16, "
-                                      "the unit flags 0 or 1");
+                                      "the unit flags 0 or 1, the FFT radix 4 or 16");
   plan->d64.conv_tc = v->conv_cols64;
   plan->d32.conv_tc = v->conv_cols32;
   plan->group32 = v->group32;
   plan->d32.near_cuda = v->near_cuda32 != 0;
   plan->d32.local_cuda = v->local_cuda32 != 0;
   plan->d32.proj_cuda = v->proj_cuda32 != 0;
+  plan->d32.fft_r4 = v->fft_radix32 == 4;
   plan->graphs.clear();          // captured applies hold the previous variants
   return LS_OK;
 }

@@ -321,17 +321,21 @@ struct LatFft<float2> {
     fft16_smem<float2>(x, N, inv, tw, t);
   }
 };
-template <>
-struct LatFft<double2> {
+// The radix-4 transform for either precision (complex64: the autotuner's
+// alternative to radix 16, ApplyData::fft_r4).
+template <typename T>
+struct LatFft4 {
   static constexpr int kDiv = 8;
   static constexpr int kColThreads = 1024;
   static constexpr int kColBlocks = 1;
   __host__ __device__ static constexpr int len(int N) { return N; }
   __device__ static int at(int i) { return i; }
-  __device__ static void run(double2* x, int N, int logN, bool inv, const double2* tw, int t) {
-    fft_smem<double2>(x, N, logN, inv, tw, t);
+  __device__ static void run(T* x, int N, int logN, bool inv, const T* tw, int t) {
+    fft_smem<T>(x, N, logN, inv, tw, t);
   }
 };
+template <>
+struct LatFft<double2> : LatFft4<double2> {};
 
 // ------------------------------------------------------------ pruned, fused lattice convolution
 // Sources live only on the L + 1 face rows a = k Ne (k = 0..L) of the M x M
@@ -347,12 +351,12 @@ struct LatFft<double2> {
 //                FFT along a, keep a < n_lat            -> Vt[a][b], n_lat x M
 //  k_inv_rows  : inverse FFT along b of rows a < n_lat, keep b < n_lat -> V
 // face row k of one right-hand side (sigma and R of that RHS), kind 0 monopole / 1 dipole
-template <typename T>
+template <typename T, class F>
 __device__ __forceinline__ void src_row_body(int M, int logM, int n_lat, int Ne, int L,
                                              const int* __restrict__ occ_of_cell, const T* __restrict__ sigma,
                                              int n_es, const T* __restrict__ tw, T* __restrict__ R, int k, int kind) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* s = reinterpret_cast<T*>(smem_raw);       // LatFft<T> layout
+  T* s = reinterpret_cast<T*>(smem_raw);       // F layout
   for (int b = threadIdx.x; b < M; b += blockDim.x) {
     T v = czero(T{});
     if (b < n_lat) {
@@ -369,22 +373,22 @@ __device__ __forceinline__ void src_row_body(int M, int logM, int n_lat, int Ne,
         }
       }
     }
-    s[LatFft<T>::at(b)] = v;
+    s[F::at(b)] = v;
   }
   __syncthreads();
-  LatFft<T>::run(s, M, logM, false, tw, threadIdx.x);
+  F::run(s, M, logM, false, tw, threadIdx.x);
   __syncthreads();
   T* out = R + (int64_t(kind) * (L + 1) + k) * M;
-  for (int b = threadIdx.x; b < M; b += blockDim.x) out[b] = s[LatFft<T>::at(b)];
+  for (int b = threadIdx.x; b < M; b += blockDim.x) out[b] = s[F::at(b)];
 }
 
-template <typename T>
-__global__ void __launch_bounds__(kFftMaxM / LatFft<T>::kDiv) k_src_rows(int M, int logM, int n_lat, int Ne, int L,
+template <typename T, class F = LatFft<T>>
+__global__ void __launch_bounds__(kFftMaxM / F::kDiv) k_src_rows(int M, int logM, int n_lat, int Ne, int L,
                                                             const int* __restrict__ occ_of_cell,
                                                             const T* __restrict__ sigma_all, int n_es, int nocc,
                                                             const T* __restrict__ tw, T* __restrict__ R_all,
                                                             int64_t stride) {
-  src_row_body<T>(M, logM, n_lat, Ne, L, occ_of_cell, sigma_all + int64_t(blockIdx.z) * nocc * n_es, n_es, tw,
+  src_row_body<T, F>(M, logM, n_lat, Ne, L, occ_of_cell, sigma_all + int64_t(blockIdx.z) * nocc * n_es, n_es, tw,
                   R_all + int64_t(blockIdx.z) * stride, blockIdx.x, blockIdx.y);
 }
 
@@ -394,17 +398,17 @@ __global__ void __launch_bounds__(kFftMaxM / LatFft<T>::kDiv) k_src_rows(int M, 
 // repeated Ne times: X[f] = Y[f mod (M/Ne)].  Ms = M/Ne (0: use the full
 // length), logMs its log2.
 // columns b0 .. b0 + TC - 1 of one right-hand side (R and Vt of that RHS)
-template <typename T>
+template <typename T, class F>
 __device__ __forceinline__ void conv_cols_body(int M, int logM, int n_lat, int Ne, int L, int TC, int Ms, int logMs,
                                                const T* __restrict__ R, const T* __restrict__ Gq,
                                                const T* __restrict__ Dq, const T* __restrict__ tw,
                                                T* __restrict__ Vt, int b0) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int PM = LatFft<T>::len(M);            // one column in the LatFft<T> layout
+  const int PM = F::len(M);            // one column in the F layout
   T* xm = reinterpret_cast<T*>(smem_raw);      // [TC][PM]
   T* xd = xm + TC * PM;                        // [TC][PM]
   const int half = M / 2;
-  constexpr int kDiv = LatFft<T>::kDiv;
+  constexpr int kDiv = F::kDiv;
   const int G = M / kDiv;                      // threads per column
   const int c = threadIdx.x / G, t = threadIdx.x % G;
   // the spectral product of column element e (column e >> logM, row e & (M - 1)):
@@ -427,7 +431,7 @@ __device__ __forceinline__ void conv_cols_body(int M, int logM, int n_lat, int N
         const T d = a > half ? mk(-dq[q].x, -dq[q].y) : dq[q];
         T vm, vd;
         value_of(cc, a, vm, vd);
-        xm[cc * PM + LatFft<T>::at(a)] = cfma(vd, d, cmul(vm, gq[q]));
+        xm[cc * PM + F::at(a)] = cfma(vd, d, cmul(vm, gq[q]));
       }
     }
   };
@@ -464,61 +468,61 @@ __device__ __forceinline__ void conv_cols_body(int M, int logM, int n_lat, int N
         vm = R[int64_t(k) * M + b0 + cc];
         vd = R[(int64_t(L + 1) + k) * M + b0 + cc];
       }
-      xm[cc * PM + LatFft<T>::at(a)] = vm;
-      xd[cc * PM + LatFft<T>::at(a)] = vd;
+      xm[cc * PM + F::at(a)] = vm;
+      xd[cc * PM + F::at(a)] = vd;
     }
     __syncthreads();
-    LatFft<T>::run(xm + c * PM, M, logM, false, tw, t);
+    F::run(xm + c * PM, M, logM, false, tw, t);
     __syncthreads();
-    LatFft<T>::run(xd + c * PM, M, logM, false, tw, t);
+    F::run(xd + c * PM, M, logM, false, tw, t);
     __syncthreads();
     product([&](int cc, int a, T& vm, T& vd) {
-      vm = xm[cc * PM + LatFft<T>::at(a)];
-      vd = xd[cc * PM + LatFft<T>::at(a)];
+      vm = xm[cc * PM + F::at(a)];
+      vd = xd[cc * PM + F::at(a)];
     });
     __syncthreads();
   }
-  LatFft<T>::run(xm + c * PM, M, logM, true, tw, t);
+  F::run(xm + c * PM, M, logM, true, tw, t);
   __syncthreads();
   for (int e = threadIdx.x; e < TC * n_lat; e += blockDim.x) {
     const int a = e / TC, cc = e % TC;
-    Vt[int64_t(a) * M + b0 + cc] = xm[cc * PM + LatFft<T>::at(a)];
+    Vt[int64_t(a) * M + b0 + cc] = xm[cc * PM + F::at(a)];
   }
 }
 
-template <typename T>
-__global__ void __launch_bounds__(LatFft<T>::kColThreads, LatFft<T>::kColBlocks) k_conv_cols(int M, int logM, int n_lat, int Ne, int L, int TC, int Ms,
+template <typename T, class F = LatFft<T>>
+__global__ void __launch_bounds__(F::kColThreads, F::kColBlocks) k_conv_cols(int M, int logM, int n_lat, int Ne, int L, int TC, int Ms,
                                                     int logMs, const T* __restrict__ R_all,
                                                     const T* __restrict__ Gq, const T* __restrict__ Dq,
                                                     const T* __restrict__ tw, T* __restrict__ Vt_all,
                                                     int64_t stride) {
-  conv_cols_body<T>(M, logM, n_lat, Ne, L, TC, Ms, logMs, R_all + int64_t(blockIdx.y) * stride, Gq, Dq, tw,
+  conv_cols_body<T, F>(M, logM, n_lat, Ne, L, TC, Ms, logMs, R_all + int64_t(blockIdx.y) * stride, Gq, Dq, tw,
                     Vt_all + int64_t(blockIdx.y) * stride, blockIdx.x * TC);
 }
 
 // kept row a of one right-hand side (Vt and V of that RHS)
-template <typename T>
+template <typename T, class F>
 __device__ __forceinline__ void inv_row_body(int M, int logM, int n_lat, const T* __restrict__ tw,
                                              const T* __restrict__ Vt, T* __restrict__ V, int64_t a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* s = reinterpret_cast<T*>(smem_raw);       // LatFft<T> layout
-  constexpr int kDiv = LatFft<T>::kDiv;
+  T* s = reinterpret_cast<T*>(smem_raw);       // F layout
+  constexpr int kDiv = F::kDiv;
   T v[kDiv];                                   // M / kDiv threads: kDiv loads each, issued together
 #pragma unroll
   for (int q = 0; q < kDiv; ++q) v[q] = Vt[a * M + threadIdx.x + q * blockDim.x];
 #pragma unroll
-  for (int q = 0; q < kDiv; ++q) s[LatFft<T>::at(threadIdx.x + q * blockDim.x)] = v[q];
+  for (int q = 0; q < kDiv; ++q) s[F::at(threadIdx.x + q * blockDim.x)] = v[q];
   __syncthreads();
-  LatFft<T>::run(s, M, logM, true, tw, threadIdx.x);
+  F::run(s, M, logM, true, tw, threadIdx.x);
   __syncthreads();
-  for (int b = threadIdx.x; b < n_lat; b += blockDim.x) V[a * M + b] = s[LatFft<T>::at(b)];
+  for (int b = threadIdx.x; b < n_lat; b += blockDim.x) V[a * M + b] = s[F::at(b)];
 }
 
-template <typename T>
-__global__ void __launch_bounds__(kFftMaxM / LatFft<T>::kDiv) k_inv_rows(int M, int logM, int n_lat, const T* __restrict__ tw,
+template <typename T, class F = LatFft<T>>
+__global__ void __launch_bounds__(kFftMaxM / F::kDiv) k_inv_rows(int M, int logM, int n_lat, const T* __restrict__ tw,
                                                             const T* __restrict__ Vt_all, T* __restrict__ V_all,
                                                             int64_t stride) {
-  inv_row_body<T>(M, logM, n_lat, tw, Vt_all + int64_t(blockIdx.y) * stride, V_all + int64_t(blockIdx.y) * stride,
+  inv_row_body<T, F>(M, logM, n_lat, tw, Vt_all + int64_t(blockIdx.y) * stride, V_all + int64_t(blockIdx.y) * stride,
                   blockIdx.x);
 }
 
@@ -526,12 +530,11 @@ __global__ void __launch_bounds__(kFftMaxM / LatFft<T>::kDiv) k_inv_rows(int M, 
 // source rows sit on every Ne-th lattice row, so when Ne divides M the column
 // transform is a length-M/Ne transform repeated; it needs 2 (M/Ne) / 8 threads
 // of the column's M / kDiv.
-template <typename T>
-__host__ __device__ inline int short_len(int M, int Ne, int L, int& logMs) {
+__host__ __device__ inline int short_len(int M, int Ne, int L, int kDiv, int& logMs) {
   logMs = 0;
   if (M % Ne != 0 || L + 1 > M / Ne) return 0;
   const int m = M / Ne;
-  if (m < 16 || m > 4 * M / LatFft<T>::kDiv || (m & (m - 1)) != 0) return 0;
+  if (m < 16 || m > 4 * M / kDiv || (m & (m - 1)) != 0) return 0;
   while ((1 << logMs) < m) ++logMs;
   return m;
 }
@@ -544,32 +547,40 @@ int conv_cols_tc(int) {
   return 1;
 }
 
-template <typename T>
-cudaError_t lattice_conv(const ApplyData<T>& d, int nr, cudaStream_t st) {
+template <typename T, class F>
+cudaError_t lattice_conv_f(const ApplyData<T>& d, int nr, cudaStream_t st) {
   const int M = d.M;
   if (M < 256 || M > kFftMaxM || (M & (M - 1))) return cudaErrorInvalidValue;
   const int TC = d.conv_tc > 0 ? d.conv_tc : conv_cols_tc<T>(M);
-  constexpr int kDiv = LatFft<T>::kDiv;
-  const size_t pm = size_t(LatFft<T>::len(M)) * sizeof(T);   // one column or row in the LatFft<T> layout
-  if (M % TC != 0 || TC * (M / kDiv) > LatFft<T>::kColThreads || 2 * TC * pm > 200 * 1024)
+  constexpr int kDiv = F::kDiv;
+  const size_t pm = size_t(F::len(M)) * sizeof(T);   // one column or row in the F layout
+  if (M % TC != 0 || TC * (M / kDiv) > F::kColThreads || 2 * TC * pm > 200 * 1024)
     return cudaErrorInvalidValue;
   static unsigned long long attr_done = 0;
   if (first_on_device(attr_done)) {
-    const int prow = int(LatFft<T>::len(kFftMaxM) * sizeof(T));
-    cudaFuncSetAttribute(k_src_rows<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, prow);
-    cudaFuncSetAttribute(k_inv_rows<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, prow);
-    cudaFuncSetAttribute(k_conv_cols<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    const int prow = int(F::len(kFftMaxM) * sizeof(T));
+    cudaFuncSetAttribute(k_src_rows<T, F>, cudaFuncAttributeMaxDynamicSharedMemorySize, prow);
+    cudaFuncSetAttribute(k_inv_rows<T, F>, cudaFuncAttributeMaxDynamicSharedMemorySize, prow);
+    cudaFuncSetAttribute(k_conv_cols<T, F>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   }
   // R (2 (L+1) x M) lives in Sd, Vt (n_lat x M) in Sm, V (n_lat x M) back in Sd
   const int64_t stride = d.lattice_rows() * M;
-  k_src_rows<T><<<dim3(d.L + 1, 2, nr), M / kDiv, pm, st>>>(M, d.logM, d.n_lat, d.Ne, d.L, d.occ_of_cell,
+  k_src_rows<T, F><<<dim3(d.L + 1, 2, nr), M / kDiv, pm, st>>>(M, d.logM, d.n_lat, d.Ne, d.L, d.occ_of_cell,
                                                                      d.sigma, d.n_es, d.nocc, d.tw, d.Sd, stride);
   int logMs = 0;
-  const int Ms = short_len<T>(M, d.Ne, d.L, logMs);
-  k_conv_cols<T><<<dim3(M / TC, nr), TC * (M / kDiv), 2 * TC * pm, st>>>(
+  const int Ms = short_len(M, d.Ne, d.L, kDiv, logMs);
+  k_conv_cols<T, F><<<dim3(M / TC, nr), TC * (M / kDiv), 2 * TC * pm, st>>>(
       M, d.logM, d.n_lat, d.Ne, d.L, TC, Ms, logMs, d.Sd, d.Gq, d.Dq, d.tw, d.Sm, stride);
-  k_inv_rows<T><<<dim3(d.n_lat, nr), M / kDiv, pm, st>>>(M, d.logM, d.n_lat, d.tw, d.Sm, d.Sd, stride);
+  k_inv_rows<T, F><<<dim3(d.n_lat, nr), M / kDiv, pm, st>>>(M, d.logM, d.n_lat, d.tw, d.Sm, d.Sd, stride);
   return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t lattice_conv(const ApplyData<T>& d, int nr, cudaStream_t st) {
+  if constexpr (sizeof(T) == 8) {
+    if (d.fft_r4) return lattice_conv_f<T, LatFft4<T>>(d, nr, st);
+  }
+  return lattice_conv_f<T, LatFft<T>>(d, nr, st);
 }
 
 // The lattice convolutions of several instances of one lattice size at once
@@ -582,7 +593,7 @@ __global__ void __launch_bounds__(kFftMaxM / LatFft<T>::kDiv) k_src_rows_multi(c
                                                                               const InstData<T>* __restrict__ I) {
   const int2 w = work[blockIdx.x];
   const ApplyData<T>& d = I[w.x].d;
-  src_row_body<T>(d.M, d.logM, d.n_lat, d.Ne, d.L, d.occ_of_cell, d.sigma, d.n_es, d.tw, d.Sd, w.y, blockIdx.y);
+  src_row_body<T, LatFft<T>>(d.M, d.logM, d.n_lat, d.Ne, d.L, d.occ_of_cell, d.sigma, d.n_es, d.tw, d.Sd, w.y, blockIdx.y);
 }
 
 template <typename T>
@@ -591,8 +602,8 @@ __global__ void __launch_bounds__(kFftMaxM / LatFft<T>::kDiv) k_conv_cols_multi(
   const int2 w = work[blockIdx.x];
   const ApplyData<T>& d = I[w.x].d;
   int logMs = 0;
-  const int Ms = short_len<T>(d.M, d.Ne, d.L, logMs);
-  conv_cols_body<T>(d.M, d.logM, d.n_lat, d.Ne, d.L, 1, Ms, logMs, d.Sd, d.Gq, d.Dq, d.tw, d.Sm, w.y);
+  const int Ms = short_len(d.M, d.Ne, d.L, LatFft<T>::kDiv, logMs);
+  conv_cols_body<T, LatFft<T>>(d.M, d.logM, d.n_lat, d.Ne, d.L, 1, Ms, logMs, d.Sd, d.Gq, d.Dq, d.tw, d.Sm, w.y);
 }
 
 template <typename T>
@@ -600,7 +611,7 @@ __global__ void __launch_bounds__(kFftMaxM / LatFft<T>::kDiv) k_inv_rows_multi(c
                                                                               const InstData<T>* __restrict__ I) {
   const int2 w = work[blockIdx.x];
   const ApplyData<T>& d = I[w.x].d;
-  inv_row_body<T>(d.M, d.logM, d.n_lat, d.tw, d.Sm, d.Sd, w.y);
+  inv_row_body<T, LatFft<T>>(d.M, d.logM, d.n_lat, d.tw, d.Sm, d.Sd, w.y);
 }
 
 template <typename T>

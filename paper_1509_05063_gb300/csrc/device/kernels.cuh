@@ -62,6 +62,7 @@ struct ApplyData {
   bool near_cuda = false;               // complex64, 8 or 16 RHS: CUDA-core near field instead of tensor cores
   bool local_cuda = false;              // complex64, 8 or 16 RHS: CUDA-core local coefficients instead of tensor cores
   bool proj_cuda = false;               // complex64, 8 or 16 RHS: CUDA-core projection instead of tensor cores
+  bool fft_r4 = false;                  // complex64: radix-4 lattice transforms instead of radix 16 (single plans)
   const unsigned char* LAt = nullptr;   // complex64 only: LA in the tensor-core tile layout (local_tc_tiles)
   const T* Wt = nullptr;                // complex64 only: the blocks in the tensor-core tile layout
   const float* tc_rscale = nullptr;     // complex64 only: 1 / (power-of-two scale) of each near-field row

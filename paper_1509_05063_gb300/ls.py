@@ -71,7 +71,7 @@ class SolveInfo(C.Structure):
 class TuneReport(C.Structure):
     _fields_ = [("nrhs", C.c_int), ("conv_cols64", C.c_int), ("conv_cols32", C.c_int), ("group32", C.c_int),
                 ("near_cuda32", C.c_int), ("n_candidates", C.c_int), ("local_cuda32", C.c_int),
-                ("proj_cuda32", C.c_int),
+                ("proj_cuda32", C.c_int), ("fft_radix32", C.c_int),
                 ("ms64_default", C.c_double),
                 ("ms64_best", C.c_double), ("ms32_default", C.c_double), ("ms32_best", C.c_double)]
 
@@ -297,19 +297,21 @@ class Plan:
     def autotune(self, nrhs: int = 16):
         """Time the apply's kernel variants on this plan's GPU and keep the
         fastest (ls_plan_autotune): lattice column-pass width (FP64 and
-        complex64), complex64 right-hand-side group, and tensor or CUDA cores
-        for the near field, the local coefficients and the projection.
+        complex64), complex64 right-hand-side group, tensor or CUDA cores
+        for the near field, the local coefficients and the projection, and
+        the complex64 lattice FFT's radix (16 or 4).
         Returns the choice and the default / best milliseconds."""
         r = TuneReport()
         _check(_lib.ls_plan_autotune(self._h, int(nrhs), C.byref(r)), self._h)
         return {f: getattr(r, f) for f, _ in TuneReport._fields_}
 
     def set_variants(self, conv_cols64: int = 1, conv_cols32: int = 1, group32: int = 16, near_cuda32: int = 0,
-                     local_cuda32: int = 0, proj_cuda32: int = 0, **_ignored):
+                     local_cuda32: int = 0, proj_cuda32: int = 0, fft_radix32: int = 16, **_ignored):
         """Set the kernel variants (ls_plan_set_variants); accepts a dict
         returned by autotune() as keyword arguments."""
         r = TuneReport(conv_cols64=int(conv_cols64), conv_cols32=int(conv_cols32), group32=int(group32),
-                       near_cuda32=int(near_cuda32), local_cuda32=int(local_cuda32), proj_cuda32=int(proj_cuda32))
+                       near_cuda32=int(near_cuda32), local_cuda32=int(local_cuda32), proj_cuda32=int(proj_cuda32),
+                       fft_radix32=int(fft_radix32))
         _check(_lib.ls_plan_set_variants(self._h, C.byref(r)), self._h)
 
     def set_wait_limit(self, polls: int):

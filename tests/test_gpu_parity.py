@@ -142,7 +142,8 @@ def test_every_complex64_unit_variant(kite, nrhs):
     """Pinned by ls_plan_set_variants, each tensor-core / CUDA-core choice for
     the projection (3xTF32), local coefficients (3xTF32) and near field (split
     FP16) reproduces the FP64 oracle within the mixed bound, element by
-    element, and the eight variants agree with one another to FP32 rounding."""
+    element, and the eight variants agree with one another to FP32 rounding;
+    two of them take the radix-4 lattice transforms."""
     from paper_1509_05063_gb300 import LS_MIXED
     U = W.random_density(kite.dz.N, nrhs=nrhs, seed=W.SEED + 13)
     refs = [kite.to_plan(kite.op.apply(U[r])) for r in range(nrhs)]
@@ -151,7 +152,8 @@ def test_every_complex64_unit_variant(kite, nrhs):
     try:
         for var in range(8):
             kite.plan.set_variants(conv_cols32=1 + (var % 2), group32=nrhs, near_cuda32=var & 1,
-                                   local_cuda32=(var >> 1) & 1, proj_cuda32=var >> 2)
+                                   local_cuda32=(var >> 1) & 1, proj_cuda32=var >> 2,
+                                   fft_radix32=4 if var in (3, 4) else 16)
             got = kite.plan.apply(Ud, prec=LS_MIXED).cpu().numpy()
             for r in range(nrhs):
                 check_mixed(got[r], refs[r])
@@ -166,6 +168,8 @@ def test_every_complex64_unit_variant(kite, nrhs):
         kite.plan.set_variants(group32=5)
     with pytest.raises(LSError):
         kite.plan.set_variants(proj_cuda32=2)
+    with pytest.raises(LSError):
+        kite.plan.set_variants(fft_radix32=8)
 
 
 @pytest.mark.parametrize("name", ["disc", "kite"])
@@ -349,6 +353,9 @@ def test_largest_lattice_sampled_rows():
     got16 = plan.apply(Ud.to(torch.complex64), prec=LS_MIXED).cpu().numpy()[:, sel]
     for r in checked:
         check_mixed(got16[r], ref[r])
+    plan.set_variants(fft_radix32=4)            # the radix-4 transform at M = 2048 too
+    got32 = plan.apply(Ud[0].to(torch.complex64), prec=LS_MIXED).cpu().numpy()[sel]
+    check_mixed(got32, ref[0])
     plan.close()
 
 
