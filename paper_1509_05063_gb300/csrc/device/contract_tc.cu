@@ -248,7 +248,7 @@ __global__ void __launch_bounds__(kLT) k_local_tc(ApplyData<float2> d, const flo
 // Equivalent-source projection (Section 3.2: the strengths of cell c solve the
 // fit to the scaled field on the cell's nodes, sigma_c = P_c u_c with P_c the
 // fit's pseudo-inverse folded with the quadrature weights) for R = 8 or 16
-// right-hand sides:  one block per piece (cell k, nodes [jb, je)),
+// right-hand sides:  one block per occupied cell (largest first),
 // D (128 x 2R) = P' (128 x 2n) . [u_hi | u_lo] (2n x 2R) with u
 // interleaved along K (B[r][2j] = Re u_j, B[r][2j + 1] = Im u_j, the layout of
 // u in memory) and the rows of P' built from P_c as it is stored ([node][n_es]):
@@ -258,34 +258,29 @@ __global__ void __launch_bounds__(kLT) k_local_tc(ApplyData<float2> d, const flo
 // MMAs on [B_hi | B_lo] (N = 2R: an MMA of M = 128 needs N >= 16, so the
 // A_lo . B_lo product of R = 8 comes for free; the epilogue adds columns r and
 // R + r).  Nodes are taken 16 per chunk (K = 32 real, four K steps of 8).
-// A cell of one piece writes sigma directly; a cell of several pieces writes
-// per-piece partial sums and the last piece to finish adds them in piece
-// order, as on the CUDA cores.  The apply passes whole cells, largest first:
+// Whole cells, unlike the CUDA-core projection's pieces of at most 128 nodes:
 // the tensor cores take a long cell in stride, and without partial sums no
-// block waits on a merge.
+// block waits on a merge (pieces with a merge ran 8% slower).
 constexpr int kPB = 4096;                // B chunk: 2R <= 32 rows x 128 bytes
 constexpr int kPStage = 2 * kLA + kPB;   // one pipeline stage: P' hi, P' lo, [u_hi | u_lo]
 constexpr int kPSmem = 2 * kPStage + 64;
 
 template <int R>
-__global__ void __launch_bounds__(kLT) k_project_tc(const int4* __restrict__ pieces, const int* __restrict__ piece_off,
-                                                    int nocc, const int64_t* __restrict__ occ_start,
+__global__ void __launch_bounds__(kLT) k_project_tc(const int4* __restrict__ cells, int nocc,
+                                                    const int64_t* __restrict__ occ_start,
                                                     const int64_t* __restrict__ P_off, const float2* __restrict__ P,
                                                     const float2* __restrict__ u, int64_t N,
-                                                    float2* __restrict__ sigma, float2* __restrict__ part,
-                                                    int* __restrict__ count, int n_es, int* __restrict__ tc_err,
+                                                    float2* __restrict__ sigma, int n_es, int* __restrict__ tc_err,
                                                     int spin) {
   extern __shared__ __align__(1024) unsigned char psm[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(psm + 2 * kPStage);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 2);
   int* flag = reinterpret_cast<int*>(tslot + 1);
-  __shared__ int last;
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
-  const int4 pc = pieces[blockIdx.x];
-  const int k = pc.x, p = pc.w >> 16, np = pc.w & 0xffff;
-  const int nc = pc.z - pc.y, nch = (nc + kLChunk - 1) / kLChunk;
-  const int64_t s0 = occ_start[k] + pc.y;
-  const float2* Pk = P + P_off[k] + int64_t(pc.y) * n_es;
+  const int k = cells[blockIdx.x].x;            // (cell, 0, nodes, 1)
+  const int64_t s0 = occ_start[k];
+  const int nc = int(occ_start[k + 1] - s0), nch = (nc + kLChunk - 1) / kLChunk;
+  const float2* Pk = P + P_off[k];
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" :: "r"(ls_u32(tslot)), "r"(32)
@@ -418,9 +413,8 @@ __global__ void __launch_bounds__(kLT) k_project_tc(const int4* __restrict__ pie
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const bool good = *flag == 0 && nch > 0;
   if (*flag && t == 0 && tc_err) atomicExch(tc_err, 1);
-  // a cell of one piece writes sigma ([r][cell][i]); otherwise slot p of the cell ([piece][r][i])
-  float2* out = np == 1 ? sigma + int64_t(k) * n_es : part + (int64_t(piece_off[k]) + p) * R * n_es;
-  const int64_t rs = np == 1 ? int64_t(nocc) * n_es : n_es;
+  float2* out = sigma + int64_t(k) * n_es;      // sigma: [r][cell][i]
+  const int64_t rs = int64_t(nocc) * n_es;
   if (warp < 4) {
     const int m = 32 * warp + lane, o = m & 63, im = m >> 6;
     float v[2 * R];
@@ -443,21 +437,6 @@ __global__ void __launch_bounds__(kLT) k_project_tc(const int4* __restrict__ pie
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(32) : "memory");
   }
-  if (np == 1) return;
-  __threadfence();
-  __syncthreads();
-  if (t == 0) last = atomicAdd(count + k, 1) == np - 1;
-  __syncthreads();
-  if (!last) return;
-  __threadfence();
-  const float2* slots = part + int64_t(piece_off[k]) * R * n_es;
-  for (int e = t; e < R * n_es; e += kLT) {
-    float2 v = __ldcg(slots + e);
-    for (int q = 1; q < np; ++q) v = cadd(v, __ldcg(slots + int64_t(q) * R * n_es + e));
-    const int r = e / n_es, i = e - r * n_es;
-    sigma[(int64_t(r) * nocc + k) * n_es + i] = v;
-  }
-  if (t == 0) count[k] = 0;
 }
 
 // plan time: LA' in the tile layout, per chunk of 16 complex K columns the 64
@@ -518,9 +497,9 @@ cudaError_t project_tc(const ApplyData<float2>& d, const float2* u, cudaStream_t
     if (e != cudaSuccess) return e;
   }
   if (d.n_es <= 0 || d.n_es > 64 || d.nocc <= 0 || !d.cell_pieces) return cudaErrorInvalidValue;
-  // one block per whole cell, largest first: no partial sums (a block streams its cell's chunks)
-  k_project_tc<R><<<d.nocc, kLT, kPSmem, st>>>(d.cell_pieces, d.piece_off, d.nocc, d.occ_start, d.P_off, d.P, u, d.N,
-                                               d.sigma, d.proj_part, d.proj_count, d.n_es, d.tc_err, d.tc_spin);
+  // one block per whole cell, largest first (d.cell_pieces)
+  k_project_tc<R><<<d.nocc, kLT, kPSmem, st>>>(d.cell_pieces, d.nocc, d.occ_start, d.P_off, d.P, u, d.N, d.sigma,
+                                               d.n_es, d.tc_err, d.tc_spin);
   return cudaGetLastError();
 }
 
