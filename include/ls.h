@@ -325,8 +325,10 @@ ls_status ls_plan_autotune(ls_plan plan, int nrhs, ls_tune_report* report);
  * tests.  Every variant gives the same result up to rounding.  A plan whose
  * tables do not fit a tensor-core unit (2 n_fb + 1 > 32 for the local
  * coefficients, n_es > 64 for the projection) keeps the CUDA-core kernel
- * there.  LS_ERR_INVALID on a null argument or a value outside these sets,
- * LS_ERR_UNSUPPORTED for 3-D plans; drops the plan's captured applies. */
+ * there.  LS_ERR_INVALID on a null argument, a value outside these sets or a
+ * column width the plan's lattice size does not fit (shared memory or the
+ * column pass's launch bound), LS_ERR_UNSUPPORTED for 3-D plans; drops the
+ * plan's captured applies. */
 ls_status ls_plan_set_variants(ls_plan plan, const ls_tune_report* variants);
 
 /* Per-stage device timing of ls_apply with CUDA events recorded on the call's

@@ -2366,13 +2366,19 @@ ls_status ls_plan_set_variants(ls_plan plan, const ls_tune_report* v) {
       (v->fft_radix32 != 0 && v->fft_radix32 != 4 && v->fft_radix32 != 16))
     return fail(plan, LS_ERR_INVALID, "ls_plan_set_variants: columns must be 1, 2, 4 or 8, the group 4, 8 or 16, "
                                       "the unit flags 0 or 1, the FFT radix 4 or 16");
+  const bool r4 = v->fft_radix32 == 4;
+  if (!lsd::lattice_cols_fit(true, false, plan->d64.M, v->conv_cols64) ||
+      !lsd::lattice_cols_fit(false, r4, plan->d32.M, v->conv_cols32))
+    return fail(plan, LS_ERR_INVALID, "ls_plan_set_variants: the lattice column pass does not fit " +
+                                          std::to_string(v->conv_cols64) + " / " + std::to_string(v->conv_cols32) +
+                                          " columns per block at lattice size " + std::to_string(plan->d64.M));
   plan->d64.conv_tc = v->conv_cols64;
   plan->d32.conv_tc = v->conv_cols32;
   plan->group32 = v->group32;
   plan->d32.near_cuda = v->near_cuda32 != 0;
   plan->d32.local_cuda = v->local_cuda32 != 0;
   plan->d32.proj_cuda = v->proj_cuda32 != 0;
-  plan->d32.fft_r4 = v->fft_radix32 == 4;
+  plan->d32.fft_r4 = r4;
   plan->graphs.clear();          // captured applies hold the previous variants
   return LS_OK;
 }

@@ -547,15 +547,27 @@ int conv_cols_tc(int) {
   return 1;
 }
 
+// whether the lattice passes run at size M with TC columns per block of the
+// column pass (threads within the launch bound, shared memory within 200 KB)
+template <typename T, class F>
+bool lattice_fits(int M, int TC) {
+  if (M < 256 || M > kFftMaxM || (M & (M - 1)) || TC < 1 || M % TC != 0) return false;
+  const size_t pm = size_t(F::len(M)) * sizeof(T);
+  return TC * (M / F::kDiv) <= F::kColThreads && 2 * TC * pm <= 200 * 1024;
+}
+
+bool lattice_cols_fit(bool fp64, bool radix4, int M, int TC) {
+  if (fp64) return lattice_fits<double2, LatFft<double2>>(M, TC);
+  return radix4 ? lattice_fits<float2, LatFft4<float2>>(M, TC) : lattice_fits<float2, LatFft<float2>>(M, TC);
+}
+
 template <typename T, class F>
 cudaError_t lattice_conv_f(const ApplyData<T>& d, int nr, cudaStream_t st) {
   const int M = d.M;
-  if (M < 256 || M > kFftMaxM || (M & (M - 1))) return cudaErrorInvalidValue;
   const int TC = d.conv_tc > 0 ? d.conv_tc : conv_cols_tc<T>(M);
+  if (!lattice_fits<T, F>(M, TC)) return cudaErrorInvalidValue;
   constexpr int kDiv = F::kDiv;
   const size_t pm = size_t(F::len(M)) * sizeof(T);   // one column or row in the F layout
-  if (M % TC != 0 || TC * (M / kDiv) > F::kColThreads || 2 * TC * pm > 200 * 1024)
-    return cudaErrorInvalidValue;
   static unsigned long long attr_done = 0;
   if (first_on_device(attr_done)) {
     const int prow = int(F::len(kFftMaxM) * sizeof(T));

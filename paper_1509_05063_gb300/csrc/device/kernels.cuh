@@ -124,6 +124,10 @@ size_t local_tc_bytes(int K);
 cudaError_t local_tc_tiles(const float2* LA, int K, int nfb2, unsigned char* LAt, cudaStream_t st);
 template <int R>
 cudaError_t local_coeffs_tc(const ApplyData<float2>& d, cudaStream_t st);
+// Whether a plan's lattice passes run with TC columns per block of the column
+// pass at lattice size M (FP64; complex64 with the radix-4 or radix-16 FFT):
+// the same test the passes make before they launch.
+bool lattice_cols_fit(bool fp64, bool radix4, int M, int TC);
 // Equivalent-source projection of 8 or 16 complex64 RHS on the tensor cores (device/contract_tc.cu,
 // 3xTF32): the sums of k_es_project, one block per whole cell (d.cell_pieces), P_c read as stored;
 // n_es <= 64.
