@@ -96,11 +96,30 @@ void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w) {
 
 // Lagrange weights of the integer nodes s..s+p at t
 void lagrange_row(double t, int64_t s, int p, double* L) {
+  constexpr int kMax = 16;
+  if (p >= kMax) {
+    for (int k = 0; k <= p; ++k) {
+      double v = 1;
+      for (int m = 0; m <= p; ++m)
+        if (m != k) v *= (t - double(s + m)) / double(k - m);
+      L[k] = v;
+    }
+    return;
+  }
+  // L_k = prod_{m != k} (t - s - m) / (k - m): prefix and suffix products of the
+  // differences d_m = t - s - m over the denominator (-1)^(p - k) k! (p - k)!
+  // (exact in double for p < 16), one division per weight instead of p
+  double d[kMax], suf[kMax + 1], fact[kMax];
+  fact[0] = 1;
+  for (int m = 1; m <= p; ++m) fact[m] = fact[m - 1] * m;
+  for (int m = 0; m <= p; ++m) d[m] = t - double(s + m);
+  suf[p + 1] = 1;
+  for (int m = p; m >= 0; --m) suf[m] = suf[m + 1] * d[m];
+  double pre = 1;
   for (int k = 0; k <= p; ++k) {
-    double v = 1;
-    for (int m = 0; m <= p; ++m)
-      if (m != k) v *= (t - double(s + m)) / double(k - m);
-    L[k] = v;
+    const double den = ((p - k) & 1 ? -1.0 : 1.0) * fact[k] * fact[p - k];
+    L[k] = pre * suf[k + 1] / den;
+    pre *= d[k];
   }
 }
 
@@ -306,11 +325,12 @@ inline void scatter(RowAcc& acc, const int64_t* node_of, int na, int nb, int nc,
 struct Win3 {
   int64_t o[3] = {0, 0, 0};
   int n[3] = {0, 0, 0};
-  std::vector<cd> a;
+  std::vector<double> re, im;      // real and imaginary parts apart: the stencil loops vectorise
   void reset(int64_t o0, int64_t o1, int64_t o2, int n0, int n1, int n2) {
     o[0] = o0; o[1] = o1; o[2] = o2;
     n[0] = n0; n[1] = n1; n[2] = n2;
-    a.assign(size_t(n0) * n1 * n2, cd(0.0));
+    re.assign(size_t(n0) * n1 * n2, 0.0);
+    im.assign(size_t(n0) * n1 * n2, 0.0);
   }
   bool inside(const int64_t* st, int pa, int pc) const {
     return st[0] >= o[0] && st[0] + pa < o[0] + n[0] && st[1] >= o[1] && st[1] + pa < o[1] + n[1] &&
@@ -322,8 +342,14 @@ struct Win3 {
       const size_t bi = size_t(st[0] + i - o[0]) * n[1];
       for (int j = 0; j <= pa; ++j) {
         const cd fij = f * (La[i] * Lb[j]);
-        cd* row = &a[(bi + size_t(st[1] + j - o[1])) * n[2] + size_t(st[2] - o[2])];
-        for (int k = 0; k <= pc; ++k) row[k] += fij * Lc[k];
+        const double fr = fij.real(), fi = fij.imag();
+        const size_t r0 = (bi + size_t(st[1] + j - o[1])) * n[2] + size_t(st[2] - o[2]);
+        double* __restrict__ rr = &re[r0];
+        double* __restrict__ ri = &im[r0];
+        for (int k = 0; k <= pc; ++k) {
+          rr[k] += fr * Lc[k];
+          ri[k] += fi * Lc[k];
+        }
       }
     }
   }
@@ -337,7 +363,8 @@ struct Win3 {
         for (int k = 0; k < n[2]; ++k) {
           const int64_t gk = o[2] + k;
           if (gk < 0 || gk >= nc) continue;
-          const cd v = a[(size_t(i) * n[1] + j) * n[2] + k];
+          const size_t e = (size_t(i) * n[1] + j) * n[2] + k;
+          const cd v(re[e], im[e]);
           if (v == 0.0) continue;
           const int64_t nd = node_of[(size_t(gi) * nb + size_t(gj)) * nc + size_t(gk)];
           if (nd >= 0) acc.add(nd, v * factor[nd]);
@@ -527,8 +554,11 @@ void singular_parts(const Ball3& B, double kappa, const Rules3& ru, int64_t qn, 
         for (int j = 0; j < wn; ++j) {
           cd& v = plane[size_t(i) * wn + j];
           if (v == 0.0) continue;
-          cd* dst = &w.a[(size_t(i) * wn + j) * ns + size_t(line_s)];
-          for (int k = 0; k <= ps; ++k) dst[k] += v * Lline[k];
+          const size_t d0 = (size_t(i) * wn + j) * ns + size_t(line_s);
+          for (int k = 0; k <= ps; ++k) {
+            w.re[d0 + k] += v.real() * Lline[k];
+            w.im[d0 + k] += v.imag() * Lline[k];
+          }
           v = 0.0;
         }
       plane_used = false;
